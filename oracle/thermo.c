@@ -1,0 +1,169 @@
+/*
+ * Pointwise physics of the oracle: thermodynamics and saturation adjustment
+ * (Sec. 2), the inviscid flux and the Rusanov numerical flux (Sec. 3.1,
+ * Eq. nonviscFlux) and the Smagorinsky-Lilly closure with the Richardson
+ * correction (Sec. 4, Eqs. smago and richardson).
+ * Test infrastructure only (see oracle.h).
+ */
+#include <math.h>
+#include "oracle.h"
+
+/* Saturation vapour pressure over liquid from the Clausius-Clapeyron relation
+ * integrated with constant heat capacities (Sec. 2.6 cites Romps 2008 for
+ * this closed form; values of p_tr, T_tr are a reading):
+ *   p_v*(T) = p_tr (T/T_tr)^{(c_pv - c_pl)/R_v}
+ *             exp[ (L_v0 - (c_pv - c_pl) T_0)/R_v (1/T_tr - 1/T) ],
+ * with c_pv = c_vv + R_v and c_pl = c_vl. */
+double orc_pvsat(const orc_params *p, double T) {
+  double cpv = p->cvv + p->Rv;
+  double cpl = p->cvl;
+  double dcp = cpv - cpl;
+  return p->ptr * pow(T / p->Ttr, dcp / p->Rv) *
+         exp((p->Lv0 - dcp * p->T0) / p->Rv * (1.0 / p->Ttr - 1.0 / T));
+}
+
+/* Saturation specific humidity q_sat = p_v* / (rho R_v T) (ideal-gas vapour). */
+double orc_qsat(const orc_params *p, double T, double rho) {
+  return orc_pvsat(p, T) / (rho * p->Rv * T);
+}
+
+/* I(T, q) = (1-q_t) I_d + q_v I_v + q_l I_l  (Eqs. total_internal_energy,
+ * internal_energies; q_i = 0), I_v0 = L_v0 - R_v T_0. */
+double orc_internal_energy(const orc_params *p, double T, double qt, double ql) {
+  double qv = qt - ql;
+  double Iv0 = p->Lv0 - p->Rv * p->T0;
+  double Id = p->cvd * (T - p->T0);
+  double Iv = p->cvv * (T - p->T0) + Iv0;
+  double Il = p->cvl * (T - p->T0);
+  return (1.0 - qt) * Id + qv * Iv + ql * Il;
+}
+
+/* Saturation adjustment (Eq. sat_adjustment): find T with I*(T; rho, q_t) = I.
+ * Unsaturated: q_v = q_t, closed form T = T_0 + (I - q_t I_v0)/c_vm.
+ * Saturated: Newton on f(T) = I*(T) - I with q_v = q_sat(T, rho),
+ * q_l = q_t - q_v, and the analytic derivative
+ *   f'(T) = c_vm + dq_sat/dT [ (c_vv - c_vl)(T - T_0) + I_v0 ],
+ *   dq_sat/dT = q_sat ( L(T)/(R_v T^2) - 1/T ),  L(T) = L_v0 + (c_pv - c_pl)(T - T_0).
+ * Reading: liquid only (all cases are warm); stop when |dT| <= 1e-10 K, cap 50. */
+int orc_saturation_adjustment(const orc_params *p, double rho, double qt, double I, double *T, double *ql) {
+  double Iv0 = p->Lv0 - p->Rv * p->T0;
+  double cvm_u = (1.0 - qt) * p->cvd + qt * p->cvv;
+  double Tu = p->T0 + (I - qt * Iv0) / cvm_u;
+  if (!p->moist || qt <= orc_qsat(p, Tu, rho)) {
+    *T = Tu;
+    *ql = 0.0;
+    return 0;
+  }
+  double cpv = p->cvv + p->Rv;
+  double dcp = cpv - p->cvl;
+  double Tn = Tu;
+  for (int it = 1; it <= 50; ++it) {
+    double qs = orc_qsat(p, Tn, rho);
+    double qv = qs;
+    double qln = qt - qv;
+    double cvm = (1.0 - qt) * p->cvd + qv * p->cvv + qln * p->cvl;
+    double f = cvm * (Tn - p->T0) + qv * Iv0 - I;
+    double L = p->Lv0 + dcp * (Tn - p->T0);
+    double dqs = qs * (L / (p->Rv * Tn * Tn) - 1.0 / Tn);
+    double fp = cvm + dqs * ((p->cvv - p->cvl) * (Tn - p->T0) + Iv0);
+    double dT = f / fp;
+    Tn -= dT;
+    if (fabs(dT) <= 1e-10) {
+      double qsf = orc_qsat(p, Tn, rho);
+      *T = Tn;
+      *ql = qt - qsf;
+      if (*ql < 0.0) *ql = 0.0;
+      return it;
+    }
+  }
+  *T = Tn;
+  *ql = qt - orc_qsat(p, Tn, rho);
+  return -1;
+}
+
+/* Diagnostic state of one node (Sec. 2): u = rho u / rho, q_t, e_tot,
+ * I = e_tot - |u|^2/2 - g z (Eq. total_energy_def with Phi = g z),
+ * saturation adjustment, R_m (Eq. R_m), p = rho R_m T (Eq. eos),
+ * c_vm, c_pm = c_vm + R_m, sound speed c = sqrt(c_pm/c_vm R_m T),
+ * total enthalpy h_tot = e_tot + R_m T, potential temperature with the dry
+ * Exner function (p/p0)^{R_d/c_pd} and theta_v = theta R_m / R_d. */
+int orc_thermo(const orc_params *p, const double Y[6], double z, orc_thermo_state *s) {
+  s->rho = Y[0];
+  for (int d = 0; d < 3; ++d) s->u[d] = Y[1 + d] / Y[0];
+  s->etot = Y[4] / Y[0];
+  s->qt = Y[5] / Y[0];
+  double ke = 0.5 * (s->u[0] * s->u[0] + s->u[1] * s->u[1] + s->u[2] * s->u[2]);
+  s->I = s->etot - ke - p->g * z;
+  int it = orc_saturation_adjustment(p, s->rho, s->qt, s->I, &s->T, &s->ql);
+  s->newton = it;
+  s->qv = s->qt - s->ql;
+  s->Rm = p->Rd * (1.0 - s->qt) + p->Rv * s->qv;
+  s->cvm = (1.0 - s->qt) * p->cvd + s->qv * p->cvv + s->ql * p->cvl;
+  s->cpm = s->cvm + s->Rm;
+  s->p = s->rho * s->Rm * s->T;
+  s->c = sqrt(s->cpm / s->cvm * s->Rm * s->T);
+  s->htot = s->etot + s->Rm * s->T;
+  double cpd = p->cvd + p->Rd;
+  double exner = pow(s->p / p->p0, p->Rd / cpd);
+  s->theta = s->T / exner;
+  s->thetav = s->theta * s->Rm / p->Rd;
+  return it < 0 ? -1 : 0;
+}
+
+/* n . F1(Y): F1 = [rho u, rho u (x) u + (p - p_r) I_3, (rho e + p) u, rho q_t u]
+ * (Eqs. mass, moisture, momentum and energy_balance, advective parts). */
+void orc_flux1_normal(const orc_params *p, const double Y[6], double z, double pr, const double n[3], double out[6]) {
+  orc_thermo_state s;
+  orc_thermo(p, Y, z, &s);
+  double un = s.u[0] * n[0] + s.u[1] * n[1] + s.u[2] * n[2];
+  out[0] = Y[0] * un;
+  for (int j = 0; j < 3; ++j) out[1 + j] = Y[1 + j] * un + (s.p - pr) * n[j];
+  out[4] = (Y[4] + s.p) * un;
+  out[5] = Y[5] * un;
+}
+
+/* Rusanov flux, Eq. nonviscFlux with the standard reading of its garbled
+ * dissipation term:  n.F* = 1/2 n.(F(Y-) + F(Y+)) + lambda/2 (Y- - Y+),
+ * lambda = max over both sides of |u.n| + c. */
+void orc_rusanov(const orc_params *p, const double Ym[6], const double Yp[6], double z, double pr,
+                 const double n[3], double out[6]) {
+  double fm[6], fp[6];
+  orc_flux1_normal(p, Ym, z, pr, n, fm);
+  orc_flux1_normal(p, Yp, z, pr, n, fp);
+  orc_thermo_state sm, sp;
+  orc_thermo(p, Ym, z, &sm);
+  orc_thermo(p, Yp, z, &sp);
+  double lm = fabs(sm.u[0] * n[0] + sm.u[1] * n[1] + sm.u[2] * n[2]) + sm.c;
+  double lp = fabs(sp.u[0] * n[0] + sp.u[1] * n[1] + sp.u[2] * n[2]) + sp.c;
+  double lam = lm > lp ? lm : lp;
+  for (int v = 0; v < 6; ++v) out[v] = 0.5 * (fm[v] + fp[v]) + 0.5 * lam * (Ym[v] - Yp[v]);
+}
+
+/* Smagorinsky-Lilly eddy viscosity nu_t = (C_s Delta)^2 |S| f_b with
+ * S = sym(grad u) (Eq. strain_rate), |S| = sqrt(2 S_ij S_ij) (Eq. smago) and
+ * f_b the Richardson correction (Eq. richardson):
+ *   Ri = (g/theta_v d theta_v/dz) / |S|^2,
+ *   f_b = 1 for Ri <= 0, max(0, 1 - Ri/Pr_t)^{1/4} otherwise.
+ * Reading: nu_t = 0 when |S| = 0. */
+double orc_smagorinsky(const orc_params *p, const double gu[9], double dthvdz, double thv, double Delta) {
+  double S2 = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double Sij = 0.5 * (gu[3 * i + j] + gu[3 * j + i]);
+      S2 += Sij * Sij;
+    }
+  double Smag2 = 2.0 * S2;
+  if (Smag2 == 0.0) return 0.0;
+  double Smag = sqrt(Smag2);
+  double fb = 1.0;
+  if (p->richardson) {
+    double N2 = p->g / thv * dthvdz;
+    double Ri = N2 / Smag2;
+    if (Ri > 0.0) {
+      double a = 1.0 - Ri / p->Prt;
+      fb = a > 0.0 ? pow(a, 0.25) : 0.0;
+    }
+  }
+  double l = p->Cs * Delta;
+  return l * l * Smag * fb;
+}

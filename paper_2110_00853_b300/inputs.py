@@ -1,0 +1,141 @@
+"""Seeded synthetic workloads: mesh sizes, case parameters and random inputs.
+
+This module holds no arithmetic of the method.  It only states the
+synthetic configurations (mesh, physical set-up, seeds) and draws the random
+tables a case needs; both the CUDA path and the CPU oracle evaluate the
+initial states from these descriptions with their own code.
+
+Configurations (sizes as in the workload list of the project):
+  c1  dry 3D warm bubble, 4x4x4 elements, N=4, 2 km cube
+  c2  moist convective layer, 32x32x16 elements, 6.4x6.4x3.2 km, surface fluxes
+  c3  flow over a Gaussian ridge, warped 128x16x64 elements, 40x4x20 km
+  c4  learned-closure training: coarse c2 grid, fine 128x128x64 elements
+  c5  throughput box, 160x160x80 elements (256M nodes), stratified, random-phase
+      k^-5/3 velocity
+The paper's own BOMEX case needs an external case definition that is not
+reproduced; c2 is a synthetic stand-in with the shape the workload list gives.
+"""
+import math
+
+import numpy as np
+
+
+def mesh(name, N=4):
+    """Mesh description for a named configuration."""
+    m = dict(N=N, x0=0.0, y0=0.0, z0=0.0, periodic=(1, 1, 0), warp=False, hill_h=0.0, hill_a=1.0, hill_xc=0.0)
+    if name == "c1":
+        m.update(nex=4, ney=4, nez=4, Lx=2000.0, Ly=2000.0, Lz=2000.0)
+    elif name == "c2":
+        m.update(nex=32, ney=32, nez=16, Lx=6400.0, Ly=6400.0, Lz=3200.0)
+    elif name == "c3":
+        m.update(nex=128, ney=16, nez=64, Lx=40000.0, Ly=4000.0, Lz=20000.0, warp=True, hill_h=400.0,
+                 hill_a=1000.0, hill_xc=20000.0)
+    elif name == "c4fine":
+        m.update(nex=128, ney=128, nez=64, Lx=6400.0, Ly=6400.0, Lz=3200.0)
+    elif name == "c5":
+        m.update(nex=160, ney=160, nez=80, Lx=32000.0, Ly=32000.0, Lz=16000.0)
+    else:
+        raise ValueError(name)
+    return m
+
+
+def sub_mesh(name, nex, ney, nez, N=4):
+    """A mesh of the same element size as `name` but with fewer elements
+    (same per-node work; used for the CPU baseline and reduced parity cases)."""
+    m = mesh(name, N=N)
+    for k, n, L in (("nex", nex, "Lx"), ("ney", ney, "Ly"), ("nez", nez, "Lz")):
+        m[L] = m[L] / m[k] * n
+        m[k] = n
+    return m
+
+
+def physics(name, closure="sl", moist=None):
+    """Physical parameters of a configuration (closure, moisture, sponge,
+    surface fluxes, time step).  Thermodynamic constants are not part of this
+    description: each side carries the paper's Table t:constants itself."""
+    p = dict(closure=closure, Cs=0.21, Prt=1.0 / 3.0, richardson=True, moist=False, sponge_alpha=0.0,
+             sponge_zs=0.0, sponge_gamma=2.0, u_relax=(0.0, 0.0, 0.0), lateral_sponge_frac=0.0,
+             surface_flux=False, shf=0.0, lhf=0.0, Omega=(0.0, 0.0, 0.0), dt=0.02)
+    if name == "c1":
+        pass
+    elif name in ("c2", "c4fine"):
+        p.update(moist=True, sponge_alpha=0.5, sponge_zs=0.75 * 3200.0, surface_flux=True, shf=9.5, lhf=147.2)
+    elif name == "c3":
+        p.update(sponge_alpha=0.5, sponge_zs=0.8 * 20000.0, u_relax=(10.0, 0.0, 0.0), lateral_sponge_frac=0.2)
+    elif name == "c5":
+        p.update(moist=True)
+    else:
+        raise ValueError(name)
+    if moist is not None:
+        p["moist"] = bool(moist)
+    return p
+
+
+def case(name, moist=None, modes=None):
+    """Initial-state description of a configuration."""
+    c = dict(seed=0, theta0=300.0, dtheta=0.0, r0=1.0, xc=0.0, yc=0.0, zc=0.0, noise_theta=0.0, noise_qt=0.0,
+             noise_zmax=-1.0, NBV=0.0, u0=(0.0, 0.0, 0.0), qt_sfc=0.0, qt_ml=0.0, z_ml=1.0, qt_top=0.0,
+             dthdz_above=0.0, vortex_beta=0.0, vortex_R=1.0, vortex_U=0.0, vortex_T=300.0, vortex_rho=1.0,
+             moist=False, qt_H=2000.0)
+    if name == "c1":
+        # +2 K cosine bubble of radius 2 km/4 centred at z = 0.35 km, +-0.01 K noise
+        c.update(id=1, seed=1, dtheta=2.0, r0=500.0, xc=1000.0, yc=1000.0, zc=350.0, noise_theta=0.01,
+                 noise_zmax=1.0e30)
+    elif name in ("c2", "c4fine"):
+        # theta_l mixed to 520 m then +3.85 K/km; q_t 17 -> 16.3 g/kg in the
+        # mixed layer, then linear to 4 g/kg at the lid (our choice); noise
+        # +-0.1 K / +-0.025 g/kg below 1.6 km.  theta_sfc = 297 K is our
+        # choice: it puts a saturated layer near the mixed-layer top.
+        c.update(id=2, seed=2 if name == "c2" else 4, theta0=297.0, z_ml=520.0, dthdz_above=3.85e-3, qt_sfc=17.0e-3,
+                 qt_ml=16.3e-3, qt_top=4.0e-3, noise_theta=0.1, noise_qt=0.025e-3, noise_zmax=1600.0, moist=True)
+    elif name == "c3":
+        c.update(id=3, NBV=0.01, u0=(10.0, 0.0, 0.0))
+    elif name == "c5":
+        c.update(id=5, seed=5, NBV=0.01, noise_theta=0.1, noise_qt=0.025e-3, noise_zmax=1600.0, qt_sfc=16.0e-3,
+                 qt_H=2000.0, moist=True)
+        if modes is None:
+            modes = velocity_modes(32000.0, 32000.0, 16000.0, seed=5)
+        c["modes"] = modes
+    else:
+        raise ValueError(name)
+    if moist is not None:
+        c["moist"] = bool(moist)
+    return c
+
+
+def velocity_modes(Lx, Ly, Lz, nmodes=1000, urms=1.0, kmin=1, kmax=24, seed=5):
+    """Random-phase solenoidal velocity table for the throughput box.
+
+    Rows (kx, ky, kz, ax, ay, az, phase): u(x) = sum_m a_m cos(k_m . x + phase_m)
+    with integer horizontal wavenumbers (periodic in x, y), amplitude vectors
+    orthogonal to k (divergence free), shell energies E(k) ~ k^-5/3 and the
+    whole table scaled so that the expected rms speed is `urms`."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    shells = np.arange(kmin, kmax + 1)
+    per_shell = np.full(shells.size, nmodes // shells.size)
+    per_shell[: nmodes - per_shell.sum()] += 1
+    for ks, cnt in zip(shells, per_shell):
+        energy = float(ks) ** (-5.0 / 3.0)
+        for _ in range(cnt):
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+            n = np.round(d * ks).astype(int)
+            if not n.any():
+                n[0] = 1
+            k = 2 * math.pi * np.array([n[0] / Lx, n[1] / Ly, n[2] / (2 * Lz)])
+            a = rng.normal(size=3)
+            a -= a.dot(k) / k.dot(k) * k
+            a /= np.linalg.norm(a)
+            rows.append([k[0], k[1], k[2], *(a * math.sqrt(energy / cnt)), rng.uniform(0, 2 * math.pi)])
+    t = np.array(rows)
+    # expected mean of |u|^2 for random phases is sum |a|^2 / 2
+    ms = 0.5 * (t[:, 3:6] ** 2).sum()
+    t[:, 3:6] *= urms / math.sqrt(ms)
+    return t
+
+
+def random_state_perturbation(shape, seed, amplitude):
+    """Seeded uniform noise in [-amplitude, amplitude) for fuzz tests."""
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(-1.0, 1.0, size=shape) * amplitude).astype(np.float64)

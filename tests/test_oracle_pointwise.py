@@ -1,0 +1,257 @@
+"""Pins of the oracle's pointwise pieces against what the paper and the
+mathematics fix: LGL closed forms and exactness (Sec. 3.1), the constants
+table (Table t:constants), the Clausius-Clapeyron closed form and the
+saturation-adjustment round trip (Sec. 2), Rusanov consistency and
+conservation (Eq. nonviscFlux), Smagorinsky-Lilly and Richardson closed forms
+(Sec. 4), the LSRK(5,4) stability polynomial (Sec. 3.2), the MLP gradient and
+the SplitMix64 generator."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read(name):
+    rows = []
+    for line in open(os.path.join(GOLD, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append(line.split())
+    return rows
+
+
+# ------------------------------------------------------------------ LGL
+
+def test_lgl_closed_form_n4(orc):
+    xi, w, D = orc.lgl(4)
+    gold = np.array([[float(r[1]), float(r[2])] for r in _read("lgl_n4.txt")])
+    assert np.allclose(xi, gold[:, 0], atol=1e-15, rtol=0)
+    assert np.allclose(w, gold[:, 1], atol=1e-15, rtol=0)
+    assert abs(xi[3] - math.sqrt(3.0 / 7.0)) < 1e-15
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+def test_lgl_derivative_exact_on_polynomials(orc, N):
+    xi, w, D = orc.lgl(N)
+    for m in range(N + 1):
+        f = xi ** m
+        df = m * xi ** (m - 1) if m > 0 else np.zeros_like(xi)
+        assert np.abs(D @ f - df).max() < 1e-12 * max(1, m * m)
+    # quadrature exact to degree 2N-1
+    for m in range(2 * N):
+        exact = 0.0 if m % 2 else 2.0 / (m + 1)
+        assert abs((w * xi ** m).sum() - exact) < 1e-14
+    assert np.abs(D.sum(axis=1)).max() < 1e-13
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 6])
+def test_lgl_summation_by_parts(orc, N):
+    xi, w, D = orc.lgl(N)
+    Qm = np.diag(w) @ D
+    B = np.zeros((N + 1, N + 1))
+    B[0, 0], B[N, N] = -1.0, 1.0
+    assert np.abs(Qm + Qm.T - B).max() < 1e-13
+
+
+# ------------------------------------------------------------------ constants
+
+def test_constants_table(orc):
+    for name, val, *_unit in _read("constants.txt"):
+        assert orc.CONSTANTS[name] == float(val), name
+
+
+# ------------------------------------------------------------------ thermodynamics
+
+def test_pvsat_triple_point_and_clausius_clapeyron(orc):
+    P = orc.make_params(moist=True)
+    assert abs(orc.pvsat(P, P.Ttr) - P.ptr) < 1e-12
+    for T in (250.0, 273.16, 290.0, 300.0, 310.0):
+        h = 1e-3
+        dln = (math.log(orc.pvsat(P, T + h)) - math.log(orc.pvsat(P, T - h))) / (2 * h)
+        L = P.Lv0 + (P.cvv + P.Rv - P.cvl) * (T - P.T0)
+        assert abs(dln - L / (P.Rv * T * T)) < 1e-8 * dln
+
+
+def test_pvsat_physical_magnitude(orc):
+    # Saturation vapour pressure over liquid water near 300 K is about 3.5 kPa
+    # and about 2.3 kPa near 293 K (standard psychrometric values); the closed
+    # form must land within a few percent of these.
+    P = orc.make_params(moist=True)
+    assert abs(orc.pvsat(P, 300.0) / 3537.0 - 1.0) < 0.03
+    assert abs(orc.pvsat(P, 293.15) / 2339.0 - 1.0) < 0.03
+
+
+def test_internal_energy_definition(orc):
+    P = orc.make_params(moist=True)
+    # dry air: I = c_vd (T - T0); vapour carries I_v0 = L_v0 - R_v T0 at T0
+    assert abs(orc.internal_energy(P, 300.0, 0.0, 0.0) - 717.5 * (300.0 - 273.16)) < 1e-9
+    Iv0 = 2.5008e6 - 462.0 * 273.16
+    assert abs(orc.internal_energy(P, 273.16, 1.0, 0.0) - Iv0) < 1e-6
+    assert abs(orc.internal_energy(P, 273.16, 1.0, 1.0)) < 1e-9
+
+
+def test_saturation_adjustment_round_trip(orc):
+    P = orc.make_params(moist=True)
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        T = rng.uniform(275.0, 305.0)
+        rho = rng.uniform(0.8, 1.25)
+        qs = orc.qsat(P, T, rho)
+        if rng.uniform() < 0.5:
+            qt = qs * rng.uniform(1.0001, 1.2)       # saturated, with condensate
+            ql = qt - qs
+        else:
+            qt = qs * rng.uniform(0.2, 0.999)        # unsaturated
+            ql = 0.0
+        I = orc.internal_energy(P, T, qt, ql)
+        T2, ql2, it = orc.saturation_adjustment(P, rho, qt, I)
+        assert it >= 0
+        assert abs(T2 - T) < 1e-9 * T
+        assert abs(ql2 - ql) < 1e-12
+        if ql == 0.0:
+            assert it == 0
+            cvm = (1 - qt) * P.cvd + qt * P.cvv
+            assert abs(T2 - (P.T0 + (I - qt * (P.Lv0 - P.Rv * P.T0)) / cvm)) < 1e-12 * T
+
+
+# ------------------------------------------------------------------ fluxes
+
+def _state(orc, P, T, qt, rho, u, z):
+    I = orc.internal_energy(P, T, qt, 0.0)
+    return np.array([rho, rho * u[0], rho * u[1], rho * u[2], rho * (I + 0.5 * np.dot(u, u) + P.g * z), rho * qt])
+
+
+def test_inviscid_flux_closed_form(orc):
+    P = orc.make_params(moist=True)
+    T, qt, rho, z, pr = 290.0, 0.005, 1.1, 300.0, 9.0e4
+    u = np.array([3.0, -2.0, 0.5])
+    Y = _state(orc, P, T, qt, rho, u, z)
+    p = rho * (P.Rd * (1 - qt) + P.Rv * qt) * T     # Eq. eos, unsaturated
+    for n in np.eye(3):
+        f = orc.flux1_normal(P, Y, z, pr, n)
+        un = u @ n
+        assert abs(f[0] - rho * un) < 1e-12
+        assert np.allclose(f[1:4], rho * u * un + (p - pr) * n, rtol=1e-12, atol=1e-9)
+        assert abs(f[4] - (Y[4] + p) * un) < 1e-9 * abs(Y[4] * un)
+        assert abs(f[5] - rho * qt * un) < 1e-14
+
+
+def test_rusanov_consistency_and_conservation(orc):
+    P = orc.make_params(moist=True)
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        Ym = _state(orc, P, rng.uniform(280, 300), rng.uniform(0, 0.01), rng.uniform(0.9, 1.2),
+                    rng.normal(size=3) * 5, 500.0)
+        Yp = _state(orc, P, rng.uniform(280, 300), rng.uniform(0, 0.01), rng.uniform(0.9, 1.2),
+                    rng.normal(size=3) * 5, 500.0)
+        # consistency: F*(Y, Y, n) = n.F(Y)
+        assert np.allclose(orc.rusanov(P, Ym, Ym, 500.0, 9.5e4, n), orc.flux1_normal(P, Ym, 500.0, 9.5e4, n),
+                           rtol=1e-14, atol=1e-10)
+        # conservation: F*(Y-, Y+, n) = -F*(Y+, Y-, -n), exactly
+        a = orc.rusanov(P, Ym, Yp, 500.0, 9.5e4, n)
+        b = orc.rusanov(P, Yp, Ym, 500.0, 9.5e4, -n)
+        assert np.array_equal(a, -b)
+        # dissipation is upwinding: jump in rho times lambda/2 >= sound speed/2
+        f0 = 0.5 * (orc.flux1_normal(P, Ym, 500.0, 9.5e4, n)[0] + orc.flux1_normal(P, Yp, 500.0, 9.5e4, n)[0])
+        lam = 2 * (a[0] - f0) / (Ym[0] - Yp[0])
+        assert lam > 300.0
+
+
+# ------------------------------------------------------------------ closure
+
+def test_smagorinsky_simple_shear(orc):
+    P = orc.make_params(Cs=0.21, richardson=True)
+    gamma, Delta = 0.02, 25.0
+    gu = np.zeros((3, 3))
+    gu[0, 2] = gamma                  # u = gamma z: S_13 = S_31 = gamma/2, |S| = gamma
+    assert abs(orc.smagorinsky(P, gu, 0.0, 300.0, Delta) - (0.21 * Delta) ** 2 * gamma) < 1e-15
+    # pure rotation has no strain
+    rot = np.array([[0, 1.0, 0], [-1.0, 0, 0], [0, 0, 0]])
+    assert orc.smagorinsky(P, rot, 0.0, 300.0, Delta) == 0.0
+
+
+def test_richardson_correction(orc):
+    P = orc.make_params(Cs=0.2, richardson=True)
+    gamma, Delta, thv = 0.01, 10.0, 300.0
+    gu = np.zeros((3, 3))
+    gu[0, 2] = gamma
+    base = (0.2 * Delta) ** 2 * gamma
+    for Ri in (-1.0, 0.0, 0.1, 0.25, 0.33, 0.34, 0.5):
+        dthdz = Ri * gamma * gamma * thv / P.g
+        fb = 1.0 if Ri <= 0 else max(0.0, 1.0 - 3.0 * Ri) ** 0.25
+        assert abs(orc.smagorinsky(P, gu, dthdz, thv, Delta) - base * fb) < 1e-12 * base
+
+
+# ------------------------------------------------------------------ LSRK(5,4)
+
+def test_lsrk54_stability_polynomial(orc):
+    A, B, c = orc.lsrk54_coefficients()
+    # stage times are consistent: c_s = sum of the weights reached so far
+    assert abs(B[0] - c[1]) < 1e-16
+    for z in (-0.3, -1.0 + 0.5j, 0.7j, -2.5, 1.2 - 0.4j):
+        y, dy = 1.0 + 0j, 0j
+        for s in range(5):
+            dy = A[s] * dy + z * y
+            y = y + B[s] * dy
+        Rz = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24 + z ** 5 / 200
+        assert abs(y - Rz) < 1e-10 * max(1, abs(Rz))
+
+
+# ------------------------------------------------------------------ MLP
+
+def _rand_w(rng, scale=0.3):
+    return dict(W1=rng.normal(size=(64, 13)) * scale, b1=rng.normal(size=64) * 0.1,
+                W2=rng.normal(size=(64, 64)) * scale / 2, b2=rng.normal(size=64) * 0.1,
+                W3=rng.normal(size=(2, 64)) * scale, b3=rng.normal(size=2) * 0.1)
+
+
+def test_mlp_forward_silu_closed_form(orc):
+    W = dict(W1=np.zeros((64, 13)), b1=np.full(64, 0.7), W2=np.zeros((64, 64)), b2=np.full(64, -1.3),
+             W3=np.ones((2, 64)), b3=np.array([0.5, -0.5]))
+    silu = lambda a: a / (1 + math.exp(-a))
+    Y = orc.mlp_forward(np.zeros((1, 13)), W)
+    assert abs(Y[0, 0] - (64 * silu(-1.3) + 0.5)) < 1e-12
+
+
+def test_mlp_gradient_finite_difference(orc):
+    rng = np.random.default_rng(11)
+    W = _rand_w(rng)
+    X = rng.normal(size=(17, 13))
+    T = rng.normal(size=(17, 2))
+    loss, g = orc.mlp_loss_grad(X, T, W)
+    for key in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        flat = W[key].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            h = 1e-5
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = orc.mlp_loss_grad(X, T, W)
+            flat[idx] = old - h
+            lm, _ = orc.mlp_loss_grad(X, T, W)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            an = g[key].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-7 * max(1e-3, abs(an)), (key, idx, fd, an)
+
+
+def test_adam_first_step(orc):
+    theta = np.array([1.0, -2.0, 3.0])
+    g = np.array([0.5, -4.0, 1e-3])
+    m, v = np.zeros(3), np.zeros(3)
+    orc.adam(theta, g, m, v, 1, lr=0.01, eps=1e-12)
+    # bias-corrected first step moves each parameter by lr * sign(g)
+    assert np.allclose(theta, [0.99, -1.99, 2.99], atol=1e-9)
+
+
+# ------------------------------------------------------------------ generator
+
+def test_splitmix64_published_vector(orc):
+    # First output of SplitMix64 seeded with 0 is 0xE220A8397B1DCDAF; the
+    # uniform double keeps its top 53 bits.
+    assert orc.uniform(0, 0) == (0xE220A8397B1DCDAF >> 11) * 2.0 ** -53
+    assert orc.uniform(0, 1) == (0x6E789E6AA1B965F4 >> 11) * 2.0 ** -53
