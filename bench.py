@@ -1,0 +1,284 @@
+"""Throughput benchmark of the DG-LES hot path on B300.
+
+Metric: DG node-stage updates per second (one node advanced through one
+LSRK(5,4) stage: a full right-hand-side evaluation plus the stage update) on
+the throughput box (160 x 160 x 80 elements, N = 4, 256M nodes), and the HBM
+roofline fraction of the dominant kernel.  A step is one LSRK(5,4) step
+(5 stages) over the whole box; inputs are resident in HBM and much larger than
+L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cmles|reference]
+
+--impl reference times the FP64 CPU oracle (the method's plain reference
+implementation) on a bounded sub-box of the same workload on the host cores.
+With N > 1 (torchrun) each rank runs an independent replica of the box on its
+own GPU (weak scaling, no data-path collective); rank 0 prints the line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2110_00853_b300 import inputs as I  # noqa: E402
+
+WORKLOAD = "c5"
+STAGES = 5
+METRIC = "DG node-stage updates/s at 1 B300 and HBM roofline %, FP32+learned vs FP64 plain"
+# algorithmic bytes per node for each kernel launch (compulsory traffic):
+#   gradient pass: read Q, write F2 (15 words) and aux (2 words)
+#   flux/update pass: read Q, F2, aux, read+write dQ, write Q_out
+BYTES = {
+    "fp64": {"grad": (6 + 15 + 2) * 8, "rhs": (6 + 15 + 2 + 12 + 6) * 8},
+}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6400.0), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_variant(name, precision, closure, steps, warmup, world, rank, torch):
+    from paper_2110_00853_b300 import cmles
+    mesh, phys, case = I.mesh(WORKLOAD), I.physics(WORKLOAD, closure=closure), I.case(WORKLOAD)
+    G = cmles.Solver(mesh, phys, precision=precision)
+    G.init_case(case)
+    G.step(warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = G.launch_count()
+    G.enable_timing(True)
+    G.kernel_times()  # reset counters
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    torch.cuda.synchronize()
+    e0.record(s)
+    G.step(steps)
+    e1.record(s)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    kt = G.kernel_times()
+    launches = G.launch_count() - launches0
+    G.enable_timing(False)
+    diag = G.diagnostics(raise_on_error=False)
+    nodes = G.E * G.Np
+    G.close()
+    del G
+    torch.cuda.empty_cache()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return dict(name=name, ms=ms, kt=kt, launches=launches, nodes=nodes, clocks=clocks,
+                finite=not diag["nonfinite"], satadj_failures=diag["satadj_failures"])
+
+
+def run_e2e(precision, closure, steps, torch):
+    """Same metric through the C ABI with host buffers: every step uploads the
+    state from pinned host memory, advances one LSRK step and reads back the
+    budget diagnostics."""
+    from paper_2110_00853_b300 import cmles
+    mesh, phys, case = I.mesh(WORKLOAD), I.physics(WORKLOAD, closure=closure), I.case(WORKLOAD)
+    G = cmles.Solver(mesh, phys, precision=precision)
+    G.init_case(case)
+    host = G.get_state_host()
+    G.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        G.set_state_host(host)
+        G.step(1)
+        G.diagnostics(raise_on_error=False)
+    t1 = time.perf_counter()
+    nodes = G.E * G.Np
+    h2d = nodes * 6 * 8
+    G.close()
+    del host, G
+    torch.cuda.empty_cache()
+    sec = (t1 - t0) / steps
+    return dict(value=nodes * STAGES / sec, unit="node-stage/s", h2d_bytes_per_step=h2d,
+                d2h_bytes_per_step=7 * 8 + 16 * 4)
+
+
+def cpu_baseline(max_seconds=20.0):
+    """The FP64 CPU oracle, as it stands, on a sub-box of the throughput
+    workload (same element size and physics, fewer elements)."""
+    from oracle import oracle as O
+    n = (20, 20, 16)
+    m = I.sub_mesh(WORKLOAD, *n)
+    c = I.case(WORKLOAD)
+    c["modes"] = I.velocity_modes(m["Lx"], m["Ly"], m["Lz"], nmodes=200, seed=5)
+    S, Q, rr, pr, _ = O.from_inputs(m, I.physics(WORKLOAD), c)
+    S.lsrk54(Q, 1, 0.02)   # warm-up
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        Q, _ = S.lsrk54(Q, 1, 0.02)
+        steps += 1
+        if time.perf_counter() - t0 > max_seconds / 2 or steps >= 4:
+            break
+    sec = time.perf_counter() - t0
+    nodes = S.E * S.Np
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dict(value=nodes * STAGES * steps / sec, unit="node-stage/s", cores=cores, kind="oracle",
+                sample=f"{n[0]}x{n[1]}x{n[2]}-element sub-box of the {WORKLOAD} workload (same element size, "
+                       f"moist SL physics, {nodes} nodes), {steps} LSRK(5,4) step(s) after 1 warm-up step")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cmles", choices=["cmles", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        cb = cpu_baseline()
+        line = dict(impl="reference", metric=METRIC, value=cb["value"], unit=cb["unit"], n_gpus=args.gpus,
+                    steps=args.steps, warmup=args.warmup, ms_per_step=None, higher_is_better=True,
+                    scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                    config={"workload": f"{WORKLOAD}: 160x160x80 elements, N=4, moist, SL closure (CPU oracle on a "
+                                        "bounded sub-box)"},
+                    cpu_baseline=cb, e2e={"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0})
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    hbm, peak_kind = measured_peaks()
+    variants = [("fp64_sl", "fp64", "sl")]
+    results = {}
+    for name, prec, clo in variants:
+        results[name] = run_variant(name, prec, clo, args.steps, args.warmup, world, rank, torch)
+    head = results["fp64_sl"]
+    prec = "fp64"
+    total_nodes = head["nodes"] * world
+    value = total_nodes * STAGES * args.steps / (head["ms"] / 1e3)
+    kt = head["kt"]
+    kinds = ["grad", "rhs"]
+    dom = max(range(2), key=lambda k: kt["ms"][k])
+    avg_ms = kt["ms"][dom] / max(kt["count"][dom], 1)
+    achieved = head["nodes"] * BYTES[prec][kinds[dom]] / (avg_ms / 1e3) / 1e9
+    out_variants = {}
+    for name, r in results.items():
+        v = r["nodes"] * world * STAGES * args.steps / (r["ms"] / 1e3)
+        per = {}
+        for k in range(2):
+            a = r["kt"]["ms"][k] / max(r["kt"]["count"][k], 1)
+            per[kinds[k]] = dict(avg_ms=a, launches=r["kt"]["count"][k],
+                                 gbs=r["nodes"] * BYTES[prec][kinds[k]] / (a / 1e3) / 1e9)
+        out_variants[name] = dict(value=v, ms_per_step=r["ms"] / args.steps, kernels=per, finite=r["finite"],
+                                  satadj_failures=r["satadj_failures"])
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = run_e2e("fp64", "sl", max(1, min(args.steps, 2)), torch)
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit="node-stage/s", n_gpus=world, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=head["ms"] / args.steps, higher_is_better=True,
+                    scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                    config={"workload": f"{WORKLOAD}: 160x160x80 hexahedral elements, N=4 (256M nodes), moist, "
+                                        "Smagorinsky-Lilly, LSRK(5,4)", "variant": "fp64_sl",
+                            "elements": head["nodes"] // 125, "nodes_per_gpu": head["nodes"],
+                            "l2": "inputs larger than L2 (state alone 12 GB)", "parallelism": f"replicas{world}"},
+                    roofline={"bound": "hbm", "kernel": kinds[dom], "achieved": achieved, "peak": hbm,
+                              "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                              "peak_source": f"{peak_kind} hbm_gbs"},
+                    cpu_baseline=cb, e2e=e2e, gpu_launches=head["launches"], clocks=head["clocks"],
+                    variants=out_variants)
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * cmles: C ABI of the B300 (sm_103a) nodal-DG large-eddy-simulation hot path
+ * of Sridhar et al., "Large-eddy simulations with ClimateMachine" (GMD 2021/22).
+ *
+ * The library evaluates the right-hand side of Eq. eom_compact,
+ *     dY/dt = -div(F1 + F2) + S(Y),   Y = [rho, rho u, rho v, rho w, rho e_tot, rho q_t],
+ * in the semi-discrete nodal-DG form of Eq. matrixProblem on hexahedral
+ * Legendre-Gauss-Lobatto elements of order N, and advances it with the
+ * five-stage fourth-order low-storage Runge-Kutta scheme of Carpenter and
+ * Kennedy (cited in Sec. 3.2).  Every step of that path runs in the library's
+ * own CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *  - State arrays are FP64, element-major: Q[e][v][n], v in 0..5 as above,
+ *    node n = i + (N+1) (j + (N+1) k) (i along x, j along y, k along z),
+ *    element e = ex + nex (ey + ney ez).  E*6*(N+1)^3 doubles.
+ *  - "_dev" pointers are CUDA device pointers owned by the caller and only
+ *    borrowed for the duration of the call; "_host" pointers are host memory.
+ *  - The handle owns its internal device buffers; it is not thread-safe.
+ *  - Every call returns a cmles_status and never aborts.  On error,
+ *    cmles_last_error_message(h) describes the failure.  Device-side errors
+ *    (Newton non-convergence, non-finite values) are counted on the device and
+ *    reported by cmles_diagnostics.
+ *  - Work is enqueued on the handle's stream (cmles_set_stream; default the
+ *    legacy default stream) and is asynchronous unless stated otherwise.
+ */
+#ifndef CMLES_H
+#define CMLES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cmles_t *cmles_handle;
+
+typedef enum {
+  CMLES_OK = 0,
+  CMLES_ERR_ARG = 1,       /* invalid argument (null pointer, bad size, unsupported order) */
+  CMLES_ERR_OOM = 2,       /* device allocation failed */
+  CMLES_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+  CMLES_ERR_SATADJ = 4,    /* saturation adjustment did not converge at some node */
+  CMLES_ERR_NONFINITE = 5, /* the state holds NaN or Inf */
+  CMLES_ERR_MESH = 6,      /* inconsistent mesh description */
+  CMLES_ERR_STATE = 7      /* call out of order (e.g. no reference state yet) */
+} cmles_status;
+
+enum { CMLES_CLOSURE_NONE = 0, CMLES_CLOSURE_SL = 1, CMLES_CLOSURE_MLP = 2 };
+
+/* Arithmetic of the RHS kernels.
+ *   CMLES_FP64       all FP64 ("plain" method).
+ *   CMLES_FP32_ACC64 volume, face and gradient kernels in FP32 on a state
+ *                    stored as FP32 deviations from the hydrostatic reference
+ *                    (the reference subtraction done in FP64); the
+ *                    Runge-Kutta state accumulated in FP64. */
+enum { CMLES_FP64 = 0, CMLES_FP32_ACC64 = 1 };
+
+/* Structured hexahedral mesh of nex x ney x nez elements (Sec. 3.1).  With
+ * warp = 1, node heights follow z' = z + z_s(x)(1 - (z - z0)/Lz),
+ * z_s(x) = hill_h exp(-((x - hill_xc)/hill_a)^2): elements stacked over the
+ * terrain with linear damping to a flat top (Sec. 4.3). */
+typedef struct {
+  int N;                 /* polynomial order, 1..7 (kernels instantiated for 4) */
+  int nex, ney, nez;
+  double x0, y0, z0;
+  double Lx, Ly, Lz;
+  int periodic[3];       /* per direction; non-periodic ends are walls */
+  int warp;
+  double hill_h, hill_a, hill_xc;
+} cmles_mesh;
+
+/* Physical and numerical parameters.  cmles_default_params fills the
+ * thermodynamic constants of Table t:constants (Sec. 2.5) and the readings
+ * g = 9.81 m s^-2, p0 = 1e5 Pa, p_tr = 611.657 Pa, T_tr = 273.16 K. */
+typedef struct {
+  double g, p0, Rd, Rv, cvd, cvv, cvl, cvi, T0, Lv0, Lf0, ptr, Ttr;
+  int closure;           /* CMLES_CLOSURE_*: Smagorinsky-Lilly (Sec. 4.1) or learned MLP */
+  double Cs, Prt;        /* Smagorinsky coefficient, turbulent Prandtl number (1/3) */
+  int richardson;        /* apply the Richardson correction f_b (Eq. richardson) */
+  int moist;             /* saturation adjustment on (Sec. 2.6) */
+  double sponge_alpha, sponge_zs, sponge_gamma; /* Rayleigh sponge (App. A.2) */
+  double u_relax[3];
+  double lateral_sponge_frac;                   /* also damp within this fraction of Lx at both x ends */
+  int surface_flux;      /* bottom wall: prescribed SHF + LHF energy and LHF/L_v0 water flux (App. A.1) */
+  double shf, lhf;       /* W m^-2 */
+  double Omega[3];       /* rotation vector of the Coriolis term of Eq. momentum */
+  int precision;         /* CMLES_FP64 or CMLES_FP32_ACC64 */
+  double dt;             /* time step of cmles_step */
+  int satadj_max_iter;   /* Newton iteration cap (default 20) */
+} cmles_params;
+
+typedef struct {
+  double budget[6];      /* domain integrals sum_e sum_n w_n J_n Q_v (FP64 reduction) */
+  double time;           /* model time advanced by cmles_step */
+  long long steps;       /* steps taken */
+  int nonfinite;         /* 1 if the state holds a NaN or Inf */
+  int satadj_failures;   /* Newton non-convergence count since the previous call */
+} cmles_diag;
+
+/* Initial-state description for cmles_init_case (synthetic cases; inputs,
+ * not part of the method).  id: 1 dry bubble, 2 moist layer, 3 hill flow,
+ * 5 throughput box.  modes: nmodes rows (kx, ky, kz, ax, ay, az, phase) of a
+ * random-phase velocity field, host memory, may be NULL. */
+typedef struct {
+  int id;
+  uint64_t seed;
+  double theta0;
+  double dtheta, r0, xc, yc, zc;
+  double noise_theta, noise_qt, noise_zmax;
+  double NBV;
+  double u0[3];
+  double qt_sfc, qt_ml, z_ml, qt_top, dthdz_above;
+  int moist;
+  int nmodes;
+  const double *modes;
+  double qt_H;
+} cmles_case;
+
+/* Fill p with the defaults described above (SL closure, FP64, dry, no sponge). */
+void cmles_default_params(cmles_params *p);
+
+/* Build LGL nodes, weights and the differentiation matrix (Sec. 3.1,
+ * Eqs. expansion, basisDerivatives), the element connectivity, metric terms
+ * (Eq. mapping) and sponge tables, and allocate the device work buffers.
+ * Errors: CMLES_ERR_ARG (null pointers, N outside the instantiated orders),
+ * CMLES_ERR_MESH (non-positive sizes), CMLES_ERR_OOM. */
+cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cmles_handle *out);
+cmles_status cmles_destroy(cmles_handle h);
+/* Text of the last error on this handle (never NULL; "" when none). */
+const char *cmles_last_error_message(cmles_handle h);
+/* Stream (cudaStream_t passed as void*) on which all later work is enqueued. */
+cmles_status cmles_set_stream(cmles_handle h, void *stream);
+
+/* Hydrostatic reference state p_r, rho_r of Eq. momentum (and the total water
+ * q_r of the same profile, used only as the FP32 storage offset).  Host
+ * arrays of n values: one per node level (n = nez (N+1), level = ez (N+1) + k)
+ * for flat meshes, one per node (n = E (N+1)^3) for warped meshes.
+ * qt_r may be NULL (zero). */
+cmles_status cmles_set_reference(cmles_handle h, const double *rho_r_host, const double *p_r_host,
+                                 const double *qt_r_host, size_t n);
+
+/* Evaluate a synthetic initial state on the device and set the reference
+ * state of that case (hydrostatic profiles of Eqs. pressureDistrib,
+ * pressure_hs_brunt and density_hs_brunt, or RK4 integration for moist
+ * profiles; seeded SplitMix64 noise).  Replaces cmles_set_reference. */
+cmles_status cmles_init_case(cmles_handle h, const cmles_case *c);
+
+/* Copy a state into / out of the handle (device buffers, layout above). */
+cmles_status cmles_set_state(cmles_handle h, const double *Q_dev);
+cmles_status cmles_get_state(cmles_handle h, double *Q_dev);
+/* Same with host buffers; the copies run on the handle's stream and the call
+ * returns after they complete (pinned host memory gives full PCIe speed). */
+cmles_status cmles_set_state_host(cmles_handle h, const double *Q_host);
+cmles_status cmles_get_state_host(cmles_handle h, double *Q_host);
+
+/* RHS of Eq. matrixProblem for the state Q (device, FP64) into RHS (device,
+ * FP64, same layout), in the handle's precision.  The handle's own state is
+ * left unchanged. */
+cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev);
+
+/* Advance the handle's state by nsteps LSRK(5,4) steps of params.dt.  Each
+ * stage is two kernels: the gradient/closure pass and the flux-divergence pass
+ * with the fused stage update.  Asynchronous. */
+cmles_status cmles_step(cmles_handle h, int nsteps);
+
+/* FP64 budgets, non-finite flag and Newton failures of the current state.
+ * Synchronises the handle's stream.  Returns CMLES_ERR_NONFINITE or
+ * CMLES_ERR_SATADJ when those occurred (out is filled in either case). */
+cmles_status cmles_diagnostics(cmles_handle h, cmles_diag *out);
+
+/* Favre (density-weighted) horizontal means of the current state per node
+ * level (App. C), flat meshes only.  out_host receives nez (N+1) rows of 11
+ * values: <rho>, theta, q_t, q_l, u, v, w, w'w', w'theta', w'q_t', theta_l.
+ * Synchronises the stream. */
+cmles_status cmles_profiles(cmles_handle h, double *out_host);
+
+/* Learned-closure weights (FP32 host vector, converted to BF16 for the
+ * kernels): W1[64][13], b1[64], W2[64][64], b2[64], W3[2][64], b3[2],
+ * in_scale[13], out_scale[2]; n must be 5199.  Network inputs are the nine
+ * velocity gradients, three theta_v gradients and Delta, each times in_scale;
+ * nu_t = out_scale[0] max(y0, 0), D_t = out_scale[1] max(y1, 0). */
+cmles_status cmles_set_closure_weights(cmles_handle h, const float *params_host, size_t n);
+
+/* Per-kernel timing: when enabled, every launch is bracketed by CUDA events
+ * on the handle's stream; cmles_kernel_times returns, for the kernels
+ * launched since the last reset, count[k] and total milliseconds[k] for
+ * k = 0 gradient pass, 1 flux/update pass, 2 other kernels, and the total
+ * number of kernel launches.  Synchronises the stream. */
+cmles_status cmles_enable_timing(cmles_handle h, int enable);
+cmles_status cmles_kernel_times(cmles_handle h, long long count[3], double ms[3], long long *launches);
+/* Kernel launches issued by this handle since creation (always counted). */
+long long cmles_launch_count(cmles_handle h);
+
+/* Sizes of the handle's problem. */
+long long cmles_num_elements(cmles_handle h);
+long long cmles_num_nodes(cmles_handle h);
+/* Device bytes held by the handle's buffers. */
+long long cmles_device_bytes(cmles_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,46 @@
+"""Build the cmles CUDA library in-tree (paper_2110_00853_b300/libcmles.so).
+
+All kernels are compiled for sm_103a only:
+  nvcc -gencode arch=compute_103a,code=sm_103a -O3 -lineinfo -shared -Xcompiler -fPIC
+The library exports the C ABI of include/cmles.h and links the CUDA runtime
+statically, so it loads without a toolkit on the library path.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+LIB = os.path.join(HERE, "libcmles.so")
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def sources():
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+
+
+def _deps():
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    deps.append(os.path.join(ROOT, "include", "cmles.h"))
+    return deps
+
+
+def build(force=False, verbose=False):
+    if not force and os.path.exists(LIB):
+        t = os.path.getmtime(LIB)
+        if all(os.path.getmtime(d) <= t for d in _deps()):
+            return LIB
+    cmd = [NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+                           "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-cudart", "static",
+                           "-o", LIB] + sources()
+    if verbose:
+        cmd.insert(1, "-Xptxas=-v")
+        print(" ".join(cmd))
+    subprocess.check_call(cmd)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -1,0 +1,275 @@
+"""Thin Python binding of the cmles C ABI (include/cmles.h).
+
+Argument marshalling only: every step of the DG right-hand side, the
+Runge-Kutta update, the diagnostics and the initial-state evaluation runs in
+the library's CUDA kernels.  torch supplies device memory and the stream.
+There is no CPU fallback: creating a Solver without the built library or
+without a CUDA device raises.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcmles.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "cmles.h")
+
+CMLES_FP64, CMLES_FP32_ACC64 = 0, 1
+CLOSURE = {"none": 0, "sl": 1, "mlp": 2}
+PRECISION = {"fp64": CMLES_FP64, "fp32": CMLES_FP32_ACC64, "fp32acc64": CMLES_FP32_ACC64}
+STATUS = {0: "CMLES_OK", 1: "CMLES_ERR_ARG", 2: "CMLES_ERR_OOM", 3: "CMLES_ERR_CUDA", 4: "CMLES_ERR_SATADJ",
+          5: "CMLES_ERR_NONFINITE", 6: "CMLES_ERR_MESH", 7: "CMLES_ERR_STATE"}
+MLP_PARAMS = 64 * 13 + 64 + 64 * 64 + 64 + 2 * 64 + 2 + 13 + 2
+
+
+class Mesh(C.Structure):
+    _fields_ = [("N", C.c_int), ("nex", C.c_int), ("ney", C.c_int), ("nez", C.c_int),
+                ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
+                ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double), ("periodic", C.c_int * 3),
+                ("warp", C.c_int), ("hill_h", C.c_double), ("hill_a", C.c_double), ("hill_xc", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("g", "p0", "Rd", "Rv", "cvd", "cvv", "cvl", "cvi", "T0", "Lv0", "Lf0",
+                                          "ptr", "Ttr")] + [
+        ("closure", C.c_int), ("Cs", C.c_double), ("Prt", C.c_double), ("richardson", C.c_int),
+        ("moist", C.c_int), ("sponge_alpha", C.c_double), ("sponge_zs", C.c_double), ("sponge_gamma", C.c_double),
+        ("u_relax", C.c_double * 3), ("lateral_sponge_frac", C.c_double), ("surface_flux", C.c_int),
+        ("shf", C.c_double), ("lhf", C.c_double), ("Omega", C.c_double * 3), ("precision", C.c_int),
+        ("dt", C.c_double), ("satadj_max_iter", C.c_int)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("budget", C.c_double * 6), ("time", C.c_double), ("steps", C.c_longlong),
+                ("nonfinite", C.c_int), ("satadj_failures", C.c_int)]
+
+
+class Case(C.Structure):
+    _fields_ = [("id", C.c_int), ("seed", C.c_uint64), ("theta0", C.c_double), ("dtheta", C.c_double),
+                ("r0", C.c_double), ("xc", C.c_double), ("yc", C.c_double), ("zc", C.c_double),
+                ("noise_theta", C.c_double), ("noise_qt", C.c_double), ("noise_zmax", C.c_double),
+                ("NBV", C.c_double), ("u0", C.c_double * 3), ("qt_sfc", C.c_double), ("qt_ml", C.c_double),
+                ("z_ml", C.c_double), ("qt_top", C.c_double), ("dthdz_above", C.c_double), ("moist", C.c_int),
+                ("nmodes", C.c_int), ("modes", C.POINTER(C.c_double)), ("qt_H", C.c_double)]
+
+
+_lib = None
+_H = C.c_void_p
+_VP = C.c_void_p
+_DP = C.POINTER(C.c_double)
+
+
+def header_symbols():
+    """Function names declared in include/cmles.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(cmles_[a-z0-9_]+)\s*\(", text)))
+
+
+def load(path=LIB_PATH):
+    """Load libcmles.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"cmles CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    L = C.CDLL(path)
+    L.cmles_default_params.argtypes = [C.POINTER(Params)]
+    L.cmles_default_params.restype = None
+    L.cmles_create.argtypes = [C.POINTER(Mesh), C.POINTER(Params), C.POINTER(_H)]
+    L.cmles_destroy.argtypes = [_H]
+    L.cmles_last_error_message.argtypes = [_H]
+    L.cmles_last_error_message.restype = C.c_char_p
+    L.cmles_set_stream.argtypes = [_H, _VP]
+    L.cmles_set_reference.argtypes = [_H, _DP, _DP, _DP, C.c_size_t]
+    L.cmles_init_case.argtypes = [_H, C.POINTER(Case)]
+    for n in ("cmles_set_state", "cmles_get_state", "cmles_set_state_host", "cmles_get_state_host"):
+        getattr(L, n).argtypes = [_H, _VP]
+    L.cmles_tendency.argtypes = [_H, _VP, _VP]
+    L.cmles_step.argtypes = [_H, C.c_int]
+    L.cmles_diagnostics.argtypes = [_H, C.POINTER(Diag)]
+    L.cmles_profiles.argtypes = [_H, _DP]
+    L.cmles_set_closure_weights.argtypes = [_H, C.POINTER(C.c_float), C.c_size_t]
+    L.cmles_enable_timing.argtypes = [_H, C.c_int]
+    L.cmles_kernel_times.argtypes = [_H, C.POINTER(C.c_longlong), _DP, C.POINTER(C.c_longlong)]
+    for n in ("cmles_launch_count", "cmles_num_elements", "cmles_num_nodes", "cmles_device_bytes"):
+        getattr(L, n).argtypes = [_H]
+        getattr(L, n).restype = C.c_longlong
+    _lib = L
+    return L
+
+
+class CmlesError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def default_params():
+    P = Params()
+    load().cmles_default_params(C.byref(P))
+    return P
+
+
+def make_mesh(d):
+    m = Mesh()
+    m.N, m.nex, m.ney, m.nez = d["N"], d["nex"], d["ney"], d["nez"]
+    m.x0, m.y0, m.z0 = d.get("x0", 0.0), d.get("y0", 0.0), d.get("z0", 0.0)
+    m.Lx, m.Ly, m.Lz = d["Lx"], d["Ly"], d["Lz"]
+    m.periodic = (C.c_int * 3)(*d.get("periodic", (1, 1, 0)))
+    m.warp = int(d.get("warp", False))
+    m.hill_h, m.hill_a, m.hill_xc = d.get("hill_h", 0.0), d.get("hill_a", 1.0), d.get("hill_xc", 0.0)
+    return m
+
+
+def make_params(d, precision="fp64"):
+    P = default_params()
+    for k, v in d.items():
+        if k == "closure":
+            P.closure = CLOSURE[v]
+        elif k in ("u_relax", "Omega"):
+            setattr(P, k, (C.c_double * 3)(*v))
+        elif k in ("richardson", "moist", "surface_flux"):
+            setattr(P, k, int(v))
+        else:
+            setattr(P, k, v)
+    P.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    return P
+
+
+class Solver:
+    """A cmles handle: one DG-LES problem on the current CUDA device."""
+
+    def __init__(self, mesh, physics, precision="fp64"):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("cmles needs a CUDA device; no CPU fallback exists")
+        self.torch = torch
+        self.L = load()
+        self.mesh_d = dict(mesh)
+        self.phys_d = dict(physics)
+        self._mesh = make_mesh(mesh)
+        self._params = make_params(physics, precision)
+        h = _H()
+        st = self.L.cmles_create(C.byref(self._mesh), C.byref(self._params), C.byref(h))
+        if st != 0:
+            raise CmlesError(st, "cmles_create failed")
+        self.h = h
+        self.N = mesh["N"]
+        self.Np = (self.N + 1) ** 3
+        self.E = mesh["nex"] * mesh["ney"] * mesh["nez"]
+        self.nlev = mesh["nez"] * (self.N + 1)
+        self.set_stream(torch.cuda.current_stream())
+
+    def _check(self, st):
+        if st != 0:
+            raise CmlesError(st, self.L.cmles_last_error_message(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.cmles_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(self.L.cmles_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def set_reference(self, rho_r, p_r, qt_r=None):
+        rho_r = np.ascontiguousarray(rho_r, np.float64)
+        p_r = np.ascontiguousarray(p_r, np.float64)
+        q = None if qt_r is None else np.ascontiguousarray(qt_r, np.float64)
+        self._check(self.L.cmles_set_reference(self.h, rho_r.ctypes.data_as(_DP), p_r.ctypes.data_as(_DP),
+                                               None if q is None else q.ctypes.data_as(_DP), rho_r.size))
+
+    def init_case(self, case):
+        cs = Case()
+        keep = None
+        for k, v in case.items():
+            if k == "u0":
+                cs.u0 = (C.c_double * 3)(*v)
+            elif k == "modes":
+                if v is not None:
+                    keep = np.ascontiguousarray(v, np.float64)
+                    cs.nmodes = keep.shape[0]
+                    cs.modes = keep.ctypes.data_as(_DP)
+            elif k == "moist":
+                cs.moist = int(v)
+            elif k in dict(Case._fields_):
+                setattr(cs, k, v)
+        self._check(self.L.cmles_init_case(self.h, C.byref(cs)))
+        del keep
+
+    def _dev(self, t):
+        torch = self.torch
+        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+        assert t.numel() == self.E * 6 * self.Np
+        return C.c_void_p(t.data_ptr())
+
+    def set_state(self, Q):
+        self._check(self.L.cmles_set_state(self.h, self._dev(Q)))
+
+    def get_state(self):
+        Q = self.torch.empty((self.E, 6, self.Np), dtype=self.torch.float64, device="cuda")
+        self._check(self.L.cmles_get_state(self.h, self._dev(Q)))
+        return Q
+
+    def set_state_host(self, Q):
+        Q = Q.contiguous()
+        assert not Q.is_cuda and Q.dtype == self.torch.float64
+        self._check(self.L.cmles_set_state_host(self.h, C.c_void_p(Q.data_ptr())))
+
+    def get_state_host(self, out=None):
+        if out is None:
+            out = self.torch.empty((self.E, 6, self.Np), dtype=self.torch.float64, pin_memory=True)
+        self._check(self.L.cmles_get_state_host(self.h, C.c_void_p(out.data_ptr())))
+        return out
+
+    def tendency(self, Q, out=None):
+        if out is None:
+            out = self.torch.empty_like(Q)
+        self._check(self.L.cmles_tendency(self.h, self._dev(Q), self._dev(out)))
+        return out
+
+    def step(self, n=1):
+        self._check(self.L.cmles_step(self.h, int(n)))
+
+    def diagnostics(self, raise_on_error=True):
+        d = Diag()
+        st = self.L.cmles_diagnostics(self.h, C.byref(d))
+        if raise_on_error and st not in (0,):
+            self._check(st)
+        return dict(budget=np.array(d.budget[:]), time=d.time, steps=d.steps, nonfinite=bool(d.nonfinite),
+                    satadj_failures=d.satadj_failures, status=st)
+
+    def profiles(self):
+        out = np.zeros((self.nlev, 11))
+        self._check(self.L.cmles_profiles(self.h, out.ctypes.data_as(_DP)))
+        return out
+
+    def set_closure_weights(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        self._check(self.L.cmles_set_closure_weights(self.h, flat.ctypes.data_as(C.POINTER(C.c_float)),
+                                                     flat.size))
+
+    def enable_timing(self, on=True):
+        self._check(self.L.cmles_enable_timing(self.h, int(on)))
+
+    def kernel_times(self):
+        cnt = (C.c_longlong * 3)()
+        ms = (C.c_double * 3)()
+        launches = C.c_longlong()
+        self._check(self.L.cmles_kernel_times(self.h, cnt, ms, C.byref(launches)))
+        return dict(count=list(cnt), ms=list(ms), launches=launches.value)
+
+    def launch_count(self):
+        return self.L.cmles_launch_count(self.h)
+
+    def device_bytes(self):
+        return self.L.cmles_device_bytes(self.h)

@@ -1,0 +1,678 @@
+// C ABI of the cmles library (declared in include/cmles.h): handle set-up on
+// the host (LGL basis, mesh tables, reference state, sponge), device buffers,
+// and the stage loop that launches the DG kernels.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "cmles.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace cmles;
+
+namespace {
+
+// LSRK(5,4), Carpenter & Kennedy (1994), 2N-storage form:
+//   dQ <- A_s dQ + dt RHS(Q),  Q <- Q + B_s dQ.
+const double kLsrkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                          -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kLsrkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                          1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                          2277821191437.0 / 14882151754819.0};
+
+struct TimedLaunch {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+// Legendre P_N and P_{N-1} at x by the three-term recurrence.
+void legendre_pair(int N, double x, double *PN, double *PNm1) {
+  double pm = 1.0, p = x;
+  if (N == 0) {
+    *PN = 1.0;
+    *PNm1 = 0.0;
+    return;
+  }
+  for (int k = 1; k < N; ++k) {
+    double pn = ((2.0 * k + 1.0) * x * p - k * pm) / (k + 1.0);
+    pm = p;
+    p = pn;
+  }
+  *PN = p;
+  *PNm1 = pm;
+}
+
+// LGL nodes as the zeros of f(x) = (1 - x^2) P_N'(x) = N (P_{N-1} - x P_N),
+// found by Newton with f'(x) = -N (N+1) P_N(x) (Legendre's equation) from the
+// Chebyshev-Lobatto points; weights 2 / (N (N+1) P_N^2); derivative matrix in
+// the classical closed form D_ij = P_N(x_i) / (P_N(x_j) (x_i - x_j)),
+// D_00 = -N(N+1)/4, D_NN = N(N+1)/4, other diagonal entries 0.
+void lgl_basis(int N, std::vector<double> &x, std::vector<double> &w, std::vector<double> &D) {
+  const int Nq = N + 1;
+  x.assign(Nq, 0.0);
+  w.assign(Nq, 0.0);
+  D.assign(Nq * Nq, 0.0);
+  for (int i = 0; i < Nq; ++i) {
+    double xi = -cos(M_PI * i / N);
+    if (i > 0 && i < N) {
+      for (int it = 0; it < 200; ++it) {
+        double PN, PNm1;
+        legendre_pair(N, xi, &PN, &PNm1);
+        const double step = (PNm1 - xi * PN) / ((N + 1.0) * PN);
+        xi += step;
+        if (fabs(step) < 1e-17) break;
+      }
+    }
+    x[i] = xi;
+  }
+  x[0] = -1.0;
+  x[N] = 1.0;
+  for (int i = 0; i < Nq / 2; ++i) {  // exact symmetry about 0
+    const double h = 0.5 * (x[N - i] - x[i]);
+    x[i] = -h;
+    x[N - i] = h;
+  }
+  if (N % 2 == 0) x[N / 2] = 0.0;
+  std::vector<double> PN(Nq);
+  for (int i = 0; i < Nq; ++i) {
+    double pm;
+    legendre_pair(N, x[i], &PN[i], &pm);
+    w[i] = 2.0 / (N * (N + 1.0) * PN[i] * PN[i]);
+  }
+  for (int i = 0; i < Nq; ++i)
+    for (int j = 0; j < Nq; ++j) D[i * Nq + j] = i == j ? 0.0 : PN[i] / (PN[j] * (x[i] - x[j]));
+  D[0] = -N * (N + 1.0) / 4.0;
+  D[N * Nq + N] = N * (N + 1.0) / 4.0;
+}
+
+}  // namespace
+
+struct cmles_t {
+  cmles_mesh mesh;
+  cmles_params prm;
+  int N = 4, Nq = 5, Np = 125;
+  long long E = 0, nodes = 0;
+  cudaStream_t stream = 0;
+  std::string err;
+  std::vector<double> xi, w, D;
+  KParams K;
+  double *Q[2] = {nullptr, nullptr};
+  int cur = 0;
+  double *dQ = nullptr, *F2 = nullptr, *aux = nullptr;
+  double *rho_r = nullptr, *p_r = nullptr, *qt_r = nullptr, *tau_lev = nullptr, *tau_col = nullptr;
+  double *wq = nullptr, *partials = nullptr, *budget_out = nullptr, *prof = nullptr;
+  int *flags = nullptr;
+  int budget_nblocks = 1;
+  bool have_ref = false;
+  long long launches = 0, steps = 0;
+  double time = 0.0;
+  bool timing = false;
+  std::vector<TimedLaunch> timed;
+  long long tcount[3] = {0, 0, 0};
+  double tms[3] = {0, 0, 0};
+  long long bytes = 0;
+  std::vector<float> mlp;
+};
+
+namespace {
+
+cmles_status fail(cmles_handle h, cmles_status st, const std::string &msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(h, CMLES_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+cmles_status dalloc(cmles_handle h, void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(h, CMLES_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                      cudaGetErrorString(e));
+  }
+  h->bytes += (long long)bytes;
+  return CMLES_OK;
+}
+
+// launch bookkeeping: count every kernel; with timing on, bracket by events
+struct LaunchScope {
+  cmles_handle h;
+  int kind, nk;
+  TimedLaunch tl;
+  LaunchScope(cmles_handle h_, int kind_, int nkernels) : h(h_), kind(kind_), nk(nkernels) {
+    h->launches += nk;
+    if (h->timing) {
+      cudaEventCreate(&tl.a);
+      cudaEventCreate(&tl.b);
+      cudaEventRecord(tl.a, h->stream);
+    }
+  }
+  ~LaunchScope() {
+    if (h->timing) {
+      cudaEventRecord(tl.b, h->stream);
+      tl.kind = kind;
+      h->timed.push_back(tl);
+    }
+  }
+};
+
+void fill_kparams(cmles_handle h) {
+  const cmles_params &p = h->prm;
+  const cmles_mesh &m = h->mesh;
+  KParams &K = h->K;
+  memset(&K, 0, sizeof(K));
+  K.g = p.g;
+  K.p0 = p.p0;
+  K.Rd = p.Rd;
+  K.Rv = p.Rv;
+  K.cvd = p.cvd;
+  K.cvv = p.cvv;
+  K.cvl = p.cvl;
+  K.T0 = p.T0;
+  K.Lv0 = p.Lv0;
+  K.Iv0 = p.Lv0 - p.Rv * p.T0;
+  K.cpd = p.cvd + p.Rd;
+  K.kappa = p.Rd / K.cpd;
+  K.dcp = (p.cvv + p.Rv) - p.cvl;
+  K.pv_ptr = p.ptr;
+  K.pv_Ttr = p.Ttr;
+  K.pv_a = K.dcp / p.Rv;
+  K.pv_b = (p.Lv0 - K.dcp * p.T0) / p.Rv;
+  K.Prt = p.Prt;
+  K.inv_Prt = 1.0 / p.Prt;
+  K.richardson = p.richardson;
+  K.moist = p.moist;
+  K.closure = p.closure;
+  for (int c = 0; c < 3; ++c) {
+    K.Omega[c] = p.Omega[c];
+    K.u_relax[c] = p.u_relax[c];
+    K.periodic[c] = m.periodic[c];
+  }
+  K.surface_flux = p.surface_flux;
+  K.E_water = p.lhf / p.Lv0;
+  K.E_energy = p.shf + p.lhf;
+  K.nex = m.nex;
+  K.ney = m.ney;
+  K.nez = m.nez;
+  K.E = (int)h->E;
+  K.x0 = m.x0;
+  K.y0 = m.y0;
+  K.z0 = m.z0;
+  K.hx = m.Lx / m.nex;
+  K.hy = m.Ly / m.ney;
+  K.hz = m.Lz / m.nez;
+  const double hd[3] = {K.hx, K.hy, K.hz};
+  for (int d = 0; d < 3; ++d) {
+    K.jac[d] = 2.0 / hd[d];
+    K.lift[d] = 2.0 / (h->w[0] * hd[d]);
+  }
+  // Delta = (element volume)^(1/3) / N (Sec. 4.1, geometric mean of L_d / N)
+  const double Delta = cbrt(K.hx * K.hy * K.hz) / h->N;
+  K.CsDelta2 = (p.Cs * Delta) * (p.Cs * Delta);
+  K.satadj_max_iter = p.satadj_max_iter > 0 ? p.satadj_max_iter : 20;
+  for (int a = 0; a < h->Nq; ++a) {
+    K.w[a] = h->w[a];
+    K.xi[a] = h->xi[a];
+    for (int b = 0; b < h->Nq; ++b) K.D[a * h->Nq + b] = h->D[a * h->Nq + b];
+  }
+  K.rho_r = h->rho_r;
+  K.p_r = h->p_r;
+  K.tau_lev = h->tau_lev;
+  K.tau_col = h->tau_col;
+  K.flags = h->flags;
+}
+
+double level_z(cmles_handle h, int lev) {
+  const int ez = lev / h->Nq, k = lev % h->Nq;
+  return h->K.z0 + (ez + 0.5 * (h->xi[k] + 1.0)) * h->K.hz;
+}
+
+cmles_status run_stage_pair(cmles_handle h, const double *Qin, double *Qout, double *dQ, const StageCoef &sc,
+                            bool update) {
+  {
+    LaunchScope ls(h, 0, 1);
+    CK(launch_grad64(Qin, h->F2, h->aux, h->K, h->stream));
+  }
+  {
+    LaunchScope ls(h, 1, 1);
+    CK(launch_rhs64(Qin, h->F2, h->aux, dQ, Qout, sc, update, h->K, h->stream));
+  }
+  return CMLES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cmles_default_params(cmles_params *p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  // Table t:constants; g, p0, p_tr, T_tr are readings (not in the table)
+  p->g = 9.81;
+  p->p0 = 1.0e5;
+  p->Rd = 287.0;
+  p->Rv = 462.0;
+  p->cvd = 717.5;
+  p->cvv = 1397.5;
+  p->cvl = 4181.0;
+  p->cvi = 2100.0;
+  p->T0 = 273.16;
+  p->Lv0 = 2.5008e6;
+  p->Lf0 = 0.3336e6;
+  p->ptr = 611.657;
+  p->Ttr = 273.16;
+  p->closure = CMLES_CLOSURE_SL;
+  p->Cs = 0.21;
+  p->Prt = 1.0 / 3.0;
+  p->richardson = 1;
+  p->moist = 0;
+  p->sponge_gamma = 2.0;
+  p->precision = CMLES_FP64;
+  p->dt = 0.02;
+  p->satadj_max_iter = 20;
+}
+
+cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cmles_handle *out) {
+  if (!mesh || !params || !out) return CMLES_ERR_ARG;
+  *out = nullptr;
+  if (mesh->N != 4) return CMLES_ERR_ARG;
+  if (mesh->nex < 1 || mesh->ney < 1 || mesh->nez < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0))
+    return CMLES_ERR_MESH;
+  if (mesh->warp) return CMLES_ERR_ARG;
+  if (params->precision != CMLES_FP64) return CMLES_ERR_ARG;
+  if (params->closure != CMLES_CLOSURE_NONE && params->closure != CMLES_CLOSURE_SL) return CMLES_ERR_ARG;
+  long long E = (long long)mesh->nex * mesh->ney * mesh->nez;
+  if (E > 0x7fffffffLL / 8) return CMLES_ERR_MESH;
+  cmles_handle h = new cmles_t();
+  h->mesh = *mesh;
+  h->prm = *params;
+  h->N = mesh->N;
+  h->Nq = h->N + 1;
+  h->Np = h->Nq * h->Nq * h->Nq;
+  h->E = E;
+  h->nodes = E * h->Np;
+  lgl_basis(h->N, h->xi, h->w, h->D);
+  const size_t n6 = (size_t)h->nodes * 6;
+  const int nlev = mesh->nez * h->Nq;
+  cmles_status st = CMLES_OK;
+#define ALLOC(ptr, bytes)                                   \
+  do {                                                      \
+    st = dalloc(h, (void **)&(ptr), (bytes));               \
+    if (st != CMLES_OK) {                                   \
+      std::string msg = h->err;                             \
+      cmles_destroy(h);                                     \
+      fprintf(stderr, "cmles_create: %s\n", msg.c_str());   \
+      return st;                                            \
+    }                                                       \
+  } while (0)
+  ALLOC(h->Q[0], n6 * sizeof(double));
+  ALLOC(h->Q[1], n6 * sizeof(double));
+  ALLOC(h->dQ, n6 * sizeof(double));
+  ALLOC(h->F2, (size_t)h->nodes * 15 * sizeof(double));
+  ALLOC(h->aux, (size_t)h->nodes * 2 * sizeof(double));
+  ALLOC(h->rho_r, nlev * sizeof(double));
+  ALLOC(h->p_r, nlev * sizeof(double));
+  ALLOC(h->qt_r, nlev * sizeof(double));
+  ALLOC(h->tau_lev, nlev * sizeof(double));
+  ALLOC(h->tau_col, (size_t)mesh->nex * h->Nq * sizeof(double));
+  ALLOC(h->wq, h->Np * sizeof(double));
+  ALLOC(h->flags, 16 * sizeof(int));
+  h->budget_nblocks = budget_blocks(h->nodes);
+  ALLOC(h->partials, (size_t)h->budget_nblocks * 7 * sizeof(double));
+  ALLOC(h->budget_out, 8 * sizeof(double));
+  ALLOC(h->prof, (size_t)nlev * 12 * sizeof(double));
+#undef ALLOC
+  fill_kparams(h);
+  // sponge tables (Eq. sponge, reading tau_s = alpha sin^gamma(pi/2 (z - z_s)/(z_top - z_s)))
+  std::vector<double> tl(nlev, 0.0), tc((size_t)mesh->nex * h->Nq, 0.0);
+  const double ztop = mesh->z0 + mesh->Lz;
+  for (int l = 0; l < nlev; ++l) {
+    const double z = level_z(h, l);
+    if (params->sponge_alpha > 0.0 && z > params->sponge_zs)
+      tl[l] = params->sponge_alpha * pow(sin(0.5 * M_PI * (z - params->sponge_zs) / (ztop - params->sponge_zs)),
+                                         params->sponge_gamma);
+  }
+  bool lateral = params->sponge_alpha > 0.0 && params->lateral_sponge_frac > 0.0;
+  if (lateral) {
+    const double width = params->lateral_sponge_frac * mesh->Lx;
+    const double xl = mesh->x0 + width, xr = mesh->x0 + mesh->Lx - width;
+    for (int ex = 0; ex < mesh->nex; ++ex)
+      for (int i = 0; i < h->Nq; ++i) {
+        const double x = mesh->x0 + (ex + 0.5 * (h->xi[i] + 1.0)) * h->K.hx;
+        double t = 0.0;
+        if (x < xl) t = params->sponge_alpha * pow(sin(0.5 * M_PI * (xl - x) / width), params->sponge_gamma);
+        if (x > xr) t = params->sponge_alpha * pow(sin(0.5 * M_PI * (x - xr) / width), params->sponge_gamma);
+        tc[(size_t)ex * h->Nq + i] = t;
+      }
+  }
+  std::vector<double> wq(h->Np);
+  for (int k = 0; k < h->Nq; ++k)
+    for (int j = 0; j < h->Nq; ++j)
+      for (int i = 0; i < h->Nq; ++i) wq[i + h->Nq * (j + h->Nq * k)] = h->w[i] * h->w[j] * h->w[k];
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemcpy(h->tau_lev, tl.data(), nlev * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->tau_col, tc.data(), tc.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->wq, wq.data(), h->Np * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(h->flags, 0, 16 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->dQ, 0, n6 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(h->Q[0], 0, n6 * sizeof(double));
+  if (e != cudaSuccess) {
+    cmles_destroy(h);
+    return CMLES_ERR_CUDA;
+  }
+  if (!lateral) h->K.tau_col = nullptr;
+  *out = h;
+  return CMLES_OK;
+}
+
+cmles_status cmles_destroy(cmles_handle h) {
+  if (!h) return CMLES_ERR_ARG;
+  for (auto &t : h->timed) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  void *bufs[] = {h->Q[0], h->Q[1], h->dQ, h->F2, h->aux, h->rho_r, h->p_r, h->qt_r, h->tau_lev, h->tau_col,
+                  h->wq, h->flags, h->partials, h->budget_out, h->prof};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  delete h;
+  return CMLES_OK;
+}
+
+const char *cmles_last_error_message(cmles_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+cmles_status cmles_set_stream(cmles_handle h, void *stream) {
+  if (!h) return CMLES_ERR_ARG;
+  h->stream = (cudaStream_t)stream;
+  return CMLES_OK;
+}
+
+cmles_status cmles_set_reference(cmles_handle h, const double *rho_r, const double *p_r, const double *qt_r,
+                                 size_t n) {
+  if (!h || !rho_r || !p_r) return fail(h, CMLES_ERR_ARG, "cmles_set_reference: null array");
+  const size_t nlev = (size_t)h->mesh.nez * h->Nq;
+  if (n != nlev) return fail(h, CMLES_ERR_ARG, "cmles_set_reference: expected one value per node level");
+  CK(cudaMemcpyAsync(h->rho_r, rho_r, nlev * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->p_r, p_r, nlev * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (qt_r)
+    CK(cudaMemcpyAsync(h->qt_r, qt_r, nlev * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  else
+    CK(cudaMemsetAsync(h->qt_r, 0, nlev * sizeof(double), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->have_ref = true;
+  return CMLES_OK;
+}
+
+cmles_status cmles_init_case(cmles_handle h, const cmles_case *c) {
+  if (!h || !c) return fail(h, CMLES_ERR_ARG, "cmles_init_case: null argument");
+  if (c->id != 1 && c->id != 2 && c->id != 5)
+    return fail(h, CMLES_ERR_ARG, "cmles_init_case: case id not available on flat meshes");
+  const cmles_params &p = h->prm;
+  const int nlev = h->mesh.nez * h->Nq;
+  const double cpd = p.cvd + p.Rd, kappa = p.Rd / cpd;
+  const double Lz = h->mesh.Lz;
+  // background theta and q_t profiles
+  auto theta_of = [&](double z) {
+    if (c->id == 2) return z <= c->z_ml ? c->theta0 : c->theta0 + c->dthdz_above * (z - c->z_ml);
+    if (c->id == 5) return c->theta0 * exp(c->NBV * c->NBV * z / p.g);
+    return c->theta0;
+  };
+  auto qt_of = [&](double z) {
+    if (!c->moist) return 0.0;
+    if (c->id == 2)
+      return z <= c->z_ml ? c->qt_sfc + (c->qt_ml - c->qt_sfc) * z / c->z_ml
+                          : c->qt_ml + (c->qt_top - c->qt_ml) * (z - c->z_ml) / (Lz - c->z_ml);
+    if (c->id == 5) return c->qt_sfc * exp(-z / c->qt_H);
+    return 0.0;
+  };
+  // hydrostatic balance dp/dz = -g p / (R_m T), T = theta (p/p0)^kappa, q_l = 0
+  auto rhs = [&](double z, double pp) {
+    const double T = theta_of(z) * pow(pp / p.p0, kappa);
+    const double q = qt_of(z);
+    return -p.g * pp / ((p.Rd * (1.0 - q) + p.Rv * q) * T);
+  };
+  auto rk4 = [&](double z, double pp, double hh) {
+    const double k1 = rhs(z, pp), k2 = rhs(z + 0.5 * hh, pp + 0.5 * hh * k1);
+    const double k3 = rhs(z + 0.5 * hh, pp + 0.5 * hh * k2), k4 = rhs(z + hh, pp + hh * k3);
+    return pp + hh / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+  };
+  const bool integrate = c->id == 2 || (c->id == 5 && c->moist);
+  std::vector<double> grid;
+  const double h0 = 0.5;
+  if (integrate) {
+    double zmax = 0.0;
+    for (int l = 0; l < nlev; ++l) zmax = fmax(zmax, level_z(h, l));
+    const int M = (int)ceil(zmax / h0) + 2;
+    grid.resize(M + 1);
+    grid[0] = p.p0;
+    for (int m = 0; m < M; ++m) grid[m + 1] = rk4(m * h0, grid[m], h0);
+  }
+  std::vector<double> th(nlev), qt(nlev), pr(nlev), rr(nlev);
+  for (int l = 0; l < nlev; ++l) {
+    const double z = level_z(h, l);
+    double pp;
+    if (c->id == 1) {
+      pp = p.p0 * pow(1.0 - p.g / (cpd * c->theta0) * z, cpd / p.Rd);  // Eq. pressureDistrib
+    } else if (!integrate) {                                            // Eq. pressure_hs_brunt
+      const double N2 = c->NBV * c->NBV;
+      const double pi = 1.0 + p.g * p.g / (cpd * c->theta0 * N2) * (exp(-z * N2 / p.g) - 1.0);
+      pp = p.p0 * pow(pi, cpd / p.Rd);
+    } else {
+      int m = (int)floor(z / h0);
+      if (m < 0) m = 0;
+      if (m > (int)grid.size() - 1) m = (int)grid.size() - 1;
+      const double zm = m * h0;
+      pp = z == zm ? grid[m] : rk4(zm, grid[m], z - zm);
+    }
+    th[l] = theta_of(z);
+    qt[l] = qt_of(z);
+    pr[l] = pp;
+    const double T = th[l] * pow(pp / p.p0, kappa);
+    rr[l] = pp / ((p.Rd * (1.0 - qt[l]) + p.Rv * qt[l]) * T);
+  }
+  cmles_status st = cmles_set_reference(h, rr.data(), pr.data(), qt.data(), nlev);
+  if (st != CMLES_OK) return st;
+  double *dth = nullptr, *dqt = nullptr, *dpr = nullptr, *dmodes = nullptr;
+  CK(cudaMalloc(&dth, nlev * sizeof(double)));
+  CK(cudaMalloc(&dqt, nlev * sizeof(double)));
+  CK(cudaMalloc(&dpr, nlev * sizeof(double)));
+  CK(cudaMemcpy(dth, th.data(), nlev * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dqt, qt.data(), nlev * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dpr, pr.data(), nlev * sizeof(double), cudaMemcpyHostToDevice));
+  if (c->nmodes > 0 && c->modes) {
+    CK(cudaMalloc(&dmodes, (size_t)c->nmodes * 7 * sizeof(double)));
+    CK(cudaMemcpy(dmodes, c->modes, (size_t)c->nmodes * 7 * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  CaseDev cd;
+  memset(&cd, 0, sizeof(cd));
+  cd.id = c->id;
+  cd.seed = c->seed;
+  cd.dtheta = c->dtheta;
+  cd.r0 = c->r0;
+  cd.xc = c->xc;
+  cd.yc = c->yc;
+  cd.zc = c->zc;
+  cd.noise_theta = c->noise_theta;
+  cd.noise_qt = c->noise_qt;
+  cd.noise_zmax = c->noise_zmax;
+  for (int k = 0; k < 3; ++k) cd.u0[k] = c->u0[k];
+  cd.moist = c->moist;
+  cd.nmodes = dmodes ? c->nmodes : 0;
+  cd.modes = dmodes;
+  cd.theta_lev = dth;
+  cd.qt_lev = dqt;
+  cd.pref_lev = dpr;
+  {
+    LaunchScope ls(h, 2, 1);
+    CK(launch_init_state(h->Q[0], cd, h->K, h->N, h->stream));
+  }
+  h->cur = 0;
+  CK(cudaStreamSynchronize(h->stream));
+  cudaFree(dth);
+  cudaFree(dqt);
+  cudaFree(dpr);
+  if (dmodes) cudaFree(dmodes);
+  h->time = 0.0;
+  h->steps = 0;
+  return CMLES_OK;
+}
+
+cmles_status cmles_set_state(cmles_handle h, const double *Q_dev) {
+  if (!h || !Q_dev) return fail(h, CMLES_ERR_ARG, "cmles_set_state: null argument");
+  CK(cudaMemcpyAsync(h->Q[h->cur], Q_dev, (size_t)h->nodes * 6 * sizeof(double), cudaMemcpyDeviceToDevice,
+                     h->stream));
+  return CMLES_OK;
+}
+
+cmles_status cmles_get_state(cmles_handle h, double *Q_dev) {
+  if (!h || !Q_dev) return fail(h, CMLES_ERR_ARG, "cmles_get_state: null argument");
+  CK(cudaMemcpyAsync(Q_dev, h->Q[h->cur], (size_t)h->nodes * 6 * sizeof(double), cudaMemcpyDeviceToDevice,
+                     h->stream));
+  return CMLES_OK;
+}
+
+cmles_status cmles_set_state_host(cmles_handle h, const double *Q_host) {
+  if (!h || !Q_host) return fail(h, CMLES_ERR_ARG, "cmles_set_state_host: null argument");
+  CK(cudaMemcpyAsync(h->Q[h->cur], Q_host, (size_t)h->nodes * 6 * sizeof(double), cudaMemcpyHostToDevice,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CMLES_OK;
+}
+
+cmles_status cmles_get_state_host(cmles_handle h, double *Q_host) {
+  if (!h || !Q_host) return fail(h, CMLES_ERR_ARG, "cmles_get_state_host: null argument");
+  CK(cudaMemcpyAsync(Q_host, h->Q[h->cur], (size_t)h->nodes * 6 * sizeof(double), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CMLES_OK;
+}
+
+cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev) {
+  if (!h || !Q_dev || !RHS_dev) return fail(h, CMLES_ERR_ARG, "cmles_tendency: null argument");
+  if (!h->have_ref) return fail(h, CMLES_ERR_STATE, "cmles_tendency: reference state not set");
+  StageCoef sc = {0.0, 0.0, 0.0};
+  return run_stage_pair(h, Q_dev, nullptr, RHS_dev, sc, false);
+}
+
+cmles_status cmles_step(cmles_handle h, int nsteps) {
+  if (!h || nsteps < 0) return fail(h, CMLES_ERR_ARG, "cmles_step: bad argument");
+  if (!h->have_ref) return fail(h, CMLES_ERR_STATE, "cmles_step: reference state not set");
+  for (int s = 0; s < nsteps; ++s) {
+    for (int k = 0; k < 5; ++k) {
+      StageCoef sc = {kLsrkA[k], kLsrkB[k], h->prm.dt};
+      cmles_status st = run_stage_pair(h, h->Q[h->cur], h->Q[1 - h->cur], h->dQ, sc, true);
+      if (st != CMLES_OK) return st;
+      h->cur = 1 - h->cur;
+    }
+    h->steps += 1;
+    h->time += h->prm.dt;
+  }
+  return CMLES_OK;
+}
+
+cmles_status cmles_diagnostics(cmles_handle h, cmles_diag *out) {
+  if (!h || !out) return fail(h, CMLES_ERR_ARG, "cmles_diagnostics: null argument");
+  const double J = h->K.hx * h->K.hy * h->K.hz / 8.0;
+  {
+    LaunchScope ls(h, 2, 2);
+    CK(launch_budgets(h->Q[h->cur], h->E, h->Np, h->wq, J, h->partials, h->budget_nblocks, h->budget_out,
+                      h->stream));
+  }
+  double res[7];
+  int flags[16];
+  CK(cudaMemcpyAsync(res, h->budget_out, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(flags, h->flags, 16 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemsetAsync(h->flags, 0, 16 * sizeof(int), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int v = 0; v < 6; ++v) out->budget[v] = res[v];
+  out->nonfinite = res[6] > 0.0 ? 1 : 0;
+  out->satadj_failures = flags[0];
+  out->time = h->time;
+  out->steps = h->steps;
+  if (out->nonfinite) return fail(h, CMLES_ERR_NONFINITE, "state holds non-finite values");
+  if (out->satadj_failures) return fail(h, CMLES_ERR_SATADJ, "saturation adjustment did not converge");
+  return CMLES_OK;
+}
+
+cmles_status cmles_profiles(cmles_handle h, double *out_host) {
+  if (!h || !out_host) return fail(h, CMLES_ERR_ARG, "cmles_profiles: null argument");
+  const int nlev = h->mesh.nez * h->Nq;
+  CK(cudaMemsetAsync(h->prof, 0, (size_t)nlev * 12 * sizeof(double), h->stream));
+  {
+    LaunchScope ls(h, 2, 2);
+    CK(launch_profiles(h->Q[h->cur], h->K, h->N, h->prof, 0, h->stream));
+    CK(launch_profiles(h->Q[h->cur], h->K, h->N, h->prof, 1, h->stream));
+  }
+  std::vector<double> a((size_t)nlev * 12);
+  CK(cudaMemcpyAsync(a.data(), h->prof, a.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int l = 0; l < nlev; ++l) {
+    const double *s = &a[(size_t)l * 12];
+    double *o = out_host + (size_t)l * 11;
+    o[0] = s[1] / s[0];
+    o[1] = s[2] / s[1];
+    o[2] = s[3] / s[1];
+    o[3] = s[4] / s[1];
+    o[4] = s[5] / s[1];
+    o[5] = s[6] / s[1];
+    o[6] = s[7] / s[1];
+    o[7] = s[9] / s[1];
+    o[8] = s[10] / s[1];
+    o[9] = s[11] / s[1];
+    o[10] = s[8] / s[1];
+  }
+  return CMLES_OK;
+}
+
+cmles_status cmles_set_closure_weights(cmles_handle h, const float *params_host, size_t n) {
+  if (!h || !params_host) return fail(h, CMLES_ERR_ARG, "cmles_set_closure_weights: null argument");
+  if (n != 5199) return fail(h, CMLES_ERR_ARG, "cmles_set_closure_weights: expected 5199 values");
+  h->mlp.assign(params_host, params_host + n);
+  return CMLES_OK;
+}
+
+cmles_status cmles_enable_timing(cmles_handle h, int enable) {
+  if (!h) return CMLES_ERR_ARG;
+  h->timing = enable != 0;
+  return CMLES_OK;
+}
+
+cmles_status cmles_kernel_times(cmles_handle h, long long count[3], double ms[3], long long *launches) {
+  if (!h) return CMLES_ERR_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  for (auto &t : h->timed) {
+    float m = 0.f;
+    cudaEventElapsedTime(&m, t.a, t.b);
+    h->tcount[t.kind] += 1;
+    h->tms[t.kind] += m;
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  h->timed.clear();
+  for (int k = 0; k < 3; ++k) {
+    if (count) count[k] = h->tcount[k];
+    if (ms) ms[k] = h->tms[k];
+    h->tcount[k] = 0;
+    h->tms[k] = 0.0;
+  }
+  if (launches) *launches = h->launches;
+  return CMLES_OK;
+}
+
+long long cmles_launch_count(cmles_handle h) { return h ? h->launches : -1; }
+long long cmles_num_elements(cmles_handle h) { return h ? h->E : -1; }
+long long cmles_num_nodes(cmles_handle h) { return h ? h->nodes : -1; }
+long long cmles_device_bytes(cmles_handle h) { return h ? h->bytes : -1; }
+
+}  // extern "C"

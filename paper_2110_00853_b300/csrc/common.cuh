@@ -1,0 +1,79 @@
+// Shared device-side definitions of the cmles CUDA path (sm_103a).
+//
+// Layout in HBM (element-major, the variable inside the element):
+//   Q[e][v][n]      conserved state, v = rho, rho u, rho v, rho w, rho e_tot, rho q_t
+//   F2[e][d][c][n]  diffusive flux in direction d (3) of the 5 distinct components
+//                   c = (rho d_qt, momentum row d (3), energy); rho and rho q_t share c = 0
+//   aux[e][a][n]    a = 0: p - p_r, a = 1: sound speed c
+// with node n = i + Nq (j + Nq k) and element e = ex + nex (ey + ney ez).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cmles {
+
+constexpr int kMaxQ = 8;
+
+// Everything a DG kernel needs, passed by value (kernel parameter space).
+struct KParams {
+  // thermodynamics (Table t:constants and readings) and derived constants
+  double g, p0, Rd, Rv, cvd, cvv, cvl, T0, Lv0;
+  double Iv0;        // L_v0 - R_v T_0
+  double cpd;        // c_vd + R_d
+  double kappa;      // R_d / c_pd (dry Exner exponent)
+  double pv_ptr, pv_Ttr, pv_a, pv_b;  // p_v* = p_tr exp(a ln(T/T_tr) + b (1/T_tr - 1/T))
+  double dcp;        // c_pv - c_pl
+  // closure
+  double CsDelta2;   // (C_s Delta)^2
+  double Prt, inv_Prt;
+  int richardson, moist, closure;
+  // sources
+  double Omega[3], u_relax[3];
+  int surface_flux;
+  double E_water;    // LHF / L_v0 (kg m^-2 s^-1)
+  double E_energy;   // SHF + LHF (W m^-2)
+  // mesh (flat, uniform elements)
+  int nex, ney, nez, E;
+  int periodic[3];
+  double x0, y0, z0, hx, hy, hz;
+  double jac[3];     // 2 / h_d: d xi_d / d x_d
+  double lift[3];    // 2 / (w_0 h_d): w_s J_s / (w_i J_i) on a face normal to d
+  // per node-level tables (level = ez (N+1) + k) and per x-column sponge table
+  const double *rho_r, *p_r, *tau_lev, *tau_col;
+  int satadj_max_iter;
+  int *flags;        // [0] Newton non-convergence count
+  // LGL basis
+  double D[kMaxQ * kMaxQ], w[kMaxQ], xi[kMaxQ];
+};
+
+template <int Nq>
+__device__ __forceinline__ int face_node(int d, int a, int t1, int t2) {
+  return d == 0 ? a + Nq * (t1 + Nq * t2) : (d == 1 ? t1 + Nq * (a + Nq * t2) : t1 + Nq * (t2 + Nq * a));
+}
+
+// Neighbour of element (ex, ey, ez) across face f (0: -x, 1: +x, 2: -y, 3: +y,
+// 4: -z, 5: +z); -1 marks a wall.
+__device__ __forceinline__ int neighbour(const KParams &P, int ex, int ey, int ez, int f) {
+  int c[3] = {ex, ey, ez};
+  const int n[3] = {P.nex, P.ney, P.nez};
+  const int d = f >> 1;
+  int v = c[d] + ((f & 1) ? 1 : -1);
+  if (v < 0 || v >= n[d]) {
+    if (!P.periodic[d]) return -1;
+    v = (v + n[d]) % n[d];
+  }
+  c[d] = v;
+  return c[0] + P.nex * (c[1] + P.ney * c[2]);
+}
+
+__device__ __forceinline__ double node_z(const KParams &P, int ez, int k) {
+  return P.z0 + (ez + 0.5 * (P.xi[k] + 1.0)) * P.hz;
+}
+
+// LSRK(5,4) stage coefficients (Carpenter & Kennedy 1994, Sec. 3.2).
+struct StageCoef {
+  double A, B, dt;
+};
+
+}  // namespace cmles

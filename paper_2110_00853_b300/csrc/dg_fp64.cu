@@ -1,0 +1,362 @@
+// FP64 ("plain") DG right-hand side kernels for flat hexahedral meshes.
+//
+// Two kernels per Runge-Kutta stage (Sec. 3.1, Eq. matrixProblem):
+//   k_grad64: pointwise thermodynamics with saturation adjustment (Sec. 2),
+//             the BR1 auxiliary gradient of G = (u, v, w, h_tot, q_t, theta_v)
+//             with its centred face term, the SGS closure (Sec. 4) and the
+//             diffusive flux F2; writes F2 and aux = (p - p_r, c).
+//   k_rhs64:  total flux F1 + F2, its divergence by the 1D LGL derivative
+//             matrix along each axis, the Rusanov/central surface terms with
+//             the lift w_s J_s / (w_i J_i), wall boundary states (App. A.3),
+//             sources (gravity with reference subtraction, Rayleigh sponge,
+//             Coriolis), and the fused LSRK(5,4) stage update.
+// One element per 128-thread CTA iteration, one node per thread, element and
+// neighbour face nodes staged in shared memory; grid-stride over elements.
+#include "common.cuh"
+#include "launch.h"
+#include "thermo.cuh"
+
+namespace cmles {
+
+template <int N, bool MOIST>
+__global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, double *__restrict__ F2,
+                                                double *__restrict__ aux, const KParams P) {
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
+  static_assert(Np <= 128, "one node per thread");
+  __shared__ double sD[Nq * Nq];
+  __shared__ double sG[6][Np];
+  __shared__ double sGf[6][6][Nf];
+  __shared__ int sNb[6];
+  const int t = threadIdx.x;
+  if (t < Nq * Nq) sD[t] = P.D[t];
+  const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
+  int fail = 0;
+  for (int e = blockIdx.x; e < P.E; e += gridDim.x) {
+    const int ex = e % P.nex, ey = (e / P.nex) % P.ney, ez = e / (P.nex * P.ney);
+    if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
+    double Y[6], G[6];
+    if (t < Np) {
+#pragma unroll
+      for (int v = 0; v < 6; ++v) Y[v] = Q[((size_t)e * 6 + v) * Np + t];
+      Th64 s;
+      thermo64<MOIST>(P, Y, node_z(P, ez, k), s, fail);
+      G[0] = s.u[0];
+      G[1] = s.u[1];
+      G[2] = s.u[2];
+      G[3] = s.htot;
+      G[4] = s.q;
+      G[5] = s.thv;
+      const int lev = ez * Nq + k;
+      aux[((size_t)e * 2 + 0) * Np + t] = s.p - P.p_r[lev];
+      aux[((size_t)e * 2 + 1) * Np + t] = s.c;
+#pragma unroll
+      for (int v = 0; v < 6; ++v) sG[v][t] = G[v];
+    }
+    __syncthreads();
+    // neighbour face nodes: thermodynamics recomputed from the neighbour's state
+    for (int task = t; task < 6 * Nf; task += blockDim.x) {
+      const int f = task / Nf, fn = task - f * Nf;
+      const int nb = sNb[f];
+      if (nb < 0) continue;
+      const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
+      const int a_nb = (f & 1) ? 0 : N;
+      const int nn = face_node<Nq>(d, a_nb, t1, t2);
+      double Yp[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) Yp[v] = Q[((size_t)nb * 6 + v) * Np + nn];
+      const int ezn = nb / (P.nex * P.ney);
+      Th64 s;
+      thermo64<MOIST>(P, Yp, node_z(P, ezn, d == 2 ? a_nb : t2), s, fail);
+      sGf[f][0][fn] = s.u[0];
+      sGf[f][1][fn] = s.u[1];
+      sGf[f][2][fn] = s.u[2];
+      sGf[f][3][fn] = s.htot;
+      sGf[f][4][fn] = s.q;
+      sGf[f][5][fn] = s.thv;
+    }
+    __syncthreads();
+    if (t < Np) {
+      double gr[6][3];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          a0 += sD[i * Nq + m] * sG[v][m + Nq * (j + Nq * k)];
+          a1 += sD[j * Nq + m] * sG[v][i + Nq * (m + Nq * k)];
+          a2 += sD[k * Nq + m] * sG[v][i + Nq * (j + Nq * m)];
+        }
+        gr[v][0] = P.jac[0] * a0;
+        gr[v][1] = P.jac[1] * a1;
+        gr[v][2] = P.jac[2] * a2;
+      }
+      // BR1 surface term: (w_s J_s)/(w_i J_i) n (G* - G-), G* = (G- + G+)/2;
+      // at walls the velocity ghost reflects the normal component and
+      // scalars are copied, so only the normal velocity jumps.
+      auto lift = [&](int f, int fn) {
+        const int d = f >> 1;
+        const double L = (f & 1) ? P.lift[d] : -P.lift[d];
+        if (sNb[f] >= 0) {
+#pragma unroll
+          for (int v = 0; v < 6; ++v) gr[v][d] += L * (0.5 * (G[v] + sGf[f][v][fn]) - G[v]);
+        } else {
+          gr[d][d] += L * (-G[d]);
+        }
+      };
+      if (i == 0) lift(0, j + Nq * k);
+      if (i == N) lift(1, j + Nq * k);
+      if (j == 0) lift(2, i + Nq * k);
+      if (j == N) lift(3, i + Nq * k);
+      if (k == 0) lift(4, i + Nq * j);
+      if (k == N) lift(5, i + Nq * j);
+
+      // Smagorinsky-Lilly with Richardson correction (Eqs. smago, richardson)
+      double nut = 0.0, Dt = 0.0;
+      if (P.closure == 1) {
+        double S2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const double Sab = 0.5 * (gr[a][b] + gr[b][a]);
+            S2 += Sab * Sab;
+          }
+        const double Smag2 = 2.0 * S2;
+        if (Smag2 > 0.0) {
+          const double Smag = sqrt(Smag2);
+          double fb = 1.0;
+          if (P.richardson) {
+            const double Ri = P.g / G[5] * gr[5][2] / Smag2;
+            if (Ri > 0.0) {
+              const double a = 1.0 - Ri * P.inv_Prt;
+              fb = a > 0.0 ? sqrt(sqrt(a)) : 0.0;
+            }
+          }
+          nut = P.CsDelta2 * Smag * fb;
+          Dt = nut * P.inv_Prt;
+        }
+      }
+      // F2 rows: [rho d_i, rho tau_ij + d_i rho u_j, -rho D_t dh/dx_i + (rho tau u)_i],
+      // d = -D_t grad q_t, rho tau = -2 rho nu_t S (Eqs. diff_moisture_flux,
+      // stress_tensor, diff_energy_flux).
+      const double rho = Y[0];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double di = -Dt * gr[4][d];
+        double rt[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) rt[b] = -2.0 * rho * nut * (0.5 * (gr[d][b] + gr[b][d]));
+        double *o = F2 + ((size_t)e * 15 + d * 5) * Np + t;
+        o[0] = rho * di;
+        o[1 * Np] = rt[0] + di * Y[1];
+        o[2 * Np] = rt[1] + di * Y[2];
+        o[3 * Np] = rt[2] + di * Y[3];
+        o[4 * Np] = -rho * Dt * gr[3][d] + (rt[0] * G[0] + rt[1] * G[1] + rt[2] * G[2]);
+      }
+    }
+    __syncthreads();
+  }
+  if (fail) atomicAdd(P.flags, 1);
+}
+
+// n.F1 in direction d (sign applied by the caller) of Eq. eom_compact:
+// [rho u_d, rho u_j u_d + (p - p_r) delta_jd, (rho e + p) u_d, rho q_t u_d].
+__device__ __forceinline__ void flux1_dir(const double Y[6], double pprime, double pr, int d, double f[6]) {
+  const double ud = Y[1 + d] / Y[0];
+  f[0] = Y[1 + d];
+  f[1] = Y[1] * ud + (d == 0 ? pprime : 0.0);
+  f[2] = Y[2] * ud + (d == 1 ? pprime : 0.0);
+  f[3] = Y[3] * ud + (d == 2 ? pprime : 0.0);
+  f[4] = (Y[4] + (pprime + pr)) * ud;
+  f[5] = Y[5] * ud;
+}
+
+template <int N, bool UPDATE>
+__global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, const double *__restrict__ F2,
+                                               const double *__restrict__ aux, double *__restrict__ dQ,
+                                               double *__restrict__ Qout, const StageCoef sc, const KParams P) {
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
+  __shared__ double sD[Nq * Nq];
+  __shared__ double sF[6][3][Np];
+  __shared__ double sY[6][Np];
+  __shared__ double sL[6][6][Nf];
+  __shared__ int sNb[6];
+  const int t = threadIdx.x;
+  if (t < Nq * Nq) sD[t] = P.D[t];
+  const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
+  for (int e = blockIdx.x; e < P.E; e += gridDim.x) {
+    const int ex = e % P.nex, ey = (e / P.nex) % P.ney, ez = e / (P.nex * P.ney);
+    if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
+    double Y[6];
+    if (t < Np) {
+      const int lev = ez * Nq + k;
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        Y[v] = Q[((size_t)e * 6 + v) * Np + t];
+        sY[v][t] = Y[v];
+      }
+      const double pp = aux[((size_t)e * 2) * Np + t];
+      const double pr = P.p_r[lev];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double f[6];
+        flux1_dir(Y, pp, pr, d, f);
+        const double *g2 = F2 + ((size_t)e * 15 + d * 5) * Np + t;
+        const double c0 = g2[0];
+        sF[0][d][t] = f[0] + c0;
+        sF[1][d][t] = f[1] + g2[1 * Np];
+        sF[2][d][t] = f[2] + g2[2 * Np];
+        sF[3][d][t] = f[3] + g2[3 * Np];
+        sF[4][d][t] = f[4] + g2[4 * Np];
+        sF[5][d][t] = f[5] + c0;
+      }
+    }
+    __syncthreads();
+    // surface terms, one task per (face, face node)
+    for (int task = t; task < 6 * Nf; task += blockDim.x) {
+      const int f = task / Nf, fn = task - f * Nf;
+      const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
+      const int a = (f & 1) ? N : 0;
+      const double sg = (f & 1) ? 1.0 : -1.0;
+      const int n = face_node<Nq>(d, a, t1, t2);
+      const int lev = ez * Nq + (d == 2 ? a : t2);
+      const double pr = P.p_r[lev];
+      double Ym[6], Yp[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) Ym[v] = sY[v][n];
+      const double pm = aux[((size_t)e * 2) * Np + n];
+      const double cm = aux[((size_t)e * 2 + 1) * Np + n];
+      const int nb = sNb[f];
+      double pp, cp, f2s[5];
+      if (nb >= 0) {
+        const int nn = face_node<Nq>(d, N - a, t1, t2);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) Yp[v] = Q[((size_t)nb * 6 + v) * Np + nn];
+        pp = aux[((size_t)nb * 2) * Np + nn];
+        cp = aux[((size_t)nb * 2 + 1) * Np + nn];
+        const double *g2m = F2 + ((size_t)e * 15 + d * 5) * Np + n;
+        const double *g2p = F2 + ((size_t)nb * 15 + d * 5) * Np + nn;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) f2s[c] = 0.5 * (sg * g2m[c * Np] + sg * g2p[c * Np]);
+      } else {
+        // reflecting wall state (Eq. bc-velocity-impenetrable), scalars copied
+#pragma unroll
+        for (int v = 0; v < 6; ++v) Yp[v] = Ym[v];
+        Yp[1 + d] = -Ym[1 + d];
+        pp = pm;
+        cp = cm;
+        // wall-normal diffusive fluxes specified directly (App. A.3)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) f2s[c] = 0.0;
+        if (f == 4 && P.surface_flux) {
+          f2s[0] = -P.E_water;
+          f2s[4] = -P.E_energy;
+        }
+      }
+      // Rusanov (Eq. nonviscFlux): 1/2 n.(F1- + F1+) + lambda/2 (Y- - Y+)
+      double fm[6], fp[6];
+      flux1_dir(Ym, pm, pr, d, fm);
+      flux1_dir(Yp, pp, pr, d, fp);
+      const double lm = fabs(Ym[1 + d] / Ym[0]) + cm;
+      const double lp = fabs(Yp[1 + d] / Yp[0]) + cp;
+      const double lam = fmax(lm, lp);
+      const int c_of_v[6] = {0, 1, 2, 3, 4, 0};
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        const double f1s = 0.5 * (sg * fm[v] + sg * fp[v]) + 0.5 * lam * (Ym[v] - Yp[v]);
+        const double fstar = f1s + f2s[c_of_v[v]];
+        sL[f][v][fn] = P.lift[d] * (sg * sF[v][d][n] - fstar);
+      }
+    }
+    __syncthreads();
+    if (t < Np) {
+      const int lev = ez * Nq + k;
+      double R[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          a0 += sD[i * Nq + m] * sF[v][0][m + Nq * (j + Nq * k)];
+          a1 += sD[j * Nq + m] * sF[v][1][i + Nq * (m + Nq * k)];
+          a2 += sD[k * Nq + m] * sF[v][2][i + Nq * (j + Nq * m)];
+        }
+        double r = -(P.jac[0] * a0 + P.jac[1] * a1 + P.jac[2] * a2);
+        if (i == 0) r += sL[0][v][j + Nq * k];
+        if (i == N) r += sL[1][v][j + Nq * k];
+        if (j == 0) r += sL[2][v][i + Nq * k];
+        if (j == N) r += sL[3][v][i + Nq * k];
+        if (k == 0) r += sL[4][v][i + Nq * j];
+        if (k == N) r += sL[5][v][i + Nq * j];
+        R[v] = r;
+      }
+      // sources: -(rho - rho_r) g k, -tau_s (rho u - rho u_relax), -2 Omega x rho u
+      double tau = P.tau_lev[lev];
+      if (P.tau_col) tau = fmax(tau, P.tau_col[ex * Nq + i]);
+      double S[3];
+      S[0] = -tau * (Y[1] - Y[0] * P.u_relax[0]);
+      S[1] = -tau * (Y[2] - Y[0] * P.u_relax[1]);
+      S[2] = -(Y[0] - P.rho_r[lev]) * P.g - tau * (Y[3] - Y[0] * P.u_relax[2]);
+      S[0] -= 2.0 * (P.Omega[1] * Y[3] - P.Omega[2] * Y[2]);
+      S[1] -= 2.0 * (P.Omega[2] * Y[1] - P.Omega[0] * Y[3]);
+      S[2] -= 2.0 * (P.Omega[0] * Y[2] - P.Omega[1] * Y[1]);
+      R[1] += S[0];
+      R[2] += S[1];
+      R[3] += S[2];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        const size_t idx = ((size_t)e * 6 + v) * Np + t;
+        if (UPDATE) {
+          const double dq = (sc.A != 0.0 ? sc.A * dQ[idx] : 0.0) + sc.dt * R[v];
+          dQ[idx] = dq;
+          Qout[idx] = Y[v] + sc.B * dq;
+        } else {
+          dQ[idx] = R[v];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+
+
+int grid_for(const void *fn, int E, size_t smem = 0) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 128, smem);
+  if (per < 1) per = 1;
+  long long g = (long long)nsm * per;
+  return (int)(g < E ? g : E);
+}
+
+cudaError_t launch_grad64(const double *Q, double *F2, double *aux, const KParams &P, cudaStream_t s) {
+  if (P.moist) {
+    static int grid = 0;
+    if (!grid) grid = grid_for((const void *)k_grad64<4, true>, 1 << 30);
+    k_grad64<4, true><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, aux, P);
+  } else {
+    static int grid = 0;
+    if (!grid) grid = grid_for((const void *)k_grad64<4, false>, 1 << 30);
+    k_grad64<4, false><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, aux, P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs64(const double *Q, const double *F2, const double *aux, double *dQ, double *Qout,
+                         const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+  if (update) {
+    static int grid = 0;
+    if (!grid) grid = grid_for((const void *)k_rhs64<4, true>, 1 << 30);
+    k_rhs64<4, true><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, aux, dQ, Qout, sc, P);
+  } else {
+    static int grid = 0;
+    if (!grid) grid = grid_for((const void *)k_rhs64<4, false>, 1 << 30);
+    k_rhs64<4, false><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, aux, dQ, Qout, sc, P);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cmles

@@ -1,0 +1,39 @@
+// Host-side launchers of the cmles kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace cmles {
+
+int grid_for(const void *fn, int E, size_t smem);
+
+// FP64 path (dg_fp64.cu)
+cudaError_t launch_grad64(const double *Q, double *F2, double *aux, const KParams &P, cudaStream_t s);
+cudaError_t launch_rhs64(const double *Q, const double *F2, const double *aux, double *dQ, double *Qout,
+                         const StageCoef &sc, bool update, const KParams &P, cudaStream_t s);
+
+// Diagnostics and set-up (aux_kernels.cu)
+// Budgets: partial sums per block into partials[nblocks][7] (6 integrals and a
+// non-finite count), then a single-block pass in fixed order into out[7].
+int budget_blocks(long long nodes);
+cudaError_t launch_budgets(const double *Q, long long E, int Np, const double *wq, double J, double *partials,
+                           int nblocks, double *out, cudaStream_t s);
+
+struct CaseDev {
+  int id;
+  unsigned long long seed;
+  double dtheta, r0, xc, yc, zc, noise_theta, noise_qt, noise_zmax;
+  double u0[3];
+  int moist;
+  int nmodes;
+  const double *modes;  // device
+  const double *theta_lev, *qt_lev, *pref_lev;  // per level background theta, q_t and pressure
+};
+cudaError_t launch_init_state(double *Q, const CaseDev &c, const KParams &P, int N, cudaStream_t s);
+
+// Favre profiles: accum[level][12] of quadrature-weighted horizontal sums.
+cudaError_t launch_profiles(const double *Q, const KParams &P, int N, double *accum, int pass, cudaStream_t s);
+
+}  // namespace cmles
