@@ -108,9 +108,15 @@ def dist_setup():
     return world, rank, local
 
 
-def run_variant(name, precision, closure, steps, warmup, world, rank, torch):
+def workload_mesh(sub):
+    """the throughput box, or a sub-box of it with the same element size
+    (used for small profiling cases)"""
+    return I.mesh(WORKLOAD) if sub is None else I.sub_mesh(WORKLOAD, *sub)
+
+
+def run_variant(name, precision, closure, steps, warmup, world, rank, torch, sub=None):
     from paper_2110_00853_b300 import cmles
-    mesh, phys, case = I.mesh(WORKLOAD), I.physics(WORKLOAD, closure=closure), I.case(WORKLOAD)
+    mesh, phys, case = workload_mesh(sub), I.physics(WORKLOAD, closure=closure), I.case(WORKLOAD)
     G = cmles.Solver(mesh, phys, precision=precision)
     G.init_case(case)
     G.step(warmup)
@@ -210,7 +216,10 @@ def main():
     ap.add_argument("--impl", default="cmles", choices=["cmles", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sub", default=None, help="nex,ney,nez: run a sub-box of the workload (profiling cases)")
+    ap.add_argument("--variants", default="fp64_sl")
     args = ap.parse_args()
+    sub = tuple(int(x) for x in args.sub.split(",")) if args.sub else None
     world, rank, local = dist_setup()
 
     if args.impl == "reference":
@@ -232,11 +241,12 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl")
     hbm, peak_kind = measured_peaks()
-    variants = [("fp64_sl", "fp64", "sl")]
+    known = {"fp64_sl": ("fp64", "sl")}
+    variants = [(n,) + known[n] for n in args.variants.split(",")]
     results = {}
     for name, prec, clo in variants:
-        results[name] = run_variant(name, prec, clo, args.steps, args.warmup, world, rank, torch)
-    head = results["fp64_sl"]
+        results[name] = run_variant(name, prec, clo, args.steps, args.warmup, world, rank, torch, sub)
+    head = results[variants[0][0]]
     prec = "fp64"
     total_nodes = head["nodes"] * world
     value = total_nodes * STAGES * args.steps / (head["ms"] / 1e3)
@@ -256,10 +266,10 @@ def main():
         out_variants[name] = dict(value=v, ms_per_step=r["ms"] / args.steps, kernels=per, finite=r["finite"],
                                   satadj_failures=r["satadj_failures"])
     e2e = None
-    if not args.no_e2e and rank == 0:
+    if not args.no_e2e and rank == 0 and sub is None:
         e2e = run_e2e("fp64", "sl", max(1, min(args.steps, 2)), torch)
     cb = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and sub is None:
         cb = cpu_baseline()
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit="node-stage/s", n_gpus=world, steps=args.steps,
