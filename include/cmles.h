@@ -193,6 +193,25 @@ cmles_status cmles_kernel_times(cmles_handle h, long long count[3], double ms[3]
 /* Kernel launches issued by this handle since creation (always counted). */
 long long cmles_launch_count(cmles_handle h);
 
+/* Allocation-free budgets.  The paper has no counterpart: this is a service
+ * for callers that cannot call cudaMalloc, such as applications whose own
+ * pool allocator owns all device memory, or time-stepping loops that cannot
+ * accept the device-wide synchronisation cudaMalloc/cudaFree imply.  It
+ * computes the same FP64 quadrature sums as cmles_diagnostics,
+ * out_dev[v] = sum_e sum_n w_n J Q_v for v = 0..5 and out_dev[6] = number of
+ * non-finite entries, for a caller-owned device state Q_dev (layout above) of
+ * a flat mesh with constant element Jacobian `jacobian` (h_x h_y h_z / 8), on
+ * `stream`.  No handle is needed and nothing is allocated: the block partial
+ * sums live in a file-scope device array of 2 MiB that every GPU loading the
+ * library keeps until exit.  Limits: 1 <= N <= 7 and at most 2,097,152
+ * elements; larger sizes return CMLES_ERR_ARG without launching.  The first
+ * call on each device looks up the array's device address (with that device
+ * current) and should come before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU race: serialise them.  Errors:
+ * CMLES_ERR_ARG (null pointers, sizes), CMLES_ERR_CUDA (lookup or launch). */
+cmles_status cmles_budgets_noalloc(const double *Q_dev, long long num_elements, int N, double jacobian,
+                                   double *out_dev, void *stream);
+
 /* Sizes of the handle's problem. */
 long long cmles_num_elements(cmles_handle h);
 long long cmles_num_nodes(cmles_handle h);

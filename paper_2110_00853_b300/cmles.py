@@ -93,6 +93,7 @@ def load(path=LIB_PATH):
     L.cmles_set_closure_weights.argtypes = [_H, C.POINTER(C.c_float), C.c_size_t]
     L.cmles_enable_timing.argtypes = [_H, C.c_int]
     L.cmles_kernel_times.argtypes = [_H, C.POINTER(C.c_longlong), _DP, C.POINTER(C.c_longlong)]
+    L.cmles_budgets_noalloc.argtypes = [_VP, C.c_longlong, C.c_int, C.c_double, _VP, _VP]
     for n in ("cmles_launch_count", "cmles_num_elements", "cmles_num_nodes", "cmles_device_bytes"):
         getattr(L, n).argtypes = [_H]
         getattr(L, n).restype = C.c_longlong
