@@ -103,6 +103,13 @@ struct cmles_t {
   double *Q[2] = {nullptr, nullptr};
   int cur = 0;
   double *dQ = nullptr, *F2 = nullptr, *aux = nullptr;
+  // FP32 path: shadow ping-pong, FP32 LSRK register, FP32 F2/aux, tables
+  bool fp32 = false;
+  float *S32[2] = {nullptr, nullptr};
+  int scur = 0;
+  bool shadow_valid = false;
+  float *dQ32 = nullptr, *F2_32 = nullptr, *aux32 = nullptr, *lev32 = nullptr, *dH32 = nullptr;
+  double *qref64 = nullptr;
   double *rho_r = nullptr, *p_r = nullptr, *qt_r = nullptr, *tau_lev = nullptr, *tau_col = nullptr;
   double *wq = nullptr, *partials = nullptr, *budget_out = nullptr, *prof = nullptr;
   int *flags = nullptr;
@@ -225,6 +232,36 @@ void fill_kparams(cmles_handle h) {
     K.xi[a] = h->xi[a];
     for (int b = 0; b < h->Nq; ++b) K.D[a * h->Nq + b] = h->D[a * h->Nq + b];
   }
+  KF &F = K.f;
+  F.g = (float)p.g;
+  F.Rd = (float)p.Rd;
+  F.Rv = (float)p.Rv;
+  F.cvd = (float)p.cvd;
+  F.cvv = (float)p.cvv;
+  F.cvl = (float)p.cvl;
+  F.T0 = (float)p.T0;
+  F.Lv0 = (float)p.Lv0;
+  F.Iv0 = (float)K.Iv0;
+  F.kappa = (float)K.kappa;
+  F.pv_ptr = (float)K.pv_ptr;
+  F.pv_Ttr = (float)K.pv_Ttr;
+  F.pv_a = (float)K.pv_a;
+  F.pv_b = (float)K.pv_b;
+  F.dcp = (float)K.dcp;
+  F.CsDelta2 = (float)K.CsDelta2;
+  F.inv_Prt = (float)K.inv_Prt;
+  for (int d = 0; d < 3; ++d) {
+    F.jac[d] = (float)K.jac[d];
+    F.lift[d] = (float)K.lift[d];
+    F.u_relax[d] = (float)p.u_relax[d];
+    F.Omega[d] = (float)p.Omega[d];
+  }
+  F.E_water = (float)K.E_water;
+  F.E_energy = (float)K.E_energy;
+  K.tiled = (m.nex % 4 == 0 && m.ney % 4 == 0) ? 1 : 0;
+  K.lev32 = h->lev32;
+  K.dH32 = h->dH32;
+  K.qref64 = h->qref64;
   K.rho_r = h->rho_r;
   K.p_r = h->p_r;
   K.tau_lev = h->tau_lev;
@@ -235,6 +272,28 @@ void fill_kparams(cmles_handle h) {
 double level_z(cmles_handle h, int lev) {
   const int ez = lev / h->Nq, k = lev % h->Nq;
   return h->K.z0 + (ez + 0.5 * (h->xi[k] + 1.0)) * h->K.hz;
+}
+
+cmles_status run_stage_pair32(cmles_handle h, const float *Sin, float *Sout, double *Rout, const StageCoef &sc,
+                              bool update) {
+  {
+    LaunchScope ls(h, 0, 1);
+    CK(launch_grad32(Sin, h->F2_32, h->aux32, h->K, h->stream));
+  }
+  {
+    LaunchScope ls(h, 1, 1);
+    CK(launch_rhs32(Sin, h->F2_32, h->aux32, h->dQ32, h->Q[0], Sout, Rout, sc, update, h->K, h->stream));
+  }
+  return CMLES_OK;
+}
+
+cmles_status ensure_shadow(cmles_handle h) {
+  if (h->fp32 && !h->shadow_valid) {
+    LaunchScope ls(h, 2, 1);
+    CK(launch_shadow32(h->Q[0], h->S32[h->scur], h->K, h->N, h->stream));
+    h->shadow_valid = true;
+  }
+  return CMLES_OK;
 }
 
 cmles_status run_stage_pair(cmles_handle h, const double *Qin, double *Qout, double *dQ, const StageCoef &sc,
@@ -289,7 +348,9 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   if (mesh->nex < 1 || mesh->ney < 1 || mesh->nez < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0))
     return CMLES_ERR_MESH;
   if (mesh->warp) return CMLES_ERR_ARG;
-  if (params->precision != CMLES_FP64) return CMLES_ERR_ARG;
+  if (params->precision != CMLES_FP64 && params->precision != CMLES_FP32_ACC64) return CMLES_ERR_ARG;
+  // the FP32 shadow is relative to a per-level reference: z must not wrap
+  if (params->precision == CMLES_FP32_ACC64 && mesh->periodic[2]) return CMLES_ERR_ARG;
   if (params->closure != CMLES_CLOSURE_NONE && params->closure != CMLES_CLOSURE_SL) return CMLES_ERR_ARG;
   long long E = (long long)mesh->nex * mesh->ney * mesh->nez;
   if (E > 0x7fffffffLL / 8) return CMLES_ERR_MESH;
@@ -315,11 +376,24 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
       return st;                                            \
     }                                                       \
   } while (0)
+  h->fp32 = params->precision == CMLES_FP32_ACC64;
   ALLOC(h->Q[0], n6 * sizeof(double));
-  ALLOC(h->Q[1], n6 * sizeof(double));
-  ALLOC(h->dQ, n6 * sizeof(double));
-  ALLOC(h->F2, (size_t)h->nodes * 15 * sizeof(double));
-  ALLOC(h->aux, (size_t)h->nodes * 2 * sizeof(double));
+  if (!h->fp32) {
+    ALLOC(h->Q[1], n6 * sizeof(double));
+    ALLOC(h->dQ, n6 * sizeof(double));
+    ALLOC(h->F2, (size_t)h->nodes * 15 * sizeof(double));
+    ALLOC(h->aux, (size_t)h->nodes * 2 * sizeof(double));
+  } else {
+    const size_t n32 = (size_t)E * 128;  // padded nodes
+    ALLOC(h->S32[0], n32 * 6 * sizeof(float));
+    ALLOC(h->S32[1], n32 * 6 * sizeof(float));
+    ALLOC(h->dQ32, n32 * 6 * sizeof(float));
+    ALLOC(h->F2_32, n32 * 15 * sizeof(float));
+    ALLOC(h->aux32, n32 * 2 * sizeof(float));
+  }
+  ALLOC(h->lev32, (size_t)nlev * L_NF * sizeof(float));
+  ALLOC(h->dH32, (size_t)mesh->nez * h->Nq * h->Nq * sizeof(float));
+  ALLOC(h->qref64, (size_t)nlev * 4 * sizeof(double));
   ALLOC(h->rho_r, nlev * sizeof(double));
   ALLOC(h->p_r, nlev * sizeof(double));
   ALLOC(h->qt_r, nlev * sizeof(double));
@@ -365,7 +439,8 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
     e = cudaMemcpy(h->tau_col, tc.data(), tc.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->wq, wq.data(), h->Np * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(h->flags, 0, 16 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(h->dQ, 0, n6 * sizeof(double));
+  if (e == cudaSuccess && h->dQ) e = cudaMemset(h->dQ, 0, n6 * sizeof(double));
+  if (e == cudaSuccess && h->dQ32) e = cudaMemset(h->dQ32, 0, (size_t)E * 128 * 6 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(h->Q[0], 0, n6 * sizeof(double));
   if (e != cudaSuccess) {
     cmles_destroy(h);
@@ -382,8 +457,10 @@ cmles_status cmles_destroy(cmles_handle h) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
   }
-  void *bufs[] = {h->Q[0], h->Q[1], h->dQ, h->F2, h->aux, h->rho_r, h->p_r, h->qt_r, h->tau_lev, h->tau_col,
-                  h->wq, h->flags, h->partials, h->budget_out, h->prof};
+  void *bufs[] = {h->Q[0],   h->Q[1],    h->dQ,      h->F2,       h->aux,     h->rho_r,    h->p_r,
+                  h->qt_r,   h->tau_lev, h->tau_col, h->wq,       h->flags,   h->partials, h->budget_out,
+                  h->prof,   h->S32[0],  h->S32[1],  h->dQ32,     h->F2_32,   h->aux32,    h->lev32,
+                  h->dH32,   h->qref64};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete h;
@@ -403,14 +480,83 @@ cmles_status cmles_set_reference(cmles_handle h, const double *rho_r, const doub
   if (!h || !rho_r || !p_r) return fail(h, CMLES_ERR_ARG, "cmles_set_reference: null array");
   const size_t nlev = (size_t)h->mesh.nez * h->Nq;
   if (n != nlev) return fail(h, CMLES_ERR_ARG, "cmles_set_reference: expected one value per node level");
+  // levels (ez, N) and (ez+1, 0) are the same height: the physical profile
+  // must agree there; the total-water offset is taken from the lower element
+  const int Nq0 = h->Nq;
+  for (int ez = 0; ez + 1 < h->mesh.nez; ++ez) {
+    const size_t a = (size_t)ez * Nq0 + Nq0 - 1, b = (size_t)(ez + 1) * Nq0;
+    if (fabs(rho_r[a] - rho_r[b]) > 1e-12 * fabs(rho_r[a]) || fabs(p_r[a] - p_r[b]) > 1e-12 * fabs(p_r[a]))
+      return fail(h, CMLES_ERR_ARG, "cmles_set_reference: levels of equal height differ");
+  }
+  std::vector<double> qcanon(nlev, 0.0);
+  if (qt_r) {
+    for (size_t l = 0; l < nlev; ++l) qcanon[l] = qt_r[l];
+    for (int ez = 0; ez + 1 < h->mesh.nez; ++ez) qcanon[(size_t)(ez + 1) * Nq0] = qcanon[(size_t)ez * Nq0 + Nq0 - 1];
+    qt_r = qcanon.data();
+  }
   CK(cudaMemcpyAsync(h->rho_r, rho_r, nlev * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->p_r, p_r, nlev * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   if (qt_r)
     CK(cudaMemcpyAsync(h->qt_r, qt_r, nlev * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   else
     CK(cudaMemsetAsync(h->qt_r, 0, nlev * sizeof(double), h->stream));
+  // FP32-path tables from the reference profile, built in FP64:
+  // Q_ref = (rho_r, 0, 0, 0, rho e_r, rho q_r) with T_r = p_r / (rho_r R_m,r),
+  // rho e_r = rho_r (I(T_r, q_r, 0) + g z), H_r = rho e_r + p_r, h_r = H_r/rho_r,
+  // theta_v,r = T_r (p0/p_r)^kappa R_m,r / R_d, and the derivatives of h_r and
+  // theta_v,r along z within each element (D applied to the level values).
+  const cmles_params &p = h->prm;
+  const KParams &K = h->K;
+  std::vector<float> lev(nlev * L_NF, 0.0f), dH((size_t)h->mesh.nez * h->Nq * h->Nq);
+  std::vector<double> qref(nlev * 4, 0.0), hr(nlev), thvr(nlev), tau(nlev);
+  CK(cudaMemcpy(tau.data(), h->tau_lev, nlev * sizeof(double), cudaMemcpyDeviceToHost));
+  for (size_t l = 0; l < nlev; ++l) {
+    const double q = qt_r ? qt_r[l] : 0.0;
+    const double z = level_z(h, (int)l);
+    const double Rm = p.Rd * (1.0 - q) + p.Rv * q;
+    const double Tr = p_r[l] / (rho_r[l] * Rm);
+    const double I = (1.0 - q) * p.cvd * (Tr - p.T0) + q * (p.cvv * (Tr - p.T0) + K.Iv0);
+    const double rhoe = rho_r[l] * (I + p.g * z);
+    qref[l * 4 + 0] = rho_r[l];
+    qref[l * 4 + 1] = rhoe;
+    qref[l * 4 + 2] = rho_r[l] * q;
+    hr[l] = (rhoe + p_r[l]) / rho_r[l];
+    thvr[l] = Tr * pow(p.p0 / p_r[l], K.kappa) * Rm / p.Rd;
+    float *L = &lev[l * L_NF];
+    L[L_RHO] = (float)rho_r[l];
+    L[L_RHOQ] = (float)(rho_r[l] * q);
+    L[L_T] = (float)Tr;
+    L[L_T_T0] = (float)(Tr - p.T0);
+    L[L_GZ] = (float)(p.g * z);
+    L[L_P] = (float)p_r[l];
+    L[L_H] = (float)(rhoe + p_r[l]);
+    L[L_HM] = (float)hr[l];
+    L[L_THV] = (float)thvr[l];
+    L[L_RHORM] = (float)(rho_r[l] * Rm);
+    L[L_TAU] = (float)tau[l];
+    L[L_QM] = (float)q;
+  }
+  const int Nq = h->Nq;
+  for (int ez = 0; ez < h->mesh.nez; ++ez)
+    for (int k = 0; k < Nq; ++k) {
+      double dh = 0.0, dth = 0.0, dq = 0.0;
+      for (int m = 0; m < Nq; ++m) {
+        dq += h->D[k * Nq + m] * (qt_r ? qt_r[ez * Nq + m] : 0.0);
+        dh += h->D[k * Nq + m] * hr[ez * Nq + m];
+        dth += h->D[k * Nq + m] * thvr[ez * Nq + m];
+        dH[(size_t)ez * Nq * Nq + k * Nq + m] =
+            (float)((qref[(ez * Nq + m) * 4 + 1] + p_r[ez * Nq + m]) - (qref[(ez * Nq + k) * 4 + 1] + p_r[ez * Nq + k]));
+      }
+      lev[(ez * Nq + k) * L_NF + L_DZ_HM] = (float)(K.jac[2] * dh);
+      lev[(ez * Nq + k) * L_NF + L_DZ_THV] = (float)(K.jac[2] * dth);
+      lev[(ez * Nq + k) * L_NF + L_DZ_Q] = (float)(K.jac[2] * dq);
+    }
+  CK(cudaMemcpy(h->lev32, lev.data(), lev.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->dH32, dH.data(), dH.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->qref64, qref.data(), qref.size() * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaStreamSynchronize(h->stream));
   h->have_ref = true;
+  h->shadow_valid = false;
   return CMLES_OK;
 }
 
@@ -518,6 +664,7 @@ cmles_status cmles_init_case(cmles_handle h, const cmles_case *c) {
     CK(launch_init_state(h->Q[0], cd, h->K, h->N, h->stream));
   }
   h->cur = 0;
+  h->shadow_valid = false;
   CK(cudaStreamSynchronize(h->stream));
   cudaFree(dth);
   cudaFree(dqt);
@@ -532,6 +679,7 @@ cmles_status cmles_set_state(cmles_handle h, const double *Q_dev) {
   if (!h || !Q_dev) return fail(h, CMLES_ERR_ARG, "cmles_set_state: null argument");
   CK(cudaMemcpyAsync(h->Q[h->cur], Q_dev, (size_t)h->nodes * 6 * sizeof(double), cudaMemcpyDeviceToDevice,
                      h->stream));
+  h->shadow_valid = false;
   return CMLES_OK;
 }
 
@@ -547,6 +695,7 @@ cmles_status cmles_set_state_host(cmles_handle h, const double *Q_host) {
   CK(cudaMemcpyAsync(h->Q[h->cur], Q_host, (size_t)h->nodes * 6 * sizeof(double), cudaMemcpyHostToDevice,
                      h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  h->shadow_valid = false;
   return CMLES_OK;
 }
 
@@ -562,18 +711,37 @@ cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev
   if (!h || !Q_dev || !RHS_dev) return fail(h, CMLES_ERR_ARG, "cmles_tendency: null argument");
   if (!h->have_ref) return fail(h, CMLES_ERR_STATE, "cmles_tendency: reference state not set");
   StageCoef sc = {0.0, 0.0, 0.0};
+  if (h->fp32) {
+    // shadow of Q_dev into the idle shadow buffer; the handle's state is untouched
+    float *tmp = h->S32[1 - h->scur];
+    {
+      LaunchScope ls(h, 2, 1);
+      CK(launch_shadow32(Q_dev, tmp, h->K, h->N, h->stream));
+    }
+    return run_stage_pair32(h, tmp, nullptr, RHS_dev, sc, false);
+  }
   return run_stage_pair(h, Q_dev, nullptr, RHS_dev, sc, false);
 }
 
 cmles_status cmles_step(cmles_handle h, int nsteps) {
   if (!h || nsteps < 0) return fail(h, CMLES_ERR_ARG, "cmles_step: bad argument");
   if (!h->have_ref) return fail(h, CMLES_ERR_STATE, "cmles_step: reference state not set");
+  if (h->fp32) {
+    cmles_status st = ensure_shadow(h);
+    if (st != CMLES_OK) return st;
+  }
   for (int s = 0; s < nsteps; ++s) {
     for (int k = 0; k < 5; ++k) {
       StageCoef sc = {kLsrkA[k], kLsrkB[k], h->prm.dt};
-      cmles_status st = run_stage_pair(h, h->Q[h->cur], h->Q[1 - h->cur], h->dQ, sc, true);
+      cmles_status st;
+      if (h->fp32) {
+        st = run_stage_pair32(h, h->S32[h->scur], h->S32[1 - h->scur], nullptr, sc, true);
+        h->scur = 1 - h->scur;
+      } else {
+        st = run_stage_pair(h, h->Q[h->cur], h->Q[1 - h->cur], h->dQ, sc, true);
+        h->cur = 1 - h->cur;
+      }
       if (st != CMLES_OK) return st;
-      h->cur = 1 - h->cur;
     }
     h->steps += 1;
     h->time += h->prm.dt;

@@ -15,6 +15,21 @@ namespace cmles {
 
 constexpr int kMaxQ = 8;
 
+// FP32 copies of the constants used by the FP32 kernels.
+struct KF {
+  float g, Rd, Rv, cvd, cvv, cvl, T0, Lv0, Iv0, kappa, pv_ptr, pv_Ttr, pv_a, pv_b, dcp;
+  float CsDelta2, inv_Prt;
+  float jac[3], lift[3];
+  float u_relax[3], Omega[3];
+  float E_water, E_energy;
+};
+
+// Per-level FP32 table of the FP32 path (16 floats per node level).
+enum {
+  L_RHO = 0, L_RHOQ, L_T, L_T_T0, L_GZ, L_P, L_H, L_HM, L_THV, L_DZ_HM, L_DZ_THV, L_RHORM, L_TAU, L_QM, L_DZ_Q,
+  L_NF = 16
+};
+
 // Everything a DG kernel needs, passed by value (kernel parameter space).
 struct KParams {
   // thermodynamics (Table t:constants and readings) and derived constants
@@ -43,8 +58,14 @@ struct KParams {
   const double *rho_r, *p_r, *tau_lev, *tau_col;
   int satadj_max_iter;
   int *flags;        // [0] Newton non-convergence count
+  int tiled;         // 1: visit elements in 4 x 4 column tiles (nex, ney multiples of 4)
+  // FP32 path tables (see dg_fp32.cu): per level 16 floats, per element layer
+  // the 5 x 5 differences of rho e_r + p_r along z, per level FP64 offsets
+  const float *lev32, *dH32;
+  const double *qref64;
   // LGL basis
   double D[kMaxQ * kMaxQ], w[kMaxQ], xi[kMaxQ];
+  KF f;
 };
 
 template <int Nq>
@@ -65,6 +86,26 @@ __device__ __forceinline__ int neighbour(const KParams &P, int ex, int ey, int e
   }
   c[d] = v;
   return c[0] + P.nex * (c[1] + P.ney * c[2]);
+}
+
+// Element visited at position g of a kernel's traversal.  With tiling, the
+// traversal walks 4 x 4 columns of elements bottom to top, so that the x, y
+// and z neighbours of an element are visited close in time and their face
+// data is still in L2 when it is gathered.
+__device__ __forceinline__ int element_at(const KParams &P, int g, int &ex, int &ey, int &ez) {
+  if (P.tiled) {
+    const int per_tile = 16 * P.nez;
+    const int t = g / per_tile, r = g - t * per_tile;
+    const int tiles_x = P.nex >> 2;
+    ez = r >> 4;
+    ex = ((t % tiles_x) << 2) + (r & 3);
+    ey = ((t / tiles_x) << 2) + ((r >> 2) & 3);
+  } else {
+    ex = g % P.nex;
+    ey = (g / P.nex) % P.ney;
+    ez = g / (P.nex * P.ney);
+  }
+  return ex + P.nex * (ey + P.ney * ez);
 }
 
 __device__ __forceinline__ double node_z(const KParams &P, int ez, int k) {

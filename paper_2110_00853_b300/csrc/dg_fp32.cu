@@ -1,0 +1,484 @@
+// FP32 DG right-hand side kernels with FP64 accumulation (CMLES_FP32_ACC64).
+//
+// Same two passes as the FP64 path (Sec. 3.1, Eq. matrixProblem), evaluated
+// in FP32 on a shadow state stored as the deviation from the hydrostatic
+// reference of its node level, s = Q - Q_ref(z) with
+// Q_ref = (rho_r, 0, 0, 0, rho e_r, rho q_r); the subtraction is done in FP64
+// when the shadow is written.  Every quantity whose full value is large next
+// to its variation is evaluated in deviation form, which is exact algebra:
+//   * temperature: rho c_vm (T - T_r) from the deviations of rho I, rho and
+//     rho q_t (internal-energy balance of Eq. internal_energies);
+//     saturation adjustment (Eq. sat_adjustment) as Newton on T - T_r with the
+//     residual written relative to the reference identity;
+//   * pressure: p - p_r = [rho R_m] (T - T_r) + ([rho R_m] - [rho R_m]_r) T_r
+//     (Eq. eos), so the reference subtraction never cancels in FP32;
+//   * h_tot, q_t and theta_v as deviations, with the reference parts' derivatives
+//     (D applied to the level values in FP64) added to the gradient;
+//   * the energy flux (rho e + p) u = H_r u + H' u: along x and y H_r is
+//     constant on the derivative line and factors out; along z the line
+//     differences H_r(m) - H_r(k) come from an FP64-built table.
+// The LSRK register dQ is FP32; the state Q is accumulated in FP64 and the
+// shadow rewritten from it.  Element traversal: 4 x 4 column tiles.
+#include "common.cuh"
+#include "launch.h"
+
+namespace cmles {
+
+constexpr int kNP = 128;  // padded nodes per element in the FP32 arrays
+
+struct Th32 {
+  float rho, u[3], qp, Tp, pp, c, hp, thvp;
+};
+
+// p_v*(T) of the integrated Clausius-Clapeyron relation, FP32.
+__device__ __forceinline__ float pvsat32(const KF &F, float T) {
+  return F.pv_ptr * expf(F.pv_a * logf(T / F.pv_Ttr) + F.pv_b * (1.0f / F.pv_Ttr - 1.0f / T));
+}
+
+// Thermodynamics of one node from its deviation state s and its level table L.
+template <bool MOIST>
+__device__ __forceinline__ void thermo32(const KParams &P, const float *__restrict__ L, const float s[6], Th32 &o,
+                                         int &fail) {
+  const KF &F = P.f;
+  const float rho_r = L[L_RHO], rhoq_r = L[L_RHOQ], Tr = L[L_T], TrT0 = L[L_T_T0];
+  const float rp = s[0], qp = s[5];
+  const float rho = rho_r + rp;
+  const float rinv = 1.0f / rho;
+  o.rho = rho;
+  o.u[0] = s[1] * rinv;
+  o.u[1] = s[2] * rinv;
+  o.u[2] = s[3] * rinv;
+  const float rhoq = rhoq_r + qp;
+  o.qp = (qp - L[L_QM] * rp) * rinv;  // q_t - q_r
+  const float rke = 0.5f * (s[1] * o.u[0] + s[2] * o.u[1] + s[3] * o.u[2]);
+  const float dRI = s[4] - rke - rp * L[L_GZ];  // rho I - rho_r I_r
+  // unsaturated: rho c_vm (T - T_r) = d(rho I) - d(rho q) I_v0 - d(rho c_vm) (T_r - T_0)
+  // drqv = rho q_v - rho q_r is carried as a deviation (never formed as the
+  // difference of two near-equal FP32 numbers)
+  float rhoqv = rhoq, rhoql = 0.0f, drqv = qp;
+  float Tp = (dRI - qp * F.Iv0 - (rp * F.cvd + qp * (F.cvv - F.cvd)) * TrT0) /
+             (rho * F.cvd + rhoq * (F.cvv - F.cvd));
+  if (MOIST) {
+    float T = Tr + Tp;
+    if (rhoq > pvsat32(F, T) / (F.Rv * T)) {
+      bool conv = false;
+      for (int it = 0; it < P.satadj_max_iter; ++it) {
+        T = Tr + Tp;
+        const float rqs = pvsat32(F, T) / (F.Rv * T);
+        const float rql = rhoq - rqs;
+        const float rcvm = (rho - rhoq) * F.cvd + rqs * F.cvv + rql * F.cvl;
+        const float drcvm = (rp - qp) * F.cvd + (rqs - rhoq_r) * F.cvv + rql * F.cvl;
+        const float rf = rcvm * Tp + drcvm * TrT0 + (rqs - rhoq_r) * F.Iv0 - dRI;
+        const float Lh = F.Lv0 + F.dcp * (T - F.T0);
+        const float drqs = rqs * (Lh / (F.Rv * T * T) - 1.0f / T);
+        const float rfp = rcvm + drqs * ((F.cvv - F.cvl) * (T - F.T0) + F.Iv0);
+        const float dT = rf / rfp;
+        Tp -= dT;
+        if (fabsf(dT) <= 5e-5f) {
+          conv = true;
+          break;
+        }
+      }
+      if (!conv) fail = 1;
+      T = Tr + Tp;
+      rhoqv = pvsat32(F, T) / (F.Rv * T);
+      rhoql = rhoq - rhoqv;
+      drqv = rhoqv - rhoq_r;
+      if (rhoql < 0.0f) {
+        rhoql = 0.0f;
+        rhoqv = rhoq;
+        drqv = qp;
+      }
+    }
+  }
+  o.Tp = Tp;
+  const float rRm = F.Rd * (rho - rhoq) + F.Rv * rhoqv;
+  const float drRm = F.Rd * (rp - qp) + F.Rv * drqv;
+  const float pp = rRm * Tp + drRm * Tr;  // p - p_r
+  o.pp = pp;
+  const float rcvm = (rho - rhoq) * F.cvd + rhoqv * F.cvv + rhoql * F.cvl;
+  const float pr = L[L_P];
+  o.c = sqrtf((rcvm + rRm) / rcvm * (pr + pp) * rinv);
+  o.hp = (s[4] + pp - L[L_HM] * rp) * rinv;  // h_tot - h_r
+  const float lnr = log1pf(Tp / Tr) - F.kappa * log1pf(pp / pr) + log1pf(drRm / L[L_RHORM]) - log1pf(rp / rho_r);
+  o.thvp = L[L_THV] * expm1f(lnr);  // theta_v - theta_v,r
+}
+
+template <int N, bool MOIST>
+__global__ void __launch_bounds__(128, 8) k_grad32(const float *__restrict__ S, float *__restrict__ F2,
+                                                   float *__restrict__ aux, const KParams P) {
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
+  static_assert(Np <= kNP, "one node per thread");
+  __shared__ float sD[Nq * Nq];
+  __shared__ float sG[6][kNP];
+  __shared__ float sGf[6][6][Nf];
+  __shared__ int sNb[6];
+  const KF &F = P.f;
+  const int t = threadIdx.x;
+  if (t < Nq * Nq) sD[t] = (float)P.D[t];
+  const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
+  int fail = 0;
+  for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
+    int ex, ey, ez;
+    const int e = element_at(P, g, ex, ey, ez);
+    if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
+    float sv[6], G[6];
+    const float *L = P.lev32 + (size_t)(ez * Nq + (k < Nq ? k : 0)) * L_NF;
+    if (t < Np) {
+#pragma unroll
+      for (int v = 0; v < 6; ++v) sv[v] = S[((size_t)e * 6 + v) * kNP + t];
+      Th32 o;
+      thermo32<MOIST>(P, L, sv, o, fail);
+      G[0] = o.u[0];
+      G[1] = o.u[1];
+      G[2] = o.u[2];
+      G[3] = o.hp;
+      G[4] = o.qp;
+      G[5] = o.thvp;
+      aux[((size_t)e * 2 + 0) * kNP + t] = o.pp;
+      aux[((size_t)e * 2 + 1) * kNP + t] = o.c;
+#pragma unroll
+      for (int v = 0; v < 6; ++v) sG[v][t] = G[v];
+    }
+    __syncthreads();
+    for (int task = t; task < 6 * Nf; task += blockDim.x) {
+      const int f = task / Nf, fn = task - f * Nf;
+      const int nb = sNb[f];
+      if (nb < 0) continue;
+      const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
+      const int a_nb = (f & 1) ? 0 : N;
+      const int nn = face_node<Nq>(d, a_nb, t1, t2);
+      float sp[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
+      // the shared face node has the same height, hence the same level values
+      const int lev = ez * Nq + (d == 2 ? (f & 1 ? N : 0) : t2);
+      Th32 o;
+      thermo32<MOIST>(P, P.lev32 + (size_t)lev * L_NF, sp, o, fail);
+      sGf[f][0][fn] = o.u[0];
+      sGf[f][1][fn] = o.u[1];
+      sGf[f][2][fn] = o.u[2];
+      sGf[f][3][fn] = o.hp;
+      sGf[f][4][fn] = o.qp;
+      sGf[f][5][fn] = o.thvp;
+    }
+    __syncthreads();
+    if (t < Np) {
+      float gr[6][3];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          a0 += sD[i * Nq + m] * sG[v][m + Nq * (j + Nq * k)];
+          a1 += sD[j * Nq + m] * sG[v][i + Nq * (m + Nq * k)];
+          a2 += sD[k * Nq + m] * sG[v][i + Nq * (j + Nq * m)];
+        }
+        gr[v][0] = F.jac[0] * a0;
+        gr[v][1] = F.jac[1] * a1;
+        gr[v][2] = F.jac[2] * a2;
+      }
+      // reference parts of h_tot, q_t and theta_v: derivative along z only
+      gr[3][2] += L[L_DZ_HM];
+      gr[4][2] += L[L_DZ_Q];
+      gr[5][2] += L[L_DZ_THV];
+      auto lift = [&](int f, int fn) {
+        const int d = f >> 1;
+        const float Lf = (f & 1) ? F.lift[d] : -F.lift[d];
+        if (sNb[f] >= 0) {
+#pragma unroll
+          for (int v = 0; v < 6; ++v) gr[v][d] += Lf * (0.5f * (G[v] + sGf[f][v][fn]) - G[v]);
+        } else {
+          gr[d][d] += Lf * (-G[d]);
+        }
+      };
+      if (i == 0) lift(0, j + Nq * k);
+      if (i == N) lift(1, j + Nq * k);
+      if (j == 0) lift(2, i + Nq * k);
+      if (j == N) lift(3, i + Nq * k);
+      if (k == 0) lift(4, i + Nq * j);
+      if (k == N) lift(5, i + Nq * j);
+
+      float nut = 0.f, Dt = 0.f;
+      if (P.closure == 1) {
+        float S2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const float Sab = 0.5f * (gr[a][b] + gr[b][a]);
+            S2 += Sab * Sab;
+          }
+        const float Smag2 = 2.0f * S2;
+        if (Smag2 > 0.0f) {
+          const float Smag = sqrtf(Smag2);
+          float fb = 1.0f;
+          if (P.richardson) {
+            const float thv = L[L_THV] + G[5];
+            const float Ri = F.g / thv * gr[5][2] / Smag2;
+            if (Ri > 0.0f) {
+              const float a = 1.0f - Ri * F.inv_Prt;
+              fb = a > 0.0f ? sqrtf(sqrtf(a)) : 0.0f;
+            }
+          }
+          nut = F.CsDelta2 * Smag * fb;
+          Dt = nut * F.inv_Prt;
+        }
+      }
+      const float rho = L[L_RHO] + sv[0];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float di = -Dt * gr[4][d];
+        float rt[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) rt[b] = -2.0f * rho * nut * (0.5f * (gr[d][b] + gr[b][d]));
+        float *o = F2 + ((size_t)e * 15 + d * 5) * kNP + t;
+        o[0] = rho * di;
+        o[1 * kNP] = rt[0] + di * sv[1];
+        o[2 * kNP] = rt[1] + di * sv[2];
+        o[3 * kNP] = rt[2] + di * sv[3];
+        o[4 * kNP] = -rho * Dt * gr[3][d] + (rt[0] * G[0] + rt[1] * G[1] + rt[2] * G[2]);
+      }
+    }
+    __syncthreads();
+  }
+  if (fail) atomicAdd(P.flags, 1);
+}
+
+// Deviation part of n.F1 along d (sign by the caller):
+// [rho u_d, rho u_j u_d + (p - p_r) delta_jd, (rho e' + p') u_d, rho q_t u_d].
+// The reference part H_r u_d of the energy flux is handled separately.
+__device__ __forceinline__ void flux1_dev32(const float s[6], float rho_r, float rhoq_r, float pp, int d,
+                                           float f[6]) {
+  const float ud = s[1 + d] / (rho_r + s[0]);
+  f[0] = s[1 + d];
+  f[1] = s[1] * ud + (d == 0 ? pp : 0.f);
+  f[2] = s[2] * ud + (d == 1 ? pp : 0.f);
+  f[3] = s[3] * ud + (d == 2 ? pp : 0.f);
+  f[4] = (s[4] + pp) * ud;
+  f[5] = (rhoq_r + s[5]) * ud;
+}
+
+template <int N, bool UPDATE>
+__global__ void __launch_bounds__(128, 8) k_rhs32(const float *__restrict__ S, const float *__restrict__ F2,
+                                                  const float *__restrict__ aux, float *__restrict__ dQ,
+                                                  double *__restrict__ Q64, float *__restrict__ Sout,
+                                                  double *__restrict__ Rout, const StageCoef sc, const KParams P) {
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
+  __shared__ float sD[Nq * Nq];
+  __shared__ float sF[6][3][kNP];
+  __shared__ float sS[6][kNP];
+  __shared__ float sU[3][kNP];
+  __shared__ float sLf[6][6][Nf];
+  __shared__ int sNb[6];
+  const KF &F = P.f;
+  const int t = threadIdx.x;
+  if (t < Nq * Nq) sD[t] = (float)P.D[t];
+  const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
+  for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
+    int ex, ey, ez;
+    const int e = element_at(P, g, ex, ey, ez);
+    if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
+    const float *L = P.lev32 + (size_t)(ez * Nq + (k < Nq ? k : 0)) * L_NF;
+    float sv[6];
+    if (t < Np) {
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        sv[v] = S[((size_t)e * 6 + v) * kNP + t];
+        sS[v][t] = sv[v];
+      }
+      const float pp = aux[((size_t)e * 2) * kNP + t];
+      const float rho = L[L_RHO] + sv[0];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        float f[6];
+        flux1_dev32(sv, L[L_RHO], L[L_RHOQ], pp, d, f);
+        const float *g2 = F2 + ((size_t)e * 15 + d * 5) * kNP + t;
+        const float c0 = g2[0];
+        sF[0][d][t] = f[0] + c0;
+        sF[1][d][t] = f[1] + g2[1 * kNP];
+        sF[2][d][t] = f[2] + g2[2 * kNP];
+        sF[3][d][t] = f[3] + g2[3 * kNP];
+        sF[4][d][t] = f[4] + g2[4 * kNP];
+        sF[5][d][t] = f[5] + c0;
+        sU[d][t] = sv[1 + d] / rho;
+      }
+    }
+    __syncthreads();
+    for (int task = t; task < 6 * Nf; task += blockDim.x) {
+      const int f = task / Nf, fn = task - f * Nf;
+      const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
+      const int a = (f & 1) ? N : 0;
+      const float sg = (f & 1) ? 1.f : -1.f;
+      const int n = face_node<Nq>(d, a, t1, t2);
+      const float *Lf = P.lev32 + (size_t)(ez * Nq + (d == 2 ? a : t2)) * L_NF;
+      const float rho_r = Lf[L_RHO], rhoq_r = Lf[L_RHOQ];
+      float sm[6], sp[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) sm[v] = sS[v][n];
+      const float pm = aux[((size_t)e * 2) * kNP + n];
+      const float cm = aux[((size_t)e * 2 + 1) * kNP + n];
+      const int nb = sNb[f];
+      float pp, cp, f2s[5];
+      if (nb >= 0) {
+        const int nn = face_node<Nq>(d, N - a, t1, t2);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
+        pp = aux[((size_t)nb * 2) * kNP + nn];
+        cp = aux[((size_t)nb * 2 + 1) * kNP + nn];
+        const float *g2m = F2 + ((size_t)e * 15 + d * 5) * kNP + n;
+        const float *g2p = F2 + ((size_t)nb * 15 + d * 5) * kNP + nn;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) f2s[c] = 0.5f * (sg * g2m[c * kNP] + sg * g2p[c * kNP]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 6; ++v) sp[v] = sm[v];
+        sp[1 + d] = -sm[1 + d];
+        pp = pm;
+        cp = cm;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) f2s[c] = 0.f;
+        if (f == 4 && P.surface_flux) {
+          f2s[0] = -F.E_water;
+          f2s[4] = -F.E_energy;
+        }
+      }
+      float fm[6], fp[6];
+      flux1_dev32(sm, rho_r, rhoq_r, pm, d, fm);
+      flux1_dev32(sp, rho_r, rhoq_r, pp, d, fp);
+      const float um = sm[1 + d] / (rho_r + sm[0]), up = sp[1 + d] / (rho_r + sp[0]);
+      const float lam = fmaxf(fabsf(um) + cm, fabsf(up) + cp);
+      const int c_of_v[6] = {0, 1, 2, 3, 4, 0};
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        const float f1s = 0.5f * (sg * fm[v] + sg * fp[v]) + 0.5f * lam * (sm[v] - sp[v]);
+        float r = sg * sF[v][d][n] - (f1s + f2s[c_of_v[v]]);
+        // reference part of the energy flux: H_r (u-.n) - H_r (u-.n + u+.n)/2
+        if (v == 4) r += 0.5f * sg * Lf[L_H] * (um - up);
+        sLf[f][v][fn] = F.lift[d] * r;
+      }
+    }
+    __syncthreads();
+    if (t < Np) {
+      float R[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          a0 += sD[i * Nq + m] * sF[v][0][m + Nq * (j + Nq * k)];
+          a1 += sD[j * Nq + m] * sF[v][1][i + Nq * (m + Nq * k)];
+          a2 += sD[k * Nq + m] * sF[v][2][i + Nq * (j + Nq * m)];
+        }
+        float r = -(F.jac[0] * a0 + F.jac[1] * a1 + F.jac[2] * a2);
+        if (i == 0) r += sLf[0][v][j + Nq * k];
+        if (i == N) r += sLf[1][v][j + Nq * k];
+        if (j == 0) r += sLf[2][v][i + Nq * k];
+        if (j == N) r += sLf[3][v][i + Nq * k];
+        if (k == 0) r += sLf[4][v][i + Nq * j];
+        if (k == N) r += sLf[5][v][i + Nq * j];
+        R[v] = r;
+      }
+      {
+        // divergence of H_r u: H_r(k) D u along x and y, and along z
+        // H_r(k) D w + sum_m D_km (H_r(m) - H_r(k)) w_m
+        float ux = 0.f, vy = 0.f, wz = 0.f, wdh = 0.f;
+        const float *dH = P.dH32 + (size_t)ez * Nq * Nq + k * Nq;
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          ux += sD[i * Nq + m] * sU[0][m + Nq * (j + Nq * k)];
+          vy += sD[j * Nq + m] * sU[1][i + Nq * (m + Nq * k)];
+          const float wm = sU[2][i + Nq * (j + Nq * m)];
+          wz += sD[k * Nq + m] * wm;
+          wdh += sD[k * Nq + m] * dH[m] * wm;
+        }
+        R[4] -= L[L_H] * (F.jac[0] * ux + F.jac[1] * vy + F.jac[2] * wz) + F.jac[2] * wdh;
+      }
+      float tau = L[L_TAU];
+      if (P.tau_col) tau = fmaxf(tau, (float)P.tau_col[ex * Nq + i]);
+      const float rho = L[L_RHO] + sv[0];
+      float Sr[3];
+      Sr[0] = -tau * (sv[1] - rho * F.u_relax[0]);
+      Sr[1] = -tau * (sv[2] - rho * F.u_relax[1]);
+      Sr[2] = -sv[0] * F.g - tau * (sv[3] - rho * F.u_relax[2]);
+      Sr[0] -= 2.0f * (F.Omega[1] * sv[3] - F.Omega[2] * sv[2]);
+      Sr[1] -= 2.0f * (F.Omega[2] * sv[1] - F.Omega[0] * sv[3]);
+      Sr[2] -= 2.0f * (F.Omega[0] * sv[2] - F.Omega[1] * sv[1]);
+      R[1] += Sr[0];
+      R[2] += Sr[1];
+      R[3] += Sr[2];
+      const double *qr = P.qref64 + (size_t)(ez * Nq + k) * 4;
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        const size_t i64 = ((size_t)e * 6 + v) * Np + t;
+        if (UPDATE) {
+          const size_t i32 = ((size_t)e * 6 + v) * kNP + t;
+          const float dq = (sc.A != 0.0 ? (float)sc.A * dQ[i32] : 0.f) + (float)sc.dt * R[v];
+          dQ[i32] = dq;
+          const double qn = Q64[i64] + sc.B * (double)dq;
+          Q64[i64] = qn;
+          const double ref = v == 0 ? qr[0] : (v == 4 ? qr[1] : (v == 5 ? qr[2] : 0.0));
+          Sout[i32] = (float)(qn - ref);
+        } else {
+          Rout[i64] = (double)R[v];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Shadow of an FP64 state: s = (float)(Q - Q_ref(level)), subtraction in FP64.
+__global__ void k_shadow32(const double *__restrict__ Q64, float *__restrict__ S, const KParams P, int Np, int Nq) {
+  const long long n = (long long)P.E * Np;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const long long e = q / Np;
+    const int node = (int)(q - e * Np);
+    const int ez = (int)(e / ((long long)P.nex * P.ney));
+    const int k = node / (Nq * Nq);
+    const double *qr = P.qref64 + (size_t)(ez * Nq + k) * 4;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) {
+      const double ref = v == 0 ? qr[0] : (v == 4 ? qr[1] : (v == 5 ? qr[2] : 0.0));
+      S[(e * 6 + v) * kNP + node] = (float)(Q64[(e * 6 + v) * Np + node] - ref);
+    }
+  }
+}
+
+cudaError_t launch_shadow32(const double *Q64, float *S, const KParams &P, int N, cudaStream_t s) {
+  const int Nq = N + 1, Np = Nq * Nq * Nq;
+  long long nodes = (long long)P.E * Np;
+  int blocks = (int)((nodes + 255) / 256);
+  if (blocks > 148 * 32) blocks = 148 * 32;
+  k_shadow32<<<blocks, 256, 0, s>>>(Q64, S, P, Np, Nq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad32(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s) {
+  if (P.moist) {
+    static int grid = 0;
+    if (!grid) grid = grid_for((const void *)k_grad32<4, true>, 1 << 30, 0);
+    k_grad32<4, true><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, P);
+  } else {
+    static int grid = 0;
+    if (!grid) grid = grid_for((const void *)k_grad32<4, false>, 1 << 30, 0);
+    k_grad32<4, false><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs32(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
+                         double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+  if (update) {
+    static int grid = 0;
+    if (!grid) grid = grid_for((const void *)k_rhs32<4, true>, 1 << 30, 0);
+    k_rhs32<4, true><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+  } else {
+    static int grid = 0;
+    if (!grid) grid = grid_for((const void *)k_rhs32<4, false>, 1 << 30, 0);
+    k_rhs32<4, false><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cmles

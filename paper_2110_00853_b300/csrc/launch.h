@@ -14,6 +14,12 @@ cudaError_t launch_grad64(const double *Q, double *F2, double *aux, const KParam
 cudaError_t launch_rhs64(const double *Q, const double *F2, const double *aux, double *dQ, double *Qout,
                          const StageCoef &sc, bool update, const KParams &P, cudaStream_t s);
 
+// FP32 path with FP64 accumulation (dg_fp32.cu); FP32 arrays padded to 128 nodes
+cudaError_t launch_shadow32(const double *Q64, float *S, const KParams &P, int N, cudaStream_t s);
+cudaError_t launch_grad32(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s);
+cudaError_t launch_rhs32(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
+                         double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s);
+
 // Diagnostics and set-up (aux_kernels.cu)
 // Budgets: partial sums per block into partials[nblocks][7] (6 integrals and a
 // non-finite count), then a single-block pass in fixed order into out[7].
