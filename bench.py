@@ -33,9 +33,13 @@ METRIC = "DG node-stage updates/s at 1 B300 and HBM roofline %, FP32+learned vs 
 # algorithmic bytes per node for each kernel launch (compulsory traffic):
 #   gradient pass: read Q, write F2 (15 words) and aux (2 words)
 #   flux/update pass: read Q, F2, aux, read+write dQ, write Q_out
+#   FP32 path: FP32 shadow, F2, aux and dQ; FP64 state read and written once
 BYTES = {
     "fp64": {"grad": (6 + 15 + 2) * 8, "rhs": (6 + 15 + 2 + 12 + 6) * 8},
+    "fp32": {"grad": (6 + 15 + 2) * 4, "rhs": (6 + 15 + 2 + 12 + 6) * 4 + 12 * 8},
 }
+VARIANTS = {"fp32acc64_sl": ("fp32", "sl"), "fp64_sl": ("fp64", "sl")}
+DTYPE = {"fp32": "f32", "fp64": "f64"}
 
 
 def measured_peaks():
@@ -217,7 +221,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sub", default=None, help="nex,ney,nez: run a sub-box of the workload (profiling cases)")
-    ap.add_argument("--variants", default="fp64_sl")
+    ap.add_argument("--variants", default="fp32acc64_sl,fp64_sl",
+                    help="comma list; the first is the headline value")
     args = ap.parse_args()
     sub = tuple(int(x) for x in args.sub.split(",")) if args.sub else None
     world, rank, local = dist_setup()
@@ -241,13 +246,12 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl")
     hbm, peak_kind = measured_peaks()
-    known = {"fp64_sl": ("fp64", "sl")}
-    variants = [(n,) + known[n] for n in args.variants.split(",")]
+    variants = [(n,) + VARIANTS[n] for n in args.variants.split(",")]
     results = {}
     for name, prec, clo in variants:
         results[name] = run_variant(name, prec, clo, args.steps, args.warmup, world, rank, torch, sub)
     head = results[variants[0][0]]
-    prec = "fp64"
+    prec = variants[0][1]
     total_nodes = head["nodes"] * world
     value = total_nodes * STAGES * args.steps / (head["ms"] / 1e3)
     kt = head["kt"]
@@ -256,27 +260,27 @@ def main():
     avg_ms = kt["ms"][dom] / max(kt["count"][dom], 1)
     achieved = head["nodes"] * BYTES[prec][kinds[dom]] / (avg_ms / 1e3) / 1e9
     out_variants = {}
-    for name, r in results.items():
+    for (name, vprec, _), r in zip(variants, results.values()):
         v = r["nodes"] * world * STAGES * args.steps / (r["ms"] / 1e3)
         per = {}
         for k in range(2):
             a = r["kt"]["ms"][k] / max(r["kt"]["count"][k], 1)
-            per[kinds[k]] = dict(avg_ms=a, launches=r["kt"]["count"][k],
-                                 gbs=r["nodes"] * BYTES[prec][kinds[k]] / (a / 1e3) / 1e9)
+            gbs = r["nodes"] * BYTES[vprec][kinds[k]] / (a / 1e3) / 1e9
+            per[kinds[k]] = dict(avg_ms=a, launches=r["kt"]["count"][k], gbs=gbs, hbm_frac=gbs / hbm)
         out_variants[name] = dict(value=v, ms_per_step=r["ms"] / args.steps, kernels=per, finite=r["finite"],
                                   satadj_failures=r["satadj_failures"])
     e2e = None
     if not args.no_e2e and rank == 0 and sub is None:
-        e2e = run_e2e("fp64", "sl", max(1, min(args.steps, 2)), torch)
+        e2e = run_e2e(variants[0][1], variants[0][2], max(1, min(args.steps, 2)), torch)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and sub is None:
         cb = cpu_baseline()
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit="node-stage/s", n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=head["ms"] / args.steps, higher_is_better=True,
-                    scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                    scaling="weak", vs_baseline=None, dtype=DTYPE[prec], data="synthetic",
                     config={"workload": f"{WORKLOAD}: 160x160x80 hexahedral elements, N=4 (256M nodes), moist, "
-                                        "Smagorinsky-Lilly, LSRK(5,4)", "variant": "fp64_sl",
+                                        "Smagorinsky-Lilly, LSRK(5,4)", "variant": variants[0][0],
                             "elements": head["nodes"] // 125, "nodes_per_gpu": head["nodes"],
                             "l2": "inputs larger than L2 (state alone 12 GB)", "parallelism": f"replicas{world}"},
                     roofline={"bound": "hbm", "kernel": kinds[dom], "achieved": achieved, "peak": hbm,
