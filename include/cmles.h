@@ -176,12 +176,33 @@ cmles_status cmles_diagnostics(cmles_handle h, cmles_diag *out);
  * Synchronises the stream. */
 cmles_status cmles_profiles(cmles_handle h, double *out_host);
 
-/* Learned-closure weights (FP32 host vector, converted to BF16 for the
- * kernels): W1[64][13], b1[64], W2[64][64], b2[64], W3[2][64], b3[2],
- * in_scale[13], out_scale[2]; n must be 5199.  Network inputs are the nine
- * velocity gradients, three theta_v gradients and Delta, each times in_scale;
- * nu_t = out_scale[0] max(y0, 0), D_t = out_scale[1] max(y1, 0). */
+/* Learned SGS closure (not in the paper; the workload's extension of Sec. 4):
+ * a per-node network 13 -> 64 -> 64 -> 2 with SiLU hidden activations, BF16
+ * weights and activations and FP32 accumulation on tensor cores, evaluated
+ * inside the FP32 gradient pass when params.closure == CMLES_CLOSURE_MLP
+ * (FP32_ACC64 precision only).  Inputs: the nine velocity gradients
+ * du_i/dx_j (index 3i+j), the three theta_v gradients and Delta, each times
+ * in_scale; outputs nu_t = out_scale[0] max(y0, 0), D_t = out_scale[1] max(y1, 0).
+ * Parameter vector (FP32, 5201 values): W1[64][13], b1[64], W2[64][64],
+ * b2[64], W3[2][64], b3[2], in_scale[13], out_scale[2] (weights out-major).
+ * cmles_set_closure_weights takes it from host memory (n must be 5201),
+ * cmles_set_closure_weights_device from device memory (e.g. after training). */
 cmles_status cmles_set_closure_weights(cmles_handle h, const float *params_host, size_t n);
+cmles_status cmles_set_closure_weights_device(cmles_handle h, const float *params_dev);
+
+/* Training kernels of the closure network on device buffers (no handle):
+ * cmles_mlp_forward: Y[n][2] = network(X[n][13]) with BF16 tensor cores.
+ * cmles_mlp_loss_grad: loss = 1/(2n) sum |y - t|^2 over T[n][2] and its
+ *   gradient with respect to the first 5186 parameters (W1 .. b3), written
+ *   to grad_dev[5186] and loss_dev[1] (both overwritten).
+ * cmles_mlp_adam: one Adam step (Kingma & Ba 2015) of those 5186 parameters
+ *   with moment buffers m_dev, v_dev (5186 each, zero at t = 1); t >= 1.
+ * All run on `stream`; errors CMLES_ERR_ARG (null/size), CMLES_ERR_CUDA. */
+cmles_status cmles_mlp_forward(const float *params_dev, const float *X_dev, float *Y_dev, long long n, void *stream);
+cmles_status cmles_mlp_loss_grad(const float *params_dev, const float *X_dev, const float *T_dev, long long n,
+                                 float *grad_dev, float *loss_dev, void *stream);
+cmles_status cmles_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, int t, float lr,
+                            float beta1, float beta2, float eps, void *stream);
 
 /* Per-kernel timing: when enabled, every launch is bracketed by CUDA events
  * on the handle's stream; cmles_kernel_times returns, for the kernels

@@ -368,7 +368,7 @@ int orc_rhs(orc_solver *s, const double *Q, double *RHS, int form) {
         for (int k = 0; k < 9; ++k) xin[k] = gu[k] * s->mlp_in[k];
         for (int k = 0; k < 3; ++k) xin[9 + k] = gth[k] * s->mlp_in[9 + k];
         xin[12] = s->Delta[e] * s->mlp_in[12];
-        orc_mlp_forward(1, xin, s->mlp_W1, s->mlp_b1, s->mlp_W2, s->mlp_b2, s->mlp_W3, s->mlp_b3, yout);
+        orc_mlp_forward_bf16(1, xin, s->mlp_W1, s->mlp_b1, s->mlp_W2, s->mlp_b2, s->mlp_W3, s->mlp_b3, yout);
         nut = (yout[0] > 0.0 ? yout[0] : 0.0) * s->mlp_out[0];
         Dt = (yout[1] > 0.0 ? yout[1] : 0.0) * s->mlp_out[1];
       }

@@ -9,6 +9,7 @@
  * Test infrastructure only (see oracle.h).
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include "oracle.h"
 
@@ -27,6 +28,42 @@ void orc_mlp_forward(int n, const double *X, const double *W1, const double *b1,
       double a = b2[o];
       for (int i = 0; i < 64; ++i) a += W2[o * 64 + i] * h1[i];
       h2[o] = a * sigmoid(a);
+    }
+    for (int o = 0; o < 2; ++o) {
+      double a = b3[o];
+      for (int i = 0; i < 64; ++i) a += W3[o * 64 + i] * h2[i];
+      Y[s * 2 + o] = a;
+    }
+  }
+}
+
+/* BF16 (8-bit significand) value of x: x rounded to FP32, then to BF16 with
+ * round-to-nearest-even on the 16 dropped bits. */
+double orc_bf16(double x) {
+  union { float f; uint32_t u; } v;
+  v.f = (float)x;
+  uint32_t lsb = (v.u >> 16) & 1u;
+  v.u = (v.u + 0x7FFFu + lsb) & 0xFFFF0000u;
+  return (double)v.f;
+}
+
+/* The closure network as the learned closure defines it: inputs and hidden
+ * activations stored in BF16, weights given (BF16 values), biases and the
+ * sums exact. */
+void orc_mlp_forward_bf16(int n, const double *X, const double *W1, const double *b1, const double *W2,
+                          const double *b2, const double *W3, const double *b3, double *Y) {
+  for (int s = 0; s < n; ++s) {
+    double x[13], h1[64], h2[64];
+    for (int i = 0; i < 13; ++i) x[i] = orc_bf16(X[s * 13 + i]);
+    for (int o = 0; o < 64; ++o) {
+      double a = b1[o];
+      for (int i = 0; i < 13; ++i) a += W1[o * 13 + i] * x[i];
+      h1[o] = orc_bf16(a * sigmoid(a));
+    }
+    for (int o = 0; o < 64; ++o) {
+      double a = b2[o];
+      for (int i = 0; i < 64; ++i) a += W2[o * 64 + i] * h1[i];
+      h2[o] = orc_bf16(a * sigmoid(a));
     }
     for (int o = 0; o < 2; ++o) {
       double a = b3[o];

@@ -164,6 +164,12 @@ void orc_vortex_exact(orc_solver *s, const orc_case *c, double t, double *Q);
 void orc_mlp_forward(int n, const double *X /*[n][13]*/, const double *W1, const double *b1,
                      const double *W2, const double *b2, const double *W3, const double *b3,
                      double *Y /*[n][2]*/);
+/* BF16 rounding (FP32 first, then round-to-nearest-even to 8 significand bits). */
+double orc_bf16(double x);
+/* The closure network with BF16 inputs and hidden activations (the learned
+ * closure's definition); used by orc_rhs when closure == MLP. */
+void orc_mlp_forward_bf16(int n, const double *X, const double *W1, const double *b1, const double *W2,
+                          const double *b2, const double *W3, const double *b3, double *Y);
 /* Mean-squared-error loss 1/(2n) sum |Y - T|^2 and its gradients. */
 double orc_mlp_loss_grad(int n, const double *X, const double *T, const double *W1, const double *b1,
                          const double *W2, const double *b2, const double *W3, const double *b3,

@@ -101,6 +101,9 @@ def _declare(L):
     L.orc_init_case.argtypes = [C.c_void_p, C.POINTER(Case), _DP, _DP, _DP]
     L.orc_vortex_exact.argtypes = [C.c_void_p, C.POINTER(Case), C.c_double, _DP]
     L.orc_mlp_forward.argtypes = [C.c_int, _DP] + [_DP] * 6 + [_DP]
+    L.orc_mlp_forward_bf16.argtypes = [C.c_int, _DP] + [_DP] * 6 + [_DP]
+    L.orc_bf16.argtypes = [C.c_double]
+    L.orc_bf16.restype = C.c_double
     L.orc_mlp_loss_grad.argtypes = [C.c_int, _DP, _DP] + [_DP] * 6 + [_DP] * 6
     L.orc_mlp_loss_grad.restype = C.c_double
     L.orc_adam.argtypes = [C.c_int, _DP, _DP, _DP, _DP, C.c_int, C.c_double, C.c_double, C.c_double,
@@ -214,6 +217,18 @@ def mlp_forward(X, W):
     lib().orc_mlp_forward(X.shape[0], _p(X), *[_p(np.ascontiguousarray(W[k], float))
                                                 for k in ("W1", "b1", "W2", "b2", "W3", "b3")], _p(Y))
     return Y
+
+
+def mlp_forward_bf16(X, W):
+    X = np.ascontiguousarray(X, float)
+    Y = np.zeros((X.shape[0], 2))
+    lib().orc_mlp_forward_bf16(X.shape[0], _p(X), *[_p(np.ascontiguousarray(W[k], float))
+                                                     for k in ("W1", "b1", "W2", "b2", "W3", "b3")], _p(Y))
+    return Y
+
+
+def bf16(x):
+    return lib().orc_bf16(x)
 
 
 def mlp_loss_grad(X, T, W):

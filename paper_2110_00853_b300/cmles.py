@@ -21,7 +21,8 @@ CLOSURE = {"none": 0, "sl": 1, "mlp": 2}
 PRECISION = {"fp64": CMLES_FP64, "fp32": CMLES_FP32_ACC64, "fp32acc64": CMLES_FP32_ACC64}
 STATUS = {0: "CMLES_OK", 1: "CMLES_ERR_ARG", 2: "CMLES_ERR_OOM", 3: "CMLES_ERR_CUDA", 4: "CMLES_ERR_SATADJ",
           5: "CMLES_ERR_NONFINITE", 6: "CMLES_ERR_MESH", 7: "CMLES_ERR_STATE"}
-MLP_PARAMS = 64 * 13 + 64 + 64 * 64 + 64 + 2 * 64 + 2 + 13 + 2
+MLP_PARAMS = 64 * 13 + 64 + 64 * 64 + 64 + 2 * 64 + 2 + 13 + 2   # 5201
+MLP_NET = MLP_PARAMS - 15                                        # trainable part: W1 .. b3
 
 
 class Mesh(C.Structure):
@@ -94,11 +95,51 @@ def load(path=LIB_PATH):
     L.cmles_enable_timing.argtypes = [_H, C.c_int]
     L.cmles_kernel_times.argtypes = [_H, C.POINTER(C.c_longlong), _DP, C.POINTER(C.c_longlong)]
     L.cmles_budgets_noalloc.argtypes = [_VP, C.c_longlong, C.c_int, C.c_double, _VP, _VP]
+    L.cmles_set_closure_weights_device.argtypes = [_H, _VP]
+    L.cmles_mlp_forward.argtypes = [_VP, _VP, _VP, C.c_longlong, _VP]
+    L.cmles_mlp_loss_grad.argtypes = [_VP, _VP, _VP, C.c_longlong, _VP, _VP, _VP]
+    L.cmles_mlp_adam.argtypes = [_VP, _VP, _VP, _VP, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, _VP]
     for n in ("cmles_launch_count", "cmles_num_elements", "cmles_num_nodes", "cmles_device_bytes"):
         getattr(L, n).argtypes = [_H]
         getattr(L, n).restype = C.c_longlong
     _lib = L
     return L
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def mlp_forward(params, X):
+    """Y[n][2] = closure network(X[n][13]) on BF16 tensor cores (device tensors)."""
+    import torch
+    Y = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+    st = load().cmles_mlp_forward(_ptr(params), _ptr(X), _ptr(Y), X.shape[0], _stream())
+    if st != 0:
+        raise CmlesError(st, "cmles_mlp_forward failed")
+    return Y
+
+
+def mlp_loss_grad(params, X, T):
+    """(loss, grad[5186]) of the closure network on a batch (device tensors)."""
+    import torch
+    grad = torch.empty(MLP_NET, dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    st = load().cmles_mlp_loss_grad(_ptr(params), _ptr(X), _ptr(T), X.shape[0], _ptr(grad), _ptr(loss), _stream())
+    if st != 0:
+        raise CmlesError(st, "cmles_mlp_loss_grad failed")
+    return loss, grad
+
+
+def mlp_adam(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    st = load().cmles_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(t), lr, beta1, beta2, eps, _stream())
+    if st != 0:
+        raise CmlesError(st, "cmles_mlp_adam failed")
 
 
 class CmlesError(RuntimeError):
@@ -258,6 +299,10 @@ class Solver:
         flat = np.ascontiguousarray(flat, np.float32)
         self._check(self.L.cmles_set_closure_weights(self.h, flat.ctypes.data_as(C.POINTER(C.c_float)),
                                                      flat.size))
+
+    def set_closure_weights_device(self, params):
+        assert params.is_cuda and params.dtype == self.torch.float32 and params.numel() == MLP_PARAMS
+        self._check(self.L.cmles_set_closure_weights_device(self.h, C.c_void_p(params.data_ptr())))
 
     def enable_timing(self, on=True):
         self._check(self.L.cmles_enable_timing(self.h, int(on)))

@@ -11,6 +11,7 @@
 #include "cmles.h"
 #include "common.cuh"
 #include "launch.h"
+#include "mlp.cuh"
 
 using namespace cmles;
 
@@ -123,6 +124,8 @@ struct cmles_t {
   double tms[3] = {0, 0, 0};
   long long bytes = 0;
   std::vector<float> mlp;
+  MlpPacked *mlp_dev = nullptr;
+  bool have_mlp = false;
 };
 
 namespace {
@@ -249,6 +252,8 @@ void fill_kparams(cmles_handle h) {
   F.pv_b = (float)K.pv_b;
   F.dcp = (float)K.dcp;
   F.CsDelta2 = (float)K.CsDelta2;
+  F.Delta = (float)Delta;
+  K.mlp = h->mlp_dev;
   F.inv_Prt = (float)K.inv_Prt;
   for (int d = 0; d < 3; ++d) {
     F.jac[d] = (float)K.jac[d];
@@ -351,7 +356,11 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   if (params->precision != CMLES_FP64 && params->precision != CMLES_FP32_ACC64) return CMLES_ERR_ARG;
   // the FP32 shadow is relative to a per-level reference: z must not wrap
   if (params->precision == CMLES_FP32_ACC64 && mesh->periodic[2]) return CMLES_ERR_ARG;
-  if (params->closure != CMLES_CLOSURE_NONE && params->closure != CMLES_CLOSURE_SL) return CMLES_ERR_ARG;
+  if (params->closure != CMLES_CLOSURE_NONE && params->closure != CMLES_CLOSURE_SL &&
+      params->closure != CMLES_CLOSURE_MLP)
+    return CMLES_ERR_ARG;
+  // the learned closure runs on BF16 tensor cores inside the FP32 kernels
+  if (params->closure == CMLES_CLOSURE_MLP && params->precision != CMLES_FP32_ACC64) return CMLES_ERR_ARG;
   long long E = (long long)mesh->nex * mesh->ney * mesh->nez;
   if (E > 0x7fffffffLL / 8) return CMLES_ERR_MESH;
   cmles_handle h = new cmles_t();
@@ -394,6 +403,7 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   ALLOC(h->lev32, (size_t)nlev * L_NF * sizeof(float));
   ALLOC(h->dH32, (size_t)mesh->nez * h->Nq * h->Nq * sizeof(float));
   ALLOC(h->qref64, (size_t)nlev * 4 * sizeof(double));
+  ALLOC(h->mlp_dev, sizeof(MlpPacked));
   ALLOC(h->rho_r, nlev * sizeof(double));
   ALLOC(h->p_r, nlev * sizeof(double));
   ALLOC(h->qt_r, nlev * sizeof(double));
@@ -439,6 +449,7 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
     e = cudaMemcpy(h->tau_col, tc.data(), tc.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->wq, wq.data(), h->Np * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(h->flags, 0, 16 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->mlp_dev, 0, sizeof(MlpPacked));
   if (e == cudaSuccess && h->dQ) e = cudaMemset(h->dQ, 0, n6 * sizeof(double));
   if (e == cudaSuccess && h->dQ32) e = cudaMemset(h->dQ32, 0, (size_t)E * 128 * 6 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(h->Q[0], 0, n6 * sizeof(double));
@@ -460,7 +471,7 @@ cmles_status cmles_destroy(cmles_handle h) {
   void *bufs[] = {h->Q[0],   h->Q[1],    h->dQ,      h->F2,       h->aux,     h->rho_r,    h->p_r,
                   h->qt_r,   h->tau_lev, h->tau_col, h->wq,       h->flags,   h->partials, h->budget_out,
                   h->prof,   h->S32[0],  h->S32[1],  h->dQ32,     h->F2_32,   h->aux32,    h->lev32,
-                  h->dH32,   h->qref64};
+                  h->dH32,   h->qref64,  h->mlp_dev};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete h;
@@ -710,6 +721,8 @@ cmles_status cmles_get_state_host(cmles_handle h, double *Q_host) {
 cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev) {
   if (!h || !Q_dev || !RHS_dev) return fail(h, CMLES_ERR_ARG, "cmles_tendency: null argument");
   if (!h->have_ref) return fail(h, CMLES_ERR_STATE, "cmles_tendency: reference state not set");
+  if (h->prm.closure == CMLES_CLOSURE_MLP && !h->have_mlp)
+    return fail(h, CMLES_ERR_STATE, "cmles_tendency: closure weights not set");
   StageCoef sc = {0.0, 0.0, 0.0};
   if (h->fp32) {
     // shadow of Q_dev into the idle shadow buffer; the handle's state is untouched
@@ -726,6 +739,8 @@ cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev
 cmles_status cmles_step(cmles_handle h, int nsteps) {
   if (!h || nsteps < 0) return fail(h, CMLES_ERR_ARG, "cmles_step: bad argument");
   if (!h->have_ref) return fail(h, CMLES_ERR_STATE, "cmles_step: reference state not set");
+  if (h->prm.closure == CMLES_CLOSURE_MLP && !h->have_mlp)
+    return fail(h, CMLES_ERR_STATE, "cmles_step: closure weights not set");
   if (h->fp32) {
     cmles_status st = ensure_shadow(h);
     if (st != CMLES_OK) return st;
@@ -805,8 +820,24 @@ cmles_status cmles_profiles(cmles_handle h, double *out_host) {
 
 cmles_status cmles_set_closure_weights(cmles_handle h, const float *params_host, size_t n) {
   if (!h || !params_host) return fail(h, CMLES_ERR_ARG, "cmles_set_closure_weights: null argument");
-  if (n != 5199) return fail(h, CMLES_ERR_ARG, "cmles_set_closure_weights: expected 5199 values");
+  if (n != (size_t)kMlpParams)
+    return fail(h, CMLES_ERR_ARG, "cmles_set_closure_weights: expected " + std::to_string(kMlpParams) + " values");
   h->mlp.assign(params_host, params_host + n);
+  MlpPacked pk;
+  pack_mlp_host(params_host, &pk);
+  CK(cudaMemcpyAsync(h->mlp_dev, &pk, sizeof(pk), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->have_mlp = true;
+  return CMLES_OK;
+}
+
+cmles_status cmles_set_closure_weights_device(cmles_handle h, const float *params_dev) {
+  if (!h || !params_dev) return fail(h, CMLES_ERR_ARG, "cmles_set_closure_weights_device: null argument");
+  {
+    LaunchScope ls(h, 2, 1);
+    CK(launch_pack_mlp(params_dev, h->mlp_dev, h->stream));
+  }
+  h->have_mlp = true;
   return CMLES_OK;
 }
 

@@ -18,7 +18,7 @@ constexpr int kMaxQ = 8;
 // FP32 copies of the constants used by the FP32 kernels.
 struct KF {
   float g, Rd, Rv, cvd, cvv, cvl, T0, Lv0, Iv0, kappa, pv_ptr, pv_Ttr, pv_a, pv_b, dcp;
-  float CsDelta2, inv_Prt;
+  float CsDelta2, inv_Prt, Delta;
   float jac[3], lift[3];
   float u_relax[3], Omega[3];
   float E_water, E_energy;
@@ -63,6 +63,7 @@ struct KParams {
   // the 5 x 5 differences of rho e_r + p_r along z, per level FP64 offsets
   const float *lev32, *dH32;
   const double *qref64;
+  const struct MlpPacked *mlp;  // learned-closure weights (closure == 2)
   // LGL basis
   double D[kMaxQ * kMaxQ], w[kMaxQ], xi[kMaxQ];
   KF f;

@@ -21,6 +21,7 @@
 // shadow rewritten from it.  Element traversal: 4 x 4 column tiles.
 #include "common.cuh"
 #include "launch.h"
+#include "mlp.cuh"
 
 namespace cmles {
 
@@ -104,18 +105,29 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
   o.thvp = L[L_THV] * expm1f(lnr);  // theta_v - theta_v,r
 }
 
-template <int N, bool MOIST>
-__global__ void __launch_bounds__(128, 8) k_grad32(const float *__restrict__ S, float *__restrict__ F2,
-                                                   float *__restrict__ aux, const KParams P) {
+// CL: 1 Smagorinsky-Lilly with Richardson correction, 2 learned closure
+// (tensor-core MLP on the velocity and theta_v gradients and Delta).
+template <int N, bool MOIST, int CL>
+__global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__restrict__ S, float *__restrict__ F2,
+                                                                 float *__restrict__ aux, const KParams P) {
   constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
   static_assert(Np <= kNP, "one node per thread");
   __shared__ float sD[Nq * Nq];
   __shared__ float sG[6][kNP];
   __shared__ float sGf[6][6][Nf];
   __shared__ int sNb[6];
+  __shared__ __align__(16) uint8_t sMlpRaw[CL == 2 ? sizeof(MlpPacked) : 16];
+  __shared__ __align__(16) __nv_bfloat16 sX[CL == 2 ? kNP * kMlpInPad : 8];
+  __shared__ float sY[CL == 2 ? kNP * 2 : 2];
   const KF &F = P.f;
   const int t = threadIdx.x;
   if (t < Nq * Nq) sD[t] = (float)P.D[t];
+  const MlpPacked &W = *reinterpret_cast<const MlpPacked *>(sMlpRaw);
+  if (CL == 2) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(P.mlp);
+    uint4 *dst = reinterpret_cast<uint4 *>(sMlpRaw);
+    for (int q = t; q < (int)(sizeof(MlpPacked) / 16); q += blockDim.x) dst[q] = src[q];
+  }
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
   int fail = 0;
   for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
@@ -163,8 +175,9 @@ __global__ void __launch_bounds__(128, 8) k_grad32(const float *__restrict__ S, 
       sGf[f][5][fn] = o.thvp;
     }
     __syncthreads();
+    float gr[6][3];
+    float nut = 0.f, Dt = 0.f;
     if (t < Np) {
-      float gr[6][3];
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
@@ -199,8 +212,7 @@ __global__ void __launch_bounds__(128, 8) k_grad32(const float *__restrict__ S, 
       if (k == 0) lift(4, i + Nq * j);
       if (k == N) lift(5, i + Nq * j);
 
-      float nut = 0.f, Dt = 0.f;
-      if (P.closure == 1) {
+      if (CL == 1 && P.closure == 1) {
         float S2 = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -225,6 +237,35 @@ __global__ void __launch_bounds__(128, 8) k_grad32(const float *__restrict__ S, 
           Dt = nut * F.inv_Prt;
         }
       }
+    }
+    if (CL == 2) {
+      // closure network inputs: 9 velocity gradients, 3 theta_v gradients, Delta
+      uint32_t *xr = reinterpret_cast<uint32_t *>(sX + t * kMlpInPad);
+      if (t < Np) {
+        float x[kMlpInPad];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) x[3 * a + b] = gr[a][b] * W.in_scale[3 * a + b];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) x[9 + b] = gr[5][b] * W.in_scale[9 + b];
+        x[12] = F.Delta * W.in_scale[12];
+        x[13] = x[14] = x[15] = 0.f;
+#pragma unroll
+        for (int q = 0; q < kMlpInPad / 2; ++q) xr[q] = pack_bf16(x[2 * q], x[2 * q + 1]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < kMlpInPad / 2; ++q) xr[q] = 0u;
+      }
+      __syncwarp();
+      mlp_warp_forward(W, sX, sY, 32 * (t >> 5));
+      __syncwarp();
+      if (t < Np) {
+        nut = W.out_scale[0] * fmaxf(sY[2 * t], 0.f);
+        Dt = W.out_scale[1] * fmaxf(sY[2 * t + 1], 0.f);
+      }
+    }
+    if (t < Np) {
       const float rho = L[L_RHO] + sv[0];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -454,15 +495,24 @@ cudaError_t launch_shadow32(const double *Q64, float *S, const KParams &P, int N
   return cudaGetLastError();
 }
 
+template <bool MOIST, int CL>
+static void grad32_instance(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s) {
+  static int grid = 0;
+  if (!grid) grid = grid_for((const void *)k_grad32<4, MOIST, CL>, 1 << 30, 0);
+  k_grad32<4, MOIST, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, P);
+}
+
 cudaError_t launch_grad32(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s) {
-  if (P.moist) {
-    static int grid = 0;
-    if (!grid) grid = grid_for((const void *)k_grad32<4, true>, 1 << 30, 0);
-    k_grad32<4, true><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, P);
+  if (P.closure == 2) {
+    if (P.moist)
+      grad32_instance<true, 2>(S, F2, aux, P, s);
+    else
+      grad32_instance<false, 2>(S, F2, aux, P, s);
   } else {
-    static int grid = 0;
-    if (!grid) grid = grid_for((const void *)k_grad32<4, false>, 1 << 30, 0);
-    k_grad32<4, false><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, P);
+    if (P.moist)
+      grad32_instance<true, 1>(S, F2, aux, P, s);
+    else
+      grad32_instance<false, 1>(S, F2, aux, P, s);
   }
   return cudaGetLastError();
 }

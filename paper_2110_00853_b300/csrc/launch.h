@@ -20,6 +20,11 @@ cudaError_t launch_grad32(const float *S, float *F2, float *aux, const KParams &
 cudaError_t launch_rhs32(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
                          double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s);
 
+// Learned closure network (mlp.cu)
+struct MlpPacked;
+void pack_mlp_host(const float *params, MlpPacked *out);
+cudaError_t launch_pack_mlp(const float *params_dev, MlpPacked *out, cudaStream_t s);
+
 // Diagnostics and set-up (aux_kernels.cu)
 // Budgets: partial sums per block into partials[nblocks][7] (6 integrals and a
 // non-finite count), then a single-block pass in fixed order into out[7].

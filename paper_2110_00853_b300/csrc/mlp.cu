@@ -1,0 +1,358 @@
+// Learned-closure network: weight packing, batched inference, BF16
+// tensor-core training step (forward, backward, weight gradients) and Adam.
+//
+// Loss: L = 1/(2n) sum_s |y_s - t_s|^2 over the n samples of a call.
+// Backward (per sample, FP32 with BF16 tensor-core products):
+//   dy = (y - t)/n,  dh2 = W3^T dy,  da2 = dh2 * silu'(a2),
+//   dh1 = W2^T da2,  da1 = dh1 * silu'(a1),  silu'(a) = s (1 + a (1 - s)),
+//   gW3 += dy h2^T, gW2 += da2 h1^T, gW1 += da1 x^T, gb_l += da_l.
+// One CTA of 128 threads handles 128 samples per iteration (one row per
+// thread for pointwise work, 4 warps x 32 rows for the mma.sync products) and
+// keeps its gradient partial sums in shared memory until the end.
+#include <string.h>
+
+#include "cmles.h"
+#include "common.cuh"
+#include "launch.h"
+#include "mlp.cuh"
+
+namespace cmles {
+
+// ------------------------------------------------------------------ packing
+
+void pack_mlp_host(const float *p, MlpPacked *o) {
+  memset(o, 0, sizeof(*o));
+  for (int n = 0; n < kMlpH; ++n)
+    for (int k = 0; k < kMlpIn; ++k) o->W1[n * kMlpInPad + k] = __float2bfloat16_rn(p[kMlpOffW1 + n * kMlpIn + k]);
+  for (int n = 0; n < kMlpH; ++n)
+    for (int k = 0; k < kMlpH; ++k) o->W2[n * kMlpH + k] = __float2bfloat16_rn(p[kMlpOffW2 + n * kMlpH + k]);
+  for (int n = 0; n < kMlpOut; ++n)
+    for (int k = 0; k < kMlpH; ++k) o->W3[n * kMlpH + k] = __float2bfloat16_rn(p[kMlpOffW3 + n * kMlpH + k]);
+  for (int n = 0; n < kMlpH; ++n) {
+    o->b1[n] = p[kMlpOffB1 + n];
+    o->b2[n] = p[kMlpOffB2 + n];
+  }
+  o->b3[0] = p[kMlpOffB3];
+  o->b3[1] = p[kMlpOffB3 + 1];
+  for (int k = 0; k < kMlpIn; ++k) o->in_scale[k] = p[kMlpOffIn + k];
+  o->out_scale[0] = p[kMlpOffOut];
+  o->out_scale[1] = p[kMlpOffOut + 1];
+}
+
+__global__ void k_pack_mlp(const float *__restrict__ p, MlpPacked *__restrict__ o) {
+  const int t = threadIdx.x + blockIdx.x * blockDim.x, nt = blockDim.x * gridDim.x;
+  for (int q = t; q < kMlpH * kMlpInPad; q += nt) {
+    const int n = q / kMlpInPad, k = q % kMlpInPad;
+    o->W1[q] = __float2bfloat16_rn(k < kMlpIn ? p[kMlpOffW1 + n * kMlpIn + k] : 0.f);
+  }
+  for (int q = t; q < kMlpH * kMlpH; q += nt) o->W2[q] = __float2bfloat16_rn(p[kMlpOffW2 + q]);
+  for (int q = t; q < kMlpOutPad * kMlpH; q += nt) {
+    const int n = q / kMlpH;
+    o->W3[q] = __float2bfloat16_rn(n < kMlpOut ? p[kMlpOffW3 + q] : 0.f);
+  }
+  for (int q = t; q < kMlpH; q += nt) {
+    o->b1[q] = p[kMlpOffB1 + q];
+    o->b2[q] = p[kMlpOffB2 + q];
+  }
+  for (int q = t; q < kMlpOutPad; q += nt) o->b3[q] = q < kMlpOut ? p[kMlpOffB3 + q] : 0.f;
+  for (int q = t; q < kMlpInPad; q += nt) o->in_scale[q] = q < kMlpIn ? p[kMlpOffIn + q] : 0.f;
+  if (t < 2) o->out_scale[t] = p[kMlpOffOut + t];
+}
+
+cudaError_t launch_pack_mlp(const float *params_dev, MlpPacked *out, cudaStream_t s) {
+  k_pack_mlp<<<8, 256, 0, s>>>(params_dev, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ inference
+
+__global__ void __launch_bounds__(128) k_mlp_forward(const MlpPacked *__restrict__ Wg, const float *__restrict__ X,
+                                                     float *__restrict__ Y, long long n) {
+  __shared__ __align__(16) uint8_t sWraw[sizeof(MlpPacked)];
+  __shared__ __align__(16) __nv_bfloat16 sX[128 * kMlpInPad];
+  __shared__ float sY[128 * 2];
+  const int t = threadIdx.x;
+  for (int q = t; q < (int)(sizeof(MlpPacked) / 16); q += 128)
+    reinterpret_cast<uint4 *>(sWraw)[q] = reinterpret_cast<const uint4 *>(Wg)[q];
+  __syncthreads();
+  const MlpPacked &W = *reinterpret_cast<const MlpPacked *>(sWraw);
+  for (long long b = (long long)blockIdx.x * 128; b < n; b += (long long)gridDim.x * 128) {
+    const long long s = b + t;
+    uint32_t *xr = reinterpret_cast<uint32_t *>(sX + t * kMlpInPad);
+    float x[kMlpInPad];
+#pragma unroll
+    for (int k = 0; k < kMlpInPad; ++k) x[k] = (s < n && k < kMlpIn) ? X[s * kMlpIn + k] : 0.f;
+#pragma unroll
+    for (int q = 0; q < kMlpInPad / 2; ++q) xr[q] = pack_bf16(x[2 * q], x[2 * q + 1]);
+    __syncwarp();
+    mlp_warp_forward(W, sX, sY, 32 * (t >> 5));
+    __syncwarp();
+    if (s < n) {
+      Y[s * 2 + 0] = sY[2 * t];
+      Y[s * 2 + 1] = sY[2 * t + 1];
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ training
+
+struct TrainSmem {
+  MlpPacked W;
+  __nv_bfloat16 W2T[kMlpH * kMlpH];     // W2^T: [in][out]
+  __nv_bfloat16 X[128 * kMlpInPad];     // inputs, row-major
+  __nv_bfloat16 XT[kMlpInPad * 128];    // inputs, [feature][sample]
+  float A1[128 * kMlpH], A2[128 * kMlpH];  // pre-activations
+  float Y[128 * 2], DY[128 * 2];
+  __nv_bfloat16 DA2[128 * kMlpH];       // da2, row-major
+  __nv_bfloat16 DA2T[kMlpH * 128];      // da2, [unit][sample]
+  __nv_bfloat16 DA1T[kMlpH * 128];      // da1, [unit][sample]
+  __nv_bfloat16 H1T[kMlpH * 128];       // h1 = silu(a1), [unit][sample]
+  float g[kMlpNet];                     // gradient partial sums (parameter-vector layout)
+  float loss;
+};
+
+__device__ __forceinline__ float dsilu(float a) {
+  const float sg = 1.0f / (1.0f + expf(-a));
+  return sg * (1.0f + a * (1.0f - sg));
+}
+
+__global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__ Wg, const float *__restrict__ X,
+                                                   const float *__restrict__ T, long long n,
+                                                   float *__restrict__ grad, float *__restrict__ loss) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  TrainSmem &S = *reinterpret_cast<TrainSmem *>(smem_raw);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, c = lane & 3;
+  for (int q = t; q < (int)(sizeof(MlpPacked) / 16); q += 128)
+    reinterpret_cast<uint4 *>(&S.W)[q] = reinterpret_cast<const uint4 *>(Wg)[q];
+  for (int q = t; q < kMlpNet; q += 128) S.g[q] = 0.f;
+  if (t == 0) S.loss = 0.f;
+  __syncthreads();
+  for (int q = t; q < kMlpH * kMlpH; q += 128) {
+    const int o = q / kMlpH, i = q % kMlpH;
+    S.W2T[i * kMlpH + o] = S.W.W2[q];
+  }
+  __syncthreads();
+  const float inv_n = 1.0f / (float)n;
+  for (long long b = (long long)blockIdx.x * 128; b < n; b += (long long)gridDim.x * 128) {
+    const long long s = b + t;
+    const bool valid = s < n;
+    // inputs (bf16), row-major and transposed
+    {
+      uint32_t *xr = reinterpret_cast<uint32_t *>(S.X + t * kMlpInPad);
+      float x[kMlpInPad];
+#pragma unroll
+      for (int k = 0; k < kMlpInPad; ++k) x[k] = (valid && k < kMlpIn) ? X[s * kMlpIn + k] : 0.f;
+#pragma unroll
+      for (int q = 0; q < kMlpInPad / 2; ++q) xr[q] = pack_bf16(x[2 * q], x[2 * q + 1]);
+#pragma unroll
+      for (int k = 0; k < kMlpInPad; ++k) S.XT[k * 128 + t] = __float2bfloat16_rn(x[k]);
+    }
+    __syncwarp();
+    mlp_warp_forward(S.W, S.X, S.Y, 32 * warp, S.A1, S.A2, kMlpH);
+    __syncthreads();
+    // output error, loss, gW3 and gb3 pieces
+    float dy0 = 0.f, dy1 = 0.f;
+    if (valid) {
+      const float r0 = S.Y[2 * t] - T[s * 2], r1 = S.Y[2 * t + 1] - T[s * 2 + 1];
+      atomicAdd(&S.loss, 0.5f * (r0 * r0 + r1 * r1) * inv_n);
+      dy0 = r0 * inv_n;
+      dy1 = r1 * inv_n;
+    }
+    S.DY[2 * t] = dy0;
+    S.DY[2 * t + 1] = dy1;
+    __syncthreads();
+    {
+      // thread t: output unit o = t / 64, hidden unit i = t % 64
+      const int o = t >> 6, i = t & 63;
+      float acc = 0.f, accb = 0.f;
+      for (int r = 0; r < 128; ++r) {
+        const float d = S.DY[2 * r + o];
+        acc += d * silu(S.A2[r * kMlpH + i]);
+        accb += d;
+      }
+      S.g[kMlpOffW3 + o * kMlpH + i] += acc;
+      if (i == 0) S.g[kMlpOffB3 + o] += accb;
+    }
+    // da2 = (W3^T dy) * silu'(a2): thread per sample
+    for (int i = 0; i < kMlpH; ++i) {
+      const float w0 = __bfloat162float(S.W.W3[0 * kMlpH + i]), w1 = __bfloat162float(S.W.W3[1 * kMlpH + i]);
+      const float da = (w0 * dy0 + w1 * dy1) * dsilu(S.A2[t * kMlpH + i]);
+      const __nv_bfloat16 db = __float2bfloat16_rn(da);
+      S.DA2[t * kMlpH + i] = db;
+      S.DA2T[i * 128 + t] = db;
+      atomicAdd(&S.g[kMlpOffB2 + i], da);
+    }
+    // h1^T (bf16)
+    for (int i = 0; i < kMlpH; ++i) S.H1T[i * 128 + t] = __float2bfloat16_rn(silu(S.A1[t * kMlpH + i]));
+    __syncthreads();
+    // dh1 = da2 W2 (per warp: its 32 rows), then da1 = dh1 * silu'(a1)
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+      const int rb = 32 * warp + 16 * mt;
+      uint32_t a[4][4];
+#pragma unroll
+      for (int kt = 0; kt < 4; ++kt) {
+        a[kt][0] = ld_u32(S.DA2 + (rb + g) * kMlpH + 16 * kt + 2 * c);
+        a[kt][1] = ld_u32(S.DA2 + (rb + g + 8) * kMlpH + 16 * kt + 2 * c);
+        a[kt][2] = ld_u32(S.DA2 + (rb + g) * kMlpH + 16 * kt + 2 * c + 8);
+        a[kt][3] = ld_u32(S.DA2 + (rb + g + 8) * kMlpH + 16 * kt + 2 * c + 8);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt)
+          mma_bf16_16816(d, a[kt], ld_u32(S.W2T + (8 * nt + g) * kMlpH + 16 * kt + 2 * c),
+                         ld_u32(S.W2T + (8 * nt + g) * kMlpH + 16 * kt + 2 * c + 8));
+        const int col = 8 * nt + 2 * c;
+        const int rows[2] = {rb + g, rb + g + 8};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int r = rows[h], cc = col + e;
+            const float da = d[2 * h + e] * dsilu(S.A1[r * kMlpH + cc]);
+            S.DA1T[cc * 128 + r] = __float2bfloat16_rn(b + r < n ? da : 0.f);
+            if (b + r < n) atomicAdd(&S.g[kMlpOffB1 + cc], da);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // gW2 = da2^T h1 (warp w: output rows 16w..16w+15), K = 128 samples
+    {
+      const int ob = 16 * warp;
+      float acc[8][4];
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll 2
+      for (int kt = 0; kt < 8; ++kt) {
+        uint32_t a[4];
+        a[0] = ld_u32(S.DA2T + (ob + g) * 128 + 16 * kt + 2 * c);
+        a[1] = ld_u32(S.DA2T + (ob + g + 8) * 128 + 16 * kt + 2 * c);
+        a[2] = ld_u32(S.DA2T + (ob + g) * 128 + 16 * kt + 2 * c + 8);
+        a[3] = ld_u32(S.DA2T + (ob + g + 8) * 128 + 16 * kt + 2 * c + 8);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+          mma_bf16_16816(acc[nt], a, ld_u32(S.H1T + (8 * nt + g) * 128 + 16 * kt + 2 * c),
+                         ld_u32(S.H1T + (8 * nt + g) * 128 + 16 * kt + 2 * c + 8));
+      }
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const int col = 8 * nt + 2 * c;
+        S.g[kMlpOffW2 + (ob + g) * kMlpH + col] += acc[nt][0];
+        S.g[kMlpOffW2 + (ob + g) * kMlpH + col + 1] += acc[nt][1];
+        S.g[kMlpOffW2 + (ob + g + 8) * kMlpH + col] += acc[nt][2];
+        S.g[kMlpOffW2 + (ob + g + 8) * kMlpH + col + 1] += acc[nt][3];
+      }
+      // gW1 = da1^T x, 2 n-tiles of 8 inputs (13 used)
+      float acc1[2][4];
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) acc1[nt][0] = acc1[nt][1] = acc1[nt][2] = acc1[nt][3] = 0.f;
+#pragma unroll 2
+      for (int kt = 0; kt < 8; ++kt) {
+        uint32_t a[4];
+        a[0] = ld_u32(S.DA1T + (ob + g) * 128 + 16 * kt + 2 * c);
+        a[1] = ld_u32(S.DA1T + (ob + g + 8) * 128 + 16 * kt + 2 * c);
+        a[2] = ld_u32(S.DA1T + (ob + g) * 128 + 16 * kt + 2 * c + 8);
+        a[3] = ld_u32(S.DA1T + (ob + g + 8) * 128 + 16 * kt + 2 * c + 8);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+          mma_bf16_16816(acc1[nt], a, ld_u32(S.XT + (8 * nt + g) * 128 + 16 * kt + 2 * c),
+                         ld_u32(S.XT + (8 * nt + g) * 128 + 16 * kt + 2 * c + 8));
+      }
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int col = 8 * nt + 2 * c;
+        if (col < kMlpIn) {
+          S.g[kMlpOffW1 + (ob + g) * kMlpIn + col] += acc1[nt][0];
+          S.g[kMlpOffW1 + (ob + g + 8) * kMlpIn + col] += acc1[nt][2];
+        }
+        if (col + 1 < kMlpIn) {
+          S.g[kMlpOffW1 + (ob + g) * kMlpIn + col + 1] += acc1[nt][1];
+          S.g[kMlpOffW1 + (ob + g + 8) * kMlpIn + col + 1] += acc1[nt][3];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int q = t; q < kMlpNet; q += 128) atomicAdd(&grad[q], S.g[q]);
+  if (t == 0) atomicAdd(loss, S.loss);
+}
+
+// Adam (Kingma & Ba 2015) on the network parameters of the FP32 vector.
+__global__ void k_mlp_adam(float *__restrict__ p, const float *__restrict__ gr, float *__restrict__ m,
+                           float *__restrict__ v, int count, float lr, float b1, float b2, float eps, float c1,
+                           float c2) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const float gq = gr[q];
+  const float mq = b1 * m[q] + (1.0f - b1) * gq;
+  const float vq = b2 * v[q] + (1.0f - b2) * gq * gq;
+  m[q] = mq;
+  v[q] = vq;
+  p[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+}
+
+static int train_grid() {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return nsm;
+}
+
+}  // namespace cmles
+
+using namespace cmles;
+
+extern "C" {
+
+cmles_status cmles_mlp_forward(const float *params_dev, const float *X_dev, float *Y_dev, long long n, void *stream) {
+  if (!params_dev || !X_dev || !Y_dev || n < 0) return CMLES_ERR_ARG;
+  if (n == 0) return CMLES_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  MlpPacked *pk = nullptr;
+  if (cudaMallocAsync((void **)&pk, sizeof(MlpPacked), s) != cudaSuccess) return CMLES_ERR_OOM;
+  k_pack_mlp<<<8, 256, 0, s>>>(params_dev, pk);
+  long long blocks = (n + 127) / 128;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  k_mlp_forward<<<(int)blocks, 128, 0, s>>>(pk, X_dev, Y_dev, n);
+  cudaFreeAsync(pk, s);
+  return cudaGetLastError() == cudaSuccess ? CMLES_OK : CMLES_ERR_CUDA;
+}
+
+cmles_status cmles_mlp_loss_grad(const float *params_dev, const float *X_dev, const float *T_dev, long long n,
+                                 float *grad_dev, float *loss_dev, void *stream) {
+  if (!params_dev || !X_dev || !T_dev || !grad_dev || !loss_dev || n <= 0) return CMLES_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  static bool attr = false;
+  const int smem = (int)sizeof(TrainSmem);
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return CMLES_ERR_CUDA;
+    attr = true;
+  }
+  MlpPacked *pk = nullptr;
+  if (cudaMallocAsync((void **)&pk, sizeof(MlpPacked), s) != cudaSuccess) return CMLES_ERR_OOM;
+  k_pack_mlp<<<8, 256, 0, s>>>(params_dev, pk);
+  cudaMemsetAsync(grad_dev, 0, kMlpNet * sizeof(float), s);
+  cudaMemsetAsync(loss_dev, 0, sizeof(float), s);
+  long long blocks = (n + 127) / 128;
+  const int cap = train_grid();
+  if (blocks > cap) blocks = cap;
+  k_mlp_train<<<(int)blocks, 128, smem, s>>>(pk, X_dev, T_dev, n, grad_dev, loss_dev);
+  cudaFreeAsync(pk, s);
+  return cudaGetLastError() == cudaSuccess ? CMLES_OK : CMLES_ERR_CUDA;
+}
+
+cmles_status cmles_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, int t, float lr,
+                            float beta1, float beta2, float eps, void *stream) {
+  if (!params_dev || !grad_dev || !m_dev || !v_dev || t < 1) return CMLES_ERR_ARG;
+  const float c1 = 1.0f - powf(beta1, (float)t), c2 = 1.0f - powf(beta2, (float)t);
+  k_mlp_adam<<<(kMlpNet + 255) / 256, 256, 0, (cudaStream_t)stream>>>(params_dev, grad_dev, m_dev, v_dev, kMlpNet,
+                                                                      lr, beta1, beta2, eps, c1, c2);
+  return cudaGetLastError() == cudaSuccess ? CMLES_OK : CMLES_ERR_CUDA;
+}
+
+}  // extern "C"

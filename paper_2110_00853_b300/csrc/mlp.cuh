@@ -1,0 +1,124 @@
+// Learned SGS closure network on tensor cores: 13 -> 64 -> 64 -> 2, SiLU
+// hidden activations, BF16 weights and activations, FP32 accumulation.
+// (The paper has no learned closure; this network is the workload's
+// extension of the method, with Smagorinsky-Lilly kept as fallback.)
+//
+// One warp evaluates 32 rows (two m16 tiles) with mma.sync m16n8k16 BF16.
+// The accumulator fragment of two neighbouring n8 tiles is exactly the A
+// fragment of the next layer's k16 tile, so hidden activations never leave
+// registers.  Weights are stored out-major with the input index contiguous
+// (W[n][k]), which is the k-contiguous B layout the instruction wants.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace cmles {
+
+constexpr int kMlpIn = 13, kMlpH = 64, kMlpOut = 2;
+constexpr int kMlpInPad = 16, kMlpOutPad = 8;
+// FP32 parameter vector: W1[64][13], b1[64], W2[64][64], b2[64], W3[2][64],
+// b3[2], in_scale[13], out_scale[2]
+constexpr int kMlpOffW1 = 0, kMlpOffB1 = 832, kMlpOffW2 = 896, kMlpOffB2 = 4992, kMlpOffW3 = 5056,
+              kMlpOffB3 = 5184, kMlpOffIn = 5186, kMlpOffOut = 5199, kMlpParams = 5201, kMlpNet = 5186;
+
+// Packed device copy used by the kernels (16-byte aligned, size a multiple of
+// 16 so that it can be staged into shared memory with 16-byte copies).
+struct __align__(16) MlpPacked {
+  __nv_bfloat16 W1[kMlpH * kMlpInPad];   // [64][16], k >= 13 zero
+  __nv_bfloat16 W2[kMlpH * kMlpH];       // [64][64]
+  __nv_bfloat16 W3[kMlpOutPad * kMlpH];  // [8][64], n >= 2 zero
+  float b1[kMlpH], b2[kMlpH], b3[kMlpOutPad];
+  float in_scale[kMlpInPad], out_scale[2];
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float silu(float x) { return x / (1.0f + expf(-x)); }
+
+__device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+// Forward pass of the 32 rows [r0, r0 + 32) of X (bf16 [rows][16], shared
+// memory) by one warp; writes Y[row][0..1] (FP32, shared memory).
+// Optionally stores the pre-activations of both hidden layers (FP32,
+// [rows][64] each) for the backward pass.
+__device__ __forceinline__ void mlp_warp_forward(const MlpPacked &W, const __nv_bfloat16 *X, float *Y, int r0,
+                                                 float *A1 = nullptr, float *A2 = nullptr, int lda = 0) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+#pragma unroll 1
+  for (int mt = 0; mt < 2; ++mt) {
+    const int rb = r0 + 16 * mt;
+    uint32_t a[4];
+    a[0] = ld_u32(X + (rb + g) * kMlpInPad + 2 * c);
+    a[1] = ld_u32(X + (rb + g + 8) * kMlpInPad + 2 * c);
+    a[2] = ld_u32(X + (rb + g) * kMlpInPad + 2 * c + 8);
+    a[3] = ld_u32(X + (rb + g + 8) * kMlpInPad + 2 * c + 8);
+    // layer 1: 8 n-tiles, one k-tile; outputs repacked as 4 k-tiles of layer 2
+    uint32_t h1[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      float d[4];
+      d[0] = d[2] = W.b1[8 * nt + 2 * c];
+      d[1] = d[3] = W.b1[8 * nt + 2 * c + 1];
+      mma_bf16_16816(d, a, ld_u32(W.W1 + (8 * nt + g) * kMlpInPad + 2 * c),
+                     ld_u32(W.W1 + (8 * nt + g) * kMlpInPad + 2 * c + 8));
+      if (A1) {
+        A1[(rb + g) * lda + 8 * nt + 2 * c] = d[0];
+        A1[(rb + g) * lda + 8 * nt + 2 * c + 1] = d[1];
+        A1[(rb + g + 8) * lda + 8 * nt + 2 * c] = d[2];
+        A1[(rb + g + 8) * lda + 8 * nt + 2 * c + 1] = d[3];
+      }
+      const int kt = nt >> 1, hi = nt & 1;
+      h1[kt][0 + 2 * hi] = pack_bf16(silu(d[0]), silu(d[1]));
+      h1[kt][1 + 2 * hi] = pack_bf16(silu(d[2]), silu(d[3]));
+    }
+    // layer 2 and 3
+    float y[4] = {0.f, 0.f, 0.f, 0.f};
+    y[0] = y[2] = W.b3[2 * c];
+    y[1] = y[3] = W.b3[2 * c + 1];
+    uint32_t h2[4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      float d[4];
+      d[0] = d[2] = W.b2[8 * nt + 2 * c];
+      d[1] = d[3] = W.b2[8 * nt + 2 * c + 1];
+#pragma unroll
+      for (int kt = 0; kt < 4; ++kt)
+        mma_bf16_16816(d, h1[kt], ld_u32(W.W2 + (8 * nt + g) * kMlpH + 16 * kt + 2 * c),
+                       ld_u32(W.W2 + (8 * nt + g) * kMlpH + 16 * kt + 2 * c + 8));
+      if (A2) {
+        A2[(rb + g) * lda + 8 * nt + 2 * c] = d[0];
+        A2[(rb + g) * lda + 8 * nt + 2 * c + 1] = d[1];
+        A2[(rb + g + 8) * lda + 8 * nt + 2 * c] = d[2];
+        A2[(rb + g + 8) * lda + 8 * nt + 2 * c + 1] = d[3];
+      }
+      const int hi = nt & 1;
+      h2[0 + 2 * hi] = pack_bf16(silu(d[0]), silu(d[1]));
+      h2[1 + 2 * hi] = pack_bf16(silu(d[2]), silu(d[3]));
+      if (hi) {  // a full k-tile of layer 3 is ready
+        const int kt = nt >> 1;
+        mma_bf16_16816(y, h2, ld_u32(W.W3 + g * kMlpH + 16 * kt + 2 * c),
+                       ld_u32(W.W3 + g * kMlpH + 16 * kt + 2 * c + 8));
+      }
+    }
+    if (c == 0) {
+      Y[(rb + g) * 2 + 0] = y[0];
+      Y[(rb + g) * 2 + 1] = y[1];
+      Y[(rb + g + 8) * 2 + 0] = y[2];
+      Y[(rb + g + 8) * 2 + 1] = y[3];
+    }
+  }
+}
+
+}  // namespace cmles
