@@ -38,7 +38,7 @@ BYTES = {
     "fp64": {"grad": (6 + 15 + 2) * 8, "rhs": (6 + 15 + 2 + 12 + 6) * 8},
     "fp32": {"grad": (6 + 15 + 2) * 4, "rhs": (6 + 15 + 2 + 12 + 6) * 4 + 12 * 8},
 }
-VARIANTS = {"fp32acc64_sl": ("fp32", "sl"), "fp64_sl": ("fp64", "sl")}
+VARIANTS = {"fp32acc64_mlp": ("fp32", "mlp"), "fp32acc64_sl": ("fp32", "sl"), "fp64_sl": ("fp64", "sl")}
 DTYPE = {"fp32": "f32", "fp64": "f64"}
 
 
@@ -112,6 +112,16 @@ def dist_setup():
     return world, rank, local
 
 
+def closure_weights():
+    """Seeded network of the closure's architecture (13 -> 64 -> 64 -> 2); the
+    throughput does not depend on the weight values.  Input scales match the
+    magnitudes of the box's gradients, output scales give nu_t, D_t of a few
+    m^2/s."""
+    from paper_2110_00853_b300 import closure
+    return closure.init_params(seed=0, in_scale=[100.0] * 9 + [300.0] * 3 + [0.02], out_scale=(5.0, 10.0),
+                               b3=(0.5, 0.5))
+
+
 def workload_mesh(sub):
     """the throughput box, or a sub-box of it with the same element size
     (used for small profiling cases)"""
@@ -123,6 +133,8 @@ def run_variant(name, precision, closure, steps, warmup, world, rank, torch, sub
     mesh, phys, case = workload_mesh(sub), I.physics(WORKLOAD, closure=closure), I.case(WORKLOAD)
     G = cmles.Solver(mesh, phys, precision=precision)
     G.init_case(case)
+    if closure == "mlp":
+        G.set_closure_weights(closure_weights())
     G.step(warmup)
     torch.cuda.synchronize()
     if world > 1:
@@ -168,6 +180,8 @@ def run_e2e(precision, closure, steps, torch):
     mesh, phys, case = I.mesh(WORKLOAD), I.physics(WORKLOAD, closure=closure), I.case(WORKLOAD)
     G = cmles.Solver(mesh, phys, precision=precision)
     G.init_case(case)
+    if closure == "mlp":
+        G.set_closure_weights(closure_weights())
     host = G.get_state_host()
     G.step(1)
     torch.cuda.synchronize()
@@ -221,7 +235,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sub", default=None, help="nex,ney,nez: run a sub-box of the workload (profiling cases)")
-    ap.add_argument("--variants", default="fp32acc64_sl,fp64_sl",
+    ap.add_argument("--variants", default="fp32acc64_mlp,fp32acc64_sl,fp64_sl",
                     help="comma list; the first is the headline value")
     args = ap.parse_args()
     sub = tuple(int(x) for x in args.sub.split(",")) if args.sub else None
@@ -280,7 +294,9 @@ def main():
                     warmup=args.warmup, ms_per_step=head["ms"] / args.steps, higher_is_better=True,
                     scaling="weak", vs_baseline=None, dtype=DTYPE[prec], data="synthetic",
                     config={"workload": f"{WORKLOAD}: 160x160x80 hexahedral elements, N=4 (256M nodes), moist, "
-                                        "Smagorinsky-Lilly, LSRK(5,4)", "variant": variants[0][0],
+                                        "LSRK(5,4)", "variant": variants[0][0],
+                            "closure": {"mlp": "learned (BF16 tensor-core MLP 13-64-64-2, seeded weights)",
+                                        "sl": "Smagorinsky-Lilly + Richardson"}[variants[0][2]],
                             "elements": head["nodes"] // 125, "nodes_per_gpu": head["nodes"],
                             "l2": "inputs larger than L2 (state alone 12 GB)", "parallelism": f"replicas{world}"},
                     roofline={"bound": "hbm", "kernel": kinds[dom], "achieved": achieved, "peak": hbm,

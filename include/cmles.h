@@ -204,6 +204,18 @@ cmles_status cmles_mlp_loss_grad(const float *params_dev, const float *X_dev, co
 cmles_status cmles_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, int t, float lr,
                             float beta1, float beta2, float eps, void *stream);
 
+/* Training samples for the learned closure from the handle's current state
+ * (a fine-resolution run): the fine field is top-hat filtered, width one
+ * coarse node spacing, onto the nodes of the mesh coarser by `factor` in every
+ * direction (element counts must be multiples of factor).  Per coarse node
+ * (coarse element-major, node-minor): X_dev[13] = filtered du_i/dx_j (index
+ * 3i+j), filtered d theta_v/dx_j (3), Delta_c; T_dev[2] = least-squares eddy
+ * viscosity and diffusivity max(0, -tau:S/(2 S:S)), max(0, -tau_th.g/|g|^2)
+ * from the filtered subgrid stress and theta_v flux.  *n_out receives the
+ * sample count; CMLES_ERR_ARG if capacity is smaller. */
+cmles_status cmles_closure_samples(cmles_handle h, int factor, float *X_dev, float *T_dev, long long capacity,
+                                   long long *n_out);
+
 /* Per-kernel timing: when enabled, every launch is bracketed by CUDA events
  * on the handle's stream; cmles_kernel_times returns, for the kernels
  * launched since the last reset, count[k] and total milliseconds[k] for

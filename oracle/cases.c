@@ -204,7 +204,7 @@ void orc_init_case(orc_solver *s, const orc_case *c, double *Q, double *rho_r, d
           double r = sqrt(ax * ax + az * az);
           if (r <= 1.0) th += 0.5 * c->dtheta * (1.0 + cos(M_PI * r));
         }
-        if (c->id == 5 && c->modes) {
+        if (c->modes) { /* random-phase velocity modes (throughput box, training runs) */
           for (int k = 0; k < c->nmodes; ++k) {
             const double *md = c->modes + (size_t)k * 7;
             double ph = md[0] * s->x[q] + md[1] * s->y[q] + md[2] * z + md[6];

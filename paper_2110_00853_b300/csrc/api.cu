@@ -841,6 +841,23 @@ cmles_status cmles_set_closure_weights_device(cmles_handle h, const float *param
   return CMLES_OK;
 }
 
+cmles_status cmles_closure_samples(cmles_handle h, int factor, float *X_dev, float *T_dev, long long capacity,
+                                   long long *n_out) {
+  if (!h || !X_dev || !T_dev || factor < 1) return fail(h, CMLES_ERR_ARG, "cmles_closure_samples: bad argument");
+  const cmles_mesh &m = h->mesh;
+  if (m.nex % factor || m.ney % factor || m.nez % factor)
+    return fail(h, CMLES_ERR_ARG, "cmles_closure_samples: element counts must be multiples of factor");
+  const long long nc = (long long)(m.nex / factor) * (m.ney / factor) * (m.nez / factor) * h->Np;
+  if (n_out) *n_out = nc;
+  if (capacity < nc) return fail(h, CMLES_ERR_ARG, "cmles_closure_samples: output capacity too small");
+  {
+    LaunchScope ls(h, 2, 3);
+    CK(launch_closure_samples(h->Q[h->cur], h->K, h->N, h->xi.data(), h->w.data(), h->D.data(), factor,
+                              m.periodic, X_dev, T_dev, nc, h->stream));
+  }
+  return CMLES_OK;
+}
+
 cmles_status cmles_enable_timing(cmles_handle h, int enable) {
   if (!h) return CMLES_ERR_ARG;
   h->timing = enable != 0;

@@ -25,6 +25,11 @@ struct MlpPacked;
 void pack_mlp_host(const float *params, MlpPacked *out);
 cudaError_t launch_pack_mlp(const float *params_dev, MlpPacked *out, cudaStream_t s);
 
+// Closure training samples from a fine run (filter.cu)
+cudaError_t launch_closure_samples(const double *Q, const KParams &P, int N, const double *xi, const double *w,
+                                   const double *D, int factor, const int periodic[3], float *X, float *T,
+                                   long long ncoarse, cudaStream_t s);
+
 // Diagnostics and set-up (aux_kernels.cu)
 // Budgets: partial sums per block into partials[nblocks][7] (6 integrals and a
 // non-finite count), then a single-block pass in fixed order into out[7].

@@ -113,7 +113,7 @@ struct TrainSmem {
 };
 
 __device__ __forceinline__ float dsilu(float a) {
-  const float sg = 1.0f / (1.0f + expf(-a));
+  const float sg = __fdividef(1.0f, 1.0f + __expf(-a));
   return sg * (1.0f + a * (1.0f - sg));
 }
 

@@ -239,6 +239,15 @@ def test_mlp_gradient_finite_difference(orc):
             assert abs(fd - an) <= 1e-7 * max(1e-3, abs(an)), (key, idx, fd, an)
 
 
+def test_bf16_rounding_definition(orc):
+    # BF16 keeps 8 significand bits: spacing 2^-7 at 1.0.  Round to nearest,
+    # ties to even.
+    assert orc.bf16(1.0 + 2.0 ** -8) == 1.0
+    assert orc.bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    assert orc.bf16(1.0 + 2.0 ** -8 + 2.0 ** -20) == 1.0 + 2.0 ** -7
+    assert orc.bf16(-3.0) == -3.0 and orc.bf16(0.0) == 0.0
+
+
 def test_adam_first_step(orc):
     theta = np.array([1.0, -2.0, 3.0])
     g = np.array([0.5, -4.0, 1e-3])
