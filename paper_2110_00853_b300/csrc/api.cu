@@ -126,6 +126,11 @@ struct cmles_t {
   std::vector<float> mlp;
   MlpPacked *mlp_dev = nullptr;
   bool have_mlp = false;
+  // curvilinear (warped) meshes: device tables and host geometry (FP64)
+  bool curved = false;
+  float *geo32 = nullptr, *node32 = nullptr;
+  double *wJn = nullptr;
+  std::vector<double> hx_, hz_, hJ_, hJa_, hdelta_;
 };
 
 namespace {
@@ -283,11 +288,17 @@ cmles_status run_stage_pair32(cmles_handle h, const float *Sin, float *Sout, dou
                               bool update) {
   {
     LaunchScope ls(h, 0, 1);
-    CK(launch_grad32(Sin, h->F2_32, h->aux32, h->K, h->stream));
+    if (h->curved)
+      CK(launch_grad32c(Sin, h->F2_32, h->aux32, h->K, h->stream));
+    else
+      CK(launch_grad32(Sin, h->F2_32, h->aux32, h->K, h->stream));
   }
   {
     LaunchScope ls(h, 1, 1);
-    CK(launch_rhs32(Sin, h->F2_32, h->aux32, h->dQ32, h->Q[0], Sout, Rout, sc, update, h->K, h->stream));
+    if (h->curved)
+      CK(launch_rhs32c(Sin, h->F2_32, h->aux32, h->dQ32, h->Q[0], Sout, Rout, sc, update, h->K, h->stream));
+    else
+      CK(launch_rhs32(Sin, h->F2_32, h->aux32, h->dQ32, h->Q[0], Sout, Rout, sc, update, h->K, h->stream));
   }
   return CMLES_OK;
 }
@@ -295,7 +306,10 @@ cmles_status run_stage_pair32(cmles_handle h, const float *Sin, float *Sout, dou
 cmles_status ensure_shadow(cmles_handle h) {
   if (h->fp32 && !h->shadow_valid) {
     LaunchScope ls(h, 2, 1);
-    CK(launch_shadow32(h->Q[0], h->S32[h->scur], h->K, h->N, h->stream));
+    if (h->curved)
+      CK(launch_shadow32c(h->Q[0], h->S32[h->scur], h->K, h->N, h->stream));
+    else
+      CK(launch_shadow32(h->Q[0], h->S32[h->scur], h->K, h->N, h->stream));
     h->shadow_valid = true;
   }
   return CMLES_OK;
@@ -311,6 +325,189 @@ cmles_status run_stage_pair(cmles_handle h, const double *Qin, double *Qout, dou
     LaunchScope ls(h, 1, 1);
     CK(launch_rhs64(Qin, h->F2, h->aux, dQ, Qout, sc, update, h->K, h->stream));
   }
+  return CMLES_OK;
+}
+
+// ---- curvilinear (warped) meshes ----
+
+// Terrain height of the warped mesh: z_s(x) = h exp(-((x - x_c)/a)^2).
+double terrain(const cmles_mesh &m, double x) {
+  const double s = (x - m.hill_xc) / m.hill_a;
+  return m.hill_h * exp(-s * s);
+}
+
+// Node coordinates (z' = z + z_s(x)(1 - (z - z0)/Lz)), Jacobian, metric terms
+// in the conservative curl form (J a^r)_c = -[curl_xi(X_l grad_xi X_m)]_r with
+// (c, m, l) cyclic, and the per-element filter width; uploads the FP32
+// metrics [E][10][128] and the quadrature weights w_n J_n.
+cmles_status build_curved(cmles_handle h) {
+  const cmles_mesh &m = h->mesh;
+  const int Nq = h->Nq, Np = h->Np;
+  const long long E = h->E;
+  const double hx = m.Lx / m.nex, hy = m.Ly / m.ney, hz = m.Lz / m.nez;
+  h->hx_.resize((size_t)E * Np);
+  h->hz_.resize((size_t)E * Np);
+  h->hJ_.resize((size_t)E * Np);
+  h->hJa_.resize((size_t)E * Np * 9);
+  h->hdelta_.resize(E);
+  std::vector<float> geo((size_t)E * 10 * 128, 0.0f);
+  std::vector<double> wJ((size_t)E * Np);
+  std::vector<double> X(3 * Np), dX(9 * Np), V(3 * Np);
+  auto at = [&](int i, int j, int k) { return i + Nq * (j + Nq * k); };
+  // derivative along reference direction r of nodal field f at node n
+  auto dref = [&](const double *f, int n, int r) {
+    int ijk[3] = {n % Nq, (n / Nq) % Nq, n / (Nq * Nq)};
+    double acc = 0.0;
+    for (int q = 0; q < Nq; ++q) {
+      int t[3] = {ijk[0], ijk[1], ijk[2]};
+      t[r] = q;
+      acc += h->D[ijk[r] * Nq + q] * f[at(t[0], t[1], t[2])];
+    }
+    return acc;
+  };
+  for (long long e = 0; e < E; ++e) {
+    const int ex = (int)(e % m.nex), ey = (int)((e / m.nex) % m.ney), ez = (int)(e / ((long long)m.nex * m.ney));
+    for (int n = 0; n < Np; ++n) {
+      const int i = n % Nq, j = (n / Nq) % Nq, k = n / (Nq * Nq);
+      const double x = m.x0 + (ex + 0.5 * (h->xi[i] + 1.0)) * hx;
+      const double y = m.y0 + (ey + 0.5 * (h->xi[j] + 1.0)) * hy;
+      double z = m.z0 + (ez + 0.5 * (h->xi[k] + 1.0)) * hz;
+      if (m.warp) z = z + terrain(m, x) * (1.0 - (z - m.z0) / m.Lz);
+      X[n] = x;
+      X[Np + n] = y;
+      X[2 * Np + n] = z;
+      h->hx_[e * Np + n] = x;
+      h->hz_[e * Np + n] = z;
+    }
+    for (int c = 0; c < 3; ++c)
+      for (int r = 0; r < 3; ++r)
+        for (int n = 0; n < Np; ++n) dX[(c * 3 + r) * Np + n] = dref(&X[c * Np], n, r);
+    double vol = 0.0;
+    for (int n = 0; n < Np; ++n) {
+      const double *a = &dX[n];
+      auto d = [&](int c, int r) { return a[(c * 3 + r) * Np]; };
+      const double J = d(0, 0) * (d(1, 1) * d(2, 2) - d(1, 2) * d(2, 1)) -
+                       d(0, 1) * (d(1, 0) * d(2, 2) - d(1, 2) * d(2, 0)) +
+                       d(0, 2) * (d(1, 0) * d(2, 1) - d(1, 1) * d(2, 0));
+      h->hJ_[e * Np + n] = J;
+      const int i = n % Nq, j = (n / Nq) % Nq, k = n / (Nq * Nq);
+      wJ[e * Np + n] = h->w[i] * h->w[j] * h->w[k] * J;
+      vol += wJ[e * Np + n];
+    }
+    h->hdelta_[e] = cbrt(vol) / h->N;
+    for (int c = 0; c < 3; ++c) {
+      const int mm = (c + 1) % 3, ll = (c + 2) % 3;
+      for (int r = 0; r < 3; ++r)
+        for (int n = 0; n < Np; ++n) V[r * Np + n] = X[ll * Np + n] * dX[(mm * 3 + r) * Np + n];
+      for (int n = 0; n < Np; ++n) {
+        const double c0 = dref(&V[2 * Np], n, 1) - dref(&V[1 * Np], n, 2);
+        const double c1 = dref(&V[0 * Np], n, 2) - dref(&V[2 * Np], n, 0);
+        const double c2 = dref(&V[1 * Np], n, 0) - dref(&V[0 * Np], n, 1);
+        double *ja = &h->hJa_[(e * Np + n) * 9];
+        ja[0 * 3 + c] = -c0;
+        ja[1 * 3 + c] = -c1;
+        ja[2 * 3 + c] = -c2;
+      }
+    }
+    for (int n = 0; n < Np; ++n) {
+      for (int q = 0; q < 9; ++q) geo[((size_t)e * 10 + q) * 128 + n] = (float)h->hJa_[(e * Np + n) * 9 + q];
+      geo[((size_t)e * 10 + 9) * 128 + n] = (float)h->hJ_[e * Np + n];
+    }
+  }
+  CK(cudaMemcpy(h->geo32, geo.data(), geo.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->wJn, wJ.data(), wJ.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return CMLES_OK;
+}
+
+// Per-node FP32 tables and FP64 offsets of a curvilinear mesh from the
+// per-node reference (rho_r, p_r, q_r): the level-table fields of the flat
+// path per node, the full reference gradients of h_r, q_r, theta_v,r (the
+// DG gradient operator applied to the nodal reference values), Delta,
+// (C_s Delta)^2 and the sponge coefficient.
+cmles_status curved_reference(cmles_handle h, const double *rho_r, const double *p_r, const double *qt_r) {
+  const cmles_params &p = h->prm;
+  const cmles_mesh &m = h->mesh;
+  const KParams &K = h->K;
+  const int Nq = h->Nq, Np = h->Np, NF = kCurvedNF;
+  const long long E = h->E;
+  std::vector<float> tab((size_t)E * NF * 128, 0.0f);
+  std::vector<double> qref((size_t)E * 3 * Np);
+  std::vector<double> hr(Np), thr(Np), qr(Np);
+  const double ztop = m.z0 + m.Lz;
+  for (long long e = 0; e < E; ++e) {
+    for (int n = 0; n < Np; ++n) {
+      const size_t g = (size_t)e * Np + n;
+      const double q = qt_r ? qt_r[g] : 0.0, z = h->hz_[g], x = h->hx_[g];
+      const double Rm = p.Rd * (1.0 - q) + p.Rv * q;
+      const double Tr = p_r[g] / (rho_r[g] * Rm);
+      const double I = (1.0 - q) * p.cvd * (Tr - p.T0) + q * (p.cvv * (Tr - p.T0) + K.Iv0);
+      const double rhoe = rho_r[g] * (I + p.g * z);
+      qref[((size_t)e * 3 + 0) * Np + n] = rho_r[g];
+      qref[((size_t)e * 3 + 1) * Np + n] = rhoe;
+      qref[((size_t)e * 3 + 2) * Np + n] = rho_r[g] * q;
+      hr[n] = (rhoe + p_r[g]) / rho_r[g];
+      thr[n] = Tr * pow(p.p0 / p_r[g], K.kappa) * Rm / p.Rd;
+      qr[n] = q;
+      double tau = 0.0;
+      if (p.sponge_alpha > 0.0) {
+        if (z > p.sponge_zs) tau = p.sponge_alpha * pow(sin(0.5 * M_PI * (z - p.sponge_zs) / (ztop - p.sponge_zs)),
+                                                        p.sponge_gamma);
+        if (p.lateral_sponge_frac > 0.0) {
+          const double width = p.lateral_sponge_frac * m.Lx, xl = m.x0 + width, xr = m.x0 + m.Lx - width;
+          double tl = 0.0;
+          if (x < xl) tl = p.sponge_alpha * pow(sin(0.5 * M_PI * (xl - x) / width), p.sponge_gamma);
+          if (x > xr) tl = p.sponge_alpha * pow(sin(0.5 * M_PI * (x - xr) / width), p.sponge_gamma);
+          tau = fmax(tau, tl);
+        }
+      }
+      float *T = &tab[(size_t)e * NF * 128 + n];
+      T[L_RHO * 128] = (float)rho_r[g];
+      T[L_RHOQ * 128] = (float)(rho_r[g] * q);
+      T[L_T * 128] = (float)Tr;
+      T[L_T_T0 * 128] = (float)(Tr - p.T0);
+      T[L_GZ * 128] = (float)(p.g * z);
+      T[L_P * 128] = (float)p_r[g];
+      T[L_H * 128] = (float)(rhoe + p_r[g]);
+      T[L_HM * 128] = (float)hr[n];
+      T[L_THV * 128] = (float)thr[n];
+      T[L_RHORM * 128] = (float)(rho_r[g] * Rm);
+      T[L_TAU * 128] = (float)tau;
+      T[L_QM * 128] = (float)q;
+      const double delta = h->hdelta_[e];
+      T[(NF - 2) * 128] = (float)delta;
+      T[(NF - 1) * 128] = (float)((p.Cs * delta) * (p.Cs * delta));
+    }
+    // reference gradients: (1/J) sum_r (J a^r)_c d/dxi_r
+    const double *fields[3] = {hr.data(), qr.data(), thr.data()};
+    const int zslot[3] = {L_DZ_HM, L_DZ_Q, L_DZ_THV}, xslot[3] = {L_NF, L_NF + 2, L_NF + 4};
+    for (int n = 0; n < Np; ++n) {
+      const int ijk[3] = {n % Nq, (n / Nq) % Nq, n / (Nq * Nq)};
+      const double *ja = &h->hJa_[((size_t)e * Np + n) * 9];
+      const double Jn = h->hJ_[(size_t)e * Np + n];
+      for (int fi = 0; fi < 3; ++fi) {
+        double dr[3];
+        for (int r = 0; r < 3; ++r) {
+          double acc = 0.0;
+          for (int q = 0; q < Nq; ++q) {
+            int t[3] = {ijk[0], ijk[1], ijk[2]};
+            t[r] = q;
+            acc += h->D[ijk[r] * Nq + q] * fields[fi][t[0] + Nq * (t[1] + Nq * t[2])];
+          }
+          dr[r] = acc;
+        }
+        double gc[3];
+        for (int c = 0; c < 3; ++c) gc[c] = (ja[0 + c] * dr[0] + ja[3 + c] * dr[1] + ja[6 + c] * dr[2]) / Jn;
+        float *T = &tab[(size_t)e * NF * 128 + n];
+        T[xslot[fi] * 128] = (float)gc[0];
+        T[(xslot[fi] + 1) * 128] = (float)gc[1];
+        T[zslot[fi] * 128] = (float)gc[2];
+      }
+    }
+  }
+  CK(cudaMemcpy(h->node32, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->qref64, qref.data(), qref.size() * sizeof(double), cudaMemcpyHostToDevice));
+  h->have_ref = true;
+  h->shadow_valid = false;
   return CMLES_OK;
 }
 
@@ -352,7 +549,8 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   if (mesh->N != 4) return CMLES_ERR_ARG;
   if (mesh->nex < 1 || mesh->ney < 1 || mesh->nez < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0))
     return CMLES_ERR_MESH;
-  if (mesh->warp) return CMLES_ERR_ARG;
+  // warped (curvilinear) meshes run on the FP32 path
+  if (mesh->warp && params->precision != CMLES_FP32_ACC64) return CMLES_ERR_ARG;
   if (params->precision != CMLES_FP64 && params->precision != CMLES_FP32_ACC64) return CMLES_ERR_ARG;
   // the FP32 shadow is relative to a per-level reference: z must not wrap
   if (params->precision == CMLES_FP32_ACC64 && mesh->periodic[2]) return CMLES_ERR_ARG;
@@ -400,9 +598,17 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
     ALLOC(h->F2_32, n32 * 15 * sizeof(float));
     ALLOC(h->aux32, n32 * 2 * sizeof(float));
   }
+  h->curved = mesh->warp != 0;
   ALLOC(h->lev32, (size_t)nlev * L_NF * sizeof(float));
   ALLOC(h->dH32, (size_t)mesh->nez * h->Nq * h->Nq * sizeof(float));
-  ALLOC(h->qref64, (size_t)nlev * 4 * sizeof(double));
+  if (h->curved) {
+    ALLOC(h->qref64, (size_t)E * 3 * h->Np * sizeof(double));
+    ALLOC(h->geo32, (size_t)E * 10 * 128 * sizeof(float));
+    ALLOC(h->node32, (size_t)E * kCurvedNF * 128 * sizeof(float));
+    ALLOC(h->wJn, (size_t)E * h->Np * sizeof(double));
+  } else {
+    ALLOC(h->qref64, (size_t)nlev * 4 * sizeof(double));
+  }
   ALLOC(h->mlp_dev, sizeof(MlpPacked));
   ALLOC(h->rho_r, nlev * sizeof(double));
   ALLOC(h->p_r, nlev * sizeof(double));
@@ -458,6 +664,15 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
     return CMLES_ERR_CUDA;
   }
   if (!lateral) h->K.tau_col = nullptr;
+  if (h->curved) {
+    h->K.curved = 1;
+    h->K.geo32 = h->geo32;
+    h->K.node32 = h->node32;
+    if (build_curved(h) != CMLES_OK) {
+      cmles_destroy(h);
+      return CMLES_ERR_CUDA;
+    }
+  }
   *out = h;
   return CMLES_OK;
 }
@@ -471,7 +686,7 @@ cmles_status cmles_destroy(cmles_handle h) {
   void *bufs[] = {h->Q[0],   h->Q[1],    h->dQ,      h->F2,       h->aux,     h->rho_r,    h->p_r,
                   h->qt_r,   h->tau_lev, h->tau_col, h->wq,       h->flags,   h->partials, h->budget_out,
                   h->prof,   h->S32[0],  h->S32[1],  h->dQ32,     h->F2_32,   h->aux32,    h->lev32,
-                  h->dH32,   h->qref64,  h->mlp_dev};
+                  h->dH32,   h->qref64,  h->mlp_dev, h->geo32,   h->node32,  h->wJn};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete h;
@@ -489,6 +704,10 @@ cmles_status cmles_set_stream(cmles_handle h, void *stream) {
 cmles_status cmles_set_reference(cmles_handle h, const double *rho_r, const double *p_r, const double *qt_r,
                                  size_t n) {
   if (!h || !rho_r || !p_r) return fail(h, CMLES_ERR_ARG, "cmles_set_reference: null array");
+  if (h->curved) {
+    if (n != (size_t)h->nodes) return fail(h, CMLES_ERR_ARG, "cmles_set_reference: expected one value per node");
+    return curved_reference(h, rho_r, p_r, qt_r);
+  }
   const size_t nlev = (size_t)h->mesh.nez * h->Nq;
   if (n != nlev) return fail(h, CMLES_ERR_ARG, "cmles_set_reference: expected one value per node level");
   // levels (ez, N) and (ez+1, 0) are the same height: the physical profile
@@ -573,6 +792,43 @@ cmles_status cmles_set_reference(cmles_handle h, const double *rho_r, const doub
 
 cmles_status cmles_init_case(cmles_handle h, const cmles_case *c) {
   if (!h || !c) return fail(h, CMLES_ERR_ARG, "cmles_init_case: null argument");
+  if (h->curved) {
+    // flow over the terrain (case 3): dry, constant Brunt-Vaisala frequency
+    // (Eqs. pressure_hs_brunt and the ideal gas law), uniform velocity u0
+    if (c->id != 3) return fail(h, CMLES_ERR_ARG, "cmles_init_case: warped meshes support case 3 only");
+    const cmles_params &p = h->prm;
+    const double cpd = p.cvd + p.Rd, kappa = p.Rd / cpd, N2 = c->NBV * c->NBV;
+    const size_t nn = (size_t)h->nodes;
+    std::vector<double> Q(nn * 6), rr(nn), pr(nn);
+    for (long long e = 0; e < h->E; ++e)
+      for (int n = 0; n < h->Np; ++n) {
+        const size_t g = (size_t)e * h->Np + n;
+        const double z = h->hz_[g];
+        const double th = c->theta0 * exp(N2 * z / p.g);
+        const double pi = 1.0 + p.g * p.g / (cpd * c->theta0 * N2) * (exp(-z * N2 / p.g) - 1.0);
+        const double pp = p.p0 * pow(pi, cpd / p.Rd);
+        const double T = th * pow(pp / p.p0, kappa);
+        const double rho = pp / (p.Rd * T);
+        const double ke = 0.5 * (c->u0[0] * c->u0[0] + c->u0[1] * c->u0[1] + c->u0[2] * c->u0[2]);
+        double *q = &Q[(size_t)e * 6 * h->Np + n];
+        q[0] = rho;
+        q[h->Np] = rho * c->u0[0];
+        q[2 * h->Np] = rho * c->u0[1];
+        q[3 * h->Np] = rho * c->u0[2];
+        q[4 * h->Np] = rho * (p.cvd * (T - p.T0) + ke + p.g * z);
+        q[5 * h->Np] = 0.0;
+        rr[g] = rho;
+        pr[g] = pp;
+      }
+    cmles_status st = curved_reference(h, rr.data(), pr.data(), nullptr);
+    if (st != CMLES_OK) return st;
+    CK(cudaMemcpy(h->Q[0], Q.data(), Q.size() * sizeof(double), cudaMemcpyHostToDevice));
+    h->cur = 0;
+    h->shadow_valid = false;
+    h->time = 0.0;
+    h->steps = 0;
+    return CMLES_OK;
+  }
   if (c->id != 1 && c->id != 2 && c->id != 5)
     return fail(h, CMLES_ERR_ARG, "cmles_init_case: case id not available on flat meshes");
   const cmles_params &p = h->prm;
@@ -729,7 +985,10 @@ cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev
     float *tmp = h->S32[1 - h->scur];
     {
       LaunchScope ls(h, 2, 1);
-      CK(launch_shadow32(Q_dev, tmp, h->K, h->N, h->stream));
+      if (h->curved)
+        CK(launch_shadow32c(Q_dev, tmp, h->K, h->N, h->stream));
+      else
+        CK(launch_shadow32(Q_dev, tmp, h->K, h->N, h->stream));
     }
     return run_stage_pair32(h, tmp, nullptr, RHS_dev, sc, false);
   }
@@ -770,7 +1029,7 @@ cmles_status cmles_diagnostics(cmles_handle h, cmles_diag *out) {
   {
     LaunchScope ls(h, 2, 2);
     CK(launch_budgets(h->Q[h->cur], h->E, h->Np, h->wq, J, h->partials, h->budget_nblocks, h->budget_out,
-                      h->stream));
+                      h->stream, h->curved ? h->wJn : nullptr));
   }
   double res[7];
   int flags[16];
@@ -790,6 +1049,7 @@ cmles_status cmles_diagnostics(cmles_handle h, cmles_diag *out) {
 
 cmles_status cmles_profiles(cmles_handle h, double *out_host) {
   if (!h || !out_host) return fail(h, CMLES_ERR_ARG, "cmles_profiles: null argument");
+  if (h->curved) return fail(h, CMLES_ERR_ARG, "cmles_profiles: flat meshes only");
   const int nlev = h->mesh.nez * h->Nq;
   CK(cudaMemsetAsync(h->prof, 0, (size_t)nlev * 12 * sizeof(double), h->stream));
   {
@@ -844,6 +1104,7 @@ cmles_status cmles_set_closure_weights_device(cmles_handle h, const float *param
 cmles_status cmles_closure_samples(cmles_handle h, int factor, float *X_dev, float *T_dev, long long capacity,
                                    long long *n_out) {
   if (!h || !X_dev || !T_dev || factor < 1) return fail(h, CMLES_ERR_ARG, "cmles_closure_samples: bad argument");
+  if (h->curved) return fail(h, CMLES_ERR_ARG, "cmles_closure_samples: flat meshes only");
   const cmles_mesh &m = h->mesh;
   if (m.nex % factor || m.ney % factor || m.nez % factor)
     return fail(h, CMLES_ERR_ARG, "cmles_closure_samples: element counts must be multiples of factor");

@@ -27,14 +27,15 @@ int budget_blocks(long long nodes) {
 // non-finite entries.  Fixed grid and fixed reduction order: deterministic.
 __global__ void __launch_bounds__(kBudgetThreads) k_budget_partial(const double *__restrict__ Q, long long E,
                                                                    int Np, const double *__restrict__ wq,
-                                                                   double J, double *__restrict__ partials) {
+                                                                   double J, double *__restrict__ partials,
+                                                                   const double *__restrict__ wJn) {
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   const long long nodes = E * Np;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nodes;
        g += (long long)gridDim.x * blockDim.x) {
     const long long e = g / Np;
     const int n = (int)(g - e * Np);
-    const double w = wq[n] * J;
+    const double w = wJn ? wJn[g] : wq[n] * J;
 #pragma unroll
     for (int v = 0; v < 6; ++v) {
       const double q = Q[(e * 6 + v) * Np + n];
@@ -67,8 +68,8 @@ __global__ void k_budget_final(const double *__restrict__ partials, int nblocks,
 }
 
 cudaError_t launch_budgets(const double *Q, long long E, int Np, const double *wq, double J, double *partials,
-                           int nblocks, double *out, cudaStream_t s) {
-  k_budget_partial<<<nblocks, kBudgetThreads, 0, s>>>(Q, E, Np, wq, J, partials);
+                           int nblocks, double *out, cudaStream_t s, const double *wJn) {
+  k_budget_partial<<<nblocks, kBudgetThreads, 0, s>>>(Q, E, Np, wq, J, partials, wJn);
   k_budget_final<<<1, 32, 0, s>>>(partials, nblocks, out);
   return cudaGetLastError();
 }

@@ -64,6 +64,10 @@ struct KParams {
   const float *lev32, *dH32;
   const double *qref64;
   const struct MlpPacked *mlp;  // learned-closure weights (closure == 2)
+  // curvilinear meshes (dg_curved32.cu): per-node metrics [E][10][128]
+  // ((J grad xi_r)_c at 3r + c, J at 9) and per-node tables [E][24][128]
+  int curved;
+  const float *geo32, *node32;
   // LGL basis
   double D[kMaxQ * kMaxQ], w[kMaxQ], xi[kMaxQ];
   KF f;

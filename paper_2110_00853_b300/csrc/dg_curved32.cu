@@ -1,0 +1,478 @@
+// FP32 DG kernels (FP64 accumulation) on curvilinear hexahedra: the
+// terrain-following warped mesh of Sec. 4.3 (elements stacked over the
+// terrain, linear damping to a flat top).
+//
+// Same two passes as dg_fp32.cu with the metric terms of Eq. mapping stored
+// per node: (J grad xi_r)_c for r, c = 1..3 and J, in the conservative curl
+// form (Kopriva 2006), so that free-stream flows are preserved.
+//   gradient   grad G = (1/J) sum_r (J a^r) dG/dxi_r  + lift on faces
+//   divergence div F  = (1/J) sum_r d/dxi_r (J a^r . F)  (contravariant flux)
+//   faces      n = +-J a^d / |J a^d|, lift factor |J a^d| / (w_0 J)
+// Reference values vary from node to node (z depends on x over the terrain),
+// so the deviation-form tables are per node, and the reference parts of the
+// h_tot, q_t and theta_v gradients are full 3-vectors.  The energy flux is
+// formed as (H_r + H') u in FP32.
+#include "common.cuh"
+#include "launch.h"
+#include "mlp.cuh"
+#include "thermo32.cuh"
+
+namespace cmles {
+
+// per-node table fields beyond the level-table layout: x and y components of
+// the reference gradients of h_r, q_r and theta_v,r
+// and the per-element filter width Delta and (C_s Delta)^2
+enum { C_DX_HM = L_NF, C_DY_HM, C_DX_Q, C_DY_Q, C_DX_THV, C_DY_THV, C_DELTA, C_CSD2, C_NF = 24 };
+
+__device__ __forceinline__ void load_node_table(const float *__restrict__ tab, size_t e, int n, float L[L_NF]) {
+  const float *p = tab + e * C_NF * kNP + n;
+#pragma unroll
+  for (int f = 0; f < L_NF; ++f) L[f] = p[f * kNP];
+}
+
+template <int N, bool MOIST, int CL>
+__global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *__restrict__ S, float *__restrict__ F2,
+                                                                  float *__restrict__ aux, const KParams P) {
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
+  __shared__ float sD[Nq * Nq];
+  __shared__ float sG[6][kNP];
+  __shared__ float sGf[6][6][Nf];
+  __shared__ int sNb[6];
+  __shared__ __align__(16) uint8_t sMlpRaw[CL == 2 ? sizeof(MlpPacked) : 16];
+  __shared__ __align__(16) __nv_bfloat16 sX[CL == 2 ? kNP * kMlpInPad : 8];
+  __shared__ float sY[CL == 2 ? kNP * 2 : 2];
+  const KF &F = P.f;
+  const int t = threadIdx.x;
+  if (t < Nq * Nq) sD[t] = (float)P.D[t];
+  const MlpPacked &W = *reinterpret_cast<const MlpPacked *>(sMlpRaw);
+  if (CL == 2) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(P.mlp);
+    uint4 *dst = reinterpret_cast<uint4 *>(sMlpRaw);
+    for (int q = t; q < (int)(sizeof(MlpPacked) / 16); q += blockDim.x) dst[q] = src[q];
+  }
+  const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
+  int fail = 0;
+  for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
+    int ex, ey, ez;
+    const int e = element_at(P, g, ex, ey, ez);
+    if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
+    float sv[6], G[6], L[L_NF];
+    if (t < Np) {
+      load_node_table(P.node32, e, t, L);
+#pragma unroll
+      for (int v = 0; v < 6; ++v) sv[v] = S[((size_t)e * 6 + v) * kNP + t];
+      Th32 o;
+      thermo32<MOIST>(P, L, sv, o, fail);
+      G[0] = o.u[0];
+      G[1] = o.u[1];
+      G[2] = o.u[2];
+      G[3] = o.hp;
+      G[4] = o.qp;
+      G[5] = o.thvp;
+      aux[((size_t)e * 2 + 0) * kNP + t] = o.pp;
+      aux[((size_t)e * 2 + 1) * kNP + t] = o.c;
+#pragma unroll
+      for (int v = 0; v < 6; ++v) sG[v][t] = G[v];
+    }
+    __syncthreads();
+    for (int task = t; task < 6 * Nf; task += blockDim.x) {
+      const int f = task / Nf, fn = task - f * Nf;
+      const int nb = sNb[f];
+      if (nb < 0) continue;
+      const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
+      const int nn = face_node<Nq>(d, (f & 1) ? 0 : N, t1, t2);
+      float sp[6], Ln[L_NF];
+      load_node_table(P.node32, nb, nn, Ln);
+#pragma unroll
+      for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
+      Th32 o;
+      thermo32<MOIST>(P, Ln, sp, o, fail);
+      sGf[f][0][fn] = o.u[0];
+      sGf[f][1][fn] = o.u[1];
+      sGf[f][2][fn] = o.u[2];
+      sGf[f][3][fn] = o.hp;
+      sGf[f][4][fn] = o.qp;
+      sGf[f][5][fn] = o.thvp;
+    }
+    __syncthreads();
+    float gr[6][3];
+    float nut = 0.f, Dt = 0.f;
+    if (t < Np) {
+      const float *geo = P.geo32 + (size_t)e * 10 * kNP + t;
+      float Ja[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Ja[q] = geo[q * kNP];
+      const float Jinv = 1.0f / geo[9 * kNP];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          a0 += sD[i * Nq + m] * sG[v][m + Nq * (j + Nq * k)];
+          a1 += sD[j * Nq + m] * sG[v][i + Nq * (m + Nq * k)];
+          a2 += sD[k * Nq + m] * sG[v][i + Nq * (j + Nq * m)];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gr[v][c] = Jinv * (Ja[0 + c] * a0 + Ja[3 + c] * a1 + Ja[6 + c] * a2);
+      }
+      const float *tab = P.node32 + (size_t)e * C_NF * kNP + t;
+      gr[3][0] += tab[C_DX_HM * kNP];
+      gr[3][1] += tab[C_DY_HM * kNP];
+      gr[3][2] += L[L_DZ_HM];
+      gr[4][0] += tab[C_DX_Q * kNP];
+      gr[4][1] += tab[C_DY_Q * kNP];
+      gr[4][2] += L[L_DZ_Q];
+      gr[5][0] += tab[C_DX_THV * kNP];
+      gr[5][1] += tab[C_DY_THV * kNP];
+      gr[5][2] += L[L_DZ_THV];
+      auto lift = [&](int f, int fn) {
+        const int d = f >> 1;
+        const float sg = (f & 1) ? 1.f : -1.f;
+        const float ax = Ja[3 * d], ay = Ja[3 * d + 1], az = Ja[3 * d + 2];
+        const float mag = sqrtf(ax * ax + ay * ay + az * az);
+        const float nv[3] = {sg * ax / mag, sg * ay / mag, sg * az / mag};
+        const float Lf = mag * Jinv / (float)P.w[0];
+        if (sNb[f] >= 0) {
+#pragma unroll
+          for (int v = 0; v < 6; ++v) {
+            const float jump = 0.5f * (G[v] + sGf[f][v][fn]) - G[v];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gr[v][c] += Lf * nv[c] * jump;
+          }
+        } else {
+          const float un = G[0] * nv[0] + G[1] * nv[1] + G[2] * nv[2];
+#pragma unroll
+          for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gr[v][c] += Lf * nv[c] * (-un * nv[v]);
+        }
+      };
+      if (i == 0) lift(0, j + Nq * k);
+      if (i == N) lift(1, j + Nq * k);
+      if (j == 0) lift(2, i + Nq * k);
+      if (j == N) lift(3, i + Nq * k);
+      if (k == 0) lift(4, i + Nq * j);
+      if (k == N) lift(5, i + Nq * j);
+      if (CL == 1 && P.closure == 1) {
+        float S2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const float Sab = 0.5f * (gr[a][b] + gr[b][a]);
+            S2 += Sab * Sab;
+          }
+        const float Smag2 = 2.0f * S2;
+        if (Smag2 > 0.0f) {
+          const float Smag = sqrtf(Smag2);
+          float fb = 1.0f;
+          if (P.richardson) {
+            const float Ri = F.g / (L[L_THV] + G[5]) * gr[5][2] / Smag2;
+            if (Ri > 0.0f) {
+              const float a = 1.0f - Ri * F.inv_Prt;
+              fb = a > 0.0f ? sqrtf(sqrtf(a)) : 0.0f;
+            }
+          }
+          // (C_s Delta)^2 with Delta = (element volume)^(1/3) / N, per node
+          nut = tab[C_CSD2 * kNP] * Smag * fb;
+          Dt = nut * F.inv_Prt;
+        }
+      }
+    }
+    if (CL == 2) {
+      uint32_t *xr = reinterpret_cast<uint32_t *>(sX + t * kMlpInPad);
+      if (t < Np) {
+        const float Delta = P.node32[(size_t)e * C_NF * kNP + C_DELTA * kNP + t];
+        float x[kMlpInPad];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) x[3 * a + b] = gr[a][b] * W.in_scale[3 * a + b];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) x[9 + b] = gr[5][b] * W.in_scale[9 + b];
+        x[12] = Delta * W.in_scale[12];
+        x[13] = x[14] = x[15] = 0.f;
+#pragma unroll
+        for (int q = 0; q < kMlpInPad / 2; ++q) xr[q] = pack_bf16(x[2 * q], x[2 * q + 1]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < kMlpInPad / 2; ++q) xr[q] = 0u;
+      }
+      __syncwarp();
+      mlp_warp_forward(W, sX, sY, 32 * (t >> 5));
+      __syncwarp();
+      if (t < Np) {
+        nut = W.out_scale[0] * fmaxf(sY[2 * t], 0.f);
+        Dt = W.out_scale[1] * fmaxf(sY[2 * t + 1], 0.f);
+      }
+    }
+    if (t < Np) {
+      const float rho = L[L_RHO] + sv[0];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float di = -Dt * gr[4][d];
+        float rt[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) rt[b] = -2.0f * rho * nut * (0.5f * (gr[d][b] + gr[b][d]));
+        float *o = F2 + ((size_t)e * 15 + d * 5) * kNP + t;
+        o[0] = rho * di;
+        o[1 * kNP] = rt[0] + di * sv[1];
+        o[2 * kNP] = rt[1] + di * sv[2];
+        o[3 * kNP] = rt[2] + di * sv[3];
+        o[4 * kNP] = -rho * Dt * gr[3][d] + (rt[0] * G[0] + rt[1] * G[1] + rt[2] * G[2]);
+      }
+    }
+    __syncthreads();
+  }
+  if (fail) atomicAdd(P.flags, 1);
+}
+
+// n.F1 for a general unit normal: [rho u.n, rho u_j (u.n) + p' n_j,
+// (H_r + rho e' + p') (u.n), rho q_t (u.n)].
+__device__ __forceinline__ void flux1_normal32(const float s[6], float rho_r, float rhoq_r, float Hr, float pp,
+                                               const float n[3], float f[6]) {
+  const float mn = s[1] * n[0] + s[2] * n[1] + s[3] * n[2];
+  const float un = mn / (rho_r + s[0]);
+  f[0] = mn;
+  f[1] = s[1] * un + pp * n[0];
+  f[2] = s[2] * un + pp * n[1];
+  f[3] = s[3] * un + pp * n[2];
+  f[4] = (Hr + (s[4] + pp)) * un;
+  f[5] = (rhoq_r + s[5]) * un;
+}
+
+template <int N, bool UPDATE>
+__global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, const float *__restrict__ F2,
+                                                   const float *__restrict__ aux, float *__restrict__ dQ,
+                                                   double *__restrict__ Q64, float *__restrict__ Sout,
+                                                   double *__restrict__ Rout, const StageCoef sc, const KParams P) {
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
+  __shared__ float sD[Nq * Nq];
+  __shared__ float sF[6][3][kNP];  // contravariant fluxes J a^r . F
+  __shared__ float sS[6][kNP];
+  __shared__ float sLf[6][6][Nf];
+  __shared__ int sNb[6];
+  const KF &F = P.f;
+  const int t = threadIdx.x;
+  if (t < Nq * Nq) sD[t] = (float)P.D[t];
+  const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
+  for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
+    int ex, ey, ez;
+    const int e = element_at(P, g, ex, ey, ez);
+    if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
+    float sv[6];
+    const float *tab = P.node32 + (size_t)e * C_NF * kNP + (t < Np ? t : 0);
+    const float *geo = P.geo32 + (size_t)e * 10 * kNP + (t < Np ? t : 0);
+    if (t < Np) {
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        sv[v] = S[((size_t)e * 6 + v) * kNP + t];
+        sS[v][t] = sv[v];
+      }
+      const float pp = aux[((size_t)e * 2) * kNP + t];
+      const float rho = tab[L_RHO * kNP] + sv[0];
+      const float u[3] = {sv[1] / rho, sv[2] / rho, sv[3] / rho};
+      const float H = tab[L_H * kNP] + (sv[4] + pp);
+      const float rq = tab[L_RHOQ * kNP] + sv[5];
+      float Fc[6][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float *g2 = F2 + ((size_t)e * 15 + c * 5) * kNP + t;
+        const float c0 = g2[0];
+        Fc[0][c] = sv[1 + c] + c0;
+        Fc[1][c] = sv[1] * u[c] + (c == 0 ? pp : 0.f) + g2[1 * kNP];
+        Fc[2][c] = sv[2] * u[c] + (c == 1 ? pp : 0.f) + g2[2 * kNP];
+        Fc[3][c] = sv[3] * u[c] + (c == 2 ? pp : 0.f) + g2[3 * kNP];
+        Fc[4][c] = H * u[c] + g2[4 * kNP];
+        Fc[5][c] = rq * u[c] + c0;
+      }
+      float Ja[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Ja[q] = geo[q * kNP];
+#pragma unroll
+      for (int v = 0; v < 6; ++v)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) sF[v][r][t] = Ja[3 * r] * Fc[v][0] + Ja[3 * r + 1] * Fc[v][1] + Ja[3 * r + 2] * Fc[v][2];
+    }
+    __syncthreads();
+    for (int task = t; task < 6 * Nf; task += blockDim.x) {
+      const int f = task / Nf, fn = task - f * Nf;
+      const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
+      const int a = (f & 1) ? N : 0;
+      const float sg = (f & 1) ? 1.f : -1.f;
+      const int n = face_node<Nq>(d, a, t1, t2);
+      const float *tn = P.node32 + (size_t)e * C_NF * kNP + n;
+      const float *gn = P.geo32 + (size_t)e * 10 * kNP + n;
+      const float ax = gn[(3 * d) * kNP], ay = gn[(3 * d + 1) * kNP], az = gn[(3 * d + 2) * kNP];
+      const float mag = sqrtf(ax * ax + ay * ay + az * az);
+      const float nv[3] = {sg * ax / mag, sg * ay / mag, sg * az / mag};
+      const float rho_r = tn[L_RHO * kNP], rhoq_r = tn[L_RHOQ * kNP], Hr = tn[L_H * kNP];
+      float sm[6], sp[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) sm[v] = sS[v][n];
+      const float pm = aux[((size_t)e * 2) * kNP + n];
+      const float cm = aux[((size_t)e * 2 + 1) * kNP + n];
+      const int nb = sNb[f];
+      float pp, cp, f2s[5];
+      if (nb >= 0) {
+        const int nn = face_node<Nq>(d, N - a, t1, t2);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
+        pp = aux[((size_t)nb * 2) * kNP + nn];
+        cp = aux[((size_t)nb * 2 + 1) * kNP + nn];
+#pragma unroll
+        for (int c5 = 0; c5 < 5; ++c5) {
+          float fm = 0.f, fq = 0.f;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            fm += nv[c] * F2[((size_t)e * 15 + c * 5 + c5) * kNP + n];
+            fq += nv[c] * F2[((size_t)nb * 15 + c * 5 + c5) * kNP + nn];
+          }
+          f2s[c5] = 0.5f * (fm + fq);
+        }
+      } else {
+        const float mn = sm[1] * nv[0] + sm[2] * nv[1] + sm[3] * nv[2];
+#pragma unroll
+        for (int v = 0; v < 6; ++v) sp[v] = sm[v];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sp[1 + c] = sm[1 + c] - 2.0f * mn * nv[c];
+        pp = pm;
+        cp = cm;
+#pragma unroll
+        for (int c5 = 0; c5 < 5; ++c5) f2s[c5] = 0.f;
+        if (f == 4 && P.surface_flux) {
+          f2s[0] = -F.E_water * (-nv[2]);
+          f2s[4] = -F.E_energy * (-nv[2]);
+        }
+      }
+      float fm[6], fp[6];
+      flux1_normal32(sm, rho_r, rhoq_r, Hr, pm, nv, fm);
+      flux1_normal32(sp, rho_r, rhoq_r, Hr, pp, nv, fp);
+      const float um = (sm[1] * nv[0] + sm[2] * nv[1] + sm[3] * nv[2]) / (rho_r + sm[0]);
+      const float up = (sp[1] * nv[0] + sp[2] * nv[1] + sp[3] * nv[2]) / (rho_r + sp[0]);
+      const float lam = fmaxf(fabsf(um) + cm, fabsf(up) + cp);
+      const float Lf = mag / (gn[9 * kNP] * (float)P.w[0]);
+      const int c_of_v[6] = {0, 1, 2, 3, 4, 0};
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        const float f1s = 0.5f * (fm[v] + fp[v]) + 0.5f * lam * (sm[v] - sp[v]);
+        const float fnm = sg * sF[v][d][n] / mag;  // n . F at the own node
+        sLf[f][v][fn] = Lf * (fnm - (f1s + f2s[c_of_v[v]]));
+      }
+    }
+    __syncthreads();
+    if (t < Np) {
+      const float Jinv = 1.0f / geo[9 * kNP];
+      float R[6];
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int m = 0; m < Nq; ++m) {
+          a0 += sD[i * Nq + m] * sF[v][0][m + Nq * (j + Nq * k)];
+          a1 += sD[j * Nq + m] * sF[v][1][i + Nq * (m + Nq * k)];
+          a2 += sD[k * Nq + m] * sF[v][2][i + Nq * (j + Nq * m)];
+        }
+        float r = -Jinv * (a0 + a1 + a2);
+        if (i == 0) r += sLf[0][v][j + Nq * k];
+        if (i == N) r += sLf[1][v][j + Nq * k];
+        if (j == 0) r += sLf[2][v][i + Nq * k];
+        if (j == N) r += sLf[3][v][i + Nq * k];
+        if (k == 0) r += sLf[4][v][i + Nq * j];
+        if (k == N) r += sLf[5][v][i + Nq * j];
+        R[v] = r;
+      }
+      const float tau = tab[L_TAU * kNP];
+      const float rho = tab[L_RHO * kNP] + sv[0];
+      float Sr[3];
+      Sr[0] = -tau * (sv[1] - rho * F.u_relax[0]);
+      Sr[1] = -tau * (sv[2] - rho * F.u_relax[1]);
+      Sr[2] = -sv[0] * F.g - tau * (sv[3] - rho * F.u_relax[2]);
+      Sr[0] -= 2.0f * (F.Omega[1] * sv[3] - F.Omega[2] * sv[2]);
+      Sr[1] -= 2.0f * (F.Omega[2] * sv[1] - F.Omega[0] * sv[3]);
+      Sr[2] -= 2.0f * (F.Omega[0] * sv[2] - F.Omega[1] * sv[1]);
+      R[1] += Sr[0];
+      R[2] += Sr[1];
+      R[3] += Sr[2];
+      const double *qr = P.qref64 + (size_t)e * 3 * Np + t;
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        const size_t i64 = ((size_t)e * 6 + v) * Np + t;
+        if (UPDATE) {
+          const size_t i32 = ((size_t)e * 6 + v) * kNP + t;
+          const float dq = (sc.A != 0.0 ? (float)sc.A * dQ[i32] : 0.f) + (float)sc.dt * R[v];
+          dQ[i32] = dq;
+          const double qn = Q64[i64] + sc.B * (double)dq;
+          Q64[i64] = qn;
+          const double ref = v == 0 ? qr[0] : (v == 4 ? qr[Np] : (v == 5 ? qr[2 * Np] : 0.0));
+          Sout[i32] = (float)(qn - ref);
+        } else {
+          Rout[i64] = (double)R[v];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Shadow of an FP64 state on a curvilinear mesh: per-node reference offsets.
+__global__ void k_shadow32c(const double *__restrict__ Q64, float *__restrict__ S, const KParams P, int Np) {
+  const long long n = (long long)P.E * Np;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const long long e = q / Np;
+    const int node = (int)(q - e * Np);
+    const double *qr = P.qref64 + (size_t)e * 3 * Np + node;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) {
+      const double ref = v == 0 ? qr[0] : (v == 4 ? qr[Np] : (v == 5 ? qr[2 * Np] : 0.0));
+      S[(e * 6 + v) * kNP + node] = (float)(Q64[(e * 6 + v) * Np + node] - ref);
+    }
+  }
+}
+
+cudaError_t launch_shadow32c(const double *Q64, float *S, const KParams &P, int N, cudaStream_t s) {
+  const int Nq = N + 1, Np = Nq * Nq * Nq;
+  long long nodes = (long long)P.E * Np;
+  int blocks = (int)((nodes + 255) / 256);
+  if (blocks > 148 * 32) blocks = 148 * 32;
+  k_shadow32c<<<blocks, 256, 0, s>>>(Q64, S, P, Np);
+  return cudaGetLastError();
+}
+
+template <bool MOIST, int CL>
+static void grad32c_instance(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s) {
+  static int grid = 0;
+  if (!grid) grid = grid_for((const void *)k_grad32c<4, MOIST, CL>, 1 << 30, 0);
+  k_grad32c<4, MOIST, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, P);
+}
+
+cudaError_t launch_grad32c(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s) {
+  if (P.closure == 2) {
+    if (P.moist)
+      grad32c_instance<true, 2>(S, F2, aux, P, s);
+    else
+      grad32c_instance<false, 2>(S, F2, aux, P, s);
+  } else {
+    if (P.moist)
+      grad32c_instance<true, 1>(S, F2, aux, P, s);
+    else
+      grad32c_instance<false, 1>(S, F2, aux, P, s);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs32c(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
+                          double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+  if (update) {
+    static int grid = 0;
+    if (!grid) grid = grid_for((const void *)k_rhs32c<4, true>, 1 << 30, 0);
+    k_rhs32c<4, true><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+  } else {
+    static int grid = 0;
+    if (!grid) grid = grid_for((const void *)k_rhs32c<4, false>, 1 << 30, 0);
+    k_rhs32c<4, false><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cmles

@@ -22,88 +22,9 @@
 #include "common.cuh"
 #include "launch.h"
 #include "mlp.cuh"
+#include "thermo32.cuh"
 
 namespace cmles {
-
-constexpr int kNP = 128;  // padded nodes per element in the FP32 arrays
-
-struct Th32 {
-  float rho, u[3], qp, Tp, pp, c, hp, thvp;
-};
-
-// p_v*(T) of the integrated Clausius-Clapeyron relation, FP32.
-__device__ __forceinline__ float pvsat32(const KF &F, float T) {
-  return F.pv_ptr * expf(F.pv_a * logf(T / F.pv_Ttr) + F.pv_b * (1.0f / F.pv_Ttr - 1.0f / T));
-}
-
-// Thermodynamics of one node from its deviation state s and its level table L.
-template <bool MOIST>
-__device__ __forceinline__ void thermo32(const KParams &P, const float *__restrict__ L, const float s[6], Th32 &o,
-                                         int &fail) {
-  const KF &F = P.f;
-  const float rho_r = L[L_RHO], rhoq_r = L[L_RHOQ], Tr = L[L_T], TrT0 = L[L_T_T0];
-  const float rp = s[0], qp = s[5];
-  const float rho = rho_r + rp;
-  const float rinv = 1.0f / rho;
-  o.rho = rho;
-  o.u[0] = s[1] * rinv;
-  o.u[1] = s[2] * rinv;
-  o.u[2] = s[3] * rinv;
-  const float rhoq = rhoq_r + qp;
-  o.qp = (qp - L[L_QM] * rp) * rinv;  // q_t - q_r
-  const float rke = 0.5f * (s[1] * o.u[0] + s[2] * o.u[1] + s[3] * o.u[2]);
-  const float dRI = s[4] - rke - rp * L[L_GZ];  // rho I - rho_r I_r
-  // unsaturated: rho c_vm (T - T_r) = d(rho I) - d(rho q) I_v0 - d(rho c_vm) (T_r - T_0)
-  // drqv = rho q_v - rho q_r is carried as a deviation (never formed as the
-  // difference of two near-equal FP32 numbers)
-  float rhoqv = rhoq, rhoql = 0.0f, drqv = qp;
-  float Tp = (dRI - qp * F.Iv0 - (rp * F.cvd + qp * (F.cvv - F.cvd)) * TrT0) /
-             (rho * F.cvd + rhoq * (F.cvv - F.cvd));
-  if (MOIST) {
-    float T = Tr + Tp;
-    if (rhoq > pvsat32(F, T) / (F.Rv * T)) {
-      bool conv = false;
-      for (int it = 0; it < P.satadj_max_iter; ++it) {
-        T = Tr + Tp;
-        const float rqs = pvsat32(F, T) / (F.Rv * T);
-        const float rql = rhoq - rqs;
-        const float rcvm = (rho - rhoq) * F.cvd + rqs * F.cvv + rql * F.cvl;
-        const float drcvm = (rp - qp) * F.cvd + (rqs - rhoq_r) * F.cvv + rql * F.cvl;
-        const float rf = rcvm * Tp + drcvm * TrT0 + (rqs - rhoq_r) * F.Iv0 - dRI;
-        const float Lh = F.Lv0 + F.dcp * (T - F.T0);
-        const float drqs = rqs * (Lh / (F.Rv * T * T) - 1.0f / T);
-        const float rfp = rcvm + drqs * ((F.cvv - F.cvl) * (T - F.T0) + F.Iv0);
-        const float dT = rf / rfp;
-        Tp -= dT;
-        if (fabsf(dT) <= 5e-5f) {
-          conv = true;
-          break;
-        }
-      }
-      if (!conv) fail = 1;
-      T = Tr + Tp;
-      rhoqv = pvsat32(F, T) / (F.Rv * T);
-      rhoql = rhoq - rhoqv;
-      drqv = rhoqv - rhoq_r;
-      if (rhoql < 0.0f) {
-        rhoql = 0.0f;
-        rhoqv = rhoq;
-        drqv = qp;
-      }
-    }
-  }
-  o.Tp = Tp;
-  const float rRm = F.Rd * (rho - rhoq) + F.Rv * rhoqv;
-  const float drRm = F.Rd * (rp - qp) + F.Rv * drqv;
-  const float pp = rRm * Tp + drRm * Tr;  // p - p_r
-  o.pp = pp;
-  const float rcvm = (rho - rhoq) * F.cvd + rhoqv * F.cvv + rhoql * F.cvl;
-  const float pr = L[L_P];
-  o.c = sqrtf((rcvm + rRm) / rcvm * (pr + pp) * rinv);
-  o.hp = (s[4] + pp - L[L_HM] * rp) * rinv;  // h_tot - h_r
-  const float lnr = log1pf(Tp / Tr) - F.kappa * log1pf(pp / pr) + log1pf(drRm / L[L_RHORM]) - log1pf(rp / rho_r);
-  o.thvp = L[L_THV] * expm1f(lnr);  // theta_v - theta_v,r
-}
 
 // CL: 1 Smagorinsky-Lilly with Richardson correction, 2 learned closure
 // (tensor-core MLP on the velocity and theta_v gradients and Delta).
@@ -284,20 +205,6 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
     __syncthreads();
   }
   if (fail) atomicAdd(P.flags, 1);
-}
-
-// Deviation part of n.F1 along d (sign by the caller):
-// [rho u_d, rho u_j u_d + (p - p_r) delta_jd, (rho e' + p') u_d, rho q_t u_d].
-// The reference part H_r u_d of the energy flux is handled separately.
-__device__ __forceinline__ void flux1_dev32(const float s[6], float rho_r, float rhoq_r, float pp, int d,
-                                           float f[6]) {
-  const float ud = s[1 + d] / (rho_r + s[0]);
-  f[0] = s[1 + d];
-  f[1] = s[1] * ud + (d == 0 ? pp : 0.f);
-  f[2] = s[2] * ud + (d == 1 ? pp : 0.f);
-  f[3] = s[3] * ud + (d == 2 ? pp : 0.f);
-  f[4] = (s[4] + pp) * ud;
-  f[5] = (rhoq_r + s[5]) * ud;
 }
 
 template <int N, bool UPDATE>

@@ -20,6 +20,13 @@ cudaError_t launch_grad32(const float *S, float *F2, float *aux, const KParams &
 cudaError_t launch_rhs32(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
                          double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s);
 
+// FP32 path on curvilinear (warped) meshes (dg_curved32.cu)
+enum { kCurvedNF = 24 };
+cudaError_t launch_shadow32c(const double *Q64, float *S, const KParams &P, int N, cudaStream_t s);
+cudaError_t launch_grad32c(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s);
+cudaError_t launch_rhs32c(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
+                          double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s);
+
 // Learned closure network (mlp.cu)
 struct MlpPacked;
 void pack_mlp_host(const float *params, MlpPacked *out);
@@ -34,8 +41,9 @@ cudaError_t launch_closure_samples(const double *Q, const KParams &P, int N, con
 // Budgets: partial sums per block into partials[nblocks][7] (6 integrals and a
 // non-finite count), then a single-block pass in fixed order into out[7].
 int budget_blocks(long long nodes);
+// wJn: optional per-node w_n J_n (curvilinear meshes); otherwise wq[n] * J
 cudaError_t launch_budgets(const double *Q, long long E, int Np, const double *wq, double J, double *partials,
-                           int nblocks, double *out, cudaStream_t s);
+                           int nblocks, double *out, cudaStream_t s, const double *wJn = nullptr);
 
 struct CaseDev {
   int id;
