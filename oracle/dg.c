@@ -116,9 +116,19 @@ orc_solver *orc_create(const orc_mesh *m, const orc_params *p) {
    * J = det(dX/dxi); J grad(xi_r) in the conservative curl form of Kopriva
    * (2006) (reading: the paper does not state how metrics are evaluated):
    *   (J a^r)_c = -[ curl_xi ( X_l grad_xi X_m ) ]_r,  (c, m, l) cyclic. */
+  /* The curl form is invariant under translation of the coordinates (the
+   * derivative operators along different directions commute), so the metric
+   * terms are evaluated from element-local coordinates X - X(node 0), which
+   * keeps their rounding independent of the element's distance from the
+   * origin. */
   double *V = (double *)malloc((size_t)Np * 3 * sizeof(double));
+  double *XL = (double *)malloc((size_t)Np * 3 * sizeof(double));
   for (int e = 0; e < E; ++e) {
-    const double *X[3] = {s->x + (size_t)e * Np, s->y + (size_t)e * Np, s->z + (size_t)e * Np};
+    for (int c = 0; c < 3; ++c) {
+      const double *Xa = (c == 0 ? s->x : (c == 1 ? s->y : s->z)) + (size_t)e * Np;
+      for (int n = 0; n < Np; ++n) XL[c * Np + n] = Xa[n] - Xa[0];
+    }
+    const double *X[3] = {XL, XL + Np, XL + 2 * Np};
     double vol = 0.0;
     for (int n = 0; n < Np; ++n) {
       int ijk[3];
@@ -163,6 +173,7 @@ orc_solver *orc_create(const orc_mesh *m, const orc_params *p) {
     }
   }
   free(V);
+  free(XL);
 
   /* Rayleigh sponge coefficient (Eq. sponge).  Reading of the garbled
    * profile: tau_s = alpha sin^gamma( pi/2 (z - z_s)/(z_top - z_s) ) above z_s;

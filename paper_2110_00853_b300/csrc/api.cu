@@ -379,6 +379,12 @@ cmles_status build_curved(cmles_handle h) {
       h->hx_[e * Np + n] = x;
       h->hz_[e * Np + n] = z;
     }
+    // metrics from element-local coordinates (the curl form is translation
+    // invariant; local coordinates keep the rounding independent of position)
+    for (int c = 0; c < 3; ++c) {
+      const double x0n = X[c * Np];
+      for (int n = 0; n < Np; ++n) X[c * Np + n] -= x0n;
+    }
     for (int c = 0; c < 3; ++c)
       for (int r = 0; r < 3; ++r)
         for (int n = 0; n < Np; ++n) dX[(c * 3 + r) * Np + n] = dref(&X[c * Np], n, r);
