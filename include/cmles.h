@@ -100,8 +100,9 @@ typedef struct {
 } cmles_diag;
 
 /* Initial-state description for cmles_init_case (synthetic cases; inputs,
- * not part of the method).  id: 1 dry bubble, 2 moist layer, 3 hill flow,
- * 5 throughput box.  modes: nmodes rows (kx, ky, kz, ax, ay, az, phase) of a
+ * not part of the method).  id: 1 dry bubble, 2 moist layer, 3 hill flow
+ * (warped meshes), 5 throughput box, 11 density current (theta_c/2 (1 +
+ * cos(pi r)) with radii r0 in x and r0/2 in z).  modes: nmodes rows (kx, ky, kz, ax, ay, az, phase) of a
  * random-phase velocity field, host memory, may be NULL. */
 typedef struct {
   int id;

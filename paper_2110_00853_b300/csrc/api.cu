@@ -835,7 +835,7 @@ cmles_status cmles_init_case(cmles_handle h, const cmles_case *c) {
     h->steps = 0;
     return CMLES_OK;
   }
-  if (c->id != 1 && c->id != 2 && c->id != 5)
+  if (c->id != 1 && c->id != 2 && c->id != 5 && c->id != 11)
     return fail(h, CMLES_ERR_ARG, "cmles_init_case: case id not available on flat meshes");
   const cmles_params &p = h->prm;
   const int nlev = h->mesh.nez * h->Nq;
@@ -881,7 +881,7 @@ cmles_status cmles_init_case(cmles_handle h, const cmles_case *c) {
   for (int l = 0; l < nlev; ++l) {
     const double z = level_z(h, l);
     double pp;
-    if (c->id == 1) {
+    if (c->id == 1 || c->id == 11) {
       pp = p.p0 * pow(1.0 - p.g / (cpd * c->theta0) * z, cpd / p.Rd);  // Eq. pressureDistrib
     } else if (!integrate) {                                            // Eq. pressure_hs_brunt
       const double N2 = c->NBV * c->NBV;

@@ -172,6 +172,11 @@ __global__ void k_init_state(double *__restrict__ Q, const CaseDev c, const KPar
         th += c.dtheta * cs * cs;
       }
     }
+    if (c.id == 11) {  // density current: theta_c/2 (1 + cos(pi r)), r <= 1
+      const double ax = (x - c.xc) / c.r0, az = (z - c.zc) / (0.5 * c.r0);
+      const double r = sqrt(ax * ax + az * az);
+      if (r <= 1.0) th += 0.5 * c.dtheta * (1.0 + cos(M_PI * r));
+    }
     if (c.nmodes > 0) {
       double su = 0.0, sv = 0.0, sw = 0.0;
       for (int m = 0; m < c.nmodes; ++m) {

@@ -34,6 +34,11 @@ def mesh(name, N=4):
         m.update(nex=128, ney=128, nez=64, Lx=6400.0, Ly=6400.0, Lz=3200.0)
     elif name == "c5":
         m.update(nex=160, ney=160, nez=80, Lx=32000.0, Ly=32000.0, Lz=16000.0)
+    elif name == "dc":
+        # 2.5D density current (Sec. 5.2): [0, 25.6 km] x [0, 6.4 km], one
+        # periodic element in y, walls in x and z; 200 m elements at N = 4
+        # give the 50 m effective resolution of one row of the front table
+        m.update(nex=128, ney=1, nez=32, Lx=25600.0, Ly=200.0, Lz=6400.0, periodic=(0, 1, 0))
     else:
         raise ValueError(name)
     return m
@@ -64,6 +69,8 @@ def physics(name, closure="sl", moist=None):
         p.update(sponge_alpha=0.5, sponge_zs=0.8 * 20000.0, u_relax=(10.0, 0.0, 0.0), lateral_sponge_frac=0.2)
     elif name == "c5":
         p.update(moist=True)
+    elif name == "dc":
+        p.update(Cs=0.18, dt=0.025)
     else:
         raise ValueError(name)
     if moist is not None:
@@ -90,6 +97,9 @@ def case(name, moist=None, modes=None):
                  qt_ml=16.3e-3, qt_top=4.0e-3, noise_theta=0.1, noise_qt=0.025e-3, noise_zmax=1600.0, moist=True)
     elif name == "c3":
         c.update(id=3, NBV=0.01, u0=(10.0, 0.0, 0.0))
+    elif name == "dc":
+        # theta_c = -15 K cosine bubble centred at (0, 3 km), radii 4 km x 2 km
+        c.update(id=11, dtheta=-15.0, r0=4000.0, xc=0.0, yc=0.0, zc=3000.0)
     elif name == "c5":
         c.update(id=5, seed=5, NBV=0.01, noise_theta=0.1, noise_qt=0.025e-3, noise_zmax=1600.0, qt_sfc=16.0e-3,
                  qt_H=2000.0, moist=True)
