@@ -70,7 +70,11 @@ def physics(name, closure="sl", moist=None):
     elif name == "c5":
         p.update(moist=True)
     elif name == "dc":
-        p.update(Cs=0.18, dt=0.025)
+        # C_s = 0.18 as in Sec. 5.2; the case is neutral and runs without the
+        # stable-stratification correction (reading: Eq. richardson is stated
+        # for stable regions of the atmosphere; with it the cold pool loses
+        # all eddy viscosity and the run diverges near t = 600 s)
+        p.update(Cs=0.18, dt=0.025, richardson=False)
     else:
         raise ValueError(name)
     if moist is not None:

@@ -1,6 +1,7 @@
 """Physics check of the whole solver: the 2.5D density current of Sec. 5.2
 run to t = 900 s at 50 m effective resolution (200 m elements, N = 4) with
-Smagorinsky-Lilly (C_s = 0.18) and the Rusanov flux, on the FP32 path.  The
+Smagorinsky-Lilly (C_s = 0.18, no Richardson correction: the case is
+neutral) and the Rusanov flux, on the FP32 path.  The
 paper reports the front at 14770 m for this resolution (Appendix B, Table
 t:densityCurrentComparisonTAB; stored in tests/golden/density_current_front.txt).
 The front is read as the largest x where the surface potential-temperature
