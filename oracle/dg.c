@@ -68,6 +68,7 @@ orc_solver *orc_create(const orc_mesh *m, const orc_params *p) {
   s->J = (double *)malloc(nn * sizeof(double));
   s->Ja = (double *)malloc(nn * 9 * sizeof(double));
   s->Delta = (double *)malloc((size_t)E * sizeof(double));
+  s->Dm = (double *)malloc((size_t)E * 3 * sizeof(double));
   s->EToE = (int *)malloc((size_t)E * 6 * sizeof(int));
   s->rho_r = (double *)calloc(nn, sizeof(double));
   s->p_r = (double *)calloc(nn, sizeof(double));
@@ -148,6 +149,15 @@ orc_solver *orc_create(const orc_mesh *m, const orc_params *p) {
     }
     s->Delta[e] = cbrt(vol) / N;
     for (int c = 0; c < 3; ++c) {
+      const double *Xa = (c == 0 ? s->x : (c == 1 ? s->y : s->z)) + (size_t)e * Np;
+      double lo = Xa[0], hi = Xa[0];
+      for (int n = 1; n < Np; ++n) {
+        if (Xa[n] < lo) lo = Xa[n];
+        if (Xa[n] > hi) hi = Xa[n];
+      }
+      s->Dm[e * 3 + c] = (hi - lo) / N;
+    }
+    for (int c = 0; c < 3; ++c) {
       int mm = (c + 1) % 3, ll = (c + 2) % 3;
       /* V_r = X_l * d X_m / d xi_r at every node */
       for (int n = 0; n < Np; ++n) {
@@ -204,7 +214,7 @@ orc_solver *orc_create(const orc_mesh *m, const orc_params *p) {
 
 void orc_destroy(orc_solver *s) {
   if (!s) return;
-  free(s->x); free(s->y); free(s->z); free(s->J); free(s->Ja); free(s->Delta); free(s->EToE);
+  free(s->x); free(s->y); free(s->z); free(s->J); free(s->Ja); free(s->Delta); free(s->Dm); free(s->EToE);
   free(s->rho_r); free(s->p_r); free(s->tau);
   free(s->G); free(s->gradG); free(s->nut); free(s->Dt); free(s->F2); free(s->aux); free(s->Ftot);
   free(s);
@@ -373,6 +383,9 @@ int orc_rhs(orc_solver *s, const double *Q, double *RHS, int form) {
       double nut = 0.0, Dt = 0.0;
       if (P->closure == ORC_CLOSURE_SL) {
         nut = orc_smagorinsky(P, gu, gth[2], thv, s->Delta[e]);
+        Dt = nut / P->Prt;
+      } else if (P->closure == ORC_CLOSURE_VREMAN) {
+        nut = orc_vreman(P, gu, gth[2], thv, s->Dm + (size_t)e * 3);
         Dt = nut / P->Prt;
       } else if (P->closure == ORC_CLOSURE_MLP && s->has_mlp) {
         double xin[13], yout[2];

@@ -12,7 +12,7 @@
  *   Sec. 3.1 nodal DG on LGL hexahedra (Eqs. expansion .. matrixProblem),
  *            Rusanov flux (Eq. nonviscFlux), BR1 auxiliary gradient
  *   Sec. 3.2 low-storage Runge-Kutta (Carpenter & Kennedy 1994, 5 stages)
- *   Sec. 4   Smagorinsky-Lilly closure with the Richardson correction
+ *   Sec. 4   Smagorinsky-Lilly and Vreman closures with the Richardson correction
  *   App. A   wall boundary conditions, prescribed wall fluxes, Rayleigh sponge
  *   App. C   Favre (density-weighted) horizontal means
  * Readings where the paper is silent or garbled are listed in the design doc and
@@ -31,6 +31,7 @@
 #define ORC_CLOSURE_NONE 0
 #define ORC_CLOSURE_SL 1
 #define ORC_CLOSURE_MLP 2
+#define ORC_CLOSURE_VREMAN 3
 
 typedef struct {
   int N;                      /* polynomial order */
@@ -93,6 +94,11 @@ void orc_rusanov(const orc_params *p, const double Ym[6], const double Yp[6], do
 /* Smagorinsky-Lilly nu_t from the velocity gradient gu[i][j] = du_i/dx_j,
  * d(theta_v)/dz, theta_v and Delta (Eqs. smago, richardson). */
 double orc_smagorinsky(const orc_params *p, const double gu[9], double dthvdz, double thv, double Delta);
+/* Vreman nu_t (Eq. vreman-sgs) from the velocity gradient gu[i][j] = du_i/dx_j
+ * and the directional lengths Dm[m] = L_m / N, times the same Richardson
+ * factor as Smagorinsky-Lilly when p->richardson is set (reading: the
+ * correction multiplies "the eddy viscosity" of either model). */
+double orc_vreman(const orc_params *p, const double gu[9], double dthvdz, double thv, const double Dm[3]);
 
 /* ---- solver ---- */
 orc_solver *orc_create(const orc_mesh *m, const orc_params *p);

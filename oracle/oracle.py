@@ -55,7 +55,7 @@ class Case(C.Structure):
                 ("qt_H", C.c_double)]
 
 
-CLOSURE = {"none": 0, "sl": 1, "mlp": 2}
+CLOSURE = {"none": 0, "sl": 1, "mlp": 2, "vreman": 3}
 
 # Table t:constants; g, p0, p_tr, T_tr are readings (the table omits them).
 CONSTANTS = dict(g=9.81, p0=1.0e5, Rd=287.0, Rv=462.0, cvd=717.5, cvv=1397.5, cvl=4181.0, cvi=2100.0,
@@ -78,6 +78,8 @@ def _declare(L):
     L.orc_rusanov.argtypes = [C.POINTER(Params), _DP, _DP, C.c_double, C.c_double, _DP, _DP]
     L.orc_smagorinsky.argtypes = [C.POINTER(Params), _DP, C.c_double, C.c_double, C.c_double]
     L.orc_smagorinsky.restype = C.c_double
+    L.orc_vreman.argtypes = [C.POINTER(Params), _DP, C.c_double, C.c_double, _DP]
+    L.orc_vreman.restype = C.c_double
     L.orc_create.argtypes = [C.POINTER(Mesh), C.POINTER(Params)]
     L.orc_create.restype = C.c_void_p
     L.orc_destroy.argtypes = [C.c_void_p]
@@ -199,6 +201,11 @@ def rusanov(P, Ym, Yp, z, pr, n):
 
 def smagorinsky(P, gu, dthvdz, thv, Delta):
     return lib().orc_smagorinsky(C.byref(P), _p(np.ascontiguousarray(gu, float).ravel()), dthvdz, thv, Delta)
+
+
+def vreman(P, gu, dthvdz, thv, Dm):
+    return lib().orc_vreman(C.byref(P), _p(np.ascontiguousarray(gu, float).ravel()), dthvdz, thv,
+                            _p(np.ascontiguousarray(Dm, float).ravel()))
 
 
 def uniform(seed, counter):

@@ -13,6 +13,7 @@ struct orc_solver {
   double xi[ORC_MAXQ], w[ORC_MAXQ], D[ORC_MAXQ * ORC_MAXQ];
   double *x, *y, *z, *J, *Ja; /* Ja[e][n][r][c] = J * d xi_r / d x_c */
   double *Delta;              /* [E] */
+  double *Dm;                 /* [E][3], L_m / N from the element's extent along axis m */
   int *EToE;                  /* [E][6], -1 = wall */
   double *rho_r, *p_r, *tau;  /* [E][Np] */
   /* work arrays of the last RHS */

@@ -145,6 +145,42 @@ void orc_rusanov(const orc_params *p, const double Ym[6], const double Yp[6], do
  *   Ri = (g/theta_v d theta_v/dz) / |S|^2,
  *   f_b = 1 for Ri <= 0, max(0, 1 - Ri/Pr_t)^{1/4} otherwise.
  * Reading: nu_t = 0 when |S| = 0. */
+/* Richardson factor f_b (Eq. richardson) for |S|^2 = 2 S:S > 0. */
+static double richardson_factor(const orc_params *p, double dthvdz, double thv, double Smag2) {
+  double N2 = p->g / thv * dthvdz;
+  double Ri = N2 / Smag2;
+  if (Ri <= 0.0) return 1.0;
+  double a = 1.0 - Ri / p->Prt;
+  return a > 0.0 ? pow(a, 0.25) : 0.0;
+}
+
+double orc_vreman(const orc_params *p, const double gu[9], double dthvdz, double thv, const double Dm[3]) {
+  /* beta_ij = sum_m Delta_m^2 u_i,m u_j,m */
+  double beta[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0.0;
+      for (int m = 0; m < 3; ++m) acc += Dm[m] * Dm[m] * gu[3 * i + m] * gu[3 * j + m];
+      beta[i][j] = acc;
+    }
+  double B = beta[0][0] * beta[1][1] + beta[0][0] * beta[2][2] + beta[1][1] * beta[2][2] -
+             (beta[0][2] * beta[0][2] + beta[0][1] * beta[0][1] + beta[1][2] * beta[1][2]);
+  double uu = 0.0;
+  for (int k = 0; k < 9; ++k) uu += gu[k] * gu[k];
+  if (uu == 0.0 || B <= 0.0) return 0.0;
+  double nut = 2.5 * p->Cs * p->Cs * sqrt(B / uu);
+  if (p->richardson) {
+    double S2 = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double Sij = 0.5 * (gu[3 * i + j] + gu[3 * j + i]);
+        S2 += Sij * Sij;
+      }
+    if (S2 > 0.0) nut *= richardson_factor(p, dthvdz, thv, 2.0 * S2);
+  }
+  return nut;
+}
+
 double orc_smagorinsky(const orc_params *p, const double gu[9], double dthvdz, double thv, double Delta) {
   double S2 = 0.0;
   for (int i = 0; i < 3; ++i)

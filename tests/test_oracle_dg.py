@@ -148,6 +148,39 @@ def test_linear_shear_smagorinsky_through_pipeline(orc):
     assert np.abs(it["nut"] / nut_exact - 1.0).max() < 1e-6
 
 
+def test_solid_body_rotation_vreman_through_pipeline(orc):
+    """u = (-Om (y - yc), Om (x - xc), 0) is linear, so the BR1 gradient is
+    exact in elements away from the walls and Vreman's nu_t takes its
+    closed form 2.5 C_s^2 Delta^2 Om / sqrt(2) (isotropic Delta = 125 m)."""
+    m = dict(I.mesh("c1"), periodic=(0, 0, 0))
+    c = I.case("c1")
+    c.update(dtheta=0.0, noise_theta=0.0)
+    ph = dict(I.physics("c1"), closure="vreman", Cs=0.18, richardson=False)
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, c)
+    g = S.geometry()
+    Om = 0.01
+    u, v = -Om * (g["y"] - 1000.0), Om * (g["x"] - 1000.0)
+    Q = Q.copy()
+    Q[:, 4] += 0.5 * Q[:, 0] * (u * u + v * v)
+    Q[:, 1] = Q[:, 0] * u
+    Q[:, 2] = Q[:, 0] * v
+    S.rhs(Q)
+    it = S.intermediates()
+    e = np.arange(S.E)
+    ex, ey = e % 4, (e // 4) % 4
+    inner = (ex > 0) & (ex < 3) & (ey > 0) & (ey < 3)
+    want = 2.5 * 0.18 ** 2 * 125.0 ** 2 * Om / np.sqrt(2.0)
+    assert np.abs(it["nut"][inner] / want - 1.0).max() < 1e-8
+    # a pure shear gives no Vreman viscosity
+    Q2 = Q.copy()
+    w = 0.01 * (g["z"] - 1000.0)
+    Q2[:, 1] = Q[:, 0] * w
+    Q2[:, 2] = 0.0
+    Q2[:, 4] = Q[:, 4] - 0.5 * Q[:, 0] * (u * u + v * v) + 0.5 * Q[:, 0] * w * w
+    S.rhs(Q2)
+    assert np.abs(S.intermediates()["nut"][inner]).max() < 1e-8 * want
+
+
 def _vortex_error(orc, N, nel, T=0.02, cfl=0.3):
     M = orc.make_mesh(N, nel, nel, 1, 10.0, 10.0, 10.0 / nel, x0=-5.0, y0=-5.0, periodic=(1, 1, 1))
     P = orc.make_params(closure="none", g=0.0)

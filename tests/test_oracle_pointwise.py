@@ -187,6 +187,56 @@ def test_richardson_correction(orc):
         assert abs(orc.smagorinsky(P, gu, dthdz, thv, Delta) - base * fb) < 1e-12 * base
 
 
+def test_vreman_special_cases(orc):
+    """Eq. vreman-sgs: zero for a pure shear (the model's design property), a
+    closed form for solid-body rotation with isotropic lengths."""
+    P = orc.make_params(Cs=0.18, richardson=False)
+    Dm = [25.0, 25.0, 25.0]
+    gu = np.zeros((3, 3))
+    gu[0, 2] = 0.02                  # u = gamma z
+    assert orc.vreman(P, gu, 0.0, 300.0, Dm) == 0.0
+    Om = 0.03                        # u = (-Om y, Om x, 0): singular values Om, Om, 0
+    rot = np.array([[0.0, -Om, 0.0], [Om, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    want = 2.5 * 0.18 ** 2 * 25.0 ** 2 * Om / np.sqrt(2.0)
+    assert abs(orc.vreman(P, rot, 0.0, 300.0, Dm) - want) < 1e-14 * want
+    assert orc.vreman(P, np.zeros((3, 3)), 0.0, 300.0, Dm) == 0.0
+
+
+def test_vreman_against_singular_values(orc):
+    """B_beta is the sum of the 2x2 principal minors of beta = A A^T with
+    A = grad(u) diag(Delta_m), i.e. sum_{i<j} s_i^2 s_j^2 over the singular
+    values of A; checked on random gradients and anisotropic lengths."""
+    P = orc.make_params(Cs=0.21, richardson=False)
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        gu = rng.normal(size=(3, 3)) * 0.05
+        Dm = rng.uniform(10.0, 80.0, size=3)
+        s = np.linalg.svd(gu @ np.diag(Dm), compute_uv=False) ** 2
+        B = s[0] * s[1] + s[0] * s[2] + s[1] * s[2]
+        want = 2.5 * 0.21 ** 2 * np.sqrt(B / (gu ** 2).sum())
+        assert abs(orc.vreman(P, gu, 0.0, 300.0, Dm) - want) < 1e-12 * want
+        # lengths enter per direction m (columns of grad u), not per component
+        gT = gu.T.copy()
+        sT = np.linalg.svd(gT @ np.diag(Dm), compute_uv=False) ** 2
+        BT = sT[0] * sT[1] + sT[0] * sT[2] + sT[1] * sT[2]
+        assert abs(orc.vreman(P, gT, 0.0, 300.0, Dm) - 2.5 * 0.21 ** 2 * np.sqrt(BT / (gu ** 2).sum())) < 1e-12 * want * 10
+
+
+def test_vreman_richardson_factor_same_as_smagorinsky(orc):
+    Pn = orc.make_params(Cs=0.2, richardson=False)
+    Pr = orc.make_params(Cs=0.2, richardson=True)
+    rng = np.random.default_rng(5)
+    for Ri in (-0.5, 0.1, 0.3, 0.4):
+        gu = rng.normal(size=(3, 3)) * 0.02
+        S = 0.5 * (gu + gu.T)
+        thv = 300.0
+        dthdz = Ri * 2.0 * (S * S).sum() * thv / Pr.g
+        Dm = [20.0, 30.0, 10.0]
+        f_sl = orc.smagorinsky(Pr, gu, dthdz, thv, 10.0) / orc.smagorinsky(Pn, gu, dthdz, thv, 10.0)
+        v0 = orc.vreman(Pn, gu, dthdz, thv, Dm)
+        assert abs(orc.vreman(Pr, gu, dthdz, thv, Dm) - f_sl * v0) <= 1e-13 * v0
+
+
 # ------------------------------------------------------------------ LSRK(5,4)
 
 def test_lsrk54_stability_polynomial(orc):
