@@ -47,7 +47,7 @@ typedef enum {
   CMLES_ERR_STATE = 7      /* call out of order (e.g. no reference state yet) */
 } cmles_status;
 
-enum { CMLES_CLOSURE_NONE = 0, CMLES_CLOSURE_SL = 1, CMLES_CLOSURE_MLP = 2 };
+enum { CMLES_CLOSURE_NONE = 0, CMLES_CLOSURE_SL = 1, CMLES_CLOSURE_MLP = 2, CMLES_CLOSURE_VREMAN = 3 };
 
 /* Arithmetic of the RHS kernels.
  *   CMLES_FP64       all FP64 ("plain" method).
@@ -76,7 +76,9 @@ typedef struct {
  * g = 9.81 m s^-2, p0 = 1e5 Pa, p_tr = 611.657 Pa, T_tr = 273.16 K. */
 typedef struct {
   double g, p0, Rd, Rv, cvd, cvv, cvl, cvi, T0, Lv0, Lf0, ptr, Ttr;
-  int closure;           /* CMLES_CLOSURE_*: Smagorinsky-Lilly (Sec. 4.1) or learned MLP */
+  int closure;           /* CMLES_CLOSURE_*: Smagorinsky-Lilly (Sec. 4.1), Vreman (Sec. 4.2,
+                            Delta_m = h_m / N; flat meshes only) or learned MLP; the
+                            Richardson factor multiplies SL and Vreman alike */
   double Cs, Prt;        /* Smagorinsky coefficient, turbulent Prandtl number (1/3) */
   int richardson;        /* apply the Richardson correction f_b (Eq. richardson) */
   int moist;             /* saturation adjustment on (Sec. 2.6) */

@@ -234,6 +234,9 @@ void fill_kparams(cmles_handle h) {
   // Delta = (element volume)^(1/3) / N (Sec. 4.1, geometric mean of L_d / N)
   const double Delta = cbrt(K.hx * K.hy * K.hz) / h->N;
   K.CsDelta2 = (p.Cs * Delta) * (p.Cs * Delta);
+  // Vreman: Delta_m = h_m / N per direction
+  K.vr_c = 2.5 * p.Cs * p.Cs;
+  for (int d = 0; d < 3; ++d) K.vr_d2[d] = (hd[d] / h->N) * (hd[d] / h->N);
   K.satadj_max_iter = p.satadj_max_iter > 0 ? p.satadj_max_iter : 20;
   for (int a = 0; a < h->Nq; ++a) {
     K.w[a] = h->w[a];
@@ -258,6 +261,8 @@ void fill_kparams(cmles_handle h) {
   F.dcp = (float)K.dcp;
   F.CsDelta2 = (float)K.CsDelta2;
   F.Delta = (float)Delta;
+  F.vr_c = (float)K.vr_c;
+  for (int d = 0; d < 3; ++d) F.vr_d2[d] = (float)K.vr_d2[d];
   K.mlp = h->mlp_dev;
   F.inv_Prt = (float)K.inv_Prt;
   for (int d = 0; d < 3; ++d) {
@@ -561,8 +566,10 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   // the FP32 shadow is relative to a per-level reference: z must not wrap
   if (params->precision == CMLES_FP32_ACC64 && mesh->periodic[2]) return CMLES_ERR_ARG;
   if (params->closure != CMLES_CLOSURE_NONE && params->closure != CMLES_CLOSURE_SL &&
-      params->closure != CMLES_CLOSURE_MLP)
+      params->closure != CMLES_CLOSURE_MLP && params->closure != CMLES_CLOSURE_VREMAN)
     return CMLES_ERR_ARG;
+  // Vreman's directional lengths are those of the flat elements
+  if (params->closure == CMLES_CLOSURE_VREMAN && mesh->warp) return CMLES_ERR_ARG;
   // the learned closure runs on BF16 tensor cores inside the FP32 kernels
   if (params->closure == CMLES_CLOSURE_MLP && params->precision != CMLES_FP32_ACC64) return CMLES_ERR_ARG;
   long long E = (long long)mesh->nex * mesh->ney * mesh->nez;

@@ -19,6 +19,7 @@ constexpr int kMaxQ = 8;
 struct KF {
   float g, Rd, Rv, cvd, cvv, cvl, T0, Lv0, Iv0, kappa, pv_ptr, pv_Ttr, pv_a, pv_b, dcp;
   float CsDelta2, inv_Prt, Delta;
+  float vr_c, vr_d2[3];
   float jac[3], lift[3];
   float u_relax[3], Omega[3];
   float E_water, E_energy;
@@ -41,6 +42,8 @@ struct KParams {
   double dcp;        // c_pv - c_pl
   // closure
   double CsDelta2;   // (C_s Delta)^2
+  double vr_c;       // 2.5 C_s^2 (Vreman)
+  double vr_d2[3];   // Delta_m^2 = (h_m / N)^2 (Vreman)
   double Prt, inv_Prt;
   int richardson, moist, closure;
   // sources
@@ -121,5 +124,35 @@ __device__ __forceinline__ double node_z(const KParams &P, int ez, int k) {
 struct StageCoef {
   double A, B, dt;
 };
+
+
+// Vreman eddy viscosity (Eq. vreman-sgs) from gr[i][m] = d u_i / d x_m and
+// d2[m] = Delta_m^2.  B_beta, the sum of the 2x2 principal minors of
+// beta = A A^T with A = grad(u) diag(Delta_m), is evaluated by the
+// Cauchy-Binet identity as sum_{i<j} sum_{m<n} Delta_m^2 Delta_n^2
+// (u_i,m u_j,n - u_i,n u_j,m)^2: a sum of squares, so rounding cannot turn
+// it negative and a nearly rank-one gradient (a shear) loses no digits.
+template <typename T>
+__device__ __forceinline__ T vreman_nu(const T (&gr)[6][3], T c25, const T (&d2)[3]) {
+  T uu = T(0), B = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) uu += gr[a][b] * gr[a][b];
+  constexpr int lo[3] = {0, 0, 1}, hi[3] = {1, 2, 2};
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int m = lo[p], n = hi[p];
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int i = lo[q], j = hi[q];
+      const T det = gr[i][m] * gr[j][n] - gr[i][n] * gr[j][m];
+      acc += det * det;
+    }
+    B += d2[m] * d2[n] * acc;
+  }
+  return uu > T(0) ? c25 * sqrt(B / uu) : T(0);
+}
 
 }  // namespace cmles

@@ -26,7 +26,8 @@
 
 namespace cmles {
 
-// CL: 1 Smagorinsky-Lilly with Richardson correction, 2 learned closure
+// CL: 1 Smagorinsky-Lilly, 3 Vreman (both with the Richardson correction),
+// 2 learned closure
 // (tensor-core MLP on the velocity and theta_v gradients and Delta).
 template <int N, bool MOIST, int CL>
 __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__restrict__ S, float *__restrict__ F2,
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
       if (k == 0) lift(4, i + Nq * j);
       if (k == N) lift(5, i + Nq * j);
 
-      if (CL == 1 && P.closure == 1) {
+      if ((CL == 1 && P.closure == 1) || CL == 3) {
         float S2 = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -143,20 +144,19 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
             S2 += Sab * Sab;
           }
         const float Smag2 = 2.0f * S2;
-        if (Smag2 > 0.0f) {
-          const float Smag = sqrtf(Smag2);
-          float fb = 1.0f;
-          if (P.richardson) {
-            const float thv = L[L_THV] + G[5];
-            const float Ri = F.g / thv * gr[5][2] / Smag2;
-            if (Ri > 0.0f) {
-              const float a = 1.0f - Ri * F.inv_Prt;
-              fb = a > 0.0f ? sqrtf(sqrtf(a)) : 0.0f;
-            }
+        if (CL == 1)
+          nut = Smag2 > 0.0f ? F.CsDelta2 * sqrtf(Smag2) : 0.0f;
+        else
+          nut = vreman_nu<float>(gr, F.vr_c, F.vr_d2);
+        if (P.richardson && Smag2 > 0.0f) {
+          const float thv = L[L_THV] + G[5];
+          const float Ri = F.g / thv * gr[5][2] / Smag2;
+          if (Ri > 0.0f) {
+            const float a = 1.0f - Ri * F.inv_Prt;
+            nut *= a > 0.0f ? sqrtf(sqrtf(a)) : 0.0f;
           }
-          nut = F.CsDelta2 * Smag * fb;
-          Dt = nut * F.inv_Prt;
         }
+        Dt = nut * F.inv_Prt;
       }
     }
     if (CL == 2) {
@@ -415,6 +415,11 @@ cudaError_t launch_grad32(const float *S, float *F2, float *aux, const KParams &
       grad32_instance<true, 2>(S, F2, aux, P, s);
     else
       grad32_instance<false, 2>(S, F2, aux, P, s);
+  } else if (P.closure == 3) {
+    if (P.moist)
+      grad32_instance<true, 3>(S, F2, aux, P, s);
+    else
+      grad32_instance<false, 3>(S, F2, aux, P, s);
   } else {
     if (P.moist)
       grad32_instance<true, 1>(S, F2, aux, P, s);

@@ -110,9 +110,10 @@ __global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, do
       if (k == 0) lift(4, i + Nq * j);
       if (k == N) lift(5, i + Nq * j);
 
-      // Smagorinsky-Lilly with Richardson correction (Eqs. smago, richardson)
+      // Smagorinsky-Lilly (Eq. smago) or Vreman (Eq. vreman-sgs), times the
+      // Richardson correction (Eq. richardson)
       double nut = 0.0, Dt = 0.0;
-      if (P.closure == 1) {
+      if (P.closure == 1 || P.closure == 3) {
         double S2 = 0.0;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -122,19 +123,18 @@ __global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, do
             S2 += Sab * Sab;
           }
         const double Smag2 = 2.0 * S2;
-        if (Smag2 > 0.0) {
-          const double Smag = sqrt(Smag2);
-          double fb = 1.0;
-          if (P.richardson) {
-            const double Ri = P.g / G[5] * gr[5][2] / Smag2;
-            if (Ri > 0.0) {
-              const double a = 1.0 - Ri * P.inv_Prt;
-              fb = a > 0.0 ? sqrt(sqrt(a)) : 0.0;
-            }
+        if (P.closure == 1)
+          nut = Smag2 > 0.0 ? P.CsDelta2 * sqrt(Smag2) : 0.0;
+        else
+          nut = vreman_nu<double>(gr, P.vr_c, P.vr_d2);
+        if (P.richardson && Smag2 > 0.0) {
+          const double Ri = P.g / G[5] * gr[5][2] / Smag2;
+          if (Ri > 0.0) {
+            const double a = 1.0 - Ri * P.inv_Prt;
+            nut *= a > 0.0 ? sqrt(sqrt(a)) : 0.0;
           }
-          nut = P.CsDelta2 * Smag * fb;
-          Dt = nut * P.inv_Prt;
         }
+        Dt = nut * P.inv_Prt;
       }
       // F2 rows: [rho d_i, rho tau_ij + d_i rho u_j, -rho D_t dh/dx_i + (rho tau u)_i],
       // d = -D_t grad q_t, rho tau = -2 rho nu_t S (Eqs. diff_moisture_flux,

@@ -103,6 +103,20 @@ def test_tendency_closure_none_and_no_richardson(orc):
         _compare_rhs(S, Q, G, 1e-12)
 
 
+@pytest.mark.parametrize("richardson", [True, False])
+def test_tendency_vreman(orc, richardson):
+    # Vreman closure (Eq. vreman-sgs) on the moist sub-box with anisotropic
+    # elements (200 x 200 x 120 m): Delta_m differs per direction
+    m = I.sub_mesh("c2", 5, 3, 16)
+    m["Lz"] = 16 * 120.0
+    ph = I.physics("c2", closure="vreman")
+    ph["richardson"] = richardson
+    S, Q, G = _setup(orc, "c2", m, phys=ph, fuzz_seed=6)
+    S.rhs(Q)
+    assert np.abs(S.intermediates()["nut"]).max() > 0.0
+    _compare_rhs(S, Q, G, 1e-12)
+
+
 def test_single_element_periodic_degenerate(orc):
     # one element periodic in x and y: every neighbour is the element itself
     m = I.sub_mesh("c1", 1, 1, 2)

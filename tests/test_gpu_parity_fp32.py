@@ -93,6 +93,16 @@ def test_fp32_tendency_walls_rotation_sponge(orc):
     print("walls fp32 rel L2", _compare(S, Q, G))
 
 
+@pytest.mark.parametrize("richardson", [True, False])
+def test_fp32_tendency_vreman(orc, richardson):
+    m = I.sub_mesh("c2", 5, 3, 16)
+    m["Lz"] = 16 * 120.0
+    ph = I.physics("c2", closure="vreman")
+    ph["richardson"] = richardson
+    S, Q, G = _setup(orc, "c2", m, phys=ph, fuzz_seed=16)
+    print("vreman fp32 rel L2", _compare(S, Q, G))
+
+
 def test_fp32_tendency_c5_subbox(orc):
     m = I.sub_mesh("c5", 4, 4, 10)
     c = I.case("c5")
