@@ -112,6 +112,21 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(ms, world, torch, device):
+    """the slowest rank's time (every rank gets it); a no-op for one rank"""
+    if world <= 1:
+        return ms
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(nodes_per_rank, world, steps, ms):
+    """node-stage updates per second of all ranks together over the slowest
+    rank's time (replicas: every rank advances its own box)"""
+    return nodes_per_rank * world * STAGES * steps / (ms / 1e3)
+
+
 def closure_weights():
     """Seeded network of the closure's architecture (13 -> 64 -> 64 -> 2); the
     throughput does not depend on the weight values.  Input scales match the
@@ -164,10 +179,7 @@ def run_variant(name, precision, closure, steps, warmup, world, rank, torch, sub
     G.close()
     del G
     torch.cuda.empty_cache()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, torch, "cuda")
     return dict(name=name, ms=ms, kt=kt, launches=launches, nodes=nodes, clocks=clocks,
                 finite=not diag["nonfinite"], satadj_failures=diag["satadj_failures"])
 
@@ -266,8 +278,7 @@ def main():
         results[name] = run_variant(name, prec, clo, args.steps, args.warmup, world, rank, torch, sub)
     head = results[variants[0][0]]
     prec = variants[0][1]
-    total_nodes = head["nodes"] * world
-    value = total_nodes * STAGES * args.steps / (head["ms"] / 1e3)
+    value = whole_job_rate(head["nodes"], world, args.steps, head["ms"])
     kt = head["kt"]
     kinds = ["grad", "rhs"]
     dom = max(range(2), key=lambda k: kt["ms"][k])
@@ -275,7 +286,7 @@ def main():
     achieved = head["nodes"] * BYTES[prec][kinds[dom]] / (avg_ms / 1e3) / 1e9
     out_variants = {}
     for (name, vprec, _), r in zip(variants, results.values()):
-        v = r["nodes"] * world * STAGES * args.steps / (r["ms"] / 1e3)
+        v = whole_job_rate(r["nodes"], world, args.steps, r["ms"])
         per = {}
         for k in range(2):
             a = r["kt"]["ms"][k] / max(r["kt"]["count"][k], 1)
