@@ -25,9 +25,9 @@ void pack_mlp_host(const float *p, MlpPacked *o) {
   for (int n = 0; n < kMlpH; ++n)
     for (int k = 0; k < kMlpIn; ++k) o->W1[n * kMlpInPad + k] = __float2bfloat16_rn(p[kMlpOffW1 + n * kMlpIn + k]);
   for (int n = 0; n < kMlpH; ++n)
-    for (int k = 0; k < kMlpH; ++k) o->W2[n * kMlpH + k] = __float2bfloat16_rn(p[kMlpOffW2 + n * kMlpH + k]);
+    for (int k = 0; k < kMlpH; ++k) o->W2[n * kLdW + k] = __float2bfloat16_rn(p[kMlpOffW2 + n * kMlpH + k]);
   for (int n = 0; n < kMlpOut; ++n)
-    for (int k = 0; k < kMlpH; ++k) o->W3[n * kMlpH + k] = __float2bfloat16_rn(p[kMlpOffW3 + n * kMlpH + k]);
+    for (int k = 0; k < kMlpH; ++k) o->W3[n * kLdW + k] = __float2bfloat16_rn(p[kMlpOffW3 + n * kMlpH + k]);
   for (int n = 0; n < kMlpH; ++n) {
     o->b1[n] = p[kMlpOffB1 + n];
     o->b2[n] = p[kMlpOffB2 + n];
@@ -45,10 +45,13 @@ __global__ void k_pack_mlp(const float *__restrict__ p, MlpPacked *__restrict__ 
     const int n = q / kMlpInPad, k = q % kMlpInPad;
     o->W1[q] = __float2bfloat16_rn(k < kMlpIn ? p[kMlpOffW1 + n * kMlpIn + k] : 0.f);
   }
-  for (int q = t; q < kMlpH * kMlpH; q += nt) o->W2[q] = __float2bfloat16_rn(p[kMlpOffW2 + q]);
-  for (int q = t; q < kMlpOutPad * kMlpH; q += nt) {
-    const int n = q / kMlpH;
-    o->W3[q] = __float2bfloat16_rn(n < kMlpOut ? p[kMlpOffW3 + q] : 0.f);
+  for (int q = t; q < kMlpH * kLdW; q += nt) {
+    const int n = q / kLdW, k = q % kLdW;
+    o->W2[q] = __float2bfloat16_rn(k < kMlpH ? p[kMlpOffW2 + n * kMlpH + k] : 0.f);
+  }
+  for (int q = t; q < kMlpOutPad * kLdW; q += nt) {
+    const int n = q / kLdW, k = q % kLdW;
+    o->W3[q] = __float2bfloat16_rn(n < kMlpOut && k < kMlpH ? p[kMlpOffW3 + n * kMlpH + k] : 0.f);
   }
   for (int q = t; q < kMlpH; q += nt) {
     o->b1[q] = p[kMlpOffB1 + q];
@@ -99,7 +102,7 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const MlpPacked *__restrict
 
 struct TrainSmem {
   MlpPacked W;
-  __nv_bfloat16 W2T[kMlpH * kMlpH];     // W2^T: [in][out]
+  __nv_bfloat16 W2T[kMlpH * kLdW];      // W2^T: [in][out], row stride kLdW
   __nv_bfloat16 X[128 * kMlpInPad];     // inputs, row-major
   __nv_bfloat16 XT[kMlpInPad * 128];    // inputs, [feature][sample]
   float A1[128 * kMlpH], A2[128 * kMlpH];  // pre-activations
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
   __syncthreads();
   for (int q = t; q < kMlpH * kMlpH; q += 128) {
     const int o = q / kMlpH, i = q % kMlpH;
-    S.W2T[i * kMlpH + o] = S.W.W2[q];
+    S.W2T[i * kLdW + o] = S.W.W2[o * kLdW + i];
   }
   __syncthreads();
   const float inv_n = 1.0f / (float)n;
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
     }
     // da2 = (W3^T dy) * silu'(a2): thread per sample
     for (int i = 0; i < kMlpH; ++i) {
-      const float w0 = __bfloat162float(S.W.W3[0 * kMlpH + i]), w1 = __bfloat162float(S.W.W3[1 * kMlpH + i]);
+      const float w0 = __bfloat162float(S.W.W3[0 * kLdW + i]), w1 = __bfloat162float(S.W.W3[1 * kLdW + i]);
       const float da = (w0 * dy0 + w1 * dy1) * dsilu(S.A2[t * kMlpH + i]);
       const __nv_bfloat16 db = __float2bfloat16_rn(da);
       S.DA2[t * kMlpH + i] = db;
@@ -203,8 +206,8 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
         float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt)
-          mma_bf16_16816(d, a[kt], ld_u32(S.W2T + (8 * nt + g) * kMlpH + 16 * kt + 2 * c),
-                         ld_u32(S.W2T + (8 * nt + g) * kMlpH + 16 * kt + 2 * c + 8));
+          mma_bf16_16816(d, a[kt], ld_u32(S.W2T + (8 * nt + g) * kLdW + 16 * kt + 2 * c),
+                         ld_u32(S.W2T + (8 * nt + g) * kLdW + 16 * kt + 2 * c + 8));
         const int col = 8 * nt + 2 * c;
         const int rows[2] = {rb + g, rb + g + 8};
 #pragma unroll

@@ -22,12 +22,17 @@ constexpr int kMlpInPad = 16, kMlpOutPad = 8;
 constexpr int kMlpOffW1 = 0, kMlpOffB1 = 832, kMlpOffW2 = 896, kMlpOffB2 = 4992, kMlpOffW3 = 5056,
               kMlpOffB3 = 5184, kMlpOffIn = 5186, kMlpOffOut = 5199, kMlpParams = 5201, kMlpNet = 5186;
 
+// Row stride of W2 and W3 in the packed copy: 72 BF16 = 144 B, so the eight
+// rows g = 0..7 that one B-fragment load touches start in eight different
+// 4-bank groups (a 128 B stride would put all eight on the same banks).
+constexpr int kLdW = 72;
+
 // Packed device copy used by the kernels (16-byte aligned, size a multiple of
 // 16 so that it can be staged into shared memory with 16-byte copies).
 struct __align__(16) MlpPacked {
   __nv_bfloat16 W1[kMlpH * kMlpInPad];   // [64][16], k >= 13 zero
-  __nv_bfloat16 W2[kMlpH * kMlpH];       // [64][64]
-  __nv_bfloat16 W3[kMlpOutPad * kMlpH];  // [8][64], n >= 2 zero
+  __nv_bfloat16 W2[kMlpH * kLdW];        // [64][72], k >= 64 zero
+  __nv_bfloat16 W3[kMlpOutPad * kLdW];   // [8][72], n >= 2 or k >= 64 zero
   float b1[kMlpH], b2[kMlpH], b3[kMlpOutPad];
   float in_scale[kMlpInPad], out_scale[2];
 };
@@ -98,8 +103,8 @@ __device__ __forceinline__ void mlp_warp_forward(const MlpPacked &W, const __nv_
       d[1] = d[3] = W.b2[8 * nt + 2 * c + 1];
 #pragma unroll
       for (int kt = 0; kt < 4; ++kt)
-        mma_bf16_16816(d, h1[kt], ld_u32(W.W2 + (8 * nt + g) * kMlpH + 16 * kt + 2 * c),
-                       ld_u32(W.W2 + (8 * nt + g) * kMlpH + 16 * kt + 2 * c + 8));
+        mma_bf16_16816(d, h1[kt], ld_u32(W.W2 + (8 * nt + g) * kLdW + 16 * kt + 2 * c),
+                       ld_u32(W.W2 + (8 * nt + g) * kLdW + 16 * kt + 2 * c + 8));
       if (A2) {
         A2[(rb + g) * lda + 8 * nt + 2 * c] = d[0];
         A2[(rb + g) * lda + 8 * nt + 2 * c + 1] = d[1];
@@ -111,8 +116,8 @@ __device__ __forceinline__ void mlp_warp_forward(const MlpPacked &W, const __nv_
       h2[1 + 2 * hi] = pack_bf16(silu(d[2]), silu(d[3]));
       if (hi) {  // a full k-tile of layer 3 is ready
         const int kt = nt >> 1;
-        mma_bf16_16816(y, h2, ld_u32(W.W3 + g * kMlpH + 16 * kt + 2 * c),
-                       ld_u32(W.W3 + g * kMlpH + 16 * kt + 2 * c + 8));
+        mma_bf16_16816(y, h2, ld_u32(W.W3 + g * kLdW + 16 * kt + 2 * c),
+                       ld_u32(W.W3 + g * kLdW + 16 * kt + 2 * c + 8));
       }
     }
     if (c == 0) {
