@@ -23,7 +23,7 @@ namespace cmles {
 void pack_mlp_host(const float *p, MlpPacked *o) {
   memset(o, 0, sizeof(*o));
   for (int n = 0; n < kMlpH; ++n)
-    for (int k = 0; k < kMlpIn; ++k) o->W1[n * kMlpInPad + k] = __float2bfloat16_rn(p[kMlpOffW1 + n * kMlpIn + k]);
+    for (int k = 0; k < kMlpIn; ++k) o->W1[n * kLdW1 + k] = __float2bfloat16_rn(p[kMlpOffW1 + n * kMlpIn + k]);
   for (int n = 0; n < kMlpH; ++n)
     for (int k = 0; k < kMlpH; ++k) o->W2[n * kLdW + k] = __float2bfloat16_rn(p[kMlpOffW2 + n * kMlpH + k]);
   for (int n = 0; n < kMlpOut; ++n)
@@ -41,8 +41,8 @@ void pack_mlp_host(const float *p, MlpPacked *o) {
 
 __global__ void k_pack_mlp(const float *__restrict__ p, MlpPacked *__restrict__ o) {
   const int t = threadIdx.x + blockIdx.x * blockDim.x, nt = blockDim.x * gridDim.x;
-  for (int q = t; q < kMlpH * kMlpInPad; q += nt) {
-    const int n = q / kMlpInPad, k = q % kMlpInPad;
+  for (int q = t; q < kMlpH * kLdW1; q += nt) {
+    const int n = q / kLdW1, k = q % kLdW1;
     o->W1[q] = __float2bfloat16_rn(k < kMlpIn ? p[kMlpOffW1 + n * kMlpIn + k] : 0.f);
   }
   for (int q = t; q < kMlpH * kLdW; q += nt) {

@@ -26,11 +26,14 @@ constexpr int kMlpOffW1 = 0, kMlpOffB1 = 832, kMlpOffW2 = 896, kMlpOffB2 = 4992,
 // rows g = 0..7 that one B-fragment load touches start in eight different
 // 4-bank groups (a 128 B stride would put all eight on the same banks).
 constexpr int kLdW = 72;
+// Row stride of W1: 24 BF16 = 48 B, so that eight consecutive rows fall in
+// eight different 16-byte bank groups for ldmatrix (32 B would pair them).
+constexpr int kLdW1 = 24;
 
 // Packed device copy used by the kernels (16-byte aligned, size a multiple of
 // 16 so that it can be staged into shared memory with 16-byte copies).
 struct __align__(16) MlpPacked {
-  __nv_bfloat16 W1[kMlpH * kMlpInPad];   // [64][16], k >= 13 zero
+  __nv_bfloat16 W1[kMlpH * kLdW1];       // [64][24], k >= 13 zero
   __nv_bfloat16 W2[kMlpH * kLdW];        // [64][72], k >= 64 zero
   __nv_bfloat16 W3[kMlpOutPad * kLdW];   // [8][72], n >= 2 or k >= 64 zero
   float b1[kMlpH], b2[kMlpH], b3[kMlpOutPad];
@@ -57,6 +60,21 @@ __device__ __forceinline__ float silu(float x) { return __fdividef(x, 1.0f + __e
 
 __device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
+// ldmatrix: four (x4) or two (x2) 8x8 BF16 tiles from shared memory; lane l
+// gives the address of row l % 8 of tile l / 8 (16-byte aligned), and
+// register m of lane (g, c) receives elements 2c, 2c + 1 of row g of tile m,
+// which for a weight tile stored [n][k] is the B fragment of mma m16n8k16.
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const __nv_bfloat16 *p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t r[2], const __nv_bfloat16 *p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+
 // Forward pass of the 32 rows [r0, r0 + 32) of X (bf16 [rows][16], shared
 // memory) by one warp; writes Y[row][0..1] (FP32, shared memory).
 // Optionally stores the pre-activations of both hidden layers (FP32,
@@ -74,13 +92,16 @@ __device__ __forceinline__ void mlp_warp_forward(const MlpPacked &W, const __nv_
     a[3] = ld_u32(X + (rb + g + 8) * kMlpInPad + 2 * c + 8);
     // layer 1: 8 n-tiles, one k-tile; outputs repacked as 4 k-tiles of layer 2
     uint32_t h1[4][4];
+    // ldmatrix row address of this lane: tile lane / 8, row lane % 8
+    const int lr = lane & 7, lt = lane >> 3;
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       float d[4];
       d[0] = d[2] = W.b1[8 * nt + 2 * c];
       d[1] = d[3] = W.b1[8 * nt + 2 * c + 1];
-      mma_bf16_16816(d, a, ld_u32(W.W1 + (8 * nt + g) * kMlpInPad + 2 * c),
-                     ld_u32(W.W1 + (8 * nt + g) * kMlpInPad + 2 * c + 8));
+      uint32_t b[2];
+      ldsm_x2(b, W.W1 + (8 * nt + lr) * kLdW1 + 8 * (lt & 1));
+      mma_bf16_16816(d, a, b[0], b[1]);
       if (A1) {
         A1[(rb + g) * lda + 8 * nt + 2 * c] = d[0];
         A1[(rb + g) * lda + 8 * nt + 2 * c + 1] = d[1];
@@ -102,9 +123,13 @@ __device__ __forceinline__ void mlp_warp_forward(const MlpPacked &W, const __nv_
       d[0] = d[2] = W.b2[8 * nt + 2 * c];
       d[1] = d[3] = W.b2[8 * nt + 2 * c + 1];
 #pragma unroll
-      for (int kt = 0; kt < 4; ++kt)
-        mma_bf16_16816(d, h1[kt], ld_u32(W.W2 + (8 * nt + g) * kLdW + 16 * kt + 2 * c),
-                       ld_u32(W.W2 + (8 * nt + g) * kLdW + 16 * kt + 2 * c + 8));
+      for (int kp = 0; kp < 2; ++kp) {
+        // tiles: (k-tile 2kp, low 8), (2kp, high 8), (2kp+1, low), (2kp+1, high)
+        uint32_t b[4];
+        ldsm_x4(b, W.W2 + (8 * nt + lr) * kLdW + 32 * kp + 8 * lt);
+        mma_bf16_16816(d, h1[2 * kp], b[0], b[1]);
+        mma_bf16_16816(d, h1[2 * kp + 1], b[2], b[3]);
+      }
       if (A2) {
         A2[(rb + g) * lda + 8 * nt + 2 * c] = d[0];
         A2[(rb + g) * lda + 8 * nt + 2 * c + 1] = d[1];
@@ -116,8 +141,9 @@ __device__ __forceinline__ void mlp_warp_forward(const MlpPacked &W, const __nv_
       h2[1 + 2 * hi] = pack_bf16(silu(d[2]), silu(d[3]));
       if (hi) {  // a full k-tile of layer 3 is ready
         const int kt = nt >> 1;
-        mma_bf16_16816(y, h2, ld_u32(W.W3 + g * kLdW + 16 * kt + 2 * c),
-                       ld_u32(W.W3 + g * kLdW + 16 * kt + 2 * c + 8));
+        uint32_t b[2];
+        ldsm_x2(b, W.W3 + lr * kLdW + 16 * kt + 8 * (lt & 1));
+        mma_bf16_16816(y, h2, b[0], b[1]);
       }
     }
     if (c == 0) {
