@@ -258,6 +258,8 @@ void fill_kparams(cmles_handle h) {
   F.pv_Ttr = (float)K.pv_Ttr;
   F.pv_a = (float)K.pv_a;
   F.pv_b = (float)K.pv_b;
+  F.inv_Ttr = (float)(1.0 / K.pv_Ttr);
+  F.inv_Rv = (float)(1.0 / p.Rv);
   F.dcp = (float)K.dcp;
   F.CsDelta2 = (float)K.CsDelta2;
   F.Delta = (float)Delta;

@@ -18,6 +18,7 @@ constexpr int kMaxQ = 8;
 // FP32 copies of the constants used by the FP32 kernels.
 struct KF {
   float g, Rd, Rv, cvd, cvv, cvl, T0, Lv0, Iv0, kappa, pv_ptr, pv_Ttr, pv_a, pv_b, dcp;
+  float inv_Ttr, inv_Rv;  // 1 / T_tr, 1 / R_v
   float CsDelta2, inv_Prt, Delta;
   float vr_c, vr_d2[3];
   float jac[3], lift[3];

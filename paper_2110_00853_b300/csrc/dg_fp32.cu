@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
           nut = vreman_nu<float>(gr, F.vr_c, F.vr_d2);
         if (P.richardson && Smag2 > 0.0f) {
           const float thv = L[L_THV] + G[5];
-          const float Ri = F.g / thv * gr[5][2] / Smag2;
+          const float Ri = fdiv(F.g * gr[5][2], thv * Smag2);
           if (Ri > 0.0f) {
             const float a = 1.0f - Ri * F.inv_Prt;
             nut *= a > 0.0f ? sqrtf(sqrtf(a)) : 0.0f;
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(128, 8) k_rhs32(const float *__restrict__ S, c
         sF[3][d][t] = f[3] + g2[3 * kNP];
         sF[4][d][t] = f[4] + g2[4 * kNP];
         sF[5][d][t] = f[5] + c0;
-        sU[d][t] = sv[1 + d] / rho;
+        sU[d][t] = fdiv(sv[1 + d], rho);
       }
     }
     __syncthreads();
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(128, 8) k_rhs32(const float *__restrict__ S, c
       float fm[6], fp[6];
       flux1_dev32(sm, rho_r, rhoq_r, pm, d, fm);
       flux1_dev32(sp, rho_r, rhoq_r, pp, d, fp);
-      const float um = sm[1 + d] / (rho_r + sm[0]), up = sp[1 + d] / (rho_r + sp[0]);
+      const float um = fdiv(sm[1 + d], rho_r + sm[0]), up = fdiv(sp[1 + d], rho_r + sp[0]);
       const float lam = fmaxf(fabsf(um) + cm, fabsf(up) + cp);
       const int c_of_v[6] = {0, 1, 2, 3, 4, 0};
 #pragma unroll

@@ -12,10 +12,16 @@ struct Th32 {
   float rho, u[3], qp, Tp, pp, c, hp, thvp;
 };
 
+// Divisions in the FP32 path use the approximate quotient (2 ulp), far below
+// the FP32 rounding of the deviations they combine.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+
 // p_v*(T) of the integrated Clausius-Clapeyron relation, FP32.
 __device__ __forceinline__ float pvsat32(const KF &F, float T) {
-  return F.pv_ptr * expf(F.pv_a * logf(T / F.pv_Ttr) + F.pv_b * (1.0f / F.pv_Ttr - 1.0f / T));
+  return F.pv_ptr * expf(F.pv_a * logf(T * F.inv_Ttr) + F.pv_b * (F.inv_Ttr - fdiv(1.0f, T)));
 }
+// saturation vapour density p_v*(T) / (R_v T)
+__device__ __forceinline__ float rhovsat32(const KF &F, float T) { return fdiv(pvsat32(F, T) * F.inv_Rv, T); }
 
 // Thermodynamics of one node from its deviation state s and its level table L.
 template <bool MOIST>
@@ -25,7 +31,7 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
   const float rho_r = L[L_RHO], rhoq_r = L[L_RHOQ], Tr = L[L_T], TrT0 = L[L_T_T0];
   const float rp = s[0], qp = s[5];
   const float rho = rho_r + rp;
-  const float rinv = 1.0f / rho;
+  const float rinv = fdiv(1.0f, rho);
   o.rho = rho;
   o.u[0] = s[1] * rinv;
   o.u[1] = s[2] * rinv;
@@ -38,23 +44,24 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
   // drqv = rho q_v - rho q_r is carried as a deviation (never formed as the
   // difference of two near-equal FP32 numbers)
   float rhoqv = rhoq, rhoql = 0.0f, drqv = qp;
-  float Tp = (dRI - qp * F.Iv0 - (rp * F.cvd + qp * (F.cvv - F.cvd)) * TrT0) /
-             (rho * F.cvd + rhoq * (F.cvv - F.cvd));
+  float Tp = fdiv(dRI - qp * F.Iv0 - (rp * F.cvd + qp * (F.cvv - F.cvd)) * TrT0,
+                  rho * F.cvd + rhoq * (F.cvv - F.cvd));
   if (MOIST) {
     float T = Tr + Tp;
-    if (rhoq > pvsat32(F, T) / (F.Rv * T)) {
+    if (rhoq > rhovsat32(F, T)) {
       bool conv = false;
       for (int it = 0; it < P.satadj_max_iter; ++it) {
         T = Tr + Tp;
-        const float rqs = pvsat32(F, T) / (F.Rv * T);
+        const float rqs = rhovsat32(F, T);
         const float rql = rhoq - rqs;
         const float rcvm = (rho - rhoq) * F.cvd + rqs * F.cvv + rql * F.cvl;
         const float drcvm = (rp - qp) * F.cvd + (rqs - rhoq_r) * F.cvv + rql * F.cvl;
         const float rf = rcvm * Tp + drcvm * TrT0 + (rqs - rhoq_r) * F.Iv0 - dRI;
         const float Lh = F.Lv0 + F.dcp * (T - F.T0);
-        const float drqs = rqs * (Lh / (F.Rv * T * T) - 1.0f / T);
+        const float iT = fdiv(1.0f, T);
+        const float drqs = rqs * iT * (Lh * F.inv_Rv * iT - 1.0f);
         const float rfp = rcvm + drqs * ((F.cvv - F.cvl) * (T - F.T0) + F.Iv0);
-        const float dT = rf / rfp;
+        const float dT = fdiv(rf, rfp);
         Tp -= dT;
         if (fabsf(dT) <= 5e-5f) {
           conv = true;
@@ -63,7 +70,7 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
       }
       if (!conv) fail = 1;
       T = Tr + Tp;
-      rhoqv = pvsat32(F, T) / (F.Rv * T);
+      rhoqv = rhovsat32(F, T);
       rhoql = rhoq - rhoqv;
       drqv = rhoqv - rhoq_r;
       if (rhoql < 0.0f) {
@@ -80,9 +87,14 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
   o.pp = pp;
   const float rcvm = (rho - rhoq) * F.cvd + rhoqv * F.cvv + rhoql * F.cvl;
   const float pr = L[L_P];
-  o.c = sqrtf((rcvm + rRm) / rcvm * (pr + pp) * rinv);
+  o.c = sqrtf(fdiv(rcvm + rRm, rcvm) * (pr + pp) * rinv);
   o.hp = (s[4] + pp - L[L_HM] * rp) * rinv;  // h_tot - h_r
-  const float lnr = log1pf(Tp / Tr) - F.kappa * log1pf(pp / pr) + log1pf(drRm / L[L_RHORM]) - log1pf(rp / rho_r);
+  // ln(theta_v / theta_v,r) = ln(T/T_r) + ln(rho R_m / (rho R_m)_r) - ln(rho/rho_r)
+  // - kappa ln(p/p_r); the first three factors combined exactly,
+  // (1+a)(1+b)/(1+c) - 1 = (a + b + ab - c)/(1 + c), so that one log1p
+  // takes all three small ratios
+  const float ra = fdiv(Tp, Tr), rb = fdiv(drRm, L[L_RHORM]), rc = fdiv(rp, rho_r);
+  const float lnr = log1pf(fdiv(ra + rb + ra * rb - rc, 1.0f + rc)) - F.kappa * log1pf(fdiv(pp, pr));
   o.thvp = L[L_THV] * expm1f(lnr);  // theta_v - theta_v,r
 }
 
@@ -91,7 +103,7 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
 // The reference part H_r u_d of the energy flux is handled separately.
 __device__ __forceinline__ void flux1_dev32(const float s[6], float rho_r, float rhoq_r, float pp, int d,
                                            float f[6]) {
-  const float ud = s[1 + d] / (rho_r + s[0]);
+  const float ud = fdiv(s[1 + d], rho_r + s[0]);
   f[0] = s[1 + d];
   f[1] = s[1] * ud + (d == 0 ? pp : 0.f);
   f[2] = s[2] * ud + (d == 1 ? pp : 0.f);
