@@ -437,6 +437,13 @@ cmles_status build_curved(cmles_handle h) {
 // path per node, the full reference gradients of h_r, q_r, theta_v,r (the
 // DG gradient operator applied to the nodal reference values), Delta,
 // (C_s Delta)^2 and the sponge coefficient.
+// saturation vapour density p_v*(T) / (R_v T) in FP64 (integrated
+// Clausius-Clapeyron relation with the constants of the handle)
+static double rhovsat64(cmles_handle h, double T) {
+  const KParams &K = h->K;
+  return K.pv_ptr * exp(K.pv_a * log(T / K.pv_Ttr) + K.pv_b * (1.0 / K.pv_Ttr - 1.0 / T)) / (h->prm.Rv * T);
+}
+
 cmles_status curved_reference(cmles_handle h, const double *rho_r, const double *p_r, const double *qt_r) {
   const cmles_params &p = h->prm;
   const cmles_mesh &m = h->mesh;
@@ -486,6 +493,7 @@ cmles_status curved_reference(cmles_handle h, const double *rho_r, const double 
       T[L_RHORM * 128] = (float)(rho_r[g] * Rm);
       T[L_TAU * 128] = (float)tau;
       T[L_QM * 128] = (float)q;
+      T[L_RVS * 128] = (float)rhovsat64(h, Tr);
       const double delta = h->hdelta_[e];
       T[(NF - 2) * 128] = (float)delta;
       T[(NF - 1) * 128] = (float)((p.Cs * delta) * (p.Cs * delta));
@@ -780,6 +788,7 @@ cmles_status cmles_set_reference(cmles_handle h, const double *rho_r, const doub
     L[L_RHORM] = (float)(rho_r[l] * Rm);
     L[L_TAU] = (float)tau[l];
     L[L_QM] = (float)q;
+    L[L_RVS] = (float)rhovsat64(h, Tr);
   }
   const int Nq = h->Nq;
   for (int ez = 0; ez < h->mesh.nez; ++ez)

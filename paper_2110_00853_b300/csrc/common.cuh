@@ -29,6 +29,7 @@ struct KF {
 // Per-level FP32 table of the FP32 path (16 floats per node level).
 enum {
   L_RHO = 0, L_RHOQ, L_T, L_T_T0, L_GZ, L_P, L_H, L_HM, L_THV, L_DZ_HM, L_DZ_THV, L_RHORM, L_TAU, L_QM, L_DZ_Q,
+  L_RVS,  // saturation vapour density p_v*(T_r) / (R_v T_r)
   L_NF = 16
 };
 

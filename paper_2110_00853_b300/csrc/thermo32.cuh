@@ -48,7 +48,15 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
                   rho * F.cvd + rhoq * (F.cvv - F.cvd));
   if (MOIST) {
     float T = Tr + Tp;
-    if (rhoq > rhovsat32(F, T)) {
+    // Certainly unsaturated without evaluating p_v*: rho_vs(T) is convex in
+    // T on [150, 450] K, so its tangent at T_r bounds it from below there,
+    // rho_vs(T) >= rho_vs(T_r) (1 + T' d ln rho_vs/dT(T_r)); the factor
+    // 1 - 1e-5 keeps the shortcut clear of the exact test's rounding.
+    const float iTr = fdiv(1.0f, Tr);
+    const float slope = (F.pv_a - 1.0f + F.pv_b * iTr) * iTr;
+    const bool dry = T >= 150.0f && T <= 450.0f && Tr >= 150.0f && Tr <= 450.0f &&
+                     rhoq <= 0.99999f * L[L_RVS] * (1.0f + slope * Tp);
+    if (!dry && rhoq > rhovsat32(F, T)) {
       bool conv = false;
       for (int it = 0; it < P.satadj_max_iter; ++it) {
         T = Tr + Tp;
@@ -89,13 +97,14 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
   const float pr = L[L_P];
   o.c = sqrtf(fdiv(rcvm + rRm, rcvm) * (pr + pp) * rinv);
   o.hp = (s[4] + pp - L[L_HM] * rp) * rinv;  // h_tot - h_r
-  // ln(theta_v / theta_v,r) = ln(T/T_r) + ln(rho R_m / (rho R_m)_r) - ln(rho/rho_r)
-  // - kappa ln(p/p_r); the first three factors combined exactly,
-  // (1+a)(1+b)/(1+c) - 1 = (a + b + ab - c)/(1 + c), so that one log1p
-  // takes all three small ratios
+  // theta_v / theta_v,r = (T/T_r)(R_m/R_m,r)(p/p_r)^-kappa with
+  // (T/T_r)(R_m/R_m,r) = (1 + a)(1 + b)/(1 + c) = 1 + (a + b + ab - c)/(1 + c),
+  // a = T'/T_r, b = (rho R_m)'/(rho R_m)_r, c = rho'/rho_r (exact algebra)
   const float ra = fdiv(Tp, Tr), rb = fdiv(drRm, L[L_RHORM]), rc = fdiv(rp, rho_r);
-  const float lnr = log1pf(fdiv(ra + rb + ra * rb - rc, 1.0f + rc)) - F.kappa * log1pf(fdiv(pp, pr));
-  o.thvp = L[L_THV] * expm1f(lnr);  // theta_v - theta_v,r
+  // theta_v / theta_v,r = (1 + u)(1 + w), w = (p/p_r)^-kappa - 1
+  const float u = fdiv(ra + rb + ra * rb - rc, 1.0f + rc);
+  const float w = expm1f(-F.kappa * log1pf(fdiv(pp, pr)));
+  o.thvp = L[L_THV] * (u + w + u * w);  // theta_v - theta_v,r
 }
 
 // Deviation part of n.F1 along d (sign by the caller):
