@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
 }
 
 template <int N, bool UPDATE>
-__global__ void __launch_bounds__(128, 8) k_rhs32(const float *__restrict__ S, const float *__restrict__ F2,
+__global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, const float *__restrict__ F2,
                                                   const float *__restrict__ aux, float *__restrict__ dQ,
                                                   double *__restrict__ Q64, float *__restrict__ Sout,
                                                   double *__restrict__ Rout, const StageCoef sc, const KParams P) {
@@ -229,6 +229,17 @@ __global__ void __launch_bounds__(128, 8) k_rhs32(const float *__restrict__ S, c
     if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
     const float *L = P.lev32 + (size_t)(ez * Nq + (k < Nq ? k : 0)) * L_NF;
     float sv[6];
+    // the update's inputs, loaded with the element's first loads so that
+    // their latency overlaps the flux computation
+    float dq0[6];
+    double q0[6];
+    if (UPDATE && t < Np) {
+#pragma unroll
+      for (int v = 0; v < 6; ++v) {
+        dq0[v] = sc.A != 0.0 ? dQ[((size_t)e * 6 + v) * kNP + t] : 0.f;
+        q0[v] = Q64[((size_t)e * 6 + v) * Np + t];
+      }
+    }
     if (t < Np) {
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
@@ -361,9 +372,9 @@ __global__ void __launch_bounds__(128, 8) k_rhs32(const float *__restrict__ S, c
         const size_t i64 = ((size_t)e * 6 + v) * Np + t;
         if (UPDATE) {
           const size_t i32 = ((size_t)e * 6 + v) * kNP + t;
-          const float dq = (sc.A != 0.0 ? (float)sc.A * dQ[i32] : 0.f) + (float)sc.dt * R[v];
+          const float dq = (float)sc.A * dq0[v] + (float)sc.dt * R[v];
           dQ[i32] = dq;
-          const double qn = Q64[i64] + sc.B * (double)dq;
+          const double qn = q0[v] + sc.B * (double)dq;
           Q64[i64] = qn;
           const double ref = v == 0 ? qr[0] : (v == 4 ? qr[1] : (v == 5 ? qr[2] : 0.0));
           Sout[i32] = (float)(qn - ref);
