@@ -514,7 +514,10 @@ int orc_rhs(orc_solver *s, const double *Q, double *RHS, int form) {
               f2s[4] = -(P->shf + P->lhf) * (-nrm[2]);
             }
           }
-          orc_rusanov(P, Ym, Yp, s->z[q], s->p_r[q], nrm, F1s);
+          if (P->flux == ORC_FLUX_HLLC)
+            orc_hllc(P, Ym, Yp, s->z[q], s->p_r[q], nrm, F1s);
+          else
+            orc_rusanov(P, Ym, Yp, s->z[q], s->p_r[q], nrm, F1s);
           F2s[0] = f2s[0];
           F2s[1] = f2s[1];
           F2s[2] = f2s[2];

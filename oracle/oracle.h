@@ -32,6 +32,8 @@
 #define ORC_CLOSURE_SL 1
 #define ORC_CLOSURE_MLP 2
 #define ORC_CLOSURE_VREMAN 3
+#define ORC_FLUX_RUSANOV 0
+#define ORC_FLUX_HLLC 1
 
 typedef struct {
   int N;                      /* polynomial order */
@@ -59,6 +61,7 @@ typedef struct {
   int surface_flux;
   double shf, lhf;
   double Omega[3];            /* planetary rotation for the Coriolis term */
+  int flux;                   /* ORC_FLUX_*: numerical flux of F1 on faces (Sec. 3.1) */
 } orc_params;
 
 typedef struct orc_solver orc_solver;
@@ -89,6 +92,11 @@ void orc_flux1_normal(const orc_params *p, const double Y[6], double z, double p
 /* Rusanov numerical flux n.F1* (Eq. nonviscFlux, standard 1/2 lambda reading). */
 void orc_rusanov(const orc_params *p, const double Ym[6], const double Yp[6], double z, double pr,
                  const double n[3], double out[6]);
+
+/* HLLC numerical flux n.F1* (Toro, Spruce & Speares 1994; named in Sec. 3.1),
+ * Davis wave-speed estimates (reading). */
+void orc_hllc(const orc_params *p, const double Ym[6], const double Yp[6], double z, double pr, const double n[3],
+              double out[6]);
 
 /* ---- closure (Sec. 4) ---- */
 /* Smagorinsky-Lilly nu_t from the velocity gradient gu[i][j] = du_i/dx_j,

@@ -40,7 +40,8 @@ class Params(C.Structure):
         ("closure", C.c_int), ("Cs", C.c_double), ("Prt", C.c_double), ("richardson", C.c_int),
         ("moist", C.c_int), ("sponge_alpha", C.c_double), ("sponge_zs", C.c_double),
         ("sponge_gamma", C.c_double), ("u_relax", C.c_double * 3), ("lateral_sponge_frac", C.c_double),
-        ("surface_flux", C.c_int), ("shf", C.c_double), ("lhf", C.c_double), ("Omega", C.c_double * 3)]
+        ("surface_flux", C.c_int), ("shf", C.c_double), ("lhf", C.c_double), ("Omega", C.c_double * 3),
+        ("flux", C.c_int)]
 
 
 class Case(C.Structure):
@@ -56,6 +57,7 @@ class Case(C.Structure):
 
 
 CLOSURE = {"none": 0, "sl": 1, "mlp": 2, "vreman": 3}
+FLUX = {"rusanov": 0, "hllc": 1}
 
 # Table t:constants; g, p0, p_tr, T_tr are readings (the table omits them).
 CONSTANTS = dict(g=9.81, p0=1.0e5, Rd=287.0, Rv=462.0, cvd=717.5, cvv=1397.5, cvl=4181.0, cvi=2100.0,
@@ -78,6 +80,8 @@ def _declare(L):
     L.orc_rusanov.argtypes = [C.POINTER(Params), _DP, _DP, C.c_double, C.c_double, _DP, _DP]
     L.orc_smagorinsky.argtypes = [C.POINTER(Params), _DP, C.c_double, C.c_double, C.c_double]
     L.orc_smagorinsky.restype = C.c_double
+    L.orc_hllc.argtypes = [C.POINTER(Params), _DP, _DP, C.c_double, C.c_double, _DP, _DP]
+    L.orc_hllc.restype = None
     L.orc_vreman.argtypes = [C.POINTER(Params), _DP, C.c_double, C.c_double, _DP]
     L.orc_vreman.restype = C.c_double
     L.orc_create.argtypes = [C.POINTER(Mesh), C.POINTER(Params)]
@@ -119,7 +123,7 @@ def _p(a):
 
 def make_params(closure="sl", moist=False, Cs=0.21, Prt=1.0 / 3.0, richardson=True, sponge_alpha=0.0,
                 sponge_zs=0.0, sponge_gamma=2.0, u_relax=(0.0, 0.0, 0.0), lateral_sponge_frac=0.0,
-                surface_flux=False, shf=0.0, lhf=0.0, Omega=(0.0, 0.0, 0.0), **const):
+                surface_flux=False, shf=0.0, lhf=0.0, Omega=(0.0, 0.0, 0.0), flux="rusanov", **const):
     c = dict(CONSTANTS)
     c.update(const)
     P = Params(**c)
@@ -130,6 +134,7 @@ def make_params(closure="sl", moist=False, Cs=0.21, Prt=1.0 / 3.0, richardson=Tr
     P.lateral_sponge_frac = lateral_sponge_frac
     P.surface_flux, P.shf, P.lhf = int(surface_flux), shf, lhf
     P.Omega = (C.c_double * 3)(*Omega)
+    P.flux = FLUX[flux]
     return P
 
 
@@ -196,6 +201,13 @@ def rusanov(P, Ym, Yp, z, pr, n):
     out = np.zeros(6)
     lib().orc_rusanov(C.byref(P), _p(np.ascontiguousarray(Ym, float)), _p(np.ascontiguousarray(Yp, float)),
                       z, pr, _p(np.ascontiguousarray(n, float)), _p(out))
+    return out
+
+
+def hllc(P, Ym, Yp, z, pr, n):
+    out = np.zeros(6)
+    lib().orc_hllc(C.byref(P), _p(np.ascontiguousarray(Ym, float)), _p(np.ascontiguousarray(Yp, float)),
+                   z, pr, _p(np.ascontiguousarray(n, float)), _p(out))
     return out
 
 

@@ -139,12 +139,57 @@ void orc_rusanov(const orc_params *p, const double Ym[6], const double Yp[6], do
   for (int v = 0; v < 6; ++v) out[v] = 0.5 * (fm[v] + fp[v]) + 0.5 * lam * (Ym[v] - Yp[v]);
 }
 
-/* Smagorinsky-Lilly eddy viscosity nu_t = (C_s Delta)^2 |S| f_b with
- * S = sym(grad u) (Eq. strain_rate), |S| = sqrt(2 S_ij S_ij) (Eq. smago) and
- * f_b the Richardson correction (Eq. richardson):
- *   Ri = (g/theta_v d theta_v/dz) / |S|^2,
- *   f_b = 1 for Ri <= 0, max(0, 1 - Ri/Pr_t)^{1/4} otherwise.
- * Reading: nu_t = 0 when |S| = 0. */
+/* HLLC flux (Toro, Spruce & Speares 1994), in the frame of the face normal n
+ * (u = u.n): with the Davis estimates S_L = min(u_L - c_L, u_R - c_R),
+ * S_R = max(u_L + c_L, u_R + c_R) (reading: the paper names the flux, not its
+ * wave speeds), the contact speed
+ *   S* = [p_R - p_L + rho_L u_L (S_L - u_L) - rho_R u_R (S_R - u_R)]
+ *        / [rho_L (S_L - u_L) - rho_R (S_R - u_R)],
+ * and for side K the star state
+ *   U*_K = rho_K (S_K - u_K)/(S_K - S*) [1, S* n + u_t,K,
+ *          E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K))), q_t,K],
+ * the flux is F_L for S_L >= 0, F_L + S_L (U*_L - U_L) for S_L < 0 <= S*,
+ * F_R + S_R (U*_R - U_R) for S* < 0 < S_R and F_R for S_R <= 0.  E = rho e_tot
+ * (with rho g z, carried by the energy flux (E + p) u) and p the full
+ * pressure; F1's momentum flux holds p - p_r, a shift common to both sides
+ * that leaves the jump conditions unchanged.  Y- is the left state. */
+void orc_hllc(const orc_params *p, const double Ym[6], const double Yp[6], double z, double pr, const double n[3],
+              double out[6]) {
+  orc_thermo_state sL, sR;
+  orc_thermo(p, Ym, z, &sL);
+  orc_thermo(p, Yp, z, &sR);
+  double uL = sL.u[0] * n[0] + sL.u[1] * n[1] + sL.u[2] * n[2];
+  double uR = sR.u[0] * n[0] + sR.u[1] * n[1] + sR.u[2] * n[2];
+  double SL = fmin(uL - sL.c, uR - sR.c), SR = fmax(uL + sL.c, uR + sR.c);
+  double Ss = (sR.p - sL.p + sL.rho * uL * (SL - uL) - sR.rho * uR * (SR - uR)) /
+              (sL.rho * (SL - uL) - sR.rho * (SR - uR));
+  double fL[6], fR[6];
+  orc_flux1_normal(p, Ym, z, pr, n, fL);
+  orc_flux1_normal(p, Yp, z, pr, n, fR);
+  if (SL >= 0.0) {
+    for (int v = 0; v < 6; ++v) out[v] = fL[v];
+    return;
+  }
+  if (SR <= 0.0) {
+    for (int v = 0; v < 6; ++v) out[v] = fR[v];
+    return;
+  }
+  const int left = Ss >= 0.0;
+  const orc_thermo_state *s = left ? &sL : &sR;
+  const double *Y = left ? Ym : Yp, *f = left ? fL : fR;
+  double S = left ? SL : SR, u = left ? uL : uR;
+  double chi = (S - u) / (S - Ss);
+  double Us[6];
+  Us[0] = s->rho * chi;
+  for (int c = 0; c < 3; ++c) {
+    double ut = s->u[c] - u * n[c];
+    Us[1 + c] = s->rho * chi * (Ss * n[c] + ut);
+  }
+  Us[4] = s->rho * chi * (Y[4] / s->rho + (Ss - u) * (Ss + s->p / (s->rho * (S - u))));
+  Us[5] = s->rho * chi * (Y[5] / s->rho);
+  for (int v = 0; v < 6; ++v) out[v] = f[v] + S * (Us[v] - Y[v]);
+}
+
 /* Richardson factor f_b (Eq. richardson) for |S|^2 = 2 S:S > 0. */
 static double richardson_factor(const orc_params *p, double dthvdz, double thv, double Smag2) {
   double N2 = p->g / thv * dthvdz;
@@ -154,6 +199,10 @@ static double richardson_factor(const orc_params *p, double dthvdz, double thv, 
   return a > 0.0 ? pow(a, 0.25) : 0.0;
 }
 
+/* Vreman eddy viscosity (Eq. vreman-sgs): beta_ij = sum_m Delta_m^2 u_i,m u_j,m,
+ * B_beta = beta11 beta22 + beta11 beta33 + beta22 beta33 - beta13^2 - beta12^2
+ * - beta23^2, nu_t = 2.5 C_s^2 sqrt(B_beta / (u_i,j u_i,j)); zero when the
+ * gradient vanishes or B_beta <= 0.  Times f_b when the correction is on. */
 double orc_vreman(const orc_params *p, const double gu[9], double dthvdz, double thv, const double Dm[3]) {
   /* beta_ij = sum_m Delta_m^2 u_i,m u_j,m */
   double beta[3][3];
@@ -181,6 +230,12 @@ double orc_vreman(const orc_params *p, const double gu[9], double dthvdz, double
   return nut;
 }
 
+/* Smagorinsky-Lilly eddy viscosity nu_t = (C_s Delta)^2 |S| f_b with
+ * S = sym(grad u) (Eq. strain_rate), |S| = sqrt(2 S_ij S_ij) (Eq. smago) and
+ * f_b the Richardson correction (Eq. richardson):
+ *   Ri = (g/theta_v d theta_v/dz) / |S|^2,
+ *   f_b = 1 for Ri <= 0, max(0, 1 - Ri/Pr_t)^{1/4} otherwise.
+ * Reading: nu_t = 0 when |S| = 0. */
 double orc_smagorinsky(const orc_params *p, const double gu[9], double dthvdz, double thv, double Delta) {
   double S2 = 0.0;
   for (int i = 0; i < 3; ++i)

@@ -60,7 +60,7 @@ def physics(name, closure="sl", moist=None):
     description: each side carries the paper's Table t:constants itself."""
     p = dict(closure=closure, Cs=0.21, Prt=1.0 / 3.0, richardson=True, moist=False, sponge_alpha=0.0,
              sponge_zs=0.0, sponge_gamma=2.0, u_relax=(0.0, 0.0, 0.0), lateral_sponge_frac=0.0,
-             surface_flux=False, shf=0.0, lhf=0.0, Omega=(0.0, 0.0, 0.0), dt=0.02)
+             surface_flux=False, shf=0.0, lhf=0.0, Omega=(0.0, 0.0, 0.0), dt=0.02, flux="rusanov")
     if name == "c1":
         pass
     elif name in ("c2", "c4fine"):

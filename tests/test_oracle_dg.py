@@ -56,11 +56,13 @@ def test_rest_state_stays_at_rest(orc):
         assert np.abs(R[:, 4]).max() < 1e-6
 
 
-@pytest.mark.parametrize("name,sub", [("c1", None), ("c2", (3, 3, 8))])
-def test_conservation_periodic_free_slip(orc, name, sub):
+@pytest.mark.parametrize("name,sub,flux", [("c1", None, "rusanov"), ("c2", (3, 3, 8), "rusanov"),
+                                           ("c2", (3, 3, 8), "hllc")])
+def test_conservation_periodic_free_slip(orc, name, sub, flux):
     m = I.mesh(name) if sub is None else I.sub_mesh(name, *sub)
     ph = I.physics(name)
     ph["surface_flux"] = False
+    ph["flux"] = flux
     S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case(name))
     Q = _fuzz_velocity(S, Q, 2.0, 1)
     R, fails = S.rhs(Q)
@@ -86,10 +88,11 @@ def test_surface_flux_budget(orc):
     assert abs((wJ * R[:, 0]).sum() / (ph["lhf"] / 2.5008e6 * area) - 1.0) < 1e-10
 
 
-@pytest.mark.parametrize("name,sub", [("c1", None), ("c2", (3, 3, 8))])
-def test_weak_equals_strong_form(orc, name, sub):
+@pytest.mark.parametrize("name,sub,flux", [("c1", None, "rusanov"), ("c2", (3, 3, 8), "rusanov"),
+                                           ("c1", None, "hllc")])
+def test_weak_equals_strong_form(orc, name, sub, flux):
     m = I.mesh(name) if sub is None else I.sub_mesh(name, *sub)
-    S, Q, rr, pr, _ = orc.from_inputs(m, I.physics(name), I.case(name))
+    S, Q, rr, pr, _ = orc.from_inputs(m, dict(I.physics(name), flux=flux), I.case(name))
     Q = _fuzz_velocity(S, Q, 2.0, 3)
     Rs, _ = S.rhs(Q, form=0)
     Rw, _ = S.rhs(Q, form=1)

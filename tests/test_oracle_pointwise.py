@@ -162,6 +162,58 @@ def test_rusanov_consistency_and_conservation(orc):
         assert lam > 300.0
 
 
+def test_hllc_consistency_symmetry_supersonic(orc):
+    P = orc.make_params(moist=True)
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        Ym = _state(orc, P, rng.uniform(280, 300), rng.uniform(0, 0.01), rng.uniform(0.9, 1.2),
+                    rng.normal(size=3) * 5, 500.0)
+        Yp = _state(orc, P, rng.uniform(280, 300), rng.uniform(0, 0.01), rng.uniform(0.9, 1.2),
+                    rng.normal(size=3) * 5, 500.0)
+        f = orc.flux1_normal(P, Ym, 500.0, 9.5e4, n)
+        assert np.allclose(orc.hllc(P, Ym, Ym, 500.0, 9.5e4, n), f, rtol=1e-13, atol=1e-9)
+        a = orc.hllc(P, Ym, Yp, 500.0, 9.5e4, n)
+        b = orc.hllc(P, Yp, Ym, 500.0, 9.5e4, -n)
+        assert np.allclose(a, -b, rtol=1e-12, atol=1e-8)
+    # supersonic to the right on both sides (u.n > c): the left flux, exactly
+    n = np.array([1.0, 0.0, 0.0])
+    Ym = _state(orc, P, 290.0, 0.005, 1.1, np.array([400.0, 3.0, 0.0]), 500.0)
+    Yp = _state(orc, P, 295.0, 0.002, 1.0, np.array([420.0, -2.0, 1.0]), 500.0)
+    assert np.array_equal(orc.hllc(P, Ym, Yp, 500.0, 9.5e4, n), orc.flux1_normal(P, Ym, 500.0, 9.5e4, n))
+    assert np.array_equal(orc.hllc(P, Yp, Ym, 500.0, 9.5e4, -n), orc.flux1_normal(P, Ym, 500.0, 9.5e4, -n))
+
+
+def test_hllc_resolves_contact_and_wall(orc):
+    """A contact (equal pressure and normal velocity, different density,
+    temperature, water and tangential velocity) is an exact solution of the
+    Riemann problem moving with u.n: HLLC returns the upwind flux, where
+    Rusanov adds dissipation.  Against its mirror image (the wall ghost) HLLC
+    carries no mass, water or energy through the face."""
+    P = orc.make_params(moist=True)
+    n = np.array([0.0, 0.6, 0.8])
+    p, z, pr = 9.6e4, 400.0, 9.5e4
+    for un in (4.0, -3.0):
+        TL, qL, TR, qR = 290.0, 0.006, 300.0, 0.001
+        rL = p / ((P.Rd * (1 - qL) + P.Rv * qL) * TL)
+        rR = p / ((P.Rd * (1 - qR) + P.Rv * qR) * TR)
+        t = np.array([1.0, 0.8, -0.6])          # tangential to n
+        YL = _state(orc, P, TL, qL, rL, un * n + 2.0 * t, z)
+        YR = _state(orc, P, TR, qR, rR, un * n - 5.0 * t, z)
+        up = YL if un > 0 else YR
+        want = orc.flux1_normal(P, up, z, pr, n)
+        got = orc.hllc(P, YL, YR, z, pr, n)
+        assert np.allclose(got, want, rtol=1e-11, atol=1e-7), (got, want)
+        assert np.abs(orc.rusanov(P, YL, YR, z, pr, n) - want).max() > 1.0
+    Y = _state(orc, P, 288.0, 0.004, 1.15, np.array([3.0, -7.0, 2.0]), z)
+    G = Y.copy()
+    rn = Y[1:4] @ n
+    G[1:4] = Y[1:4] - 2.0 * rn * n
+    f = orc.hllc(P, Y, G, z, pr, n)
+    assert abs(f[0]) < 1e-12 and abs(f[5]) < 1e-14 and abs(f[4]) < 1e-7
+
+
 # ------------------------------------------------------------------ closure
 
 def test_smagorinsky_simple_shear(orc):
