@@ -48,6 +48,9 @@ typedef enum {
 } cmles_status;
 
 enum { CMLES_CLOSURE_NONE = 0, CMLES_CLOSURE_SL = 1, CMLES_CLOSURE_MLP = 2, CMLES_CLOSURE_VREMAN = 3 };
+/* Numerical flux of F1 on element faces (Sec. 3.1): Rusanov (Eq. nonviscFlux,
+ * lambda/2 reading) or HLLC (Toro, Spruce & Speares 1994, Davis wave speeds). */
+enum { CMLES_FLUX_RUSANOV = 0, CMLES_FLUX_HLLC = 1 };
 
 /* Arithmetic of the RHS kernels.
  *   CMLES_FP64       all FP64 ("plain" method).
@@ -91,6 +94,7 @@ typedef struct {
   int precision;         /* CMLES_FP64 or CMLES_FP32_ACC64 */
   double dt;             /* time step of cmles_step */
   int satadj_max_iter;   /* Newton iteration cap (default 20) */
+  int flux;              /* CMLES_FLUX_* (default Rusanov) */
 } cmles_params;
 
 typedef struct {

@@ -18,6 +18,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "cmles.h")
 
 CMLES_FP64, CMLES_FP32_ACC64 = 0, 1
 CLOSURE = {"none": 0, "sl": 1, "mlp": 2, "vreman": 3}
+FLUX = {"rusanov": 0, "hllc": 1}
 PRECISION = {"fp64": CMLES_FP64, "fp32": CMLES_FP32_ACC64, "fp32acc64": CMLES_FP32_ACC64}
 STATUS = {0: "CMLES_OK", 1: "CMLES_ERR_ARG", 2: "CMLES_ERR_OOM", 3: "CMLES_ERR_CUDA", 4: "CMLES_ERR_SATADJ",
           5: "CMLES_ERR_NONFINITE", 6: "CMLES_ERR_MESH", 7: "CMLES_ERR_STATE"}
@@ -39,7 +40,7 @@ class Params(C.Structure):
         ("moist", C.c_int), ("sponge_alpha", C.c_double), ("sponge_zs", C.c_double), ("sponge_gamma", C.c_double),
         ("u_relax", C.c_double * 3), ("lateral_sponge_frac", C.c_double), ("surface_flux", C.c_int),
         ("shf", C.c_double), ("lhf", C.c_double), ("Omega", C.c_double * 3), ("precision", C.c_int),
-        ("dt", C.c_double), ("satadj_max_iter", C.c_int)]
+        ("dt", C.c_double), ("satadj_max_iter", C.c_int), ("flux", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -171,6 +172,8 @@ def make_params(d, precision="fp64"):
     for k, v in d.items():
         if k == "closure":
             P.closure = CLOSURE[v]
+        elif k == "flux":
+            P.flux = FLUX[v]
         elif k in ("u_relax", "Omega"):
             setattr(P, k, (C.c_double * 3)(*v))
         elif k in ("richardson", "moist", "surface_flux"):

@@ -208,6 +208,7 @@ void fill_kparams(cmles_handle h) {
   K.richardson = p.richardson;
   K.moist = p.moist;
   K.closure = p.closure;
+  K.flux = p.flux;
   for (int c = 0; c < 3; ++c) {
     K.Omega[c] = p.Omega[c];
     K.u_relax[c] = p.u_relax[c];
@@ -562,6 +563,7 @@ void cmles_default_params(cmles_params *p) {
   p->precision = CMLES_FP64;
   p->dt = 0.02;
   p->satadj_max_iter = 20;
+  p->flux = CMLES_FLUX_RUSANOV;
 }
 
 cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cmles_handle *out) {
@@ -578,6 +580,7 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   if (params->closure != CMLES_CLOSURE_NONE && params->closure != CMLES_CLOSURE_SL &&
       params->closure != CMLES_CLOSURE_MLP && params->closure != CMLES_CLOSURE_VREMAN)
     return CMLES_ERR_ARG;
+  if (params->flux != CMLES_FLUX_RUSANOV && params->flux != CMLES_FLUX_HLLC) return CMLES_ERR_ARG;
   // Vreman's directional lengths are those of the flat elements
   if (params->closure == CMLES_CLOSURE_VREMAN && mesh->warp) return CMLES_ERR_ARG;
   // the learned closure runs on BF16 tensor cores inside the FP32 kernels

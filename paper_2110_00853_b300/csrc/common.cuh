@@ -48,6 +48,7 @@ struct KParams {
   double vr_d2[3];   // Delta_m^2 = (h_m / N)^2 (Vreman)
   double Prt, inv_Prt;
   int richardson, moist, closure;
+  int flux;          // numerical flux of F1: 0 Rusanov, 1 HLLC
   // sources
   double Omega[3], u_relax[3];
   int surface_flux;
@@ -155,6 +156,46 @@ __device__ __forceinline__ T vreman_nu(const T (&gr)[6][3], T c25, const T (&d2)
     B += d2[m] * d2[n] * acc;
   }
   return uu > T(0) ? c25 * sqrt(B / uu) : T(0);
+}
+
+
+// HLLC numerical flux (Toro, Spruce & Speares 1994; named in Sec. 3.1) in the
+// form n.F* = n.F1(Y_K) + J on a face of unit normal n, with the Davis wave
+// speeds S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R),
+// u = u.n.  Returns the side K (0 = left, the own element; 1 = right) whose
+// flux is used and writes J = S_K (U*_K - U_K) (zero in the supersonic cases).
+// The star-state jump is formed as products of small factors,
+//   rho* - rho = rho (S* - u)/(S - S*) =: dr,
+//   (rho u)* - rho u = dr u + rho chi (S* - u) n,  chi = (S - u)/(S - S*),
+//   E* - E = e dr + rho chi (S* - u)(S* + p / (rho (S - u))),
+//   (rho q)* - rho q = q dr,
+// so that no large state is differenced.  Per side: density, velocity,
+// specific water q, total energy per unit mass e = E/rho (with g z), full
+// pressure p and sound speed c; dp = p_R - p_L.
+template <typename T>
+__device__ __forceinline__ int hllc_jump(T rL, const T (&uL)[3], T qL, T eL, T pL, T cL, T rR, const T (&uR)[3], T qR,
+                                         T eR, T pR, T cR, T dp, const T (&n)[3], T J[6]) {
+  const T unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
+  const T unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
+  const T SL = fmin(unL - cL, unR - cR), SR = fmax(unL + cL, unR + cR);
+#pragma unroll
+  for (int v = 0; v < 6; ++v) J[v] = T(0);
+  if (SL >= T(0)) return 0;
+  if (SR <= T(0)) return 1;
+  const T Ss = (dp + rL * unL * (SL - unL) - rR * unR * (SR - unR)) / (rL * (SL - unL) - rR * (SR - unR));
+  const int K = Ss >= T(0) ? 0 : 1;
+  const T r = K ? rR : rL, un = K ? unR : unL, S = K ? SR : SL;
+  const T q = K ? qR : qL, e = K ? eR : eL, p = K ? pR : pL;
+  const T iden = T(1) / (S - Ss);
+  const T chi = (S - un) * iden;
+  const T dr = r * (Ss - un) * iden;
+  const T rcs = r * chi * (Ss - un);
+  J[0] = S * dr;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) J[1 + c] = S * (dr * (K ? uR[c] : uL[c]) + rcs * n[c]);
+  J[4] = S * (e * dr + rcs * (Ss + p / (r * (S - un))));
+  J[5] = S * q * dr;
+  return K;
 }
 
 }  // namespace cmles

@@ -241,7 +241,8 @@ __device__ __forceinline__ void flux1_normal32(const float s[6], float rho_r, fl
   f[5] = (rhoq_r + s[5]) * un;
 }
 
-template <int N, bool UPDATE>
+// FL: numerical flux of F1, 0 Rusanov, 1 HLLC
+template <int N, bool UPDATE, int FL>
 __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, const float *__restrict__ F2,
                                                    const float *__restrict__ aux, float *__restrict__ dQ,
                                                    double *__restrict__ Q64, float *__restrict__ Sout,
@@ -350,14 +351,29 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
       flux1_normal32(sp, rho_r, rhoq_r, Hr, pp, nv, fp);
       const float um = (sm[1] * nv[0] + sm[2] * nv[1] + sm[3] * nv[2]) / (rho_r + sm[0]);
       const float up = (sp[1] * nv[0] + sp[2] * nv[1] + sp[3] * nv[2]) / (rho_r + sp[0]);
-      const float lam = fmaxf(fabsf(um) + cm, fabsf(up) + cp);
+      float f1s[6];
+      if (FL == 1) {
+        // HLLC: n.F1(Y_K) + S_K (U*_K - U_K)
+        const float rM = rho_r + sm[0], rP = rho_r + sp[0];
+        const float iM = fdiv(1.0f, rM), iP = fdiv(1.0f, rP);
+        const float uM[3] = {sm[1] * iM, sm[2] * iM, sm[3] * iM}, uP[3] = {sp[1] * iP, sp[2] * iP, sp[3] * iP};
+        const float pr = tn[L_P * kNP], Er = Hr - pr;
+        float J[6];
+        const int K = hllc_jump<float>(rM, uM, (rhoq_r + sm[5]) * iM, (Er + sm[4]) * iM, pr + pm, cm, rP, uP,
+                                       (rhoq_r + sp[5]) * iP, (Er + sp[4]) * iP, pr + pp, cp, pp - pm, nv, J);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) f1s[v] = (K ? fp[v] : fm[v]) + J[v];
+      } else {
+        const float lam = fmaxf(fabsf(um) + cm, fabsf(up) + cp);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) f1s[v] = 0.5f * (fm[v] + fp[v]) + 0.5f * lam * (sm[v] - sp[v]);
+      }
       const float Lf = mag / (gn[9 * kNP] * (float)P.w[0]);
       const int c_of_v[6] = {0, 1, 2, 3, 4, 0};
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
-        const float f1s = 0.5f * (fm[v] + fp[v]) + 0.5f * lam * (sm[v] - sp[v]);
         const float fnm = sg * sF[v][d][n] / mag;  // n . F at the own node
-        sLf[f][v][fn] = Lf * (fnm - (f1s + f2s[c_of_v[v]]));
+        sLf[f][v][fn] = Lf * (fnm - (f1s[v] + f2s[c_of_v[v]]));
       }
     }
     __syncthreads();
@@ -461,16 +477,26 @@ cudaError_t launch_grad32c(const float *S, float *F2, float *aux, const KParams 
   return cudaGetLastError();
 }
 
+template <bool UPDATE, int FL>
+static void k_rhs32c_instance(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
+                           double *Rout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
+  static int grid = 0;
+  if (!grid) grid = grid_for((const void *)k_rhs32c<4, UPDATE, FL>, 1 << 30, 0);
+  k_rhs32c<4, UPDATE, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+}
+
 cudaError_t launch_rhs32c(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
-                          double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+                         double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
   if (update) {
-    static int grid = 0;
-    if (!grid) grid = grid_for((const void *)k_rhs32c<4, true>, 1 << 30, 0);
-    k_rhs32c<4, true><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+    if (P.flux == 1)
+      k_rhs32c_instance<true, 1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+    else
+      k_rhs32c_instance<true, 0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
   } else {
-    static int grid = 0;
-    if (!grid) grid = grid_for((const void *)k_rhs32c<4, false>, 1 << 30, 0);
-    k_rhs32c<4, false><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+    if (P.flux == 1)
+      k_rhs32c_instance<false, 1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+    else
+      k_rhs32c_instance<false, 0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
   }
   return cudaGetLastError();
 }

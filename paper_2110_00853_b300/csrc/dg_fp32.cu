@@ -207,7 +207,8 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
   if (fail) atomicAdd(P.flags, 1);
 }
 
-template <int N, bool UPDATE>
+// FL: numerical flux of F1, 0 Rusanov, 1 HLLC
+template <int N, bool UPDATE, int FL>
 __global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, const float *__restrict__ F2,
                                                   const float *__restrict__ aux, float *__restrict__ dQ,
                                                   double *__restrict__ Q64, float *__restrict__ Sout,
@@ -302,18 +303,37 @@ __global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, c
           f2s[4] = -F.E_energy;
         }
       }
-      float fm[6], fp[6];
+      float fm[6], fp[6], f1s[6];
       flux1_dev32(sm, rho_r, rhoq_r, pm, d, fm);
       flux1_dev32(sp, rho_r, rhoq_r, pp, d, fp);
       const float um = fdiv(sm[1 + d], rho_r + sm[0]), up = fdiv(sp[1 + d], rho_r + sp[0]);
-      const float lam = fmaxf(fabsf(um) + cm, fabsf(up) + cp);
+      // reference part of the energy flux (H_r u.n is not in fm, fp): the
+      // own node's H_r (u-.n) minus that of the numerical flux
+      float ref4;
+      if (FL == 1) {
+        // HLLC: n.F1(Y_K) + S_K (U*_K - U_K), full states from the deviations
+        const float rM = rho_r + sm[0], rP = rho_r + sp[0];
+        const float iM = fdiv(1.0f, rM), iP = fdiv(1.0f, rP);
+        const float uM[3] = {sm[1] * iM, sm[2] * iM, sm[3] * iM}, uP[3] = {sp[1] * iP, sp[2] * iP, sp[3] * iP};
+        const float Er = Lf[L_H] - Lf[L_P];  // rho e_r
+        const float nrm[3] = {d == 0 ? sg : 0.f, d == 1 ? sg : 0.f, d == 2 ? sg : 0.f};
+        float J[6];
+        const int K = hllc_jump<float>(rM, uM, (rhoq_r + sm[5]) * iM, (Er + sm[4]) * iM, Lf[L_P] + pm, cm, rP, uP,
+                                       (rhoq_r + sp[5]) * iP, (Er + sp[4]) * iP, Lf[L_P] + pp, cp, pp - pm, nrm, J);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) f1s[v] = sg * (K ? fp[v] : fm[v]) + J[v];
+        ref4 = K ? sg * Lf[L_H] * (um - up) : 0.f;
+      } else {
+        const float lam = fmaxf(fabsf(um) + cm, fabsf(up) + cp);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) f1s[v] = 0.5f * (sg * fm[v] + sg * fp[v]) + 0.5f * lam * (sm[v] - sp[v]);
+        ref4 = 0.5f * sg * Lf[L_H] * (um - up);
+      }
       const int c_of_v[6] = {0, 1, 2, 3, 4, 0};
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
-        const float f1s = 0.5f * (sg * fm[v] + sg * fp[v]) + 0.5f * lam * (sm[v] - sp[v]);
-        float r = sg * sF[v][d][n] - (f1s + f2s[c_of_v[v]]);
-        // reference part of the energy flux: H_r (u-.n) - H_r (u-.n + u+.n)/2
-        if (v == 4) r += 0.5f * sg * Lf[L_H] * (um - up);
+        float r = sg * sF[v][d][n] - (f1s[v] + f2s[c_of_v[v]]);
+        if (v == 4) r += ref4;
         sLf[f][v][fn] = F.lift[d] * r;
       }
     }
@@ -440,16 +460,26 @@ cudaError_t launch_grad32(const float *S, float *F2, float *aux, const KParams &
   return cudaGetLastError();
 }
 
+template <bool UPDATE, int FL>
+static void k_rhs32_instance(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
+                           double *Rout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
+  static int grid = 0;
+  if (!grid) grid = grid_for((const void *)k_rhs32<4, UPDATE, FL>, 1 << 30, 0);
+  k_rhs32<4, UPDATE, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+}
+
 cudaError_t launch_rhs32(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
                          double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
   if (update) {
-    static int grid = 0;
-    if (!grid) grid = grid_for((const void *)k_rhs32<4, true>, 1 << 30, 0);
-    k_rhs32<4, true><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+    if (P.flux == 1)
+      k_rhs32_instance<true, 1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+    else
+      k_rhs32_instance<true, 0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
   } else {
-    static int grid = 0;
-    if (!grid) grid = grid_for((const void *)k_rhs32<4, false>, 1 << 30, 0);
-    k_rhs32<4, false><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+    if (P.flux == 1)
+      k_rhs32_instance<false, 1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+    else
+      k_rhs32_instance<false, 0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
   }
   return cudaGetLastError();
 }

@@ -171,7 +171,8 @@ __device__ __forceinline__ void flux1_dir(const double Y[6], double pprime, doub
   f[5] = Y[5] * ud;
 }
 
-template <int N, bool UPDATE>
+// FL: numerical flux of F1, 0 Rusanov, 1 HLLC
+template <int N, bool UPDATE, int FL>
 __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, const double *__restrict__ F2,
                                                const double *__restrict__ aux, double *__restrict__ dQ,
                                                double *__restrict__ Qout, const StageCoef sc, const KParams P) {
@@ -253,18 +254,31 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
           f2s[4] = -P.E_energy;
         }
       }
-      // Rusanov (Eq. nonviscFlux): 1/2 n.(F1- + F1+) + lambda/2 (Y- - Y+)
-      double fm[6], fp[6];
+      double fm[6], fp[6], f1s[6];
       flux1_dir(Ym, pm, pr, d, fm);
       flux1_dir(Yp, pp, pr, d, fp);
-      const double lm = fabs(Ym[1 + d] / Ym[0]) + cm;
-      const double lp = fabs(Yp[1 + d] / Yp[0]) + cp;
-      const double lam = fmax(lm, lp);
+      if (FL == 1) {
+        // HLLC: n.F1(Y_K) + S_K (U*_K - U_K)
+        const double im = 1.0 / Ym[0], ip = 1.0 / Yp[0];
+        const double uM[3] = {Ym[1] * im, Ym[2] * im, Ym[3] * im}, uP[3] = {Yp[1] * ip, Yp[2] * ip, Yp[3] * ip};
+        const double nrm[3] = {d == 0 ? sg : 0.0, d == 1 ? sg : 0.0, d == 2 ? sg : 0.0};
+        double J[6];
+        const int K = hllc_jump<double>(Ym[0], uM, Ym[5] * im, Ym[4] * im, pm + pr, cm, Yp[0], uP, Yp[5] * ip,
+                                        Yp[4] * ip, pp + pr, cp, pp - pm, nrm, J);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) f1s[v] = sg * (K ? fp[v] : fm[v]) + J[v];
+      } else {
+        // Rusanov (Eq. nonviscFlux): 1/2 n.(F1- + F1+) + lambda/2 (Y- - Y+)
+        const double lm = fabs(Ym[1 + d] / Ym[0]) + cm;
+        const double lp = fabs(Yp[1 + d] / Yp[0]) + cp;
+        const double lam = fmax(lm, lp);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) f1s[v] = 0.5 * (sg * fm[v] + sg * fp[v]) + 0.5 * lam * (Ym[v] - Yp[v]);
+      }
       const int c_of_v[6] = {0, 1, 2, 3, 4, 0};
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
-        const double f1s = 0.5 * (sg * fm[v] + sg * fp[v]) + 0.5 * lam * (Ym[v] - Yp[v]);
-        const double fstar = f1s + f2s[c_of_v[v]];
+        const double fstar = f1s[v] + f2s[c_of_v[v]];
         sL[f][v][fn] = P.lift[d] * (sg * sF[v][d][n] - fstar);
       }
     }
@@ -345,16 +359,26 @@ cudaError_t launch_grad64(const double *Q, double *F2, double *aux, const KParam
   return cudaGetLastError();
 }
 
+template <bool UPDATE, int FL>
+static void rhs64_instance(const double *Q, const double *F2, const double *aux, double *dQ, double *Qout,
+                           const StageCoef &sc, const KParams &P, cudaStream_t s) {
+  static int grid = 0;
+  if (!grid) grid = grid_for((const void *)k_rhs64<4, UPDATE, FL>, 1 << 30);
+  k_rhs64<4, UPDATE, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, aux, dQ, Qout, sc, P);
+}
+
 cudaError_t launch_rhs64(const double *Q, const double *F2, const double *aux, double *dQ, double *Qout,
                          const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
   if (update) {
-    static int grid = 0;
-    if (!grid) grid = grid_for((const void *)k_rhs64<4, true>, 1 << 30);
-    k_rhs64<4, true><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, aux, dQ, Qout, sc, P);
+    if (P.flux == 1)
+      rhs64_instance<true, 1>(Q, F2, aux, dQ, Qout, sc, P, s);
+    else
+      rhs64_instance<true, 0>(Q, F2, aux, dQ, Qout, sc, P, s);
   } else {
-    static int grid = 0;
-    if (!grid) grid = grid_for((const void *)k_rhs64<4, false>, 1 << 30);
-    k_rhs64<4, false><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, aux, dQ, Qout, sc, P);
+    if (P.flux == 1)
+      rhs64_instance<false, 1>(Q, F2, aux, dQ, Qout, sc, P, s);
+    else
+      rhs64_instance<false, 0>(Q, F2, aux, dQ, Qout, sc, P, s);
   }
   return cudaGetLastError();
 }

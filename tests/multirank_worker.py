@@ -21,7 +21,9 @@ def main():
     worst = bench.max_over_ranks(ms, world, torch, "cpu")
     rate = bench.whole_job_rate(1000, world, 3, worst)
     torch.distributed.barrier()
-    print(json.dumps(dict(rank=rank, world=world, local=local, worst=worst, rate=rate)), flush=True)
+    # one file per rank: the ranks' stdout streams interleave
+    with open(os.path.join(sys.argv[1], f"rank{rank}.json"), "w") as f:
+        json.dump(dict(rank=rank, world=world, local=local, worst=worst, rate=rate), f)
     torch.distributed.destroy_process_group()
 
 

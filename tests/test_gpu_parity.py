@@ -117,6 +117,30 @@ def test_tendency_vreman(orc, richardson):
     _compare_rhs(S, Q, G, 1e-12)
 
 
+@pytest.mark.parametrize("case", ["walls", "moist"])
+def test_tendency_hllc(orc, case):
+    # HLLC faces (Sec. 3.1): walls on all sides with rotation, or the ragged
+    # moist sub-box with saturation, sponge and surface fluxes
+    if case == "walls":
+        m = I.sub_mesh("c1", 3, 2, 3)
+        m["periodic"] = (0, 0, 0)
+        ph = I.physics("c1")
+        ph.update(Omega=(0.0, 1e-4, 7.29e-5), sponge_alpha=0.2, sponge_zs=900.0)
+        name = "c1"
+    else:
+        m = I.sub_mesh("c2", 5, 3, 16)
+        ph = I.physics("c2")
+        name = "c2"
+    ph["flux"] = "hllc"
+    S, Q, G = _setup(orc, name, m, phys=ph, fuzz_seed=8)
+    errs, R_gpu, R_orc = _compare_rhs(S, Q, G, 1e-12)
+    # HLLC and Rusanov differ on these states
+    ph2 = dict(ph, flux="rusanov")
+    S2, _, _ = _setup(orc, name, m, phys=ph2, fuzz_seed=8)
+    R_rus, _ = S2.rhs(Q)
+    assert np.abs(R_rus - R_orc).max() > 1e-6 * np.abs(R_orc).max()
+
+
 def test_single_element_periodic_degenerate(orc):
     # one element periodic in x and y: every neighbour is the element itself
     m = I.sub_mesh("c1", 1, 1, 2)

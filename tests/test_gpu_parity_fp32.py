@@ -103,6 +103,23 @@ def test_fp32_tendency_vreman(orc, richardson):
     print("vreman fp32 rel L2", _compare(S, Q, G))
 
 
+@pytest.mark.parametrize("case", ["walls", "moist"])
+def test_fp32_tendency_hllc(orc, case):
+    if case == "walls":
+        m = I.sub_mesh("c1", 3, 2, 3)
+        m["periodic"] = (0, 0, 0)
+        ph = I.physics("c1")
+        ph.update(Omega=(0.0, 1e-4, 7.29e-5), sponge_alpha=0.2, sponge_zs=900.0)
+        name = "c1"
+    else:
+        m = I.sub_mesh("c2", 5, 3, 16)
+        ph = I.physics("c2")
+        name = "c2"
+    ph["flux"] = "hllc"
+    S, Q, G = _setup(orc, name, m, phys=ph, fuzz_seed=18)
+    print("hllc fp32", case, "rel L2", _compare(S, Q, G))
+
+
 def test_fp32_tendency_c5_subbox(orc):
     m = I.sub_mesh("c5", 4, 4, 10)
     c = I.case("c5")

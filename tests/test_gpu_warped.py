@@ -29,10 +29,11 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def _setup(orc, fuzz=True):
+def _setup(orc, fuzz=True, flux="rusanov"):
     from paper_2110_00853_b300 import cmles
     m = _hill_box()
     ph = _phys(m)
+    ph["flux"] = flux
     S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case("c3"))
     if fuzz:
         rng = np.random.default_rng(31)
@@ -46,14 +47,15 @@ def _setup(orc, fuzz=True):
     return m, S, Q, G
 
 
-def test_warped_tendency_parity(orc):
-    m, S, Q, G = _setup(orc)
+@pytest.mark.parametrize("flux", ["rusanov", "hllc"])
+def test_warped_tendency_parity(orc, flux):
+    m, S, Q, G = _setup(orc, flux=flux)
     J = S.geometry()["J"]
     assert J.std() / J.mean() > 1e-2          # genuinely curved elements
     R_orc, _ = S.rhs(Q)
     R_gpu = G.tendency(torch.from_numpy(Q).cuda()).cpu().numpy()
     errs = [_rel(R_gpu[:, v], R_orc[:, v]) for v in range(5)]
-    print("warped fp32 rel L2", errs)
+    print("warped fp32", flux, "rel L2", errs)
     for v in range(5):
         assert errs[v] <= 1e-5, (v, errs)
 

@@ -18,14 +18,14 @@ def _free_port():
     return port
 
 
-def test_two_rank_max_and_rate():
+def test_two_rank_max_and_rate(tmp_path):
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
-           os.path.join(ROOT, "tests", "multirank_worker.py")]
+           os.path.join(ROOT, "tests", "multirank_worker.py"), str(tmp_path)]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, env=env, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
-    recs = [json.loads(l) for l in out.stdout.splitlines() if l.startswith("{")]
+    recs = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(2)]
     assert sorted(r["rank"] for r in recs) == [0, 1]
     for r in recs:
         assert r["world"] == 2
