@@ -98,6 +98,14 @@ void orc_rusanov(const orc_params *p, const double Ym[6], const double Yp[6], do
 void orc_hllc(const orc_params *p, const double Ym[6], const double Yp[6], double z, double pr, const double n[3],
               double out[6]);
 
+/* ---- exponential filter (Eq. exponential_filter) ---- */
+/* One-dimensional filter matrix F = V diag(exp(-alpha (k/N)^order)) V^-1,
+ * V_ik = P_k(xi_i), row-major (N+1)^2. */
+void orc_filter_matrix(int N, const double *xi, int order, double alpha, double *F);
+/* Apply the filter in place to the variables of Q [E][6][Np] selected by
+ * mask (bit v for variable v). */
+void orc_filter(orc_solver *s, double *Q, int order, double alpha, int mask);
+
 /* ---- closure (Sec. 4) ---- */
 /* Smagorinsky-Lilly nu_t from the velocity gradient gu[i][j] = du_i/dx_j,
  * d(theta_v)/dz, theta_v and Delta (Eqs. smago, richardson). */

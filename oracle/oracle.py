@@ -80,6 +80,10 @@ def _declare(L):
     L.orc_rusanov.argtypes = [C.POINTER(Params), _DP, _DP, C.c_double, C.c_double, _DP, _DP]
     L.orc_smagorinsky.argtypes = [C.POINTER(Params), _DP, C.c_double, C.c_double, C.c_double]
     L.orc_smagorinsky.restype = C.c_double
+    L.orc_filter_matrix.argtypes = [C.c_int, _DP, C.c_int, C.c_double, _DP]
+    L.orc_filter_matrix.restype = None
+    L.orc_filter.argtypes = [C.c_void_p, _DP, C.c_int, C.c_double, C.c_int]
+    L.orc_filter.restype = None
     L.orc_hllc.argtypes = [C.POINTER(Params), _DP, _DP, C.c_double, C.c_double, _DP, _DP]
     L.orc_hllc.restype = None
     L.orc_vreman.argtypes = [C.POINTER(Params), _DP, C.c_double, C.c_double, _DP]
@@ -204,6 +208,13 @@ def rusanov(P, Ym, Yp, z, pr, n):
     return out
 
 
+def filter_matrix(N, order, alpha):
+    xi, _, _ = lgl(N)
+    F = np.zeros((N + 1) * (N + 1))
+    lib().orc_filter_matrix(N, _p(np.ascontiguousarray(xi, float)), order, alpha, _p(F))
+    return F.reshape(N + 1, N + 1)
+
+
 def hllc(P, Ym, Yp, z, pr, n):
     out = np.zeros(6)
     lib().orc_hllc(C.byref(P), _p(np.ascontiguousarray(Ym, float)), _p(np.ascontiguousarray(Yp, float)),
@@ -288,6 +299,12 @@ class Solver:
         x, y, z, J, wJ = (np.zeros(shape) for _ in range(5))
         lib().orc_geometry(self.h, _p(x), _p(y), _p(z), _p(J), _p(wJ))
         return dict(x=x, y=y, z=z, J=J, wJ=wJ)
+
+    def filter(self, Q, order, alpha, mask):
+        """exponential filter (Eq. exponential_filter) applied to a copy of Q"""
+        Q = np.ascontiguousarray(Q, float).copy()
+        lib().orc_filter(self.h, _p(Q), order, alpha, mask)
+        return Q
 
     def set_reference(self, rho_r, p_r):
         lib().orc_set_reference(self.h, _p(np.ascontiguousarray(rho_r, float)),

@@ -11,6 +11,8 @@ import os
 import numpy as np
 import pytest
 
+from paper_2110_00853_b300 import inputs as I
+
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 
@@ -366,3 +368,58 @@ def test_splitmix64_published_vector(orc):
     # uniform double keeps its top 53 bits.
     assert orc.uniform(0, 0) == (0xE220A8397B1DCDAF >> 11) * 2.0 ** -53
     assert orc.uniform(0, 1) == (0x6E789E6AA1B965F4 >> 11) * 2.0 ** -53
+
+
+# ------------------------------------------------------------------ exponential filter
+
+def test_filter_matrix_modal_definition(orc):
+    """F = V diag(exp(-alpha (k/N)^s)) V^-1 against numpy's Legendre
+    Vandermonde: mode k is scaled by sigma(k/N), the element mean (LGL
+    quadrature) is kept, the top mode is removed (sigma(1) = e^-alpha)."""
+    from numpy.polynomial import legendre as npl
+    N, s, alpha = 4, 64, -np.log(np.finfo(float).eps)
+    xi, w, _ = orc.lgl(N)
+    F = orc.filter_matrix(N, s, alpha)
+    V = npl.legvander(xi, N)
+    sig = np.exp(-alpha * (np.arange(N + 1) / N) ** s)
+    assert np.abs(F - V @ np.diag(sig) @ np.linalg.inv(V)).max() < 1e-13
+    for k in range(N + 1):
+        assert np.abs(F @ V[:, k] - sig[k] * V[:, k]).max() < 1e-13
+    assert np.abs(F @ V[:, N]).max() < 1e-13          # e^-36 ~ 2e-16
+    rng = np.random.default_rng(2)
+    u = rng.normal(size=N + 1)
+    assert abs(w @ (F @ u) - w @ u) < 1e-14
+    # a gentler filter (s = 2, alpha = 1) to see every mode damped
+    F2 = orc.filter_matrix(N, 2, 1.0)
+    for k in range(N + 1):
+        assert np.abs(F2 @ V[:, k] - np.exp(-(k / N) ** 2) * V[:, k]).max() < 1e-13
+
+
+def test_filter_on_solver_state(orc):
+    """Tensor-product filter on the momentum of a 3D state: a product of
+    Legendre modes P_a(xi) P_b(eta) P_c(zeta) is scaled by
+    sigma(a/N) sigma(b/N) sigma(c/N); unselected variables are untouched and
+    each element's momentum integral is kept."""
+    from numpy.polynomial import legendre as npl
+    m = I.sub_mesh("c1", 2, 2, 2)
+    S = orc.from_inputs(m, I.physics("c1"))
+    N = 4
+    xi, w, _ = orc.lgl(N)
+    E, Np = S.E, S.Np
+    g = S.geometry()
+    V = npl.legvander(xi, N)
+    rng = np.random.default_rng(4)
+    Q = rng.normal(size=(E, 6, Np))
+    a, b, c = 4, 1, 3
+    i, j, k = np.arange(Np) % 5, (np.arange(Np) // 5) % 5, np.arange(Np) // 25
+    mode = V[i, a] * V[j, b] * V[k, c]
+    Q[:, 2] = 3.0 * mode
+    s, alpha = 8, 2.0
+    Qf = S.filter(Q, s, alpha, 0b1110)
+    sig = lambda q: np.exp(-alpha * (q / N) ** s)
+    assert np.abs(Qf[:, 2] - 3.0 * mode * sig(a) * sig(b) * sig(c)).max() < 1e-12
+    for v in (0, 4, 5):
+        assert np.array_equal(Qf[:, v], Q[:, v])
+    wJ = g["wJ"]
+    for v in (1, 2, 3):
+        assert np.abs((wJ * Qf[:, v]).sum(1) - (wJ * Q[:, v]).sum(1)).max() < 1e-12 * np.abs(wJ * Q[:, v]).sum()
