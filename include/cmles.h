@@ -95,6 +95,16 @@ typedef struct {
   double dt;             /* time step of cmles_step */
   int satadj_max_iter;   /* Newton iteration cap (default 20) */
   int flux;              /* CMLES_FLUX_* (default Rusanov) */
+  /* Exponential modal filter (Eq. exponential_filter), applied to the state
+   * after every step: mode k of the Legendre expansion along each direction
+   * is scaled by exp(-filter_alpha (k/N)^filter_order).  filter_order 0
+   * disables it (default); filter_alpha defaults to -ln(2^-52) = 36.04;
+   * filter_vars is a bit mask over the six variables and may select only the
+   * momentum components (bits 1-3, default all three), whose balanced
+   * background is zero. */
+  int filter_order;
+  double filter_alpha;
+  int filter_vars;
 } cmles_params;
 
 typedef struct {
@@ -124,6 +134,12 @@ typedef struct {
   const double *modes;
   double qt_H;
 } cmles_case;
+
+/* Apply the exponential filter of the handle's parameters once to the
+ * current state (the same operation cmles_step applies after each step when
+ * filter_order > 0); asynchronous on the handle's stream.  Errors:
+ * CMLES_ERR_ARG when filter_order is 0. */
+cmles_status cmles_filter(cmles_handle h);
 
 /* Fill p with the defaults described above (SL closure, FP64, dry, no sponge). */
 void cmles_default_params(cmles_params *p);

@@ -40,7 +40,8 @@ class Params(C.Structure):
         ("moist", C.c_int), ("sponge_alpha", C.c_double), ("sponge_zs", C.c_double), ("sponge_gamma", C.c_double),
         ("u_relax", C.c_double * 3), ("lateral_sponge_frac", C.c_double), ("surface_flux", C.c_int),
         ("shf", C.c_double), ("lhf", C.c_double), ("Omega", C.c_double * 3), ("precision", C.c_int),
-        ("dt", C.c_double), ("satadj_max_iter", C.c_int), ("flux", C.c_int)]
+        ("dt", C.c_double), ("satadj_max_iter", C.c_int), ("flux", C.c_int), ("filter_order", C.c_int),
+        ("filter_alpha", C.c_double), ("filter_vars", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -90,6 +91,7 @@ def load(path=LIB_PATH):
         getattr(L, n).argtypes = [_H, _VP]
     L.cmles_tendency.argtypes = [_H, _VP, _VP]
     L.cmles_step.argtypes = [_H, C.c_int]
+    L.cmles_filter.argtypes = [_H]
     L.cmles_diagnostics.argtypes = [_H, C.POINTER(Diag)]
     L.cmles_profiles.argtypes = [_H, _DP]
     L.cmles_set_closure_weights.argtypes = [_H, C.POINTER(C.c_float), C.c_size_t]
@@ -285,6 +287,10 @@ class Solver:
 
     def step(self, n=1):
         self._check(self.L.cmles_step(self.h, int(n)))
+
+    def filter(self):
+        """one application of the exponential filter to the current state"""
+        self._check(self.L.cmles_filter(self.h))
 
     def diagnostics(self, raise_on_error=True):
         d = Diag()

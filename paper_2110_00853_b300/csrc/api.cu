@@ -125,6 +125,7 @@ struct cmles_t {
   long long bytes = 0;
   std::vector<float> mlp;
   MlpPacked *mlp_dev = nullptr;
+  ExpFilter expf = {};
   bool have_mlp = false;
   // curvilinear (warped) meshes: device tables and host geometry (FP64)
   bool curved = false;
@@ -564,6 +565,71 @@ void cmles_default_params(cmles_params *p) {
   p->dt = 0.02;
   p->satadj_max_iter = 20;
   p->flux = CMLES_FLUX_RUSANOV;
+  p->filter_order = 0;
+  p->filter_alpha = -log(pow(2.0, -52));
+  p->filter_vars = 0xE;
+}
+
+// 1D exponential filter matrix F = V diag(sigma_k) V^-1 with V_ik = P_k(xi_i)
+// (Legendre polynomials by their three-term recurrence) and
+// sigma_k = exp(-alpha (k/N)^s); V^-1 by LU with partial pivoting.
+static void build_expfilter(cmles_handle h) {
+  const int N = h->N, Nq = h->Nq;
+  std::vector<double> V(Nq * Nq), LU(Nq * Nq), Vinv(Nq * Nq);
+  for (int i = 0; i < Nq; ++i) {
+    double p0 = 1.0, p1 = h->xi[i];
+    V[i * Nq] = p0;
+    if (N >= 1) V[i * Nq + 1] = p1;
+    for (int k = 2; k <= N; ++k) {
+      const double p2 = ((2 * k - 1) * h->xi[i] * p1 - (k - 1) * p0) / k;
+      V[i * Nq + k] = p2;
+      p0 = p1;
+      p1 = p2;
+    }
+  }
+  LU = V;
+  std::vector<int> piv(Nq);
+  for (int c = 0; c < Nq; ++c) {
+    int r = c;
+    for (int q = c + 1; q < Nq; ++q)
+      if (fabs(LU[q * Nq + c]) > fabs(LU[r * Nq + c])) r = q;
+    piv[c] = r;
+    if (r != c)
+      for (int q = 0; q < Nq; ++q) std::swap(LU[c * Nq + q], LU[r * Nq + q]);
+    for (int q = c + 1; q < Nq; ++q) {
+      LU[q * Nq + c] /= LU[c * Nq + c];
+      for (int m = c + 1; m < Nq; ++m) LU[q * Nq + m] -= LU[q * Nq + c] * LU[c * Nq + m];
+    }
+  }
+  for (int col = 0; col < Nq; ++col) {  // solve V x = e_col
+    std::vector<double> x(Nq, 0.0);
+    x[col] = 1.0;
+    for (int c = 0; c < Nq; ++c) std::swap(x[c], x[piv[c]]);
+    for (int q = 0; q < Nq; ++q)
+      for (int m = 0; m < q; ++m) x[q] -= LU[q * Nq + m] * x[m];
+    for (int q = Nq - 1; q >= 0; --q) {
+      for (int m = q + 1; m < Nq; ++m) x[q] -= LU[q * Nq + m] * x[m];
+      x[q] /= LU[q * Nq + q];
+    }
+    for (int q = 0; q < Nq; ++q) Vinv[q * Nq + col] = x[q];
+  }
+  const double s = h->prm.filter_order, alpha = h->prm.filter_alpha;
+  for (int i = 0; i < Nq; ++i)
+    for (int j = 0; j < Nq; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < Nq; ++k) acc += V[i * Nq + k] * exp(-alpha * pow((double)k / N, s)) * Vinv[k * Nq + j];
+      h->expf.F[i * Nq + j] = acc;
+    }
+  h->expf.mask = h->prm.filter_vars;
+}
+
+static cmles_status apply_expfilter(cmles_handle h) {
+  LaunchScope ls(h, 2, 1);
+  if (h->fp32)
+    CK(launch_expfilter(h->Q[0], h->shadow_valid ? h->S32[h->scur] : nullptr, h->expf, h->N, (int)h->E, h->stream));
+  else
+    CK(launch_expfilter(h->Q[h->cur], nullptr, h->expf, h->N, (int)h->E, h->stream));
+  return CMLES_OK;
 }
 
 cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cmles_handle *out) {
@@ -581,6 +647,8 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
       params->closure != CMLES_CLOSURE_MLP && params->closure != CMLES_CLOSURE_VREMAN)
     return CMLES_ERR_ARG;
   if (params->flux != CMLES_FLUX_RUSANOV && params->flux != CMLES_FLUX_HLLC) return CMLES_ERR_ARG;
+  if (params->filter_order < 0 || !(params->filter_alpha >= 0.0) || (params->filter_vars & ~0xE) != 0)
+    return CMLES_ERR_ARG;
   // Vreman's directional lengths are those of the flat elements
   if (params->closure == CMLES_CLOSURE_VREMAN && mesh->warp) return CMLES_ERR_ARG;
   // the learned closure runs on BF16 tensor cores inside the FP32 kernels
@@ -596,6 +664,7 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   h->E = E;
   h->nodes = E * h->Np;
   lgl_basis(h->N, h->xi, h->w, h->D);
+  if (params->filter_order > 0) build_expfilter(h);
   const size_t n6 = (size_t)h->nodes * 6;
   const int nlev = mesh->nez * h->Nq;
   cmles_status st = CMLES_OK;
@@ -1044,10 +1113,20 @@ cmles_status cmles_step(cmles_handle h, int nsteps) {
       }
       if (st != CMLES_OK) return st;
     }
+    if (h->prm.filter_order > 0) {
+      cmles_status st = apply_expfilter(h);
+      if (st != CMLES_OK) return st;
+    }
     h->steps += 1;
     h->time += h->prm.dt;
   }
   return CMLES_OK;
+}
+
+cmles_status cmles_filter(cmles_handle h) {
+  if (!h) return CMLES_ERR_ARG;
+  if (h->prm.filter_order <= 0) return fail(h, CMLES_ERR_ARG, "cmles_filter: filter_order is 0");
+  return apply_expfilter(h);
 }
 
 cmles_status cmles_diagnostics(cmles_handle h, cmles_diag *out) {

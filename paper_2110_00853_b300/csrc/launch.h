@@ -27,6 +27,15 @@ cudaError_t launch_grad32c(const float *S, float *F2, float *aux, const KParams 
 cudaError_t launch_rhs32c(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
                           double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s);
 
+// Exponential modal filter (expfilter.cu): F is the 1D filter matrix
+// (row-major (N+1)^2), mask selects momentum components (bits 1..3); S32,
+// when not null, is the FP32 shadow to rewrite for the filtered variables.
+struct ExpFilter {
+  double F[kMaxQ * kMaxQ];
+  int mask;
+};
+cudaError_t launch_expfilter(double *Q, float *S32, const ExpFilter &F, int N, int E, cudaStream_t s);
+
 // Learned closure network (mlp.cu)
 struct MlpPacked;
 void pack_mlp_host(const float *params, MlpPacked *out);

@@ -141,6 +141,41 @@ def test_tendency_hllc(orc, case):
     assert np.abs(R_rus - R_orc).max() > 1e-6 * np.abs(R_orc).max()
 
 
+ALPHA = -np.log(2.0 ** -52)
+
+
+@pytest.mark.parametrize("order,mask", [(64, 0b1110), (4, 0b0100)])
+def test_exponential_filter(orc, order, mask):
+    # Eq. exponential_filter on the momentum: one application on a fuzzed
+    # state, then one LSRK step followed by the filter (as cmles_step does)
+    m = I.sub_mesh("c2", 5, 3, 16)
+    ph = dict(I.physics("c2"), filter_order=order, filter_alpha=ALPHA, filter_vars=mask)
+    S, Q, G = _setup(orc, "c2", m, phys=ph, fuzz_seed=9)
+    G.set_state(torch.from_numpy(Q).cuda())
+    G.filter()
+    got = G.get_state().cpu().numpy()
+    want = S.filter(Q, order, ALPHA, mask)
+    for v in range(6):
+        assert _rel_l2(got[:, v], want[:, v]) <= 1e-14, v
+    assert np.abs(want[:, 2] - Q[:, 2]).max() > 1e-3 * np.abs(Q[:, 2]).max()
+    Q1, fails = S.lsrk54(Q, 1, ph["dt"])
+    assert fails == 0
+    want1 = S.filter(Q1, order, ALPHA, mask)
+    G.set_state(torch.from_numpy(Q).cuda())
+    G.step(1)
+    got1 = G.get_state().cpu().numpy()
+    for v in range(6):
+        d_g, d_o = got1[:, v] - Q[:, v], want1[:, v] - Q[:, v]
+        assert _rel_l2(d_g, d_o) <= 1e-12, v
+
+
+def test_filter_off_by_default(orc):
+    from paper_2110_00853_b300 import cmles
+    S, Q, G = _setup(orc, "c1", I.mesh("c1"))
+    with pytest.raises(cmles.CmlesError):
+        G.filter()
+
+
 def test_single_element_periodic_degenerate(orc):
     # one element periodic in x and y: every neighbour is the element itself
     m = I.sub_mesh("c1", 1, 1, 2)

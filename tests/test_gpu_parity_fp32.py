@@ -164,6 +164,25 @@ def test_fp32_steps_track_oracle(orc):
         assert _rel_l2(dq_g, dq_o) <= 1e-5, v
 
 
+def test_fp32_steps_with_exponential_filter(orc):
+    alpha = -np.log(2.0 ** -52)
+    m = I.sub_mesh("c2", 4, 4, 16)
+    ph = dict(I.physics("c2"), filter_order=64, filter_alpha=alpha, filter_vars=0b1110)
+    S, Q, G = _setup(orc, "c2", m, phys=ph, fuzz_seed=19)
+    Qo = Q
+    for _ in range(3):
+        Qo, fails = S.lsrk54(Qo, 1, ph["dt"])
+        assert fails == 0
+        Qo = S.filter(Qo, 64, alpha, 0b1110)
+    G.set_state(torch.from_numpy(Q).cuda())
+    G.step(3)
+    Qg = G.get_state().cpu().numpy()
+    for v in range(6):
+        err = _rel_l2(Qg[:, v] - Q[:, v], Qo[:, v] - Q[:, v])
+        print("fp32 filtered 3-step increment rel L2", v, err)
+        assert err <= 1e-5, v
+
+
 def test_fp32_mass_energy_conservation(orc):
     m = I.sub_mesh("c2", 4, 4, 16)
     ph = I.physics("c2")
