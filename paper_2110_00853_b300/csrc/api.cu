@@ -126,6 +126,7 @@ struct cmles_t {
   std::vector<float> mlp;
   MlpPacked *mlp_dev = nullptr;
   ExpFilter expf = {};
+  double *rvs_tab = nullptr;
   bool have_mlp = false;
   // curvilinear (warped) meshes: device tables and host geometry (FP64)
   bool curved = false;
@@ -204,6 +205,9 @@ void fill_kparams(cmles_handle h) {
   K.pv_Ttr = p.Ttr;
   K.pv_a = K.dcp / p.Rv;
   K.pv_b = (p.Lv0 - K.dcp * p.T0) / p.Rv;
+  K.inv_Rd = 1.0 / p.Rd;
+  K.inv_p0 = 1.0 / p.p0;
+  K.inv_Ttr = 1.0 / p.Ttr;
   K.Prt = p.Prt;
   K.inv_Prt = 1.0 / p.Prt;
   K.richardson = p.richardson;
@@ -570,6 +574,35 @@ void cmles_default_params(cmles_params *p) {
   p->filter_vars = 0xE;
 }
 
+// Tangent table of the saturation vapour density rho_vs(T) = p_v*(T)/(R_v T)
+// for the certainly-unsaturated shortcut of the thermodynamics: knots every
+// 5 K on [150, 450] K.  The shortcut relies on rho_vs being convex there;
+// that is checked here by second differences on a 0.1 K grid, and the
+// shortcut is disabled (rvs_n = 0, rvs_ok = 0) if it fails.
+static constexpr int kRvsN = 61;
+static cudaError_t build_rvs_table(cmles_handle h) {
+  KParams &K = h->K;
+  auto rvs = [&](double T) {
+    return K.pv_ptr * exp(K.pv_a * log(T / K.pv_Ttr) + K.pv_b * (1.0 / K.pv_Ttr - 1.0 / T)) / (h->prm.Rv * T);
+  };
+  bool convex = true;
+  const double dT = 0.1;
+  for (double T = 150.0 + dT; T < 450.0; T += dT)
+    if (!(rvs(T - dT) - 2.0 * rvs(T) + rvs(T + dT) > 0.0)) convex = false;
+  std::vector<double> tab(kRvsN * 2);
+  for (int k = 0; k < kRvsN; ++k) {
+    const double T = 150.0 + 5.0 * k, f = rvs(T);
+    tab[2 * k] = f;
+    tab[2 * k + 1] = f * (K.pv_a - 1.0 + K.pv_b / T) / T;
+  }
+  K.rvs_tab = h->rvs_tab;
+  K.rvs_T0 = 150.0;
+  K.rvs_dT = 5.0;
+  K.rvs_n = convex ? kRvsN : 0;
+  K.rvs_ok = convex ? 1 : 0;
+  return cudaMemcpy(h->rvs_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+}
+
 // 1D exponential filter matrix F = V diag(sigma_k) V^-1 with V_ik = P_k(xi_i)
 // (Legendre polynomials by their three-term recurrence) and
 // sigma_k = exp(-alpha (k/N)^s); V^-1 by LU with partial pivoting.
@@ -712,6 +745,7 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   ALLOC(h->tau_col, (size_t)mesh->nex * h->Nq * sizeof(double));
   ALLOC(h->wq, h->Np * sizeof(double));
   ALLOC(h->flags, 16 * sizeof(int));
+  ALLOC(h->rvs_tab, kRvsN * 2 * sizeof(double));
   h->budget_nblocks = budget_blocks(h->nodes);
   ALLOC(h->partials, (size_t)h->budget_nblocks * 7 * sizeof(double));
   ALLOC(h->budget_out, 8 * sizeof(double));
@@ -750,6 +784,7 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
     e = cudaMemcpy(h->tau_col, tc.data(), tc.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->wq, wq.data(), h->Np * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(h->flags, 0, 16 * sizeof(int));
+  if (e == cudaSuccess) e = build_rvs_table(h);
   if (e == cudaSuccess) e = cudaMemset(h->mlp_dev, 0, sizeof(MlpPacked));
   if (e == cudaSuccess && h->dQ) e = cudaMemset(h->dQ, 0, n6 * sizeof(double));
   if (e == cudaSuccess && h->dQ32) e = cudaMemset(h->dQ32, 0, (size_t)E * 128 * 6 * sizeof(float));
@@ -781,7 +816,7 @@ cmles_status cmles_destroy(cmles_handle h) {
   void *bufs[] = {h->Q[0],   h->Q[1],    h->dQ,      h->F2,       h->aux,     h->rho_r,    h->p_r,
                   h->qt_r,   h->tau_lev, h->tau_col, h->wq,       h->flags,   h->partials, h->budget_out,
                   h->prof,   h->S32[0],  h->S32[1],  h->dQ32,     h->F2_32,   h->aux32,    h->lev32,
-                  h->dH32,   h->qref64,  h->mlp_dev, h->geo32,   h->node32,  h->wJn};
+                  h->dH32,   h->qref64,  h->mlp_dev, h->geo32,   h->node32,  h->wJn,      h->rvs_tab};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete h;

@@ -42,6 +42,16 @@ struct KParams {
   double kappa;      // R_d / c_pd (dry Exner exponent)
   double pv_ptr, pv_Ttr, pv_a, pv_b;  // p_v* = p_tr exp(a ln(T/T_tr) + b (1/T_tr - 1/T))
   double dcp;        // c_pv - c_pl
+  double inv_Rd, inv_p0, inv_Ttr;
+  // tangents of the saturation vapour density rho_vs(T) = p_v*(T)/(R_v T) at
+  // T_k = rvs_T0 + k rvs_dT, k < rvs_n: [k][2] = (rho_vs(T_k), d rho_vs/dT);
+  // rho_vs is convex in T on the tabulated range (checked on the host when the
+  // table is built; rvs_n = 0 disables the shortcut), so each tangent bounds it
+  // from below there
+  const double *rvs_tab;
+  double rvs_T0, rvs_dT;
+  int rvs_n;
+  int rvs_ok;        // FP32 path: the tangent test at T_r may be used
   // closure
   double CsDelta2;   // (C_s Delta)^2
   double vr_c;       // 2.5 C_s^2 (Vreman)

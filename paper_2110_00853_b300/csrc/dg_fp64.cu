@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, do
         else
           nut = vreman_nu<double>(gr, P.vr_c, P.vr_d2);
         if (P.richardson && Smag2 > 0.0) {
-          const double Ri = P.g / G[5] * gr[5][2] / Smag2;
+          const double Ri = P.g * gr[5][2] / (G[5] * Smag2);
           if (Ri > 0.0) {
             const double a = 1.0 - Ri * P.inv_Prt;
             nut *= a > 0.0 ? sqrt(sqrt(a)) : 0.0;
@@ -161,8 +161,9 @@ __global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, do
 
 // n.F1 in direction d (sign applied by the caller) of Eq. eom_compact:
 // [rho u_d, rho u_j u_d + (p - p_r) delta_jd, (rho e + p) u_d, rho q_t u_d].
-__device__ __forceinline__ void flux1_dir(const double Y[6], double pprime, double pr, int d, double f[6]) {
-  const double ud = Y[1 + d] / Y[0];
+__device__ __forceinline__ void flux1_dir(const double Y[6], double rinv, double pprime, double pr, int d,
+                                          double f[6]) {
+  const double ud = Y[1 + d] * rinv;
   f[0] = Y[1 + d];
   f[1] = Y[1] * ud + (d == 0 ? pprime : 0.0);
   f[2] = Y[2] * ud + (d == 1 ? pprime : 0.0);
@@ -198,10 +199,11 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
       }
       const double pp = aux[((size_t)e * 2) * Np + t];
       const double pr = P.p_r[lev];
+      const double rinv = 1.0 / Y[0];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         double f[6];
-        flux1_dir(Y, pp, pr, d, f);
+        flux1_dir(Y, rinv, pp, pr, d, f);
         const double *g2 = F2 + ((size_t)e * 15 + d * 5) * Np + t;
         const double c0 = g2[0];
         sF[0][d][t] = f[0] + c0;
@@ -255,11 +257,11 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
         }
       }
       double fm[6], fp[6], f1s[6];
-      flux1_dir(Ym, pm, pr, d, fm);
-      flux1_dir(Yp, pp, pr, d, fp);
+      const double im = 1.0 / Ym[0], ip = 1.0 / Yp[0];
+      flux1_dir(Ym, im, pm, pr, d, fm);
+      flux1_dir(Yp, ip, pp, pr, d, fp);
       if (FL == 1) {
         // HLLC: n.F1(Y_K) + S_K (U*_K - U_K)
-        const double im = 1.0 / Ym[0], ip = 1.0 / Yp[0];
         const double uM[3] = {Ym[1] * im, Ym[2] * im, Ym[3] * im}, uP[3] = {Yp[1] * ip, Yp[2] * ip, Yp[3] * ip};
         const double nrm[3] = {d == 0 ? sg : 0.0, d == 1 ? sg : 0.0, d == 2 ? sg : 0.0};
         double J[6];
@@ -269,8 +271,8 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
         for (int v = 0; v < 6; ++v) f1s[v] = sg * (K ? fp[v] : fm[v]) + J[v];
       } else {
         // Rusanov (Eq. nonviscFlux): 1/2 n.(F1- + F1+) + lambda/2 (Y- - Y+)
-        const double lm = fabs(Ym[1 + d] / Ym[0]) + cm;
-        const double lp = fabs(Yp[1 + d] / Yp[0]) + cp;
+        const double lm = fabs(Ym[1 + d] * im) + cm;
+        const double lp = fabs(Yp[1 + d] * ip) + cp;
         const double lam = fmax(lm, lp);
 #pragma unroll
         for (int v = 0; v < 6; ++v) f1s[v] = 0.5 * (sg * fm[v] + sg * fp[v]) + 0.5 * lam * (Ym[v] - Yp[v]);

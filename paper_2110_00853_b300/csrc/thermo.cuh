@@ -14,7 +14,19 @@ struct Th64 {
 //   p_v* = p_tr (T/T_tr)^a exp(b (1/T_tr - 1/T)), a = (c_pv - c_pl)/R_v,
 //   b = (L_v0 - (c_pv - c_pl) T_0)/R_v, evaluated as one exp of a log-sum.
 __device__ __forceinline__ double pvsat64(const KParams &P, double T) {
-  return P.pv_ptr * exp(P.pv_a * log(T / P.pv_Ttr) + P.pv_b * (1.0 / P.pv_Ttr - 1.0 / T));
+  return P.pv_ptr * exp(P.pv_a * log(T * P.inv_Ttr) + P.pv_b * (P.inv_Ttr - 1.0 / T));
+}
+
+// True when rho q_t is certainly below rho_vs(T): below the tangent of the
+// nearest tabulated temperature, with a relative margin of 1e-9 that keeps
+// the shortcut clear of the exact test's rounding.
+__device__ __forceinline__ bool surely_unsaturated64(const KParams &P, double rhoq, double T) {
+  if (P.rvs_n <= 0) return false;
+  const double x = (T - P.rvs_T0) / P.rvs_dT;
+  if (!(x >= 0.0 && x <= P.rvs_n - 1)) return false;
+  const int k = (int)(x + 0.5);
+  const double lo = P.rvs_tab[2 * k] + P.rvs_tab[2 * k + 1] * (T - (P.rvs_T0 + k * P.rvs_dT));
+  return rhoq <= (1.0 - 1e-9) * lo;
 }
 
 // Conserved variables -> diagnostic state (Sec. 2): internal energy from
@@ -37,7 +49,7 @@ __device__ __forceinline__ void thermo64(const KParams &P, const double Y[6], do
   double ql = 0.0;
   if (MOIST) {
     const double rRv = Y[0] * P.Rv;
-    if (q > pvsat64(P, T) / (rRv * T)) {
+    if (!surely_unsaturated64(P, Y[5], T) && q > pvsat64(P, T) / (rRv * T)) {
       bool conv = false;
       for (int it = 0; it < P.satadj_max_iter; ++it) {
         const double qs = pvsat64(P, T) / (rRv * T);
@@ -67,8 +79,8 @@ __device__ __forceinline__ void thermo64(const KParams &P, const double Y[6], do
   s.p = Y[0] * Rm * T;
   s.c = sqrt((cvm + Rm) / cvm * Rm * T);
   s.htot = e + Rm * T;
-  const double exner = exp(P.kappa * log(s.p / P.p0));
-  s.thv = T / exner * Rm / P.Rd;
+  // theta_v = T (p/p0)^-kappa R_m / R_d
+  s.thv = T * Rm * P.inv_Rd * exp(-P.kappa * log(s.p * P.inv_p0));
 }
 
 }  // namespace cmles

@@ -54,7 +54,7 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
     // 1 - 1e-5 keeps the shortcut clear of the exact test's rounding.
     const float iTr = fdiv(1.0f, Tr);
     const float slope = (F.pv_a - 1.0f + F.pv_b * iTr) * iTr;
-    const bool dry = T >= 150.0f && T <= 450.0f && Tr >= 150.0f && Tr <= 450.0f &&
+    const bool dry = P.rvs_ok && T >= 150.0f && T <= 450.0f && Tr >= 150.0f && Tr <= 450.0f &&
                      rhoq <= 0.99999f * L[L_RVS] * (1.0f + slope * Tp);
     if (!dry && rhoq > rhovsat32(F, T)) {
       bool conv = false;
