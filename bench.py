@@ -30,13 +30,19 @@ from paper_2110_00853_b300 import inputs as I  # noqa: E402
 WORKLOAD = "c5"
 STAGES = 5
 METRIC = "DG node-stage updates/s at 1 B300 and HBM roofline %, FP32+learned vs FP64 plain"
-# algorithmic bytes per node for each kernel launch (compulsory traffic):
+# algorithmic bytes per node for each kernel launch (compulsory traffic),
+# averaged over the five stages of a step:
 #   gradient pass: read Q, write F2 (15 words) and aux (2 words)
-#   flux/update pass: read Q, F2, aux, read+write dQ, write Q_out
-#   FP32 path: FP32 shadow, F2, aux and dQ; FP64 state read and written once
+#   flux/update pass, FP64 path: read Q, F2, aux; write dQ and Q_out; read dQ
+#     except in the first stage (A_1 = 0): (4 * 41 + 35) words / 5
+#   flux/update pass, FP32 path (FP32 shadow S, FP32 register dQ and step
+#     increment D, FP64 state Q64): read S, F2, aux (23 words) in every stage;
+#     stage 1 writes dQ, D, S (+18); stages 2-4 read dQ, D and write dQ, D, S
+#     (+30); stage 5 reads dQ, D, reads and writes Q64 and writes S (+12 + 24
+#     FP32 words for Q64): (41 + 3 * 53 + 65) words / 5 = 53 words
 BYTES = {
-    "fp64": {"grad": (6 + 15 + 2) * 8, "rhs": (6 + 15 + 2 + 12 + 6) * 8},
-    "fp32": {"grad": (6 + 15 + 2) * 4, "rhs": (6 + 15 + 2 + 12 + 6) * 4 + 12 * 8},
+    "fp64": {"grad": (6 + 15 + 2) * 8, "rhs": (4 * 41 + 35) * 8 / 5},
+    "fp32": {"grad": (6 + 15 + 2) * 4, "rhs": (41 + 3 * 53 + 65) * 4 / 5},
 }
 VARIANTS = {"fp32acc64_mlp": ("fp32", "mlp"), "fp32acc64_sl": ("fp32", "sl"), "fp64_sl": ("fp64", "sl")}
 DTYPE = {"fp32": "f32", "fp64": "f64"}

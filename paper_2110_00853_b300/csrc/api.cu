@@ -109,7 +109,7 @@ struct cmles_t {
   float *S32[2] = {nullptr, nullptr};
   int scur = 0;
   bool shadow_valid = false;
-  float *dQ32 = nullptr, *F2_32 = nullptr, *aux32 = nullptr, *lev32 = nullptr, *dH32 = nullptr;
+  float *dQ32 = nullptr, *D32 = nullptr, *F2_32 = nullptr, *aux32 = nullptr, *lev32 = nullptr, *dH32 = nullptr;
   double *qref64 = nullptr;
   double *rho_r = nullptr, *p_r = nullptr, *qt_r = nullptr, *tau_lev = nullptr, *tau_col = nullptr;
   double *wq = nullptr, *partials = nullptr, *budget_out = nullptr, *prof = nullptr;
@@ -285,6 +285,7 @@ void fill_kparams(cmles_handle h) {
   K.lev32 = h->lev32;
   K.dH32 = h->dH32;
   K.qref64 = h->qref64;
+  K.D32 = h->D32;
   K.rho_r = h->rho_r;
   K.p_r = h->p_r;
   K.tau_lev = h->tau_lev;
@@ -723,6 +724,7 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
     ALLOC(h->S32[0], n32 * 6 * sizeof(float));
     ALLOC(h->S32[1], n32 * 6 * sizeof(float));
     ALLOC(h->dQ32, n32 * 6 * sizeof(float));
+    ALLOC(h->D32, n32 * 6 * sizeof(float));
     ALLOC(h->F2_32, n32 * 15 * sizeof(float));
     ALLOC(h->aux32, n32 * 2 * sizeof(float));
   }
@@ -815,7 +817,7 @@ cmles_status cmles_destroy(cmles_handle h) {
   }
   void *bufs[] = {h->Q[0],   h->Q[1],    h->dQ,      h->F2,       h->aux,     h->rho_r,    h->p_r,
                   h->qt_r,   h->tau_lev, h->tau_col, h->wq,       h->flags,   h->partials, h->budget_out,
-                  h->prof,   h->S32[0],  h->S32[1],  h->dQ32,     h->F2_32,   h->aux32,    h->lev32,
+                  h->prof,   h->S32[0],  h->S32[1],  h->dQ32,     h->D32,      h->F2_32,   h->aux32,    h->lev32,
                   h->dH32,   h->qref64,  h->mlp_dev, h->geo32,   h->node32,  h->wJn,      h->rvs_tab};
   for (void *b : bufs)
     if (b) cudaFree(b);
@@ -1110,7 +1112,7 @@ cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev
   if (!h->have_ref) return fail(h, CMLES_ERR_STATE, "cmles_tendency: reference state not set");
   if (h->prm.closure == CMLES_CLOSURE_MLP && !h->have_mlp)
     return fail(h, CMLES_ERR_STATE, "cmles_tendency: closure weights not set");
-  StageCoef sc = {0.0, 0.0, 0.0};
+  StageCoef sc = {0.0, 0.0, 0.0, 0};
   if (h->fp32) {
     // shadow of Q_dev into the idle shadow buffer; the handle's state is untouched
     float *tmp = h->S32[1 - h->scur];
@@ -1137,7 +1139,7 @@ cmles_status cmles_step(cmles_handle h, int nsteps) {
   }
   for (int s = 0; s < nsteps; ++s) {
     for (int k = 0; k < 5; ++k) {
-      StageCoef sc = {kLsrkA[k], kLsrkB[k], h->prm.dt};
+      StageCoef sc = {kLsrkA[k], kLsrkB[k], h->prm.dt, k == 4};
       cmles_status st;
       if (h->fp32) {
         st = run_stage_pair32(h, h->S32[h->scur], h->S32[1 - h->scur], nullptr, sc, true);

@@ -79,6 +79,8 @@ struct KParams {
   // the 5 x 5 differences of rho e_r + p_r along z, per level FP64 offsets
   const float *lev32, *dH32;
   const double *qref64;
+  // FP32 path: sum of the step's stage increments B_s dQ_s so far [E][6][128]
+  float *D32;
   const struct MlpPacked *mlp;  // learned-closure weights (closure == 2)
   // curvilinear meshes (dg_curved32.cu): per-node metrics [E][10][128]
   // ((J grad xi_r)_c at 3r + c, J at 9) and per-node tables [E][24][128]
@@ -134,8 +136,11 @@ __device__ __forceinline__ double node_z(const KParams &P, int ez, int k) {
 }
 
 // LSRK(5,4) stage coefficients (Carpenter & Kennedy 1994, Sec. 3.2).
+// last: the final stage of a step, which adds the step's accumulated
+// increment to the FP64 state (FP32 path).
 struct StageCoef {
   double A, B, dt;
+  int last;
 };
 
 

@@ -242,7 +242,9 @@ __device__ __forceinline__ void flux1_normal32(const float s[6], float rho_r, fl
 }
 
 // FL: numerical flux of F1, 0 Rusanov, 1 HLLC
-template <int N, bool UPDATE, int FL>
+// UPD as in k_rhs32: 0 right-hand side, 1 stage (FP32 step increment),
+// 2 last stage of the step (FP64 accumulation).  FL: 0 Rusanov, 1 HLLC.
+template <int N, int UPD, int FL>
 __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, const float *__restrict__ F2,
                                                    const float *__restrict__ aux, float *__restrict__ dQ,
                                                    double *__restrict__ Q64, float *__restrict__ Sout,
@@ -414,14 +416,21 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
         const size_t i64 = ((size_t)e * 6 + v) * Np + t;
-        if (UPDATE) {
+        if (UPD) {
           const size_t i32 = ((size_t)e * 6 + v) * kNP + t;
           const float dq = (sc.A != 0.0 ? (float)sc.A * dQ[i32] : 0.f) + (float)sc.dt * R[v];
-          dQ[i32] = dq;
-          const double qn = Q64[i64] + sc.B * (double)dq;
-          Q64[i64] = qn;
-          const double ref = v == 0 ? qr[0] : (v == 4 ? qr[Np] : (v == 5 ? qr[2 * Np] : 0.0));
-          Sout[i32] = (float)(qn - ref);
+          const float Bdq = (float)sc.B * dq;
+          const float D0 = sc.A != 0.0 ? P.D32[i32] : 0.f;
+          if (UPD == 1) {
+            dQ[i32] = dq;
+            P.D32[i32] = D0 + Bdq;
+            Sout[i32] = sS[v][t] + Bdq;
+          } else {
+            const double qn = Q64[i64] + (double)(D0 + Bdq);
+            Q64[i64] = qn;
+            const double ref = v == 0 ? qr[0] : (v == 4 ? qr[Np] : (v == 5 ? qr[2 * Np] : 0.0));
+            Sout[i32] = (float)(qn - ref);
+          }
         } else {
           Rout[i64] = (double)R[v];
         }
@@ -477,27 +486,31 @@ cudaError_t launch_grad32c(const float *S, float *F2, float *aux, const KParams 
   return cudaGetLastError();
 }
 
-template <bool UPDATE, int FL>
+template <int UPD, int FL>
 static void k_rhs32c_instance(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
                            double *Rout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
   static int grid = 0;
-  if (!grid) grid = grid_for((const void *)k_rhs32c<4, UPDATE, FL>, 1 << 30, 0);
-  k_rhs32c<4, UPDATE, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+  if (!grid) grid = grid_for((const void *)k_rhs32c<4, UPD, FL>, 1 << 30, 0);
+  k_rhs32c<4, UPD, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+}
+
+template <int FL>
+static void k_rhs32c_dispatch(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
+                              double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+  if (!update)
+    k_rhs32c_instance<0, FL>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+  else if (sc.last)
+    k_rhs32c_instance<2, FL>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+  else
+    k_rhs32c_instance<1, FL>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
 }
 
 cudaError_t launch_rhs32c(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
-                         double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
-  if (update) {
-    if (P.flux == 1)
-      k_rhs32c_instance<true, 1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
-    else
-      k_rhs32c_instance<true, 0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
-  } else {
-    if (P.flux == 1)
-      k_rhs32c_instance<false, 1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
-    else
-      k_rhs32c_instance<false, 0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
-  }
+                          double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+  if (P.flux == 1)
+    k_rhs32c_dispatch<1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
+  else
+    k_rhs32c_dispatch<0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
   return cudaGetLastError();
 }
 

@@ -17,8 +17,12 @@
 //   * the energy flux (rho e + p) u = H_r u + H' u: along x and y H_r is
 //     constant on the derivative line and factors out; along z the line
 //     differences H_r(m) - H_r(k) come from an FP64-built table.
-// The LSRK register dQ is FP32; the state Q is accumulated in FP64 and the
-// shadow rewritten from it.  Element traversal: 4 x 4 column tiles.
+// The LSRK register dQ is FP32.  Within a step the stage increments B_s dQ_s
+// are summed in FP32 into D (relative to the increments, not to the state)
+// and the shadow is advanced by them; the last stage adds D to the FP64 state
+// Q once per step and rewrites the shadow from it.  On B300, where FP64 runs
+// at 1/64 of the FP32 rate, four FP64 operations per variable and stage took
+// a fifth of the flux pass.  Element traversal: 4 x 4 column tiles.
 #include "common.cuh"
 #include "launch.h"
 #include "mlp.cuh"
@@ -207,8 +211,11 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
   if (fail) atomicAdd(P.flags, 1);
 }
 
-// FL: numerical flux of F1, 0 Rusanov, 1 HLLC
-template <int N, bool UPDATE, int FL>
+// UPD: 0 right-hand side only; 1 LSRK stage, the step's increment
+// D = sum_s B_s dQ_s carried in FP32 and the shadow advanced by B_s dQ_s;
+// 2 last stage of the step, Q = Q_step_start + D added in FP64 and the shadow
+// rewritten from it.  FL: numerical flux of F1, 0 Rusanov, 1 HLLC.
+template <int N, int UPD, int FL>
 __global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, const float *__restrict__ F2,
                                                   const float *__restrict__ aux, float *__restrict__ dQ,
                                                   double *__restrict__ Q64, float *__restrict__ Sout,
@@ -231,14 +238,17 @@ __global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, c
     const float *L = P.lev32 + (size_t)(ez * Nq + (k < Nq ? k : 0)) * L_NF;
     float sv[6];
     // the update's inputs, loaded with the element's first loads so that
-    // their latency overlaps the flux computation
-    float dq0[6];
+    // their latency overlaps the flux computation (the first stage has A = 0
+    // and starts the step: no register or increment to read)
+    float dq0[6], D0[6];
     double q0[6];
-    if (UPDATE && t < Np) {
+    if (UPD && t < Np) {
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
-        dq0[v] = sc.A != 0.0 ? dQ[((size_t)e * 6 + v) * kNP + t] : 0.f;
-        q0[v] = Q64[((size_t)e * 6 + v) * Np + t];
+        const size_t i32 = ((size_t)e * 6 + v) * kNP + t;
+        dq0[v] = sc.A != 0.0 ? dQ[i32] : 0.f;
+        D0[v] = sc.A != 0.0 ? P.D32[i32] : 0.f;
+        if (UPD == 2) q0[v] = Q64[((size_t)e * 6 + v) * Np + t];
       }
     }
     if (t < Np) {
@@ -390,14 +400,21 @@ __global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, c
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
         const size_t i64 = ((size_t)e * 6 + v) * Np + t;
-        if (UPDATE) {
+        if (UPD) {
           const size_t i32 = ((size_t)e * 6 + v) * kNP + t;
           const float dq = (float)sc.A * dq0[v] + (float)sc.dt * R[v];
-          dQ[i32] = dq;
-          const double qn = q0[v] + sc.B * (double)dq;
-          Q64[i64] = qn;
-          const double ref = v == 0 ? qr[0] : (v == 4 ? qr[1] : (v == 5 ? qr[2] : 0.0));
-          Sout[i32] = (float)(qn - ref);
+          const float Bdq = (float)sc.B * dq;
+          if (UPD == 1) {
+            dQ[i32] = dq;
+            P.D32[i32] = D0[v] + Bdq;
+            Sout[i32] = sS[v][t] + Bdq;
+          } else {
+            // the register is not read again before the next step's first stage
+            const double qn = q0[v] + (double)(D0[v] + Bdq);
+            Q64[i64] = qn;
+            const double ref = v == 0 ? qr[0] : (v == 4 ? qr[1] : (v == 5 ? qr[2] : 0.0));
+            Sout[i32] = (float)(qn - ref);
+          }
         } else {
           Rout[i64] = (double)R[v];
         }
@@ -460,27 +477,31 @@ cudaError_t launch_grad32(const float *S, float *F2, float *aux, const KParams &
   return cudaGetLastError();
 }
 
-template <bool UPDATE, int FL>
+template <int UPD, int FL>
 static void k_rhs32_instance(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
                            double *Rout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
   static int grid = 0;
-  if (!grid) grid = grid_for((const void *)k_rhs32<4, UPDATE, FL>, 1 << 30, 0);
-  k_rhs32<4, UPDATE, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+  if (!grid) grid = grid_for((const void *)k_rhs32<4, UPD, FL>, 1 << 30, 0);
+  k_rhs32<4, UPD, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+}
+
+template <int FL>
+static void k_rhs32_dispatch(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
+                             double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+  if (!update)
+    k_rhs32_instance<0, FL>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+  else if (sc.last)
+    k_rhs32_instance<2, FL>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+  else
+    k_rhs32_instance<1, FL>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
 }
 
 cudaError_t launch_rhs32(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
                          double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
-  if (update) {
-    if (P.flux == 1)
-      k_rhs32_instance<true, 1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
-    else
-      k_rhs32_instance<true, 0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
-  } else {
-    if (P.flux == 1)
-      k_rhs32_instance<false, 1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
-    else
-      k_rhs32_instance<false, 0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
-  }
+  if (P.flux == 1)
+    k_rhs32_dispatch<1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
+  else
+    k_rhs32_dispatch<0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
   return cudaGetLastError();
 }
 
