@@ -31,3 +31,32 @@ def test_create_rejects_bad_arguments_without_gpu_work():
     m = cmles.make_mesh(dict(N=9, nex=1, ney=1, nez=1, Lx=1.0, Ly=1.0, Lz=1.0))
     assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == 1   # CMLES_ERR_ARG
     assert L.cmles_create(None, ctypes.byref(P), ctypes.byref(h)) == 1
+
+
+def test_create_rejects_unsupported_combinations_without_gpu_work():
+    """Argument checks of cmles_create run before any device allocation."""
+    L = cmles.load()
+    h = ctypes.c_void_p()
+    good = dict(N=4, nex=2, ney=2, nez=2, Lx=1000.0, Ly=1000.0, Lz=1000.0)
+
+    def status(mesh=good, precision="fp64", **kw):
+        m = cmles.make_mesh(mesh)
+        P = cmles.make_params(kw, precision)
+        return L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h))
+
+    ERR_ARG = 1
+    assert status(closure="mlp") == ERR_ARG                         # learned closure runs in the FP32 kernels
+    assert status(mesh=dict(good, warp=True)) == ERR_ARG             # warped meshes run on the FP32 path
+    assert status(mesh=dict(good, warp=True), precision="fp32", closure="vreman") == ERR_ARG
+    assert status(mesh=dict(good, periodic=(1, 1, 1)), precision="fp32") == ERR_ARG
+    P = cmles.make_params({}, "fp64")
+    P.flux = 7
+    m = cmles.make_mesh(good)
+    assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == ERR_ARG
+    P = cmles.make_params(dict(filter_order=8, filter_vars=0b0001), "fp64")   # density is not filterable
+    assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == ERR_ARG
+    P = cmles.make_params(dict(filter_order=-1), "fp64")
+    assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == ERR_ARG
+    P = cmles.make_params({}, "fp64")
+    P.precision = 5
+    assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == ERR_ARG
