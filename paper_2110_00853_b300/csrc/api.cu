@@ -270,6 +270,7 @@ void fill_kparams(cmles_handle h) {
   F.CsDelta2 = (float)K.CsDelta2;
   F.Delta = (float)Delta;
   F.vr_c = (float)K.vr_c;
+  F.inv_w0 = (float)(1.0 / h->w[0]);
   for (int d = 0; d < 3; ++d) F.vr_d2[d] = (float)K.vr_d2[d];
   K.mlp = h->mlp_dev;
   F.inv_Prt = (float)K.inv_Prt;
@@ -1112,7 +1113,7 @@ cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev
   if (!h->have_ref) return fail(h, CMLES_ERR_STATE, "cmles_tendency: reference state not set");
   if (h->prm.closure == CMLES_CLOSURE_MLP && !h->have_mlp)
     return fail(h, CMLES_ERR_STATE, "cmles_tendency: closure weights not set");
-  StageCoef sc = {0.0, 0.0, 0.0, 0};
+  StageCoef sc = {0.0, 0.0, 0.0, 0, 0.f, 0.f, 0.f, 1};
   if (h->fp32) {
     // shadow of Q_dev into the idle shadow buffer; the handle's state is untouched
     float *tmp = h->S32[1 - h->scur];
@@ -1139,7 +1140,8 @@ cmles_status cmles_step(cmles_handle h, int nsteps) {
   }
   for (int s = 0; s < nsteps; ++s) {
     for (int k = 0; k < 5; ++k) {
-      StageCoef sc = {kLsrkA[k], kLsrkB[k], h->prm.dt, k == 4};
+      StageCoef sc = {kLsrkA[k], kLsrkB[k], h->prm.dt, k == 4, (float)kLsrkA[k], (float)kLsrkB[k],
+                      (float)h->prm.dt, kLsrkA[k] == 0.0};
       cmles_status st;
       if (h->fp32) {
         st = run_stage_pair32(h, h->S32[h->scur], h->S32[1 - h->scur], nullptr, sc, true);

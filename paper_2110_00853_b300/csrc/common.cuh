@@ -22,6 +22,7 @@ struct KF {
   float CsDelta2, inv_Prt, Delta;
   float vr_c, vr_d2[3];
   float jac[3], lift[3];
+  float inv_w0;  // 1 / w_0, the LGL end weight
   float u_relax[3], Omega[3];
   float E_water, E_energy;
 };
@@ -138,9 +139,14 @@ __device__ __forceinline__ double node_z(const KParams &P, int ez, int k) {
 // LSRK(5,4) stage coefficients (Carpenter & Kennedy 1994, Sec. 3.2).
 // last: the final stage of a step, which adds the step's accumulated
 // increment to the FP64 state (FP32 path).
+// The FP32 kernels use the FP32 copies Af, Bf, dtf (converted once on the
+// host: an FP64 operation per thread costs 64 FP32 ones on B300) and
+// first (A = 0: no register to read).
 struct StageCoef {
   double A, B, dt;
   int last;
+  float Af, Bf, dtf;
+  int first;
 };
 
 

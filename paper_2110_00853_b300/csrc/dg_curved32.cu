@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
         const float ax = Ja[3 * d], ay = Ja[3 * d + 1], az = Ja[3 * d + 2];
         const float mag = sqrtf(ax * ax + ay * ay + az * az);
         const float nv[3] = {sg * ax / mag, sg * ay / mag, sg * az / mag};
-        const float Lf = mag * Jinv / (float)P.w[0];
+        const float Lf = mag * Jinv * F.inv_w0;
         if (sNb[f] >= 0) {
 #pragma unroll
           for (int v = 0; v < 6; ++v) {
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
 #pragma unroll
         for (int v = 0; v < 6; ++v) f1s[v] = 0.5f * (fm[v] + fp[v]) + 0.5f * lam * (sm[v] - sp[v]);
       }
-      const float Lf = mag / (gn[9 * kNP] * (float)P.w[0]);
+      const float Lf = mag * F.inv_w0 / gn[9 * kNP];
       const int c_of_v[6] = {0, 1, 2, 3, 4, 0};
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
@@ -418,9 +418,9 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
         const size_t i64 = ((size_t)e * 6 + v) * Np + t;
         if (UPD) {
           const size_t i32 = ((size_t)e * 6 + v) * kNP + t;
-          const float dq = (sc.A != 0.0 ? (float)sc.A * dQ[i32] : 0.f) + (float)sc.dt * R[v];
-          const float Bdq = (float)sc.B * dq;
-          const float D0 = sc.A != 0.0 ? P.D32[i32] : 0.f;
+          const float dq = (sc.first ? 0.f : sc.Af * dQ[i32]) + sc.dtf * R[v];
+          const float Bdq = sc.Bf * dq;
+          const float D0 = sc.first ? 0.f : P.D32[i32];
           if (UPD == 1) {
             dQ[i32] = dq;
             P.D32[i32] = D0 + Bdq;

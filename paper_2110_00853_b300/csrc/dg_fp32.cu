@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, c
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
         const size_t i32 = ((size_t)e * 6 + v) * kNP + t;
-        dq0[v] = sc.A != 0.0 ? dQ[i32] : 0.f;
-        D0[v] = sc.A != 0.0 ? P.D32[i32] : 0.f;
+        dq0[v] = sc.first ? 0.f : dQ[i32];
+        D0[v] = sc.first ? 0.f : P.D32[i32];
         if (UPD == 2) q0[v] = Q64[((size_t)e * 6 + v) * Np + t];
       }
     }
@@ -402,8 +402,8 @@ __global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, c
         const size_t i64 = ((size_t)e * 6 + v) * Np + t;
         if (UPD) {
           const size_t i32 = ((size_t)e * 6 + v) * kNP + t;
-          const float dq = (float)sc.A * dq0[v] + (float)sc.dt * R[v];
-          const float Bdq = (float)sc.B * dq;
+          const float dq = sc.Af * dq0[v] + sc.dtf * R[v];
+          const float Bdq = sc.Bf * dq;
           if (UPD == 1) {
             dQ[i32] = dq;
             P.D32[i32] = D0[v] + Bdq;
