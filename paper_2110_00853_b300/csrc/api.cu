@@ -271,6 +271,13 @@ void fill_kparams(cmles_handle h) {
   F.Delta = (float)Delta;
   F.vr_c = (float)K.vr_c;
   F.inv_w0 = (float)(1.0 / h->w[0]);
+  {
+    double c = 1.0;
+    for (int n = 1; n <= 6; ++n) {
+      c *= (-K.kappa - (n - 1)) / n;
+      F.kpow[n - 1] = (float)c;
+    }
+  }
   for (int d = 0; d < 3; ++d) F.vr_d2[d] = (float)K.vr_d2[d];
   K.mlp = h->mlp_dev;
   F.inv_Prt = (float)K.inv_Prt;

@@ -23,6 +23,7 @@ struct KF {
   float vr_c, vr_d2[3];
   float jac[3], lift[3];
   float inv_w0;  // 1 / w_0, the LGL end weight
+  float kpow[6];  // binomial coefficients of (1 + v)^-kappa: kpow[n-1] = C(-kappa, n), n = 1..6
   float u_relax[3], Omega[3];
   float E_water, E_energy;
 };

@@ -23,6 +23,19 @@ __device__ __forceinline__ float pvsat32(const KF &F, float T) {
 // saturation vapour density p_v*(T) / (R_v T)
 __device__ __forceinline__ float rhovsat32(const KF &F, float T) { return fdiv(pvsat32(F, T) * F.inv_Rv, T); }
 
+// (1 + v)^-kappa - 1: the binomial series to v^6 for |v| <= 1/32 (the
+// omitted terms are below 3e-10 of the result there), expm1(-kappa log1p(v))
+// otherwise.
+__device__ __forceinline__ float pow_kappa_m1(const KF &F, float v) {
+  if (fabsf(v) <= 0.03125f) {
+    float r = F.kpow[5];
+#pragma unroll
+    for (int n = 4; n >= 0; --n) r = fmaf(r, v, F.kpow[n]);
+    return r * v;
+  }
+  return expm1f(-F.kappa * log1pf(v));
+}
+
 // Thermodynamics of one node from its deviation state s and its level table L.
 template <bool MOIST>
 __device__ __forceinline__ void thermo32(const KParams &P, const float *__restrict__ L, const float s[6], Th32 &o,
@@ -103,7 +116,7 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
   const float ra = fdiv(Tp, Tr), rb = fdiv(drRm, L[L_RHORM]), rc = fdiv(rp, rho_r);
   // theta_v / theta_v,r = (1 + u)(1 + w), w = (p/p_r)^-kappa - 1
   const float u = fdiv(ra + rb + ra * rb - rc, 1.0f + rc);
-  const float w = expm1f(-F.kappa * log1pf(fdiv(pp, pr)));
+  const float w = pow_kappa_m1(F, fdiv(pp, pr));
   o.thvp = L[L_THV] * (u + w + u * w);  // theta_v - theta_v,r
 }
 
