@@ -46,6 +46,13 @@ BYTES = {
 }
 VARIANTS = {"fp32acc64_mlp": ("fp32", "mlp"), "fp32acc64_sl": ("fp32", "sl"), "fp64_sl": ("fp64", "sl")}
 DTYPE = {"fp32": "f32", "fp64": "f64"}
+# DRAM bytes per node of one launch (dram__bytes_read.sum + dram__bytes_write.sum
+# from one ncu capture on a 40 x 40 x 20-element sub-box of the box, 4M nodes,
+# divided by the nodes; the traffic is per node, so it scales to the full box by
+# the node count).  Only kernels whose every launch does the same work: the
+# gradient pass.  Remove an entry when its kernel changes.
+TRAFFIC_B_PER_NODE = {("fp32acc64_mlp", "grad"): 92.75, ("fp32acc64_sl", "grad"): 88.26,
+                      ("fp64_sl", "grad"): 185.57}
 
 
 def measured_peaks():
@@ -290,6 +297,8 @@ def main():
     dom = max(range(2), key=lambda k: kt["ms"][k])
     avg_ms = kt["ms"][dom] / max(kt["count"][dom], 1)
     achieved = head["nodes"] * BYTES[prec][kinds[dom]] / (avg_ms / 1e3) / 1e9
+    tb = TRAFFIC_B_PER_NODE.get((variants[0][0], kinds[dom]))
+    traffic = tb * head["nodes"] if tb is not None else None
     out_variants = {}
     for (name, vprec, _), r in zip(variants, results.values()):
         v = whole_job_rate(r["nodes"], world, args.steps, r["ms"])
@@ -317,7 +326,7 @@ def main():
                             "elements": head["nodes"] // 125, "nodes_per_gpu": head["nodes"],
                             "l2": "inputs larger than L2 (state alone 12 GB)", "parallelism": f"replicas{world}"},
                     roofline={"bound": "hbm", "kernel": kinds[dom], "achieved": achieved, "peak": hbm,
-                              "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                              "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                               "peak_source": f"{peak_kind} hbm_gbs"},
                     cpu_baseline=cb, e2e=e2e, gpu_launches=head["launches"], clocks=head["clocks"],
                     variants=out_variants)
