@@ -199,7 +199,7 @@ cmles_status cmles_diagnostics(cmles_handle h, cmles_diag *out);
  * Synchronises the stream. */
 cmles_status cmles_profiles(cmles_handle h, double *out_host);
 
-/* Learned SGS closure (not in the paper; the workload's extension of Sec. 4):
+/* Learned SGS closure (not in the paper; an extension of Sec. 4):
  * a per-node network 13 -> 64 -> 64 -> 2 with SiLU hidden activations, BF16
  * weights and activations and FP32 accumulation on tensor cores, evaluated
  * inside the FP32 gradient pass when params.closure == CMLES_CLOSURE_MLP

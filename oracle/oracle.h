@@ -15,8 +15,8 @@
  *   Sec. 4   Smagorinsky-Lilly and Vreman closures with the Richardson correction
  *   App. A   wall boundary conditions, prescribed wall fluxes, Rayleigh sponge
  *   App. C   Favre (density-weighted) horizontal means
- * Readings where the paper is silent or garbled are listed in the design doc and
- * restated at the point of use.
+ * Readings where the paper is silent or garbled are stated at the point of
+ * use.
  *
  * Compiled with -O2 -ffp-contract=off (IEEE round-to-nearest, no FMA).
  */

@@ -6,9 +6,9 @@ the Adam update all run in the library's CUDA kernels (cmles_step,
 cmles_closure_samples, cmles_mlp_loss_grad, cmles_mlp_adam); this module
 chooses the batches and the normalisation constants.
 
-The paper has no learned closure; the workload asks for a network
+The paper has no learned closure.  This extension of its Sec. 4 is a network
 13 -> 64 -> 64 -> 2 trained on box-filtered fine-resolution runs, with
-Smagorinsky-Lilly kept as fallback and as the judge of its error.
+Smagorinsky-Lilly kept as the fallback and as the yardstick of its error.
 """
 import math
 

@@ -1,7 +1,7 @@
 // Training samples for the learned SGS closure from a fine-resolution run.
 //
-// The paper has no learned closure; these are the targets the workload asks
-// for ("box-filtered 4x"): the fine field is averaged with a top-hat of width
+// The paper has no learned closure; these are the targets of its extension,
+// a 4x box filter: the fine field is averaged with a top-hat of width
 // Delta_c = H_c / N (the coarse node spacing, 4 fine node spacings for a
 // factor-4 coarsening) centred on every node of the coarse mesh, using the
 // fine LGL quadrature weights.  From the filtered moments

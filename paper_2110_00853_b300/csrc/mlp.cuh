@@ -1,7 +1,7 @@
 // Learned SGS closure network on tensor cores: 13 -> 64 -> 64 -> 2, SiLU
 // hidden activations, BF16 weights and activations, FP32 accumulation.
-// (The paper has no learned closure; this network is the workload's
-// extension of the method, with Smagorinsky-Lilly kept as fallback.)
+// (The paper has no learned closure; this network extends its Sec. 4, with
+// Smagorinsky-Lilly kept as fallback.)
 //
 // One warp evaluates 32 rows (two m16 tiles) with mma.sync m16n8k16 BF16.
 // The accumulator fragment of two neighbouring n8 tiles is exactly the A

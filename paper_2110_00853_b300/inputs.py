@@ -5,7 +5,7 @@ synthetic configurations (mesh, physical set-up, seeds) and draws the random
 tables a case needs; both the CUDA path and the CPU oracle evaluate the
 initial states from these descriptions with their own code.
 
-Configurations (sizes as in the workload list of the project):
+Configurations:
   c1  dry 3D warm bubble, 4x4x4 elements, N=4, 2 km cube
   c2  moist convective layer, 32x32x16 elements, 6.4x6.4x3.2 km, surface fluxes
   c3  flow over a Gaussian ridge, warped 128x16x64 elements, 40x4x20 km
@@ -13,7 +13,8 @@ Configurations (sizes as in the workload list of the project):
   c5  throughput box, 160x160x80 elements (256M nodes), stratified, random-phase
       k^-5/3 velocity
 The paper's own BOMEX case needs an external case definition that is not
-reproduced; c2 is a synthetic stand-in with the shape the workload list gives.
+reproduced; c2 is a synthetic stand-in of the same shape (a moist mixed layer
+under an inversion, with surface heat and moisture fluxes).
 """
 import math
 

@@ -4,7 +4,7 @@ A fine run (FP32 path, 4x finer than the coarse grid, moist layer with a
 k^-5/3 random-phase velocity field reaching the coarse subgrid scales) is
 top-hat filtered onto the coarse nodes by the library's filter kernel; the
 closure network is trained on one such run with the library's BF16
-tensor-core forward/backward kernels and Adam, and judged on a second run with
+tensor-core forward/backward kernels and Adam, and evaluated on a second run with
 different random phases against the filtered subgrid targets, next to
 Smagorinsky-Lilly (C_s = 0.21 with the Richardson correction) evaluated on the
 same filtered gradients.  A priori test: the error measure is the relative L2

@@ -2,7 +2,8 @@
 the same seeded inputs, element by element.
 
 Tolerance (FP64 path): relative L2 per tendency variable <= 1e-12, the bar
-the workload description sets for the plain FP64 method.  Inputs come from the
+for the plain FP64 method (a few hundred roundings of 1e-16 each, with the
+oracle's different summation order).  Inputs come from the
 oracle's own initial-state code (or are seeded fuzz on top of it); no expected
 value comes from the CUDA path.
 """
