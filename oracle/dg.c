@@ -516,6 +516,8 @@ int orc_rhs(orc_solver *s, const double *Q, double *RHS, int form) {
           }
           if (P->flux == ORC_FLUX_HLLC)
             orc_hllc(P, Ym, Yp, s->z[q], s->p_r[q], nrm, F1s);
+          else if (P->flux == ORC_FLUX_ROE)
+            orc_roe(P, Ym, Yp, s->z[q], s->p_r[q], nrm, F1s);
           else
             orc_rusanov(P, Ym, Yp, s->z[q], s->p_r[q], nrm, F1s);
           F2s[0] = f2s[0];

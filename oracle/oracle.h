@@ -34,6 +34,7 @@
 #define ORC_CLOSURE_VREMAN 3
 #define ORC_FLUX_RUSANOV 0
 #define ORC_FLUX_HLLC 1
+#define ORC_FLUX_ROE 2
 
 typedef struct {
   int N;                      /* polynomial order */
@@ -97,6 +98,12 @@ void orc_rusanov(const orc_params *p, const double Ym[6], const double Yp[6], do
  * Davis wave-speed estimates (reading). */
 void orc_hllc(const orc_params *p, const double Ym[6], const double Yp[6], double z, double pr, const double n[3],
               double out[6]);
+
+/* Roe numerical flux n.F1* (Roe 1981; named in Sec. 3.1): flux Jacobian at
+ * Roe's averaged state with the frozen (q_l = 0) moist equation of state
+ * (reading), no entropy fix. */
+void orc_roe(const orc_params *p, const double Ym[6], const double Yp[6], double z, double pr, const double n[3],
+             double out[6]);
 
 /* ---- exponential filter (Eq. exponential_filter) ---- */
 /* One-dimensional filter matrix F = V diag(exp(-alpha (k/N)^order)) V^-1,

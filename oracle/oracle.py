@@ -57,7 +57,7 @@ class Case(C.Structure):
 
 
 CLOSURE = {"none": 0, "sl": 1, "mlp": 2, "vreman": 3}
-FLUX = {"rusanov": 0, "hllc": 1}
+FLUX = {"rusanov": 0, "hllc": 1, "roe": 2}
 
 # Table t:constants; g, p0, p_tr, T_tr are readings (the table omits them).
 CONSTANTS = dict(g=9.81, p0=1.0e5, Rd=287.0, Rv=462.0, cvd=717.5, cvv=1397.5, cvl=4181.0, cvi=2100.0,
@@ -84,6 +84,8 @@ def _declare(L):
     L.orc_filter_matrix.restype = None
     L.orc_filter.argtypes = [C.c_void_p, _DP, C.c_int, C.c_double, C.c_int]
     L.orc_filter.restype = None
+    L.orc_roe.argtypes = [C.POINTER(Params), _DP, _DP, C.c_double, C.c_double, _DP, _DP]
+    L.orc_roe.restype = None
     L.orc_hllc.argtypes = [C.POINTER(Params), _DP, _DP, C.c_double, C.c_double, _DP, _DP]
     L.orc_hllc.restype = None
     L.orc_vreman.argtypes = [C.POINTER(Params), _DP, C.c_double, C.c_double, _DP]
@@ -213,6 +215,13 @@ def filter_matrix(N, order, alpha):
     F = np.zeros((N + 1) * (N + 1))
     lib().orc_filter_matrix(N, _p(np.ascontiguousarray(xi, float)), order, alpha, _p(F))
     return F.reshape(N + 1, N + 1)
+
+
+def roe(P, Ym, Yp, z, pr, n):
+    out = np.zeros(6)
+    lib().orc_roe(C.byref(P), _p(np.ascontiguousarray(Ym, float)), _p(np.ascontiguousarray(Yp, float)),
+                  z, pr, _p(np.ascontiguousarray(n, float)), _p(out))
+    return out
 
 
 def hllc(P, Ym, Yp, z, pr, n):

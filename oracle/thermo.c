@@ -190,6 +190,60 @@ void orc_hllc(const orc_params *p, const double Ym[6], const double Yp[6], doubl
   for (int v = 0; v < 6; ++v) out[v] = f[v] + S * (Us[v] - Y[v]);
 }
 
+/* Roe flux (Roe 1981), n.F* = (n.F(Y-) + n.F(Y+))/2 - |A| (Y+ - Y-)/2 with A
+ * the flux Jacobian along n at Roe's averaged state: rho^ = sqrt(rho- rho+)
+ * and sqrt(rho)-weighted u, total specific enthalpy H = (rho e_tot + p)/rho
+ * and q_t.  Reading (the paper names the flux only): the averaged state uses
+ * the frozen moist equation of state (q_l = 0),
+ *   p = (R_m/c_vm) (E - rho |u|^2/2 - rho Phi - rho q I_v0) + rho R_m T_0,
+ * whose derivatives at fixed other conserved variables are, with
+ * G = R_m/c_vm,
+ *   dp/dE = G, dp/d(rho u) = -G u,
+ *   dp/d(rho q) = (R_v - R_d - G (c_vv - c_vd)) (T - T_0) - G I_v0 + (R_v - R_d) T_0,
+ *   dp/drho = (R_d - G c_vd) (T - T_0) + G (|u|^2/2 - Phi) + R_d T_0,
+ * T from H, and c^2 = dp/drho + u.dp/d(rho u) + H dp/dE + q dp/d(rho q).
+ * The acoustic strengths alpha_-+ = (dp -+ rho^ c du_n)/(2 c^2) (dp and
+ * du_n the jumps linearised at the averaged state) with eigenvectors
+ * r_-+ = (1, u -+ c n, H -+ u_n c, q), and every other wave travels at u_n:
+ *   |A| dY = |u_n - c| a_- r_- + |u_n + c| a_+ r_+ + |u_n| (dY - a_- r_- - a_+ r_+).
+ * For dry air this is Roe's exact linearisation.  No entropy fix. */
+void orc_roe(const orc_params *p, const double Ym[6], const double Yp[6], double z, double pr, const double n[3],
+             double out[6]) {
+  orc_thermo_state sL, sR;
+  orc_thermo(p, Ym, z, &sL);
+  orc_thermo(p, Yp, z, &sR);
+  double fL[6], fR[6];
+  orc_flux1_normal(p, Ym, z, pr, n, fL);
+  orc_flux1_normal(p, Yp, z, pr, n, fR);
+  double wL = sqrt(sL.rho), wR = sqrt(sR.rho), iw = 1.0 / (wL + wR);
+  double rh = wL * wR;
+  double u[3];
+  for (int c = 0; c < 3; ++c) u[c] = (wL * sL.u[c] + wR * sR.u[c]) * iw;
+  double HL = (Ym[4] + sL.p) / sL.rho, HR = (Yp[4] + sR.p) / sR.rho;
+  double H = (wL * HL + wR * HR) * iw;
+  double q = (wL * Ym[5] / sL.rho + wR * Yp[5] / sR.rho) * iw;
+  double Phi = p->g * z, uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  double Iv0 = p->Lv0 - p->Rv * p->T0;
+  double Rm = p->Rd + q * (p->Rv - p->Rd), cvm = p->cvd + q * (p->cvv - p->cvd), G = Rm / cvm;
+  /* H = |u|^2/2 + Phi + c_vm (T - T_0) + q I_v0 + R_m T */
+  double T = (H - 0.5 * uu - Phi - q * Iv0 + cvm * p->T0) / (cvm + Rm);
+  double p_rho = (p->Rd - G * p->cvd) * (T - p->T0) + G * (0.5 * uu - Phi) + p->Rd * p->T0;
+  double p_w = ((p->Rv - p->Rd) - G * (p->cvv - p->cvd)) * (T - p->T0) - G * Iv0 + (p->Rv - p->Rd) * p->T0;
+  double c2 = p_rho - G * uu + G * H + q * p_w, c = sqrt(c2);
+  double dY[6];
+  for (int v = 0; v < 6; ++v) dY[v] = Yp[v] - Ym[v];
+  double dp = p_rho * dY[0] - G * (u[0] * dY[1] + u[1] * dY[2] + u[2] * dY[3]) + G * dY[4] + p_w * dY[5];
+  double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  double dun = (n[0] * dY[1] + n[1] * dY[2] + n[2] * dY[3] - un * dY[0]) / rh;
+  double am = (dp - rh * c * dun) / (2.0 * c2), ap = (dp + rh * c * dun) / (2.0 * c2);
+  double rm[6] = {1.0, u[0] - c * n[0], u[1] - c * n[1], u[2] - c * n[2], H - un * c, q};
+  double rp[6] = {1.0, u[0] + c * n[0], u[1] + c * n[1], u[2] + c * n[2], H + un * c, q};
+  for (int v = 0; v < 6; ++v) {
+    double D = fabs(un - c) * am * rm[v] + fabs(un + c) * ap * rp[v] + fabs(un) * (dY[v] - am * rm[v] - ap * rp[v]);
+    out[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * D;
+  }
+}
+
 /* Richardson factor f_b (Eq. richardson) for |S|^2 = 2 S:S > 0. */
 static double richardson_factor(const orc_params *p, double dthvdz, double thv, double Smag2) {
   double N2 = p->g / thv * dthvdz;

@@ -57,7 +57,7 @@ def test_rest_state_stays_at_rest(orc):
 
 
 @pytest.mark.parametrize("name,sub,flux", [("c1", None, "rusanov"), ("c2", (3, 3, 8), "rusanov"),
-                                           ("c2", (3, 3, 8), "hllc")])
+                                           ("c2", (3, 3, 8), "hllc"), ("c2", (3, 3, 8), "roe")])
 def test_conservation_periodic_free_slip(orc, name, sub, flux):
     m = I.mesh(name) if sub is None else I.sub_mesh(name, *sub)
     ph = I.physics(name)
@@ -89,7 +89,7 @@ def test_surface_flux_budget(orc):
 
 
 @pytest.mark.parametrize("name,sub,flux", [("c1", None, "rusanov"), ("c2", (3, 3, 8), "rusanov"),
-                                           ("c1", None, "hllc")])
+                                           ("c1", None, "hllc"), ("c1", None, "roe")])
 def test_weak_equals_strong_form(orc, name, sub, flux):
     m = I.mesh(name) if sub is None else I.sub_mesh(name, *sub)
     S, Q, rr, pr, _ = orc.from_inputs(m, dict(I.physics(name), flux=flux), I.case(name))
