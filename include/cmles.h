@@ -49,8 +49,10 @@ typedef enum {
 
 enum { CMLES_CLOSURE_NONE = 0, CMLES_CLOSURE_SL = 1, CMLES_CLOSURE_MLP = 2, CMLES_CLOSURE_VREMAN = 3 };
 /* Numerical flux of F1 on element faces (Sec. 3.1): Rusanov (Eq. nonviscFlux,
- * lambda/2 reading) or HLLC (Toro, Spruce & Speares 1994, Davis wave speeds). */
-enum { CMLES_FLUX_RUSANOV = 0, CMLES_FLUX_HLLC = 1 };
+ * lambda/2 reading), HLLC (Toro, Spruce & Speares 1994, Davis wave speeds) or
+ * Roe (Roe 1981; Jacobian at Roe's averaged state with the frozen moist
+ * equation of state, no entropy fix). */
+enum { CMLES_FLUX_RUSANOV = 0, CMLES_FLUX_HLLC = 1, CMLES_FLUX_ROE = 2 };
 
 /* Arithmetic of the RHS kernels.
  *   CMLES_FP64       all FP64 ("plain" method).

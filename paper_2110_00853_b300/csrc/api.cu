@@ -688,7 +688,8 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   if (params->closure != CMLES_CLOSURE_NONE && params->closure != CMLES_CLOSURE_SL &&
       params->closure != CMLES_CLOSURE_MLP && params->closure != CMLES_CLOSURE_VREMAN)
     return CMLES_ERR_ARG;
-  if (params->flux != CMLES_FLUX_RUSANOV && params->flux != CMLES_FLUX_HLLC) return CMLES_ERR_ARG;
+  if (params->flux != CMLES_FLUX_RUSANOV && params->flux != CMLES_FLUX_HLLC && params->flux != CMLES_FLUX_ROE)
+    return CMLES_ERR_ARG;
   if (params->filter_order < 0 || !(params->filter_alpha >= 0.0) || (params->filter_vars & ~0xE) != 0)
     return CMLES_ERR_ARG;
   // Vreman's directional lengths are those of the flat elements

@@ -220,4 +220,47 @@ __device__ __forceinline__ int hllc_jump(T rL, const T (&uL)[3], T qL, T eL, T p
   return K;
 }
 
+
+// Roe flux (Roe 1981; named in Sec. 3.1): the dissipation |A| dY of
+// n.F* = (n.F(Y-) + n.F(Y+))/2 - |A| dY / 2, A the flux Jacobian along n at
+// Roe's averaged state (sqrt(rho)-weighted u, total specific enthalpy H and
+// q_t) with the frozen (q_l = 0) moist equation of state,
+//   p = G (E - rho |u|^2/2 - rho Phi - rho q I_v0) + rho R_m T_0,  G = R_m/c_vm,
+// whose derivatives give c^2 = p_rho + u.p_m + H p_E + q p_w.  Acoustic
+// strengths a_-+ = (dp -+ rho^ c du_n)/(2 c^2) on r_-+ = (1, u -+ c n,
+// H -+ u_n c, q); every other wave moves at u_n:
+//   |A| dY = |u_n - c| a_- r_- + |u_n + c| a_+ r_+ + |u_n| (dY - a_- r_- - a_+ r_+).
+template <typename T>
+struct RoeConst {
+  T Rd, dR, cvd, dc, T0, Iv0;  // R_d, R_v - R_d, c_vd, c_vv - c_vd, T_0, L_v0 - R_v T_0
+};
+template <typename T>
+__device__ __forceinline__ void roe_dissipation(T rL, const T (&uL)[3], T qL, T HL, T rR, const T (&uR)[3], T qR,
+                                                T HR, const T (&dY)[6], T Phi, const T (&n)[3],
+                                                const RoeConst<T> &k, T D[6]) {
+  const T wL = sqrt(rL), wR = sqrt(rR), iw = T(1) / (wL + wR), rh = wL * wR;
+  T u[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) u[c] = (wL * uL[c] + wR * uR[c]) * iw;
+  const T H = (wL * HL + wR * HR) * iw, q = (wL * qL + wR * qR) * iw;
+  const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T Rm = k.Rd + q * k.dR, cvm = k.cvd + q * k.dc, G = Rm / cvm;
+  const T Tt = (H - T(0.5) * uu - Phi - q * k.Iv0 + cvm * k.T0) / (cvm + Rm);
+  const T p_rho = (k.Rd - G * k.cvd) * (Tt - k.T0) + G * (T(0.5) * uu - Phi) + k.Rd * k.T0;
+  const T p_w = (k.dR - G * k.dc) * (Tt - k.T0) - G * k.Iv0 + k.dR * k.T0;
+  const T c2 = p_rho - G * uu + G * H + q * p_w, c = sqrt(c2);
+  const T dp = p_rho * dY[0] - G * (u[0] * dY[1] + u[1] * dY[2] + u[2] * dY[3]) + G * dY[4] + p_w * dY[5];
+  const T un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  const T dun = (n[0] * dY[1] + n[1] * dY[2] + n[2] * dY[3] - un * dY[0]) / rh;
+  const T am = (dp - rh * c * dun) / (T(2) * c2), ap = (dp + rh * c * dun) / (T(2) * c2);
+  const T lm = fabs(un - c), lp = fabs(un + c), l0 = fabs(un);
+  const T rm[6] = {T(1), u[0] - c * n[0], u[1] - c * n[1], u[2] - c * n[2], H - un * c, q};
+  const T rp[6] = {T(1), u[0] + c * n[0], u[1] + c * n[1], u[2] + c * n[2], H + un * c, q};
+#pragma unroll
+  for (int v = 0; v < 6; ++v) {
+    const T wm = am * rm[v], wp = ap * rp[v];
+    D[v] = lm * wm + lp * wp + l0 * (dY[v] - wm - wp);
+  }
+}
+
 }  // namespace cmles

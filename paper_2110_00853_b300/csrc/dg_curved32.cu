@@ -243,7 +243,7 @@ __device__ __forceinline__ void flux1_normal32(const float s[6], float rho_r, fl
 
 // FL: numerical flux of F1, 0 Rusanov, 1 HLLC
 // UPD as in k_rhs32: 0 right-hand side, 1 stage (FP32 step increment),
-// 2 last stage of the step (FP64 accumulation).  FL: 0 Rusanov, 1 HLLC.
+// 2 last stage of the step (FP64 accumulation).  FL: 0 Rusanov, 1 HLLC, 2 Roe.
 template <int N, int UPD, int FL>
 __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, const float *__restrict__ F2,
                                                    const float *__restrict__ aux, float *__restrict__ dQ,
@@ -365,6 +365,19 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
                                        (rhoq_r + sp[5]) * iP, (Er + sp[4]) * iP, pr + pp, cp, pp - pm, nv, J);
 #pragma unroll
         for (int v = 0; v < 6; ++v) f1s[v] = (K ? fp[v] : fm[v]) + J[v];
+      } else if (FL == 2) {
+        // Roe: 1/2 n.(F1- + F1+) - 1/2 |A| (Y+ - Y-)
+        const float rM = rho_r + sm[0], rP = rho_r + sp[0];
+        const float iM = fdiv(1.0f, rM), iP = fdiv(1.0f, rP);
+        const float uM[3] = {sm[1] * iM, sm[2] * iM, sm[3] * iM}, uP[3] = {sp[1] * iP, sp[2] * iP, sp[3] * iP};
+        float dY[6], D[6];
+#pragma unroll
+        for (int v = 0; v < 6; ++v) dY[v] = sp[v] - sm[v];
+        const RoeConst<float> rk = {F.Rd, F.Rv - F.Rd, F.cvd, F.cvv - F.cvd, F.T0, F.Iv0};
+        roe_dissipation<float>(rM, uM, (rhoq_r + sm[5]) * iM, (Hr + sm[4] + pm) * iM, rP, uP, (rhoq_r + sp[5]) * iP,
+                               (Hr + sp[4] + pp) * iP, dY, tn[L_GZ * kNP], nv, rk, D);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) f1s[v] = 0.5f * (fm[v] + fp[v]) - 0.5f * D[v];
       } else {
         const float lam = fmaxf(fabsf(um) + cm, fabsf(up) + cp);
 #pragma unroll
@@ -507,7 +520,9 @@ static void k_rhs32c_dispatch(const float *S, const float *F2, const float *aux,
 
 cudaError_t launch_rhs32c(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
                           double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
-  if (P.flux == 1)
+  if (P.flux == 2)
+    k_rhs32c_dispatch<2>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
+  else if (P.flux == 1)
     k_rhs32c_dispatch<1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
   else
     k_rhs32c_dispatch<0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);

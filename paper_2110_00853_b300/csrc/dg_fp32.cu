@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
 // UPD: 0 right-hand side only; 1 LSRK stage, the step's increment
 // D = sum_s B_s dQ_s carried in FP32 and the shadow advanced by B_s dQ_s;
 // 2 last stage of the step, Q = Q_step_start + D added in FP64 and the shadow
-// rewritten from it.  FL: numerical flux of F1, 0 Rusanov, 1 HLLC.
+// rewritten from it.  FL: numerical flux of F1, 0 Rusanov, 1 HLLC, 2 Roe.
 template <int N, int UPD, int FL>
 __global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, const float *__restrict__ F2,
                                                   const float *__restrict__ aux, float *__restrict__ dQ,
@@ -333,6 +333,21 @@ __global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, c
 #pragma unroll
         for (int v = 0; v < 6; ++v) f1s[v] = sg * (K ? fp[v] : fm[v]) + J[v];
         ref4 = K ? sg * Lf[L_H] * (um - up) : 0.f;
+      } else if (FL == 2) {
+        // Roe: 1/2 n.(F1- + F1+) - 1/2 |A| (Y+ - Y-), full states from the deviations
+        const float rM = rho_r + sm[0], rP = rho_r + sp[0];
+        const float iM = fdiv(1.0f, rM), iP = fdiv(1.0f, rP);
+        const float uM[3] = {sm[1] * iM, sm[2] * iM, sm[3] * iM}, uP[3] = {sp[1] * iP, sp[2] * iP, sp[3] * iP};
+        const float nrm[3] = {d == 0 ? sg : 0.f, d == 1 ? sg : 0.f, d == 2 ? sg : 0.f};
+        float dY[6], D[6];
+#pragma unroll
+        for (int v = 0; v < 6; ++v) dY[v] = sp[v] - sm[v];
+        const RoeConst<float> rk = {F.Rd, F.Rv - F.Rd, F.cvd, F.cvv - F.cvd, F.T0, F.Iv0};
+        roe_dissipation<float>(rM, uM, (rhoq_r + sm[5]) * iM, (Lf[L_H] + sm[4] + pm) * iM, rP, uP,
+                               (rhoq_r + sp[5]) * iP, (Lf[L_H] + sp[4] + pp) * iP, dY, Lf[L_GZ], nrm, rk, D);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) f1s[v] = 0.5f * (sg * fm[v] + sg * fp[v]) - 0.5f * D[v];
+        ref4 = 0.5f * sg * Lf[L_H] * (um - up);
       } else {
         const float lam = fmaxf(fabsf(um) + cm, fabsf(up) + cp);
 #pragma unroll
@@ -498,7 +513,9 @@ static void k_rhs32_dispatch(const float *S, const float *F2, const float *aux, 
 
 cudaError_t launch_rhs32(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
                          double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
-  if (P.flux == 1)
+  if (P.flux == 2)
+    k_rhs32_dispatch<2>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
+  else if (P.flux == 1)
     k_rhs32_dispatch<1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
   else
     k_rhs32_dispatch<0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);

@@ -172,7 +172,7 @@ __device__ __forceinline__ void flux1_dir(const double Y[6], double rinv, double
   f[5] = Y[5] * ud;
 }
 
-// FL: numerical flux of F1, 0 Rusanov, 1 HLLC
+// FL: numerical flux of F1, 0 Rusanov, 1 HLLC, 2 Roe
 template <int N, bool UPDATE, int FL>
 __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, const double *__restrict__ F2,
                                                const double *__restrict__ aux, double *__restrict__ dQ,
@@ -269,6 +269,18 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
                                         Yp[4] * ip, pp + pr, cp, pp - pm, nrm, J);
 #pragma unroll
         for (int v = 0; v < 6; ++v) f1s[v] = sg * (K ? fp[v] : fm[v]) + J[v];
+      } else if (FL == 2) {
+        // Roe: 1/2 n.(F1- + F1+) - 1/2 |A| (Y+ - Y-)
+        const double uM[3] = {Ym[1] * im, Ym[2] * im, Ym[3] * im}, uP[3] = {Yp[1] * ip, Yp[2] * ip, Yp[3] * ip};
+        const double nrm[3] = {d == 0 ? sg : 0.0, d == 1 ? sg : 0.0, d == 2 ? sg : 0.0};
+        double dY[6], D[6];
+#pragma unroll
+        for (int v = 0; v < 6; ++v) dY[v] = Yp[v] - Ym[v];
+        const RoeConst<double> rk = {P.Rd, P.Rv - P.Rd, P.cvd, P.cvv - P.cvd, P.T0, P.Iv0};
+        roe_dissipation<double>(Ym[0], uM, Ym[5] * im, (Ym[4] + pm + pr) * im, Yp[0], uP, Yp[5] * ip,
+                                (Yp[4] + pp + pr) * ip, dY, P.g * node_z(P, ez, d == 2 ? a : t2), nrm, rk, D);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) f1s[v] = 0.5 * (sg * fm[v] + sg * fp[v]) - 0.5 * D[v];
       } else {
         // Rusanov (Eq. nonviscFlux): 1/2 n.(F1- + F1+) + lambda/2 (Y- - Y+)
         const double lm = fabs(Ym[1 + d] * im) + cm;
@@ -372,12 +384,16 @@ static void rhs64_instance(const double *Q, const double *F2, const double *aux,
 cudaError_t launch_rhs64(const double *Q, const double *F2, const double *aux, double *dQ, double *Qout,
                          const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
   if (update) {
-    if (P.flux == 1)
+    if (P.flux == 2)
+      rhs64_instance<true, 2>(Q, F2, aux, dQ, Qout, sc, P, s);
+    else if (P.flux == 1)
       rhs64_instance<true, 1>(Q, F2, aux, dQ, Qout, sc, P, s);
     else
       rhs64_instance<true, 0>(Q, F2, aux, dQ, Qout, sc, P, s);
   } else {
-    if (P.flux == 1)
+    if (P.flux == 2)
+      rhs64_instance<false, 2>(Q, F2, aux, dQ, Qout, sc, P, s);
+    else if (P.flux == 1)
       rhs64_instance<false, 1>(Q, F2, aux, dQ, Qout, sc, P, s);
     else
       rhs64_instance<false, 0>(Q, F2, aux, dQ, Qout, sc, P, s);

@@ -118,10 +118,11 @@ def test_tendency_vreman(orc, richardson):
     _compare_rhs(S, Q, G, 1e-12)
 
 
+@pytest.mark.parametrize("flux", ["hllc", "roe"])
 @pytest.mark.parametrize("case", ["walls", "moist"])
-def test_tendency_hllc(orc, case):
-    # HLLC faces (Sec. 3.1): walls on all sides with rotation, or the ragged
-    # moist sub-box with saturation, sponge and surface fluxes
+def test_tendency_hllc_roe(orc, case, flux):
+    # HLLC or Roe faces (Sec. 3.1): walls on all sides with rotation, or the
+    # ragged moist sub-box with saturation, sponge and surface fluxes
     if case == "walls":
         m = I.sub_mesh("c1", 3, 2, 3)
         m["periodic"] = (0, 0, 0)
@@ -132,10 +133,10 @@ def test_tendency_hllc(orc, case):
         m = I.sub_mesh("c2", 5, 3, 16)
         ph = I.physics("c2")
         name = "c2"
-    ph["flux"] = "hllc"
+    ph["flux"] = flux
     S, Q, G = _setup(orc, name, m, phys=ph, fuzz_seed=8)
     errs, R_gpu, R_orc = _compare_rhs(S, Q, G, 1e-12)
-    # HLLC and Rusanov differ on these states
+    # the flux differs from Rusanov on these states
     ph2 = dict(ph, flux="rusanov")
     S2, _, _ = _setup(orc, name, m, phys=ph2, fuzz_seed=8)
     R_rus, _ = S2.rhs(Q)

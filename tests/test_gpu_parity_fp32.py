@@ -104,8 +104,9 @@ def test_fp32_tendency_vreman(orc, richardson):
     print("vreman fp32 rel L2", _compare(S, Q, G))
 
 
+@pytest.mark.parametrize("flux", ["hllc", "roe"])
 @pytest.mark.parametrize("case", ["walls", "moist"])
-def test_fp32_tendency_hllc(orc, case):
+def test_fp32_tendency_hllc_roe(orc, case, flux):
     if case == "walls":
         m = I.sub_mesh("c1", 3, 2, 3)
         m["periodic"] = (0, 0, 0)
@@ -116,9 +117,9 @@ def test_fp32_tendency_hllc(orc, case):
         m = I.sub_mesh("c2", 5, 3, 16)
         ph = I.physics("c2")
         name = "c2"
-    ph["flux"] = "hllc"
+    ph["flux"] = flux
     S, Q, G = _setup(orc, name, m, phys=ph, fuzz_seed=18)
-    print("hllc fp32", case, "rel L2", _compare(S, Q, G))
+    print(flux, "fp32", case, "rel L2", _compare(S, Q, G))
 
 
 def test_fp32_tendency_c5_subbox(orc):

@@ -47,7 +47,7 @@ def _setup(orc, fuzz=True, flux="rusanov"):
     return m, S, Q, G
 
 
-@pytest.mark.parametrize("flux", ["rusanov", "hllc"])
+@pytest.mark.parametrize("flux", ["rusanov", "hllc", "roe"])
 def test_warped_tendency_parity(orc, flux):
     m, S, Q, G = _setup(orc, flux=flux)
     J = S.geometry()["J"]
