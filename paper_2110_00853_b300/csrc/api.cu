@@ -127,6 +127,7 @@ struct cmles_t {
   MlpPacked *mlp_dev = nullptr;
   ExpFilter expf = {};
   double *rvs_tab = nullptr;
+  double *exr = nullptr;  // (p_r/p0)^-kappa per node level
   bool have_mlp = false;
   // curvilinear (warped) meshes: device tables and host geometry (FP64)
   bool curved = false;
@@ -208,6 +209,14 @@ void fill_kparams(cmles_handle h) {
   K.inv_Rd = 1.0 / p.Rd;
   K.inv_p0 = 1.0 / p.p0;
   K.inv_Ttr = 1.0 / p.Ttr;
+  {
+    double c = 1.0;
+    for (int n = 1; n <= 11; ++n) {
+      c *= (-K.kappa - (n - 1)) / n;
+      K.kpow64[n - 1] = c;
+    }
+  }
+  K.exr = h->exr;
   K.Prt = p.Prt;
   K.inv_Prt = 1.0 / p.Prt;
   K.richardson = p.richardson;
@@ -757,6 +766,7 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   ALLOC(h->wq, h->Np * sizeof(double));
   ALLOC(h->flags, 16 * sizeof(int));
   ALLOC(h->rvs_tab, kRvsN * 2 * sizeof(double));
+  ALLOC(h->exr, nlev * sizeof(double));
   h->budget_nblocks = budget_blocks(h->nodes);
   ALLOC(h->partials, (size_t)h->budget_nblocks * 7 * sizeof(double));
   ALLOC(h->budget_out, 8 * sizeof(double));
@@ -796,6 +806,7 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   if (e == cudaSuccess) e = cudaMemcpy(h->wq, wq.data(), h->Np * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(h->flags, 0, 16 * sizeof(int));
   if (e == cudaSuccess) e = build_rvs_table(h);
+  if (e == cudaSuccess) e = cudaMemset(h->exr, 0, nlev * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(h->mlp_dev, 0, sizeof(MlpPacked));
   if (e == cudaSuccess && h->dQ) e = cudaMemset(h->dQ, 0, n6 * sizeof(double));
   if (e == cudaSuccess && h->dQ32) e = cudaMemset(h->dQ32, 0, (size_t)E * 128 * 6 * sizeof(float));
@@ -827,7 +838,7 @@ cmles_status cmles_destroy(cmles_handle h) {
   void *bufs[] = {h->Q[0],   h->Q[1],    h->dQ,      h->F2,       h->aux,     h->rho_r,    h->p_r,
                   h->qt_r,   h->tau_lev, h->tau_col, h->wq,       h->flags,   h->partials, h->budget_out,
                   h->prof,   h->S32[0],  h->S32[1],  h->dQ32,     h->D32,      h->F2_32,   h->aux32,    h->lev32,
-                  h->dH32,   h->qref64,  h->mlp_dev, h->geo32,   h->node32,  h->wJn,      h->rvs_tab};
+                  h->dH32,   h->qref64,  h->mlp_dev, h->geo32,   h->node32,  h->wJn,      h->rvs_tab,  h->exr};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete h;
@@ -867,6 +878,11 @@ cmles_status cmles_set_reference(cmles_handle h, const double *rho_r, const doub
   }
   CK(cudaMemcpyAsync(h->rho_r, rho_r, nlev * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->p_r, p_r, nlev * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  {
+    std::vector<double> ex(nlev);
+    for (size_t l = 0; l < nlev; ++l) ex[l] = exp(-h->K.kappa * log(p_r[l] / h->prm.p0));
+    CK(cudaMemcpy(h->exr, ex.data(), nlev * sizeof(double), cudaMemcpyHostToDevice));
+  }
   if (qt_r)
     CK(cudaMemcpyAsync(h->qt_r, qt_r, nlev * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   else

@@ -96,7 +96,7 @@ __global__ void k_profiles(const double *__restrict__ Q, const KParams P, int N,
     for (int v = 0; v < 6; ++v) Y[v] = Q[(e * 6 + v) * Np + n];
     Th64 s;
     int fail = 0;
-    thermo64<MOIST>(P, Y, node_z(P, ez, k), s, fail);
+    thermo64<MOIST>(P, Y, node_z(P, ez, k), ez * Nq + k, s, fail);
     const double th = s.thv * P.Rd / (P.Rd * (1.0 - s.q) + P.Rv * (s.q - s.ql));
     const double w = P.w[i] * P.w[j];
     double *a = accum + (size_t)lev * 12;

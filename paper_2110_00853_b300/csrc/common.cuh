@@ -45,6 +45,10 @@ struct KParams {
   double pv_ptr, pv_Ttr, pv_a, pv_b;  // p_v* = p_tr exp(a ln(T/T_tr) + b (1/T_tr - 1/T))
   double dcp;        // c_pv - c_pl
   double inv_Rd, inv_p0, inv_Ttr;
+  // (p/p0)^-kappa = (p_r/p0)^-kappa (1 + p'/p_r)^-kappa: exr[level] is the
+  // first factor, kpow64[n-1] = C(-kappa, n) (n = 1..11) the series of the second
+  const double *exr;
+  double kpow64[11];
   // tangents of the saturation vapour density rho_vs(T) = p_v*(T)/(R_v T) at
   // T_k = rvs_T0 + k rvs_dT, k < rvs_n: [k][2] = (rho_vs(T_k), d rho_vs/dT);
   // rho_vs is convex in T on the tabulated range (checked on the host when the

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, do
 #pragma unroll
       for (int v = 0; v < 6; ++v) Y[v] = Q[((size_t)e * 6 + v) * Np + t];
       Th64 s;
-      thermo64<MOIST>(P, Y, node_z(P, ez, k), s, fail);
+      thermo64<MOIST>(P, Y, node_z(P, ez, k), ez * Nq + k, s, fail);
       G[0] = s.u[0];
       G[1] = s.u[1];
       G[2] = s.u[2];
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, do
       for (int v = 0; v < 6; ++v) Yp[v] = Q[((size_t)nb * 6 + v) * Np + nn];
       const int ezn = nb / (P.nex * P.ney);
       Th64 s;
-      thermo64<MOIST>(P, Yp, node_z(P, ezn, d == 2 ? a_nb : t2), s, fail);
+      thermo64<MOIST>(P, Yp, node_z(P, ezn, d == 2 ? a_nb : t2), ezn * Nq + (d == 2 ? a_nb : t2), s, fail);
       sGf[f][0][fn] = s.u[0];
       sGf[f][1][fn] = s.u[1];
       sGf[f][2][fn] = s.u[2];

@@ -37,7 +37,7 @@ __global__ void k_primitives(const double *__restrict__ Q, float *__restrict__ p
     for (int v = 0; v < 6; ++v) Y[v] = Q[(e * 6 + v) * Np + n];
     Th64 s;
     int fail = 0;
-    thermo64<MOIST>(P, Y, node_z(P, ez, k), s, fail);
+    thermo64<MOIST>(P, Y, node_z(P, ez, k), ez * Nq + k, s, fail);
     float *o = prim + e * 4 * Np + n;
     o[0] = (float)s.u[0];
     o[Np] = (float)s.u[1];

@@ -34,8 +34,25 @@ __device__ __forceinline__ bool surely_unsaturated64(const KParams &P, double rh
 // (closed form when unsaturated, Newton with analytic derivative otherwise,
 // liquid only), R_m (Eq. R_m), p (Eq. eos), sound speed, h_tot = e_tot + p/rho,
 // theta_v = T / (p/p0)^{R_d/c_pd} * R_m / R_d.
+// (p/p0)^-kappa at node level lev: the level's (p_r/p0)^-kappa times the
+// binomial series of (1 + v)^-kappa, v = p/p_r - 1, to v^11 for |v| <= 1/32
+// (omitted terms below 1e-17 relative); exp(-kappa log(p/p0)) otherwise.
+__device__ __forceinline__ double exner_inv64(const KParams &P, double p, int lev) {
+  const double pr = P.p_r[lev];
+  const double v = (p - pr) / pr;
+  if (fabs(v) <= 0.03125) {
+    double r = P.kpow64[10];
+#pragma unroll
+    for (int n = 9; n >= 0; --n) r = fma(r, v, P.kpow64[n]);
+    return P.exr[lev] * (1.0 + r * v);
+  }
+  return exp(-P.kappa * log(p * P.inv_p0));
+}
+
+// lev: the node level ez (N + 1) + k of the node, whose reference pressure
+// and Exner factor the theta_v evaluation uses.
 template <bool MOIST>
-__device__ __forceinline__ void thermo64(const KParams &P, const double Y[6], double z, Th64 &s, int &fail) {
+__device__ __forceinline__ void thermo64(const KParams &P, const double Y[6], double z, int lev, Th64 &s, int &fail) {
   const double rinv = 1.0 / Y[0];
   s.u[0] = Y[1] * rinv;
   s.u[1] = Y[2] * rinv;
@@ -80,7 +97,7 @@ __device__ __forceinline__ void thermo64(const KParams &P, const double Y[6], do
   s.c = sqrt((cvm + Rm) / cvm * Rm * T);
   s.htot = e + Rm * T;
   // theta_v = T (p/p0)^-kappa R_m / R_d
-  s.thv = T * Rm * P.inv_Rd * exp(-P.kappa * log(s.p * P.inv_p0));
+  s.thv = T * Rm * P.inv_Rd * exner_inv64(P, s.p, lev);
 }
 
 }  // namespace cmles
