@@ -1,0 +1,64 @@
+"""Failure detection without a GPU fault: a non-finite value planted in the
+state on the host, and a Newton iteration cap too small for the saturated
+nodes of the moist layer.  Both are reported by cmles_diagnostics as status
+codes (CMLES_ERR_NONFINITE, CMLES_ERR_SATADJ) with the context left usable:
+after a good state is set the next report is clean."""
+import numpy as np
+import pytest
+
+from paper_2110_00853_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ERR_SATADJ, ERR_NONFINITE = 4, 5
+
+
+def _levels(arr, mesh):
+    Nq = mesh["N"] + 1
+    return np.array([arr[ez * mesh["nex"] * mesh["ney"], k * Nq * Nq] for ez in range(mesh["nez"])
+                     for k in range(Nq)])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_nonfinite_state_is_reported_and_cleared(orc, precision):
+    from paper_2110_00853_b300 import cmles
+    m = I.sub_mesh("c2", 3, 3, 8)
+    ph = I.physics("c2")
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case("c2"))
+    G = cmles.Solver(m, ph, precision=precision)
+    G.set_reference(_levels(rr, m), _levels(pr, m), _levels(Q[:, 5] / Q[:, 0], m))
+    bad = Q.copy()
+    bad[3, 4, 17] = np.nan
+    G.set_state(torch.from_numpy(bad).cuda())
+    d = G.diagnostics(raise_on_error=False)
+    assert d["status"] == ERR_NONFINITE and d["nonfinite"]
+    with pytest.raises(cmles.CmlesError):
+        G.diagnostics()
+    G.set_state(torch.from_numpy(Q).cuda())
+    d = G.diagnostics(raise_on_error=False)
+    assert d["status"] == 0 and not d["nonfinite"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_newton_cap_failures_are_counted(orc, precision):
+    from paper_2110_00853_b300 import cmles
+    m = I.sub_mesh("c2", 5, 3, 16)
+    ph = I.physics("c2")
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case("c2"))
+    S.rhs(Q)
+    assert (S.intermediates()["aux"][:, 3] > 0).mean() > 0.1          # saturated nodes present
+    ph1 = dict(ph, satadj_max_iter=1)
+    G = cmles.Solver(m, ph1, precision=precision)
+    G.set_reference(_levels(rr, m), _levels(pr, m), _levels(Q[:, 5] / Q[:, 0], m))
+    G.tendency(torch.from_numpy(Q).cuda())
+    d = G.diagnostics(raise_on_error=False)
+    assert d["status"] == ERR_SATADJ and d["satadj_failures"] > 0
+    # the counter is cleared by the report; the default cap converges
+    G2 = cmles.Solver(m, ph, precision=precision)
+    G2.set_reference(_levels(rr, m), _levels(pr, m), _levels(Q[:, 5] / Q[:, 0], m))
+    G2.tendency(torch.from_numpy(Q).cuda())
+    d2 = G2.diagnostics(raise_on_error=False)
+    assert d2["status"] == 0 and d2["satadj_failures"] == 0
+    d = G.diagnostics(raise_on_error=False)
+    assert d["satadj_failures"] == 0
