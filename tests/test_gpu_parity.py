@@ -212,6 +212,23 @@ def test_determinism(orc):
     assert np.array_equal(a, b)
 
 
+def test_kernel_timing_and_launch_counters(orc):
+    # per-pass CUDA-event timing (the numbers bench.py reports) and the
+    # launch counter: two passes per stage, five stages per step
+    S, Q, G = _setup(orc, "c1", I.mesh("c1"), fuzz_seed=7)
+    G.set_state(torch.from_numpy(Q).cuda())
+    G.step(1)
+    n0 = G.launch_count()
+    G.enable_timing(True)
+    G.kernel_times()
+    G.step(3)
+    kt = G.kernel_times()
+    G.enable_timing(False)
+    assert G.launch_count() - n0 == 3 * 5 * 2
+    assert kt["count"][0] == 15 and kt["count"][1] == 15
+    assert kt["ms"][0] > 0.0 and kt["ms"][1] > 0.0
+
+
 def test_conservation_on_gpu(orc):
     m = I.sub_mesh("c2", 4, 4, 16)
     ph = I.physics("c2")
