@@ -58,8 +58,12 @@ enum { CMLES_FLUX_RUSANOV = 0, CMLES_FLUX_HLLC = 1, CMLES_FLUX_ROE = 2 };
  *   CMLES_FP64       all FP64 ("plain" method).
  *   CMLES_FP32_ACC64 volume, face and gradient kernels in FP32 on a state
  *                    stored as FP32 deviations from the hydrostatic reference
- *                    (the reference subtraction done in FP64); the
- *                    Runge-Kutta state accumulated in FP64. */
+ *                    (the reference subtraction done in FP64).  The state
+ *                    itself is FP64: within a step the stage increments
+ *                    B_s dQ_s are summed in FP32, and the last stage adds the
+ *                    sum to the FP64 state and rewrites the FP32 shadow from
+ *                    it, so at every step boundary the FP64 state is the
+ *                    authority (get_state, diagnostics, checkpoints). */
 enum { CMLES_FP64 = 0, CMLES_FP32_ACC64 = 1 };
 
 /* Structured hexahedral mesh of nex x ney x nez elements (Sec. 3.1).  With
@@ -187,7 +191,10 @@ cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev
 
 /* Advance the handle's state by nsteps LSRK(5,4) steps of params.dt.  Each
  * stage is two kernels: the gradient/closure pass and the flux-divergence pass
- * with the fused stage update.  Asynchronous. */
+ * with the fused stage update; with filter_order > 0 the exponential filter
+ * follows every step.  Every step starts from the FP64 state alone (the first
+ * stage has A = 0), so a state saved between calls resumes bit-identically.
+ * Asynchronous. */
 cmles_status cmles_step(cmles_handle h, int nsteps);
 
 /* FP64 budgets, non-finite flag and Newton failures of the current state.
