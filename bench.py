@@ -140,6 +140,25 @@ def whole_job_rate(nodes_per_rank, world, steps, ms):
     return nodes_per_rank * world * STAGES * steps / (ms / 1e3)
 
 
+def fp64_peak(torch, n=8192, reps=5):
+    """FP64 GEMM rate of the GPU (cuBLAS DGEMM, 2 n^3 flops, best of reps
+    after a warm-up): the measured ceiling of FP64 arithmetic the FP64 path
+    is compared with."""
+    a = torch.randn(n, n, device="cuda", dtype=torch.float64)
+    b = torch.randn(n, n, device="cuda", dtype=torch.float64)
+    torch.matmul(a, b)
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return {"fp64_gemm_tflops": 2.0 * n ** 3 / (best / 1e3) / 1e12, "n": n, "ms": best}
+
+
 def closure_weights():
     """Seeded network of the closure's architecture (13 -> 64 -> 64 -> 2); the
     throughput does not depend on the weight values.  Input scales match the
@@ -260,11 +279,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sub", default=None, help="nex,ney,nez: run a sub-box of the workload (profiling cases)")
+    ap.add_argument("--fp64-peak", action="store_true",
+                    help="print the FP64 GEMM rate of this GPU (the FP64 path's roofline) and exit")
     ap.add_argument("--variants", default="fp32acc64_mlp,fp32acc64_sl,fp64_sl",
                     help="comma list; the first is the headline value")
     args = ap.parse_args()
     sub = tuple(int(x) for x in args.sub.split(",")) if args.sub else None
     world, rank, local = dist_setup()
+
+    if args.fp64_peak:
+        import torch
+        print(json.dumps(fp64_peak(torch)))
+        return 0
 
     if args.impl == "reference":
         if rank != 0:
