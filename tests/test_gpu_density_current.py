@@ -62,10 +62,16 @@ def test_density_current_initial_state_matches_oracle(orc):
         assert np.abs(Qg[:, v] - Q[:, v]).max() <= 1e-12 * np.abs(Q[:, v]).max(), v
 
 
+@pytest.mark.parametrize("res", [50.0, 100.0])
 @pytest.mark.parametrize("closure", ["sl", "vreman"])
-def test_density_current_front_at_900s(orc, closure):
+def test_density_current_front_at_900s(orc, closure, res):
     from paper_2110_00853_b300 import cmles
     m, ph, c = I.mesh("dc"), I.physics("dc", closure=closure), I.case("dc")
+    if res != 50.0:
+        # same box, element size 4 res (N = 4), time step scaled with it
+        h = 4.0 * res
+        m.update(nex=int(round(m["Lx"] / h)), nez=int(round(m["Lz"] / h)), Ly=h)
+        ph["dt"] = 0.025 * res / 50.0
     G = cmles.Solver(m, ph, precision="fp32")
     G.init_case(c)
     nsteps = int(round(900.0 / ph["dt"]))
@@ -79,8 +85,8 @@ def test_density_current_front_at_900s(orc, closure):
     i = cold.max()
     # linear interpolation to the -1 K crossing beyond the last cold node
     front = x[i] + (x[i + 1] - x[i]) * ((th[i] - 299.0) / (th[i] - th[i + 1])) if i + 1 < len(x) else x[i]
-    ref = _front_reference(50.0, closure)
-    print("density current front at 900 s,", closure, front, "m; paper (50 m):", ref, "m; time", d["time"])
+    ref = _front_reference(res, closure)
+    print("density current front at 900 s,", closure, res, "m:", front, "m; paper:", ref, "m; time", d["time"])
     assert abs(front - ref) <= 0.03 * ref
 
 
