@@ -185,6 +185,14 @@ def test_single_element_periodic_degenerate(orc):
     _compare_rhs(S, Q, G, 1e-12)
 
 
+def test_single_element_box_walls_everywhere(orc):
+    # one element, six walls: every face is a boundary face
+    m = I.sub_mesh("c1", 1, 1, 1)
+    m["periodic"] = (0, 0, 0)
+    S, Q, G = _setup(orc, "c1", m, fuzz_seed=6)
+    _compare_rhs(S, Q, G, 1e-12)
+
+
 def test_lsrk_steps_and_budgets(orc):
     m = I.sub_mesh("c2", 3, 4, 16)
     ph = I.physics("c2")

@@ -122,6 +122,15 @@ def test_fp32_tendency_hllc_roe(orc, case, flux):
     print(flux, "fp32", case, "rel L2", _compare(S, Q, G))
 
 
+@pytest.mark.parametrize("periodic", [(1, 1, 0), (0, 0, 0)])
+def test_fp32_single_element_degenerate(orc, periodic):
+    # one element: its own periodic neighbour in x and y, or walls on all six faces
+    m = I.sub_mesh("c1", 1, 1, 1)
+    m["periodic"] = periodic
+    S, Q, G = _setup(orc, "c1", m, fuzz_seed=21)
+    print("single element fp32", periodic, _compare(S, Q, G))
+
+
 def test_fp32_tendency_c5_subbox(orc):
     m = I.sub_mesh("c5", 4, 4, 10)
     c = I.case("c5")
