@@ -303,7 +303,9 @@ __global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, c
       } else {
 #pragma unroll
         for (int v = 0; v < 6; ++v) sp[v] = sm[v];
-        sp[1 + d] = -sm[1 + d];
+        sp[1] = d == 0 ? -sm[1] : sm[1];
+        sp[2] = d == 1 ? -sm[2] : sm[2];
+        sp[3] = d == 2 ? -sm[3] : sm[3];
         pp = pm;
         cp = cm;
 #pragma unroll
@@ -316,7 +318,9 @@ __global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, c
       float fm[6], fp[6], f1s[6];
       flux1_dev32(sm, rho_r, rhoq_r, pm, d, fm);
       flux1_dev32(sp, rho_r, rhoq_r, pp, d, fp);
-      const float um = fdiv(sm[1 + d], rho_r + sm[0]), up = fdiv(sp[1 + d], rho_r + sp[0]);
+      const float smd = d == 0 ? sm[1] : (d == 1 ? sm[2] : sm[3]);
+      const float spd = d == 0 ? sp[1] : (d == 1 ? sp[2] : sp[3]);
+      const float um = fdiv(smd, rho_r + sm[0]), up = fdiv(spd, rho_r + sp[0]);
       // reference part of the energy flux (H_r u.n is not in fm, fp): the
       // own node's H_r (u-.n) minus that of the numerical flux
       float ref4;

@@ -163,8 +163,11 @@ __global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, do
 // [rho u_d, rho u_j u_d + (p - p_r) delta_jd, (rho e + p) u_d, rho q_t u_d].
 __device__ __forceinline__ void flux1_dir(const double Y[6], double rinv, double pprime, double pr, int d,
                                           double f[6]) {
-  const double ud = Y[1 + d] * rinv;
-  f[0] = Y[1 + d];
+  // the normal momentum by selection, not by a run-time index (which would
+  // move the state to local memory when d is not a compile-time constant)
+  const double yd = d == 0 ? Y[1] : (d == 1 ? Y[2] : Y[3]);
+  const double ud = yd * rinv;
+  f[0] = yd;
   f[1] = Y[1] * ud + (d == 0 ? pprime : 0.0);
   f[2] = Y[2] * ud + (d == 1 ? pprime : 0.0);
   f[3] = Y[3] * ud + (d == 2 ? pprime : 0.0);
@@ -245,7 +248,9 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
         // reflecting wall state (Eq. bc-velocity-impenetrable), scalars copied
 #pragma unroll
         for (int v = 0; v < 6; ++v) Yp[v] = Ym[v];
-        Yp[1 + d] = -Ym[1 + d];
+        Yp[1] = d == 0 ? -Ym[1] : Ym[1];
+        Yp[2] = d == 1 ? -Ym[2] : Ym[2];
+        Yp[3] = d == 2 ? -Ym[3] : Ym[3];
         pp = pm;
         cp = cm;
         // wall-normal diffusive fluxes specified directly (App. A.3)
@@ -283,8 +288,8 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
         for (int v = 0; v < 6; ++v) f1s[v] = 0.5 * (sg * fm[v] + sg * fp[v]) - 0.5 * D[v];
       } else {
         // Rusanov (Eq. nonviscFlux): 1/2 n.(F1- + F1+) + lambda/2 (Y- - Y+)
-        const double lm = fabs(Ym[1 + d] * im) + cm;
-        const double lp = fabs(Yp[1 + d] * ip) + cp;
+        const double lm = fabs((d == 0 ? Ym[1] : (d == 1 ? Ym[2] : Ym[3])) * im) + cm;
+        const double lp = fabs((d == 0 ? Yp[1] : (d == 1 ? Yp[2] : Yp[3])) * ip) + cp;
         const double lam = fmax(lm, lp);
 #pragma unroll
         for (int v = 0; v < 6; ++v) f1s[v] = 0.5 * (sg * fm[v] + sg * fp[v]) + 0.5 * lam * (Ym[v] - Yp[v]);

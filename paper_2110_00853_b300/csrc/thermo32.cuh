@@ -125,8 +125,11 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
 // The reference part H_r u_d of the energy flux is handled separately.
 __device__ __forceinline__ void flux1_dev32(const float s[6], float rho_r, float rhoq_r, float pp, int d,
                                            float f[6]) {
-  const float ud = fdiv(s[1 + d], rho_r + s[0]);
-  f[0] = s[1 + d];
+  // the normal momentum by selection, not by a run-time index, so that the
+  // state stays in registers when d is not a compile-time constant
+  const float sd = d == 0 ? s[1] : (d == 1 ? s[2] : s[3]);
+  const float ud = fdiv(sd, rho_r + s[0]);
+  f[0] = sd;
   f[1] = s[1] * ud + (d == 0 ? pp : 0.f);
   f[2] = s[2] * ud + (d == 1 ? pp : 0.f);
   f[3] = s[3] * ud + (d == 2 ? pp : 0.f);
