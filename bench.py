@@ -44,7 +44,11 @@ BYTES = {
     "fp64": {"grad": (6 + 15 + 2) * 8, "rhs": (4 * 41 + 35) * 8 / 5},
     "fp32": {"grad": (6 + 15 + 2) * 4, "rhs": (41 + 3 * 53 + 65) * 4 / 5},
 }
-VARIANTS = {"fp32acc64_mlp": ("fp32", "mlp"), "fp32acc64_sl": ("fp32", "sl"), "fp64_sl": ("fp64", "sl")}
+# name: (precision, closure, numerical flux of F1); the first three are the
+# default run, the others are reported when asked for with --variants
+VARIANTS = {"fp32acc64_mlp": ("fp32", "mlp", "rusanov"), "fp32acc64_sl": ("fp32", "sl", "rusanov"),
+            "fp64_sl": ("fp64", "sl", "rusanov"), "fp32acc64_vreman": ("fp32", "vreman", "rusanov"),
+            "fp32acc64_mlp_hllc": ("fp32", "mlp", "hllc"), "fp32acc64_mlp_roe": ("fp32", "mlp", "roe")}
 DTYPE = {"fp32": "f32", "fp64": "f64"}
 # DRAM bytes per node of one launch (dram__bytes_read.sum + dram__bytes_write.sum
 # from one ncu capture on a 40 x 40 x 20-element sub-box of the box, 4M nodes,
@@ -175,9 +179,10 @@ def workload_mesh(sub):
     return I.mesh(WORKLOAD) if sub is None else I.sub_mesh(WORKLOAD, *sub)
 
 
-def run_variant(name, precision, closure, steps, warmup, world, rank, torch, sub=None):
+def run_variant(name, precision, closure, flux, steps, warmup, world, rank, torch, sub=None):
     from paper_2110_00853_b300 import cmles
     mesh, phys, case = workload_mesh(sub), I.physics(WORKLOAD, closure=closure), I.case(WORKLOAD)
+    phys["flux"] = flux
     G = cmles.Solver(mesh, phys, precision=precision)
     G.init_case(case)
     if closure == "mlp":
@@ -216,12 +221,13 @@ def run_variant(name, precision, closure, steps, warmup, world, rank, torch, sub
                 finite=not diag["nonfinite"], satadj_failures=diag["satadj_failures"])
 
 
-def run_e2e(precision, closure, steps, torch):
+def run_e2e(precision, closure, flux, steps, torch):
     """Same metric through the C ABI with host buffers: every step uploads the
     state from pinned host memory, advances one LSRK step and reads back the
     budget diagnostics."""
     from paper_2110_00853_b300 import cmles
     mesh, phys, case = I.mesh(WORKLOAD), I.physics(WORKLOAD, closure=closure), I.case(WORKLOAD)
+    phys["flux"] = flux
     G = cmles.Solver(mesh, phys, precision=precision)
     G.init_case(case)
     if closure == "mlp":
@@ -313,8 +319,8 @@ def main():
     hbm, peak_kind = measured_peaks()
     variants = [(n,) + VARIANTS[n] for n in args.variants.split(",")]
     results = {}
-    for name, prec, clo in variants:
-        results[name] = run_variant(name, prec, clo, args.steps, args.warmup, world, rank, torch, sub)
+    for name, prec, clo, flux in variants:
+        results[name] = run_variant(name, prec, clo, flux, args.steps, args.warmup, world, rank, torch, sub)
     head = results[variants[0][0]]
     prec = variants[0][1]
     value = whole_job_rate(head["nodes"], world, args.steps, head["ms"])
@@ -326,7 +332,7 @@ def main():
     tb = TRAFFIC_B_PER_NODE.get((variants[0][0], kinds[dom]))
     traffic = tb * head["nodes"] if tb is not None else None
     out_variants = {}
-    for (name, vprec, _), r in zip(variants, results.values()):
+    for (name, vprec, _, _), r in zip(variants, results.values()):
         v = whole_job_rate(r["nodes"], world, args.steps, r["ms"])
         per = {}
         for k in range(2):
@@ -337,7 +343,7 @@ def main():
                                   satadj_failures=r["satadj_failures"])
     e2e = None
     if not args.no_e2e and rank == 0 and sub is None:
-        e2e = run_e2e(variants[0][1], variants[0][2], max(1, min(args.steps, 2)), torch)
+        e2e = run_e2e(variants[0][1], variants[0][2], variants[0][3], max(1, min(args.steps, 2)), torch)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and sub is None:
         cb = cpu_baseline()
@@ -348,7 +354,9 @@ def main():
                     config={"workload": f"{WORKLOAD}: 160x160x80 hexahedral elements, N=4 (256M nodes), moist, "
                                         "LSRK(5,4)", "variant": variants[0][0],
                             "closure": {"mlp": "learned (BF16 tensor-core MLP 13-64-64-2, seeded weights)",
-                                        "sl": "Smagorinsky-Lilly + Richardson"}[variants[0][2]],
+                                        "sl": "Smagorinsky-Lilly + Richardson",
+                                        "vreman": "Vreman + Richardson"}[variants[0][2]],
+                            "flux": variants[0][3],
                             "elements": head["nodes"] // 125, "nodes_per_gpu": head["nodes"],
                             "l2": "inputs larger than L2 (state alone 12 GB)", "parallelism": f"replicas{world}"},
                     roofline={"bound": "hbm", "kernel": kinds[dom], "achieved": achieved, "peak": hbm,
