@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
 // 2 last stage of the step, Q = Q_step_start + D added in FP64 and the shadow
 // rewritten from it.  FL: numerical flux of F1, 0 Rusanov, 1 HLLC, 2 Roe.
 template <int N, int UPD, int FL>
-__global__ void __launch_bounds__(128, 7) k_rhs32(const float *__restrict__ S, const float *__restrict__ F2,
+__global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__restrict__ S, const float *__restrict__ F2,
                                                   const float *__restrict__ aux, float *__restrict__ dQ,
                                                   double *__restrict__ Q64, float *__restrict__ Sout,
                                                   double *__restrict__ Rout, const StageCoef sc, const KParams P) {
