@@ -44,7 +44,9 @@ typedef enum {
   CMLES_ERR_SATADJ = 4,    /* saturation adjustment did not converge at some node */
   CMLES_ERR_NONFINITE = 5, /* the state holds NaN or Inf */
   CMLES_ERR_MESH = 6,      /* inconsistent mesh description */
-  CMLES_ERR_STATE = 7      /* call out of order (e.g. no reference state yet) */
+  CMLES_ERR_STATE = 7,     /* call out of order (e.g. no reference state yet) */
+  CMLES_ERR_TIMEOUT = 8    /* a bounded device-side wait (tensor-core MMA completion) gave up;
+                              the results of that launch are invalid, the context stays usable */
 } cmles_status;
 
 enum { CMLES_CLOSURE_NONE = 0, CMLES_CLOSURE_SL = 1, CMLES_CLOSURE_MLP = 2, CMLES_CLOSURE_VREMAN = 3 };
@@ -119,6 +121,7 @@ typedef struct {
   long long steps;       /* steps taken */
   int nonfinite;         /* 1 if the state holds a NaN or Inf */
   int satadj_failures;   /* Newton non-convergence count since the previous call */
+  int tc_timeouts;       /* CTAs whose tensor-core completion wait gave up since the previous call */
 } cmles_diag;
 
 /* Initial-state description for cmles_init_case (synthetic cases; inputs,
@@ -223,7 +226,10 @@ cmles_status cmles_set_closure_weights(cmles_handle h, const float *params_host,
 cmles_status cmles_set_closure_weights_device(cmles_handle h, const float *params_dev);
 
 /* Training kernels of the closure network on device buffers (no handle):
- * cmles_mlp_forward: Y[n][2] = network(X[n][13]) with BF16 tensor cores.
+ * cmles_mlp_forward: Y[n][2] = network(X[n][13]) on the tcgen05 tensor cores
+ *   (BF16 operands, FP32 accumulation, biases folded into the contraction);
+ *   synchronises the stream and returns CMLES_ERR_TIMEOUT if an MMA
+ *   completion wait gave up.
  * cmles_mlp_loss_grad: loss = 1/(2n) sum |y - t|^2 over T[n][2] and its
  *   gradient with respect to the first 5186 parameters (W1 .. b3), written
  *   to grad_dev[5186] and loss_dev[1] (both overwritten).
@@ -257,6 +263,15 @@ cmles_status cmles_enable_timing(cmles_handle h, int enable);
 cmles_status cmles_kernel_times(cmles_handle h, long long count[3], double ms[3], long long *launches);
 /* Kernel launches issued by this handle since creation (always counted). */
 long long cmles_launch_count(cmles_handle h);
+
+/* Test hook for the failure path of the bounded device-side waits (no GPU
+ * fault involved): with enable != 0, each CTA of the learned-closure
+ * gradient pass also waits, with a bound, on an mbarrier that nothing
+ * arrives on; the wait runs out, the CTA finishes its work, frees its Tensor
+ * Memory and is counted, and the next cmles_diagnostics returns
+ * CMLES_ERR_TIMEOUT with cmles_diag.tc_timeouts > 0.  enable = 0 restores
+ * normal operation. */
+cmles_status cmles_test_stall_tc(cmles_handle h, int enable);
 
 /* Allocation-free budgets.  The paper has no counterpart: this is a service
  * for callers that cannot call cudaMalloc, such as applications whose own

@@ -21,7 +21,7 @@ CLOSURE = {"none": 0, "sl": 1, "mlp": 2, "vreman": 3}
 FLUX = {"rusanov": 0, "hllc": 1, "roe": 2}
 PRECISION = {"fp64": CMLES_FP64, "fp32": CMLES_FP32_ACC64, "fp32acc64": CMLES_FP32_ACC64}
 STATUS = {0: "CMLES_OK", 1: "CMLES_ERR_ARG", 2: "CMLES_ERR_OOM", 3: "CMLES_ERR_CUDA", 4: "CMLES_ERR_SATADJ",
-          5: "CMLES_ERR_NONFINITE", 6: "CMLES_ERR_MESH", 7: "CMLES_ERR_STATE"}
+          5: "CMLES_ERR_NONFINITE", 6: "CMLES_ERR_MESH", 7: "CMLES_ERR_STATE", 8: "CMLES_ERR_TIMEOUT"}
 MLP_PARAMS = 64 * 13 + 64 + 64 * 64 + 64 + 2 * 64 + 2 + 13 + 2   # 5201
 MLP_NET = MLP_PARAMS - 15                                        # trainable part: W1 .. b3
 
@@ -46,7 +46,7 @@ class Params(C.Structure):
 
 class Diag(C.Structure):
     _fields_ = [("budget", C.c_double * 6), ("time", C.c_double), ("steps", C.c_longlong),
-                ("nonfinite", C.c_int), ("satadj_failures", C.c_int)]
+                ("nonfinite", C.c_int), ("satadj_failures", C.c_int), ("tc_timeouts", C.c_int)]
 
 
 class Case(C.Structure):
@@ -103,6 +103,7 @@ def load(path=LIB_PATH):
     L.cmles_mlp_forward.argtypes = [_VP, _VP, _VP, C.c_longlong, _VP]
     L.cmles_mlp_loss_grad.argtypes = [_VP, _VP, _VP, C.c_longlong, _VP, _VP, _VP]
     L.cmles_mlp_adam.argtypes = [_VP, _VP, _VP, _VP, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, _VP]
+    L.cmles_test_stall_tc.argtypes = [_H, C.c_int]
     for n in ("cmles_launch_count", "cmles_num_elements", "cmles_num_nodes", "cmles_device_bytes"):
         getattr(L, n).argtypes = [_H]
         getattr(L, n).restype = C.c_longlong
@@ -298,7 +299,7 @@ class Solver:
         if raise_on_error and st not in (0,):
             self._check(st)
         return dict(budget=np.array(d.budget[:]), time=d.time, steps=d.steps, nonfinite=bool(d.nonfinite),
-                    satadj_failures=d.satadj_failures, status=st)
+                    satadj_failures=d.satadj_failures, tc_timeouts=d.tc_timeouts, status=st)
 
     def profiles(self):
         out = np.zeros((self.nlev, 11))
@@ -338,6 +339,11 @@ class Solver:
 
     def launch_count(self):
         return self.L.cmles_launch_count(self.h)
+
+    def test_stall_tc(self, enable):
+        """Test hook: make the learned-closure kernels' bounded tensor-core
+        wait run out (see cmles_test_stall_tc)."""
+        self._check(self.L.cmles_test_stall_tc(self.h, 1 if enable else 0))
 
     def device_bytes(self):
         return self.L.cmles_device_bytes(self.h)

@@ -117,6 +117,7 @@ struct cmles_t {
   int budget_nblocks = 1;
   bool have_ref = false;
   long long launches = 0, steps = 0;
+  int tc_stall = 0;
   double time = 0.0;
   bool timing = false;
   std::vector<TimedLaunch> timed;
@@ -308,6 +309,7 @@ void fill_kparams(cmles_handle h) {
   K.tau_lev = h->tau_lev;
   K.tau_col = h->tau_col;
   K.flags = h->flags;
+  K.tc_stall = h->tc_stall;
 }
 
 double level_z(cmles_handle h, int lev) {
@@ -1209,10 +1211,14 @@ cmles_status cmles_diagnostics(cmles_handle h, cmles_diag *out) {
   for (int v = 0; v < 6; ++v) out->budget[v] = res[v];
   out->nonfinite = res[6] > 0.0 ? 1 : 0;
   out->satadj_failures = flags[0];
+  out->tc_timeouts = flags[1];
   out->time = h->time;
   out->steps = h->steps;
   if (out->nonfinite) return fail(h, CMLES_ERR_NONFINITE, "state holds non-finite values");
   if (out->satadj_failures) return fail(h, CMLES_ERR_SATADJ, "saturation adjustment did not converge");
+  if (out->tc_timeouts)
+    return fail(h, CMLES_ERR_TIMEOUT, "a tensor-core completion wait gave up; the results since the previous "
+                                      "report are invalid");
   return CMLES_OK;
 }
 
@@ -1317,6 +1323,13 @@ cmles_status cmles_kernel_times(cmles_handle h, long long count[3], double ms[3]
 }
 
 long long cmles_launch_count(cmles_handle h) { return h ? h->launches : -1; }
+
+cmles_status cmles_test_stall_tc(cmles_handle h, int enable) {
+  if (!h) return CMLES_ERR_ARG;
+  h->tc_stall = enable ? 1 : 0;
+  h->K.tc_stall = h->tc_stall;
+  return CMLES_OK;
+}
 long long cmles_num_elements(cmles_handle h) { return h ? h->E : -1; }
 long long cmles_num_nodes(cmles_handle h) { return h ? h->nodes : -1; }
 long long cmles_device_bytes(cmles_handle h) { return h ? h->bytes : -1; }

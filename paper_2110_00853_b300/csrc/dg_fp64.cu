@@ -365,6 +365,31 @@ int grid_for(const void *fn, int E, size_t smem = 0) {
   return (int)(g < E ? g : E);
 }
 
+// Persistent grid of a 128-thread kernel that allocates tmem_cols Tensor
+// Memory columns per CTA: the resident CTAs per SM from its registers and
+// shared memory (the occupancy query reports 1 for such kernels), capped so
+// that the resident CTAs' allocations fit in the SM's 512 columns.
+int grid_for_tc(const void *fn, int E, int tmem_cols) {
+  int dev = 0, nsm = 0, regs_sm = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
+    cudaGetLastError();
+    return nsm < E ? nsm : E;
+  }
+  const int regs_cta = ((a.numRegs * 32 + 255) / 256 * 256) * 4;  // 4 warps, 256-register granules
+  int per = regs_cta > 0 ? regs_sm / regs_cta : 1;
+  const int smem_cta = (int)a.sharedSizeBytes + 1024;  // + the per-CTA reservation
+  if (smem_cta > 0 && smem_sm / smem_cta < per) per = smem_sm / smem_cta;
+  if (512 / tmem_cols < per) per = 512 / tmem_cols;
+  if (per < 1) per = 1;
+  const long long g = (long long)nsm * per;
+  return (int)(g < E ? g : E);
+}
+
 cudaError_t launch_grad64(const double *Q, double *F2, double *aux, const KParams &P, cudaStream_t s) {
   if (P.moist) {
     static int grid = 0;

@@ -8,6 +8,7 @@
 namespace cmles {
 
 int grid_for(const void *fn, int E, size_t smem);
+int grid_for_tc(const void *fn, int E, int tmem_cols);
 
 // FP64 path (dg_fp64.cu)
 cudaError_t launch_grad64(const double *Q, double *F2, double *aux, const KParams &P, cudaStream_t s);

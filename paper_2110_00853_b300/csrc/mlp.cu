@@ -20,6 +20,45 @@ namespace cmles {
 
 // ------------------------------------------------------------------ packing
 
+// Entry (row, k) of the tensor-core operand of layer l (0, 1, 2) from the
+// FP32 parameter vector: the weight for k < K_in, then the bias split as
+// hi + mid + lo on k = K_in .. K_in + 2, zero elsewhere.
+__host__ __device__ inline __nv_bfloat16 tc_weight(const float *p, int l, int row, int k) {
+  const int kin = l == 0 ? kMlpIn : kMlpH, nout = l == 2 ? kMlpOut : kMlpH;
+  if (row >= nout) return __float2bfloat16_rn(0.f);
+  if (k < kin) {
+    const int off = l == 0 ? kMlpOffW1 : (l == 1 ? kMlpOffW2 : kMlpOffW3);
+    return __float2bfloat16_rn(p[off + row * kin + k]);
+  }
+  if (k >= kin + 3) return __float2bfloat16_rn(0.f);
+  const float b = p[(l == 0 ? kMlpOffB1 : (l == 1 ? kMlpOffB2 : kMlpOffB3)) + row];
+  const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+  const float r1 = b - __bfloat162float(hi);
+  const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+  if (k == kin) return hi;
+  if (k == kin + 1) return mid;
+  return __float2bfloat16_rn(r1 - __bfloat162float(mid));
+}
+
+// Fill entry q of the three tensor-core operand arrays (q < the largest).
+__host__ __device__ inline void tc_fill(const float *p, MlpTc *o, int q) {
+  const int c = q & 7, r = (q >> 3) & 7;
+  if (q < kMlpH * 8 * kTcKG1) {
+    const int kg = (q >> 6) % kTcKG1, rg = (q >> 6) / kTcKG1;
+    o->W1[q] = tc_weight(p, 0, rg * 8 + r, kg * 8 + c);
+  }
+  if (q < kMlpH * 8 * kTcKG) {
+    const int kg = (q >> 6) % kTcKG, rg = (q >> 6) / kTcKG;
+    o->W2[q] = tc_weight(p, 1, rg * 8 + r, kg * 8 + c);
+  }
+  if (q < kTcN3 * 8 * kTcKG) {
+    const int kg = (q >> 6) % kTcKG, rg = (q >> 6) / kTcKG;
+    o->W3[q] = tc_weight(p, 2, rg * 8 + r, kg * 8 + c);
+  }
+  if (q < kMlpInPad) o->in_scale[q] = q < kMlpIn ? p[kMlpOffIn + q] : 0.f;
+  if (q < 4) o->out_scale[q] = q < 2 ? p[kMlpOffOut + q] : 0.f;
+}
+
 void pack_mlp_host(const float *p, MlpPacked *o) {
   memset(o, 0, sizeof(*o));
   for (int n = 0; n < kMlpH; ++n)
@@ -37,6 +76,7 @@ void pack_mlp_host(const float *p, MlpPacked *o) {
   for (int k = 0; k < kMlpIn; ++k) o->in_scale[k] = p[kMlpOffIn + k];
   o->out_scale[0] = p[kMlpOffOut];
   o->out_scale[1] = p[kMlpOffOut + 1];
+  for (int q = 0; q < kMlpH * 8 * kTcKG; ++q) tc_fill(p, &o->tc, q);
 }
 
 __global__ void k_pack_mlp(const float *__restrict__ p, MlpPacked *__restrict__ o) {
@@ -60,6 +100,7 @@ __global__ void k_pack_mlp(const float *__restrict__ p, MlpPacked *__restrict__ 
   for (int q = t; q < kMlpOutPad; q += nt) o->b3[q] = q < kMlpOut ? p[kMlpOffB3 + q] : 0.f;
   for (int q = t; q < kMlpInPad; q += nt) o->in_scale[q] = q < kMlpIn ? p[kMlpOffIn + q] : 0.f;
   if (t < 2) o->out_scale[t] = p[kMlpOffOut + t];
+  for (int q = t; q < kMlpH * 8 * kTcKG; q += nt) tc_fill(p, &o->tc, q);
 }
 
 cudaError_t launch_pack_mlp(const float *params_dev, MlpPacked *out, cudaStream_t s) {
@@ -69,33 +110,35 @@ cudaError_t launch_pack_mlp(const float *params_dev, MlpPacked *out, cudaStream_
 
 // ------------------------------------------------------------------ inference
 
+// One CTA of 128 threads per 128 rows, on the tensor cores (tcgen05); a CTA
+// loops over row blocks.  err_count: CTAs whose tensor-core wait gave up.
 __global__ void __launch_bounds__(128) k_mlp_forward(const MlpPacked *__restrict__ Wg, const float *__restrict__ X,
-                                                     float *__restrict__ Y, long long n) {
-  __shared__ __align__(16) uint8_t sWraw[sizeof(MlpPacked)];
-  __shared__ __align__(16) __nv_bfloat16 sX[128 * kMlpInPad];
-  __shared__ float sY[128 * 2];
+                                                     float *__restrict__ Y, long long n, int *err_count) {
+  __shared__ __align__(16) uint8_t sWraw[sizeof(MlpTc)];
+  __shared__ __align__(128) __nv_bfloat16 sA[kTcAElems];
+  __shared__ __align__(8) uint64_t sBar;
+  __shared__ uint32_t sSlot;
   const int t = threadIdx.x;
-  for (int q = t; q < (int)(sizeof(MlpPacked) / 16); q += 128)
-    reinterpret_cast<uint4 *>(sWraw)[q] = reinterpret_cast<const uint4 *>(Wg)[q];
-  __syncthreads();
-  const MlpPacked &W = *reinterpret_cast<const MlpPacked *>(sWraw);
+  for (int q = t; q < (int)(sizeof(MlpTc) / 16); q += 128)
+    reinterpret_cast<uint4 *>(sWraw)[q] = reinterpret_cast<const uint4 *>(&Wg->tc)[q];
+  fence_proxy_async_smem();
+  TcState st;
+  tc_setup(st, &sSlot, &sBar);
+  const MlpTc &W = *reinterpret_cast<const MlpTc *>(sWraw);
   for (long long b = (long long)blockIdx.x * 128; b < n; b += (long long)gridDim.x * 128) {
     const long long s = b + t;
-    uint32_t *xr = reinterpret_cast<uint32_t *>(sX + t * kMlpInPad);
-    float x[kMlpInPad];
+    float x[kMlpIn];
 #pragma unroll
-    for (int k = 0; k < kMlpInPad; ++k) x[k] = (s < n && k < kMlpIn) ? X[s * kMlpIn + k] : 0.f;
-#pragma unroll
-    for (int q = 0; q < kMlpInPad / 2; ++q) xr[q] = pack_bf16(x[2 * q], x[2 * q + 1]);
-    __syncwarp();
-    mlp_warp_forward(W, sX, sY, 32 * (t >> 5));
-    __syncwarp();
+    for (int k = 0; k < kMlpIn; ++k) x[k] = s < n ? X[s * kMlpIn + k] : 0.f;
+    mlp_tc_put_input(sA, x);
+    float y0, y1;
+    mlp_tc_forward(W, sA, st, y0, y1);
     if (s < n) {
-      Y[s * 2 + 0] = sY[2 * t];
-      Y[s * 2 + 1] = sY[2 * t + 1];
+      Y[s * 2 + 0] = y0;
+      Y[s * 2 + 1] = y1;
     }
-    __syncwarp();
   }
+  tc_teardown(st, err_count);
 }
 
 // ------------------------------------------------------------------ training
@@ -316,13 +359,23 @@ cmles_status cmles_mlp_forward(const float *params_dev, const float *X_dev, floa
   if (n == 0) return CMLES_OK;
   cudaStream_t s = (cudaStream_t)stream;
   MlpPacked *pk = nullptr;
-  if (cudaMallocAsync((void **)&pk, sizeof(MlpPacked), s) != cudaSuccess) return CMLES_ERR_OOM;
+  const size_t bytes = sizeof(MlpPacked) + 16;
+  if (cudaMallocAsync((void **)&pk, bytes, s) != cudaSuccess) return CMLES_ERR_OOM;
+  int *err = reinterpret_cast<int *>(reinterpret_cast<char *>(pk) + sizeof(MlpPacked));
+  cudaMemsetAsync(err, 0, sizeof(int), s);
   k_pack_mlp<<<8, 256, 0, s>>>(params_dev, pk);
+  static int grid = 0;
+  if (!grid) grid = grid_for_tc((const void *)k_mlp_forward, 1 << 30, kTcCols);
   long long blocks = (n + 127) / 128;
-  if (blocks > 148 * 8) blocks = 148 * 8;
-  k_mlp_forward<<<(int)blocks, 128, 0, s>>>(pk, X_dev, Y_dev, n);
+  if (blocks > grid) blocks = grid;
+  k_mlp_forward<<<(int)blocks, 128, 0, s>>>(pk, X_dev, Y_dev, n, err);
+  int err_h = 0;
+  const cudaError_t e1 = cudaGetLastError();
+  const cudaError_t e2 = cudaMemcpyAsync(&err_h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(pk, s);
-  return cudaGetLastError() == cudaSuccess ? CMLES_OK : CMLES_ERR_CUDA;
+  const cudaError_t e3 = cudaStreamSynchronize(s);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return CMLES_ERR_CUDA;
+  return err_h ? CMLES_ERR_TIMEOUT : CMLES_OK;
 }
 
 cmles_status cmles_mlp_loss_grad(const float *params_dev, const float *X_dev, const float *T_dev, long long n,

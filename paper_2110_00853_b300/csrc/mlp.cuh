@@ -13,6 +13,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "tc.cuh"
+
 namespace cmles {
 
 constexpr int kMlpIn = 13, kMlpH = 64, kMlpOut = 2;
@@ -30,14 +32,34 @@ constexpr int kLdW = 72;
 // eight different 16-byte bank groups for ldmatrix (32 B would pair them).
 constexpr int kLdW1 = 24;
 
+// Tensor-core (tcgen05) copy of the network used by the inference kernels:
+// the weights as K-major B operands in the core-matrix layout of tc.cuh,
+// with the biases folded into the contraction.  Layer 1 has K = 16: the 13
+// inputs and three columns on which the A operand holds 1 and W1 holds the
+// bias b1 split as hi + mid + lo, three BF16 numbers whose sum is the FP32
+// bias to 2^-27 relative.  Layers 2 and 3 have K = 80: the 64 hidden units,
+// one group of 8 columns that holds (1, 1, 1, 0, ...) in A and the split
+// bias in W, and one zero group (K steps of 16).  Layer 3 has N = 16 with
+// output rows 2..15 zero.
+constexpr int kTcKG1 = 2, kTcKG = 10, kTcN3 = 16;
+struct __align__(16) MlpTc {
+  __nv_bfloat16 W1[kMlpH * 8 * kTcKG1];   // [n/8][k/8][n%8][k%8]
+  __nv_bfloat16 W2[kMlpH * 8 * kTcKG];
+  __nv_bfloat16 W3[kTcN3 * 8 * kTcKG];
+  float in_scale[kMlpInPad], out_scale[4];
+};
+
 // Packed device copy used by the kernels (16-byte aligned, size a multiple of
-// 16 so that it can be staged into shared memory with 16-byte copies).
+// 16 so that it can be staged into shared memory with 16-byte copies): the
+// row-major copy for the warp-level (mma.sync) training kernels and the
+// tensor-core copy for inference.
 struct __align__(16) MlpPacked {
   __nv_bfloat16 W1[kMlpH * kLdW1];       // [64][24], k >= 13 zero
   __nv_bfloat16 W2[kMlpH * kLdW];        // [64][72], k >= 64 zero
   __nv_bfloat16 W3[kMlpOutPad * kLdW];   // [8][72], n >= 2 or k >= 64 zero
   float b1[kMlpH], b2[kMlpH], b3[kMlpOutPad];
   float in_scale[kMlpInPad], out_scale[2];
+  MlpTc tc;
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -178,6 +200,134 @@ __device__ __forceinline__ void mlp_warp_forward(const MlpPacked &W, const __nv_
       Y[(rb + g) * 2 + 1] = y[1];
       Y[(rb + g + 8) * 2 + 0] = y[2];
       Y[(rb + g + 8) * 2 + 1] = y[3];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inference on the fifth-generation tensor cores (tcgen05): one CTA of 128
+// threads evaluates 128 rows, thread t owning row t.  Each layer is one MMA
+// chain of M = 128 rows issued by thread 0 (A: the rows' inputs or hidden
+// activations in shared memory; B: the layer's weights in shared memory;
+// D: 64 FP32 columns of Tensor Memory), whose completion arrives on an
+// mbarrier; every thread then reads its row of D from TMEM (lane t), applies
+// SiLU and writes the BF16 activations back as the next layer's A operand.
+//
+// The A buffer holds 128 rows x 80 columns (kTcKG groups): columns 64..66 are
+// the bias columns (1.0) of layers 2 and 3 and 67..79 are zero; the layer-1
+// inputs occupy columns 0..15 (13 inputs, then three 1.0 bias columns).
+
+constexpr int kTcAElems = 128 * 8 * kTcKG;  // A buffer, BF16 elements (20 KB)
+constexpr int kTcCols = 64;                 // TMEM columns per CTA
+constexpr int kTcWaitLimit = 1 << 20;       // mbarrier tries before giving up
+
+struct TcState {
+  uint32_t tmem;    // TMEM base address of this CTA's columns
+  uint64_t *mbar;   // MMA completion barrier (shared memory)
+  uint32_t parity;  // parity of the next phase to complete
+  int err;          // sticky: a wait gave up (results of this CTA invalid)
+};
+
+// Write this thread's row of the A buffer for layer 1: the 13 inputs (BF16),
+// the three bias columns, and the bias and zero groups of layers 2 and 3
+// (columns 64..79; rewritten every time, so the buffer may share storage
+// with other data between calls).
+__device__ __forceinline__ void mlp_tc_put_input(__nv_bfloat16 *A, const float x[kMlpIn]) {
+  const int t = threadIdx.x;
+  const uint32_t one2 = pack_bf16(1.0f, 1.0f);
+  *reinterpret_cast<uint4 *>(A + tc_off(t, 0, kTcKG)) =
+      make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
+  *reinterpret_cast<uint4 *>(A + tc_off(t, 8, kTcKG)) =
+      make_uint4(pack_bf16(x[8], x[9]), pack_bf16(x[10], x[11]), pack_bf16(x[12], 1.0f), one2);
+  *reinterpret_cast<uint4 *>(A + tc_off(t, 64, kTcKG)) = make_uint4(one2, pack_bf16(1.0f, 0.0f), 0u, 0u);
+  *reinterpret_cast<uint4 *>(A + tc_off(t, 72, kTcKG)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Set-up of a CTA's tensor-core state: TMEM columns (allocated by warp 0)
+// and the MMA completion barrier (initialised by thread 0).  All threads must
+// call it; it ends with a block barrier.
+__device__ __forceinline__ void tc_setup(TcState &s, uint32_t *slot, uint64_t *mbar) {
+  if (threadIdx.x < 32) tc_alloc(slot, kTcCols);
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  s.tmem = *slot;
+  s.mbar = mbar;
+  s.parity = 0;
+  s.err = 0;
+}
+
+// Tear-down: wait (bounded) until every MMA the CTA issued has completed,
+// free the TMEM columns, and count the CTA in *err_count if any wait gave up.
+// All threads must call it.
+__device__ __forceinline__ void tc_teardown(TcState &s, int *err_count) {
+  tc_fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc_fence_after_sync();
+    tc_commit(s.mbar);
+    if (!mbar_wait_bounded(s.mbar, s.parity, kTcWaitLimit)) s.err = 1;
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after_sync();
+    tc_dealloc(s.tmem, kTcCols);
+  }
+  if (s.err) atomicAdd(err_count, 1);
+}
+
+// Forward pass of the CTA's 128 rows; (y0, y1) of this thread's row.  All
+// 128 threads must call it (it contains block barriers).  The A buffer's
+// layer-1 columns must have been written by every thread and the bias and
+// zero groups (columns 64..79) set.
+__device__ __forceinline__ void mlp_tc_forward(const MlpTc &W, __nv_bfloat16 *A, TcState &s, float &y0,
+                                               float &y1) {
+  const int t = threadIdx.x;
+  const uint32_t lane_base = s.tmem + ((uint32_t)(t & ~31) << 16);
+  constexpr uint32_t kSboA = 8 * 16 * kTcKG, kSbo1 = 8 * 16 * kTcKG1;
+#pragma unroll 1
+  for (int layer = 0; layer < 3; ++layer) {
+    fence_proxy_async_smem();
+    tc_fence_before_sync();
+    __syncthreads();
+    if (t == 0 && !s.err) {
+      tc_fence_after_sync();
+      if (layer == 0) {
+        tc_mma(s.tmem, tc_sdesc(A, 128, kSboA), tc_sdesc(W.W1, 128, kSbo1), tc_idesc_bf16(128, kMlpH), 0u);
+      } else {
+        const __nv_bfloat16 *B = layer == 1 ? W.W2 : W.W3;
+        const uint32_t idesc = tc_idesc_bf16(128, layer == 1 ? kMlpH : kTcN3);
+#pragma unroll
+        for (int ks = 0; ks < kTcKG / 2; ++ks)
+          tc_mma(s.tmem, tc_sdesc(A + ks * 128, 128, kSboA), tc_sdesc(B + ks * 128, 128, kSboA), idesc,
+                 ks > 0 ? 1u : 0u);
+      }
+      tc_commit(s.mbar);
+    }
+    if (!mbar_wait_bounded(s.mbar, s.parity, s.err ? 1 : kTcWaitLimit)) s.err = 1;
+    s.parity ^= 1u;
+    __syncwarp();  // the TMEM loads below are warp-collective
+    tc_fence_after_sync();
+    if (layer < 2) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float v[32];
+        tc_ld32(lane_base + 32 * h, v);
+        uint32_t w[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) w[q] = silu2_bf16(v[2 * q], v[2 * q + 1]);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          *reinterpret_cast<uint4 *>(A + tc_off(t, 32 * h + 8 * kk, kTcKG)) =
+              make_uint4(w[4 * kk], w[4 * kk + 1], w[4 * kk + 2], w[4 * kk + 3]);
+      }
+    } else {
+      tc_ld2(lane_base, y0, y1);
     }
   }
 }

@@ -11,7 +11,7 @@ from paper_2110_00853_b300 import inputs as I
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-ERR_SATADJ, ERR_NONFINITE = 4, 5
+ERR_SATADJ, ERR_NONFINITE, ERR_TIMEOUT = 4, 5, 8
 
 
 def _levels(arr, mesh):
@@ -62,3 +62,34 @@ def test_newton_cap_failures_are_counted(orc, precision):
     assert d2["status"] == 0 and d2["satadj_failures"] == 0
     d = G.diagnostics(raise_on_error=False)
     assert d["satadj_failures"] == 0
+
+
+def test_tensor_core_wait_timeout_is_reported_and_cleared(orc):
+    """The learned-closure gradient pass bounds its waits on the tensor-core
+    completion barrier.  A test hook adds a bounded wait on a barrier that
+    nothing arrives on: the wait runs out, every CTA still finishes and frees
+    its Tensor Memory, cmles_diagnostics reports CMLES_ERR_TIMEOUT with the
+    count, and with the hook off the next report is clean.  The hook does not
+    touch the network's own waits, so the tendency is unchanged."""
+    from paper_2110_00853_b300 import cmles
+    m = I.sub_mesh("c2", 4, 3, 8)
+    ph = I.physics("c2", closure="mlp")
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case("c2"))
+    rng = np.random.default_rng(3)
+    G = cmles.Solver(m, ph, precision="fp32")
+    G.set_reference(_levels(rr, m), _levels(pr, m), _levels(Q[:, 5] / Q[:, 0], m))
+    flat = np.concatenate([rng.normal(size=5186) * 0.1, np.ones(13), [1.0, 1.0]]).astype(np.float32)
+    G.set_closure_weights(flat)
+    Qd = torch.from_numpy(Q).cuda()
+    R0 = G.tendency(Qd).cpu().numpy()
+    assert G.diagnostics(raise_on_error=False)["status"] == 0
+    G.test_stall_tc(True)
+    R1 = G.tendency(Qd).cpu().numpy()
+    d = G.diagnostics(raise_on_error=False)
+    assert d["status"] == ERR_TIMEOUT and d["tc_timeouts"] > 0
+    assert np.array_equal(R1, R0)
+    G.test_stall_tc(False)
+    R2 = G.tendency(Qd).cpu().numpy()
+    d = G.diagnostics(raise_on_error=False)
+    assert d["status"] == 0 and d["tc_timeouts"] == 0
+    assert np.array_equal(R2, R0)
