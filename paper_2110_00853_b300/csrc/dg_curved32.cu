@@ -34,21 +34,34 @@ template <int N, bool MOIST, int CL>
 __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *__restrict__ S, float *__restrict__ F2,
                                                                   float *__restrict__ aux, const KParams P) {
   constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
+  // the gradient fields share their storage with the closure network's A
+  // operand (written only after every thread has finished its gradient)
+  constexpr int kGBytes = (6 * kNP + 36 * Nf) * 4, kABytes = CL == 2 ? kTcAElems * 2 : 0;
   __shared__ float sD[Nq * Nq];
-  __shared__ float sG[6][kNP];
-  __shared__ float sGf[6][6][Nf];
+  __shared__ __align__(128) uint8_t sU[kGBytes > kABytes ? kGBytes : kABytes];
   __shared__ int sNb[6];
-  __shared__ __align__(16) uint8_t sMlpRaw[CL == 2 ? sizeof(MlpPacked) : 16];
-  __shared__ __align__(16) __nv_bfloat16 sX[CL == 2 ? kNP * kMlpInPad : 8];
-  __shared__ float sY[CL == 2 ? kNP * 2 : 2];
+  __shared__ __align__(16) uint8_t sMlpRaw[CL == 2 ? sizeof(MlpTc) : 16];
+  __shared__ __align__(8) uint64_t sBar[2];
+  __shared__ uint32_t sSlot;
+  float(*sG)[kNP] = reinterpret_cast<float(*)[kNP]>(sU);
+  float(*sGf)[6][Nf] = reinterpret_cast<float(*)[6][Nf]>(sU + 6 * kNP * 4);
+  __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(sU);
   const KF &F = P.f;
   const int t = threadIdx.x;
   if (t < Nq * Nq) sD[t] = (float)P.D[t];
-  const MlpPacked &W = *reinterpret_cast<const MlpPacked *>(sMlpRaw);
+  const MlpTc &W = *reinterpret_cast<const MlpTc *>(sMlpRaw);
+  TcState tcs;
+  int stalled = 0;
   if (CL == 2) {
-    const uint4 *src = reinterpret_cast<const uint4 *>(P.mlp);
+    const uint4 *src = reinterpret_cast<const uint4 *>(&P.mlp->tc);
     uint4 *dst = reinterpret_cast<uint4 *>(sMlpRaw);
-    for (int q = t; q < (int)(sizeof(MlpPacked) / 16); q += blockDim.x) dst[q] = src[q];
+    for (int q = t; q < (int)(sizeof(MlpTc) / 16); q += blockDim.x) dst[q] = src[q];
+    fence_proxy_async_smem();
+    if (t == 0) mbar_init(&sBar[1], 1);
+    tc_setup(tcs, &sSlot, &sBar[0]);
+    // test hook (see the flat kernel)
+    if (P.tc_stall && !mbar_wait_bounded(&sBar[1], 0, 1 << 14)) stalled = 1;
+    __syncwarp();
   }
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
   int fail = 0;
@@ -180,30 +193,22 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
       }
     }
     if (CL == 2) {
-      uint32_t *xr = reinterpret_cast<uint32_t *>(sX + t * kMlpInPad);
+      float x[kMlpIn];
+      const float Delta = t < Np ? P.node32[(size_t)e * C_NF * kNP + C_DELTA * kNP + t] : 0.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) x[3 * a + b] = t < Np ? gr[a][b] * W.in_scale[3 * a + b] : 0.f;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) x[9 + b] = t < Np ? gr[5][b] * W.in_scale[9 + b] : 0.f;
+      x[12] = Delta * W.in_scale[12];
+      __syncthreads();  // the A operand overwrites the gradient fields
+      mlp_tc_put_input(sA, x);
+      float y0, y1;
+      mlp_tc_forward(W, sA, tcs, y0, y1);
       if (t < Np) {
-        const float Delta = P.node32[(size_t)e * C_NF * kNP + C_DELTA * kNP + t];
-        float x[kMlpInPad];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) x[3 * a + b] = gr[a][b] * W.in_scale[3 * a + b];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) x[9 + b] = gr[5][b] * W.in_scale[9 + b];
-        x[12] = Delta * W.in_scale[12];
-        x[13] = x[14] = x[15] = 0.f;
-#pragma unroll
-        for (int q = 0; q < kMlpInPad / 2; ++q) xr[q] = pack_bf16(x[2 * q], x[2 * q + 1]);
-      } else {
-#pragma unroll
-        for (int q = 0; q < kMlpInPad / 2; ++q) xr[q] = 0u;
-      }
-      __syncwarp();
-      mlp_warp_forward(W, sX, sY, 32 * (t >> 5));
-      __syncwarp();
-      if (t < Np) {
-        nut = W.out_scale[0] * fmaxf(sY[2 * t], 0.f);
-        Dt = W.out_scale[1] * fmaxf(sY[2 * t + 1], 0.f);
+        nut = W.out_scale[0] * fmaxf(y0, 0.f);
+        Dt = W.out_scale[1] * fmaxf(y1, 0.f);
       }
     }
     if (t < Np) {
@@ -223,6 +228,10 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
       }
     }
     __syncthreads();
+  }
+  if (CL == 2) {
+    if (stalled) tcs.err = 1;
+    tc_teardown(tcs, P.flags + 1);
   }
   if (fail) atomicAdd(P.flags, 1);
 }
@@ -480,7 +489,9 @@ cudaError_t launch_shadow32c(const double *Q64, float *S, const KParams &P, int 
 template <bool MOIST, int CL>
 static void grad32c_instance(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s) {
   static int grid = 0;
-  if (!grid) grid = grid_for((const void *)k_grad32c<4, MOIST, CL>, 1 << 30, 0);
+  if (!grid)
+    grid = CL == 2 ? grid_for_tc((const void *)k_grad32c<4, MOIST, CL>, 1 << 30, kTcCols)
+                   : grid_for((const void *)k_grad32c<4, MOIST, CL>, 1 << 30, 0);
   k_grad32c<4, MOIST, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, P);
 }
 

@@ -110,3 +110,41 @@ def test_warped_free_stream(orc):
     inner = (ez > 0) & (ez < m["nez"] - 1)
     # interior elements see no walls: the uniform flow stays uniform up to FP32 rounding
     assert np.abs(R[inner][:, 1:4]).max() < 1e-5 * rho * 100.0 / 100.0
+
+
+def test_warped_tendency_with_learned_closure(orc):
+    """The curvilinear gradient pass with the learned closure on the tcgen05
+    tensor cores (BF16 network, per-node Delta of the curved elements)
+    against the oracle's BF16-defined network: bound 1e-4 relative L2, as
+    on the flat mesh (a hidden activation can round to the neighbouring BF16
+    value)."""
+    from paper_2110_00853_b300 import cmles
+    m = _hill_box()
+    ph = _phys(m)
+    ph["closure"] = "mlp"
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case("c3"))
+    rng = np.random.default_rng(32)
+    u = rng.uniform(-2.0, 2.0, size=(Q.shape[0], 3, Q.shape[2]))
+    Q = Q.copy()
+    Q[:, 4] += 0.5 * Q[:, 0] * (u ** 2).sum(1) + (Q[:, 1:4] * u).sum(1)
+    Q[:, 1:4] += Q[:, 0][:, None] * u
+    bf = np.vectorize(orc.bf16)
+    W = {"W1": bf(rng.normal(size=(64, 13)) * 0.3), "b1": rng.normal(size=64).astype(np.float32) * 0.1,
+         "W2": bf(rng.normal(size=(64, 64)) * 0.15), "b2": rng.normal(size=64).astype(np.float32) * 0.1,
+         "W3": bf(rng.normal(size=(2, 64)) * 0.1), "b3": np.array([0.7, 0.5], np.float32)}
+    W = {k: np.asarray(v, np.float64) for k, v in W.items()}
+    in_scale, out_scale = np.array([1.0] * 9 + [30.0] * 3 + [0.02]), np.array([20.0, 40.0])
+    S.set_mlp(W, in_scale, out_scale)
+    R_orc, _ = S.rhs(Q)
+    assert S.intermediates()["nut"].max() > 1.0
+    flat = np.concatenate([W[k].ravel() for k in ("W1", "b1", "W2", "b2", "W3", "b3")] +
+                          [in_scale, out_scale]).astype(np.float32)
+    G = cmles.Solver(m, ph, precision="fp32")
+    G.set_reference(rr.ravel(), pr.ravel(), None)
+    G.set_closure_weights(flat)
+    R_gpu = G.tendency(torch.from_numpy(Q).cuda()).cpu().numpy()
+    errs = [_rel(R_gpu[:, v], R_orc[:, v]) for v in range(5)]
+    print("warped fp32 learned closure rel L2", errs)
+    assert G.diagnostics(raise_on_error=False)["status"] == 0
+    for v in range(5):
+        assert errs[v] <= 1e-4, (v, errs)
