@@ -3,11 +3,17 @@
 // (The paper has no learned closure; this network extends its Sec. 4, with
 // Smagorinsky-Lilly kept as fallback.)
 //
-// One warp evaluates 32 rows (two m16 tiles) with mma.sync m16n8k16 BF16.
-// The accumulator fragment of two neighbouring n8 tiles is exactly the A
-// fragment of the next layer's k16 tile, so hidden activations never leave
-// registers.  Weights are stored out-major with the input index contiguous
-// (W[n][k]), which is the k-contiguous B layout the instruction wants.
+// Two evaluation paths share the packed weights:
+//  * inference (the gradient passes and cmles_mlp_forward) on the tcgen05
+//    tensor cores, one CTA per 128 rows with the accumulators in Tensor
+//    Memory (mlp_tc_forward, end of this file);
+//  * the training kernels, which also need the pre-activations and the
+//    backward products per warp, on warp-level mma.sync m16n8k16: one warp
+//    evaluates 32 rows (two m16 tiles); the accumulator fragment of two
+//    neighbouring n8 tiles is exactly the A fragment of the next layer's k16
+//    tile, so hidden activations never leave registers.  Weights are stored
+//    out-major with the input index contiguous (W[n][k]), the k-contiguous B
+//    layout the instruction wants.
 #pragma once
 
 #include <cuda_bf16.h>
