@@ -55,8 +55,8 @@ DTYPE = {"fp32": "f32", "fp64": "f64"}
 # divided by the nodes; the traffic is per node, so it scales to the full box by
 # the node count).  Only kernels whose every launch does the same work: the
 # gradient pass.  Remove an entry when its kernel changes.
-TRAFFIC_B_PER_NODE = {("fp32acc64_mlp", "grad"): 92.75, ("fp32acc64_sl", "grad"): 88.26,
-                      ("fp64_sl", "grad"): 185.57}
+TRAFFIC_B_PER_NODE = {("fp32acc64_mlp", "grad"): 88.07, ("fp32acc64_sl", "grad"): 88.19,
+                      ("fp64_sl", "grad"): 185.0}
 
 
 def measured_peaks():
