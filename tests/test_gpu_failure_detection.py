@@ -1,8 +1,9 @@
 """Failure detection without a GPU fault: a non-finite value planted in the
-state on the host, and a Newton iteration cap too small for the saturated
-nodes of the moist layer.  Both are reported by cmles_diagnostics as status
-codes (CMLES_ERR_NONFINITE, CMLES_ERR_SATADJ) with the context left usable:
-after a good state is set the next report is clean."""
+state on the host, a Newton iteration cap too small for the saturated nodes
+of the moist layer, and a bounded tensor-core wait that runs out on a barrier
+nothing arrives on (test hook).  Each is reported by cmles_diagnostics as a
+status code (CMLES_ERR_NONFINITE, CMLES_ERR_SATADJ, CMLES_ERR_TIMEOUT) with
+the context left usable: afterwards the next report is clean."""
 import numpy as np
 import pytest
 
