@@ -586,15 +586,48 @@ void orc_lsrk54_coefficients(double A[5], double B[5], double c[5]) {
   c[4] = 2802321613138.0 / 2924317926251.0;
 }
 
-int orc_lsrk54(orc_solver *s, double *Q, int nsteps, double dt) {
-  double A[5], B[5], c[5];
-  orc_lsrk54_coefficients(A, B, c);
+/* Fourteen-stage fourth-order 2N-storage coefficients of Niegemann, Diehl &
+ * Busch (2012), the integrator Sec. 3.2 names for the isotropic benchmarks
+ * (a large real-axis stability interval, about [-18.5, 0]). */
+void orc_lsrk144_coefficients(double A[14], double B[14], double c[14]) {
+  static const double a[14] = {0.0,
+                               -0.7188012108672410,
+                               -0.7785331173421570,
+                               -0.0053282796654044,
+                               -0.8552979934029281,
+                               -3.9564138245774565,
+                               -1.5780575380587385,
+                               -2.0837094552574054,
+                               -0.7483334182761610,
+                               -0.7032861106563359,
+                               0.0013917096117681,
+                               -0.0932075369637460,
+                               -0.9514200470875948,
+                               -7.1151571693922548};
+  static const double b[14] = {0.0367762454319673, 0.3136296607553959, 0.1531848691869027, 0.0030097086818182,
+                               0.3326293790646110, 0.2440251405350864, 0.3718879239592277, 0.6204126221582444,
+                               0.1524043173028741, 0.0760894927419266, 0.0077604214040978, 0.0024647284755382,
+                               0.0780348340049386, 5.5059777270269628};
+  static const double cc[14] = {0.0, 0.0367762454319673, 0.1249685262725025, 0.2446177702277698,
+                                0.2476149531070420, 0.2969311120382472, 0.3978149645802642, 0.5270854589440328,
+                                0.6981269994175695, 0.8190890835352128, 0.8527059887098624, 0.8604711817462826,
+                                0.8627060376969976, 0.8734213127600976};
+  for (int k = 0; k < 14; ++k) {
+    A[k] = a[k];
+    B[k] = b[k];
+    c[k] = cc[k];
+  }
+}
+
+/* nsteps steps of a 2N-storage scheme with S stages (Sec. 3.2):
+ * per stage dQ <- A_s dQ + dt RHS(Q), Q <- Q + B_s dQ. */
+static int lsrk_2n(orc_solver *s, double *Q, int nsteps, double dt, const double *A, const double *B, int S) {
   size_t n6 = (size_t)s->E * s->Np * 6;
   double *dQ = (double *)calloc(n6, sizeof(double));
   double *R = (double *)malloc(n6 * sizeof(double));
   int fails = 0;
   for (int st = 0; st < nsteps; ++st)
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < S; ++k) {
       fails += orc_rhs(s, Q, R, 0);
       for (size_t q = 0; q < n6; ++q) {
         dQ[q] = A[k] * dQ[q] + dt * R[q];
@@ -604,6 +637,18 @@ int orc_lsrk54(orc_solver *s, double *Q, int nsteps, double dt) {
   free(dQ);
   free(R);
   return fails;
+}
+
+int orc_lsrk54(orc_solver *s, double *Q, int nsteps, double dt) {
+  double A[5], B[5], c[5];
+  orc_lsrk54_coefficients(A, B, c);
+  return lsrk_2n(s, Q, nsteps, dt, A, B, 5);
+}
+
+int orc_lsrk144(orc_solver *s, double *Q, int nsteps, double dt) {
+  double A[14], B[14], c[14];
+  orc_lsrk144_coefficients(A, B, c);
+  return lsrk_2n(s, Q, nsteps, dt, A, B, 14);
 }
 
 /* ------------------------------------------------------------ diagnostics */

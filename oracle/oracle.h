@@ -149,6 +149,8 @@ void orc_intermediates(const orc_solver *s, double *G, double *gradG, double *nu
 /* LSRK(5,4) of Carpenter & Kennedy (1994): advance Q in place by nsteps of dt. */
 int orc_lsrk54(orc_solver *s, double *Q, int nsteps, double dt);
 void orc_lsrk54_coefficients(double A[5], double B[5], double c[5]);
+int orc_lsrk144(orc_solver *s, double *Q, int nsteps, double dt);
+void orc_lsrk144_coefficients(double A[14], double B[14], double c[14]);
 
 /* Global budgets sum_e sum_i w_i J_i Q_v for all 6 variables; returns 1 if any
  * entry of Q is non-finite. */

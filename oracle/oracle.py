@@ -105,6 +105,9 @@ def _declare(L):
     L.orc_lsrk54.argtypes = [C.c_void_p, _DP, C.c_int, C.c_double]
     L.orc_lsrk54.restype = C.c_int
     L.orc_lsrk54_coefficients.argtypes = [_DP, _DP, _DP]
+    L.orc_lsrk144.argtypes = [C.c_void_p, _DP, C.c_int, C.c_double]
+    L.orc_lsrk144.restype = C.c_int
+    L.orc_lsrk144_coefficients.argtypes = [_DP, _DP, _DP]
     L.orc_budgets.argtypes = [C.c_void_p, _DP, _DP]
     L.orc_budgets.restype = C.c_int
     L.orc_favre_profiles.argtypes = [C.c_void_p, _DP, _DP]
@@ -250,6 +253,12 @@ def lsrk54_coefficients():
     return A, B, c
 
 
+def lsrk144_coefficients():
+    A, B, c = np.zeros(14), np.zeros(14), np.zeros(14)
+    lib().orc_lsrk144_coefficients(_p(A), _p(B), _p(c))
+    return A, B, c
+
+
 def mlp_forward(X, W):
     X = np.ascontiguousarray(X, float)
     Y = np.zeros((X.shape[0], 2))
@@ -356,6 +365,11 @@ class Solver:
     def lsrk54(self, Q, nsteps, dt):
         Q = np.ascontiguousarray(Q, float).copy()
         fails = lib().orc_lsrk54(self.h, _p(Q), nsteps, dt)
+        return Q, fails
+
+    def lsrk144(self, Q, nsteps, dt):
+        Q = np.ascontiguousarray(Q, float).copy()
+        fails = lib().orc_lsrk144(self.h, _p(Q), nsteps, dt)
         return Q, fails
 
     def budgets(self, Q):

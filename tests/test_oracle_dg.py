@@ -205,12 +205,14 @@ def test_isentropic_vortex_convergence_order(orc):
     assert order > 4.5, (e8, e16, order)     # N + 1 = 5
 
 
-def test_lsrk54_fourth_order_in_time(orc):
+@pytest.mark.parametrize("scheme", ["lsrk54", "lsrk144"])
+def test_lsrk_fourth_order_in_time(orc, scheme):
     m = I.mesh("c1")
     S, Q, rr, pr, _ = orc.from_inputs(m, I.physics("c1"), I.case("c1"))
     Q = _fuzz_velocity(S, Q, 3.0, 4)
-    T = 0.32
-    sols = [S.lsrk54(Q, n, T / n)[0] for n in (4, 8, 16)]
+    T = 0.32 if scheme == "lsrk54" else 0.96
+    step = getattr(S, scheme)
+    sols = [step(Q, n, T / n)[0] for n in (4, 8, 16)]
     e1 = np.abs(sols[0] - sols[1])[:, 1:4].max()
     e2 = np.abs(sols[1] - sols[2])[:, 1:4].max()
     assert 12.0 < e1 / e2 < 20.0, (e1, e2)

@@ -368,6 +368,58 @@ def test_lsrk54_stability_polynomial(orc):
         assert abs(y - Rz) < 1e-10 * max(1, abs(Rz))
 
 
+# ------------------------------------------------------------------ LSRK order conditions
+
+def _butcher_2n(A, B):
+    """Butcher tableau (a, b) of a 2N-storage scheme: with k_j = dt RHS(Y_j),
+    the register after stage i is dQ_i = sum_{j<=i} (prod_{m=j+1..i} A_m) k_j
+    and Y_{s+1} = Q + sum_{i<=s} B_i dQ_i."""
+    S = len(A)
+    a = np.zeros((S + 1, S))
+    for s in range(1, S + 1):
+        for j in range(s):
+            a[s, j] = sum(B[i] * np.prod(A[j + 1:i + 1]) for i in range(j, s))
+    return a[:S], a[S]
+
+
+@pytest.mark.parametrize("scheme", ["lsrk54", "lsrk144"])
+def test_lsrk_fourth_order_conditions(orc, scheme):
+    """The eight order conditions of a fourth-order Runge-Kutta method (Butcher
+    trees up to order 4) hold for the 2N-storage tables of Sec. 3.2's
+    integrators, Carpenter & Kennedy (1994) with 5 stages and Niegemann, Diehl
+    & Busch (2012) with 14; the stage times are the row sums, and neither
+    scheme is fifth order."""
+    A, B, c = getattr(orc, scheme + "_coefficients")()
+    assert len(A) == {"lsrk54": 5, "lsrk144": 14}[scheme] and A[0] == 0.0
+    a, b = _butcher_2n(A, B)
+    assert np.abs(a.sum(1) - c).max() < 1e-12
+    conds = [(b.sum(), 1.0), (b @ c, 1 / 2), (b @ c ** 2, 1 / 3), (b @ (a @ c), 1 / 6), (b @ c ** 3, 1 / 4),
+             (b @ (c * (a @ c)), 1 / 8), (b @ (a @ c ** 2), 1 / 12), (b @ (a @ (a @ c)), 1 / 24)]
+    for v, t in conds:
+        assert abs(v - t) < 1e-12, (scheme, v, t)
+    assert abs(b @ c ** 4 - 1 / 5) > 1e-5
+
+
+def _amplification(A, B, z):
+    y, dy = 1.0 + 0j, 0j
+    for s in range(len(A)):
+        dy = A[s] * dy + z * y
+        y = y + B[s] * dy
+    return abs(y)
+
+
+def test_lsrk144_real_axis_stability(orc):
+    """The 14-stage scheme is stable on the negative real axis down to about
+    -18.5, 1.3 per stage against LSRK(5,4)'s 4.65 / 5 = 0.93: the large
+    explicit stability region Sec. 3.2 cites it for."""
+    A, B, _ = orc.lsrk144_coefficients()
+    assert all(_amplification(A, B, x) <= 1 + 1e-12 for x in np.linspace(-18.4, 0.0, 4001))
+    assert _amplification(A, B, -19.0) > 1.0
+    A5, B5, _ = orc.lsrk54_coefficients()
+    assert all(_amplification(A5, B5, x) <= 1 + 1e-12 for x in np.linspace(-4.6, 0.0, 1001))
+    assert _amplification(A5, B5, -4.8) > 1.0
+
+
 # ------------------------------------------------------------------ MLP
 
 def _rand_w(rng, scale=0.3):
