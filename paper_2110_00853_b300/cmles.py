@@ -19,6 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "cmles.h")
 CMLES_FP64, CMLES_FP32_ACC64 = 0, 1
 CLOSURE = {"none": 0, "sl": 1, "mlp": 2, "vreman": 3}
 FLUX = {"rusanov": 0, "hllc": 1, "roe": 2}
+INTEGRATOR = {"lsrk54": 0, "lsrk144": 1}
 PRECISION = {"fp64": CMLES_FP64, "fp32": CMLES_FP32_ACC64, "fp32acc64": CMLES_FP32_ACC64}
 STATUS = {0: "CMLES_OK", 1: "CMLES_ERR_ARG", 2: "CMLES_ERR_OOM", 3: "CMLES_ERR_CUDA", 4: "CMLES_ERR_SATADJ",
           5: "CMLES_ERR_NONFINITE", 6: "CMLES_ERR_MESH", 7: "CMLES_ERR_STATE", 8: "CMLES_ERR_TIMEOUT"}
@@ -41,7 +42,7 @@ class Params(C.Structure):
         ("u_relax", C.c_double * 3), ("lateral_sponge_frac", C.c_double), ("surface_flux", C.c_int),
         ("shf", C.c_double), ("lhf", C.c_double), ("Omega", C.c_double * 3), ("precision", C.c_int),
         ("dt", C.c_double), ("satadj_max_iter", C.c_int), ("flux", C.c_int), ("filter_order", C.c_int),
-        ("filter_alpha", C.c_double), ("filter_vars", C.c_int)]
+        ("filter_alpha", C.c_double), ("filter_vars", C.c_int), ("integrator", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -177,6 +178,8 @@ def make_params(d, precision="fp64"):
             P.closure = CLOSURE[v]
         elif k == "flux":
             P.flux = FLUX[v]
+        elif k == "integrator":
+            P.integrator = INTEGRATOR[v]
         elif k in ("u_relax", "Omega"):
             setattr(P, k, (C.c_double * 3)(*v))
         elif k in ("richardson", "moist", "surface_flux"):

@@ -25,6 +25,26 @@ const double kLsrkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 1
                           1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                           2277821191437.0 / 14882151754819.0};
 
+// LSRK(14,4), Niegemann, Diehl & Busch (2012), the same 2N-storage form.
+const double kLsrk14A[14] = {0.0,
+                             -0.7188012108672410,
+                             -0.7785331173421570,
+                             -0.0053282796654044,
+                             -0.8552979934029281,
+                             -3.9564138245774565,
+                             -1.5780575380587385,
+                             -2.0837094552574054,
+                             -0.7483334182761610,
+                             -0.7032861106563359,
+                             0.0013917096117681,
+                             -0.0932075369637460,
+                             -0.9514200470875948,
+                             -7.1151571693922548};
+const double kLsrk14B[14] = {0.0367762454319673, 0.3136296607553959, 0.1531848691869027, 0.0030097086818182,
+                             0.3326293790646110, 0.2440251405350864, 0.3718879239592277, 0.6204126221582444,
+                             0.1524043173028741, 0.0760894927419266, 0.0077604214040978, 0.0024647284755382,
+                             0.0780348340049386, 5.5059777270269628};
+
 struct TimedLaunch {
   int kind;
   cudaEvent_t a, b;
@@ -592,6 +612,7 @@ void cmles_default_params(cmles_params *p) {
   p->filter_order = 0;
   p->filter_alpha = -log(pow(2.0, -52));
   p->filter_vars = 0xE;
+  p->integrator = CMLES_LSRK54;
 }
 
 // Tangent table of the saturation vapour density rho_vs(T) = p_v*(T)/(R_v T)
@@ -703,6 +724,7 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
     return CMLES_ERR_ARG;
   if (params->filter_order < 0 || !(params->filter_alpha >= 0.0) || (params->filter_vars & ~0xE) != 0)
     return CMLES_ERR_ARG;
+  if (params->integrator != CMLES_LSRK54 && params->integrator != CMLES_LSRK144) return CMLES_ERR_ARG;
   // Vreman's directional lengths are those of the flat elements
   if (params->closure == CMLES_CLOSURE_VREMAN && mesh->warp) return CMLES_ERR_ARG;
   // the learned closure runs on BF16 tensor cores inside the FP32 kernels
@@ -1164,10 +1186,13 @@ cmles_status cmles_step(cmles_handle h, int nsteps) {
     cmles_status st = ensure_shadow(h);
     if (st != CMLES_OK) return st;
   }
+  const bool l14 = h->prm.integrator == CMLES_LSRK144;
+  const int nst = l14 ? 14 : 5;
+  const double *TA = l14 ? kLsrk14A : kLsrkA, *TB = l14 ? kLsrk14B : kLsrkB;
   for (int s = 0; s < nsteps; ++s) {
-    for (int k = 0; k < 5; ++k) {
-      StageCoef sc = {kLsrkA[k], kLsrkB[k], h->prm.dt, k == 4, (float)kLsrkA[k], (float)kLsrkB[k],
-                      (float)h->prm.dt, kLsrkA[k] == 0.0};
+    for (int k = 0; k < nst; ++k) {
+      StageCoef sc = {TA[k], TB[k], h->prm.dt, k == nst - 1, (float)TA[k], (float)TB[k], (float)h->prm.dt,
+                      TA[k] == 0.0};
       cmles_status st;
       if (h->fp32) {
         st = run_stage_pair32(h, h->S32[h->scur], h->S32[1 - h->scur], nullptr, sc, true);

@@ -110,3 +110,26 @@ def test_density_current_hllc_roe_vreman(orc, flux):
     ref = _front_reference(50.0, "vreman")
     print("density current front at 900 s, vreman +", flux, front, "m; paper (vreman, 50 m):", ref)
     assert abs(front - ref) <= 0.03 * ref
+
+
+def test_density_current_lsrk144_double_step(orc):
+    """The 14-stage integrator (Sec. 3.2) at twice the 5-stage scheme's time
+    step (0.05 s, 18000 steps to 900 s) on the 50 m SL case: stays finite and
+    puts the front within 3 % of the paper's value."""
+    from paper_2110_00853_b300 import cmles
+    m, ph, c = I.mesh("dc"), I.physics("dc", closure="sl"), I.case("dc")
+    ph["integrator"] = "lsrk144"
+    ph["dt"] = 0.05
+    G = cmles.Solver(m, ph, precision="fp32")
+    G.init_case(c)
+    G.step(int(round(900.0 / ph["dt"])))
+    d = G.diagnostics()
+    assert not d["nonfinite"] and abs(d["time"] - 900.0) < 1e-6
+    Q = G.get_state().cpu().numpy()
+    xi, _, _ = orc.lgl(4)
+    x, th = _surface_theta(Q, m, xi)
+    i = np.where(th - 300.0 <= -1.0)[0].max()
+    front = x[i] + (x[i + 1] - x[i]) * ((th[i] - 299.0) / (th[i] - th[i + 1]))
+    ref = _front_reference(50.0, "sl")
+    print("density current front at 900 s, SL, LSRK(14,4), dt 0.05 s:", front, "m; paper:", ref)
+    assert abs(front - ref) <= 0.03 * ref

@@ -212,6 +212,27 @@ def test_lsrk_steps_and_budgets(orc):
     assert diag["steps"] == nsteps and not diag["nonfinite"]
 
 
+def test_lsrk144_steps_and_budgets(orc):
+    # the 14-stage integrator of Sec. 3.2 (Niegemann, Diehl & Busch 2012) at
+    # twice the 5-stage scheme's step, against the oracle's
+    m = I.sub_mesh("c2", 3, 4, 16)
+    ph = dict(I.physics("c2"), integrator="lsrk144")
+    ph["dt"] *= 2.0
+    S, Q, G = _setup(orc, "c2", m, phys=ph, fuzz_seed=7)
+    nsteps = 2
+    Q_orc, fails = S.lsrk144(Q, nsteps, ph["dt"])
+    assert fails == 0
+    G.set_state(torch.from_numpy(Q).cuda())
+    G.step(nsteps)
+    Q_gpu = G.get_state().cpu().numpy()
+    for v in range(6):
+        assert _rel_l2(Q_gpu[:, v] - Q[:, v], Q_orc[:, v] - Q[:, v]) <= 1e-11, v
+    diag = G.diagnostics()
+    b_orc, _ = S.budgets(Q_orc)
+    assert np.allclose(diag["budget"], b_orc, rtol=1e-13, atol=0)
+    assert diag["steps"] == nsteps and abs(diag["time"] - nsteps * ph["dt"]) < 1e-12
+
+
 def test_determinism(orc):
     S, Q, G = _setup(orc, "c1", I.mesh("c1"), fuzz_seed=7)
     Qd = torch.from_numpy(Q).cuda()

@@ -175,6 +175,24 @@ def test_fp32_steps_track_oracle(orc):
         assert _rel_l2(dq_g, dq_o) <= 1e-5, v
 
 
+def test_fp32_lsrk144_steps_track_oracle(orc):
+    # 14-stage integrator on the FP32 path: the step's increments summed in
+    # FP32 over fourteen stages, one FP64 accumulation per step
+    m = I.sub_mesh("c2", 4, 4, 16)
+    ph = dict(I.physics("c2"), integrator="lsrk144")
+    ph["dt"] *= 2.0
+    S, Q, G = _setup(orc, "c2", m, phys=ph, fuzz_seed=16)
+    n = 3
+    Q_orc, _ = S.lsrk144(Q, n, ph["dt"])
+    G.set_state(torch.from_numpy(Q).cuda())
+    G.step(n)
+    Q_gpu = G.get_state().cpu().numpy()
+    for v in range(6):
+        dq_o, dq_g = Q_orc[:, v] - Q[:, v], Q_gpu[:, v] - Q[:, v]
+        print("fp32 lsrk144 3-step increment rel L2", v, _rel_l2(dq_g, dq_o))
+        assert _rel_l2(dq_g, dq_o) <= 1e-5, v
+
+
 def test_fp32_steps_with_exponential_filter(orc):
     alpha = -np.log(2.0 ** -52)
     m = I.sub_mesh("c2", 4, 4, 16)
