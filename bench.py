@@ -28,27 +28,37 @@ sys.path.insert(0, ROOT)
 from paper_2110_00853_b300 import inputs as I  # noqa: E402
 
 WORKLOAD = "c5"
-STAGES = 5
+STAGES = {"lsrk54": 5, "lsrk144": 14}
 METRIC = "DG node-stage updates/s at 1 B300 and HBM roofline %, FP32+learned vs FP64 plain"
 # algorithmic bytes per node for each kernel launch (compulsory traffic),
-# averaged over the five stages of a step:
+# averaged over the S stages of a step (S = 5 for LSRK(5,4)):
 #   gradient pass: read Q, write F2 (15 words) and aux (2 words)
 #   flux/update pass, FP64 path: read Q, F2, aux; write dQ and Q_out; read dQ
-#     except in the first stage (A_1 = 0): (4 * 41 + 35) words / 5
+#     except in the first stage (A_1 = 0): ((S - 1) * 41 + 35) words / S
 #   flux/update pass, FP32 path (FP32 shadow S, FP32 register dQ and step
 #     increment D, FP64 state Q64): read S, F2, aux (23 words) in every stage;
-#     stage 1 writes dQ, D, S (+18); stages 2-4 read dQ, D and write dQ, D, S
-#     (+30); stage 5 reads dQ, D, reads and writes Q64 and writes S (+12 + 24
-#     FP32 words for Q64): (41 + 3 * 53 + 65) words / 5 = 53 words
-BYTES = {
-    "fp64": {"grad": (6 + 15 + 2) * 8, "rhs": (4 * 41 + 35) * 8 / 5},
-    "fp32": {"grad": (6 + 15 + 2) * 4, "rhs": (41 + 3 * 53 + 65) * 4 / 5},
-}
-# name: (precision, closure, numerical flux of F1); the first three are the
-# default run, the others are reported when asked for with --variants
-VARIANTS = {"fp32acc64_mlp": ("fp32", "mlp", "rusanov"), "fp32acc64_sl": ("fp32", "sl", "rusanov"),
-            "fp64_sl": ("fp64", "sl", "rusanov"), "fp32acc64_vreman": ("fp32", "vreman", "rusanov"),
-            "fp32acc64_mlp_hllc": ("fp32", "mlp", "hllc"), "fp32acc64_mlp_roe": ("fp32", "mlp", "roe")}
+#     stage 1 writes dQ, D, S (+18); the middle stages read dQ, D and write dQ,
+#     D, S (+30); the last stage reads dQ, D, reads and writes Q64 and writes S
+#     (+12 + 24 FP32 words for Q64): (41 + (S - 2) * 53 + 65) words / S, 53
+#     words for S = 5
+def alg_bytes(prec, kind, stages=5):
+    if kind == "grad":
+        return (6 + 15 + 2) * (8 if prec == "fp64" else 4)
+    if prec == "fp64":
+        return ((stages - 1) * 41 + 35) * 8 / stages
+    return (41 + (stages - 2) * 53 + 65) * 4 / stages
+
+
+# name: (precision, closure, numerical flux of F1, integrator); the first
+# three are the default run, the others are reported when asked for with
+# --variants
+VARIANTS = {"fp32acc64_mlp": ("fp32", "mlp", "rusanov", "lsrk54"), "fp32acc64_sl": ("fp32", "sl", "rusanov", "lsrk54"),
+            "fp64_sl": ("fp64", "sl", "rusanov", "lsrk54"),
+            "fp32acc64_vreman": ("fp32", "vreman", "rusanov", "lsrk54"),
+            "fp32acc64_mlp_hllc": ("fp32", "mlp", "hllc", "lsrk54"),
+            "fp32acc64_mlp_roe": ("fp32", "mlp", "roe", "lsrk54"),
+            "fp32acc64_mlp_lsrk144": ("fp32", "mlp", "rusanov", "lsrk144"),
+            "fp64_sl_lsrk144": ("fp64", "sl", "rusanov", "lsrk144")}
 DTYPE = {"fp32": "f32", "fp64": "f64"}
 # DRAM bytes per node of one launch (dram__bytes_read.sum + dram__bytes_write.sum
 # from one ncu capture on a 40 x 40 x 20-element sub-box of the box, 4M nodes,
@@ -138,10 +148,10 @@ def max_over_ranks(ms, world, torch, device):
     return float(t.item())
 
 
-def whole_job_rate(nodes_per_rank, world, steps, ms):
+def whole_job_rate(nodes_per_rank, world, steps, ms, stages=5):
     """node-stage updates per second of all ranks together over the slowest
     rank's time (replicas: every rank advances its own box)"""
-    return nodes_per_rank * world * STAGES * steps / (ms / 1e3)
+    return nodes_per_rank * world * stages * steps / (ms / 1e3)
 
 
 def fp64_peak(torch, n=8192, reps=5):
@@ -179,10 +189,11 @@ def workload_mesh(sub):
     return I.mesh(WORKLOAD) if sub is None else I.sub_mesh(WORKLOAD, *sub)
 
 
-def run_variant(name, precision, closure, flux, steps, warmup, world, rank, torch, sub=None):
+def run_variant(name, precision, closure, flux, integrator, steps, warmup, world, rank, torch, sub=None):
     from paper_2110_00853_b300 import cmles
     mesh, phys, case = workload_mesh(sub), I.physics(WORKLOAD, closure=closure), I.case(WORKLOAD)
     phys["flux"] = flux
+    phys["integrator"] = integrator
     G = cmles.Solver(mesh, phys, precision=precision)
     G.init_case(case)
     if closure == "mlp":
@@ -221,13 +232,14 @@ def run_variant(name, precision, closure, flux, steps, warmup, world, rank, torc
                 finite=not diag["nonfinite"], satadj_failures=diag["satadj_failures"])
 
 
-def run_e2e(precision, closure, flux, steps, torch):
+def run_e2e(precision, closure, flux, integrator, steps, torch):
     """Same metric through the C ABI with host buffers: every step uploads the
     state from pinned host memory, advances one LSRK step and reads back the
     budget diagnostics."""
     from paper_2110_00853_b300 import cmles
     mesh, phys, case = I.mesh(WORKLOAD), I.physics(WORKLOAD, closure=closure), I.case(WORKLOAD)
     phys["flux"] = flux
+    phys["integrator"] = integrator
     G = cmles.Solver(mesh, phys, precision=precision)
     G.init_case(case)
     if closure == "mlp":
@@ -247,7 +259,7 @@ def run_e2e(precision, closure, flux, steps, torch):
     del host, G
     torch.cuda.empty_cache()
     sec = (t1 - t0) / steps
-    return dict(value=nodes * STAGES / sec, unit="node-stage/s", h2d_bytes_per_step=h2d,
+    return dict(value=nodes * STAGES[integrator] / sec, unit="node-stage/s", h2d_bytes_per_step=h2d,
                 d2h_bytes_per_step=7 * 8 + 16 * 4)
 
 
@@ -271,7 +283,7 @@ def cpu_baseline(max_seconds=20.0):
     sec = time.perf_counter() - t0
     nodes = S.E * S.Np
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return dict(value=nodes * STAGES * steps / sec, unit="node-stage/s", cores=cores, kind="oracle",
+    return dict(value=nodes * STAGES["lsrk54"] * steps / sec, unit="node-stage/s", cores=cores, kind="oracle",
                 sample=f"{n[0]}x{n[1]}x{n[2]}-element sub-box of the {WORKLOAD} workload (same element size, "
                        f"moist SL physics, {nodes} nodes), {steps} LSRK(5,4) step(s) after 1 warm-up step")
 
@@ -319,31 +331,33 @@ def main():
     hbm, peak_kind = measured_peaks()
     variants = [(n,) + VARIANTS[n] for n in args.variants.split(",")]
     results = {}
-    for name, prec, clo, flux in variants:
-        results[name] = run_variant(name, prec, clo, flux, args.steps, args.warmup, world, rank, torch, sub)
+    for name, prec, clo, flux, integ in variants:
+        results[name] = run_variant(name, prec, clo, flux, integ, args.steps, args.warmup, world, rank, torch, sub)
     head = results[variants[0][0]]
     prec = variants[0][1]
-    value = whole_job_rate(head["nodes"], world, args.steps, head["ms"])
+    hstages = STAGES[variants[0][4]]
+    value = whole_job_rate(head["nodes"], world, args.steps, head["ms"], hstages)
     kt = head["kt"]
     kinds = ["grad", "rhs"]
     dom = max(range(2), key=lambda k: kt["ms"][k])
     avg_ms = kt["ms"][dom] / max(kt["count"][dom], 1)
-    achieved = head["nodes"] * BYTES[prec][kinds[dom]] / (avg_ms / 1e3) / 1e9
+    achieved = head["nodes"] * alg_bytes(prec, kinds[dom], hstages) / (avg_ms / 1e3) / 1e9
     tb = TRAFFIC_B_PER_NODE.get((variants[0][0], kinds[dom]))
     traffic = tb * head["nodes"] if tb is not None else None
     out_variants = {}
-    for (name, vprec, _, _), r in zip(variants, results.values()):
-        v = whole_job_rate(r["nodes"], world, args.steps, r["ms"])
+    for (name, vprec, _, _, vint), r in zip(variants, results.values()):
+        v = whole_job_rate(r["nodes"], world, args.steps, r["ms"], STAGES[vint])
         per = {}
         for k in range(2):
             a = r["kt"]["ms"][k] / max(r["kt"]["count"][k], 1)
-            gbs = r["nodes"] * BYTES[vprec][kinds[k]] / (a / 1e3) / 1e9
+            gbs = r["nodes"] * alg_bytes(vprec, kinds[k], STAGES[vint]) / (a / 1e3) / 1e9
             per[kinds[k]] = dict(avg_ms=a, launches=r["kt"]["count"][k], gbs=gbs, hbm_frac=gbs / hbm)
         out_variants[name] = dict(value=v, ms_per_step=r["ms"] / args.steps, kernels=per, finite=r["finite"],
                                   satadj_failures=r["satadj_failures"])
     e2e = None
     if not args.no_e2e and rank == 0 and sub is None:
-        e2e = run_e2e(variants[0][1], variants[0][2], variants[0][3], max(1, min(args.steps, 2)), torch)
+        e2e = run_e2e(variants[0][1], variants[0][2], variants[0][3], variants[0][4], max(1, min(args.steps, 2)),
+                      torch)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and sub is None:
         cb = cpu_baseline()
@@ -352,11 +366,12 @@ def main():
                     warmup=args.warmup, ms_per_step=head["ms"] / args.steps, higher_is_better=True,
                     scaling="weak", vs_baseline=None, dtype=DTYPE[prec], data="synthetic",
                     config={"workload": f"{WORKLOAD}: 160x160x80 hexahedral elements, N=4 (256M nodes), moist, "
-                                        "LSRK(5,4)", "variant": variants[0][0],
+                                        + {"lsrk54": "LSRK(5,4)", "lsrk144": "LSRK(14,4)"}[variants[0][4]],
+                            "variant": variants[0][0],
                             "closure": {"mlp": "learned (BF16 tensor-core MLP 13-64-64-2, seeded weights)",
                                         "sl": "Smagorinsky-Lilly + Richardson",
                                         "vreman": "Vreman + Richardson"}[variants[0][2]],
-                            "flux": variants[0][3],
+                            "flux": variants[0][3], "integrator": variants[0][4],
                             "elements": head["nodes"] // 125, "nodes_per_gpu": head["nodes"],
                             "l2": "inputs larger than L2 (state alone 12 GB)", "parallelism": f"replicas{world}"},
                     roofline={"bound": "hbm", "kernel": kinds[dom], "achieved": achieved, "peak": hbm,
