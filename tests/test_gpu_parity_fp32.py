@@ -176,8 +176,16 @@ def test_fp32_steps_track_oracle(orc):
 
 
 def test_fp32_lsrk144_steps_track_oracle(orc):
-    # 14-stage integrator on the FP32 path: the step's increments summed in
-    # FP32 over fourteen stages, one FP64 accumulation per step
+    """14-stage integrator on the FP32 path.  The scheme's step is
+    Q + sum_j b_j k_j with sum_j |b_j| = 98.6 and internal stage weights up to
+    |a_ij| = 39 (LSRK(5,4): 1.0 and 0.82), so every per-stage rounding of the
+    FP32 tendency reaches the step increment about a hundred times larger.
+    Emulating the FP32 path on the CPU (FP64 tendencies of the FP32-rounded
+    shadow state, rounded to FP32; FP32 registers) on this fuzzed state gives
+    2e-5 / 1e-4 / 3e-4 relative L2 for rho / rho e / rho q_t with the 14-stage
+    scheme against 1e-6 / 3e-6 / 8e-6 with LSRK(5,4); keeping Q and dQ in FP64
+    every stage does not help (3e-5 / 2e-4 / 5e-4), the error being the
+    tendencies' own.  Bound: the FP32 bound 1e-5 times sum |b_j|, 1e-3."""
     m = I.sub_mesh("c2", 4, 4, 16)
     ph = dict(I.physics("c2"), integrator="lsrk144")
     ph["dt"] *= 2.0
@@ -187,10 +195,10 @@ def test_fp32_lsrk144_steps_track_oracle(orc):
     G.set_state(torch.from_numpy(Q).cuda())
     G.step(n)
     Q_gpu = G.get_state().cpu().numpy()
+    errs = [_rel_l2(Q_gpu[:, v] - Q[:, v], Q_orc[:, v] - Q[:, v]) for v in range(6)]
+    print("fp32 lsrk144 3-step increment rel L2", errs)
     for v in range(6):
-        dq_o, dq_g = Q_orc[:, v] - Q[:, v], Q_gpu[:, v] - Q[:, v]
-        print("fp32 lsrk144 3-step increment rel L2", v, _rel_l2(dq_g, dq_o))
-        assert _rel_l2(dq_g, dq_o) <= 1e-5, v
+        assert errs[v] <= 1e-3, (v, errs)
 
 
 def test_fp32_steps_with_exponential_filter(orc):
