@@ -235,7 +235,8 @@ cmles_status cmles_set_closure_weights_device(cmles_handle h, const float *param
  * cmles_mlp_forward: Y[n][2] = network(X[n][13]) on the tcgen05 tensor cores
  *   (BF16 operands, FP32 accumulation, biases folded into the contraction);
  *   synchronises the stream and returns CMLES_ERR_TIMEOUT if an MMA
- *   completion wait gave up.
+ *   completion wait gave up; n = 0 returns CMLES_OK at once (the pointers
+ *   may then be null).
  * cmles_mlp_loss_grad: loss = 1/(2n) sum |y - t|^2 over T[n][2] and its
  *   gradient with respect to the first 5186 parameters (W1 .. b3), written
  *   to grad_dev[5186] and loss_dev[1] (both overwritten).

@@ -355,8 +355,8 @@ using namespace cmles;
 extern "C" {
 
 cmles_status cmles_mlp_forward(const float *params_dev, const float *X_dev, float *Y_dev, long long n, void *stream) {
+  if (n == 0) return CMLES_OK;  // an empty batch: nothing to read or write
   if (!params_dev || !X_dev || !Y_dev || n < 0) return CMLES_ERR_ARG;
-  if (n == 0) return CMLES_OK;
   cudaStream_t s = (cudaStream_t)stream;
   MlpPacked *pk = nullptr;
   const size_t bytes = sizeof(MlpPacked) + 16;

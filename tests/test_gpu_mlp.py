@@ -73,6 +73,35 @@ def test_mlp_forward_matches_oracle_bf16(orc):
     assert err <= 1e-4
 
 
+def test_mlp_forward_persistent_ctas_and_edge_rows(orc):
+    """The tcgen05 inference kernel with many more rows than resident CTAs
+    (each CTA loops over row blocks, the mbarrier parity alternating across
+    hundreds of MMA chains) and a ragged last block, against the oracle; also
+    rows far out in the SiLU tails (|a| up to ~60), where x sigma(x) -> 0 or
+    x, and an empty batch."""
+    from paper_2110_00853_b300 import cmles
+    W = _net(orc, 5, scale=1.5)
+    rng = np.random.default_rng(6)
+    n = 300_001                                   # > 148 x 8 x 128 rows; 300001 = 2343 x 128 + 97
+    X = rng.normal(size=(n, 13)) * np.where(rng.random((n, 1)) < 0.01, 30.0, 1.0)
+    # BF16-representable inputs (round-to-nearest-even of the FP32 bits)
+    b = X.astype(np.float32).view(np.uint32)
+    X = ((b + np.uint32(0x7FFF) + ((b >> 16) & np.uint32(1))) & np.uint32(0xFFFF0000)).view(np.float32)
+    X = X.astype(np.float64)
+    assert all(orc.bf16(v) == v for v in X[:50].ravel())
+    params = torch.from_numpy(_flat(W)).cuda()
+    Yg = cmles.mlp_forward(params, torch.from_numpy(X.astype(np.float32)).cuda()).cpu().numpy()
+    Yo = orc.mlp_forward_bf16(X, W)
+    err = _rel(Yg, Yo)
+    tail = np.abs(X).max(axis=1) > 10.0
+    err_tail = _rel(Yg[tail], Yo[tail])
+    print("mlp forward 300001 rows rel L2", err, "tail rows", err_tail, int(tail.sum()))
+    assert err <= 1e-4 and err_tail <= 1e-4
+    assert np.isfinite(Yg).all()
+    Y0 = cmles.mlp_forward(params, torch.zeros((0, 13), dtype=torch.float32, device="cuda"))
+    assert Y0.shape == (0, 2)
+
+
 def test_mlp_gradient_matches_oracle(orc):
     from paper_2110_00853_b300 import cmles
     W = _net(orc, 3)
