@@ -6,9 +6,10 @@
 //   dy = (y - t)/n,  dh2 = W3^T dy,  da2 = dh2 * silu'(a2),
 //   dh1 = W2^T da2,  da1 = dh1 * silu'(a1),  silu'(a) = s (1 + a (1 - s)),
 //   gW3 += dy h2^T, gW2 += da2 h1^T, gW1 += da1 x^T, gb_l += da_l.
-// One CTA of 128 threads handles 128 samples per iteration (one row per
-// thread for pointwise work, 4 warps x 32 rows for the mma.sync products) and
-// keeps its gradient partial sums in shared memory until the end.
+// One CTA of 128 threads handles 128 samples per iteration (one sample per
+// thread for pointwise work; the products on the tcgen05 tensor cores) and
+// keeps its gradient partial sums in shared memory and Tensor Memory until
+// the end.
 #include <string.h>
 
 #include "cmles.h"
@@ -59,47 +60,21 @@ __host__ __device__ inline void tc_fill(const float *p, MlpTc *o, int q) {
   if (q < 4) o->out_scale[q] = q < 2 ? p[kMlpOffOut + q] : 0.f;
 }
 
+// Row-major BF16 copies of W2 and W3, entry q of [out][in].
+__host__ __device__ inline void rowmajor_fill(const float *p, MlpPacked *o, int q) {
+  if (q < kMlpH * kMlpH) o->W2[q] = __float2bfloat16_rn(p[kMlpOffW2 + q]);
+  if (q < kMlpOut * kMlpH) o->W3[q] = __float2bfloat16_rn(p[kMlpOffW3 + q]);
+}
+
 void pack_mlp_host(const float *p, MlpPacked *o) {
   memset(o, 0, sizeof(*o));
-  for (int n = 0; n < kMlpH; ++n)
-    for (int k = 0; k < kMlpIn; ++k) o->W1[n * kLdW1 + k] = __float2bfloat16_rn(p[kMlpOffW1 + n * kMlpIn + k]);
-  for (int n = 0; n < kMlpH; ++n)
-    for (int k = 0; k < kMlpH; ++k) o->W2[n * kLdW + k] = __float2bfloat16_rn(p[kMlpOffW2 + n * kMlpH + k]);
-  for (int n = 0; n < kMlpOut; ++n)
-    for (int k = 0; k < kMlpH; ++k) o->W3[n * kLdW + k] = __float2bfloat16_rn(p[kMlpOffW3 + n * kMlpH + k]);
-  for (int n = 0; n < kMlpH; ++n) {
-    o->b1[n] = p[kMlpOffB1 + n];
-    o->b2[n] = p[kMlpOffB2 + n];
-  }
-  o->b3[0] = p[kMlpOffB3];
-  o->b3[1] = p[kMlpOffB3 + 1];
-  for (int k = 0; k < kMlpIn; ++k) o->in_scale[k] = p[kMlpOffIn + k];
-  o->out_scale[0] = p[kMlpOffOut];
-  o->out_scale[1] = p[kMlpOffOut + 1];
+  for (int q = 0; q < kMlpH * kMlpH; ++q) rowmajor_fill(p, o, q);
   for (int q = 0; q < kMlpH * 8 * kTcKG; ++q) tc_fill(p, &o->tc, q);
 }
 
 __global__ void k_pack_mlp(const float *__restrict__ p, MlpPacked *__restrict__ o) {
   const int t = threadIdx.x + blockIdx.x * blockDim.x, nt = blockDim.x * gridDim.x;
-  for (int q = t; q < kMlpH * kLdW1; q += nt) {
-    const int n = q / kLdW1, k = q % kLdW1;
-    o->W1[q] = __float2bfloat16_rn(k < kMlpIn ? p[kMlpOffW1 + n * kMlpIn + k] : 0.f);
-  }
-  for (int q = t; q < kMlpH * kLdW; q += nt) {
-    const int n = q / kLdW, k = q % kLdW;
-    o->W2[q] = __float2bfloat16_rn(k < kMlpH ? p[kMlpOffW2 + n * kMlpH + k] : 0.f);
-  }
-  for (int q = t; q < kMlpOutPad * kLdW; q += nt) {
-    const int n = q / kLdW, k = q % kLdW;
-    o->W3[q] = __float2bfloat16_rn(n < kMlpOut && k < kMlpH ? p[kMlpOffW3 + n * kMlpH + k] : 0.f);
-  }
-  for (int q = t; q < kMlpH; q += nt) {
-    o->b1[q] = p[kMlpOffB1 + q];
-    o->b2[q] = p[kMlpOffB2 + q];
-  }
-  for (int q = t; q < kMlpOutPad; q += nt) o->b3[q] = q < kMlpOut ? p[kMlpOffB3 + q] : 0.f;
-  for (int q = t; q < kMlpInPad; q += nt) o->in_scale[q] = q < kMlpIn ? p[kMlpOffIn + q] : 0.f;
-  if (t < 2) o->out_scale[t] = p[kMlpOffOut + t];
+  for (int q = t; q < kMlpH * kMlpH; q += nt) rowmajor_fill(p, o, q);
   for (int q = t; q < kMlpH * 8 * kTcKG; q += nt) tc_fill(p, &o->tc, q);
 }
 
@@ -143,19 +118,35 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const MlpPacked *__restrict
 
 // ------------------------------------------------------------------ training
 
+// One CTA of 128 threads per SM; each iteration takes 128 samples (thread t
+// owns sample t) through the forward pass and the backward products on the
+// tcgen05 tensor cores, with every accumulator in Tensor Memory:
+//   forward  a1 = W1 x + b1, a2 = W2 h1 + b2, y = W3 h2 + b3 (biases folded
+//            as in inference); a1 stays in TMEM for the backward pass;
+//   dh1      = da2 W2 (M = 128 samples, N = 64, K = 64);
+//   gW2     += da2^T h1 and gW1 += da1^T x (K = 128 samples), accumulated in
+//            TMEM over all the CTA's iterations: one A operand holds da2^T
+//            (rows 0..63) and da1^T (rows 64..127), so each product is one
+//            M = 128 chain whose other half is discarded.
+// gW3, the bias gradients and the loss are FP32 sums in shared memory.
+constexpr uint32_t kTrCols = 512;  // TMEM columns (one CTA per SM)
+constexpr int kTrA1 = 0, kTrA2 = 64, kTrY = 128, kTrDH1 = 192, kTrGW2 = 256, kTrGW1 = 320;
+
 struct TrainSmem {
-  MlpPacked W;
-  __nv_bfloat16 W2T[kMlpH * kLdW];      // W2^T: [in][out], row stride kLdW
-  __nv_bfloat16 X[128 * kMlpInPad];     // inputs, row-major
-  __nv_bfloat16 XT[kMlpInPad * 128];    // inputs, [feature][sample]
-  float A1[128 * kMlpH], A2[128 * kMlpH];  // pre-activations
-  float Y[128 * 2], DY[128 * 2];
-  __nv_bfloat16 DA2[128 * kMlpH];       // da2, row-major
-  __nv_bfloat16 DA2T[kMlpH * 128];      // da2, [unit][sample]
-  __nv_bfloat16 DA1T[kMlpH * 128];      // da1, [unit][sample]
-  __nv_bfloat16 H1T[kMlpH * 128];       // h1 = silu(a1), [unit][sample]
-  float g[kMlpNet];                     // gradient partial sums (parameter-vector layout)
+  MlpTc W;                           // forward B operands
+  __nv_bfloat16 Aop[kTcAElems];      // forward A operand, 128 x 80
+  __nv_bfloat16 W2T[kMlpH * kMlpH];  // B of dh1: [in][out], 8 groups
+  __nv_bfloat16 DA2[128 * kMlpH];    // A of dh1: [sample][out], 8 groups
+  __nv_bfloat16 AC[128 * 128];       // A of gW2 / gW1: [da2^T; da1^T], [unit][sample], 16 groups
+  __nv_bfloat16 H1T[kMlpH * 128];    // B of gW2: [in unit][sample], 16 groups
+  __nv_bfloat16 XT[16 * 128];        // B of gW1: [input][sample], 16 groups
+  float A2[128 * kMlpH];             // layer-2 pre-activations
+  float DY[128 * 2];
+  float W3f[kMlpOut * kMlpH];        // W3 (its BF16 values)
+  float g[kMlpNet];                  // gradient partial sums (parameter-vector layout)
   float loss;
+  uint64_t bar;
+  uint32_t slot;
 };
 
 __device__ __forceinline__ float dsilu(float a) {
@@ -165,42 +156,101 @@ __device__ __forceinline__ float dsilu(float a) {
 
 __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__ Wg, const float *__restrict__ X,
                                                    const float *__restrict__ T, long long n,
-                                                   float *__restrict__ grad, float *__restrict__ loss) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
+                                                   float *__restrict__ grad, float *__restrict__ loss,
+                                                   int *err_count) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
   TrainSmem &S = *reinterpret_cast<TrainSmem *>(smem_raw);
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, c = lane & 3;
-  for (int q = t; q < (int)(sizeof(MlpPacked) / 16); q += 128)
-    reinterpret_cast<uint4 *>(&S.W)[q] = reinterpret_cast<const uint4 *>(Wg)[q];
+  const int t = threadIdx.x, warp = t >> 5;
+  for (int q = t; q < (int)(sizeof(MlpTc) / 16); q += 128)
+    reinterpret_cast<uint4 *>(&S.W)[q] = reinterpret_cast<const uint4 *>(&Wg->tc)[q];
+  for (int q = t; q < kMlpH * kMlpH; q += 128) {
+    const int in = q / kMlpH, out = q % kMlpH;
+    S.W2T[tc_off(in, out, 8)] = Wg->W2[out * kMlpH + in];
+  }
+  for (int q = t; q < kMlpOut * kMlpH; q += 128)
+    S.W3f[q] = __bfloat162float(Wg->W3[q]);
   for (int q = t; q < kMlpNet; q += 128) S.g[q] = 0.f;
   if (t == 0) S.loss = 0.f;
-  __syncthreads();
-  for (int q = t; q < kMlpH * kMlpH; q += 128) {
-    const int o = q / kMlpH, i = q % kMlpH;
-    S.W2T[i * kLdW + o] = S.W.W2[o * kLdW + i];
-  }
-  __syncthreads();
+  fence_proxy_async_smem();
+  TcState st;
+  tc_setup(st, &S.slot, &S.bar, kTrCols);
+  const uint32_t lane_base = st.tmem + ((uint32_t)(t & ~31) << 16);
+  constexpr uint32_t kSboA = 8 * 16 * kTcKG, kSbo1 = 8 * 16 * kTcKG1, kSbo8 = 8 * 16 * 8, kSbo16 = 8 * 16 * 16;
   const float inv_n = 1.0f / (float)n;
+  bool first = true;
   for (long long b = (long long)blockIdx.x * 128; b < n; b += (long long)gridDim.x * 128) {
     const long long s = b + t;
     const bool valid = s < n;
-    // inputs (bf16), row-major and transposed
-    {
-      uint32_t *xr = reinterpret_cast<uint32_t *>(S.X + t * kMlpInPad);
-      float x[kMlpInPad];
+    float x[kMlpIn];
 #pragma unroll
-      for (int k = 0; k < kMlpInPad; ++k) x[k] = (valid && k < kMlpIn) ? X[s * kMlpIn + k] : 0.f;
+    for (int k = 0; k < kMlpIn; ++k) x[k] = valid ? X[s * kMlpIn + k] : 0.f;
+    mlp_tc_put_input(S.Aop, x);
 #pragma unroll
-      for (int q = 0; q < kMlpInPad / 2; ++q) xr[q] = pack_bf16(x[2 * q], x[2 * q + 1]);
-#pragma unroll
-      for (int k = 0; k < kMlpInPad; ++k) S.XT[k * 128 + t] = __float2bfloat16_rn(x[k]);
+    for (int k = 0; k < 16; ++k) S.XT[tc_off(k, t, 16)] = __float2bfloat16_rn(k < kMlpIn ? x[k] : 0.f);
+    // ---- forward, layer 1 (a1 kept in TMEM)
+    tc_group_open();
+    if (t == 0 && !st.err) {
+      tc_fence_after_sync();
+      tc_mma(st.tmem + kTrA1, tc_sdesc(S.Aop, 128, kSboA), tc_sdesc(S.W.W1, 128, kSbo1), tc_idesc_bf16(128, kMlpH),
+             0u);
     }
-    __syncwarp();
-    mlp_warp_forward(S.W, S.X, S.Y, 32 * warp, S.A1, S.A2, kMlpH);
-    __syncthreads();
-    // output error, loss, gW3 and gb3 pieces
+    tc_group_close(st);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float v[32];
+      tc_ld32(lane_base + kTrA1 + 32 * h, v);
+      uint32_t w[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        w[q] = silu2_bf16(v[2 * q], v[2 * q + 1]);
+        S.H1T[tc_off(32 * h + 2 * q, t, 16)] = __ushort_as_bfloat16((unsigned short)(w[q] & 0xFFFFu));
+        S.H1T[tc_off(32 * h + 2 * q + 1, t, 16)] = __ushort_as_bfloat16((unsigned short)(w[q] >> 16));
+      }
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        *reinterpret_cast<uint4 *>(S.Aop + tc_off(t, 32 * h + 8 * kk, kTcKG)) =
+            make_uint4(w[4 * kk], w[4 * kk + 1], w[4 * kk + 2], w[4 * kk + 3]);
+    }
+    // ---- layer 2 (a2 to shared memory)
+    tc_group_open();
+    if (t == 0 && !st.err) {
+      tc_fence_after_sync();
+#pragma unroll
+      for (int ks = 0; ks < kTcKG / 2; ++ks)
+        tc_mma(st.tmem + kTrA2, tc_sdesc(S.Aop + ks * 128, 128, kSboA), tc_sdesc(S.W.W2 + ks * 128, 128, kSboA),
+               tc_idesc_bf16(128, kMlpH), ks > 0 ? 1u : 0u);
+    }
+    tc_group_close(st);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float v[32];
+      tc_ld32(lane_base + kTrA2 + 32 * h, v);
+      uint32_t w[16];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) S.A2[t * kMlpH + 32 * h + q] = v[q];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) w[q] = silu2_bf16(v[2 * q], v[2 * q + 1]);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        *reinterpret_cast<uint4 *>(S.Aop + tc_off(t, 32 * h + 8 * kk, kTcKG)) =
+            make_uint4(w[4 * kk], w[4 * kk + 1], w[4 * kk + 2], w[4 * kk + 3]);
+    }
+    // ---- layer 3
+    tc_group_open();
+    if (t == 0 && !st.err) {
+      tc_fence_after_sync();
+#pragma unroll
+      for (int ks = 0; ks < kTcKG / 2; ++ks)
+        tc_mma(st.tmem + kTrY, tc_sdesc(S.Aop + ks * 128, 128, kSboA), tc_sdesc(S.W.W3 + ks * 128, 128, kSboA),
+               tc_idesc_bf16(128, kTcN3), ks > 0 ? 1u : 0u);
+    }
+    tc_group_close(st);
+    float y0, y1;
+    tc_ld2(lane_base + kTrY, y0, y1);
+    // output error and loss
     float dy0 = 0.f, dy1 = 0.f;
     if (valid) {
-      const float r0 = S.Y[2 * t] - T[s * 2], r1 = S.Y[2 * t + 1] - T[s * 2 + 1];
+      const float r0 = y0 - T[s * 2], r1 = y1 - T[s * 2 + 1];
       atomicAdd(&S.loss, 0.5f * (r0 * r0 + r1 * r1) * inv_n);
       dy0 = r0 * inv_n;
       dy1 = r1 * inv_n;
@@ -209,7 +259,7 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
     S.DY[2 * t + 1] = dy1;
     __syncthreads();
     {
-      // thread t: output unit o = t / 64, hidden unit i = t % 64
+      // gW3 and gb3: thread t takes output unit o = t / 64, hidden unit i = t % 64
       const int o = t >> 6, i = t & 63;
       float acc = 0.f, accb = 0.f;
       for (int r = 0; r < 128; ++r) {
@@ -220,111 +270,75 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
       S.g[kMlpOffW3 + o * kMlpH + i] += acc;
       if (i == 0) S.g[kMlpOffB3 + o] += accb;
     }
-    // da2 = (W3^T dy) * silu'(a2): thread per sample
+    // da2 = (W3^T dy) * silu'(a2) for sample t
     for (int i = 0; i < kMlpH; ++i) {
-      const float w0 = __bfloat162float(S.W.W3[0 * kLdW + i]), w1 = __bfloat162float(S.W.W3[1 * kLdW + i]);
-      const float da = (w0 * dy0 + w1 * dy1) * dsilu(S.A2[t * kMlpH + i]);
+      const float da = (S.W3f[i] * dy0 + S.W3f[kMlpH + i] * dy1) * dsilu(S.A2[t * kMlpH + i]);
       const __nv_bfloat16 db = __float2bfloat16_rn(da);
-      S.DA2[t * kMlpH + i] = db;
-      S.DA2T[i * 128 + t] = db;
+      S.DA2[tc_off(t, i, 8)] = db;
+      S.AC[tc_off(i, t, 16)] = db;
       atomicAdd(&S.g[kMlpOffB2 + i], da);
     }
-    // h1^T (bf16)
-    for (int i = 0; i < kMlpH; ++i) S.H1T[i * 128 + t] = __float2bfloat16_rn(silu(S.A1[t * kMlpH + i]));
-    __syncthreads();
-    // dh1 = da2 W2 (per warp: its 32 rows), then da1 = dh1 * silu'(a1)
-#pragma unroll 1
-    for (int mt = 0; mt < 2; ++mt) {
-      const int rb = 32 * warp + 16 * mt;
-      uint32_t a[4][4];
+    // ---- dh1 = da2 W2
+    tc_group_open();
+    if (t == 0 && !st.err) {
+      tc_fence_after_sync();
 #pragma unroll
-      for (int kt = 0; kt < 4; ++kt) {
-        a[kt][0] = ld_u32(S.DA2 + (rb + g) * kMlpH + 16 * kt + 2 * c);
-        a[kt][1] = ld_u32(S.DA2 + (rb + g + 8) * kMlpH + 16 * kt + 2 * c);
-        a[kt][2] = ld_u32(S.DA2 + (rb + g) * kMlpH + 16 * kt + 2 * c + 8);
-        a[kt][3] = ld_u32(S.DA2 + (rb + g + 8) * kMlpH + 16 * kt + 2 * c + 8);
-      }
+      for (int ks = 0; ks < 4; ++ks)
+        tc_mma(st.tmem + kTrDH1, tc_sdesc(S.DA2 + ks * 128, 128, kSbo8), tc_sdesc(S.W2T + ks * 128, 128, kSbo8),
+               tc_idesc_bf16(128, kMlpH), ks > 0 ? 1u : 0u);
+    }
+    tc_group_close(st);
+    // da1 = dh1 * silu'(a1) for sample t (zero for the padding samples)
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        float d[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int h = 0; h < 2; ++h) {
+      float dh[32], a1[32];
+      tc_ld32(lane_base + kTrDH1 + 32 * h, dh);
+      tc_ld32(lane_base + kTrA1 + 32 * h, a1);
 #pragma unroll
-        for (int kt = 0; kt < 4; ++kt)
-          mma_bf16_16816(d, a[kt], ld_u32(S.W2T + (8 * nt + g) * kLdW + 16 * kt + 2 * c),
-                         ld_u32(S.W2T + (8 * nt + g) * kLdW + 16 * kt + 2 * c + 8));
-        const int col = 8 * nt + 2 * c;
-        const int rows[2] = {rb + g, rb + g + 8};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int r = rows[h], cc = col + e;
-            const float da = d[2 * h + e] * dsilu(S.A1[r * kMlpH + cc]);
-            S.DA1T[cc * 128 + r] = __float2bfloat16_rn(b + r < n ? da : 0.f);
-            if (b + r < n) atomicAdd(&S.g[kMlpOffB1 + cc], da);
-          }
-        }
+      for (int q = 0; q < 32; ++q) {
+        const float da = valid ? dh[q] * dsilu(a1[q]) : 0.f;
+        S.AC[tc_off(kMlpH + 32 * h + q, t, 16)] = __float2bfloat16_rn(da);
+        if (valid) atomicAdd(&S.g[kMlpOffB1 + 32 * h + q], da);
       }
     }
-    __syncthreads();
-    // gW2 = da2^T h1 (warp w: output rows 16w..16w+15), K = 128 samples
-    {
-      const int ob = 16 * warp;
-      float acc[8][4];
+    // ---- gW2 += da2^T h1 and gW1 += da1^T x over the 128 samples
+    tc_group_open();
+    if (t == 0 && !st.err) {
+      tc_fence_after_sync();
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll 2
-      for (int kt = 0; kt < 8; ++kt) {
-        uint32_t a[4];
-        a[0] = ld_u32(S.DA2T + (ob + g) * 128 + 16 * kt + 2 * c);
-        a[1] = ld_u32(S.DA2T + (ob + g + 8) * 128 + 16 * kt + 2 * c);
-        a[2] = ld_u32(S.DA2T + (ob + g) * 128 + 16 * kt + 2 * c + 8);
-        a[3] = ld_u32(S.DA2T + (ob + g + 8) * 128 + 16 * kt + 2 * c + 8);
+      for (int ks = 0; ks < 8; ++ks)
+        tc_mma(st.tmem + kTrGW2, tc_sdesc(S.AC + ks * 128, 128, kSbo16), tc_sdesc(S.H1T + ks * 128, 128, kSbo16),
+               tc_idesc_bf16(128, kMlpH), (!first || ks > 0) ? 1u : 0u);
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt)
-          mma_bf16_16816(acc[nt], a, ld_u32(S.H1T + (8 * nt + g) * 128 + 16 * kt + 2 * c),
-                         ld_u32(S.H1T + (8 * nt + g) * 128 + 16 * kt + 2 * c + 8));
-      }
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        const int col = 8 * nt + 2 * c;
-        S.g[kMlpOffW2 + (ob + g) * kMlpH + col] += acc[nt][0];
-        S.g[kMlpOffW2 + (ob + g) * kMlpH + col + 1] += acc[nt][1];
-        S.g[kMlpOffW2 + (ob + g + 8) * kMlpH + col] += acc[nt][2];
-        S.g[kMlpOffW2 + (ob + g + 8) * kMlpH + col + 1] += acc[nt][3];
-      }
-      // gW1 = da1^T x, 2 n-tiles of 8 inputs (13 used)
-      float acc1[2][4];
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt) acc1[nt][0] = acc1[nt][1] = acc1[nt][2] = acc1[nt][3] = 0.f;
-#pragma unroll 2
-      for (int kt = 0; kt < 8; ++kt) {
-        uint32_t a[4];
-        a[0] = ld_u32(S.DA1T + (ob + g) * 128 + 16 * kt + 2 * c);
-        a[1] = ld_u32(S.DA1T + (ob + g + 8) * 128 + 16 * kt + 2 * c);
-        a[2] = ld_u32(S.DA1T + (ob + g) * 128 + 16 * kt + 2 * c + 8);
-        a[3] = ld_u32(S.DA1T + (ob + g + 8) * 128 + 16 * kt + 2 * c + 8);
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
-          mma_bf16_16816(acc1[nt], a, ld_u32(S.XT + (8 * nt + g) * 128 + 16 * kt + 2 * c),
-                         ld_u32(S.XT + (8 * nt + g) * 128 + 16 * kt + 2 * c + 8));
-      }
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        const int col = 8 * nt + 2 * c;
-        if (col < kMlpIn) {
-          S.g[kMlpOffW1 + (ob + g) * kMlpIn + col] += acc1[nt][0];
-          S.g[kMlpOffW1 + (ob + g + 8) * kMlpIn + col] += acc1[nt][2];
-        }
-        if (col + 1 < kMlpIn) {
-          S.g[kMlpOffW1 + (ob + g) * kMlpIn + col + 1] += acc1[nt][1];
-          S.g[kMlpOffW1 + (ob + g + 8) * kMlpIn + col + 1] += acc1[nt][3];
-        }
-      }
+      for (int ks = 0; ks < 8; ++ks)
+        tc_mma(st.tmem + kTrGW1, tc_sdesc(S.AC + ks * 128, 128, kSbo16), tc_sdesc(S.XT + ks * 128, 128, kSbo16),
+               tc_idesc_bf16(128, 16), (!first || ks > 0) ? 1u : 0u);
     }
-    __syncthreads();
+    tc_group_close(st);
+    first = false;
   }
+  // weight gradients out of TMEM: gW2 in rows 0..63 (warps 0, 1), gW1 in rows
+  // 64..127 (warps 2, 3)
+  if (!first) {
+    if (warp < 2) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float v[32];
+        tc_ld32(lane_base + kTrGW2 + 32 * h, v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) S.g[kMlpOffW2 + t * kMlpH + 32 * h + q] += v[q];
+      }
+    } else {
+      float v[32];
+      tc_ld32(lane_base + kTrGW1, v);
+#pragma unroll
+      for (int k = 0; k < kMlpIn; ++k) S.g[kMlpOffW1 + (t - kMlpH) * kMlpIn + k] += v[k];
+    }
+  }
+  __syncthreads();
   for (int q = t; q < kMlpNet; q += 128) atomicAdd(&grad[q], S.g[q]);
   if (t == 0) atomicAdd(loss, S.loss);
+  tc_teardown(st, err_count, kTrCols);
 }
 
 // Adam (Kingma & Ba 2015) on the network parameters of the FP32 vector.
@@ -390,16 +404,25 @@ cmles_status cmles_mlp_loss_grad(const float *params_dev, const float *X_dev, co
     attr = true;
   }
   MlpPacked *pk = nullptr;
-  if (cudaMallocAsync((void **)&pk, sizeof(MlpPacked), s) != cudaSuccess) return CMLES_ERR_OOM;
+  if (cudaMallocAsync((void **)&pk, sizeof(MlpPacked) + 16, s) != cudaSuccess) return CMLES_ERR_OOM;
+  int *err = reinterpret_cast<int *>(reinterpret_cast<char *>(pk) + sizeof(MlpPacked));
+  cudaMemsetAsync(err, 0, sizeof(int), s);
   k_pack_mlp<<<8, 256, 0, s>>>(params_dev, pk);
   cudaMemsetAsync(grad_dev, 0, kMlpNet * sizeof(float), s);
   cudaMemsetAsync(loss_dev, 0, sizeof(float), s);
   long long blocks = (n + 127) / 128;
   const int cap = train_grid();
   if (blocks > cap) blocks = cap;
-  k_mlp_train<<<(int)blocks, 128, smem, s>>>(pk, X_dev, T_dev, n, grad_dev, loss_dev);
+  // one CTA per SM (its shared memory exceeds half the SM's), so its 512
+  // Tensor Memory columns are always free
+  k_mlp_train<<<(int)blocks, 128, smem, s>>>(pk, X_dev, T_dev, n, grad_dev, loss_dev, err);
+  int err_h = 0;
+  const cudaError_t e1 = cudaGetLastError();
+  const cudaError_t e2 = cudaMemcpyAsync(&err_h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(pk, s);
-  return cudaGetLastError() == cudaSuccess ? CMLES_OK : CMLES_ERR_CUDA;
+  const cudaError_t e3 = cudaStreamSynchronize(s);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return CMLES_ERR_CUDA;
+  return err_h ? CMLES_ERR_TIMEOUT : CMLES_OK;
 }
 
 cmles_status cmles_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, int t, float lr,

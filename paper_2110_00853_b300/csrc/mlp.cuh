@@ -3,17 +3,10 @@
 // (The paper has no learned closure; this network extends its Sec. 4, with
 // Smagorinsky-Lilly kept as fallback.)
 //
-// Two evaluation paths share the packed weights:
-//  * inference (the gradient passes and cmles_mlp_forward) on the tcgen05
-//    tensor cores, one CTA per 128 rows with the accumulators in Tensor
-//    Memory (mlp_tc_forward, end of this file);
-//  * the training kernels, which also need the pre-activations and the
-//    backward products per warp, on warp-level mma.sync m16n8k16: one warp
-//    evaluates 32 rows (two m16 tiles); the accumulator fragment of two
-//    neighbouring n8 tiles is exactly the A fragment of the next layer's k16
-//    tile, so hidden activations never leave registers.  Weights are stored
-//    out-major with the input index contiguous (W[n][k]), the k-contiguous B
-//    layout the instruction wants.
+// Inference (inside the gradient passes, and cmles_mlp_forward) and training
+// (cmles_mlp_loss_grad) run on the tcgen05 tensor cores: one CTA per 128
+// rows, thread t owning row t, operands in shared memory and accumulators in
+// Tensor Memory (primitives in tc.cuh).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -24,21 +17,13 @@
 namespace cmles {
 
 constexpr int kMlpIn = 13, kMlpH = 64, kMlpOut = 2;
-constexpr int kMlpInPad = 16, kMlpOutPad = 8;
+constexpr int kMlpInPad = 16;
 // FP32 parameter vector: W1[64][13], b1[64], W2[64][64], b2[64], W3[2][64],
 // b3[2], in_scale[13], out_scale[2]
 constexpr int kMlpOffW1 = 0, kMlpOffB1 = 832, kMlpOffW2 = 896, kMlpOffB2 = 4992, kMlpOffW3 = 5056,
               kMlpOffB3 = 5184, kMlpOffIn = 5186, kMlpOffOut = 5199, kMlpParams = 5201, kMlpNet = 5186;
 
-// Row stride of W2 and W3 in the packed copy: 72 BF16 = 144 B, so the eight
-// rows g = 0..7 that one B-fragment load touches start in eight different
-// 4-bank groups (a 128 B stride would put all eight on the same banks).
-constexpr int kLdW = 72;
-// Row stride of W1: 24 BF16 = 48 B, so that eight consecutive rows fall in
-// eight different 16-byte bank groups for ldmatrix (32 B would pair them).
-constexpr int kLdW1 = 24;
-
-// Tensor-core (tcgen05) copy of the network used by the inference kernels:
+// Tensor-core (tcgen05) copy of the network used by the forward passes:
 // the weights as K-major B operands in the core-matrix layout of tc.cuh,
 // with the biases folded into the contraction.  Layer 1 has K = 16: the 13
 // inputs and three columns on which the A operand holds 1 and W1 holds the
@@ -57,28 +42,17 @@ struct __align__(16) MlpTc {
 
 // Packed device copy used by the kernels (16-byte aligned, size a multiple of
 // 16 so that it can be staged into shared memory with 16-byte copies): the
-// row-major copy for the warp-level (mma.sync) training kernels and the
-// tensor-core copy for inference.
+// tensor-core forward operands, and W2, W3 row-major ([out][in], BF16) from
+// which the training kernel builds its backward operands.
 struct __align__(16) MlpPacked {
-  __nv_bfloat16 W1[kMlpH * kLdW1];       // [64][24], k >= 13 zero
-  __nv_bfloat16 W2[kMlpH * kLdW];        // [64][72], k >= 64 zero
-  __nv_bfloat16 W3[kMlpOutPad * kLdW];   // [8][72], n >= 2 or k >= 64 zero
-  float b1[kMlpH], b2[kMlpH], b3[kMlpOutPad];
-  float in_scale[kMlpInPad], out_scale[2];
+  __nv_bfloat16 W2[kMlpH * kMlpH];
+  __nv_bfloat16 W3[kMlpOut * kMlpH];
   MlpTc tc;
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t *>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // SiLU with the fast exponential and division (relative error ~1e-6, far
@@ -111,103 +85,6 @@ __device__ __forceinline__ uint32_t silu2_bf16(float x0, float x1) {
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(hv) : "l"(xv), "l"(rv));
   asm("mov.b64 {%0, %1}, %2;" : "=f"(h0), "=f"(h1) : "l"(hv));
   return pack_bf16(h0, h1);
-}
-
-__device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
-
-// ldmatrix: four (x4) or two (x2) 8x8 BF16 tiles from shared memory; lane l
-// gives the address of row l % 8 of tile l / 8 (16-byte aligned), and
-// register m of lane (g, c) receives elements 2c, 2c + 1 of row g of tile m,
-// which for a weight tile stored [n][k] is the B fragment of mma m16n8k16.
-__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const __nv_bfloat16 *p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-__device__ __forceinline__ void ldsm_x2(uint32_t r[2], const __nv_bfloat16 *p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
-}
-
-// Forward pass of the 32 rows [r0, r0 + 32) of X (bf16 [rows][16], shared
-// memory) by one warp; writes Y[row][0..1] (FP32, shared memory).
-// Optionally stores the pre-activations of both hidden layers (FP32,
-// [rows][64] each) for the backward pass.
-__device__ __forceinline__ void mlp_warp_forward(const MlpPacked &W, const __nv_bfloat16 *X, float *Y, int r0,
-                                                 float *A1 = nullptr, float *A2 = nullptr, int lda = 0) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-#pragma unroll 1
-  for (int mt = 0; mt < 2; ++mt) {
-    const int rb = r0 + 16 * mt;
-    uint32_t a[4];
-    a[0] = ld_u32(X + (rb + g) * kMlpInPad + 2 * c);
-    a[1] = ld_u32(X + (rb + g + 8) * kMlpInPad + 2 * c);
-    a[2] = ld_u32(X + (rb + g) * kMlpInPad + 2 * c + 8);
-    a[3] = ld_u32(X + (rb + g + 8) * kMlpInPad + 2 * c + 8);
-    // layer 1: 8 n-tiles, one k-tile; outputs repacked as 4 k-tiles of layer 2
-    uint32_t h1[4][4];
-    // ldmatrix row address of this lane: tile lane / 8, row lane % 8
-    const int lr = lane & 7, lt = lane >> 3;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      float d[4];
-      d[0] = d[2] = W.b1[8 * nt + 2 * c];
-      d[1] = d[3] = W.b1[8 * nt + 2 * c + 1];
-      uint32_t b[2];
-      ldsm_x2(b, W.W1 + (8 * nt + lr) * kLdW1 + 8 * (lt & 1));
-      mma_bf16_16816(d, a, b[0], b[1]);
-      if (A1) {
-        A1[(rb + g) * lda + 8 * nt + 2 * c] = d[0];
-        A1[(rb + g) * lda + 8 * nt + 2 * c + 1] = d[1];
-        A1[(rb + g + 8) * lda + 8 * nt + 2 * c] = d[2];
-        A1[(rb + g + 8) * lda + 8 * nt + 2 * c + 1] = d[3];
-      }
-      const int kt = nt >> 1, hi = nt & 1;
-      h1[kt][0 + 2 * hi] = silu2_bf16(d[0], d[1]);
-      h1[kt][1 + 2 * hi] = silu2_bf16(d[2], d[3]);
-    }
-    // layer 2 and 3
-    float y[4] = {0.f, 0.f, 0.f, 0.f};
-    y[0] = y[2] = W.b3[2 * c];
-    y[1] = y[3] = W.b3[2 * c + 1];
-    uint32_t h2[4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      float d[4];
-      d[0] = d[2] = W.b2[8 * nt + 2 * c];
-      d[1] = d[3] = W.b2[8 * nt + 2 * c + 1];
-#pragma unroll
-      for (int kp = 0; kp < 2; ++kp) {
-        // tiles: (k-tile 2kp, low 8), (2kp, high 8), (2kp+1, low), (2kp+1, high)
-        uint32_t b[4];
-        ldsm_x4(b, W.W2 + (8 * nt + lr) * kLdW + 32 * kp + 8 * lt);
-        mma_bf16_16816(d, h1[2 * kp], b[0], b[1]);
-        mma_bf16_16816(d, h1[2 * kp + 1], b[2], b[3]);
-      }
-      if (A2) {
-        A2[(rb + g) * lda + 8 * nt + 2 * c] = d[0];
-        A2[(rb + g) * lda + 8 * nt + 2 * c + 1] = d[1];
-        A2[(rb + g + 8) * lda + 8 * nt + 2 * c] = d[2];
-        A2[(rb + g + 8) * lda + 8 * nt + 2 * c + 1] = d[3];
-      }
-      const int hi = nt & 1;
-      h2[0 + 2 * hi] = silu2_bf16(d[0], d[1]);
-      h2[1 + 2 * hi] = silu2_bf16(d[2], d[3]);
-      if (hi) {  // a full k-tile of layer 3 is ready
-        const int kt = nt >> 1;
-        uint32_t b[2];
-        ldsm_x2(b, W.W3 + lr * kLdW + 16 * kt + 8 * (lt & 1));
-        mma_bf16_16816(y, h2, b[0], b[1]);
-      }
-    }
-    if (c == 0) {
-      Y[(rb + g) * 2 + 0] = y[0];
-      Y[(rb + g) * 2 + 1] = y[1];
-      Y[(rb + g + 8) * 2 + 0] = y[2];
-      Y[(rb + g + 8) * 2 + 1] = y[3];
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -252,8 +129,8 @@ __device__ __forceinline__ void mlp_tc_put_input(__nv_bfloat16 *A, const float x
 // Set-up of a CTA's tensor-core state: TMEM columns (allocated by warp 0)
 // and the MMA completion barrier (initialised by thread 0).  All threads must
 // call it; it ends with a block barrier.
-__device__ __forceinline__ void tc_setup(TcState &s, uint32_t *slot, uint64_t *mbar) {
-  if (threadIdx.x < 32) tc_alloc(slot, kTcCols);
+__device__ __forceinline__ void tc_setup(TcState &s, uint32_t *slot, uint64_t *mbar, uint32_t ncols = kTcCols) {
+  if (threadIdx.x < 32) tc_alloc(slot, ncols);
   if (threadIdx.x == 0) {
     mbar_init(mbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -270,7 +147,7 @@ __device__ __forceinline__ void tc_setup(TcState &s, uint32_t *slot, uint64_t *m
 // Tear-down: wait (bounded) until every MMA the CTA issued has completed,
 // free the TMEM columns, and count the CTA in *err_count if any wait gave up.
 // All threads must call it.
-__device__ __forceinline__ void tc_teardown(TcState &s, int *err_count) {
+__device__ __forceinline__ void tc_teardown(TcState &s, int *err_count, uint32_t ncols = kTcCols) {
   tc_fence_before_sync();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -282,9 +159,26 @@ __device__ __forceinline__ void tc_teardown(TcState &s, int *err_count) {
   __syncthreads();
   if (threadIdx.x < 32) {
     tc_fence_after_sync();
-    tc_dealloc(s.tmem, kTcCols);
+    tc_dealloc(s.tmem, ncols);
   }
   if (s.err) atomicAdd(err_count, 1);
+}
+
+// One MMA group of the CTA: every thread makes its shared-memory operand
+// writes visible to the tensor core and meets the others (tc_group_open);
+// thread 0 then issues the group's MMAs; tc_group_close commits them to the
+// barrier and waits (bounded) for their completion in every thread.
+__device__ __forceinline__ void tc_group_open() {
+  fence_proxy_async_smem();
+  tc_fence_before_sync();
+  __syncthreads();
+}
+__device__ __forceinline__ void tc_group_close(TcState &s) {
+  if (threadIdx.x == 0) tc_commit(s.mbar);
+  if (!mbar_wait_bounded(s.mbar, s.parity, s.err ? 1 : kTcWaitLimit)) s.err = 1;
+  s.parity ^= 1u;
+  __syncwarp();
+  tc_fence_after_sync();
 }
 
 // Forward pass of the CTA's 128 rows; (y0, y1) of this thread's row.  All
