@@ -239,7 +239,9 @@ cmles_status cmles_set_closure_weights_device(cmles_handle h, const float *param
  *   may then be null).
  * cmles_mlp_loss_grad: loss = 1/(2n) sum |y - t|^2 over T[n][2] and its
  *   gradient with respect to the first 5186 parameters (W1 .. b3), written
- *   to grad_dev[5186] and loss_dev[1] (both overwritten).
+ *   to grad_dev[5186] and loss_dev[1] (both overwritten); forward and
+ *   backward products on the tcgen05 tensor cores; synchronises the stream
+ *   and returns CMLES_ERR_TIMEOUT if an MMA completion wait gave up.
  * cmles_mlp_adam: one Adam step (Kingma & Ba 2015) of those 5186 parameters
  *   with moment buffers m_dev, v_dev (5186 each, zero at t = 1); t >= 1.
  * All run on `stream`; errors CMLES_ERR_ARG (null/size), CMLES_ERR_CUDA. */
