@@ -150,6 +150,10 @@ void orc_intermediates(const orc_solver *s, double *G, double *gradG, double *nu
 int orc_lsrk54(orc_solver *s, double *Q, int nsteps, double dt);
 void orc_lsrk54_coefficients(double A[5], double B[5], double c[5]);
 int orc_lsrk144(orc_solver *s, double *Q, int nsteps, double dt);
+/* HEVI (Sec. 3.2): the vertical acoustic-gravity operator linearised about
+ * the reference (hevi.c); flat meshes. */
+void orc_vlin_reference(orc_solver *s, double *Qref);
+void orc_vlin_apply(orc_solver *s, const double *Q, double *out);
 void orc_lsrk144_coefficients(double A[14], double B[14], double c[14]);
 
 /* Global budgets sum_e sum_i w_i J_i Q_v for all 6 variables; returns 1 if any

@@ -108,6 +108,8 @@ def _declare(L):
     L.orc_lsrk144.argtypes = [C.c_void_p, _DP, C.c_int, C.c_double]
     L.orc_lsrk144.restype = C.c_int
     L.orc_lsrk144_coefficients.argtypes = [_DP, _DP, _DP]
+    L.orc_vlin_reference.argtypes = [C.c_void_p, _DP]
+    L.orc_vlin_apply.argtypes = [C.c_void_p, _DP, _DP]
     L.orc_budgets.argtypes = [C.c_void_p, _DP, _DP]
     L.orc_budgets.restype = C.c_int
     L.orc_favre_profiles.argtypes = [C.c_void_p, _DP, _DP]
@@ -253,6 +255,21 @@ def lsrk54_coefficients():
     return A, B, c
 
 
+def ark2_tableaux():
+    """ARK2 of Giraldo, Kelly & Constantinescu (2013), the 2nd-order additive
+    Runge-Kutta IMEX method Sec. 3.2 cites: explicit tableau Ae, implicit
+    (singly diagonally implicit, stiffly accurate) tableau Ai, shared
+    weights b; gamma = 1 - 1/sqrt 2, delta = 1/(2 sqrt 2),
+    alpha = (3 + 2 sqrt 2)/6."""
+    g = 1.0 - 1.0 / np.sqrt(2.0)
+    d = 1.0 / (2.0 * np.sqrt(2.0))
+    a = (3.0 + 2.0 * np.sqrt(2.0)) / 6.0
+    Ae = np.array([[0.0, 0.0, 0.0], [2.0 * g, 0.0, 0.0], [1.0 - a, a, 0.0]])
+    Ai = np.array([[0.0, 0.0, 0.0], [g, g, 0.0], [d, d, g]])
+    b = np.array([d, d, g])
+    return Ae, Ai, b
+
+
 def lsrk144_coefficients():
     A, B, c = np.zeros(14), np.zeros(14), np.zeros(14)
     lib().orc_lsrk144_coefficients(_p(A), _p(B), _p(c))
@@ -365,6 +382,92 @@ class Solver:
     def lsrk54(self, Q, nsteps, dt):
         Q = np.ascontiguousarray(Q, float).copy()
         fails = lib().orc_lsrk54(self.h, _p(Q), nsteps, dt)
+        return Q, fails
+
+    # ------------------------------------------------------------ HEVI (Sec. 3.2)
+
+    def vlin_reference(self):
+        """The state the vertical linear operator is linearised about."""
+        Qr = np.zeros((self.E, 6, self.Np))
+        lib().orc_vlin_reference(self.h, _p(Qr))
+        return Qr
+
+    def vlin(self, Q):
+        """L (Q - Q_ref): the vertical acoustic-gravity operator (hevi.c)."""
+        out = np.zeros((self.E, 6, self.Np))
+        lib().orc_vlin_apply(self.h, _p(np.ascontiguousarray(Q, float)), _p(out))
+        return out
+
+    _HEVI_COMP = (0, 1, 2, 3, 4, 5)
+
+    def _line_nodes(self, ex, ey, i, j):
+        """(element, node) of the vertical line (ex, ey, i, j), bottom to top."""
+        m, Nq = self.mesh, self.N + 1
+        return [(ex + m.nex * (ey + m.ney * ez), i + Nq * (j + Nq * k)) for ez in range(m.nez) for k in range(Nq)]
+
+    def hevi_line_matrix(self, ex=0, ey=0, i=0, j=0):
+        """L on one vertical line, assembled column by column by applying the
+        operator to unit deviations; unknowns ordered (level node, component)."""
+        Qr = self.vlin_reference()
+        nodes = self._line_nodes(ex, ey, i, j)
+        nc = len(self._HEVI_COMP)
+        nl = nc * len(nodes)
+        Lm = np.zeros((nl, nl))
+        for col in range(nl):
+            e, n = nodes[col // nc]
+            Q = Qr.copy()
+            Q[e, self._HEVI_COMP[col % nc], n] += 1.0
+            out = self.vlin(Q)
+            for row, (er, nr) in enumerate(nodes):
+                for c in range(nc):
+                    Lm[nc * row + c, col] = out[er, self._HEVI_COMP[c], nr]
+        return Lm
+
+    def _hevi_solve(self, M, B, Qr):
+        """Y with (I - dt gamma L)(Y - Q_ref) = B - Q_ref on every vertical
+        line, all six components."""
+        m, Nq = self.mesh, self.N + 1
+        Y = B.copy()
+        lines = [(ex, ey, i, j) for ex in range(m.nex) for ey in range(m.ney) for i in range(Nq) for j in range(Nq)]
+        idx = [self._line_nodes(*ln) for ln in lines]
+        nc = len(self._HEVI_COMP)
+        R = np.zeros((M.shape[0], len(lines)))
+        for L_, nodes in enumerate(idx):
+            for r, (e, n) in enumerate(nodes):
+                for c, v in enumerate(self._HEVI_COMP):
+                    R[nc * r + c, L_] = B[e, v, n] - Qr[e, v, n]
+        X = np.linalg.solve(M, R)
+        for L_, nodes in enumerate(idx):
+            for r, (e, n) in enumerate(nodes):
+                for c, v in enumerate(self._HEVI_COMP):
+                    Y[e, v, n] = Qr[e, v, n] + X[nc * r + c, L_]
+        return Y
+
+    def ark2_hevi(self, Q, nsteps, dt):
+        """nsteps steps of ARK2 with the vertical linear operator implicit and
+        the rest of the right-hand side explicit: stage s solves
+        Y_s - dt Ai[s,s] L(Y_s) = Q + dt sum_{j<s} (Ae[s,j] E_j + Ai[s,j] I_j),
+        E_j = f(Y_j) - L(Y_j), I_j = L(Y_j); Q <- Q + dt sum_j b_j f(Y_j)."""
+        Ae, Ai, b = ark2_tableaux()
+        Qr = self.vlin_reference()
+        M = np.eye(len(self._HEVI_COMP) * self.mesh.nez * (self.N + 1)) - dt * Ai[1, 1] * self.hevi_line_matrix()
+        Q = np.ascontiguousarray(Q, float).copy()
+        fails = 0
+        for _ in range(nsteps):
+            E, Im, R = [], [], []
+            for s_ in range(3):
+                if s_ == 0:
+                    Y = Q
+                else:
+                    B = Q + dt * sum(Ae[s_, j] * E[j] + Ai[s_, j] * Im[j] for j in range(s_))
+                    Y = self._hevi_solve(M, B, Qr)
+                f, fl = self.rhs(Y)
+                fails += fl
+                Lq = self.vlin(Y)
+                R.append(f)
+                E.append(f - Lq)
+                Im.append(Lq)
+            Q = Q + dt * sum(b[j] * R[j] for j in range(3))
         return Q, fails
 
     def lsrk144(self, Q, nsteps, dt):
