@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 from paper_2110_00853_b300 import inputs as I  # noqa: E402
 
 WORKLOAD = "c5"
-STAGES = {"lsrk54": 5, "lsrk144": 14}
+STAGES = {"lsrk54": 5, "lsrk144": 14, "ark2_hevi": 3}
 METRIC = "DG node-stage updates/s at 1 B300 and HBM roofline %, FP32+learned vs FP64 plain"
 # algorithmic bytes per node for each kernel launch (compulsory traffic),
 # averaged over the S stages of a step (S = 5 for LSRK(5,4)):
@@ -41,9 +41,13 @@ METRIC = "DG node-stage updates/s at 1 B300 and HBM roofline %, FP32+learned vs 
 #     D, S (+30); the last stage reads dQ, D, reads and writes Q64 and writes S
 #     (+12 + 24 FP32 words for Q64): (41 + (S - 2) * 53 + 65) words / S, 53
 #     words for S = 5
-def alg_bytes(prec, kind, stages=5):
+#   flux pass of the HEVI stages (FP64): the tendency alone, read Q, F2, aux
+#     and write R: 29 words
+def alg_bytes(prec, kind, stages=5, integrator="lsrk54"):
     if kind == "grad":
         return (6 + 15 + 2) * (8 if prec == "fp64" else 4)
+    if integrator == "ark2_hevi":
+        return 29 * 8
     if prec == "fp64":
         return ((stages - 1) * 41 + 35) * 8 / stages
     return (41 + (stages - 2) * 53 + 65) * 4 / stages
@@ -58,7 +62,8 @@ VARIANTS = {"fp32acc64_mlp": ("fp32", "mlp", "rusanov", "lsrk54"), "fp32acc64_sl
             "fp32acc64_mlp_hllc": ("fp32", "mlp", "hllc", "lsrk54"),
             "fp32acc64_mlp_roe": ("fp32", "mlp", "roe", "lsrk54"),
             "fp32acc64_mlp_lsrk144": ("fp32", "mlp", "rusanov", "lsrk144"),
-            "fp64_sl_lsrk144": ("fp64", "sl", "rusanov", "lsrk144")}
+            "fp64_sl_lsrk144": ("fp64", "sl", "rusanov", "lsrk144"),
+            "fp64_sl_hevi": ("fp64", "sl", "rusanov", "ark2_hevi")}
 DTYPE = {"fp32": "f32", "fp64": "f64"}
 # DRAM bytes per node of one launch (dram__bytes_read.sum + dram__bytes_write.sum
 # from one ncu capture on a 40 x 40 x 20-element sub-box of the box, 4M nodes,
@@ -341,7 +346,7 @@ def main():
     kinds = ["grad", "rhs"]
     dom = max(range(2), key=lambda k: kt["ms"][k])
     avg_ms = kt["ms"][dom] / max(kt["count"][dom], 1)
-    achieved = head["nodes"] * alg_bytes(prec, kinds[dom], hstages) / (avg_ms / 1e3) / 1e9
+    achieved = head["nodes"] * alg_bytes(prec, kinds[dom], hstages, variants[0][4]) / (avg_ms / 1e3) / 1e9
     tb = TRAFFIC_B_PER_NODE.get((variants[0][0], kinds[dom]))
     traffic = tb * head["nodes"] if tb is not None else None
     out_variants = {}
@@ -350,7 +355,7 @@ def main():
         per = {}
         for k in range(2):
             a = r["kt"]["ms"][k] / max(r["kt"]["count"][k], 1)
-            gbs = r["nodes"] * alg_bytes(vprec, kinds[k], STAGES[vint]) / (a / 1e3) / 1e9
+            gbs = r["nodes"] * alg_bytes(vprec, kinds[k], STAGES[vint], vint) / (a / 1e3) / 1e9
             per[kinds[k]] = dict(avg_ms=a, launches=r["kt"]["count"][k], gbs=gbs, hbm_frac=gbs / hbm)
         out_variants[name] = dict(value=v, ms_per_step=r["ms"] / args.steps, kernels=per, finite=r["finite"],
                                   satadj_failures=r["satadj_failures"])
@@ -366,7 +371,8 @@ def main():
                     warmup=args.warmup, ms_per_step=head["ms"] / args.steps, higher_is_better=True,
                     scaling="weak", vs_baseline=None, dtype=DTYPE[prec], data="synthetic",
                     config={"workload": f"{WORKLOAD}: 160x160x80 hexahedral elements, N=4 (256M nodes), moist, "
-                                        + {"lsrk54": "LSRK(5,4)", "lsrk144": "LSRK(14,4)"}[variants[0][4]],
+                                        + {"lsrk54": "LSRK(5,4)", "lsrk144": "LSRK(14,4)",
+                                           "ark2_hevi": "ARK2 HEVI"}[variants[0][4]],
                             "variant": variants[0][0],
                             "closure": {"mlp": "learned (BF16 tensor-core MLP 13-64-64-2, seeded weights)",
                                         "sl": "Smagorinsky-Lilly + Richardson",

@@ -55,10 +55,18 @@ enum { CMLES_CLOSURE_NONE = 0, CMLES_CLOSURE_SL = 1, CMLES_CLOSURE_MLP = 2, CMLE
  * Roe (Roe 1981; Jacobian at Roe's averaged state with the frozen moist
  * equation of state, no entropy fix). */
 enum { CMLES_FLUX_RUSANOV = 0, CMLES_FLUX_HLLC = 1, CMLES_FLUX_ROE = 2 };
-/* Time integrators of cmles_step (Sec. 3.2), both 2N-storage and fourth
- * order: five stages (Carpenter & Kennedy 1994) or fourteen stages with a
- * larger stability region (Niegemann, Diehl & Busch 2012). */
-enum { CMLES_LSRK54 = 0, CMLES_LSRK144 = 1 };
+/* Time integrators of cmles_step (Sec. 3.2): the 2N-storage fourth-order
+ * explicit schemes with five stages (Carpenter & Kennedy 1994) or fourteen
+ * stages and a larger stability region (Niegemann, Diehl & Busch 2012); or
+ * HEVI, horizontally explicit and vertically implicit: the three-stage
+ * second-order IMEX additive Runge-Kutta method ARK2 of Giraldo, Kelly &
+ * Constantinescu (2013) with the vertical acoustic-gravity operator,
+ * linearised about the hydrostatic reference and the rest state (linear
+ * equation of state of dry air at rest, Rusanov flux at the reference sound
+ * speed), implicit, and everything else explicit; each implicit stage is one
+ * block-tridiagonal solve per vertical line of nodes.  HEVI requires
+ * CMLES_FP64, a flat mesh and walls at the bottom and top. */
+enum { CMLES_LSRK54 = 0, CMLES_LSRK144 = 1, CMLES_ARK2_HEVI = 2 };
 
 /* Arithmetic of the RHS kernels.
  *   CMLES_FP64       all FP64 ("plain" method).
@@ -117,7 +125,7 @@ typedef struct {
   int filter_order;
   double filter_alpha;
   int filter_vars;
-  int integrator;        /* CMLES_LSRK54 (default) or CMLES_LSRK144 */
+  int integrator;        /* CMLES_LSRK54 (default), CMLES_LSRK144 or CMLES_ARK2_HEVI */
 } cmles_params;
 
 typedef struct {
@@ -198,8 +206,8 @@ cmles_status cmles_get_state_host(cmles_handle h, double *Q_host);
 cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev);
 
 /* Advance the handle's state by nsteps steps of params.dt of the chosen
- * integrator (params.integrator: LSRK(5,4) or LSRK(14,4)).  Each
- * stage is two kernels: the gradient/closure pass and the flux-divergence pass
+ * integrator (params.integrator: LSRK(5,4), LSRK(14,4) or ARK2 HEVI).  Each
+ * explicit stage is two kernels: the gradient/closure pass and the flux-divergence pass
  * with the fused stage update; with filter_order > 0 the exponential filter
  * follows every step.  Every step starts from the FP64 state alone (the first
  * stage has A = 0), so a state saved between calls resumes bit-identically.

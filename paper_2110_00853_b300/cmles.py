@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "cmles.h")
 CMLES_FP64, CMLES_FP32_ACC64 = 0, 1
 CLOSURE = {"none": 0, "sl": 1, "mlp": 2, "vreman": 3}
 FLUX = {"rusanov": 0, "hllc": 1, "roe": 2}
-INTEGRATOR = {"lsrk54": 0, "lsrk144": 1}
+INTEGRATOR = {"lsrk54": 0, "lsrk144": 1, "ark2_hevi": 2}
 PRECISION = {"fp64": CMLES_FP64, "fp32": CMLES_FP32_ACC64, "fp32acc64": CMLES_FP32_ACC64}
 STATUS = {0: "CMLES_OK", 1: "CMLES_ERR_ARG", 2: "CMLES_ERR_OOM", 3: "CMLES_ERR_CUDA", 4: "CMLES_ERR_SATADJ",
           5: "CMLES_ERR_NONFINITE", 6: "CMLES_ERR_MESH", 7: "CMLES_ERR_STATE", 8: "CMLES_ERR_TIMEOUT"}

@@ -138,6 +138,13 @@ struct cmles_t {
   bool have_ref = false;
   long long launches = 0, steps = 0;
   int tc_stall = 0;
+  // HEVI: level reference (host copy), stage buffers R0 R1 R2 L0 L1 B Y and
+  // the tables of the vertical operator for the step hv_dt
+  std::vector<double> ref_rho_h, ref_p_h;
+  double *hv_buf[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *hv_tab = nullptr;
+  double hv_dt = -1.0;
+  HeviTables hv_T{};
   double time = 0.0;
   bool timing = false;
   std::vector<TimedLaunch> timed;
@@ -724,7 +731,13 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
     return CMLES_ERR_ARG;
   if (params->filter_order < 0 || !(params->filter_alpha >= 0.0) || (params->filter_vars & ~0xE) != 0)
     return CMLES_ERR_ARG;
-  if (params->integrator != CMLES_LSRK54 && params->integrator != CMLES_LSRK144) return CMLES_ERR_ARG;
+  if (params->integrator != CMLES_LSRK54 && params->integrator != CMLES_LSRK144 &&
+      params->integrator != CMLES_ARK2_HEVI)
+    return CMLES_ERR_ARG;
+  // HEVI: the FP64 path on flat meshes with walls at the bottom and top
+  if (params->integrator == CMLES_ARK2_HEVI &&
+      (params->precision != CMLES_FP64 || mesh->warp || mesh->periodic[2] || mesh->nez < 2))
+    return CMLES_ERR_ARG;
   // Vreman's directional lengths are those of the flat elements
   if (params->closure == CMLES_CLOSURE_VREMAN && mesh->warp) return CMLES_ERR_ARG;
   // the learned closure runs on BF16 tensor cores inside the FP32 kernels
@@ -865,6 +878,9 @@ cmles_status cmles_destroy(cmles_handle h) {
                   h->dH32,   h->qref64,  h->mlp_dev, h->geo32,   h->node32,  h->wJn,      h->rvs_tab,  h->exr};
   for (void *b : bufs)
     if (b) cudaFree(b);
+  for (double *b : h->hv_buf)
+    if (b) cudaFree(b);
+  if (h->hv_tab) cudaFree(h->hv_tab);
   delete h;
   return CMLES_OK;
 }
@@ -902,6 +918,9 @@ cmles_status cmles_set_reference(cmles_handle h, const double *rho_r, const doub
   }
   CK(cudaMemcpyAsync(h->rho_r, rho_r, nlev * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->p_r, p_r, nlev * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  h->ref_rho_h.assign(rho_r, rho_r + nlev);
+  h->ref_p_h.assign(p_r, p_r + nlev);
+  h->hv_dt = -1.0;  // the HEVI tables depend on the reference
   {
     std::vector<double> ex(nlev);
     for (size_t l = 0; l < nlev; ++l) ex[l] = exp(-h->K.kappa * log(p_r[l] / h->prm.p0));
@@ -1177,6 +1196,90 @@ cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev
   return run_stage_pair(h, Q_dev, nullptr, RHS_dev, sc, false);
 }
 
+// HEVI stage buffers and, for the current step, the vertical operator's
+// tables (rebuilt when dt or the reference changes).
+cmles_status ensure_hevi(cmles_handle h) {
+  const size_t n6 = (size_t)h->nodes * 6;
+  for (double *&b : h->hv_buf)
+    if (!b) {
+      cmles_status st = dalloc(h, (void **)&b, n6 * sizeof(double));
+      if (st != CMLES_OK) return st;
+    }
+  if (h->hv_dt == h->prm.dt) return CMLES_OK;
+  const int nez = h->mesh.nez, Nq = h->Nq, nlev = nez * Nq;
+  HeviSetup S{};
+  S.nez = nez;
+  S.hz = h->K.hz;
+  for (int a = 0; a < Nq; ++a) S.w[a] = h->w[a];
+  for (int a = 0; a < Nq * Nq; ++a) S.D[a] = h->D[a];
+  std::vector<double> z(nlev);
+  for (int l = 0; l < nlev; ++l) z[l] = level_z(h, l);
+  S.rho_r = h->ref_rho_h.data();
+  S.p_r = h->ref_p_h.data();
+  S.z = z.data();
+  S.g = h->prm.g;
+  S.Rd = h->prm.Rd;
+  S.cvd = h->prm.cvd;
+  S.T0 = h->prm.T0;
+  S.dtg = h->prm.dt * (1.0 - 1.0 / sqrt(2.0));
+  HeviHost H;
+  if (!hevi_build(S, H)) return fail(h, CMLES_ERR_ARG, "HEVI: I - dt gamma L is singular");
+  const size_t nb = (size_t)nez * 15 * 15;
+  if (!h->hv_tab) {
+    cmles_status st = dalloc(h, (void **)&h->hv_tab, (5 * nb + (size_t)nlev * 4) * sizeof(double));
+    if (st != CMLES_OK) return st;
+  }
+  CK(cudaMemcpy(h->hv_tab, H.Lb.data(), 3 * nb * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->hv_tab + 3 * nb, H.Gf.data(), nb * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->hv_tab + 4 * nb, H.Ef.data(), nb * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->hv_tab + 5 * nb, H.lev.data(), (size_t)nlev * 4 * sizeof(double), cudaMemcpyHostToDevice));
+  h->hv_T = HeviTables{h->hv_tab, h->hv_tab + 3 * nb, h->hv_tab + 4 * nb, h->hv_tab + 5 * nb, H.lift, S.dtg};
+  h->hv_dt = h->prm.dt;
+  return CMLES_OK;
+}
+
+// One ARK2 step (Giraldo, Kelly & Constantinescu 2013) with the vertical
+// linear operator L implicit: stage s solves
+//   Y_s - dt gamma L(Y_s) = Q + dt sum_{j<s} (Ae_sj f_j + (Ai_sj - Ae_sj) L_j),
+// f_j = f(Y_j), L_j = L(Y_j); then Q <- Q + dt sum_j b_j f_j.
+cmles_status run_ark2_hevi(cmles_handle h) {
+  const double g = 1.0 - 1.0 / sqrt(2.0), d = 1.0 / (2.0 * sqrt(2.0)), al = (3.0 + 2.0 * sqrt(2.0)) / 6.0;
+  double *R0 = h->hv_buf[0], *R1 = h->hv_buf[1], *R2 = h->hv_buf[2], *L0 = h->hv_buf[3], *L1 = h->hv_buf[4];
+  double *B = h->hv_buf[5], *Y = h->hv_buf[6];
+  const double *Qn = h->Q[h->cur];
+  double *Qo = h->Q[1 - h->cur];
+  const double dt = h->prm.dt;
+  const long long count = (long long)h->nodes * 6;
+  const StageCoef sc = {0.0, 0.0, 0.0, 0, 0.f, 0.f, 0.f, 1};
+  cmles_status st;
+  // stage 1: Y_1 = Q
+  if ((st = run_stage_pair(h, Qn, nullptr, R0, sc, false)) != CMLES_OK) return st;
+  {
+    LaunchScope ls(h, 2, 3);
+    CK(launch_hevi_apply(Qn, L0, h->hv_T, h->K, h->stream));
+    // stage 2: Ae_21 = 2 gamma, Ai_21 = gamma
+    CK(launch_lincomb(B, Qn, LinComb{2, dt, {2.0 * g, g - 2.0 * g, 0.0, 0.0}, {R0, L0, nullptr, nullptr}}, count,
+                      h->stream));
+    CK(launch_hevi_solve(B, Y, h->hv_T, h->K, h->stream));
+  }
+  if ((st = run_stage_pair(h, Y, nullptr, R1, sc, false)) != CMLES_OK) return st;
+  {
+    LaunchScope ls(h, 2, 3);
+    CK(launch_hevi_apply(Y, L1, h->hv_T, h->K, h->stream));
+    // stage 3: Ae_3 = (1 - alpha, alpha), Ai_3 = (delta, delta)
+    CK(launch_lincomb(B, Qn, LinComb{4, dt, {1.0 - al, al, d - (1.0 - al), d - al}, {R0, R1, L0, L1}}, count,
+                      h->stream));
+    CK(launch_hevi_solve(B, Y, h->hv_T, h->K, h->stream));
+  }
+  if ((st = run_stage_pair(h, Y, nullptr, R2, sc, false)) != CMLES_OK) return st;
+  {
+    LaunchScope ls(h, 2, 1);
+    CK(launch_lincomb(Qo, Qn, LinComb{3, dt, {d, d, g, 0.0}, {R0, R1, R2, nullptr}}, count, h->stream));
+  }
+  h->cur = 1 - h->cur;
+  return CMLES_OK;
+}
+
 cmles_status cmles_step(cmles_handle h, int nsteps) {
   if (!h || nsteps < 0) return fail(h, CMLES_ERR_ARG, "cmles_step: bad argument");
   if (!h->have_ref) return fail(h, CMLES_ERR_STATE, "cmles_step: reference state not set");
@@ -1185,6 +1288,17 @@ cmles_status cmles_step(cmles_handle h, int nsteps) {
   if (h->fp32) {
     cmles_status st = ensure_shadow(h);
     if (st != CMLES_OK) return st;
+  }
+  if (h->prm.integrator == CMLES_ARK2_HEVI) {
+    cmles_status st = ensure_hevi(h);
+    if (st != CMLES_OK) return st;
+    for (int s = 0; s < nsteps; ++s) {
+      if ((st = run_ark2_hevi(h)) != CMLES_OK) return st;
+      if (h->prm.filter_order > 0 && (st = apply_expfilter(h)) != CMLES_OK) return st;
+      h->steps += 1;
+      h->time += h->prm.dt;
+    }
+    return CMLES_OK;
   }
   const bool l14 = h->prm.integrator == CMLES_LSRK144;
   const int nst = l14 ? 14 : 5;

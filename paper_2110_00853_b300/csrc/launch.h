@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace cmles {
@@ -36,6 +38,36 @@ struct ExpFilter {
   int mask;
 };
 cudaError_t launch_expfilter(double *Q, float *S32, const ExpFilter &F, int N, int E, cudaStream_t s);
+
+// HEVI (hevi.cu): the vertical linear operator's element blocks and the
+// factors of I - dt gamma L, built on the host, used by the line kernels.
+struct HeviTables {
+  const double *Lb;   // [nez][sub, diag, super][15 x 15] blocks of L
+  const double *Gf;   // [nez][15 x 15] inverses of the elimination's diagonal blocks
+  const double *Ef;   // [nez][15 x 15] back-substitution blocks
+  const double *lev;  // [nez (N+1)][4]: rho_r, rho e_r, c_r, unused
+  double lift, dtg;   // 2 / (h_z w_0), dt gamma
+};
+struct HeviSetup {
+  int nez;
+  double hz, w[kMaxQ], D[kMaxQ * kMaxQ];
+  const double *rho_r, *p_r, *z;  // per level node (nez (N+1))
+  double g, Rd, cvd, T0, dtg;
+};
+struct HeviHost {
+  std::vector<double> Lb, Gf, Ef, lev;
+  double lift = 0.0;
+};
+bool hevi_build(const HeviSetup &S, HeviHost &H);
+cudaError_t launch_hevi_apply(const double *Q, double *out, const HeviTables &T, const KParams &P, cudaStream_t s);
+cudaError_t launch_hevi_solve(const double *B, double *Y, const HeviTables &T, const KParams &P, cudaStream_t s);
+// out = Q + dt sum_k c[k] X[k], k < n <= 4, over count doubles
+struct LinComb {
+  int n;
+  double dt, c[4];
+  const double *X[4];
+};
+cudaError_t launch_lincomb(double *out, const double *Q, const LinComb &lc, long long count, cudaStream_t s);
 
 // Learned closure network (mlp.cu)
 struct MlpPacked;

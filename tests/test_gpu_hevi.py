@@ -1,0 +1,68 @@
+"""HEVI on the GPU (Sec. 3.2; FP64 path): ARK2 of Giraldo, Kelly &
+Constantinescu (2013) with the vertical linear acoustic-gravity operator
+implicit, its block-tridiagonal line solves and the explicit remainder,
+against the oracle's ARK2 (dense solves of the same operator assembled by
+applying it to unit vectors): step increments to 1e-11 relative L2 on the
+bubble box, and on thin elements at a step beyond the explicit vertical
+acoustic limit."""
+import numpy as np
+import pytest
+
+from paper_2110_00853_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _levels(arr, mesh):
+    Nq = mesh["N"] + 1
+    return np.array([arr[ez * mesh["nex"] * mesh["ney"], k * Nq * Nq] for ez in range(mesh["nez"])
+                     for k in range(Nq)])
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _run(orc, m, ph, c, nsteps, dt, fuzz=0.0):
+    from paper_2110_00853_b300 import cmles
+    ph = dict(ph, integrator="ark2_hevi", dt=dt)
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, c)
+    if fuzz:
+        rng = np.random.default_rng(4)
+        u = rng.uniform(-fuzz, fuzz, size=(Q.shape[0], 3, Q.shape[2]))
+        Q = Q.copy()
+        Q[:, 4] += 0.5 * Q[:, 0] * (u ** 2).sum(1) + (Q[:, 1:4] * u).sum(1)
+        Q[:, 1:4] += Q[:, 0][:, None] * u
+    Qo, fails = S.ark2_hevi(Q, nsteps, dt)
+    assert fails == 0
+    G = cmles.Solver(m, ph, precision="fp64")
+    G.set_reference(_levels(rr, m), _levels(pr, m))
+    G.set_state(torch.from_numpy(Q).cuda())
+    G.step(nsteps)
+    Qg = G.get_state().cpu().numpy()
+    d = G.diagnostics()
+    assert not d["nonfinite"] and d["steps"] == nsteps
+    b_orc, _ = S.budgets(Qo)
+    for v in (0, 4):
+        assert abs(d["budget"][v] - b_orc[v]) <= 1e-13 * abs(b_orc[v]), v
+    return Q, Qo, Qg
+
+
+def test_hevi_steps_match_oracle_bubble(orc):
+    m, ph, c = I.mesh("c1"), I.physics("c1"), I.case("c1")
+    Q, Qo, Qg = _run(orc, m, ph, c, 3, 0.02, fuzz=1.0)
+    errs = [_rel(Qg[:, v] - Q[:, v], Qo[:, v] - Q[:, v]) for v in range(6) if np.abs(Qo[:, v] - Q[:, v]).max() > 0]
+    print("HEVI bubble 3 steps rel L2", errs)
+    assert max(errs) <= 1e-11, errs
+
+
+def test_hevi_thin_elements_beyond_explicit_limit(orc):
+    m, ph, c = I.mesh("c1"), I.physics("c1"), I.case("c1")
+    m = dict(m, nex=2, ney=2, nez=8, Lx=2000.0, Ly=2000.0, Lz=160.0)
+    c = dict(c, zc=80.0, r0=400.0)
+    Q, Qo, Qg = _run(orc, m, ph, c, 20, 0.05)
+    errs = [_rel(Qg[:, v] - Q[:, v], Qo[:, v] - Q[:, v]) for v in (0, 3, 4)]
+    print("HEVI thin elements, dt 0.05 s, 20 steps rel L2", errs)
+    assert max(errs) <= 1e-10, errs
+    assert np.isfinite(Qg).all() and np.abs(Qg[:, 3] / Qg[:, 0]).max() < 5.0
