@@ -66,3 +66,14 @@ def test_hevi_thin_elements_beyond_explicit_limit(orc):
     print("HEVI thin elements, dt 0.05 s, 20 steps rel L2", errs)
     assert max(errs) <= 1e-10, errs
     assert np.isfinite(Qg).all() and np.abs(Qg[:, 3] / Qg[:, 0]).max() < 5.0
+
+
+def test_hevi_moist_layer_matches_oracle(orc):
+    """The moist layer's sub-box (saturation adjustment, sponge, surface
+    fluxes in the explicit part; the dry linear operator implicit): two
+    steps against the oracle."""
+    m, ph, c = I.sub_mesh("c2", 4, 3, 16), I.physics("c2"), I.case("c2")
+    Q, Qo, Qg = _run(orc, m, ph, c, 2, ph["dt"], fuzz=0.5)
+    errs = [_rel(Qg[:, v] - Q[:, v], Qo[:, v] - Q[:, v]) for v in range(6)]
+    print("HEVI moist sub-box 2 steps rel L2", errs)
+    assert max(errs) <= 1e-11, errs
