@@ -281,6 +281,19 @@ cmles_status cmles_kernel_times(cmles_handle h, long long count[3], double ms[3]
 /* Kernel launches issued by this handle since creation (always counted). */
 long long cmles_launch_count(cmles_handle h);
 
+/* The HEVI pieces of a handle created with CMLES_ARK2_HEVI (Sec. 3.2), on
+ * device states in the layout of cmles_set_state:
+ * cmles_hevi_operator: out = L (Q - Q_ref), the vertical linear operator
+ *   (all six components; Q_ref = (rho_r, 0, 0, 0, rho e_r, 0) with
+ *   rho e_r = rho_r (c_vm (T_r - T_0) + q_r I_v0 + g z), T_r = p_r/(rho_r R_m),
+ *   the mixture constants at the reference total water q_r given to
+ *   cmles_set_reference, 0 if none).
+ * cmles_hevi_solve: Y = Q_ref + (I - dt gamma L)^-1 (B - Q_ref) with
+ *   gamma = 1 - 1/sqrt 2 and the handle's dt; B and Y must differ.
+ * Asynchronous; CMLES_ERR_STATE for another integrator or no reference. */
+cmles_status cmles_hevi_operator(cmles_handle h, const double *Q_dev, double *out_dev);
+cmles_status cmles_hevi_solve(cmles_handle h, const double *B_dev, double *Y_dev);
+
 /* Test hook for the failure path of the bounded device-side waits (no GPU
  * fault involved): with enable != 0, each CTA of the learned-closure
  * gradient pass also waits, with a bound, on an mbarrier that nothing

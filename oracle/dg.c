@@ -71,6 +71,7 @@ orc_solver *orc_create(const orc_mesh *m, const orc_params *p) {
   s->Dm = (double *)malloc((size_t)E * 3 * sizeof(double));
   s->EToE = (int *)malloc((size_t)E * 6 * sizeof(int));
   s->rho_r = (double *)calloc(nn, sizeof(double));
+  s->qt_r = (double *)calloc(nn, sizeof(double));
   s->p_r = (double *)calloc(nn, sizeof(double));
   s->tau = (double *)calloc(nn, sizeof(double));
   s->G = (double *)malloc(nn * 6 * sizeof(double));
@@ -215,7 +216,7 @@ orc_solver *orc_create(const orc_mesh *m, const orc_params *p) {
 void orc_destroy(orc_solver *s) {
   if (!s) return;
   free(s->x); free(s->y); free(s->z); free(s->J); free(s->Ja); free(s->Delta); free(s->Dm); free(s->EToE);
-  free(s->rho_r); free(s->p_r); free(s->tau);
+  free(s->rho_r); free(s->p_r); free(s->tau); free(s->qt_r);
   free(s->G); free(s->gradG); free(s->nut); free(s->Dt); free(s->F2); free(s->aux); free(s->Ftot);
   free(s);
 }
@@ -240,6 +241,10 @@ void orc_set_reference(orc_solver *s, const double *rho_r, const double *p_r) {
   size_t nn = (size_t)s->E * s->Np;
   memcpy(s->rho_r, rho_r, nn * sizeof(double));
   memcpy(s->p_r, p_r, nn * sizeof(double));
+}
+
+void orc_set_reference_qt(orc_solver *s, const double *qt_r) {
+  memcpy(s->qt_r, qt_r, (size_t)s->E * s->Np * sizeof(double));
 }
 
 void orc_set_mlp(orc_solver *s, const double *W1, const double *b1, const double *W2, const double *b2,

@@ -11,13 +11,21 @@
  * operator (strong-form nodal DG along z on the LGL nodes, Sec. 3.1) with a
  * Rusanov flux at the reference sound speed; it acts on the deviations
  *   y = (rho - rho_r, rho w, rho e - rho e_r)
- * with the linear equation of state of dry air at rest,
- *   p = R_d T_0 rho + (R_d / c_vd) (rho e - rho Phi),   Phi = g z,
- * (Eq. eos with the internal energy of Eq. internal_energies), so that
+ * with the equation of state of unsaturated air at rest and fixed total
+ * water q_r(z) (Eqs. eos and internal_energies with q_l = 0), linear in
+ * (rho, rho e):
+ *   p = R_m T_0 rho + kappa_m (rho e - rho Phi - rho q_r I_v0),   Phi = g z,
+ * kappa_m = R_m / c_vm, R_m and c_vm the mixture constants at q_r, so that
  *   d rho'/dt  = -d(rho w)/dz
- *   d(rho w)/dt = -d p'/dz - g rho',    p' = (R_d T_0 - kappa Phi) rho' + kappa (rho e)'
+ *   d(rho w)/dt = -d p'/dz - g rho',    p' = a rho' + kappa_m (rho e)',
  *   d(rho e)'/dt = -d(h_r rho w)/dz,    h_r = (rho e_r + p_r) / rho_r,
- * kappa = R_d / c_vd, rho e_r = (p_r - R_d T_0 rho_r) / kappa + rho_r Phi.
+ * a = R_m T_0 - kappa_m (Phi + q_r I_v0), rho e_r = rho_r (c_vm (T_r - T_0) +
+ * q_r I_v0 + Phi), T_r = p_r / (rho_r R_m), c_r^2 = (1 + kappa_m) p_r / rho_r.
+ * The linearisation point is the reference (rho_r, p_r) with the reference
+ * total water q_r (zero unless set): linearising a moist state about a dry
+ * energy would leave a deviation (rho e)' as large as the latent part of
+ * rho e, whose cancellation between the explicit and implicit parts costs
+ * digits in rho'.
  * The face flux of the full operator applies Rusanov dissipation at the
  * sound speed to every component on vertical faces; for the horizontal
  * momentum and rho q_t the linear operator keeps that dissipation,
@@ -28,15 +36,25 @@
 
 #include "oracle_internal.h"
 
-/* the reference quantities of the linear operator at node q */
-static void lin_ref(const orc_solver *s, size_t q, double *phi, double *rhoe_r, double *h_r, double *c_r) {
+/* the reference quantities of the linear operator at node q: Phi, rho e_r,
+ * h_r, c_r, kappa_m and a */
+typedef struct {
+  double phi, rhoe_r, h_r, c_r, kappa, a;
+} lin_coef;
+static lin_coef lin_ref(const orc_solver *s, size_t q) {
   const orc_params *P = &s->p;
-  const double kappa = P->Rd / P->cvd;
-  const double rr = s->rho_r[q], pr = s->p_r[q];
-  *phi = P->g * s->z[q];
-  *rhoe_r = (pr - P->Rd * P->T0 * rr) / kappa + rr * (*phi);
-  *h_r = (*rhoe_r + pr) / rr;
-  *c_r = sqrt((P->cvd + P->Rd) / P->cvd * pr / rr);
+  const double rr = s->rho_r[q], pr = s->p_r[q], qr = s->qt_r[q];
+  const double Rm = (1.0 - qr) * P->Rd + qr * P->Rv, cvm = (1.0 - qr) * P->cvd + qr * P->cvv;
+  const double Iv0 = P->Lv0 - P->Rv * P->T0;
+  lin_coef c;
+  c.phi = P->g * s->z[q];
+  c.kappa = Rm / cvm;
+  const double Tr = pr / (rr * Rm);
+  c.rhoe_r = rr * (cvm * (Tr - P->T0) + qr * Iv0 + c.phi);
+  c.h_r = (c.rhoe_r + pr) / rr;
+  c.c_r = sqrt((1.0 + c.kappa) * pr / rr);
+  c.a = Rm * P->T0 - c.kappa * (c.phi + qr * Iv0);
+  return c;
 }
 
 /* The state the operator is linearised about: (rho_r, 0, 0, 0, rho e_r, 0). */
@@ -45,20 +63,18 @@ void orc_vlin_reference(orc_solver *s, double *Qref) {
   for (int e = 0; e < s->E; ++e)
     for (int n = 0; n < Np; ++n) {
       const size_t q = (size_t)e * Np + n;
-      double phi, rer, hr, cr;
-      lin_ref(s, q, &phi, &rer, &hr, &cr);
+      const lin_coef c = lin_ref(s, q);
       for (int v = 0; v < 6; ++v) Qref[((size_t)e * 6 + v) * Np + n] = 0.0;
       Qref[((size_t)e * 6 + 0) * Np + n] = s->rho_r[q];
-      Qref[((size_t)e * 6 + 4) * Np + n] = rer;
+      Qref[((size_t)e * 6 + 4) * Np + n] = c.rhoe_r;
     }
 }
 
 /* vertical flux of the deviations y = (rho', m, E') at a node */
-static void vflux(const orc_params *P, double phi, double hr, const double y[3], double F[3]) {
-  const double kappa = P->Rd / P->cvd;
+static void vflux(const lin_coef *c, const double y[3], double F[3]) {
   F[0] = y[1];
-  F[1] = (P->Rd * P->T0 - kappa * phi) * y[0] + kappa * y[2];
-  F[2] = hr * y[1];
+  F[1] = c->a * y[0] + c->kappa * y[2];
+  F[2] = c->h_r * y[1];
 }
 
 /* out = L (Q - Qref): components 0, 3, 4 (rho, rho w, rho e); the others 0. */
@@ -74,12 +90,11 @@ void orc_vlin_apply(orc_solver *s, const double *Q, double *out) {
     double y[ORC_MAXQ * ORC_MAXQ * ORC_MAXQ][3], F[ORC_MAXQ * ORC_MAXQ * ORC_MAXQ][3];
     for (int n = 0; n < Np; ++n) {
       const size_t q = (size_t)e * Np + n;
-      double phi, rer, hr, cr;
-      lin_ref(s, q, &phi, &rer, &hr, &cr);
+      const lin_coef c = lin_ref(s, q);
       y[n][0] = Q[((size_t)e * 6 + 0) * Np + n] - s->rho_r[q];
       y[n][1] = Q[((size_t)e * 6 + 3) * Np + n];
-      y[n][2] = Q[((size_t)e * 6 + 4) * Np + n] - rer;
-      vflux(P, phi, hr, y[n], F[n]);
+      y[n][2] = Q[((size_t)e * 6 + 4) * Np + n] - c.rhoe_r;
+      vflux(&c, y[n], F[n]);
     }
     for (int n = 0; n < Np; ++n) {
       const int i = n % Nq, j = (n / Nq) % Nq, k = n / (Nq * Nq);
@@ -96,17 +111,16 @@ void orc_vlin_apply(orc_solver *s, const double *Q, double *out) {
         const double nz = side == 0 ? -1.0 : 1.0;
         const int nb = s->EToE[e * 6 + (side == 0 ? 4 : 5)];
         const size_t q = (size_t)e * Np + n;
-        double phi, rer, hr, cr;
-        lin_ref(s, q, &phi, &rer, &hr, &cr);
+        const lin_coef c = lin_ref(s, q);
+        const double cr = c.c_r;
         double yp[3], Fp[3];
         if (nb >= 0) {
           const int np = i + Nq * (j + Nq * (side == 0 ? N : 0));
           const size_t qp = (size_t)nb * Np + np;
-          double phip, rerp, hrp, crp;
-          lin_ref(s, qp, &phip, &rerp, &hrp, &crp);
+          const lin_coef cp = lin_ref(s, qp);
           yp[0] = Q[((size_t)nb * 6 + 0) * Np + np] - s->rho_r[qp];
           yp[1] = Q[((size_t)nb * 6 + 3) * Np + np];
-          yp[2] = Q[((size_t)nb * 6 + 4) * Np + np] - rerp;
+          yp[2] = Q[((size_t)nb * 6 + 4) * Np + np] - cp.rhoe_r;
         } else {
           /* reflecting wall: the normal momentum mirrored */
           yp[0] = y[n][0];
@@ -114,7 +128,7 @@ void orc_vlin_apply(orc_solver *s, const double *Q, double *out) {
           yp[2] = y[n][2];
         }
         /* the shared face node has the face's height, hence the same reference */
-        vflux(P, phi, hr, yp, Fp);
+        vflux(&c, yp, Fp);
         for (int c = 0; c < 3; ++c) {
           const double Fstar = 0.5 * nz * (F[n][c] + Fp[c]) + 0.5 * cr * (y[n][c] - yp[c]);
           r[c] += lift * (nz * F[n][c] - Fstar);
@@ -125,9 +139,7 @@ void orc_vlin_apply(orc_solver *s, const double *Q, double *out) {
       for (int side = 0; side < 2; ++side) {
         if ((side == 0 && k != 0) || (side == 1 && k != N)) continue;
         const int nb = s->EToE[e * 6 + (side == 0 ? 4 : 5)];
-        const size_t q = (size_t)e * Np + n;
-        double phi, rer, hr, cr;
-        lin_ref(s, q, &phi, &rer, &hr, &cr);
+        const double cr = lin_ref(s, (size_t)e * Np + n).c_r;
         const int np = i + Nq * (j + Nq * (side == 0 ? N : 0));
         const int vs[3] = {1, 2, 5};
         for (int c = 0; c < 3; ++c) {

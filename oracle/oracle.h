@@ -152,6 +152,7 @@ void orc_lsrk54_coefficients(double A[5], double B[5], double c[5]);
 int orc_lsrk144(orc_solver *s, double *Q, int nsteps, double dt);
 /* HEVI (Sec. 3.2): the vertical acoustic-gravity operator linearised about
  * the reference (hevi.c); flat meshes. */
+void orc_set_reference_qt(orc_solver *s, const double *qt_r /* [E][Np] */);
 void orc_vlin_reference(orc_solver *s, double *Qref);
 void orc_vlin_apply(orc_solver *s, const double *Q, double *out);
 void orc_lsrk144_coefficients(double A[14], double B[14], double c[14]);

@@ -109,6 +109,7 @@ def _declare(L):
     L.orc_lsrk144.restype = C.c_int
     L.orc_lsrk144_coefficients.argtypes = [_DP, _DP, _DP]
     L.orc_vlin_reference.argtypes = [C.c_void_p, _DP]
+    L.orc_set_reference_qt.argtypes = [C.c_void_p, _DP]
     L.orc_vlin_apply.argtypes = [C.c_void_p, _DP, _DP]
     L.orc_budgets.argtypes = [C.c_void_p, _DP, _DP]
     L.orc_budgets.restype = C.c_int
@@ -385,6 +386,10 @@ class Solver:
         return Q, fails
 
     # ------------------------------------------------------------ HEVI (Sec. 3.2)
+
+    def set_reference_qt(self, qt_r):
+        """Reference total water [E][Np] of the HEVI linearisation (default 0)."""
+        lib().orc_set_reference_qt(self.h, _p(np.ascontiguousarray(qt_r, float)))
 
     def vlin_reference(self):
         """The state the vertical linear operator is linearised about."""

@@ -16,6 +16,7 @@ struct orc_solver {
   double *Dm;                 /* [E][3], L_m / N from the element's extent along axis m */
   int *EToE;                  /* [E][6], -1 = wall */
   double *rho_r, *p_r, *tau;  /* [E][Np] */
+  double *qt_r;               /* [E][Np] reference total water of the HEVI linearisation (0 unless set) */
   /* work arrays of the last RHS */
   double *G, *gradG, *nut, *Dt, *F2, *aux, *Ftot;
   /* learned closure (FP64 copy) */

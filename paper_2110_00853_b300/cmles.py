@@ -105,6 +105,8 @@ def load(path=LIB_PATH):
     L.cmles_mlp_loss_grad.argtypes = [_VP, _VP, _VP, C.c_longlong, _VP, _VP, _VP]
     L.cmles_mlp_adam.argtypes = [_VP, _VP, _VP, _VP, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, _VP]
     L.cmles_test_stall_tc.argtypes = [_H, C.c_int]
+    L.cmles_hevi_operator.argtypes = [_H, _VP, _VP]
+    L.cmles_hevi_solve.argtypes = [_H, _VP, _VP]
     for n in ("cmles_launch_count", "cmles_num_elements", "cmles_num_nodes", "cmles_device_bytes"):
         getattr(L, n).argtypes = [_H]
         getattr(L, n).restype = C.c_longlong
@@ -342,6 +344,18 @@ class Solver:
 
     def launch_count(self):
         return self.L.cmles_launch_count(self.h)
+
+    def hevi_operator(self, Q):
+        """L (Q - Q_ref) of a HEVI handle (device tensors, FP64 state layout)."""
+        out = self.torch.empty_like(Q)
+        self._check(self.L.cmles_hevi_operator(self.h, C.c_void_p(Q.data_ptr()), C.c_void_p(out.data_ptr())))
+        return out
+
+    def hevi_solve(self, B):
+        """Q_ref + (I - dt gamma L)^-1 (B - Q_ref) of a HEVI handle."""
+        Y = self.torch.empty_like(B)
+        self._check(self.L.cmles_hevi_solve(self.h, C.c_void_p(B.data_ptr()), C.c_void_p(Y.data_ptr())))
+        return Y
 
     def test_stall_tc(self, enable):
         """Test hook: make the learned-closure kernels' bounded tensor-core

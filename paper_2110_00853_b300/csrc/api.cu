@@ -140,7 +140,7 @@ struct cmles_t {
   int tc_stall = 0;
   // HEVI: level reference (host copy), stage buffers R0 R1 R2 L0 L1 B Y and
   // the tables of the vertical operator for the step hv_dt
-  std::vector<double> ref_rho_h, ref_p_h;
+  std::vector<double> ref_rho_h, ref_p_h, ref_qt_h;
   double *hv_buf[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double *hv_tab = nullptr;
   double hv_dt = -1.0;
@@ -920,6 +920,10 @@ cmles_status cmles_set_reference(cmles_handle h, const double *rho_r, const doub
   CK(cudaMemcpyAsync(h->p_r, p_r, nlev * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   h->ref_rho_h.assign(rho_r, rho_r + nlev);
   h->ref_p_h.assign(p_r, p_r + nlev);
+  if (qt_r)
+    h->ref_qt_h.assign(qt_r, qt_r + nlev);
+  else
+    h->ref_qt_h.assign(nlev, 0.0);
   h->hv_dt = -1.0;  // the HEVI tables depend on the reference
   {
     std::vector<double> ex(nlev);
@@ -1216,11 +1220,15 @@ cmles_status ensure_hevi(cmles_handle h) {
   for (int l = 0; l < nlev; ++l) z[l] = level_z(h, l);
   S.rho_r = h->ref_rho_h.data();
   S.p_r = h->ref_p_h.data();
+  S.qt_r = h->ref_qt_h.data();
   S.z = z.data();
   S.g = h->prm.g;
   S.Rd = h->prm.Rd;
+  S.Rv = h->prm.Rv;
   S.cvd = h->prm.cvd;
+  S.cvv = h->prm.cvv;
   S.T0 = h->prm.T0;
+  S.Iv0 = h->prm.Lv0 - h->prm.Rv * h->prm.T0;
   S.dtg = h->prm.dt * (1.0 - 1.0 / sqrt(2.0));
   HeviHost H;
   if (!hevi_build(S, H)) return fail(h, CMLES_ERR_ARG, "HEVI: I - dt gamma L is singular");
@@ -1462,6 +1470,28 @@ cmles_status cmles_kernel_times(cmles_handle h, long long count[3], double ms[3]
 }
 
 long long cmles_launch_count(cmles_handle h) { return h ? h->launches : -1; }
+
+cmles_status cmles_hevi_operator(cmles_handle h, const double *Q_dev, double *out_dev) {
+  if (!h || !Q_dev || !out_dev) return fail(h, CMLES_ERR_ARG, "cmles_hevi_operator: null argument");
+  if (h->prm.integrator != CMLES_ARK2_HEVI) return fail(h, CMLES_ERR_STATE, "cmles_hevi_operator: not a HEVI handle");
+  if (!h->have_ref) return fail(h, CMLES_ERR_STATE, "cmles_hevi_operator: reference state not set");
+  cmles_status st = ensure_hevi(h);
+  if (st != CMLES_OK) return st;
+  LaunchScope ls(h, 2, 1);
+  CK(launch_hevi_apply(Q_dev, out_dev, h->hv_T, h->K, h->stream));
+  return CMLES_OK;
+}
+
+cmles_status cmles_hevi_solve(cmles_handle h, const double *B_dev, double *Y_dev) {
+  if (!h || !B_dev || !Y_dev || B_dev == Y_dev) return fail(h, CMLES_ERR_ARG, "cmles_hevi_solve: bad argument");
+  if (h->prm.integrator != CMLES_ARK2_HEVI) return fail(h, CMLES_ERR_STATE, "cmles_hevi_solve: not a HEVI handle");
+  if (!h->have_ref) return fail(h, CMLES_ERR_STATE, "cmles_hevi_solve: reference state not set");
+  cmles_status st = ensure_hevi(h);
+  if (st != CMLES_OK) return st;
+  LaunchScope ls(h, 2, 1);
+  CK(launch_hevi_solve(B_dev, Y_dev, h->hv_T, h->K, h->stream));
+  return CMLES_OK;
+}
 
 cmles_status cmles_test_stall_tc(cmles_handle h, int enable) {
   if (!h) return CMLES_ERR_ARG;

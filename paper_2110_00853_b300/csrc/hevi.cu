@@ -2,12 +2,13 @@
 // FP64 path, flat meshes, walls at the bottom and top).
 //
 // The implicit part L is the vertical acoustic-gravity operator linearised
-// about the hydrostatic reference and the rest state, with the linear
-// equation of state of dry air at rest, p = R_d T_0 rho + kappa (rho e - rho Phi):
-// on the deviations y = (rho - rho_r, rho w, rho e - rho e_r),
-//   L y = -d F(y)/dz + (0, -g rho', 0),  F = (rho w, a(z) rho' + kappa (rho e)', h_r(z) rho w),
-//   a = R_d T_0 - kappa Phi,  h_r = (rho e_r + p_r)/rho_r,
-//   rho e_r = (p_r - R_d T_0 rho_r)/kappa + rho_r Phi,
+// about the hydrostatic reference (rho_r, p_r, total water q_r) and the rest
+// state, with the equation of state of unsaturated air at rest and fixed
+// q_r, linear in (rho, rho e): p = R_m T_0 rho + kappa_m (rho e - rho Phi - rho q_r I_v0),
+// kappa_m = R_m / c_vm.  On the deviations y = (rho - rho_r, rho w, rho e - rho e_r),
+//   L y = -d F(y)/dz + (0, -g rho', 0),  F = (rho w, a rho' + kappa_m (rho e)', h_r rho w),
+//   a = R_m T_0 - kappa_m (Phi + q_r I_v0),  h_r = (rho e_r + p_r)/rho_r,
+//   rho e_r = rho_r (c_vm (T_r - T_0) + q_r I_v0 + Phi),  T_r = p_r / (rho_r R_m),
 // in strong-form nodal DG along z with a Rusanov flux at the reference sound
 // speed c_r (walls mirror rho w); the horizontal momentum and rho q_t keep
 // only that flux's dissipation on the z-faces.  The same operator holds on
@@ -293,16 +294,18 @@ bool invert(int n, const double *M, double *inv) {
 bool hevi_build(const HeviSetup &S, HeviHost &H) {
   constexpr int Nq = 5, N = 4;
   const int nez = S.nez, nlev = nez * Nq;
-  const double kappa = S.Rd / S.cvd, jz = 2.0 / S.hz;
+  const double jz = 2.0 / S.hz;
   H.lift = 2.0 / (S.hz * S.w[0]);
   H.lev.assign((size_t)nlev * 4, 0.0);
-  std::vector<double> a(nlev), hr(nlev), cr(nlev);
+  std::vector<double> a(nlev), hr(nlev), cr(nlev), kap(nlev);
   for (int l = 0; l < nlev; ++l) {
-    const double rr = S.rho_r[l], pr = S.p_r[l], phi = S.g * S.z[l];
-    const double rer = (pr - S.Rd * S.T0 * rr) / kappa + rr * phi;
-    a[l] = S.Rd * S.T0 - kappa * phi;
+    const double rr = S.rho_r[l], pr = S.p_r[l], phi = S.g * S.z[l], q = S.qt_r ? S.qt_r[l] : 0.0;
+    const double Rm = (1.0 - q) * S.Rd + q * S.Rv, cvm = (1.0 - q) * S.cvd + q * S.cvv;
+    kap[l] = Rm / cvm;
+    const double rer = rr * (cvm * (pr / (rr * Rm) - S.T0) + q * S.Iv0 + phi);
+    a[l] = Rm * S.T0 - kap[l] * (phi + q * S.Iv0);
     hr[l] = (rer + pr) / rr;
-    cr[l] = sqrt((S.cvd + S.Rd) / S.cvd * pr / rr);
+    cr[l] = sqrt((1.0 + kap[l]) * pr / rr);
     H.lev[4 * l + 0] = rr;
     H.lev[4 * l + 1] = rer;
     H.lev[4 * l + 2] = cr[l];
@@ -311,7 +314,7 @@ bool hevi_build(const HeviSetup &S, HeviHost &H) {
   H.Lb.assign((size_t)nez * 3 * kHB * kHB, 0.0);
   auto dF = [&](int l, int c, int cc) {  // d F_c / d y_cc at level node l
     if (c == 0) return cc == 1 ? 1.0 : 0.0;
-    if (c == 1) return cc == 0 ? a[l] : (cc == 2 ? kappa : 0.0);
+    if (c == 1) return cc == 0 ? a[l] : (cc == 2 ? kap[l] : 0.0);
     return cc == 1 ? hr[l] : 0.0;
   };
   for (int ez = 0; ez < nez; ++ez) {

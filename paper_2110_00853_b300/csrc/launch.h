@@ -51,8 +51,8 @@ struct HeviTables {
 struct HeviSetup {
   int nez;
   double hz, w[kMaxQ], D[kMaxQ * kMaxQ];
-  const double *rho_r, *p_r, *z;  // per level node (nez (N+1))
-  double g, Rd, cvd, T0, dtg;
+  const double *rho_r, *p_r, *qt_r, *z;  // per level node (nez (N+1)); qt_r may be null (0)
+  double g, Rd, Rv, cvd, cvv, T0, Iv0, dtg;
 };
 struct HeviHost {
   std::vector<double> Lb, Gf, Ef, lev;

@@ -24,10 +24,29 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def _qt_reference(S, Q, m):
+    """Reference total water of the linearisation: the initial column's q_t
+    per node level (the level shared by two elements taken from the lower
+    one, as cmles_set_reference does), as levels and as a per-node field."""
+    Nq = m["N"] + 1
+    lev = _levels(Q[:, 5] / Q[:, 0], m)
+    for ez in range(1, m["nez"]):
+        lev[ez * Nq] = lev[ez * Nq - 1]
+    nodes = np.zeros((S.E, S.Np))
+    slab = m["nex"] * m["ney"]
+    for e in range(S.E):
+        ez = e // slab
+        for n in range(S.Np):
+            nodes[e, n] = lev[ez * Nq + n // (Nq * Nq)]
+    return lev, nodes
+
+
 def _run(orc, m, ph, c, nsteps, dt, fuzz=0.0):
     from paper_2110_00853_b300 import cmles
     ph = dict(ph, integrator="ark2_hevi", dt=dt)
     S, Q, rr, pr, _ = orc.from_inputs(m, ph, c)
+    qlev, qnodes = _qt_reference(S, Q, m)
+    S.set_reference_qt(qnodes)
     if fuzz:
         rng = np.random.default_rng(4)
         u = rng.uniform(-fuzz, fuzz, size=(Q.shape[0], 3, Q.shape[2]))
@@ -37,7 +56,7 @@ def _run(orc, m, ph, c, nsteps, dt, fuzz=0.0):
     Qo, fails = S.ark2_hevi(Q, nsteps, dt)
     assert fails == 0
     G = cmles.Solver(m, ph, precision="fp64")
-    G.set_reference(_levels(rr, m), _levels(pr, m))
+    G.set_reference(_levels(rr, m), _levels(pr, m), qlev)
     G.set_state(torch.from_numpy(Q).cuda())
     G.step(nsteps)
     Qg = G.get_state().cpu().numpy()
@@ -66,6 +85,42 @@ def test_hevi_thin_elements_beyond_explicit_limit(orc):
     print("HEVI thin elements, dt 0.05 s, 20 steps rel L2", errs)
     assert max(errs) <= 1e-10, errs
     assert np.isfinite(Qg).all() and np.abs(Qg[:, 3] / Qg[:, 0]).max() < 5.0
+
+
+@pytest.mark.parametrize("case", ["c1", "c2"])
+def test_hevi_operator_and_solve_match_oracle(orc, case):
+    """The vertical linear operator L (Q - Q_ref) and the solve of
+    (I - dt gamma L) y = b on every vertical line, one call each, against the
+    oracle's operator and its dense solve of the operator assembled from unit
+    vectors; the dry bubble box and the moist layer's sub-box (linearised
+    about its reference total water)."""
+    from paper_2110_00853_b300 import cmles
+    m = I.mesh("c1") if case == "c1" else I.sub_mesh("c2", 4, 3, 16)
+    ph = dict(I.physics(case), integrator="ark2_hevi")
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case(case))
+    qlev, qnodes = _qt_reference(S, Q, m)
+    S.set_reference_qt(qnodes)
+    rng = np.random.default_rng(4)
+    u = rng.uniform(-0.5, 0.5, size=(Q.shape[0], 3, Q.shape[2]))
+    Q = Q.copy()
+    Q[:, 4] += 0.5 * Q[:, 0] * (u ** 2).sum(1) + (Q[:, 1:4] * u).sum(1)
+    Q[:, 1:4] += Q[:, 0][:, None] * u
+    G = cmles.Solver(m, ph, precision="fp64")
+    G.set_reference(_levels(rr, m), _levels(pr, m), qlev)
+    Qd = torch.from_numpy(Q).cuda()
+    Lg, Lo = G.hevi_operator(Qd).cpu().numpy(), S.vlin(Q)
+    errs = [_rel(Lg[:, v], Lo[:, v]) for v in range(6) if np.abs(Lo[:, v]).max() > 0]
+    print(case, "operator rel L2", errs)
+    assert max(errs) <= 1e-13, errs
+    Qr = S.vlin_reference()
+    _, Ai, _ = orc.ark2_tableaux()
+    M = np.eye(6 * m["nez"] * (m["N"] + 1)) - ph["dt"] * Ai[1, 1] * S.hevi_line_matrix()
+    Yo, Yg = S._hevi_solve(M, Q, Qr), G.hevi_solve(Qd).cpu().numpy()
+    errs = [_rel(Yg[:, v] - Qr[:, v], Yo[:, v] - Qr[:, v]) for v in range(6)]
+    print(case, "solve rel L2", errs)
+    # both solvers are accurate relative to the largest coupled unknown; rho'
+    # is some 1e4 times smaller than (rho e)' here, hence its looser bound
+    assert errs[0] <= 1e-10 and max(errs[1:]) <= 1e-12, errs
 
 
 def test_hevi_moist_layer_matches_oracle(orc):
