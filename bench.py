@@ -47,7 +47,7 @@ def alg_bytes(prec, kind, stages=5, integrator="lsrk54"):
     if kind == "grad":
         return (6 + 15 + 2) * (8 if prec == "fp64" else 4)
     if integrator == "ark2_hevi":
-        return 29 * 8
+        return 29 * 8 if prec == "fp64" else 23 * 4 + 6 * 8
     if prec == "fp64":
         return ((stages - 1) * 41 + 35) * 8 / stages
     return (41 + (stages - 2) * 53 + 65) * 4 / stages
@@ -63,7 +63,8 @@ VARIANTS = {"fp32acc64_mlp": ("fp32", "mlp", "rusanov", "lsrk54"), "fp32acc64_sl
             "fp32acc64_mlp_roe": ("fp32", "mlp", "roe", "lsrk54"),
             "fp32acc64_mlp_lsrk144": ("fp32", "mlp", "rusanov", "lsrk144"),
             "fp64_sl_lsrk144": ("fp64", "sl", "rusanov", "lsrk144"),
-            "fp64_sl_hevi": ("fp64", "sl", "rusanov", "ark2_hevi")}
+            "fp64_sl_hevi": ("fp64", "sl", "rusanov", "ark2_hevi"),
+            "fp32acc64_mlp_hevi": ("fp32", "mlp", "rusanov", "ark2_hevi")}
 DTYPE = {"fp32": "f32", "fp64": "f64"}
 # DRAM bytes per node of one launch (dram__bytes_read.sum + dram__bytes_write.sum
 # from one ncu capture on a 40 x 40 x 20-element sub-box of the box, 4M nodes,

@@ -64,8 +64,9 @@ enum { CMLES_FLUX_RUSANOV = 0, CMLES_FLUX_HLLC = 1, CMLES_FLUX_ROE = 2 };
  * linearised about the hydrostatic reference and the rest state (linear
  * equation of state of dry air at rest, Rusanov flux at the reference sound
  * speed), implicit, and everything else explicit; each implicit stage is one
- * block-tridiagonal solve per vertical line of nodes.  HEVI requires
- * CMLES_FP64, a flat mesh and walls at the bottom and top. */
+ * block-tridiagonal solve per vertical line of nodes (FP64; the stage
+ * tendencies in the handle's precision).  HEVI requires a flat mesh and
+ * walls at the bottom and top. */
 enum { CMLES_LSRK54 = 0, CMLES_LSRK144 = 1, CMLES_ARK2_HEVI = 2 };
 
 /* Arithmetic of the RHS kernels.

@@ -734,9 +734,8 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   if (params->integrator != CMLES_LSRK54 && params->integrator != CMLES_LSRK144 &&
       params->integrator != CMLES_ARK2_HEVI)
     return CMLES_ERR_ARG;
-  // HEVI: the FP64 path on flat meshes with walls at the bottom and top
-  if (params->integrator == CMLES_ARK2_HEVI &&
-      (params->precision != CMLES_FP64 || mesh->warp || mesh->periodic[2] || mesh->nez < 2))
+  // HEVI: flat meshes with walls at the bottom and top
+  if (params->integrator == CMLES_ARK2_HEVI && (mesh->warp || mesh->periodic[2] || mesh->nez < 2))
     return CMLES_ERR_ARG;
   // Vreman's directional lengths are those of the flat elements
   if (params->closure == CMLES_CLOSURE_VREMAN && mesh->warp) return CMLES_ERR_ARG;
@@ -1246,6 +1245,19 @@ cmles_status ensure_hevi(cmles_handle h) {
   return CMLES_OK;
 }
 
+// f(Y) for the HEVI stages, Y an FP64 state: the FP64 kernels, or on the
+// FP32 path the FP32 kernels on Y's shadow (built in the idle shadow buffer).
+cmles_status hevi_tendency(cmles_handle h, const double *Y, double *R) {
+  const StageCoef sc = {0.0, 0.0, 0.0, 0, 0.f, 0.f, 0.f, 1};
+  if (!h->fp32) return run_stage_pair(h, Y, nullptr, R, sc, false);
+  float *tmp = h->S32[1 - h->scur];
+  {
+    LaunchScope ls(h, 2, 1);
+    CK(launch_shadow32(Y, tmp, h->K, h->N, h->stream));
+  }
+  return run_stage_pair32(h, tmp, nullptr, R, sc, false);
+}
+
 // One ARK2 step (Giraldo, Kelly & Constantinescu 2013) with the vertical
 // linear operator L implicit: stage s solves
 //   Y_s - dt gamma L(Y_s) = Q + dt sum_{j<s} (Ae_sj f_j + (Ai_sj - Ae_sj) L_j),
@@ -1254,14 +1266,14 @@ cmles_status run_ark2_hevi(cmles_handle h) {
   const double g = 1.0 - 1.0 / sqrt(2.0), d = 1.0 / (2.0 * sqrt(2.0)), al = (3.0 + 2.0 * sqrt(2.0)) / 6.0;
   double *R0 = h->hv_buf[0], *R1 = h->hv_buf[1], *R2 = h->hv_buf[2], *L0 = h->hv_buf[3], *L1 = h->hv_buf[4];
   double *B = h->hv_buf[5], *Y = h->hv_buf[6];
-  const double *Qn = h->Q[h->cur];
-  double *Qo = h->Q[1 - h->cur];
+  // the FP32 path keeps one FP64 state: its update is made in place
+  double *Qn = h->Q[h->cur];
+  double *Qo = h->fp32 ? Qn : h->Q[1 - h->cur];
   const double dt = h->prm.dt;
   const long long count = (long long)h->nodes * 6;
-  const StageCoef sc = {0.0, 0.0, 0.0, 0, 0.f, 0.f, 0.f, 1};
   cmles_status st;
   // stage 1: Y_1 = Q
-  if ((st = run_stage_pair(h, Qn, nullptr, R0, sc, false)) != CMLES_OK) return st;
+  if ((st = hevi_tendency(h, Qn, R0)) != CMLES_OK) return st;
   {
     LaunchScope ls(h, 2, 3);
     CK(launch_hevi_apply(Qn, L0, h->hv_T, h->K, h->stream));
@@ -1270,7 +1282,7 @@ cmles_status run_ark2_hevi(cmles_handle h) {
                       h->stream));
     CK(launch_hevi_solve(B, Y, h->hv_T, h->K, h->stream));
   }
-  if ((st = run_stage_pair(h, Y, nullptr, R1, sc, false)) != CMLES_OK) return st;
+  if ((st = hevi_tendency(h, Y, R1)) != CMLES_OK) return st;
   {
     LaunchScope ls(h, 2, 3);
     CK(launch_hevi_apply(Y, L1, h->hv_T, h->K, h->stream));
@@ -1279,12 +1291,15 @@ cmles_status run_ark2_hevi(cmles_handle h) {
                       h->stream));
     CK(launch_hevi_solve(B, Y, h->hv_T, h->K, h->stream));
   }
-  if ((st = run_stage_pair(h, Y, nullptr, R2, sc, false)) != CMLES_OK) return st;
+  if ((st = hevi_tendency(h, Y, R2)) != CMLES_OK) return st;
   {
     LaunchScope ls(h, 2, 1);
     CK(launch_lincomb(Qo, Qn, LinComb{3, dt, {d, d, g, 0.0}, {R0, R1, R2, nullptr}}, count, h->stream));
   }
-  h->cur = 1 - h->cur;
+  if (h->fp32)
+    h->shadow_valid = false;  // the shadow of the new state is built when next needed
+  else
+    h->cur = 1 - h->cur;
   return CMLES_OK;
 }
 

@@ -1,5 +1,7 @@
 // HEVI time stepping (Sec. 3.2: horizontally explicit, vertically implicit;
-// FP64 path, flat meshes, walls at the bottom and top).
+// flat meshes, walls at the bottom and top).  The stages' tendencies come
+// from the DG kernels of the handle's precision; the operator, the line
+// solves and the stage combinations are FP64.
 //
 // The implicit part L is the vertical acoustic-gravity operator linearised
 // about the hydrostatic reference (rho_r, p_r, total water q_r) and the rest
@@ -217,8 +219,8 @@ __global__ void k_hevi_solve(const double *__restrict__ Bv, double *__restrict__
   }
 }
 
-// out = Q + dt sum_k c_k X_k (elementwise, up to four terms).
-__global__ void k_lincomb(double *__restrict__ out, const double *__restrict__ Q, LinComb lc, long long count) {
+// out = Q + dt sum_k c_k X_k (elementwise, up to four terms); out may be Q.
+__global__ void k_lincomb(double *out, const double *Q, LinComb lc, long long count) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
        q += (long long)gridDim.x * blockDim.x) {
     double s = 0.0;

@@ -57,9 +57,9 @@ def test_create_rejects_unsupported_combinations_without_gpu_work():
     assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == ERR_ARG
     P = cmles.make_params(dict(filter_order=-1), "fp64")
     assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == ERR_ARG
-    # HEVI: FP64, flat mesh, walls at the bottom and top; an unknown integrator
-    assert status(precision="fp32", integrator="ark2_hevi") == ERR_ARG
+    # HEVI: flat mesh, walls at the bottom and top; an unknown integrator
     assert status(mesh=dict(good, periodic=(1, 1, 1)), integrator="ark2_hevi") == ERR_ARG
+    assert status(mesh=dict(good, warp=True), precision="fp32", integrator="ark2_hevi") == ERR_ARG
     P = cmles.make_params({}, "fp64")
     P.integrator = 3
     assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == ERR_ARG
