@@ -1230,17 +1230,15 @@ cmles_status ensure_hevi(cmles_handle h) {
   S.Iv0 = h->prm.Lv0 - h->prm.Rv * h->prm.T0;
   S.dtg = h->prm.dt * (1.0 - 1.0 / sqrt(2.0));
   HeviHost H;
-  if (!hevi_build(S, H)) return fail(h, CMLES_ERR_ARG, "HEVI: I - dt gamma L is singular");
-  const size_t nb = (size_t)nez * 15 * 15;
+  if (!hevi_build(S, H)) return fail(h, CMLES_ERR_ARG, "HEVI: I - dt gamma L could not be factored");
+  const size_t nt = H.tab.size();
   if (!h->hv_tab) {
-    cmles_status st = dalloc(h, (void **)&h->hv_tab, (5 * nb + (size_t)nlev * 4) * sizeof(double));
+    cmles_status st = dalloc(h, (void **)&h->hv_tab, (nt + (size_t)nlev * 4) * sizeof(double));
     if (st != CMLES_OK) return st;
   }
-  CK(cudaMemcpy(h->hv_tab, H.Lb.data(), 3 * nb * sizeof(double), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(h->hv_tab + 3 * nb, H.Gf.data(), nb * sizeof(double), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(h->hv_tab + 4 * nb, H.Ef.data(), nb * sizeof(double), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(h->hv_tab + 5 * nb, H.lev.data(), (size_t)nlev * 4 * sizeof(double), cudaMemcpyHostToDevice));
-  h->hv_T = HeviTables{h->hv_tab, h->hv_tab + 3 * nb, h->hv_tab + 4 * nb, h->hv_tab + 5 * nb, H.lift, S.dtg};
+  CK(cudaMemcpy(h->hv_tab, H.tab.data(), nt * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->hv_tab + nt, H.lev.data(), (size_t)nlev * 4 * sizeof(double), cudaMemcpyHostToDevice));
+  h->hv_T = HeviTables{h->hv_tab, h->hv_tab + nt, H.lift, S.dtg};
   h->hv_dt = h->prm.dt;
   return CMLES_OK;
 }

@@ -40,18 +40,27 @@ __device__ __forceinline__ void hevi_line(const KParams &P, long long line, int 
   n0 = ij;  // i + Nq j: the line's node index at level k is n0 + Nq^2 k
 }
 
+// Per-level table layout (doubles): the diagonal block of L (15 x 15), the
+// two face-coupling blocks of L (3 x 3: rows of the element's bottom level
+// against the lower element's top level, rows of the top level against the
+// upper element's bottom level; every other entry of L's off-diagonal blocks
+// is zero), the inverse G of the elimination's diagonal block (15 x 15) and
+// the three nonzero columns of the back-substitution block E = G C^M (15 x 3).
+constexpr int kTB = 0, kTA = 225, kTC = 234, kTG = 243, kTE = 468, kTStride = 513;
+
 // out = L (Q - Q_ref) on every vertical line (all six components).
 __global__ void k_hevi_apply(const double *__restrict__ Q, double *__restrict__ out, const HeviTables T,
                              const KParams P) {
   constexpr int Nq = 5, Np = 125, Nf = 25;
   const long long nlines = (long long)P.nex * P.ney * Nf;
+  const size_t slab = (size_t)P.nex * P.ney;
   for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < nlines;
        line += (long long)gridDim.x * blockDim.x) {
     int ex, ey, n0;
     hevi_line(P, line, ex, ey, n0);
-    double yp[kHB], yc[kHB], yn[kHB];
+    const size_t e0 = (size_t)ex + (size_t)P.nex * ey;
     auto load = [&](int ez, double *y) {
-      const size_t e = (size_t)ex + (size_t)P.nex * (ey + (size_t)P.ney * ez);
+      const size_t e = e0 + slab * ez;
 #pragma unroll
       for (int k = 0; k < Nq; ++k) {
         const int n = n0 + Nf * k, lev = ez * Nq + k;
@@ -60,23 +69,28 @@ __global__ void k_hevi_apply(const double *__restrict__ Q, double *__restrict__ 
         y[3 * k + 2] = Q[(e * 6 + 4) * Np + n] - T.lev[4 * lev + 1];
       }
     };
+    double yc[kHB], yn[kHB], ytop_prev[3] = {0.0, 0.0, 0.0};
     load(0, yc);
     for (int ez = 0; ez < P.nez; ++ez) {
       if (ez + 1 < P.nez) load(ez + 1, yn);
-      const double *A = T.Lb + (size_t)ez * 3 * kHB * kHB;
-      const double *B = A + kHB * kHB, *C = B + kHB * kHB;
+      const double *Tz = T.tab + (size_t)ez * kTStride;
       double r[kHB];
-#pragma unroll 1
+#pragma unroll
       for (int a = 0; a < kHB; ++a) {
         double s = 0.0;
-        for (int b = 0; b < kHB; ++b) s += B[a * kHB + b] * yc[b];
-        if (ez > 0)
-          for (int b = 0; b < kHB; ++b) s += A[a * kHB + b] * yp[b];
-        if (ez + 1 < P.nez)
-          for (int b = 0; b < kHB; ++b) s += C[a * kHB + b] * yn[b];
+#pragma unroll
+        for (int b = 0; b < kHB; ++b) s += Tz[kTB + a * kHB + b] * yc[b];
         r[a] = s;
       }
-      const size_t e = (size_t)ex + (size_t)P.nex * (ey + (size_t)P.ney * ez);
+      if (ez > 0)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          r[a] += Tz[kTA + 3 * a] * ytop_prev[0] + Tz[kTA + 3 * a + 1] * ytop_prev[1] + Tz[kTA + 3 * a + 2] * ytop_prev[2];
+      if (ez + 1 < P.nez)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          r[12 + a] += Tz[kTC + 3 * a] * yn[0] + Tz[kTC + 3 * a + 1] * yn[1] + Tz[kTC + 3 * a + 2] * yn[2];
+      const size_t e = e0 + slab * ez;
 #pragma unroll
       for (int k = 0; k < Nq; ++k) {
         const int n = n0 + Nf * k;
@@ -90,20 +104,19 @@ __global__ void k_hevi_apply(const double *__restrict__ Q, double *__restrict__ 
           double o = 0.0;
           const double q = Q[(e * 6 + vs[c]) * Np + n];
           if (k == Nq - 1 && ez + 1 < P.nez) {
-            const size_t eu = e + (size_t)P.nex * P.ney;
+            const size_t eu = e + slab;
             o = -T.lift * 0.5 * T.lev[4 * (ez * Nq + k) + 2] * (q - Q[(eu * 6 + vs[c]) * Np + n0]);
           } else if (k == 0 && ez > 0) {
-            const size_t ed = e - (size_t)P.nex * P.ney;
+            const size_t ed = e - slab;
             o = -T.lift * 0.5 * T.lev[4 * (ez * Nq + k) + 2] * (q - Q[(ed * 6 + vs[c]) * Np + n0 + Nf * (Nq - 1)]);
           }
           out[(e * 6 + vs[c]) * Np + n] = o;
         }
       }
 #pragma unroll
-      for (int a = 0; a < kHB; ++a) {
-        yp[a] = yc[a];
-        yc[a] = yn[a];
-      }
+      for (int c = 0; c < 3; ++c) ytop_prev[c] = yc[12 + c];
+#pragma unroll
+      for (int a = 0; a < kHB; ++a) yc[a] = yn[a];
     }
   }
 }
@@ -119,11 +132,13 @@ __global__ void k_hevi_solve(const double *__restrict__ Bv, double *__restrict__
     int ex, ey, n0;
     hevi_line(P, line, ex, ey, n0);
     const size_t e0 = (size_t)ex + (size_t)P.nex * ey;
-    // forward sweep of the block elimination: y_ez = G_ez (b_ez - A^M_ez y_ez-1),
-    // A^M = -dt gamma A^L; y kept in Y (as deviations) until the back sweep
-    double yprev[kHB];
+    // forward sweep of the block elimination: y_ez = G_ez (b_ez - A^M_ez y_ez-1)
+    // with A^M = -dt gamma A^L (nonzero on the face levels only); y kept in Y
+    // (as deviations) until the back sweep
+    double ytop[3] = {0.0, 0.0, 0.0};
     for (int ez = 0; ez < P.nez; ++ez) {
       const size_t e = e0 + slab * ez;
+      const double *Tz = T.tab + (size_t)ez * kTStride;
       double r[kHB];
 #pragma unroll
       for (int k = 0; k < Nq; ++k) {
@@ -132,34 +147,34 @@ __global__ void k_hevi_solve(const double *__restrict__ Bv, double *__restrict__
         r[3 * k + 1] = Bv[(e * 6 + 3) * Np + n];
         r[3 * k + 2] = Bv[(e * 6 + 4) * Np + n] - T.lev[4 * lev + 1];
       }
-      if (ez > 0) {
-        const double *A = T.Lb + (size_t)ez * 3 * kHB * kHB;
-#pragma unroll 1
-        for (int a = 0; a < kHB; ++a) {
-          double s = 0.0;
-          for (int b = 0; b < kHB; ++b) s += A[a * kHB + b] * yprev[b];
-          r[a] += T.dtg * s;
-        }
-      }
-      const double *G = T.Gf + (size_t)ez * kHB * kHB;
-#pragma unroll 1
+      if (ez > 0)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          r[a] += T.dtg * (Tz[kTA + 3 * a] * ytop[0] + Tz[kTA + 3 * a + 1] * ytop[1] + Tz[kTA + 3 * a + 2] * ytop[2]);
+      double y[kHB];
+#pragma unroll
       for (int a = 0; a < kHB; ++a) {
         double s = 0.0;
-        for (int b = 0; b < kHB; ++b) s += G[a * kHB + b] * r[b];
-        yprev[a] = s;
+#pragma unroll
+        for (int b = 0; b < kHB; ++b) s += Tz[kTG + a * kHB + b] * r[b];
+        y[a] = s;
       }
 #pragma unroll
       for (int k = 0; k < Nq; ++k) {
         const int n = n0 + Nf * k;
-        Y[(e * 6 + 0) * Np + n] = yprev[3 * k + 0];
-        Y[(e * 6 + 3) * Np + n] = yprev[3 * k + 1];
-        Y[(e * 6 + 4) * Np + n] = yprev[3 * k + 2];
+        Y[(e * 6 + 0) * Np + n] = y[3 * k + 0];
+        Y[(e * 6 + 3) * Np + n] = y[3 * k + 1];
+        Y[(e * 6 + 4) * Np + n] = y[3 * k + 2];
       }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ytop[c] = y[12 + c];
     }
-    // back sweep: x_ez = y_ez - E_ez x_ez+1, then Y = Q_ref + x
-    double xnext[kHB];
+    // back sweep: x_ez = y_ez - E_ez x_ez+1 (E nonzero in the columns of the
+    // upper element's bottom level), then Y = Q_ref + x
+    double xbot[3] = {0.0, 0.0, 0.0};
     for (int ez = P.nez - 1; ez >= 0; --ez) {
       const size_t e = e0 + slab * ez;
+      const double *Tz = T.tab + (size_t)ez * kTStride;
       double x[kHB];
 #pragma unroll
       for (int k = 0; k < Nq; ++k) {
@@ -168,15 +183,10 @@ __global__ void k_hevi_solve(const double *__restrict__ Bv, double *__restrict__
         x[3 * k + 1] = Y[(e * 6 + 3) * Np + n];
         x[3 * k + 2] = Y[(e * 6 + 4) * Np + n];
       }
-      if (ez + 1 < P.nez) {
-        const double *E = T.Ef + (size_t)ez * kHB * kHB;
-#pragma unroll 1
-        for (int a = 0; a < kHB; ++a) {
-          double s = 0.0;
-          for (int b = 0; b < kHB; ++b) s += E[a * kHB + b] * xnext[b];
-          x[a] -= s;
-        }
-      }
+      if (ez + 1 < P.nez)
+#pragma unroll
+        for (int a = 0; a < kHB; ++a)
+          x[a] -= Tz[kTE + 3 * a] * xbot[0] + Tz[kTE + 3 * a + 1] * xbot[1] + Tz[kTE + 3 * a + 2] * xbot[2];
 #pragma unroll
       for (int k = 0; k < Nq; ++k) {
         const int n = n0 + Nf * k, lev = ez * Nq + k;
@@ -185,7 +195,7 @@ __global__ void k_hevi_solve(const double *__restrict__ Bv, double *__restrict__
         Y[(e * 6 + 4) * Np + n] = T.lev[4 * lev + 1] + x[3 * k + 2];
       }
 #pragma unroll
-      for (int a = 0; a < kHB; ++a) xnext[a] = x[a];
+      for (int c = 0; c < 3; ++c) xbot[c] = x[c];
     }
     // horizontal momentum and rho q_t: each z-face couples only its two face
     // nodes, (1 + a) q_t - a q_b = b_t and -a q_t + (1 + a) q_b = b_b with
@@ -376,6 +386,28 @@ bool hevi_build(const HeviSetup &S, HeviHost &H) {
         double s = 0.0;
         for (int k = 0; k < kHB; ++k) s += G[i * kHB + k] * (-S.dtg * C[k * kHB + j]);
         E[i * kHB + j] = s;
+      }
+  }
+  // the kernels' per-level table; the face-coupling blocks must be the only
+  // nonzeros of L's off-diagonal blocks and of E
+  H.tab.assign((size_t)nez * kTStride, 0.0);
+  for (int ez = 0; ez < nez; ++ez) {
+    const double *A = H.Lb.data() + (size_t)ez * 3 * kHB * kHB, *B = A + kHB * kHB, *C = B + kHB * kHB;
+    const double *G = H.Gf.data() + (size_t)ez * kHB * kHB, *E = H.Ef.data() + (size_t)ez * kHB * kHB;
+    double *Tz = H.tab.data() + (size_t)ez * kTStride;
+    for (int i = 0; i < kHB * kHB; ++i) {
+      Tz[kTB + i] = B[i];
+      Tz[kTG + i] = G[i];
+    }
+    for (int i = 0; i < kHB; ++i)
+      for (int j = 0; j < kHB; ++j) {
+        const bool a_face = i < 3 && j >= 12, c_face = i >= 12 && j < 3, e_col = j < 3;
+        if ((A[i * kHB + j] != 0.0 && !a_face) || (C[i * kHB + j] != 0.0 && !c_face) ||
+            (E[i * kHB + j] != 0.0 && !e_col))
+          return false;
+        if (a_face) Tz[kTA + 3 * i + (j - 12)] = A[i * kHB + j];
+        if (c_face) Tz[kTC + 3 * (i - 12) + j] = C[i * kHB + j];
+        if (e_col) Tz[kTE + 3 * i + j] = E[i * kHB + j];
       }
   }
   return true;

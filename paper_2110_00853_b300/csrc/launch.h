@@ -42,9 +42,7 @@ cudaError_t launch_expfilter(double *Q, float *S32, const ExpFilter &F, int N, i
 // HEVI (hevi.cu): the vertical linear operator's element blocks and the
 // factors of I - dt gamma L, built on the host, used by the line kernels.
 struct HeviTables {
-  const double *Lb;   // [nez][sub, diag, super][15 x 15] blocks of L
-  const double *Gf;   // [nez][15 x 15] inverses of the elimination's diagonal blocks
-  const double *Ef;   // [nez][15 x 15] back-substitution blocks
+  const double *tab;  // [nez][513]: L's diagonal and face blocks, G and E's columns (hevi.cu)
   const double *lev;  // [nez (N+1)][4]: rho_r, rho e_r, c_r, unused
   double lift, dtg;   // 2 / (h_z w_0), dt gamma
 };
@@ -55,7 +53,8 @@ struct HeviSetup {
   double g, Rd, Rv, cvd, cvv, T0, Iv0, dtg;
 };
 struct HeviHost {
-  std::vector<double> Lb, Gf, Ef, lev;
+  std::vector<double> Lb, Gf, Ef, lev;  // full blocks of L, G and E; level values
+  std::vector<double> tab;              // the kernels' packed per-level table
   double lift = 0.0;
 };
 bool hevi_build(const HeviSetup &S, HeviHost &H);
