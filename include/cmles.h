@@ -201,6 +201,20 @@ cmles_status cmles_get_state(cmles_handle h, double *Q_dev);
 cmles_status cmles_set_state_host(cmles_handle h, const double *Q_host);
 cmles_status cmles_get_state_host(cmles_handle h, double *Q_host);
 
+/* Double-buffered upload of host states, so that a step can run while the
+ * next state is copied.  cmles_stage_state_host starts an asynchronous copy
+ * of Q_host (same layout; pinned memory for full speed, and it must stay
+ * unchanged until the copy is committed) into the handle's staging buffer on
+ * an internal copy stream, after the work already queued on the handle's
+ * stream, and returns at once.  cmles_commit_staged_state makes the handle's
+ * stream wait for that copy and takes the staged state as the handle's state,
+ * as cmles_set_state would; the previous state buffer becomes the next
+ * staging buffer.  The staging buffer (one state) is allocated at the first
+ * call.  Errors: CMLES_ERR_ARG, CMLES_ERR_OOM, CMLES_ERR_CUDA; commit without
+ * a staged copy gives CMLES_ERR_STATE. */
+cmles_status cmles_stage_state_host(cmles_handle h, const double *Q_host);
+cmles_status cmles_commit_staged_state(cmles_handle h);
+
 /* RHS of Eq. matrixProblem for the state Q (device, FP64) into RHS (device,
  * FP64, same layout), in the handle's precision.  The handle's own state is
  * left unchanged. */

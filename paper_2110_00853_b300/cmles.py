@@ -105,6 +105,8 @@ def load(path=LIB_PATH):
     L.cmles_mlp_loss_grad.argtypes = [_VP, _VP, _VP, C.c_longlong, _VP, _VP, _VP]
     L.cmles_mlp_adam.argtypes = [_VP, _VP, _VP, _VP, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, _VP]
     L.cmles_test_stall_tc.argtypes = [_H, C.c_int]
+    L.cmles_stage_state_host.argtypes = [_H, _VP]
+    L.cmles_commit_staged_state.argtypes = [_H]
     L.cmles_hevi_operator.argtypes = [_H, _VP, _VP]
     L.cmles_hevi_solve.argtypes = [_H, _VP, _VP]
     for n in ("cmles_launch_count", "cmles_num_elements", "cmles_num_nodes", "cmles_device_bytes"):
@@ -278,6 +280,17 @@ class Solver:
         Q = Q.contiguous()
         assert not Q.is_cuda and Q.dtype == self.torch.float64
         self._check(self.L.cmles_set_state_host(self.h, C.c_void_p(Q.data_ptr())))
+
+    def stage_state_host(self, Q):
+        """Start copying the pinned host state Q into the staging buffer
+        (asynchronous; Q must stay unchanged until committed)."""
+        assert not Q.is_cuda and Q.dtype == self.torch.float64 and Q.is_contiguous()
+        self._staged_host = Q
+        self._check(self.L.cmles_stage_state_host(self.h, C.c_void_p(Q.data_ptr())))
+
+    def commit_staged_state(self):
+        """Take the staged state as the state (the handle's stream waits for the copy)."""
+        self._check(self.L.cmles_commit_staged_state(self.h))
 
     def get_state_host(self, out=None):
         if out is None:

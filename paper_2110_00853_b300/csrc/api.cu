@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "cmles.h"
@@ -145,6 +146,11 @@ struct cmles_t {
   double *hv_tab = nullptr;
   double hv_dt = -1.0;
   HeviTables hv_T{};
+  // double-buffered host uploads: staging buffer, copy stream and events
+  double *Qstage = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t staged_ev = nullptr, compute_ev = nullptr;
+  bool staged = false;
   double time = 0.0;
   bool timing = false;
   std::vector<TimedLaunch> timed;
@@ -880,6 +886,10 @@ cmles_status cmles_destroy(cmles_handle h) {
   for (double *b : h->hv_buf)
     if (b) cudaFree(b);
   if (h->hv_tab) cudaFree(h->hv_tab);
+  if (h->Qstage) cudaFree(h->Qstage);
+  if (h->staged_ev) cudaEventDestroy(h->staged_ev);
+  if (h->compute_ev) cudaEventDestroy(h->compute_ev);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   delete h;
   return CMLES_OK;
 }
@@ -1166,6 +1176,36 @@ cmles_status cmles_set_state_host(cmles_handle h, const double *Q_host) {
   CK(cudaMemcpyAsync(h->Q[h->cur], Q_host, (size_t)h->nodes * 6 * sizeof(double), cudaMemcpyHostToDevice,
                      h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  h->shadow_valid = false;
+  return CMLES_OK;
+}
+
+cmles_status cmles_stage_state_host(cmles_handle h, const double *Q_host) {
+  if (!h || !Q_host) return fail(h, CMLES_ERR_ARG, "cmles_stage_state_host: null argument");
+  if (!h->Qstage) {
+    cmles_status st = dalloc(h, (void **)&h->Qstage, (size_t)h->nodes * 6 * sizeof(double));
+    if (st != CMLES_OK) return st;
+    CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->staged_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->compute_ev, cudaEventDisableTiming));
+  }
+  // the staging buffer may have held the state of work still queued on the
+  // handle's stream: the copy waits for that work, not for later launches
+  CK(cudaEventRecord(h->compute_ev, h->stream));
+  CK(cudaStreamWaitEvent(h->copy_stream, h->compute_ev, 0));
+  CK(cudaMemcpyAsync(h->Qstage, Q_host, (size_t)h->nodes * 6 * sizeof(double), cudaMemcpyHostToDevice,
+                     h->copy_stream));
+  CK(cudaEventRecord(h->staged_ev, h->copy_stream));
+  h->staged = true;
+  return CMLES_OK;
+}
+
+cmles_status cmles_commit_staged_state(cmles_handle h) {
+  if (!h) return CMLES_ERR_ARG;
+  if (!h->staged) return fail(h, CMLES_ERR_STATE, "cmles_commit_staged_state: nothing staged");
+  CK(cudaStreamWaitEvent(h->stream, h->staged_ev, 0));
+  std::swap(h->Q[h->cur], h->Qstage);
+  h->staged = false;
   h->shadow_valid = false;
   return CMLES_OK;
 }
