@@ -32,17 +32,19 @@ STAGES = {"lsrk54": 5, "lsrk144": 14, "ark2_hevi": 3}
 METRIC = "DG node-stage updates/s at 1 B300 and HBM roofline %, FP32+learned vs FP64 plain"
 # algorithmic bytes per node for each kernel launch (compulsory traffic),
 # averaged over the S stages of a step (S = 5 for LSRK(5,4)):
-#   gradient pass: read Q, write F2 (15 words) and aux (2 words)
+#   gradient pass, FP64 path: read Q, write F2 (15 words) and aux (2 words);
+#     FP32 path: read S and the state's h', theta_v' (2 words), write F2
 #   flux/update pass, FP64 path: read Q, F2, aux; write dQ and Q_out; read dQ
 #     except in the first stage (A_1 = 0): ((S - 1) * 41 + 35) words / S
 #   flux/update pass, FP32 path (FP32 shadow S, FP32 register dQ and step
-#     increment D, FP64 state Q64): read S, F2, aux (23 words) in every stage;
+#     increment D, FP64 state Q64): read S, F2, p' and c (23 words) in every
+#     stage; every stage writes the new state's thermodynamic fields (+4);
 #     stage 1 writes dQ, D, S (+18); the middle stages read dQ, D and write dQ,
 #     D, S (+30); the last stage reads dQ, D, reads and writes Q64 and writes S
-#     (+12 + 24 FP32 words for Q64): (41 + (S - 2) * 53 + 65) words / S, 53
+#     (+12 + 24 FP32 words for Q64): (45 + (S - 2) * 57 + 69) words / S, 57
 #     words for S = 5
-#   flux pass of the HEVI stages (FP64): the tendency alone, read Q, F2, aux
-#     and write R: 29 words
+#   flux pass of the HEVI stages: the tendency alone, read Q (S), F2, aux (p',
+#     c) and write R (FP64)
 def alg_bytes(prec, kind, stages=5, integrator="lsrk54"):
     if kind == "grad":
         return (6 + 15 + 2) * (8 if prec == "fp64" else 4)
@@ -50,7 +52,7 @@ def alg_bytes(prec, kind, stages=5, integrator="lsrk54"):
         return 29 * 8 if prec == "fp64" else 23 * 4 + 6 * 8
     if prec == "fp64":
         return ((stages - 1) * 41 + 35) * 8 / stages
-    return (41 + (stages - 2) * 53 + 65) * 4 / stages
+    return (45 + (stages - 2) * 57 + 69) * 4 / stages
 
 
 # name: (precision, closure, numerical flux of F1, integrator); the first
@@ -71,8 +73,7 @@ DTYPE = {"fp32": "f32", "fp64": "f64"}
 # divided by the nodes; the traffic is per node, so it scales to the full box by
 # the node count).  Only kernels whose every launch does the same work: the
 # gradient pass.  Remove an entry when its kernel changes.
-TRAFFIC_B_PER_NODE = {("fp32acc64_mlp", "grad"): 88.07, ("fp32acc64_sl", "grad"): 88.19,
-                      ("fp64_sl", "grad"): 185.0}
+TRAFFIC_B_PER_NODE = {("fp64_sl", "grad"): 185.0}
 
 
 def measured_peaks():

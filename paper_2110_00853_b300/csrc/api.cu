@@ -128,6 +128,7 @@ struct cmles_t {
   // FP32 path: shadow ping-pong, FP32 LSRK register, FP32 F2/aux, tables
   bool fp32 = false;
   float *S32[2] = {nullptr, nullptr};
+  float *TH32[2] = {nullptr, nullptr};  // flat mesh: thermodynamic fields of S32[i]
   int scur = 0;
   bool shadow_valid = false;
   float *dQ32 = nullptr, *D32 = nullptr, *F2_32 = nullptr, *aux32 = nullptr, *lev32 = nullptr, *dH32 = nullptr;
@@ -350,32 +351,43 @@ double level_z(cmles_handle h, int lev) {
   return h->K.z0 + (ez + 0.5 * (h->xi[k] + 1.0)) * h->K.hz;
 }
 
-cmles_status run_stage_pair32(cmles_handle h, const float *Sin, float *Sout, double *Rout, const StageCoef &sc,
-                              bool update) {
+// One gradient pass and one flux pass on the shadow S32[in]; with update the
+// stage's new shadow and its thermodynamic fields go to buffer 1 - in.
+cmles_status run_stage_pair32(cmles_handle h, int in, double *Rout, const StageCoef &sc, bool update) {
+  const float *Sin = h->S32[in];
+  float *Sout = update ? h->S32[1 - in] : nullptr;
   {
     LaunchScope ls(h, 0, 1);
     if (h->curved)
       CK(launch_grad32c(Sin, h->F2_32, h->aux32, h->K, h->stream));
     else
-      CK(launch_grad32(Sin, h->F2_32, h->aux32, h->K, h->stream));
+      CK(launch_grad32(Sin, h->TH32[in], h->F2_32, h->K, h->stream));
   }
   {
     LaunchScope ls(h, 1, 1);
     if (h->curved)
       CK(launch_rhs32c(Sin, h->F2_32, h->aux32, h->dQ32, h->Q[0], Sout, Rout, sc, update, h->K, h->stream));
     else
-      CK(launch_rhs32(Sin, h->F2_32, h->aux32, h->dQ32, h->Q[0], Sout, Rout, sc, update, h->K, h->stream));
+      CK(launch_rhs32(Sin, h->F2_32, h->TH32[in], h->dQ32, h->Q[0], Sout, update ? h->TH32[1 - in] : nullptr, Rout,
+                      sc, update, h->K, h->stream));
   }
+  return CMLES_OK;
+}
+
+// the shadow of the FP64 state Q (with its thermodynamic fields) into buffer i
+cmles_status write_shadow(cmles_handle h, const double *Q, int i) {
+  LaunchScope ls(h, 2, 1);
+  if (h->curved)
+    CK(launch_shadow32c(Q, h->S32[i], h->K, h->N, h->stream));
+  else
+    CK(launch_shadow32(Q, h->S32[i], h->TH32[i], h->K, h->N, h->stream));
   return CMLES_OK;
 }
 
 cmles_status ensure_shadow(cmles_handle h) {
   if (h->fp32 && !h->shadow_valid) {
-    LaunchScope ls(h, 2, 1);
-    if (h->curved)
-      CK(launch_shadow32c(h->Q[0], h->S32[h->scur], h->K, h->N, h->stream));
-    else
-      CK(launch_shadow32(h->Q[0], h->S32[h->scur], h->K, h->N, h->stream));
+    cmles_status st = write_shadow(h, h->Q[0], h->scur);
+    if (st != CMLES_OK) return st;
     h->shadow_valid = true;
   }
   return CMLES_OK;
@@ -712,10 +724,14 @@ static void build_expfilter(cmles_handle h) {
 
 static cmles_status apply_expfilter(cmles_handle h) {
   LaunchScope ls(h, 2, 1);
-  if (h->fp32)
+  if (h->fp32) {
     CK(launch_expfilter(h->Q[0], h->shadow_valid ? h->S32[h->scur] : nullptr, h->expf, h->N, (int)h->E, h->stream));
-  else
+    // the filtered shadow's thermodynamic fields
+    if (h->shadow_valid && !h->curved)
+      CK(launch_shadow32(nullptr, h->S32[h->scur], h->TH32[h->scur], h->K, h->N, h->stream));
+  } else {
     CK(launch_expfilter(h->Q[h->cur], nullptr, h->expf, h->N, (int)h->E, h->stream));
+  }
   return CMLES_OK;
 }
 
@@ -786,7 +802,12 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
     ALLOC(h->dQ32, n32 * 6 * sizeof(float));
     ALLOC(h->D32, n32 * 6 * sizeof(float));
     ALLOC(h->F2_32, n32 * 15 * sizeof(float));
-    ALLOC(h->aux32, n32 * 2 * sizeof(float));
+    if (mesh->warp != 0) {
+      ALLOC(h->aux32, n32 * 2 * sizeof(float));
+    } else {
+      ALLOC(h->TH32[0], n32 * 4 * sizeof(float));
+      ALLOC(h->TH32[1], n32 * 4 * sizeof(float));
+    }
   }
   h->curved = mesh->warp != 0;
   ALLOC(h->lev32, (size_t)nlev * L_NF * sizeof(float));
@@ -880,6 +901,7 @@ cmles_status cmles_destroy(cmles_handle h) {
   void *bufs[] = {h->Q[0],   h->Q[1],    h->dQ,      h->F2,       h->aux,     h->rho_r,    h->p_r,
                   h->qt_r,   h->tau_lev, h->tau_col, h->wq,       h->flags,   h->partials, h->budget_out,
                   h->prof,   h->S32[0],  h->S32[1],  h->dQ32,     h->D32,      h->F2_32,   h->aux32,    h->lev32,
+                  h->TH32[0], h->TH32[1],
                   h->dH32,   h->qref64,  h->mlp_dev, h->geo32,   h->node32,  h->wJn,      h->rvs_tab,  h->exr};
   for (void *b : bufs)
     if (b) cudaFree(b);
@@ -1226,15 +1248,9 @@ cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev
   StageCoef sc = {0.0, 0.0, 0.0, 0, 0.f, 0.f, 0.f, 1};
   if (h->fp32) {
     // shadow of Q_dev into the idle shadow buffer; the handle's state is untouched
-    float *tmp = h->S32[1 - h->scur];
-    {
-      LaunchScope ls(h, 2, 1);
-      if (h->curved)
-        CK(launch_shadow32c(Q_dev, tmp, h->K, h->N, h->stream));
-      else
-        CK(launch_shadow32(Q_dev, tmp, h->K, h->N, h->stream));
-    }
-    return run_stage_pair32(h, tmp, nullptr, RHS_dev, sc, false);
+    cmles_status st = write_shadow(h, Q_dev, 1 - h->scur);
+    if (st != CMLES_OK) return st;
+    return run_stage_pair32(h, 1 - h->scur, RHS_dev, sc, false);
   }
   return run_stage_pair(h, Q_dev, nullptr, RHS_dev, sc, false);
 }
@@ -1288,12 +1304,9 @@ cmles_status ensure_hevi(cmles_handle h) {
 cmles_status hevi_tendency(cmles_handle h, const double *Y, double *R) {
   const StageCoef sc = {0.0, 0.0, 0.0, 0, 0.f, 0.f, 0.f, 1};
   if (!h->fp32) return run_stage_pair(h, Y, nullptr, R, sc, false);
-  float *tmp = h->S32[1 - h->scur];
-  {
-    LaunchScope ls(h, 2, 1);
-    CK(launch_shadow32(Y, tmp, h->K, h->N, h->stream));
-  }
-  return run_stage_pair32(h, tmp, nullptr, R, sc, false);
+  cmles_status st = write_shadow(h, Y, 1 - h->scur);
+  if (st != CMLES_OK) return st;
+  return run_stage_pair32(h, 1 - h->scur, R, sc, false);
 }
 
 // One ARK2 step (Giraldo, Kelly & Constantinescu 2013) with the vertical
@@ -1370,7 +1383,7 @@ cmles_status cmles_step(cmles_handle h, int nsteps) {
                       TA[k] == 0.0};
       cmles_status st;
       if (h->fp32) {
-        st = run_stage_pair32(h, h->S32[h->scur], h->S32[1 - h->scur], nullptr, sc, true);
+        st = run_stage_pair32(h, h->scur, nullptr, sc, true);
         h->scur = 1 - h->scur;
       } else {
         st = run_stage_pair(h, h->Q[h->cur], h->Q[1 - h->cur], h->dQ, sc, true);

@@ -23,6 +23,12 @@
 // Q once per step and rewrites the shadow from it.  On B300, where FP64 runs
 // at 1/64 of the FP32 rate, four FP64 operations per variable and stage took
 // a fifth of the flux pass.  Element traversal: 4 x 4 column tiles.
+// The thermodynamics (temperature, saturation adjustment, pressure) runs once
+// per node and state, in the kernel that writes the state: the flux pass for
+// the state it advances to, the shadow kernel otherwise.  It stores p', the
+// sound speed, h' and theta_v' (TH, four planes per element) for the flux
+// pass and the gradient pass of the next stage, so that neither evaluates it
+// again for its own nodes or its neighbours' face nodes.
 #include "common.cuh"
 #include "launch.h"
 #include "mlp.cuh"
@@ -33,9 +39,9 @@ namespace cmles {
 // CL: 1 Smagorinsky-Lilly, 3 Vreman (both with the Richardson correction),
 // 2 learned closure
 // (tensor-core MLP on the velocity and theta_v gradients and Delta).
-template <int N, bool MOIST, int CL>
-__global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__restrict__ S, float *__restrict__ F2,
-                                                                 float *__restrict__ aux, const KParams P) {
+template <int N, int CL>
+__global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__restrict__ S, const float *__restrict__ TH,
+                                                                 float *__restrict__ F2, const KParams P) {
   constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
   static_assert(Np <= kNP, "one node per thread");
   // the gradient fields (own and neighbour face nodes) share their storage
@@ -70,7 +76,6 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
     __syncwarp();
   }
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
-  int fail = 0;
   for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
     int ex, ey, ez;
     const int e = element_at(P, g, ex, ey, ez);
@@ -80,16 +85,15 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
     if (t < Np) {
 #pragma unroll
       for (int v = 0; v < 6; ++v) sv[v] = S[((size_t)e * 6 + v) * kNP + t];
-      Th32 o;
-      thermo32<MOIST>(P, L, sv, o, fail);
-      G[0] = o.u[0];
-      G[1] = o.u[1];
-      G[2] = o.u[2];
-      G[3] = o.hp;
-      G[4] = o.qp;
-      G[5] = o.thvp;
-      aux[((size_t)e * 2 + 0) * kNP + t] = o.pp;
-      aux[((size_t)e * 2 + 1) * kNP + t] = o.c;
+      // h' and theta_v' come with the state (its producer ran the
+      // thermodynamics); u and q' are formed here exactly as there
+      const float rinv = fdiv(1.0f, L[L_RHO] + sv[0]);
+      G[0] = sv[1] * rinv;
+      G[1] = sv[2] * rinv;
+      G[2] = sv[3] * rinv;
+      G[3] = TH[((size_t)e * 4 + 2) * kNP + t];
+      G[4] = (sv[5] - L[L_QM] * sv[0]) * rinv;
+      G[5] = TH[((size_t)e * 4 + 3) * kNP + t];
 #pragma unroll
       for (int v = 0; v < 6; ++v) sG[v][t] = G[v];
     }
@@ -103,17 +107,18 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
       const int nn = face_node<Nq>(d, a_nb, t1, t2);
       float sp[6];
 #pragma unroll
-      for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
+      for (int v = 0; v < 4; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
+      sp[5] = S[((size_t)nb * 6 + 5) * kNP + nn];
       // the shared face node has the same height, hence the same level values
       const int lev = ez * Nq + (d == 2 ? (f & 1 ? N : 0) : t2);
-      Th32 o;
-      thermo32<MOIST>(P, P.lev32 + (size_t)lev * L_NF, sp, o, fail);
-      sGf[f][0][fn] = o.u[0];
-      sGf[f][1][fn] = o.u[1];
-      sGf[f][2][fn] = o.u[2];
-      sGf[f][3][fn] = o.hp;
-      sGf[f][4][fn] = o.qp;
-      sGf[f][5][fn] = o.thvp;
+      const float *Lf = P.lev32 + (size_t)lev * L_NF;
+      const float rinv = fdiv(1.0f, Lf[L_RHO] + sp[0]);
+      sGf[f][0][fn] = sp[1] * rinv;
+      sGf[f][1][fn] = sp[2] * rinv;
+      sGf[f][2][fn] = sp[3] * rinv;
+      sGf[f][3][fn] = TH[((size_t)nb * 4 + 2) * kNP + nn];
+      sGf[f][4][fn] = (sp[5] - Lf[L_QM] * sp[0]) * rinv;
+      sGf[f][5][fn] = TH[((size_t)nb * 4 + 3) * kNP + nn];
     }
     __syncthreads();
     float gr[6][3];
@@ -220,7 +225,22 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
     if (stalled) tcs.err = 1;
     tc_teardown(tcs, P.flags + 1);
   }
-  if (fail) atomicAdd(P.flags, 1);
+}
+
+// The thermodynamic fields of a shadow node s that the two passes read
+// (planes of TH per element: p', c, h', theta_v'), stored by whoever writes
+// the node's state.
+__device__ __forceinline__ void thermo_store32(const KParams &P, const float *L, const float s[6], float *TH,
+                                               size_t e, int t, int &fail) {
+  Th32 o;
+  if (P.moist)
+    thermo32<true>(P, L, s, o, fail);
+  else
+    thermo32<false>(P, L, s, o, fail);
+  TH[(e * 4 + 0) * kNP + t] = o.pp;
+  TH[(e * 4 + 1) * kNP + t] = o.c;
+  TH[(e * 4 + 2) * kNP + t] = o.hp;
+  TH[(e * 4 + 3) * kNP + t] = o.thvp;
 }
 
 // UPD: 0 right-hand side only; 1 LSRK stage, the step's increment
@@ -229,9 +249,10 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
 // rewritten from it.  FL: numerical flux of F1, 0 Rusanov, 1 HLLC, 2 Roe.
 template <int N, int UPD, int FL>
 __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__restrict__ S, const float *__restrict__ F2,
-                                                  const float *__restrict__ aux, float *__restrict__ dQ,
+                                                  const float *__restrict__ TH, float *__restrict__ dQ,
                                                   double *__restrict__ Q64, float *__restrict__ Sout,
-                                                  double *__restrict__ Rout, const StageCoef sc, const KParams P) {
+                                                  float *__restrict__ THout, double *__restrict__ Rout,
+                                                  const StageCoef sc, const KParams P) {
   constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
   __shared__ float sD[Nq * Nq];
   __shared__ float sF[6][3][kNP];
@@ -243,6 +264,7 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
   const int t = threadIdx.x;
   if (t < Nq * Nq) sD[t] = (float)P.D[t];
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
+  int fail = 0;
   for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
     int ex, ey, ez;
     const int e = element_at(P, g, ex, ey, ez);
@@ -269,7 +291,7 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
         sv[v] = S[((size_t)e * 6 + v) * kNP + t];
         sS[v][t] = sv[v];
       }
-      const float pp = aux[((size_t)e * 2) * kNP + t];
+      const float pp = TH[((size_t)e * 4) * kNP + t];
       const float rho = L[L_RHO] + sv[0];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -298,16 +320,16 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
       float sm[6], sp[6];
 #pragma unroll
       for (int v = 0; v < 6; ++v) sm[v] = sS[v][n];
-      const float pm = aux[((size_t)e * 2) * kNP + n];
-      const float cm = aux[((size_t)e * 2 + 1) * kNP + n];
+      const float pm = TH[((size_t)e * 4) * kNP + n];
+      const float cm = TH[((size_t)e * 4 + 1) * kNP + n];
       const int nb = sNb[f];
       float pp, cp, f2s[5];
       if (nb >= 0) {
         const int nn = face_node<Nq>(d, N - a, t1, t2);
 #pragma unroll
         for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
-        pp = aux[((size_t)nb * 2) * kNP + nn];
-        cp = aux[((size_t)nb * 2 + 1) * kNP + nn];
+        pp = TH[((size_t)nb * 4) * kNP + nn];
+        cp = TH[((size_t)nb * 4 + 1) * kNP + nn];
         const float *g2m = F2 + ((size_t)e * 15 + d * 5) * kNP + n;
         const float *g2p = F2 + ((size_t)nb * 15 + d * 5) * kNP + nn;
 #pragma unroll
@@ -428,6 +450,7 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
       R[2] += Sr[1];
       R[3] += Sr[2];
       const double *qr = P.qref64 + (size_t)(ez * Nq + k) * 4;
+      float sn[6];
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
         const size_t i64 = ((size_t)e * 6 + v) * Np + t;
@@ -438,105 +461,113 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
           if (UPD == 1) {
             dQ[i32] = dq;
             P.D32[i32] = D0[v] + Bdq;
-            Sout[i32] = sS[v][t] + Bdq;
+            sn[v] = sS[v][t] + Bdq;
           } else {
             // the register is not read again before the next step's first stage
             const double qn = q0[v] + (double)(D0[v] + Bdq);
             Q64[i64] = qn;
             const double ref = v == 0 ? qr[0] : (v == 4 ? qr[1] : (v == 5 ? qr[2] : 0.0));
-            Sout[i32] = (float)(qn - ref);
+            sn[v] = (float)(qn - ref);
           }
+          Sout[i32] = sn[v];
         } else {
           Rout[i64] = (double)R[v];
         }
       }
+      // the thermodynamics of the new state, for the next stage's two passes
+      if (UPD) thermo_store32(P, L, sn, THout, e, t, fail);
     }
     __syncthreads();
   }
+  if (fail) atomicAdd(P.flags, 1);
 }
 
-// Shadow of an FP64 state: s = (float)(Q - Q_ref(level)), subtraction in FP64.
-__global__ void k_shadow32(const double *__restrict__ Q64, float *__restrict__ S, const KParams P, int Np, int Nq) {
+// Shadow of an FP64 state: s = (float)(Q - Q_ref(level)), subtraction in
+// FP64, with its thermodynamic fields.  Q64 null: the shadow S is given and
+// only its thermodynamic fields are written.
+__global__ void k_shadow32(const double *__restrict__ Q64, float *__restrict__ S, float *__restrict__ TH,
+                           const KParams P, int Np, int Nq) {
   const long long n = (long long)P.E * Np;
+  int fail = 0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     const long long e = q / Np;
     const int node = (int)(q - e * Np);
     const int ez = (int)(e / ((long long)P.nex * P.ney));
     const int k = node / (Nq * Nq);
     const double *qr = P.qref64 + (size_t)(ez * Nq + k) * 4;
+    float s[6];
 #pragma unroll
     for (int v = 0; v < 6; ++v) {
-      const double ref = v == 0 ? qr[0] : (v == 4 ? qr[1] : (v == 5 ? qr[2] : 0.0));
-      S[(e * 6 + v) * kNP + node] = (float)(Q64[(e * 6 + v) * Np + node] - ref);
+      if (Q64) {
+        const double ref = v == 0 ? qr[0] : (v == 4 ? qr[1] : (v == 5 ? qr[2] : 0.0));
+        s[v] = (float)(Q64[(e * 6 + v) * Np + node] - ref);
+        S[(e * 6 + v) * kNP + node] = s[v];
+      } else {
+        s[v] = S[(e * 6 + v) * kNP + node];
+      }
     }
+    thermo_store32(P, P.lev32 + (size_t)(ez * Nq + k) * L_NF, s, TH, (size_t)e, node, fail);
   }
+  if (fail) atomicAdd(P.flags, 1);
 }
 
-cudaError_t launch_shadow32(const double *Q64, float *S, const KParams &P, int N, cudaStream_t s) {
+cudaError_t launch_shadow32(const double *Q64, float *S, float *TH, const KParams &P, int N, cudaStream_t s) {
   const int Nq = N + 1, Np = Nq * Nq * Nq;
   long long nodes = (long long)P.E * Np;
   int blocks = (int)((nodes + 255) / 256);
   if (blocks > 148 * 32) blocks = 148 * 32;
-  k_shadow32<<<blocks, 256, 0, s>>>(Q64, S, P, Np, Nq);
+  k_shadow32<<<blocks, 256, 0, s>>>(Q64, S, TH, P, Np, Nq);
   return cudaGetLastError();
 }
 
-template <bool MOIST, int CL>
-static void grad32_instance(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s) {
+template <int CL>
+static void grad32_instance(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
   static int grid = 0;
   if (!grid)
-    grid = CL == 2 ? grid_for_tc((const void *)k_grad32<4, MOIST, CL>, 1 << 30, kTcCols)
-                   : grid_for((const void *)k_grad32<4, MOIST, CL>, 1 << 30, 0);
-  k_grad32<4, MOIST, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, P);
+    grid = CL == 2 ? grid_for_tc((const void *)k_grad32<4, CL>, 1 << 30, kTcCols)
+                   : grid_for((const void *)k_grad32<4, CL>, 1 << 30, 0);
+  k_grad32<4, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, TH, F2, P);
 }
 
-cudaError_t launch_grad32(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s) {
-  if (P.closure == 2) {
-    if (P.moist)
-      grad32_instance<true, 2>(S, F2, aux, P, s);
-    else
-      grad32_instance<false, 2>(S, F2, aux, P, s);
-  } else if (P.closure == 3) {
-    if (P.moist)
-      grad32_instance<true, 3>(S, F2, aux, P, s);
-    else
-      grad32_instance<false, 3>(S, F2, aux, P, s);
-  } else {
-    if (P.moist)
-      grad32_instance<true, 1>(S, F2, aux, P, s);
-    else
-      grad32_instance<false, 1>(S, F2, aux, P, s);
-  }
+cudaError_t launch_grad32(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
+  if (P.closure == 2)
+    grad32_instance<2>(S, TH, F2, P, s);
+  else if (P.closure == 3)
+    grad32_instance<3>(S, TH, F2, P, s);
+  else
+    grad32_instance<1>(S, TH, F2, P, s);
   return cudaGetLastError();
 }
 
 template <int UPD, int FL>
-static void k_rhs32_instance(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
-                           double *Rout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
+static void k_rhs32_instance(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
+                             float *THout, double *Rout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
   static int grid = 0;
   if (!grid) grid = grid_for((const void *)k_rhs32<4, UPD, FL>, 1 << 30, 0);
-  k_rhs32<4, UPD, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+  k_rhs32<4, UPD, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P);
 }
 
 template <int FL>
-static void k_rhs32_dispatch(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
-                             double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+static void k_rhs32_dispatch(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
+                             float *THout, double *Rout, const StageCoef &sc, bool update, const KParams &P,
+                             cudaStream_t s) {
   if (!update)
-    k_rhs32_instance<0, FL>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+    k_rhs32_instance<0, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
   else if (sc.last)
-    k_rhs32_instance<2, FL>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+    k_rhs32_instance<2, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
   else
-    k_rhs32_instance<1, FL>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+    k_rhs32_instance<1, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
 }
 
-cudaError_t launch_rhs32(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
-                         double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+cudaError_t launch_rhs32(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
+                         float *THout, double *Rout, const StageCoef &sc, bool update, const KParams &P,
+                         cudaStream_t s) {
   if (P.flux == 2)
-    k_rhs32_dispatch<2>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
+    k_rhs32_dispatch<2>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
   else if (P.flux == 1)
-    k_rhs32_dispatch<1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
+    k_rhs32_dispatch<1>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
   else
-    k_rhs32_dispatch<0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
+    k_rhs32_dispatch<0>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
   return cudaGetLastError();
 }
 

@@ -17,11 +17,16 @@ cudaError_t launch_grad64(const double *Q, double *F2, double *aux, const KParam
 cudaError_t launch_rhs64(const double *Q, const double *F2, const double *aux, double *dQ, double *Qout,
                          const StageCoef &sc, bool update, const KParams &P, cudaStream_t s);
 
-// FP32 path with FP64 accumulation (dg_fp32.cu); FP32 arrays padded to 128 nodes
-cudaError_t launch_shadow32(const double *Q64, float *S, const KParams &P, int N, cudaStream_t s);
-cudaError_t launch_grad32(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s);
-cudaError_t launch_rhs32(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
-                         double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s);
+// FP32 path with FP64 accumulation (dg_fp32.cu); FP32 arrays padded to 128
+// nodes.  TH: the state's thermodynamic fields (p', c, h', theta_v'; four
+// planes per element), written with the state (shadow kernel, or the flux
+// pass for the state it advances to) and read by the next two passes.
+// launch_shadow32 with Q64 null writes only TH for the given shadow S.
+cudaError_t launch_shadow32(const double *Q64, float *S, float *TH, const KParams &P, int N, cudaStream_t s);
+cudaError_t launch_grad32(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s);
+cudaError_t launch_rhs32(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
+                         float *THout, double *Rout, const StageCoef &sc, bool update, const KParams &P,
+                         cudaStream_t s);
 
 // FP32 path on curvilinear (warped) meshes (dg_curved32.cu)
 enum { kCurvedNF = 24 };
