@@ -73,7 +73,8 @@ DTYPE = {"fp32": "f32", "fp64": "f64"}
 # divided by the nodes; the traffic is per node, so it scales to the full box by
 # the node count).  Only kernels whose every launch does the same work: the
 # gradient pass.  Remove an entry when its kernel changes.
-TRAFFIC_B_PER_NODE = {("fp64_sl", "grad"): 185.0}
+TRAFFIC_B_PER_NODE = {("fp32acc64_mlp", "grad"): 85.20, ("fp32acc64_sl", "grad"): 83.38,
+                      ("fp64_sl", "grad"): 185.0}
 
 
 def measured_peaks():
