@@ -128,10 +128,10 @@ struct cmles_t {
   // FP32 path: shadow ping-pong, FP32 LSRK register, FP32 F2/aux, tables
   bool fp32 = false;
   float *S32[2] = {nullptr, nullptr};
-  float *TH32[2] = {nullptr, nullptr};  // flat mesh: thermodynamic fields of S32[i]
+  float *TH32[2] = {nullptr, nullptr};  // thermodynamic fields of S32[i]
   int scur = 0;
   bool shadow_valid = false;
-  float *dQ32 = nullptr, *D32 = nullptr, *F2_32 = nullptr, *aux32 = nullptr, *lev32 = nullptr, *dH32 = nullptr;
+  float *dQ32 = nullptr, *D32 = nullptr, *F2_32 = nullptr, *lev32 = nullptr, *dH32 = nullptr;
   double *qref64 = nullptr;
   double *rho_r = nullptr, *p_r = nullptr, *qt_r = nullptr, *tau_lev = nullptr, *tau_col = nullptr;
   double *wq = nullptr, *partials = nullptr, *budget_out = nullptr, *prof = nullptr;
@@ -359,17 +359,17 @@ cmles_status run_stage_pair32(cmles_handle h, int in, double *Rout, const StageC
   {
     LaunchScope ls(h, 0, 1);
     if (h->curved)
-      CK(launch_grad32c(Sin, h->F2_32, h->aux32, h->K, h->stream));
+      CK(launch_grad32c(Sin, h->TH32[in], h->F2_32, h->K, h->stream));
     else
       CK(launch_grad32(Sin, h->TH32[in], h->F2_32, h->K, h->stream));
   }
   {
     LaunchScope ls(h, 1, 1);
+    float *THout = update ? h->TH32[1 - in] : nullptr;
     if (h->curved)
-      CK(launch_rhs32c(Sin, h->F2_32, h->aux32, h->dQ32, h->Q[0], Sout, Rout, sc, update, h->K, h->stream));
+      CK(launch_rhs32c(Sin, h->F2_32, h->TH32[in], h->dQ32, h->Q[0], Sout, THout, Rout, sc, update, h->K, h->stream));
     else
-      CK(launch_rhs32(Sin, h->F2_32, h->TH32[in], h->dQ32, h->Q[0], Sout, update ? h->TH32[1 - in] : nullptr, Rout,
-                      sc, update, h->K, h->stream));
+      CK(launch_rhs32(Sin, h->F2_32, h->TH32[in], h->dQ32, h->Q[0], Sout, THout, Rout, sc, update, h->K, h->stream));
   }
   return CMLES_OK;
 }
@@ -378,7 +378,7 @@ cmles_status run_stage_pair32(cmles_handle h, int in, double *Rout, const StageC
 cmles_status write_shadow(cmles_handle h, const double *Q, int i) {
   LaunchScope ls(h, 2, 1);
   if (h->curved)
-    CK(launch_shadow32c(Q, h->S32[i], h->K, h->N, h->stream));
+    CK(launch_shadow32c(Q, h->S32[i], h->TH32[i], h->K, h->N, h->stream));
   else
     CK(launch_shadow32(Q, h->S32[i], h->TH32[i], h->K, h->N, h->stream));
   return CMLES_OK;
@@ -727,8 +727,12 @@ static cmles_status apply_expfilter(cmles_handle h) {
   if (h->fp32) {
     CK(launch_expfilter(h->Q[0], h->shadow_valid ? h->S32[h->scur] : nullptr, h->expf, h->N, (int)h->E, h->stream));
     // the filtered shadow's thermodynamic fields
-    if (h->shadow_valid && !h->curved)
-      CK(launch_shadow32(nullptr, h->S32[h->scur], h->TH32[h->scur], h->K, h->N, h->stream));
+    if (h->shadow_valid) {
+      if (h->curved)
+        CK(launch_shadow32c(nullptr, h->S32[h->scur], h->TH32[h->scur], h->K, h->N, h->stream));
+      else
+        CK(launch_shadow32(nullptr, h->S32[h->scur], h->TH32[h->scur], h->K, h->N, h->stream));
+    }
   } else {
     CK(launch_expfilter(h->Q[h->cur], nullptr, h->expf, h->N, (int)h->E, h->stream));
   }
@@ -802,12 +806,8 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
     ALLOC(h->dQ32, n32 * 6 * sizeof(float));
     ALLOC(h->D32, n32 * 6 * sizeof(float));
     ALLOC(h->F2_32, n32 * 15 * sizeof(float));
-    if (mesh->warp != 0) {
-      ALLOC(h->aux32, n32 * 2 * sizeof(float));
-    } else {
-      ALLOC(h->TH32[0], n32 * 4 * sizeof(float));
-      ALLOC(h->TH32[1], n32 * 4 * sizeof(float));
-    }
+    ALLOC(h->TH32[0], n32 * 4 * sizeof(float));
+    ALLOC(h->TH32[1], n32 * 4 * sizeof(float));
   }
   h->curved = mesh->warp != 0;
   ALLOC(h->lev32, (size_t)nlev * L_NF * sizeof(float));
@@ -898,11 +898,11 @@ cmles_status cmles_destroy(cmles_handle h) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
   }
-  void *bufs[] = {h->Q[0],   h->Q[1],    h->dQ,      h->F2,       h->aux,     h->rho_r,    h->p_r,
-                  h->qt_r,   h->tau_lev, h->tau_col, h->wq,       h->flags,   h->partials, h->budget_out,
-                  h->prof,   h->S32[0],  h->S32[1],  h->dQ32,     h->D32,      h->F2_32,   h->aux32,    h->lev32,
-                  h->TH32[0], h->TH32[1],
-                  h->dH32,   h->qref64,  h->mlp_dev, h->geo32,   h->node32,  h->wJn,      h->rvs_tab,  h->exr};
+  void *bufs[] = {h->Q[0],   h->Q[1],    h->dQ,      h->F2,      h->aux,     h->rho_r,    h->p_r,
+                  h->qt_r,   h->tau_lev, h->tau_col, h->wq,      h->flags,   h->partials, h->budget_out,
+                  h->prof,   h->S32[0],  h->S32[1],  h->dQ32,    h->D32,     h->F2_32,    h->lev32,
+                  h->TH32[0], h->TH32[1], h->dH32,   h->qref64,  h->mlp_dev, h->geo32,    h->node32,
+                  h->wJn,    h->rvs_tab, h->exr};
   for (void *b : bufs)
     if (b) cudaFree(b);
   for (double *b : h->hv_buf)

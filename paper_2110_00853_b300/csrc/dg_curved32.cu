@@ -11,7 +11,9 @@
 // Reference values vary from node to node (z depends on x over the terrain),
 // so the deviation-form tables are per node, and the reference parts of the
 // h_tot, q_t and theta_v gradients are full 3-vectors.  The energy flux is
-// formed as (H_r + H') u in FP32.
+// formed as (H_r + H') u in FP32.  As on flat meshes, the thermodynamics runs
+// once per node and state, in the kernel that writes the state, which stores
+// p', c, h' and theta_v' (TH) for the next two passes.
 #include "common.cuh"
 #include "launch.h"
 #include "mlp.cuh"
@@ -30,9 +32,10 @@ __device__ __forceinline__ void load_node_table(const float *__restrict__ tab, s
   for (int f = 0; f < L_NF; ++f) L[f] = p[f * kNP];
 }
 
-template <int N, bool MOIST, int CL>
-__global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *__restrict__ S, float *__restrict__ F2,
-                                                                  float *__restrict__ aux, const KParams P) {
+template <int N, int CL>
+__global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *__restrict__ S,
+                                                                  const float *__restrict__ TH,
+                                                                  float *__restrict__ F2, const KParams P) {
   constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
   // the gradient fields share their storage with the closure network's A
   // operand (written only after every thread has finished its gradient)
@@ -64,7 +67,6 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
     __syncwarp();
   }
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
-  int fail = 0;
   for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
     int ex, ey, ez;
     const int e = element_at(P, g, ex, ey, ez);
@@ -74,16 +76,14 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
       load_node_table(P.node32, e, t, L);
 #pragma unroll
       for (int v = 0; v < 6; ++v) sv[v] = S[((size_t)e * 6 + v) * kNP + t];
-      Th32 o;
-      thermo32<MOIST>(P, L, sv, o, fail);
-      G[0] = o.u[0];
-      G[1] = o.u[1];
-      G[2] = o.u[2];
-      G[3] = o.hp;
-      G[4] = o.qp;
-      G[5] = o.thvp;
-      aux[((size_t)e * 2 + 0) * kNP + t] = o.pp;
-      aux[((size_t)e * 2 + 1) * kNP + t] = o.c;
+      // h' and theta_v' come with the state; u and q' formed as there
+      const float rinv = fdiv(1.0f, L[L_RHO] + sv[0]);
+      G[0] = sv[1] * rinv;
+      G[1] = sv[2] * rinv;
+      G[2] = sv[3] * rinv;
+      G[3] = TH[((size_t)e * 4 + 2) * kNP + t];
+      G[4] = (sv[5] - L[L_QM] * sv[0]) * rinv;
+      G[5] = TH[((size_t)e * 4 + 3) * kNP + t];
 #pragma unroll
       for (int v = 0; v < 6; ++v) sG[v][t] = G[v];
     }
@@ -94,18 +94,18 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
       if (nb < 0) continue;
       const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
       const int nn = face_node<Nq>(d, (f & 1) ? 0 : N, t1, t2);
-      float sp[6], Ln[L_NF];
-      load_node_table(P.node32, nb, nn, Ln);
+      const float *tn = P.node32 + (size_t)nb * C_NF * kNP + nn;
+      float sp[6];
 #pragma unroll
-      for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
-      Th32 o;
-      thermo32<MOIST>(P, Ln, sp, o, fail);
-      sGf[f][0][fn] = o.u[0];
-      sGf[f][1][fn] = o.u[1];
-      sGf[f][2][fn] = o.u[2];
-      sGf[f][3][fn] = o.hp;
-      sGf[f][4][fn] = o.qp;
-      sGf[f][5][fn] = o.thvp;
+      for (int v = 0; v < 4; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
+      sp[5] = S[((size_t)nb * 6 + 5) * kNP + nn];
+      const float rinv = fdiv(1.0f, tn[L_RHO * kNP] + sp[0]);
+      sGf[f][0][fn] = sp[1] * rinv;
+      sGf[f][1][fn] = sp[2] * rinv;
+      sGf[f][2][fn] = sp[3] * rinv;
+      sGf[f][3][fn] = TH[((size_t)nb * 4 + 2) * kNP + nn];
+      sGf[f][4][fn] = (sp[5] - tn[L_QM * kNP] * sp[0]) * rinv;
+      sGf[f][5][fn] = TH[((size_t)nb * 4 + 3) * kNP + nn];
     }
     __syncthreads();
     float gr[6][3];
@@ -233,7 +233,6 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
     if (stalled) tcs.err = 1;
     tc_teardown(tcs, P.flags + 1);
   }
-  if (fail) atomicAdd(P.flags, 1);
 }
 
 // n.F1 for a general unit normal: [rho u.n, rho u_j (u.n) + p' n_j,
@@ -255,9 +254,10 @@ __device__ __forceinline__ void flux1_normal32(const float s[6], float rho_r, fl
 // 2 last stage of the step (FP64 accumulation).  FL: 0 Rusanov, 1 HLLC, 2 Roe.
 template <int N, int UPD, int FL>
 __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, const float *__restrict__ F2,
-                                                   const float *__restrict__ aux, float *__restrict__ dQ,
+                                                   const float *__restrict__ TH, float *__restrict__ dQ,
                                                    double *__restrict__ Q64, float *__restrict__ Sout,
-                                                   double *__restrict__ Rout, const StageCoef sc, const KParams P) {
+                                                   float *__restrict__ THout, double *__restrict__ Rout,
+                                                   const StageCoef sc, const KParams P) {
   constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
   __shared__ float sD[Nq * Nq];
   __shared__ float sF[6][3][kNP];  // contravariant fluxes J a^r . F
@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
   const int t = threadIdx.x;
   if (t < Nq * Nq) sD[t] = (float)P.D[t];
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
+  int fail = 0;
   for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
     int ex, ey, ez;
     const int e = element_at(P, g, ex, ey, ez);
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
         sv[v] = S[((size_t)e * 6 + v) * kNP + t];
         sS[v][t] = sv[v];
       }
-      const float pp = aux[((size_t)e * 2) * kNP + t];
+      const float pp = TH[((size_t)e * 4) * kNP + t];
       const float rho = tab[L_RHO * kNP] + sv[0];
       const float u[3] = {sv[1] / rho, sv[2] / rho, sv[3] / rho};
       const float H = tab[L_H * kNP] + (sv[4] + pp);
@@ -322,16 +323,16 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
       float sm[6], sp[6];
 #pragma unroll
       for (int v = 0; v < 6; ++v) sm[v] = sS[v][n];
-      const float pm = aux[((size_t)e * 2) * kNP + n];
-      const float cm = aux[((size_t)e * 2 + 1) * kNP + n];
+      const float pm = TH[((size_t)e * 4) * kNP + n];
+      const float cm = TH[((size_t)e * 4 + 1) * kNP + n];
       const int nb = sNb[f];
       float pp, cp, f2s[5];
       if (nb >= 0) {
         const int nn = face_node<Nq>(d, N - a, t1, t2);
 #pragma unroll
         for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
-        pp = aux[((size_t)nb * 2) * kNP + nn];
-        cp = aux[((size_t)nb * 2 + 1) * kNP + nn];
+        pp = TH[((size_t)nb * 4) * kNP + nn];
+        cp = TH[((size_t)nb * 4 + 1) * kNP + nn];
 #pragma unroll
         for (int c5 = 0; c5 < 5; ++c5) {
           float fm = 0.f, fq = 0.f;
@@ -435,6 +436,7 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
       R[2] += Sr[1];
       R[3] += Sr[2];
       const double *qr = P.qref64 + (size_t)e * 3 * Np + t;
+      float sn[6];
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
         const size_t i64 = ((size_t)e * 6 + v) * Np + t;
@@ -446,97 +448,112 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
           if (UPD == 1) {
             dQ[i32] = dq;
             P.D32[i32] = D0 + Bdq;
-            Sout[i32] = sS[v][t] + Bdq;
+            sn[v] = sS[v][t] + Bdq;
           } else {
             const double qn = Q64[i64] + (double)(D0 + Bdq);
             Q64[i64] = qn;
             const double ref = v == 0 ? qr[0] : (v == 4 ? qr[Np] : (v == 5 ? qr[2 * Np] : 0.0));
-            Sout[i32] = (float)(qn - ref);
+            sn[v] = (float)(qn - ref);
           }
+          Sout[i32] = sn[v];
         } else {
           Rout[i64] = (double)R[v];
         }
       }
+      // the thermodynamics of the new state, for the next stage's two passes
+      if (UPD) {
+        float L[L_NF];
+        load_node_table(P.node32, e, t, L);
+        thermo_store32(P, L, sn, THout, e, t, fail);
+      }
     }
     __syncthreads();
   }
+  if (fail) atomicAdd(P.flags, 1);
 }
 
-// Shadow of an FP64 state on a curvilinear mesh: per-node reference offsets.
-__global__ void k_shadow32c(const double *__restrict__ Q64, float *__restrict__ S, const KParams P, int Np) {
+// Shadow of an FP64 state on a curvilinear mesh (per-node reference offsets)
+// with its thermodynamic fields; Q64 null: only the fields of the given S.
+__global__ void k_shadow32c(const double *__restrict__ Q64, float *__restrict__ S, float *__restrict__ TH,
+                            const KParams P, int Np) {
   const long long n = (long long)P.E * Np;
+  int fail = 0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     const long long e = q / Np;
     const int node = (int)(q - e * Np);
     const double *qr = P.qref64 + (size_t)e * 3 * Np + node;
+    float s[6], L[L_NF];
 #pragma unroll
     for (int v = 0; v < 6; ++v) {
-      const double ref = v == 0 ? qr[0] : (v == 4 ? qr[Np] : (v == 5 ? qr[2 * Np] : 0.0));
-      S[(e * 6 + v) * kNP + node] = (float)(Q64[(e * 6 + v) * Np + node] - ref);
+      if (Q64) {
+        const double ref = v == 0 ? qr[0] : (v == 4 ? qr[Np] : (v == 5 ? qr[2 * Np] : 0.0));
+        s[v] = (float)(Q64[(e * 6 + v) * Np + node] - ref);
+        S[(e * 6 + v) * kNP + node] = s[v];
+      } else {
+        s[v] = S[(e * 6 + v) * kNP + node];
+      }
     }
+    load_node_table(P.node32, (size_t)e, node, L);
+    thermo_store32(P, L, s, TH, (size_t)e, node, fail);
   }
+  if (fail) atomicAdd(P.flags, 1);
 }
 
-cudaError_t launch_shadow32c(const double *Q64, float *S, const KParams &P, int N, cudaStream_t s) {
+cudaError_t launch_shadow32c(const double *Q64, float *S, float *TH, const KParams &P, int N, cudaStream_t s) {
   const int Nq = N + 1, Np = Nq * Nq * Nq;
   long long nodes = (long long)P.E * Np;
   int blocks = (int)((nodes + 255) / 256);
   if (blocks > 148 * 32) blocks = 148 * 32;
-  k_shadow32c<<<blocks, 256, 0, s>>>(Q64, S, P, Np);
+  k_shadow32c<<<blocks, 256, 0, s>>>(Q64, S, TH, P, Np);
   return cudaGetLastError();
 }
 
-template <bool MOIST, int CL>
-static void grad32c_instance(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s) {
+template <int CL>
+static void grad32c_instance(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
   static int grid = 0;
   if (!grid)
-    grid = CL == 2 ? grid_for_tc((const void *)k_grad32c<4, MOIST, CL>, 1 << 30, kTcCols)
-                   : grid_for((const void *)k_grad32c<4, MOIST, CL>, 1 << 30, 0);
-  k_grad32c<4, MOIST, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, P);
+    grid = CL == 2 ? grid_for_tc((const void *)k_grad32c<4, CL>, 1 << 30, kTcCols)
+                   : grid_for((const void *)k_grad32c<4, CL>, 1 << 30, 0);
+  k_grad32c<4, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, TH, F2, P);
 }
 
-cudaError_t launch_grad32c(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s) {
-  if (P.closure == 2) {
-    if (P.moist)
-      grad32c_instance<true, 2>(S, F2, aux, P, s);
-    else
-      grad32c_instance<false, 2>(S, F2, aux, P, s);
-  } else {
-    if (P.moist)
-      grad32c_instance<true, 1>(S, F2, aux, P, s);
-    else
-      grad32c_instance<false, 1>(S, F2, aux, P, s);
-  }
+cudaError_t launch_grad32c(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
+  if (P.closure == 2)
+    grad32c_instance<2>(S, TH, F2, P, s);
+  else
+    grad32c_instance<1>(S, TH, F2, P, s);
   return cudaGetLastError();
 }
 
 template <int UPD, int FL>
-static void k_rhs32c_instance(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
-                           double *Rout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
+static void k_rhs32c_instance(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
+                              float *THout, double *Rout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
   static int grid = 0;
   if (!grid) grid = grid_for((const void *)k_rhs32c<4, UPD, FL>, 1 << 30, 0);
-  k_rhs32c<4, UPD, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P);
+  k_rhs32c<4, UPD, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P);
 }
 
 template <int FL>
-static void k_rhs32c_dispatch(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
-                              double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+static void k_rhs32c_dispatch(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
+                              float *THout, double *Rout, const StageCoef &sc, bool update, const KParams &P,
+                              cudaStream_t s) {
   if (!update)
-    k_rhs32c_instance<0, FL>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+    k_rhs32c_instance<0, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
   else if (sc.last)
-    k_rhs32c_instance<2, FL>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+    k_rhs32c_instance<2, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
   else
-    k_rhs32c_instance<1, FL>(S, F2, aux, dQ, Q64, Sout, Rout, sc, P, s);
+    k_rhs32c_instance<1, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
 }
 
-cudaError_t launch_rhs32c(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
-                          double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+cudaError_t launch_rhs32c(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
+                          float *THout, double *Rout, const StageCoef &sc, bool update, const KParams &P,
+                          cudaStream_t s) {
   if (P.flux == 2)
-    k_rhs32c_dispatch<2>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
+    k_rhs32c_dispatch<2>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
   else if (P.flux == 1)
-    k_rhs32c_dispatch<1>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
+    k_rhs32c_dispatch<1>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
   else
-    k_rhs32c_dispatch<0>(S, F2, aux, dQ, Q64, Sout, Rout, sc, update, P, s);
+    k_rhs32c_dispatch<0>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
   return cudaGetLastError();
 }
 

@@ -227,22 +227,6 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
   }
 }
 
-// The thermodynamic fields of a shadow node s that the two passes read
-// (planes of TH per element: p', c, h', theta_v'), stored by whoever writes
-// the node's state.
-__device__ __forceinline__ void thermo_store32(const KParams &P, const float *L, const float s[6], float *TH,
-                                               size_t e, int t, int &fail) {
-  Th32 o;
-  if (P.moist)
-    thermo32<true>(P, L, s, o, fail);
-  else
-    thermo32<false>(P, L, s, o, fail);
-  TH[(e * 4 + 0) * kNP + t] = o.pp;
-  TH[(e * 4 + 1) * kNP + t] = o.c;
-  TH[(e * 4 + 2) * kNP + t] = o.hp;
-  TH[(e * 4 + 3) * kNP + t] = o.thvp;
-}
-
 // UPD: 0 right-hand side only; 1 LSRK stage, the step's increment
 // D = sum_s B_s dQ_s carried in FP32 and the shadow advanced by B_s dQ_s;
 // 2 last stage of the step, Q = Q_step_start + D added in FP64 and the shadow

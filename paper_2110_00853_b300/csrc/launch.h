@@ -21,7 +21,7 @@ cudaError_t launch_rhs64(const double *Q, const double *F2, const double *aux, d
 // nodes.  TH: the state's thermodynamic fields (p', c, h', theta_v'; four
 // planes per element), written with the state (shadow kernel, or the flux
 // pass for the state it advances to) and read by the next two passes.
-// launch_shadow32 with Q64 null writes only TH for the given shadow S.
+// launch_shadow32[c] with Q64 null writes only TH for the given shadow S.
 cudaError_t launch_shadow32(const double *Q64, float *S, float *TH, const KParams &P, int N, cudaStream_t s);
 cudaError_t launch_grad32(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s);
 cudaError_t launch_rhs32(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
@@ -30,10 +30,11 @@ cudaError_t launch_rhs32(const float *S, const float *F2, const float *TH, float
 
 // FP32 path on curvilinear (warped) meshes (dg_curved32.cu)
 enum { kCurvedNF = 24 };
-cudaError_t launch_shadow32c(const double *Q64, float *S, const KParams &P, int N, cudaStream_t s);
-cudaError_t launch_grad32c(const float *S, float *F2, float *aux, const KParams &P, cudaStream_t s);
-cudaError_t launch_rhs32c(const float *S, const float *F2, const float *aux, float *dQ, double *Q64, float *Sout,
-                          double *Rout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s);
+cudaError_t launch_shadow32c(const double *Q64, float *S, float *TH, const KParams &P, int N, cudaStream_t s);
+cudaError_t launch_grad32c(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s);
+cudaError_t launch_rhs32c(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
+                          float *THout, double *Rout, const StageCoef &sc, bool update, const KParams &P,
+                          cudaStream_t s);
 
 // Exponential modal filter (expfilter.cu): F is the 1D filter matrix
 // (row-major (N+1)^2), mask selects momentum components (bits 1..3); S32,

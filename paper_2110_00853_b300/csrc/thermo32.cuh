@@ -137,4 +137,20 @@ __device__ __forceinline__ void flux1_dev32(const float s[6], float rho_r, float
   f[5] = (rhoq_r + s[5]) * ud;
 }
 
+// The thermodynamic fields of a shadow node s that the two passes read
+// (planes of TH per element: p', c, h', theta_v'), stored by whoever writes
+// the node's state.
+__device__ __forceinline__ void thermo_store32(const KParams &P, const float *L, const float s[6], float *TH,
+                                               size_t e, int t, int &fail) {
+  Th32 o;
+  if (P.moist)
+    thermo32<true>(P, L, s, o, fail);
+  else
+    thermo32<false>(P, L, s, o, fail);
+  TH[(e * 4 + 0) * kNP + t] = o.pp;
+  TH[(e * 4 + 1) * kNP + t] = o.c;
+  TH[(e * 4 + 2) * kNP + t] = o.hp;
+  TH[(e * 4 + 3) * kNP + t] = o.thvp;
+}
+
 }  // namespace cmles

@@ -65,6 +65,27 @@ def test_newton_cap_failures_are_counted(orc, precision):
     assert d["satadj_failures"] == 0
 
 
+def test_newton_cap_failures_are_counted_in_the_flux_pass(orc):
+    """On flat meshes the FP32 path runs the thermodynamics in the kernel that
+    writes a state: the shadow kernel, and the flux pass for the state each
+    stage advances to.  With the Newton cap at one iteration both count: a
+    step (one shadow write, then five flux passes) reports more failures than
+    a tendency call (one shadow write alone)."""
+    from paper_2110_00853_b300 import cmles
+    m = I.sub_mesh("c2", 5, 3, 16)
+    ph = dict(I.physics("c2"), satadj_max_iter=1)
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case("c2"))
+    G = cmles.Solver(m, ph, precision="fp32")
+    G.set_reference(_levels(rr, m), _levels(pr, m), _levels(Q[:, 5] / Q[:, 0], m))
+    G.tendency(torch.from_numpy(Q).cuda())
+    n_shadow = G.diagnostics(raise_on_error=False)["satadj_failures"]
+    assert n_shadow > 0
+    G.set_state(torch.from_numpy(Q).cuda())
+    G.step(1)
+    d = G.diagnostics(raise_on_error=False)
+    assert d["status"] == ERR_SATADJ and d["satadj_failures"] > n_shadow, (d["satadj_failures"], n_shadow)
+
+
 def test_tensor_core_wait_timeout_is_reported_and_cleared(orc):
     """The learned-closure gradient pass bounds its waits on the tensor-core
     completion barrier.  A test hook adds a bounded wait on a barrier that
