@@ -230,7 +230,9 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
 // UPD: 0 right-hand side only; 1 LSRK stage, the step's increment
 // D = sum_s B_s dQ_s carried in FP32 and the shadow advanced by B_s dQ_s;
 // 2 last stage of the step, Q = Q_step_start + D added in FP64 and the shadow
-// rewritten from it.  FL: numerical flux of F1, 0 Rusanov, 1 HLLC, 2 Roe.
+// rewritten from it.  With UPD 1 and 2 the new shadow's thermodynamic fields
+// go to THout.  p' and c of the input state come from TH.  FL: numerical
+// flux of F1, 0 Rusanov, 1 HLLC, 2 Roe.
 template <int N, int UPD, int FL>
 __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__restrict__ S, const float *__restrict__ F2,
                                                   const float *__restrict__ TH, float *__restrict__ dQ,
