@@ -234,3 +234,22 @@ def test_fp32_mass_energy_conservation(orc):
         # right-hand side: bound 1e-10 relative over 10 steps
         print("fp32 budget drift", v, (b1[v] - b0[v]) / b0[v])
         assert abs(b1[v] - b0[v]) <= 1e-10 * abs(b0[v]), (v, (b1[v] - b0[v]) / b0[v])
+
+
+def test_fp32_tendency_between_steps_leaves_the_state_alone(orc):
+    """The FP32 path keeps two shadow buffers, each with the thermodynamic
+    fields of its state.  A tendency call builds its shadow in the idle
+    buffer; the state being stepped, its shadow and their thermodynamic
+    fields stay as they were, so that two steps with a tendency call (of
+    another state) between them end bit-identical to two steps without."""
+    m = I.sub_mesh("c2", 4, 3, 8)
+    S, Q, G = _setup(orc, "c2", m, fuzz_seed=23)
+    Qd = torch.from_numpy(Q).cuda()
+    G.set_state(Qd)
+    G.step(2)
+    ref = G.get_state().cpu().numpy()
+    G.set_state(Qd)
+    G.step(1)
+    G.tendency(torch.from_numpy(_fuzz(Q, 29)).cuda())
+    G.step(1)
+    assert np.array_equal(G.get_state().cpu().numpy(), ref)

@@ -148,3 +148,19 @@ def test_warped_tendency_with_learned_closure(orc):
     assert G.diagnostics(raise_on_error=False)["status"] == 0
     for v in range(5):
         assert errs[v] <= 1e-4, (v, errs)
+
+
+def test_warped_tendency_between_steps_leaves_the_state_alone(orc):
+    """As on flat meshes: a tendency call between two steps (of another
+    state) leaves the stepped state, its shadow and its thermodynamic fields
+    alone; the result is bit-identical to two steps without it."""
+    m, S, Q, G = _setup(orc)
+    Qd = torch.from_numpy(Q).cuda()
+    G.set_state(Qd)
+    G.step(2)
+    ref = G.get_state().cpu().numpy()
+    G.set_state(Qd)
+    G.step(1)
+    G.tendency(torch.from_numpy(Q * (1.0 + 1e-4)).cuda())
+    G.step(1)
+    assert np.array_equal(G.get_state().cpu().numpy(), ref)
