@@ -75,6 +75,23 @@ DTYPE = {"fp32": "f32", "fp64": "f64"}
 # gradient pass.  Remove an entry when its kernel changes.
 TRAFFIC_B_PER_NODE = {("fp32acc64_mlp", "grad"): 85.20, ("fp32acc64_sl", "grad"): 83.38,
                       ("fp64_sl", "grad"): 185.0}
+# Warp instructions per element of the FP32 gradient passes (ncu
+# smsp__inst_executed.sum over the elements of the same capture), for the
+# issue-rate view of those passes, which are bound by instruction issue rather
+# than by HBM: peak = 148 SMs x 4 schedulers x the maximum SM clock, one warp
+# instruction per scheduler and clock.  Remove an entry when its kernel changes.
+WARP_INST_PER_ELEM = {("fp32acc64_mlp", "grad"): 6119, ("fp32acc64_sl", "grad"): 3171}
+
+
+def issue_peak():
+    """warp instructions per second the SMs can issue at the maximum SM clock
+    (MEASURED_PEAKS.json's sm_max_mhz, else B300's 2032 MHz)"""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = json.load(f).get("sm_max_mhz", 2032.0)
+    except Exception:
+        mhz = 2032.0
+    return 148 * 4 * mhz * 1e6
 
 
 def measured_peaks():
@@ -357,6 +374,12 @@ def main():
     achieved = head["nodes"] * alg_bytes(prec, kinds[dom], hstages, variants[0][4]) / (avg_ms / 1e3) / 1e9
     tb = TRAFFIC_B_PER_NODE.get((variants[0][0], kinds[dom]))
     traffic = tb * head["nodes"] if tb is not None else None
+    wi = WARP_INST_PER_ELEM.get((variants[0][0], kinds[dom]))
+    issue = None
+    if wi is not None:
+        ipk = issue_peak()
+        ach = wi * (head["nodes"] // 125) / (avg_ms / 1e3)
+        issue = {"warp_inst_per_element": wi, "achieved": ach, "peak": ipk, "unit": "warp-inst/s", "frac": ach / ipk}
     out_variants = {}
     for (name, vprec, _, _, vint), r in zip(variants, results.values()):
         v = whole_job_rate(r["nodes"], world, args.steps, r["ms"], STAGES[vint])
@@ -390,7 +413,7 @@ def main():
                             "l2": "inputs larger than L2 (state alone 12 GB)", "parallelism": f"replicas{world}"},
                     roofline={"bound": "hbm", "kernel": kinds[dom], "achieved": achieved, "peak": hbm,
                               "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                              "peak_source": f"{peak_kind} hbm_gbs"},
+                              "peak_source": f"{peak_kind} hbm_gbs", "issue": issue},
                     cpu_baseline=cb, e2e=e2e, gpu_launches=head["launches"], clocks=head["clocks"],
                     variants=out_variants)
         print(json.dumps(line))
