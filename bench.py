@@ -32,10 +32,11 @@ STAGES = {"lsrk54": 5, "lsrk144": 14, "ark2_hevi": 3}
 METRIC = "DG node-stage updates/s at 1 B300 and HBM roofline %, FP32+learned vs FP64 plain"
 # algorithmic bytes per node for each kernel launch (compulsory traffic),
 # averaged over the S stages of a step (S = 5 for LSRK(5,4)):
-#   gradient pass, FP64 path: read Q, write F2 (15 words) and aux (2 words);
-#     FP32 path: read S and the state's h', theta_v' (2 words), write F2
-#   flux/update pass, FP64 path: read Q, F2, aux; write dQ and Q_out; read dQ
-#     except in the first stage (A_1 = 0): ((S - 1) * 41 + 35) words / S
+#   gradient pass: read the state (Q or the FP32 shadow S) and its h_tot,
+#     theta_v (2 words), write F2 (15 words)
+#   flux/update pass, FP64 path: read Q, F2, p - p_r and c; write dQ, Q_out
+#     and Q_out's four thermodynamic fields; read dQ except in the first stage
+#     (A_1 = 0): ((S - 1) * 45 + 39) words / S
 #   flux/update pass, FP32 path (FP32 shadow S, FP32 register dQ and step
 #     increment D, FP64 state Q64): read S, F2, p' and c (23 words) in every
 #     stage; every stage writes the new state's thermodynamic fields (+4);
@@ -51,7 +52,7 @@ def alg_bytes(prec, kind, stages=5, integrator="lsrk54"):
     if integrator == "ark2_hevi":
         return 29 * 8 if prec == "fp64" else 23 * 4 + 6 * 8
     if prec == "fp64":
-        return ((stages - 1) * 41 + 35) * 8 / stages
+        return ((stages - 1) * 45 + 39) * 8 / stages
     return (45 + (stages - 2) * 57 + 69) * 4 / stages
 
 
@@ -73,8 +74,7 @@ DTYPE = {"fp32": "f32", "fp64": "f64"}
 # divided by the nodes; the traffic is per node, so it scales to the full box by
 # the node count).  Only kernels whose every launch does the same work: the
 # gradient pass.  Remove an entry when its kernel changes.
-TRAFFIC_B_PER_NODE = {("fp32acc64_mlp", "grad"): 85.20, ("fp32acc64_sl", "grad"): 83.38,
-                      ("fp64_sl", "grad"): 185.0}
+TRAFFIC_B_PER_NODE = {("fp32acc64_mlp", "grad"): 85.20, ("fp32acc64_sl", "grad"): 83.38}
 # Warp instructions per element of the FP32 gradient passes (ncu
 # smsp__inst_executed.sum over the elements of the same capture), for the
 # issue-rate view of those passes, which are bound by instruction issue rather

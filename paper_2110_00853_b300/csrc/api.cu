@@ -124,13 +124,14 @@ struct cmles_t {
   KParams K;
   double *Q[2] = {nullptr, nullptr};
   int cur = 0;
-  double *dQ = nullptr, *F2 = nullptr, *aux = nullptr;
+  double *dQ = nullptr, *F2 = nullptr;
+  double *TH64[2] = {nullptr, nullptr};  // FP64 path: thermodynamic fields of Q[i]
   // FP32 path: shadow ping-pong, FP32 LSRK register, FP32 F2/aux, tables
   bool fp32 = false;
   float *S32[2] = {nullptr, nullptr};
   float *TH32[2] = {nullptr, nullptr};  // thermodynamic fields of S32[i]
   int scur = 0;
-  bool shadow_valid = false;
+  bool shadow_valid = false;  // FP32: S32[scur] and TH32[scur] are Q's; FP64: TH64[cur] is Q[cur]'s
   float *dQ32 = nullptr, *D32 = nullptr, *F2_32 = nullptr, *lev32 = nullptr, *dH32 = nullptr;
   double *qref64 = nullptr;
   double *rho_r = nullptr, *p_r = nullptr, *qt_r = nullptr, *tau_lev = nullptr, *tau_col = nullptr;
@@ -384,27 +385,40 @@ cmles_status write_shadow(cmles_handle h, const double *Q, int i) {
   return CMLES_OK;
 }
 
+// the thermodynamic fields of the FP64 state Q into TH
+cmles_status write_thermo64(cmles_handle h, const double *Q, double *TH) {
+  LaunchScope ls(h, 2, 1);
+  CK(launch_thermo64(Q, TH, h->K, h->N, h->stream));
+  return CMLES_OK;
+}
+
+// FP32: the shadow of the state and its thermodynamic fields; FP64: the
+// state's thermodynamic fields (both built when the state has changed).
 cmles_status ensure_shadow(cmles_handle h) {
-  if (h->fp32 && !h->shadow_valid) {
-    cmles_status st = write_shadow(h, h->Q[0], h->scur);
+  if (!h->shadow_valid) {
+    cmles_status st = h->fp32 ? write_shadow(h, h->Q[0], h->scur) : write_thermo64(h, h->Q[h->cur], h->TH64[h->cur]);
     if (st != CMLES_OK) return st;
     h->shadow_valid = true;
   }
   return CMLES_OK;
 }
 
-cmles_status run_stage_pair(cmles_handle h, const double *Qin, double *Qout, double *dQ, const StageCoef &sc,
-                            bool update) {
+// One gradient pass and one flux pass of the FP64 path on Qin, whose
+// thermodynamic fields are THin; with update the stage's new state and its
+// fields go to Qout and THout.
+cmles_status run_stage_pair(cmles_handle h, const double *Qin, const double *THin, double *Qout, double *THout,
+                            double *dQ, const StageCoef &sc, bool update) {
   {
     LaunchScope ls(h, 0, 1);
-    CK(launch_grad64(Qin, h->F2, h->aux, h->K, h->stream));
+    CK(launch_grad64(Qin, THin, h->F2, h->K, h->stream));
   }
   {
     LaunchScope ls(h, 1, 1);
-    CK(launch_rhs64(Qin, h->F2, h->aux, dQ, Qout, sc, update, h->K, h->stream));
+    CK(launch_rhs64(Qin, h->F2, THin, dQ, Qout, THout, sc, update, h->K, h->stream));
   }
   return CMLES_OK;
 }
+
 
 // ---- curvilinear (warped) meshes ----
 
@@ -735,6 +749,7 @@ static cmles_status apply_expfilter(cmles_handle h) {
     }
   } else {
     CK(launch_expfilter(h->Q[h->cur], nullptr, h->expf, h->N, (int)h->E, h->stream));
+    if (h->shadow_valid) CK(launch_thermo64(h->Q[h->cur], h->TH64[h->cur], h->K, h->N, h->stream));
   }
   return CMLES_OK;
 }
@@ -798,7 +813,8 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
     ALLOC(h->Q[1], n6 * sizeof(double));
     ALLOC(h->dQ, n6 * sizeof(double));
     ALLOC(h->F2, (size_t)h->nodes * 15 * sizeof(double));
-    ALLOC(h->aux, (size_t)h->nodes * 2 * sizeof(double));
+    ALLOC(h->TH64[0], (size_t)h->nodes * 4 * sizeof(double));
+    ALLOC(h->TH64[1], (size_t)h->nodes * 4 * sizeof(double));
   } else {
     const size_t n32 = (size_t)E * 128;  // padded nodes
     ALLOC(h->S32[0], n32 * 6 * sizeof(float));
@@ -898,7 +914,7 @@ cmles_status cmles_destroy(cmles_handle h) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
   }
-  void *bufs[] = {h->Q[0],   h->Q[1],    h->dQ,      h->F2,      h->aux,     h->rho_r,    h->p_r,
+  void *bufs[] = {h->Q[0],   h->Q[1],    h->dQ,      h->F2,      h->TH64[0], h->TH64[1],  h->rho_r,    h->p_r,
                   h->qt_r,   h->tau_lev, h->tau_col, h->wq,      h->flags,   h->partials, h->budget_out,
                   h->prof,   h->S32[0],  h->S32[1],  h->dQ32,    h->D32,     h->F2_32,    h->lev32,
                   h->TH32[0], h->TH32[1], h->dH32,   h->qref64,  h->mlp_dev, h->geo32,    h->node32,
@@ -1252,7 +1268,10 @@ cmles_status cmles_tendency(cmles_handle h, const double *Q_dev, double *RHS_dev
     if (st != CMLES_OK) return st;
     return run_stage_pair32(h, 1 - h->scur, RHS_dev, sc, false);
   }
-  return run_stage_pair(h, Q_dev, nullptr, RHS_dev, sc, false);
+  // the thermodynamic fields of Q_dev into the idle buffer
+  cmles_status st = write_thermo64(h, Q_dev, h->TH64[1 - h->cur]);
+  if (st != CMLES_OK) return st;
+  return run_stage_pair(h, Q_dev, h->TH64[1 - h->cur], nullptr, nullptr, RHS_dev, sc, false);
 }
 
 // HEVI stage buffers and, for the current step, the vertical operator's
@@ -1303,7 +1322,11 @@ cmles_status ensure_hevi(cmles_handle h) {
 // FP32 path the FP32 kernels on Y's shadow (built in the idle shadow buffer).
 cmles_status hevi_tendency(cmles_handle h, const double *Y, double *R) {
   const StageCoef sc = {0.0, 0.0, 0.0, 0, 0.f, 0.f, 0.f, 1};
-  if (!h->fp32) return run_stage_pair(h, Y, nullptr, R, sc, false);
+  if (!h->fp32) {
+    cmles_status st = write_thermo64(h, Y, h->TH64[1 - h->cur]);
+    if (st != CMLES_OK) return st;
+    return run_stage_pair(h, Y, h->TH64[1 - h->cur], nullptr, nullptr, R, sc, false);
+  }
   cmles_status st = write_shadow(h, Y, 1 - h->scur);
   if (st != CMLES_OK) return st;
   return run_stage_pair32(h, 1 - h->scur, R, sc, false);
@@ -1347,10 +1370,10 @@ cmles_status run_ark2_hevi(cmles_handle h) {
     LaunchScope ls(h, 2, 1);
     CK(launch_lincomb(Qo, Qn, LinComb{3, dt, {d, d, g, 0.0}, {R0, R1, R2, nullptr}}, count, h->stream));
   }
-  if (h->fp32)
-    h->shadow_valid = false;  // the shadow of the new state is built when next needed
-  else
-    h->cur = 1 - h->cur;
+  // the shadow (FP32) or the thermodynamic fields (FP64) of the new state are
+  // built when next needed
+  h->shadow_valid = false;
+  if (!h->fp32) h->cur = 1 - h->cur;
   return CMLES_OK;
 }
 
@@ -1359,7 +1382,7 @@ cmles_status cmles_step(cmles_handle h, int nsteps) {
   if (!h->have_ref) return fail(h, CMLES_ERR_STATE, "cmles_step: reference state not set");
   if (h->prm.closure == CMLES_CLOSURE_MLP && !h->have_mlp)
     return fail(h, CMLES_ERR_STATE, "cmles_step: closure weights not set");
-  if (h->fp32) {
+  {
     cmles_status st = ensure_shadow(h);
     if (st != CMLES_OK) return st;
   }
@@ -1386,7 +1409,8 @@ cmles_status cmles_step(cmles_handle h, int nsteps) {
         st = run_stage_pair32(h, h->scur, nullptr, sc, true);
         h->scur = 1 - h->scur;
       } else {
-        st = run_stage_pair(h, h->Q[h->cur], h->Q[1 - h->cur], h->dQ, sc, true);
+        st = run_stage_pair(h, h->Q[h->cur], h->TH64[h->cur], h->Q[1 - h->cur], h->TH64[1 - h->cur], h->dQ, sc,
+                            true);
         h->cur = 1 - h->cur;
       }
       if (st != CMLES_OK) return st;

@@ -1,15 +1,19 @@
 // FP64 ("plain") DG right-hand side kernels for flat hexahedral meshes.
 //
 // Two kernels per Runge-Kutta stage (Sec. 3.1, Eq. matrixProblem):
-//   k_grad64: pointwise thermodynamics with saturation adjustment (Sec. 2),
-//             the BR1 auxiliary gradient of G = (u, v, w, h_tot, q_t, theta_v)
-//             with its centred face term, the SGS closure (Sec. 4) and the
-//             diffusive flux F2; writes F2 and aux = (p - p_r, c).
+//   k_grad64: the BR1 auxiliary gradient of G = (u, v, w, h_tot, q_t,
+//             theta_v) with its centred face term, the SGS closure (Sec. 4)
+//             and the diffusive flux F2; writes F2.
 //   k_rhs64:  total flux F1 + F2, its divergence by the 1D LGL derivative
 //             matrix along each axis, the Rusanov/central surface terms with
 //             the lift w_s J_s / (w_i J_i), wall boundary states (App. A.3),
 //             sources (gravity with reference subtraction, Rayleigh sponge,
 //             Coriolis), and the fused LSRK(5,4) stage update.
+// The pointwise thermodynamics with saturation adjustment (Sec. 2) runs once
+// per node and state, in the kernel that writes the state: the flux pass for
+// the state it advances to, k_thermo64 otherwise.  It stores p - p_r, the
+// sound speed, h_tot and theta_v (TH, four planes per element), which the
+// next gradient pass (own and neighbour face nodes) and flux pass read.
 // One element per 128-thread CTA iteration, one node per thread, element and
 // neighbour face nodes staged in shared memory; grid-stride over elements.
 #include "common.cuh"
@@ -18,9 +22,27 @@
 
 namespace cmles {
 
-template <int N, bool MOIST>
-__global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, double *__restrict__ F2,
-                                                double *__restrict__ aux, const KParams P) {
+// The thermodynamic fields of a node's state Y at height z and level lev.
+// Not inlined: the flux pass (for the state it advances to) and k_thermo64
+// (for a state set from outside) then run the same compiled code, so that a
+// state gets bit-identical fields whichever kernel wrote them (a run resumed
+// from a saved state continues bit-identically).
+__device__ __noinline__ void thermo_store64(const KParams &P, const double Y[6], double z, int lev, double *TH,
+                                               size_t e, int t, int Np, int &fail) {
+  Th64 s;
+  if (P.moist)
+    thermo64<true>(P, Y, z, lev, s, fail);
+  else
+    thermo64<false>(P, Y, z, lev, s, fail);
+  TH[(e * 4 + 0) * Np + t] = s.p - P.p_r[lev];
+  TH[(e * 4 + 1) * Np + t] = s.c;
+  TH[(e * 4 + 2) * Np + t] = s.htot;
+  TH[(e * 4 + 3) * Np + t] = s.thv;
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, const double *__restrict__ TH,
+                                                double *__restrict__ F2, const KParams P) {
   constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
   static_assert(Np <= 128, "one node per thread");
   __shared__ double sD[Nq * Nq];
@@ -30,7 +52,6 @@ __global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, do
   const int t = threadIdx.x;
   if (t < Nq * Nq) sD[t] = P.D[t];
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
-  int fail = 0;
   for (int e = blockIdx.x; e < P.E; e += gridDim.x) {
     const int ex = e % P.nex, ey = (e / P.nex) % P.ney, ez = e / (P.nex * P.ney);
     if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
@@ -38,22 +59,20 @@ __global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, do
     if (t < Np) {
 #pragma unroll
       for (int v = 0; v < 6; ++v) Y[v] = Q[((size_t)e * 6 + v) * Np + t];
-      Th64 s;
-      thermo64<MOIST>(P, Y, node_z(P, ez, k), ez * Nq + k, s, fail);
-      G[0] = s.u[0];
-      G[1] = s.u[1];
-      G[2] = s.u[2];
-      G[3] = s.htot;
-      G[4] = s.q;
-      G[5] = s.thv;
-      const int lev = ez * Nq + k;
-      aux[((size_t)e * 2 + 0) * Np + t] = s.p - P.p_r[lev];
-      aux[((size_t)e * 2 + 1) * Np + t] = s.c;
+      // h_tot and theta_v come with the state; u and q_t formed exactly as
+      // the thermodynamics forms them
+      const double rinv = 1.0 / Y[0];
+      G[0] = Y[1] * rinv;
+      G[1] = Y[2] * rinv;
+      G[2] = Y[3] * rinv;
+      G[3] = TH[((size_t)e * 4 + 2) * Np + t];
+      G[4] = Y[5] * rinv;
+      G[5] = TH[((size_t)e * 4 + 3) * Np + t];
 #pragma unroll
       for (int v = 0; v < 6; ++v) sG[v][t] = G[v];
     }
     __syncthreads();
-    // neighbour face nodes: thermodynamics recomputed from the neighbour's state
+    // neighbour face nodes
     for (int task = t; task < 6 * Nf; task += blockDim.x) {
       const int f = task / Nf, fn = task - f * Nf;
       const int nb = sNb[f];
@@ -61,18 +80,14 @@ __global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, do
       const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
       const int a_nb = (f & 1) ? 0 : N;
       const int nn = face_node<Nq>(d, a_nb, t1, t2);
-      double Yp[6];
-#pragma unroll
-      for (int v = 0; v < 6; ++v) Yp[v] = Q[((size_t)nb * 6 + v) * Np + nn];
-      const int ezn = nb / (P.nex * P.ney);
-      Th64 s;
-      thermo64<MOIST>(P, Yp, node_z(P, ezn, d == 2 ? a_nb : t2), ezn * Nq + (d == 2 ? a_nb : t2), s, fail);
-      sGf[f][0][fn] = s.u[0];
-      sGf[f][1][fn] = s.u[1];
-      sGf[f][2][fn] = s.u[2];
-      sGf[f][3][fn] = s.htot;
-      sGf[f][4][fn] = s.q;
-      sGf[f][5][fn] = s.thv;
+      const double *Yp = Q + (size_t)nb * 6 * Np + nn;
+      const double rinv = 1.0 / Yp[0];
+      sGf[f][0][fn] = Yp[1 * Np] * rinv;
+      sGf[f][1][fn] = Yp[2 * Np] * rinv;
+      sGf[f][2][fn] = Yp[3 * Np] * rinv;
+      sGf[f][3][fn] = TH[((size_t)nb * 4 + 2) * Np + nn];
+      sGf[f][4][fn] = Yp[5 * Np] * rinv;
+      sGf[f][5][fn] = TH[((size_t)nb * 4 + 3) * Np + nn];
     }
     __syncthreads();
     if (t < Np) {
@@ -156,7 +171,6 @@ __global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, do
     }
     __syncthreads();
   }
-  if (fail) atomicAdd(P.flags, 1);
 }
 
 // n.F1 in direction d (sign applied by the caller) of Eq. eom_compact:
@@ -178,8 +192,9 @@ __device__ __forceinline__ void flux1_dir(const double Y[6], double rinv, double
 // FL: numerical flux of F1, 0 Rusanov, 1 HLLC, 2 Roe
 template <int N, bool UPDATE, int FL>
 __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, const double *__restrict__ F2,
-                                               const double *__restrict__ aux, double *__restrict__ dQ,
-                                               double *__restrict__ Qout, const StageCoef sc, const KParams P) {
+                                               const double *__restrict__ TH, double *__restrict__ dQ,
+                                               double *__restrict__ Qout, double *__restrict__ THout,
+                                               const StageCoef sc, const KParams P) {
   constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
   __shared__ double sD[Nq * Nq];
   __shared__ double sF[6][3][Np];
@@ -189,6 +204,7 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
   const int t = threadIdx.x;
   if (t < Nq * Nq) sD[t] = P.D[t];
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
+  int fail = 0;
   for (int e = blockIdx.x; e < P.E; e += gridDim.x) {
     const int ex = e % P.nex, ey = (e / P.nex) % P.ney, ez = e / (P.nex * P.ney);
     if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
@@ -200,7 +216,7 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
         Y[v] = Q[((size_t)e * 6 + v) * Np + t];
         sY[v][t] = Y[v];
       }
-      const double pp = aux[((size_t)e * 2) * Np + t];
+      const double pp = TH[((size_t)e * 4) * Np + t];
       const double pr = P.p_r[lev];
       const double rinv = 1.0 / Y[0];
 #pragma unroll
@@ -230,16 +246,16 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
       double Ym[6], Yp[6];
 #pragma unroll
       for (int v = 0; v < 6; ++v) Ym[v] = sY[v][n];
-      const double pm = aux[((size_t)e * 2) * Np + n];
-      const double cm = aux[((size_t)e * 2 + 1) * Np + n];
+      const double pm = TH[((size_t)e * 4) * Np + n];
+      const double cm = TH[((size_t)e * 4 + 1) * Np + n];
       const int nb = sNb[f];
       double pp, cp, f2s[5];
       if (nb >= 0) {
         const int nn = face_node<Nq>(d, N - a, t1, t2);
 #pragma unroll
         for (int v = 0; v < 6; ++v) Yp[v] = Q[((size_t)nb * 6 + v) * Np + nn];
-        pp = aux[((size_t)nb * 2) * Np + nn];
-        cp = aux[((size_t)nb * 2 + 1) * Np + nn];
+        pp = TH[((size_t)nb * 4) * Np + nn];
+        cp = TH[((size_t)nb * 4 + 1) * Np + nn];
         const double *g2m = F2 + ((size_t)e * 15 + d * 5) * Np + n;
         const double *g2p = F2 + ((size_t)nb * 15 + d * 5) * Np + nn;
 #pragma unroll
@@ -336,20 +352,42 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
       R[1] += S[0];
       R[2] += S[1];
       R[3] += S[2];
+      double Yn[6];
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
         const size_t idx = ((size_t)e * 6 + v) * Np + t;
         if (UPDATE) {
           const double dq = (sc.A != 0.0 ? sc.A * dQ[idx] : 0.0) + sc.dt * R[v];
           dQ[idx] = dq;
-          Qout[idx] = Y[v] + sc.B * dq;
+          Yn[v] = Y[v] + sc.B * dq;
+          Qout[idx] = Yn[v];
         } else {
           dQ[idx] = R[v];
         }
       }
+      // the thermodynamics of the new state, for the next stage's two passes
+      if (UPDATE) thermo_store64(P, Yn, node_z(P, ez, k), ez * Nq + k, THout, e, t, Np, fail);
     }
     __syncthreads();
   }
+  if (fail) atomicAdd(P.flags, 1);
+}
+
+// The thermodynamic fields of a given state Q (one thread per node).
+__global__ void k_thermo64(const double *__restrict__ Q, double *__restrict__ TH, const KParams P, int Np, int Nq) {
+  const long long n = (long long)P.E * Np;
+  int fail = 0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const long long e = q / Np;
+    const int node = (int)(q - e * Np);
+    const int ez = (int)(e / ((long long)P.nex * P.ney));
+    const int k = node / (Nq * Nq);
+    double Y[6];
+#pragma unroll
+    for (int v = 0; v < 6; ++v) Y[v] = Q[(e * 6 + v) * Np + node];
+    thermo_store64(P, Y, node_z(P, ez, k), ez * Nq + k, TH, (size_t)e, node, Np, fail);
+  }
+  if (fail) atomicAdd(P.flags, 1);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -390,43 +428,46 @@ int grid_for_tc(const void *fn, int E, int tmem_cols) {
   return (int)(g < E ? g : E);
 }
 
-cudaError_t launch_grad64(const double *Q, double *F2, double *aux, const KParams &P, cudaStream_t s) {
-  if (P.moist) {
-    static int grid = 0;
-    if (!grid) grid = grid_for((const void *)k_grad64<4, true>, 1 << 30);
-    k_grad64<4, true><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, aux, P);
-  } else {
-    static int grid = 0;
-    if (!grid) grid = grid_for((const void *)k_grad64<4, false>, 1 << 30);
-    k_grad64<4, false><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, aux, P);
-  }
+cudaError_t launch_thermo64(const double *Q, double *TH, const KParams &P, int N, cudaStream_t s) {
+  const int Nq = N + 1, Np = Nq * Nq * Nq;
+  const long long nodes = (long long)P.E * Np;
+  int blocks = (int)((nodes + 127) / 128);
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  k_thermo64<<<blocks, 128, 0, s>>>(Q, TH, P, Np, Nq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad64(const double *Q, const double *TH, double *F2, const KParams &P, cudaStream_t s) {
+  static int grid = 0;
+  if (!grid) grid = grid_for((const void *)k_grad64<4>, 1 << 30);
+  k_grad64<4><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, TH, F2, P);
   return cudaGetLastError();
 }
 
 template <bool UPDATE, int FL>
-static void rhs64_instance(const double *Q, const double *F2, const double *aux, double *dQ, double *Qout,
-                           const StageCoef &sc, const KParams &P, cudaStream_t s) {
+static void rhs64_instance(const double *Q, const double *F2, const double *TH, double *dQ, double *Qout,
+                           double *THout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
   static int grid = 0;
   if (!grid) grid = grid_for((const void *)k_rhs64<4, UPDATE, FL>, 1 << 30);
-  k_rhs64<4, UPDATE, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, aux, dQ, Qout, sc, P);
+  k_rhs64<4, UPDATE, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, TH, dQ, Qout, THout, sc, P);
 }
 
-cudaError_t launch_rhs64(const double *Q, const double *F2, const double *aux, double *dQ, double *Qout,
-                         const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+cudaError_t launch_rhs64(const double *Q, const double *F2, const double *TH, double *dQ, double *Qout,
+                         double *THout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
   if (update) {
     if (P.flux == 2)
-      rhs64_instance<true, 2>(Q, F2, aux, dQ, Qout, sc, P, s);
+      rhs64_instance<true, 2>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
     else if (P.flux == 1)
-      rhs64_instance<true, 1>(Q, F2, aux, dQ, Qout, sc, P, s);
+      rhs64_instance<true, 1>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
     else
-      rhs64_instance<true, 0>(Q, F2, aux, dQ, Qout, sc, P, s);
+      rhs64_instance<true, 0>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
   } else {
     if (P.flux == 2)
-      rhs64_instance<false, 2>(Q, F2, aux, dQ, Qout, sc, P, s);
+      rhs64_instance<false, 2>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
     else if (P.flux == 1)
-      rhs64_instance<false, 1>(Q, F2, aux, dQ, Qout, sc, P, s);
+      rhs64_instance<false, 1>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
     else
-      rhs64_instance<false, 0>(Q, F2, aux, dQ, Qout, sc, P, s);
+      rhs64_instance<false, 0>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
   }
   return cudaGetLastError();
 }

@@ -12,10 +12,14 @@ namespace cmles {
 int grid_for(const void *fn, int E, size_t smem);
 int grid_for_tc(const void *fn, int E, int tmem_cols);
 
-// FP64 path (dg_fp64.cu)
-cudaError_t launch_grad64(const double *Q, double *F2, double *aux, const KParams &P, cudaStream_t s);
-cudaError_t launch_rhs64(const double *Q, const double *F2, const double *aux, double *dQ, double *Qout,
-                         const StageCoef &sc, bool update, const KParams &P, cudaStream_t s);
+// FP64 path (dg_fp64.cu).  TH: the state's thermodynamic fields (p - p_r, c,
+// h_tot, theta_v; four planes per element), written with the state (the flux
+// pass with update for Qout, launch_thermo64 otherwise) and read by the next
+// two passes.
+cudaError_t launch_thermo64(const double *Q, double *TH, const KParams &P, int N, cudaStream_t s);
+cudaError_t launch_grad64(const double *Q, const double *TH, double *F2, const KParams &P, cudaStream_t s);
+cudaError_t launch_rhs64(const double *Q, const double *F2, const double *TH, double *dQ, double *Qout,
+                         double *THout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s);
 
 // FP32 path with FP64 accumulation (dg_fp32.cu); FP32 arrays padded to 128
 // nodes.  TH: the state's thermodynamic fields (p', c, h', theta_v'; four
