@@ -74,7 +74,8 @@ DTYPE = {"fp32": "f32", "fp64": "f64"}
 # divided by the nodes; the traffic is per node, so it scales to the full box by
 # the node count).  Only kernels whose every launch does the same work: the
 # gradient pass.  Remove an entry when its kernel changes.
-TRAFFIC_B_PER_NODE = {("fp32acc64_mlp", "grad"): 85.20, ("fp32acc64_sl", "grad"): 83.38}
+TRAFFIC_B_PER_NODE = {("fp32acc64_mlp", "grad"): 85.20, ("fp32acc64_sl", "grad"): 83.38,
+                      ("fp64_sl", "grad"): 183.8}
 # Warp instructions per element of the FP32 gradient passes (ncu
 # smsp__inst_executed.sum over the elements of the same capture), for the
 # issue-rate view of those passes, which are bound by instruction issue rather
