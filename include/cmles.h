@@ -310,13 +310,19 @@ cmles_status cmles_hevi_operator(cmles_handle h, const double *Q_dev, double *ou
 cmles_status cmles_hevi_solve(cmles_handle h, const double *B_dev, double *Y_dev);
 
 /* Test hook for the failure path of the bounded device-side waits (no GPU
- * fault involved): with enable != 0, each CTA of the learned-closure
- * gradient pass also waits, with a bound, on an mbarrier that nothing
- * arrives on; the wait runs out, the CTA finishes its work, frees its Tensor
- * Memory and is counted, and the next cmles_diagnostics returns
- * CMLES_ERR_TIMEOUT with cmles_diag.tc_timeouts > 0.  enable = 0 restores
- * normal operation. */
-cmles_status cmles_test_stall_tc(cmles_handle h, int enable);
+ * fault involved), in the learned-closure gradient pass:
+ *   mode 1: each CTA also waits, with a bound, on an mbarrier that nothing
+ *           arrives on; the wait runs out, the CTA finishes its work
+ *           (results intact), frees its Tensor Memory and is counted;
+ *   mode 2: each CTA's first MMA completion wait gives up at once, while its
+ *           MMA is still in flight; the CTA issues no further MMA, skips its
+ *           Tensor Memory reads (results invalid), and at its tear-down waits
+ *           (bounded) for that MMA to complete before freeing the columns.
+ * Either way the next cmles_diagnostics returns CMLES_ERR_TIMEOUT with
+ * cmles_diag.tc_timeouts = the number of CTAs that gave up (each counted
+ * once).  Mode 0 restores normal operation; other values give
+ * CMLES_ERR_ARG. */
+cmles_status cmles_test_stall_tc(cmles_handle h, int mode);
 
 /* Allocation-free budgets.  The paper has no counterpart: this is a service
  * for callers that cannot call cudaMalloc, such as applications whose own
@@ -331,9 +337,14 @@ cmles_status cmles_test_stall_tc(cmles_handle h, int enable);
  * library keeps until exit.  Limits: 1 <= N <= 7 and at most 2,097,152
  * elements; larger sizes return CMLES_ERR_ARG without launching.  The first
  * call on each device looks up the array's device address (with that device
- * current) and should come before any stream capture.  All calls share the
+ * current) and should come before any stream capture; the address is cached
+ * for the life of the loaded library, so after cudaDeviceReset the library
+ * must be loaded again (a new process) before this call is used on that
+ * device.  All calls share the
  * array, so calls that overlap on the GPU race: serialise them.  Errors:
- * CMLES_ERR_ARG (null pointers, sizes), CMLES_ERR_CUDA (lookup or launch). */
+ * CMLES_ERR_ARG (null pointers, sizes), CMLES_ERR_CUDA (lookup, or the launch
+ * of one of its two kernels; an earlier non-sticky error of other code is
+ * left for that code to read). */
 cmles_status cmles_budgets_noalloc(const double *Q_dev, long long num_elements, int N, double jacobian,
                                    double *out_dev, void *stream);
 

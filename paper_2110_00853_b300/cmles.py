@@ -370,10 +370,12 @@ class Solver:
         self._check(self.L.cmles_hevi_solve(self.h, C.c_void_p(B.data_ptr()), C.c_void_p(Y.data_ptr())))
         return Y
 
-    def test_stall_tc(self, enable):
-        """Test hook: make the learned-closure kernels' bounded tensor-core
-        wait run out (see cmles_test_stall_tc)."""
-        self._check(self.L.cmles_test_stall_tc(self.h, 1 if enable else 0))
+    def test_stall_tc(self, mode):
+        """Test hook of the learned-closure kernels' bounded tensor-core waits
+        (see cmles_test_stall_tc): 0 off, 1 (or True) an extra wait on a
+        barrier nothing arrives on, 2 the first MMA completion wait of each CTA
+        gives up at once."""
+        self._check(self.L.cmles_test_stall_tc(self.h, int(mode)))
 
     def device_bytes(self):
         return self.L.cmles_device_bytes(self.h)

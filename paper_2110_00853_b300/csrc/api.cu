@@ -1585,7 +1585,8 @@ cmles_status cmles_hevi_solve(cmles_handle h, const double *B_dev, double *Y_dev
 
 cmles_status cmles_test_stall_tc(cmles_handle h, int enable) {
   if (!h) return CMLES_ERR_ARG;
-  h->tc_stall = enable ? 1 : 0;
+  if (enable < 0 || enable > 2) return fail(h, CMLES_ERR_ARG, "cmles_test_stall_tc: mode must be 0, 1 or 2");
+  h->tc_stall = enable;
   h->K.tc_stall = h->tc_stall;
   return CMLES_OK;
 }

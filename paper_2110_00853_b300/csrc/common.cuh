@@ -80,7 +80,8 @@ struct KParams {
   const double *rho_r, *p_r, *tau_lev, *tau_col;
   int satadj_max_iter;
   int *flags;        // [0] Newton non-convergence count, [1] CTAs whose tensor-core wait gave up
-  int tc_stall;      // test hook: the tensor-core kernels also wait on a barrier nothing arrives on
+  int tc_stall;      // test hook: 1 the tensor-core kernels also wait on a barrier nothing arrives on;
+                    // 2 their first MMA completion wait gives up at once
   int tiled;         // 1: visit elements in 4 x 4 column tiles (nex, ney multiples of 4)
   // FP32 path tables (see dg_fp32.cu): per level 16 floats, per element layer
   // the 5 x 5 differences of rho e_r + p_r along z, per level FP64 offsets

@@ -63,7 +63,10 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
     if (t == 0) mbar_init(&sBar[1], 1);
     tc_setup(tcs, &sSlot, &sBar[0]);
     // test hook (see the flat kernel)
-    if (P.tc_stall && !mbar_wait_bounded(&sBar[1], 0, 1 << 14)) stalled = 1;
+    if (P.tc_stall == 1 && !mbar_wait_bounded(&sBar[1], 0, 1 << 14)) stalled = 1;
+    // test hook 2: the first MMA completion wait gives up at once, so the
+    // CTA reaches its tear-down with a committed phase to drain
+    if (P.tc_stall == 2) tcs.first_limit = 0;
     __syncwarp();
   }
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;

@@ -72,7 +72,10 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
     tc_setup(tcs, &sSlot, &sBar[0]);
     // test hook: a bounded wait on a barrier that nothing arrives on runs
     // out; it is reported like a failed MMA wait but leaves the work intact
-    if (P.tc_stall && !mbar_wait_bounded(&sBar[1], 0, 1 << 14)) stalled = 1;
+    if (P.tc_stall == 1 && !mbar_wait_bounded(&sBar[1], 0, 1 << 14)) stalled = 1;
+    // test hook 2: the first MMA completion wait gives up at once, so the
+    // CTA reaches its tear-down with a committed phase to drain
+    if (P.tc_stall == 2) tcs.first_limit = 0;
     __syncwarp();
   }
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;

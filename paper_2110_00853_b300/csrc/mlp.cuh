@@ -107,8 +107,10 @@ constexpr int kTcWaitLimit = 1 << 20;       // mbarrier tries before giving up
 struct TcState {
   uint32_t tmem;    // TMEM base address of this CTA's columns
   uint64_t *mbar;   // MMA completion barrier (shared memory)
-  uint32_t parity;  // parity of the next phase to complete
-  int err;          // sticky: a wait gave up (results of this CTA invalid)
+  uint32_t parity;  // parity of the oldest committed phase this thread has not seen complete
+  int pending;      // thread 0: a committed phase it has not seen complete (its wait gave up)
+  int err;          // sticky and CTA-uniform after each group opening: a wait gave up
+  int first_limit;  // tries of the next completion wait (test hook: 0 gives up at once)
 };
 
 // Write this thread's row of the A buffer for layer 1: the 13 inputs (BF16),
@@ -141,19 +143,22 @@ __device__ __forceinline__ void tc_setup(TcState &s, uint32_t *slot, uint64_t *m
   s.tmem = *slot;
   s.mbar = mbar;
   s.parity = 0;
+  s.pending = 0;
   s.err = 0;
+  s.first_limit = kTcWaitLimit;
 }
 
-// Tear-down: wait (bounded) until every MMA the CTA issued has completed,
-// free the TMEM columns, and count the CTA in *err_count if any wait gave up.
-// All threads must call it.
+// Tear-down: make sure no MMA of the CTA is still running, free the TMEM
+// columns, and count the CTA once in *err_count if any wait gave up.  Thread
+// 0 issues every commit and waits for each, so at most one committed phase
+// can be unseen (its wait gave up); commits complete in order and none
+// follows it, so a bounded wait on that phase drains the CTA's MMAs before
+// the columns are freed.  All threads must call it.
 __device__ __forceinline__ void tc_teardown(TcState &s, int *err_count, uint32_t ncols = kTcCols) {
   tc_fence_before_sync();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    tc_fence_after_sync();
-    tc_commit(s.mbar);
-    if (!mbar_wait_bounded(s.mbar, s.parity, kTcWaitLimit)) s.err = 1;
+  s.err = __syncthreads_or(s.err);
+  if (threadIdx.x == 0 && s.pending) {
+    if (mbar_wait_bounded(s.mbar, s.parity, kTcWaitLimit)) s.pending = 0;
   }
   tc_fence_before_sync();
   __syncthreads();
@@ -161,24 +166,57 @@ __device__ __forceinline__ void tc_teardown(TcState &s, int *err_count, uint32_t
     tc_fence_after_sync();
     tc_dealloc(s.tmem, ncols);
   }
-  if (s.err) atomicAdd(err_count, 1);
+  if (threadIdx.x == 0 && s.err) atomicAdd(err_count, 1);
 }
 
 // One MMA group of the CTA: every thread makes its shared-memory operand
-// writes visible to the tensor core and meets the others (tc_group_open);
-// thread 0 then issues the group's MMAs; tc_group_close commits them to the
-// barrier and waits (bounded) for their completion in every thread.
-__device__ __forceinline__ void tc_group_open() {
+// writes visible to the tensor core and meets the others (tc_group_open,
+// which also makes the error flag CTA-uniform); thread 0 then issues the
+// group's MMAs unless a wait has given up; tc_group_close commits them to the
+// barrier and waits (bounded) for their completion in every thread.  A wait
+// that gives up keeps its phase as the one to drain and sets the error flag;
+// later groups of the CTA issue nothing and wait for nothing.
+__device__ __forceinline__ void tc_group_open(TcState &s) {
   fence_proxy_async_smem();
   tc_fence_before_sync();
-  __syncthreads();
+  s.err = __syncthreads_or(s.err);
 }
 __device__ __forceinline__ void tc_group_close(TcState &s) {
-  if (threadIdx.x == 0) tc_commit(s.mbar);
-  if (!mbar_wait_bounded(s.mbar, s.parity, s.err ? 1 : kTcWaitLimit)) s.err = 1;
-  s.parity ^= 1u;
-  __syncwarp();
+  if (s.err) return;
+  if (threadIdx.x == 0) {
+    tc_commit(s.mbar);
+    s.pending = 1;
+  }
+  const int limit = s.first_limit;
+  s.first_limit = kTcWaitLimit;
+  if (mbar_wait_bounded(s.mbar, s.parity, limit)) {
+    s.parity ^= 1u;
+    s.pending = 0;
+  } else {
+    s.err = 1;
+  }
+  // warp-uniform, so that the warp-collective TMEM loads that follow are
+  // skipped (tc_ld32_if) by whole warps
+  s.err = __any_sync(0xffffffffu, s.err);
   tc_fence_after_sync();
+}
+
+// TMEM loads of a group's results, skipped (zeros) once a wait has given up:
+// the accumulator may then still be written by a running MMA.
+__device__ __forceinline__ void tc_ld32_if(const TcState &s, uint32_t taddr, float v[32]) {
+  if (!s.err) {
+    tc_ld32(taddr, v);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = 0.f;
+  }
+}
+__device__ __forceinline__ void tc_ld2_if(const TcState &s, uint32_t taddr, float &v0, float &v1) {
+  if (!s.err) {
+    tc_ld2(taddr, v0, v1);
+  } else {
+    v0 = v1 = 0.f;
+  }
 }
 
 // Forward pass of the CTA's 128 rows; (y0, y1) of this thread's row.  All
@@ -192,9 +230,7 @@ __device__ __forceinline__ void mlp_tc_forward(const MlpTc &W, __nv_bfloat16 *A,
   constexpr uint32_t kSboA = 8 * 16 * kTcKG, kSbo1 = 8 * 16 * kTcKG1;
 #pragma unroll 1
   for (int layer = 0; layer < 3; ++layer) {
-    fence_proxy_async_smem();
-    tc_fence_before_sync();
-    __syncthreads();
+    tc_group_open(s);
     if (t == 0 && !s.err) {
       tc_fence_after_sync();
       if (layer == 0) {
@@ -207,17 +243,13 @@ __device__ __forceinline__ void mlp_tc_forward(const MlpTc &W, __nv_bfloat16 *A,
           tc_mma(s.tmem, tc_sdesc(A + ks * 128, 128, kSboA), tc_sdesc(B + ks * 128, 128, kSboA), idesc,
                  ks > 0 ? 1u : 0u);
       }
-      tc_commit(s.mbar);
     }
-    if (!mbar_wait_bounded(s.mbar, s.parity, s.err ? 1 : kTcWaitLimit)) s.err = 1;
-    s.parity ^= 1u;
-    __syncwarp();  // the TMEM loads below are warp-collective
-    tc_fence_after_sync();
+    tc_group_close(s);  // the TMEM loads below are warp-collective: close ends with __syncwarp
     if (layer < 2) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         float v[32];
-        tc_ld32(lane_base + 32 * h, v);
+        tc_ld32_if(s, lane_base + 32 * h, v);
         uint32_t w[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) w[q] = silu2_bf16(v[2 * q], v[2 * q + 1]);
@@ -227,7 +259,7 @@ __device__ __forceinline__ void mlp_tc_forward(const MlpTc &W, __nv_bfloat16 *A,
               make_uint4(w[4 * kk], w[4 * kk + 1], w[4 * kk + 2], w[4 * kk + 3]);
       }
     } else {
-      tc_ld2(lane_base, y0, y1);
+      tc_ld2_if(s, lane_base, y0, y1);
     }
   }
 }

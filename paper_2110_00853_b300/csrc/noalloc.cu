@@ -9,10 +9,13 @@
 // in the file-scope device array below instead of a handle's buffer.
 //
 // The array is shared by every call in the process (and every GPU that loads
-// the library holds one copy until exit).  Each block overwrites its own
-// slots before they are read, so nothing needs clearing between calls, but
-// calls that overlap on the GPU race on the array and must be serialised by
-// the caller (same stream, or ordered by events).
+// the library holds one copy until exit).  Its device address is looked up
+// once per device and cached; it belongs to that device's primary context,
+// so after cudaDeviceReset the library must be unloaded and loaded again (a
+// new process) before this entry point is used on that device.  Each block
+// overwrites its own slots before they are read, so nothing needs clearing
+// between calls, but calls that overlap on the GPU race on the array and
+// must be serialised by the caller (same stream, or ordered by events).
 #include <math.h>
 
 #include <mutex>
@@ -125,16 +128,27 @@ extern "C" cmles_status cmles_budgets_noalloc(const double *Q_dev, long long num
     }
     scratch = g_scratch[dev];
   }
-  const int Nq = N + 1, Np = Nq * Nq * Nq;
+  const int Nq = N + 1;
+  int Np = Nq * Nq * Nq;
   double w1[8];
   lgl_weights_fixed(N, w1);
   QuadWeights W;
   for (int k = 0; k < Nq; ++k)
     for (int j = 0; j < Nq; ++j)
       for (int i = 0; i < Nq; ++i) W.w[i + Nq * (j + Nq * k)] = w1[i] * w1[j] * w1[k];
-  const int nblocks = (int)((num_elements + kElemsPerBlock - 1) / kElemsPerBlock);
+  int nblocks = (int)((num_elements + kElemsPerBlock - 1) / kElemsPerBlock);
   cudaStream_t s = (cudaStream_t)stream;
-  k_budget_noalloc_partial<<<nblocks, kThreads, 0, s>>>(Q_dev, num_elements, Np, W, jacobian, scratch);
-  k_budget_noalloc_final<<<1, 32, 0, s>>>(scratch, nblocks, out_dev);
-  return cudaGetLastError() == cudaSuccess ? CMLES_OK : CMLES_ERR_CUDA;
+  // the status of each launch is taken from cudaLaunchKernel itself, not
+  // from cudaGetLastError, so an earlier non-sticky error of other code on
+  // this thread is neither reported here nor cleared (a sticky fault of the
+  // context is reported by every call)
+  long long E = num_elements;
+  void *args1[] = {(void *)&Q_dev, (void *)&E, (void *)&Np, (void *)&W, (void *)&jacobian, (void *)&scratch};
+  if (cudaLaunchKernel((const void *)k_budget_noalloc_partial, dim3(nblocks), dim3(kThreads), args1, 0, s) !=
+      cudaSuccess)
+    return CMLES_ERR_CUDA;
+  void *args2[] = {(void *)&scratch, (void *)&nblocks, (void *)&out_dev};
+  if (cudaLaunchKernel((const void *)k_budget_noalloc_final, dim3(1), dim3(32), args2, 0, s) != cudaSuccess)
+    return CMLES_ERR_CUDA;
+  return CMLES_OK;
 }

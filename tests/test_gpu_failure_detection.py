@@ -108,10 +108,46 @@ def test_tensor_core_wait_timeout_is_reported_and_cleared(orc):
     G.test_stall_tc(True)
     R1 = G.tendency(Qd).cpu().numpy()
     d = G.diagnostics(raise_on_error=False)
-    assert d["status"] == ERR_TIMEOUT and d["tc_timeouts"] > 0
+    # one CTA per element here (96 elements, fewer than the persistent grid),
+    # each counted once
+    assert d["status"] == ERR_TIMEOUT and d["tc_timeouts"] == G.E, (d["tc_timeouts"], G.E)
     assert np.array_equal(R1, R0)
     G.test_stall_tc(False)
     R2 = G.tendency(Qd).cpu().numpy()
     d = G.diagnostics(raise_on_error=False)
     assert d["status"] == 0 and d["tc_timeouts"] == 0
     assert np.array_equal(R2, R0)
+
+
+def test_tensor_core_drain_after_a_wait_gives_up(orc):
+    """A CTA whose MMA completion wait gives up while its MMA is still in
+    flight (test hook mode 2: the first wait of each CTA makes no try) issues
+    no further MMA, skips its Tensor Memory reads, and at its tear-down waits
+    (bounded) for that MMA before freeing the columns.  The launch reports
+    CMLES_ERR_TIMEOUT with every CTA counted once; the context stays usable
+    and the next tendency, with the hook off, is bit-identical to one taken
+    before (its CTAs allocate the same Tensor Memory columns)."""
+    from paper_2110_00853_b300 import cmles
+    m = I.sub_mesh("c2", 4, 3, 8)
+    ph = I.physics("c2", closure="mlp")
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case("c2"))
+    rng = np.random.default_rng(5)
+    G = cmles.Solver(m, ph, precision="fp32")
+    G.set_reference(_levels(rr, m), _levels(pr, m), _levels(Q[:, 5] / Q[:, 0], m))
+    flat = np.concatenate([rng.normal(size=5186) * 0.1, np.ones(13), [1.0, 1.0]]).astype(np.float32)
+    G.set_closure_weights(flat)
+    Qd = torch.from_numpy(Q).cuda()
+    R0 = G.tendency(Qd).cpu().numpy()
+    assert G.diagnostics(raise_on_error=False)["status"] == 0
+    for _ in range(2):
+        G.test_stall_tc(2)
+        G.tendency(Qd)
+        d = G.diagnostics(raise_on_error=False)
+        assert d["status"] == ERR_TIMEOUT and d["tc_timeouts"] == G.E, (d["tc_timeouts"], G.E)
+        G.test_stall_tc(0)
+        R2 = G.tendency(Qd).cpu().numpy()
+        d = G.diagnostics(raise_on_error=False)
+        assert d["status"] == 0 and d["tc_timeouts"] == 0
+        assert np.array_equal(R2, R0)
+    with pytest.raises(cmles.CmlesError):
+        G.test_stall_tc(3)
