@@ -275,16 +275,27 @@ cmles_status cmles_mlp_adam(float *params_dev, const float *grad_dev, float *m_d
                             float beta1, float beta2, float eps, void *stream);
 
 /* Training samples for the learned closure from the handle's current state
- * (a fine-resolution run): the fine field is top-hat filtered, width one
- * coarse node spacing, onto the nodes of the mesh coarser by `factor` in every
- * direction (element counts must be multiples of factor).  Per coarse node
- * (coarse element-major, node-minor): X_dev[13] = filtered du_i/dx_j (index
- * 3i+j), filtered d theta_v/dx_j (3), Delta_c; T_dev[2] = least-squares eddy
- * viscosity and diffusivity max(0, -tau:S/(2 S:S)), max(0, -tau_th.g/|g|^2)
- * from the filtered subgrid stress and theta_v flux.  *n_out receives the
- * sample count; CMLES_ERR_ARG if capacity is smaller. */
-cmles_status cmles_closure_samples(cmles_handle h, int factor, float *X_dev, float *T_dev, long long capacity,
-                                   long long *n_out);
+ * (a fine-resolution run; flat meshes).  The paper has no learned closure;
+ * these targets extend its Sec. 4.  The fine field's velocity and theta_v
+ * (FP64 thermodynamics of Sec. 2) are top-hat filtered, width one coarse node
+ * spacing H / N, onto the nodes of the mesh coarser by `factor` in every
+ * direction (element counts must be multiples of factor): each fine node (a
+ * node on a shared face once per element) within H / (2N) of the coarse node
+ * in every direction, the edge included, weighs its LGL quadrature weight;
+ * periodic directions wrap, walls cut the box.  Per coarse node (coarse
+ * element-major, node-minor): X_dev[13] = filtered du_i/dx_j (index 3i+j,
+ * element-local derivatives), filtered d theta_v/dx_j (3), Delta_c =
+ * (H_x H_y H_z)^(1/3) / N; T_dev[2] = least-squares eddy viscosity and
+ * diffusivity max(0, -tau:S/(2 S:S)), max(0, -tau_th.g/|g|^2) from the
+ * filtered subgrid stress tau_ij = <u_i u_j> - <u_i><u_j> and theta_v flux
+ * tau_th,j = <u_j th> - <u_j><th>, S the symmetric part of the filtered
+ * velocity gradient and g the filtered theta_v gradient (0 where S or g
+ * vanishes); thv_dev (may be NULL) = filtered theta_v.  Device FP32 outputs;
+ * the call allocates its FP64 scratch (4 values per fine node) on the
+ * handle's stream.  *n_out receives the sample count; CMLES_ERR_ARG if
+ * capacity is smaller or the mesh is warped. */
+cmles_status cmles_closure_samples(cmles_handle h, int factor, float *X_dev, float *T_dev, float *thv_dev,
+                                   long long capacity, long long *n_out);
 
 /* Per-kernel timing: when enabled, every launch is bracketed by CUDA events
  * on the handle's stream; cmles_kernel_times returns, for the kernels

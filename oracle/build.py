@@ -10,7 +10,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["lgl.c", "thermo.c", "dg.c", "cases.c", "mlp.c", "filter.c", "hevi.c"]
+SOURCES = ["lgl.c", "thermo.c", "dg.c", "cases.c", "mlp.c", "filter.c", "hevi.c", "closure.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

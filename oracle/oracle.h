@@ -214,4 +214,15 @@ double orc_mlp_loss_grad(int n, const double *X, const double *T, const double *
 void orc_adam(int n, double *theta, const double *g, double *m, double *v, int t,
               double lr, double beta1, double beta2, double eps);
 
+/* ---- learned-closure training samples (closure.c; the paper has no learned
+ * closure: these follow the readings stated there) ---- */
+/* u, v, w and theta_v of every node's thermodynamic state, prim[E][4][Np]. */
+void orc_closure_primitives(const orc_solver *s, const double *Q, double *prim);
+/* Top-hat filter of the primitive field onto the nodes of the mesh coarser by
+ * `factor` (flat meshes): X[n][13] network inputs, T[n][2] least-squares
+ * (nu*, kappa*), thv_bar[n] filtered theta_v (may be NULL).  Returns the
+ * sample count, or -1 if the element counts are not multiples of factor. */
+long long orc_closure_samples(const orc_solver *s, const double *prim, int factor, double *X, double *T,
+                              double *thv_bar);
+
 #endif

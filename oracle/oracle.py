@@ -56,6 +56,11 @@ class Case(C.Structure):
                 ("qt_H", C.c_double)]
 
 
+class ThermoState(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("rho", "u0", "u1", "u2", "qt", "etot", "I", "T", "ql", "qv", "Rm", "cvm",
+                                          "cpm", "p", "c", "htot", "theta", "thetav")] + [("newton", C.c_int)]
+
+
 CLOSURE = {"none": 0, "sl": 1, "mlp": 2, "vreman": 3}
 FLUX = {"rusanov": 0, "hllc": 1, "roe": 2}
 
@@ -124,6 +129,12 @@ def _declare(L):
     L.orc_bf16.restype = C.c_double
     L.orc_mlp_loss_grad.argtypes = [C.c_int, _DP, _DP] + [_DP] * 6 + [_DP] * 6
     L.orc_mlp_loss_grad.restype = C.c_double
+    L.orc_thermo.argtypes = [C.POINTER(Params), _DP, C.c_double, C.POINTER(ThermoState)]
+    L.orc_thermo.restype = C.c_int
+    L.orc_closure_primitives.argtypes = [C.c_void_p, _DP, _DP]
+    L.orc_closure_primitives.restype = None
+    L.orc_closure_samples.argtypes = [C.c_void_p, _DP, C.c_int, _DP, _DP, _DP]
+    L.orc_closure_samples.restype = C.c_longlong
     L.orc_adam.argtypes = [C.c_int, _DP, _DP, _DP, _DP, C.c_int, C.c_double, C.c_double, C.c_double,
                            C.c_double]
 
@@ -244,6 +255,17 @@ def smagorinsky(P, gu, dthvdz, thv, Delta):
 def vreman(P, gu, dthvdz, thv, Dm):
     return lib().orc_vreman(C.byref(P), _p(np.ascontiguousarray(gu, float).ravel()), dthvdz, thv,
                             _p(np.ascontiguousarray(Dm, float).ravel()))
+
+
+def thermo(P, Y, z):
+    """The pointwise thermodynamic state of conserved variables Y at height z
+    (Sec. 2): a dict of rho, u, q_t, e_tot, I, T, q_l, q_v, R_m, c_vm, c_pm,
+    p, c, h_tot, theta, theta_v and the Newton iteration count."""
+    st = ThermoState()
+    lib().orc_thermo(C.byref(P), _p(np.ascontiguousarray(Y, float)), z, C.byref(st))
+    d = {n: getattr(st, n) for n, _ in ThermoState._fields_}
+    d["u"] = np.array([d.pop("u0"), d.pop("u1"), d.pop("u2")])
+    return d
 
 
 def uniform(seed, counter):
@@ -484,6 +506,27 @@ class Solver:
         out = np.zeros(6)
         bad = lib().orc_budgets(self.h, _p(np.ascontiguousarray(Q, float)), _p(out))
         return out, bool(bad)
+
+    def closure_primitives(self, Q):
+        """u, v, w, theta_v at every node, [E][4][Np] (closure.c step 1)."""
+        prim = np.zeros((self.E, 4, self.Np))
+        lib().orc_closure_primitives(self.h, _p(np.ascontiguousarray(Q, float)), _p(prim))
+        return prim
+
+    def closure_samples_from_primitives(self, prim, factor=4):
+        """(X[n][13], T[n][2], thv_bar[n]) of the top-hat filter onto the mesh
+        coarser by `factor` (closure.c steps 2-5)."""
+        m = self.mesh
+        n = (m.nex // factor) * (m.ney // factor) * (m.nez // factor) * self.Np
+        X, T, th = np.zeros((n, 13)), np.zeros((n, 2)), np.zeros(n)
+        got = lib().orc_closure_samples(self.h, _p(np.ascontiguousarray(prim, float)), factor, _p(X), _p(T), _p(th))
+        if got != n:
+            raise ValueError("element counts must be multiples of factor on a flat mesh")
+        return X, T, th
+
+    def closure_samples(self, Q, factor=4):
+        """Training samples of the learned closure from the state Q."""
+        return self.closure_samples_from_primitives(self.closure_primitives(Q), factor)
 
     def favre_profiles(self, Q):
         nl = self.mesh.nez * (self.N + 1)

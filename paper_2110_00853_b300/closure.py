@@ -31,10 +31,11 @@ def init_params(seed=0, in_scale=None, out_scale=(1.0, 1.0), b3=(0.0, 0.0)):
 
 
 def fine_run_samples(torch, name="c4fine", steps=20, dt=0.005, factor=4, nmodes=2000, kmax=200, seed=4,
-                     sub=None):
+                     sub=None, with_thv=False):
     """Run the fine mesh (FP32 path, Smagorinsky-Lilly) from a state with a
     k^-5/3 random-phase velocity field that reaches the subgrid scales of the
-    coarse mesh, then filter it onto the coarse nodes."""
+    coarse mesh, then filter it onto the coarse nodes: (X, T), and the
+    filtered theta_v with with_thv."""
     mesh = I.mesh(name) if sub is None else I.sub_mesh(name, *sub)
     phys = I.physics(name)
     phys["dt"] = dt
@@ -43,9 +44,9 @@ def fine_run_samples(torch, name="c4fine", steps=20, dt=0.005, factor=4, nmodes=
     G = cmles.Solver(mesh, phys, precision="fp32")
     G.init_case(case)
     G.step(steps)
-    X, T = G.closure_samples(factor)
+    out = G.closure_samples(factor, with_thv=with_thv)
     G.close()
-    return X, T
+    return out
 
 
 def normalisation(X, T):

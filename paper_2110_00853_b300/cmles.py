@@ -100,7 +100,7 @@ def load(path=LIB_PATH):
     L.cmles_kernel_times.argtypes = [_H, C.POINTER(C.c_longlong), _DP, C.POINTER(C.c_longlong)]
     L.cmles_budgets_noalloc.argtypes = [_VP, C.c_longlong, C.c_int, C.c_double, _VP, _VP]
     L.cmles_set_closure_weights_device.argtypes = [_H, _VP]
-    L.cmles_closure_samples.argtypes = [_H, C.c_int, _VP, _VP, C.c_longlong, C.POINTER(C.c_longlong)]
+    L.cmles_closure_samples.argtypes = [_H, C.c_int, _VP, _VP, _VP, C.c_longlong, C.POINTER(C.c_longlong)]
     L.cmles_mlp_forward.argtypes = [_VP, _VP, _VP, C.c_longlong, _VP]
     L.cmles_mlp_loss_grad.argtypes = [_VP, _VP, _VP, C.c_longlong, _VP, _VP, _VP]
     L.cmles_mlp_adam.argtypes = [_VP, _VP, _VP, _VP, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, _VP]
@@ -333,17 +333,20 @@ class Solver:
         assert params.is_cuda and params.dtype == self.torch.float32 and params.numel() == MLP_PARAMS
         self._check(self.L.cmles_set_closure_weights_device(self.h, C.c_void_p(params.data_ptr())))
 
-    def closure_samples(self, factor=4):
-        """(X[n][13], T[n][2]) training samples filtered from the current state."""
+    def closure_samples(self, factor=4, with_thv=False):
+        """(X[n][13], T[n][2]) training samples filtered from the current
+        state; with_thv also returns the filtered theta_v [n]."""
         torch = self.torch
         m = self.mesh_d
         n = (m["nex"] // factor) * (m["ney"] // factor) * (m["nez"] // factor) * self.Np
         X = torch.empty((n, 13), dtype=torch.float32, device="cuda")
         T = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+        th = torch.empty(n, dtype=torch.float32, device="cuda") if with_thv else None
         cnt = C.c_longlong()
         self._check(self.L.cmles_closure_samples(self.h, factor, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
-                                                 n, C.byref(cnt)))
-        return X, T
+                                                 None if th is None else C.c_void_p(th.data_ptr()), n,
+                                                 C.byref(cnt)))
+        return (X, T, th) if with_thv else (X, T)
 
     def enable_timing(self, on=True):
         self._check(self.L.cmles_enable_timing(self.h, int(on)))

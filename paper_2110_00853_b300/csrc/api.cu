@@ -1513,8 +1513,8 @@ cmles_status cmles_set_closure_weights_device(cmles_handle h, const float *param
   return CMLES_OK;
 }
 
-cmles_status cmles_closure_samples(cmles_handle h, int factor, float *X_dev, float *T_dev, long long capacity,
-                                   long long *n_out) {
+cmles_status cmles_closure_samples(cmles_handle h, int factor, float *X_dev, float *T_dev, float *thv_dev,
+                                   long long capacity, long long *n_out) {
   if (!h || !X_dev || !T_dev || factor < 1) return fail(h, CMLES_ERR_ARG, "cmles_closure_samples: bad argument");
   if (h->curved) return fail(h, CMLES_ERR_ARG, "cmles_closure_samples: flat meshes only");
   const cmles_mesh &m = h->mesh;
@@ -1526,7 +1526,7 @@ cmles_status cmles_closure_samples(cmles_handle h, int factor, float *X_dev, flo
   {
     LaunchScope ls(h, 2, 3);
     CK(launch_closure_samples(h->Q[h->cur], h->K, h->N, h->xi.data(), h->w.data(), h->D.data(), factor,
-                              m.periodic, X_dev, T_dev, nc, h->stream));
+                              m.periodic, X_dev, T_dev, thv_dev, nc, h->stream));
   }
   return CMLES_OK;
 }

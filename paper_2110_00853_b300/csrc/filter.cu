@@ -11,7 +11,12 @@
 //   nu* = max(0, -tau:S / (2 S:S)),   kappa* = max(0, -tau_th.g / |g|^2),
 // and the network inputs are the filtered velocity gradients (9), the
 // filtered theta_v gradient (3) and Delta_c.  Fine-node derivatives are the
-// element-local LGL derivatives (the BR1 face term is left out here).
+// element-local LGL derivatives (the BR1 face term is left out here).  Fine
+// nodes on a shared face count once per element; a node within 1e-9
+// (relative) of the box edge counts as inside.  The primitive fields are kept
+// in FP64 (scratch memory of the call): the subgrid moments are small
+// differences of large ones (<u u> - <u><u>), which FP32 inputs would leave
+// with only a few correct digits.
 #include <math.h>
 #include <string.h>
 
@@ -22,9 +27,9 @@
 
 namespace cmles {
 
-// u, v, w, theta_v at every fine node (FP64 thermodynamics), FP32 output [E][4][Np].
+// u, v, w, theta_v at every fine node (FP64 thermodynamics), [E][4][Np].
 template <bool MOIST>
-__global__ void k_primitives(const double *__restrict__ Q, float *__restrict__ prim, const KParams P, int N) {
+__global__ void k_primitives(const double *__restrict__ Q, double *__restrict__ prim, const KParams P, int N) {
   const int Nq = N + 1, Np = Nq * Nq * Nq;
   const long long nodes = (long long)P.E * Np;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nodes;
@@ -38,11 +43,11 @@ __global__ void k_primitives(const double *__restrict__ Q, float *__restrict__ p
     Th64 s;
     int fail = 0;
     thermo64<MOIST>(P, Y, node_z(P, ez, k), ez * Nq + k, s, fail);
-    float *o = prim + e * 4 * Np + n;
-    o[0] = (float)s.u[0];
-    o[Np] = (float)s.u[1];
-    o[2 * Np] = (float)s.u[2];
-    o[3 * Np] = (float)s.thv;
+    double *o = prim + e * 4 * Np + n;
+    o[0] = s.u[0];
+    o[Np] = s.u[1];
+    o[2 * Np] = s.u[2];
+    o[3 * Np] = s.thv;
   }
 }
 
@@ -53,8 +58,8 @@ struct FilterGeom {
   double Delta_c;
 };
 
-__global__ void k_filter_samples(const float *__restrict__ prim, const FilterGeom G, float *__restrict__ X,
-                                 float *__restrict__ T, long long ncoarse) {
+__global__ void k_filter_samples(const double *__restrict__ prim, const FilterGeom G, float *__restrict__ X,
+                                 float *__restrict__ T, float *__restrict__ thv, long long ncoarse) {
   const int N = G.N, Nq = N + 1, Np = Nq * Nq * Nq;
   const int cnx = G.nex / G.factor, cny = G.ney / G.factor;
   const int nel[3] = {G.nex, G.ney, G.nez};
@@ -87,7 +92,7 @@ __global__ void k_filter_samples(const float *__restrict__ prim, const FilterGeo
           int fw[3];
           for (int d = 0; d < 3; ++d) fw[d] = ((f[d] % nel[d]) + nel[d]) % nel[d];
           const long long fe = fw[0] + (long long)G.nex * (fw[1] + (long long)G.ney * fw[2]);
-          const float *pe = prim + fe * 4 * Np;
+          const double *pe = prim + fe * 4 * Np;
           for (int c = 0; c < Nq; ++c)
             for (int bb = 0; bb < Nq; ++bb)
               for (int a = 0; a < Nq; ++a) {
@@ -161,15 +166,16 @@ __global__ void k_filter_samples(const float *__restrict__ prim, const FilterGeo
     x[12] = (float)G.Delta_c;
     T[q * 2] = (float)nu;
     T[q * 2 + 1] = (float)ka;
+    if (thv) thv[q] = (float)thb;
   }
 }
 
 cudaError_t launch_closure_samples(const double *Q, const KParams &P, int N, const double *xi, const double *w,
                                    const double *D, int factor, const int periodic[3], float *X, float *T,
-                                   long long ncoarse, cudaStream_t s) {
+                                   float *thv, long long ncoarse, cudaStream_t s) {
   const int Nq = N + 1, Np = Nq * Nq * Nq;
-  float *prim = nullptr;
-  cudaError_t e = cudaMallocAsync((void **)&prim, (size_t)P.E * 4 * Np * sizeof(float), s);
+  double *prim = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&prim, (size_t)P.E * 4 * Np * sizeof(double), s);
   if (e != cudaSuccess) return e;
   const long long nodes = (long long)P.E * Np;
   int blocks = (int)((nodes + 255) / 256);
@@ -200,7 +206,7 @@ cudaError_t launch_closure_samples(const double *Q, const KParams &P, int N, con
   G.Delta_c = cbrt(factor * P.hx * factor * P.hy * factor * P.hz) / N;
   int cb = (int)((ncoarse + 127) / 128);
   if (cb > 148 * 16) cb = 148 * 16;
-  k_filter_samples<<<cb, 128, 0, s>>>(prim, G, X, T, ncoarse);
+  k_filter_samples<<<cb, 128, 0, s>>>(prim, G, X, T, thv, ncoarse);
   e = cudaGetLastError();
   cudaFreeAsync(prim, s);
   return e;

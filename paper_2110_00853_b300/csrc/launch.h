@@ -86,7 +86,7 @@ cudaError_t launch_pack_mlp(const float *params_dev, MlpPacked *out, cudaStream_
 // Closure training samples from a fine run (filter.cu)
 cudaError_t launch_closure_samples(const double *Q, const KParams &P, int N, const double *xi, const double *w,
                                    const double *D, int factor, const int periodic[3], float *X, float *T,
-                                   long long ncoarse, cudaStream_t s);
+                                   float *thv, long long ncoarse, cudaStream_t s);
 
 // Diagnostics and set-up (aux_kernels.cu)
 // Budgets: partial sums per block into partials[nblocks][7] (6 integrals and a

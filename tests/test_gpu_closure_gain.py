@@ -7,7 +7,7 @@ closure network is trained on one such run with the library's BF16
 tensor-core forward/backward kernels and Adam, and evaluated on a second run with
 different random phases against the filtered subgrid targets, next to
 Smagorinsky-Lilly (C_s = 0.21 with the Richardson correction) evaluated on the
-same filtered gradients.  A priori test: the error measure is the relative L2
+same filtered gradients and each sample's filtered theta_v.  A priori test: the error measure is the relative L2
 distance of the predicted eddy viscosity / diffusivity from the least-squares
 targets nu*, kappa*.
 """
@@ -18,7 +18,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _sl(X, Cs=0.21, Prt=1.0 / 3.0, g=9.81, thv=300.0):
+def _sl(X, thv, Cs=0.21, Prt=1.0 / 3.0, g=9.81):
+    """Smagorinsky-Lilly with the Richardson correction (Eqs. smago,
+    richardson) on the filtered gradients of each sample, with the sample's
+    own filtered theta_v in the Richardson number."""
     gu = X[:, :9].reshape(-1, 3, 3)
     S = 0.5 * (gu + gu.transpose(0, 2, 1))
     S2 = 2.0 * (S ** 2).sum(axis=(1, 2))
@@ -37,14 +40,14 @@ def test_trained_closure_beats_smagorinsky_a_priori():
     from paper_2110_00853_b300 import closure
     sub = (64, 64, 32)
     Xtr, Ttr = closure.fine_run_samples(torch, steps=20, seed=4, sub=sub)
-    Xte, Tte = closure.fine_run_samples(torch, steps=20, seed=44, sub=sub)
+    Xte, Tte, thv_te = closure.fine_run_samples(torch, steps=20, seed=44, sub=sub, with_thv=True)
     assert Xtr.shape[0] == 16 * 16 * 8 * 125
     assert bool(torch.isfinite(Xtr).all()) and bool(torch.isfinite(Ttr).all())
     P, hist = closure.fit(torch, Xtr, Ttr, steps=1500, batch=65536, lr=2e-3, log_every=100)
     nu_m, ka_m = (a.cpu().numpy().astype(np.float64) for a in closure.predict(torch, P, Xte))
     x = Xte.cpu().numpy().astype(np.float64)
     t = Tte.cpu().numpy().astype(np.float64)
-    nu_sl, ka_sl = _sl(x)
+    nu_sl, ka_sl = _sl(x, thv_te.cpu().numpy().astype(np.float64))
     e = dict(nu_mlp=_rel(nu_m, t[:, 0]), nu_sl=_rel(nu_sl, t[:, 0]), ka_mlp=_rel(ka_m, t[:, 1]),
              ka_sl=_rel(ka_sl, t[:, 1]))
     print("loss history", hist)

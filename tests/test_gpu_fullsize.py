@@ -96,6 +96,13 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def _node_bound(got, want, tol, label):
+    """Node by node: max |GPU - oracle| <= 10 tol max |oracle| (a wrong value
+    on a few nodes can hide in a norm over many)."""
+    err = np.abs(got - want).max()
+    assert err <= 10 * tol * np.abs(want).max(), (label, err, np.abs(want).max())
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_fullsize_tendency_sampled(orc, precision):
     from paper_2110_00853_b300 import cmles
@@ -122,8 +129,10 @@ def test_fullsize_tendency_sampled(orc, precision):
     torch.cuda.empty_cache()
     errs = [_rel(got[:, v], want[:, v]) for v in range(6)]
     print(precision, "full-size sampled tendency rel L2", errs)
+    tol = 1e-12 if precision == "fp64" else 1e-5
     for v in range(6):
-        assert errs[v] <= (1e-12 if precision == "fp64" else 1e-5), (v, errs)
+        assert errs[v] <= tol, (v, errs)
+        _node_bound(got[:, v], want[:, v], tol, v)
 
 
 def test_fullsize_lsrk_step_sampled(orc):
@@ -221,6 +230,7 @@ def test_fullsize_tendency_learned_closure(orc):
     print("closure contribution rel L2", errs_c)
     for v in range(6):
         assert errs[v] <= 1e-4, (v, errs)
+        _node_bound(got[:, v], want[:, v], 1e-4, v)
     # the closure's own contribution (measured 3e-5 momentum, 4e-4 energy,
     # 2e-4 water): FP32 gradients and BF16 activation flips; the mass
     # equation's share (the water diffusion, 1e-5 of its tendency) is below
