@@ -69,19 +69,62 @@ VARIANTS = {"fp32acc64_mlp": ("fp32", "mlp", "rusanov", "lsrk54"), "fp32acc64_sl
             "fp64_sl_hevi": ("fp64", "sl", "rusanov", "ark2_hevi"),
             "fp32acc64_mlp_hevi": ("fp32", "mlp", "rusanov", "ark2_hevi")}
 DTYPE = {"fp32": "f32", "fp64": "f64"}
-# DRAM bytes per node of one launch (dram__bytes_read.sum + dram__bytes_write.sum
-# from one ncu capture on a 40 x 40 x 20-element sub-box of the box, 4M nodes,
-# divided by the nodes; the traffic is per node, so it scales to the full box by
-# the node count).  Only kernels whose every launch does the same work: the
-# gradient pass.  Remove an entry when its kernel changes.
-TRAFFIC_B_PER_NODE = {("fp32acc64_mlp", "grad"): 85.20, ("fp32acc64_sl", "grad"): 83.38,
-                      ("fp64_sl", "grad"): 183.8}
-# Warp instructions per element of the FP32 gradient passes (ncu
-# smsp__inst_executed.sum over the elements of the same capture), for the
-# issue-rate view of those passes, which are bound by instruction issue rather
-# than by HBM: peak = 148 SMs x 4 schedulers x the maximum SM clock, one warp
-# instruction per scheduler and clock.  Remove an entry when its kernel changes.
-WARP_INST_PER_ELEM = {("fp32acc64_mlp", "grad"): 6119, ("fp32acc64_sl", "grad"): 3171}
+# What bounds each dominant kernel, from its ncu capture (profiles/): the
+# roofline above is HBM's, the metric's; the gradient passes are limited by
+# instruction issue and the FP64 passes by the FP64 pipe.
+LIMITER = {("fp32acc64_mlp", "grad"): "issue (SiLU epilogue of the tensor-core network)",
+           ("fp32acc64_sl", "grad"): "issue", ("fp32acc64_sl", "rhs"): "latency and LSU",
+           ("fp32acc64_mlp", "rhs"): "latency and LSU", ("fp64_sl", "rhs"): "FP64 pipe",
+           ("fp64_sl", "grad"): "FP64 pipe"}
+# The tendency's parity bound against the FP64 oracle (tests/): the FP32 path's
+# 1e-5 relative L2 holds with Smagorinsky-Lilly; with the learned closure the
+# BF16 activations (defined by the oracle's BF16 network, rounded sums on the
+# GPU) hold 1e-4.
+PARITY = {"fp32acc64_mlp": "1e-4 rel L2 per variable vs the FP64 oracle with its BF16 network",
+          "fp32acc64_sl": "1e-5 rel L2 per variable vs the FP64 oracle",
+          "fp64_sl": "1e-12 rel L2 per variable vs the FP64 oracle"}
+# ncu counters of the dominant kernels are not constants of this script: they
+# come from profiles/ncu_counters_c5.txt, written from one ncu capture (its
+# command is in that file), one line per kernel:
+#   <variant> <kernel> dram_B_per_node=<x> warp_inst_per_element=<y> sources=<sha>
+# where sha is the SHA-256 (first 16 hex digits) of the kernel's source files
+# at capture time.  A line whose kernel sources have changed since is stale and
+# is not used (traffic and issue then read null).
+COUNTERS = os.path.join(ROOT, "profiles", "ncu_counters_c5.txt")
+KERNEL_SOURCES = {
+    "grad": ["dg_fp32.cu", "mlp.cuh", "tc.cuh", "common.cuh", "thermo32.cuh"],
+    "rhs": ["dg_fp32.cu", "common.cuh", "thermo32.cuh"],
+    "grad64": ["dg_fp64.cu", "common.cuh", "thermo.cuh"],
+    "rhs64": ["dg_fp64.cu", "common.cuh", "thermo.cuh"],
+}
+
+
+def kernel_sources_sha(kind):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_2110_00853_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_counters(variant, kind, prec):
+    """(DRAM bytes per node, warp instructions per element) of one launch from
+    the committed ncu capture, or (None, None) when absent or stale."""
+    key = kind if prec == "fp32" else kind + "64"
+    try:
+        lines = open(COUNTERS).read().splitlines()
+    except OSError:
+        return None, None
+    for ln in lines:
+        parts = ln.split()
+        if len(parts) < 3 or parts[0] != variant or parts[1] != kind:
+            continue
+        kv = dict(p.split("=", 1) for p in parts[2:] if "=" in p)
+        if kv.get("sources") != kernel_sources_sha(key):
+            return None, None
+        return float(kv["dram_B_per_node"]), float(kv.get("warp_inst_per_element", "nan"))
+    return None, None
 
 
 def issue_peak():
@@ -259,11 +302,13 @@ def run_variant(name, precision, closure, flux, integrator, steps, warmup, world
 
 
 def run_e2e(precision, closure, flux, integrator, steps, torch):
-    """Same metric through the C ABI with host buffers: every step's state is
-    uploaded from pinned host memory, the step advanced and its budget
-    diagnostics read back.  The uploads are double-buffered through the ABI's
-    staging calls: the copy of step k+1's state runs on the library's copy
-    stream while step k computes; the first copy is not overlapped."""
+    """Same metric through the C ABI with host buffers, as a host-resident
+    application would use it: every step starts from the state in pinned host
+    memory (cmles_set_state_host), advances it (cmles_step) and brings the
+    advanced state back to pinned host memory (cmles_get_state_host), which
+    becomes the next step's input; each step's budget diagnostics are read
+    too.  Two host buffers alternate as input and output.  The copies cannot
+    overlap the step: each step's input is the previous step's output."""
     from paper_2110_00853_b300 import cmles
     mesh, phys, case = I.mesh(WORKLOAD), I.physics(WORKLOAD, closure=closure), I.case(WORKLOAD)
     phys["flux"] = flux
@@ -272,51 +317,78 @@ def run_e2e(precision, closure, flux, integrator, steps, torch):
     G.init_case(case)
     if closure == "mlp":
         G.set_closure_weights(closure_weights())
-    host = G.get_state_host()
+    bufs = [G.get_state_host(), G.get_state_host()]
     G.step(1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    G.stage_state_host(host)
     for k in range(steps):
-        G.commit_staged_state()
-        if k + 1 < steps:
-            G.stage_state_host(host)
+        G.set_state_host(bufs[k % 2])
         G.step(1)
+        G.get_state_host(out=bufs[(k + 1) % 2])
         G.diagnostics(raise_on_error=False)
     t1 = time.perf_counter()
     nodes = G.E * G.Np
-    h2d = nodes * 6 * 8
+    state_bytes = nodes * 6 * 8
     G.close()
-    del host, G
+    del bufs, G
     torch.cuda.empty_cache()
     sec = (t1 - t0) / steps
-    return dict(value=nodes * STAGES[integrator] / sec, unit="node-stage/s", h2d_bytes_per_step=h2d,
-                d2h_bytes_per_step=7 * 8 + 16 * 4)
+    return dict(value=nodes * STAGES[integrator] / sec, unit="node-stage/s", h2d_bytes_per_step=state_bytes,
+                d2h_bytes_per_step=state_bytes + 7 * 8 + 16 * 4, ms_per_step=sec * 1e3,
+                note="host state in, one step, host state out; the next step starts from that host state")
 
 
-def cpu_baseline(max_seconds=20.0):
+def _omp_threads(n):
+    """Set the OpenMP thread count of the oracle (libgomp) at run time."""
+    import ctypes
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(n))
+        return True
+    except OSError:
+        return False
+
+
+def _cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(max_seconds=20.0, threads=None):
     """The FP64 CPU oracle, as it stands, on a sub-box of the throughput
-    workload (same element size and physics, fewer elements)."""
+    workload (same element size and physics, fewer elements), with OpenMP
+    over elements on `threads` host threads (default all)."""
     from oracle import oracle as O
-    n = (20, 20, 16)
+    nproc = os.cpu_count() or 1
+    threads = threads or int(os.environ.get("OMP_NUM_THREADS", nproc))
+    n = (20, 20, 16) if threads > 1 else (8, 8, 8)
     m = I.sub_mesh(WORKLOAD, *n)
     c = I.case(WORKLOAD)
     c["modes"] = I.velocity_modes(m["Lx"], m["Ly"], m["Lz"], nmodes=200, seed=5)
     S, Q, rr, pr, _ = O.from_inputs(m, I.physics(WORKLOAD), c)
-    S.lsrk54(Q, 1, 0.02)   # warm-up
-    t0 = time.perf_counter()
-    steps = 0
-    while True:
-        Q, _ = S.lsrk54(Q, 1, 0.02)
-        steps += 1
-        if time.perf_counter() - t0 > max_seconds / 2 or steps >= 4:
-            break
-    sec = time.perf_counter() - t0
+    _omp_threads(threads)
+    try:
+        S.lsrk54(Q, 1, 0.02)   # warm-up
+        t0 = time.perf_counter()
+        steps = 0
+        while True:
+            Q, _ = S.lsrk54(Q, 1, 0.02)
+            steps += 1
+            if time.perf_counter() - t0 > max_seconds / 2 or steps >= 4:
+                break
+        sec = time.perf_counter() - t0
+    finally:
+        _omp_threads(nproc)
     nodes = S.E * S.Np
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return dict(value=nodes * STAGES["lsrk54"] * steps / sec, unit="node-stage/s", cores=cores, kind="oracle",
+    return dict(value=nodes * STAGES["lsrk54"] * steps / sec, unit="node-stage/s", cores=threads, kind="oracle",
+                nproc=nproc, cpu=_cpu_model(),
                 sample=f"{n[0]}x{n[1]}x{n[2]}-element sub-box of the {WORKLOAD} workload (same element size, "
-                       f"moist SL physics, {nodes} nodes), {steps} LSRK(5,4) step(s) after 1 warm-up step")
+                       f"moist SL physics, {nodes} nodes), {steps} LSRK(5,4) step(s) after 1 warm-up step, "
+                       f"{threads} OpenMP thread(s)")
 
 
 def main():
@@ -373,11 +445,10 @@ def main():
     dom = max(range(2), key=lambda k: kt["ms"][k])
     avg_ms = kt["ms"][dom] / max(kt["count"][dom], 1)
     achieved = head["nodes"] * alg_bytes(prec, kinds[dom], hstages, variants[0][4]) / (avg_ms / 1e3) / 1e9
-    tb = TRAFFIC_B_PER_NODE.get((variants[0][0], kinds[dom]))
+    tb, wi = ncu_counters(variants[0][0], kinds[dom], prec)
     traffic = tb * head["nodes"] if tb is not None else None
-    wi = WARP_INST_PER_ELEM.get((variants[0][0], kinds[dom]))
     issue = None
-    if wi is not None:
+    if wi is not None and wi == wi:
         ipk = issue_peak()
         ach = wi * (head["nodes"] // 125) / (avg_ms / 1e3)
         issue = {"warp_inst_per_element": wi, "achieved": ach, "peak": ipk, "unit": "warp-inst/s", "frac": ach / ipk}
@@ -398,6 +469,7 @@ def main():
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and sub is None:
         cb = cpu_baseline()
+        cb["single_thread"] = cpu_baseline(threads=1)
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit="node-stage/s", n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=head["ms"] / args.steps, higher_is_better=True,
@@ -414,7 +486,10 @@ def main():
                             "l2": "inputs larger than L2 (state alone 12 GB)", "parallelism": f"replicas{world}"},
                     roofline={"bound": "hbm", "kernel": kinds[dom], "achieved": achieved, "peak": hbm,
                               "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                              "peak_source": f"{peak_kind} hbm_gbs", "issue": issue},
+                              "peak_source": f"{peak_kind} hbm_gbs",
+                              "limiter": LIMITER.get((variants[0][0], kinds[dom]), "unmeasured"),
+                              "issue": issue},
+                    parity=PARITY[variants[0][0]] if variants[0][0] in PARITY else None,
                     cpu_baseline=cb, e2e=e2e, gpu_launches=head["launches"], clocks=head["clocks"],
                     variants=out_variants)
         print(json.dumps(line))

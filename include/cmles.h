@@ -326,9 +326,10 @@ cmles_status cmles_hevi_solve(cmles_handle h, const double *B_dev, double *Y_dev
  *           arrives on; the wait runs out, the CTA finishes its work
  *           (results intact), frees its Tensor Memory and is counted;
  *   mode 2: each CTA's first MMA completion wait gives up at once, while its
- *           MMA is still in flight; the CTA issues no further MMA, skips its
- *           Tensor Memory reads (results invalid), and at its tear-down waits
- *           (bounded) for that MMA to complete before freeing the columns.
+ *           MMA is still in flight (a test instance of the pass); the CTA
+ *           issues no further MMA, reads no Tensor Memory (results invalid),
+ *           and at its tear-down waits (bounded) for that MMA's completion
+ *           before freeing the columns.
  * Either way the next cmles_diagnostics returns CMLES_ERR_TIMEOUT with
  * cmles_diag.tc_timeouts = the number of CTAs that gave up (each counted
  * once).  Mode 0 restores normal operation; other values give
@@ -358,6 +359,73 @@ cmles_status cmles_test_stall_tc(cmles_handle h, int mode);
  * left for that code to read). */
 cmles_status cmles_budgets_noalloc(const double *Q_dev, long long num_elements, int N, double jacobian,
                                    double *out_dev, void *stream);
+
+/* ---- Domain decomposition (Sec. 3.1: the element loop split over
+ * partitions that exchange the face data their neighbours need) ----
+ *
+ * A cmles_group is one mesh split into px x py pencils of whole element
+ * columns (x and y; every partition keeps all nez layers), each partition a
+ * set of device buffers of its own: its interior elements plus one ghost
+ * element on each side in x and y.  Every explicit stage makes two halo
+ * exchanges: before the gradient pass, the state and its four thermodynamic
+ * fields at the face nodes of the partition's boundary elements; before the
+ * flux pass, the five components of the diffusive flux F2 of the face's
+ * direction.  An exchange packs each side's face nodes into a send buffer (a
+ * kernel), copies it into the neighbouring partition's receive buffer and
+ * unpacks it into that partition's ghost elements (a kernel).  All
+ * partitions live on the calling thread's current GPU and the copies are
+ * device-to-device on the group's stream: the single-GPU form of the
+ * decomposition, in which a multi-GPU run would replace each copy with a
+ * point-to-point send and receive.  Results are bit-identical to the whole
+ * mesh's handle (every element runs the same kernels on the same values);
+ * budgets are summed over partitions, so they agree to rounding.
+ *
+ * Scope: flat meshes, both precisions, every closure and numerical flux, the
+ * explicit integrators (LSRK(5,4), LSRK(14,4)); no exponential filter, HEVI
+ * or warped meshes (CMLES_ERR_ARG).  px <= nex and py <= ney; element columns
+ * are split into nearly equal runs (the first nex mod px partitions in x get
+ * one more), partition rank = ix + px iy.  State arrays passed to the group
+ * calls use the whole mesh's layout of the conventions above. */
+typedef struct cmles_group_t *cmles_group;
+cmles_status cmles_group_create(const cmles_mesh *mesh, const cmles_params *params, int px, int py,
+                                cmles_group *out);
+cmles_status cmles_group_destroy(cmles_group g);
+const char *cmles_group_last_error_message(cmles_group g);
+/* The stream of every partition's work and of the exchanges' copies. */
+cmles_status cmles_group_set_stream(cmles_group g, void *stream);
+/* As cmles_set_reference and cmles_set_closure_weights, for every partition
+ * (the reference is per node level, which the (x, y) split does not cut). */
+cmles_status cmles_group_set_reference(cmles_group g, const double *rho_r_host, const double *p_r_host,
+                                       const double *qt_r_host, size_t n);
+cmles_status cmles_group_set_closure_weights(cmles_group g, const float *params_host, size_t n);
+/* Scatter a whole-mesh device state into the partitions / gather it back. */
+cmles_status cmles_group_set_state(cmles_group g, const double *Q_dev);
+cmles_status cmles_group_get_state(cmles_group g, double *Q_dev);
+/* As cmles_tendency and cmles_step, with the halo exchanges. */
+cmles_status cmles_group_tendency(cmles_group g, const double *Q_dev, double *RHS_dev);
+cmles_status cmles_group_step(cmles_group g, int nsteps);
+/* As cmles_diagnostics: budgets and failure counts summed over the
+ * partitions (the allreduce of a multi-GPU run).  Synchronises the stream. */
+cmles_status cmles_group_diagnostics(cmles_group g, cmles_diag *out);
+/* Bytes the halo exchanges of one stage move between partitions. */
+long long cmles_group_halo_bytes(cmles_group g);
+/* Host-only (no GPU needed): the halo plan of partition `rank` of a px x py
+ * split of `mesh`, the one the group uses.  For each side s (0 -x, 1 +x,
+ * 2 -y, 3 +y): neighbour[s] = the partition across that side (the partition
+ * itself across a periodic boundary when it spans the mesh; -1 at a wall)
+ * and count[s] face nodes.  send_index and recv_index (may be NULL; else
+ * room for count[0] + .. + count[3] entries) receive, side after side, the
+ * partition's storage node indices e Np + n (storage element e = (ex + 1) +
+ * (nx + 2) ((ey + 1) + (ny + 2) ez) of the interior coordinates ex, ey, ez,
+ * -1 and nx / ny being the ghosts; nx x ny interior columns): send = the face
+ * nodes of its boundary elements on side s, in the order the neighbour across
+ * s receives them into its side s ^ 1; recv = the ghost nodes on side s that
+ * the neighbour's send on side s ^ 1 fills, entry for entry.  Order within a
+ * side: element layer ez, then the element's index along the side, then the
+ * face node t1 + (N+1) t2 (the two in-face indices in x, y, z order).
+ * Errors: CMLES_ERR_ARG for a bad split, order or null counts. */
+cmles_status cmles_halo_plan(const cmles_mesh *mesh, int px, int py, int rank, int neighbour[4], long long count[4],
+                             long long *send_index, long long *recv_index);
 
 /* Sizes of the handle's problem. */
 long long cmles_num_elements(cmles_handle h);

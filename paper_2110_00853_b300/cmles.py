@@ -109,6 +109,22 @@ def load(path=LIB_PATH):
     L.cmles_commit_staged_state.argtypes = [_H]
     L.cmles_hevi_operator.argtypes = [_H, _VP, _VP]
     L.cmles_hevi_solve.argtypes = [_H, _VP, _VP]
+    L.cmles_group_create.argtypes = [C.POINTER(Mesh), C.POINTER(Params), C.c_int, C.c_int, C.POINTER(_VP)]
+    L.cmles_group_destroy.argtypes = [_VP]
+    L.cmles_group_last_error_message.argtypes = [_VP]
+    L.cmles_group_last_error_message.restype = C.c_char_p
+    L.cmles_group_set_stream.argtypes = [_VP, _VP]
+    L.cmles_group_set_reference.argtypes = [_VP, _DP, _DP, _DP, C.c_size_t]
+    L.cmles_group_set_closure_weights.argtypes = [_VP, C.POINTER(C.c_float), C.c_size_t]
+    for n in ("cmles_group_set_state", "cmles_group_get_state"):
+        getattr(L, n).argtypes = [_VP, _VP]
+    L.cmles_group_tendency.argtypes = [_VP, _VP, _VP]
+    L.cmles_group_step.argtypes = [_VP, C.c_int]
+    L.cmles_group_diagnostics.argtypes = [_VP, C.POINTER(Diag)]
+    L.cmles_group_halo_bytes.argtypes = [_VP]
+    L.cmles_group_halo_bytes.restype = C.c_longlong
+    L.cmles_halo_plan.argtypes = [C.POINTER(Mesh), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                  C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     for n in ("cmles_launch_count", "cmles_num_elements", "cmles_num_nodes", "cmles_device_bytes"):
         getattr(L, n).argtypes = [_H]
         getattr(L, n).restype = C.c_longlong
@@ -382,3 +398,109 @@ class Solver:
 
     def device_bytes(self):
         return self.L.cmles_device_bytes(self.h)
+
+
+def halo_plan(mesh, px, py, rank):
+    """The halo plan of partition `rank` of a px x py split (host-only, see
+    cmles_halo_plan): (neighbour[4], count[4], send[4], recv[4]) with send[s]
+    and recv[s] arrays of storage node indices."""
+    L = load()
+    m = make_mesh(mesh)
+    nb = (C.c_int * 4)()
+    cnt = (C.c_longlong * 4)()
+    st = L.cmles_halo_plan(C.byref(m), px, py, rank, nb, cnt, None, None)
+    if st != 0:
+        raise CmlesError(st, "cmles_halo_plan failed")
+    tot = sum(cnt)
+    send = np.zeros(max(tot, 1), dtype=np.int64)
+    recv = np.zeros(max(tot, 1), dtype=np.int64)
+    st = L.cmles_halo_plan(C.byref(m), px, py, rank, nb, cnt, send.ctypes.data_as(C.POINTER(C.c_longlong)),
+                           recv.ctypes.data_as(C.POINTER(C.c_longlong)))
+    if st != 0:
+        raise CmlesError(st, "cmles_halo_plan failed")
+    off = np.concatenate([[0], np.cumsum(list(cnt))])
+    return (list(nb), list(cnt), [send[off[k]:off[k + 1]] for k in range(4)],
+            [recv[off[k]:off[k + 1]] for k in range(4)])
+
+
+class Group:
+    """One mesh split into px x py (x, y) partitions that exchange face halos
+    every stage (cmles_group, the single-GPU form of the decomposition)."""
+
+    def __init__(self, mesh, physics, px, py, precision="fp64"):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("cmles needs a CUDA device; no CPU fallback exists")
+        self.torch = torch
+        self.L = load()
+        self._mesh = make_mesh(mesh)
+        self._params = make_params(physics, precision)
+        g = _VP()
+        st = self.L.cmles_group_create(C.byref(self._mesh), C.byref(self._params), px, py, C.byref(g))
+        if st != 0:
+            raise CmlesError(st, "cmles_group_create failed")
+        self.g = g
+        self.N = mesh["N"]
+        self.Np = (self.N + 1) ** 3
+        self.E = mesh["nex"] * mesh["ney"] * mesh["nez"]
+        self._check(self.L.cmles_group_set_stream(self.g, C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+    def _check(self, st):
+        if st != 0:
+            raise CmlesError(st, self.L.cmles_group_last_error_message(self.g).decode())
+
+    def close(self):
+        if getattr(self, "g", None):
+            self.L.cmles_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_reference(self, rho_r, p_r, qt_r=None):
+        rho_r = np.ascontiguousarray(rho_r, np.float64)
+        p_r = np.ascontiguousarray(p_r, np.float64)
+        q = None if qt_r is None else np.ascontiguousarray(qt_r, np.float64)
+        self._check(self.L.cmles_group_set_reference(self.g, rho_r.ctypes.data_as(_DP), p_r.ctypes.data_as(_DP),
+                                                     None if q is None else q.ctypes.data_as(_DP), rho_r.size))
+
+    def set_closure_weights(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        self._check(self.L.cmles_group_set_closure_weights(self.g, flat.ctypes.data_as(C.POINTER(C.c_float)),
+                                                           flat.size))
+
+    def _dev(self, t):
+        assert t.is_cuda and t.dtype == self.torch.float64 and t.is_contiguous()
+        assert t.numel() == self.E * 6 * self.Np
+        return C.c_void_p(t.data_ptr())
+
+    def set_state(self, Q):
+        self._check(self.L.cmles_group_set_state(self.g, self._dev(Q)))
+
+    def get_state(self):
+        Q = self.torch.empty((self.E, 6, self.Np), dtype=self.torch.float64, device="cuda")
+        self._check(self.L.cmles_group_get_state(self.g, self._dev(Q)))
+        return Q
+
+    def tendency(self, Q, out=None):
+        if out is None:
+            out = self.torch.empty_like(Q)
+        self._check(self.L.cmles_group_tendency(self.g, self._dev(Q), self._dev(out)))
+        return out
+
+    def step(self, n=1):
+        self._check(self.L.cmles_group_step(self.g, int(n)))
+
+    def diagnostics(self, raise_on_error=True):
+        d = Diag()
+        st = self.L.cmles_group_diagnostics(self.g, C.byref(d))
+        if raise_on_error and st != 0:
+            self._check(st)
+        return dict(budget=np.array(d.budget[:]), time=d.time, steps=d.steps, nonfinite=bool(d.nonfinite),
+                    satadj_failures=d.satadj_failures, tc_timeouts=d.tc_timeouts, status=st)
+
+    def halo_bytes(self):
+        return self.L.cmles_group_halo_bytes(self.g)

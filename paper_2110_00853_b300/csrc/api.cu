@@ -9,12 +9,7 @@
 #include <utility>
 #include <vector>
 
-#include "cmles.h"
-#include "common.cuh"
-#include "launch.h"
-#include "mlp.cuh"
-
-using namespace cmles;
+#include "handle.h"
 
 namespace {
 
@@ -45,11 +40,6 @@ const double kLsrk14B[14] = {0.0367762454319673, 0.3136296607553959, 0.153184869
                              0.3326293790646110, 0.2440251405350864, 0.3718879239592277, 0.6204126221582444,
                              0.1524043173028741, 0.0760894927419266, 0.0077604214040978, 0.0024647284755382,
                              0.0780348340049386, 5.5059777270269628};
-
-struct TimedLaunch {
-  int kind;
-  cudaEvent_t a, b;
-};
 
 // Legendre P_N and P_{N-1} at x by the three-term recurrence.
 void legendre_pair(int N, double x, double *PN, double *PNm1) {
@@ -113,78 +103,13 @@ void lgl_basis(int N, std::vector<double> &x, std::vector<double> &w, std::vecto
 
 }  // namespace
 
-struct cmles_t {
-  cmles_mesh mesh;
-  cmles_params prm;
-  int N = 4, Nq = 5, Np = 125;
-  long long E = 0, nodes = 0;
-  cudaStream_t stream = 0;
-  std::string err;
-  std::vector<double> xi, w, D;
-  KParams K;
-  double *Q[2] = {nullptr, nullptr};
-  int cur = 0;
-  double *dQ = nullptr, *F2 = nullptr;
-  double *TH64[2] = {nullptr, nullptr};  // FP64 path: thermodynamic fields of Q[i]
-  // FP32 path: shadow ping-pong, FP32 LSRK register, FP32 F2/aux, tables
-  bool fp32 = false;
-  float *S32[2] = {nullptr, nullptr};
-  float *TH32[2] = {nullptr, nullptr};  // thermodynamic fields of S32[i]
-  int scur = 0;
-  bool shadow_valid = false;  // FP32: S32[scur] and TH32[scur] are Q's; FP64: TH64[cur] is Q[cur]'s
-  float *dQ32 = nullptr, *D32 = nullptr, *F2_32 = nullptr, *lev32 = nullptr, *dH32 = nullptr;
-  double *qref64 = nullptr;
-  double *rho_r = nullptr, *p_r = nullptr, *qt_r = nullptr, *tau_lev = nullptr, *tau_col = nullptr;
-  double *wq = nullptr, *partials = nullptr, *budget_out = nullptr, *prof = nullptr;
-  int *flags = nullptr;
-  int budget_nblocks = 1;
-  bool have_ref = false;
-  long long launches = 0, steps = 0;
-  int tc_stall = 0;
-  // HEVI: level reference (host copy), stage buffers R0 R1 R2 L0 L1 B Y and
-  // the tables of the vertical operator for the step hv_dt
-  std::vector<double> ref_rho_h, ref_p_h, ref_qt_h;
-  double *hv_buf[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  double *hv_tab = nullptr;
-  double hv_dt = -1.0;
-  HeviTables hv_T{};
-  // double-buffered host uploads: staging buffer, copy stream and events
-  double *Qstage = nullptr;
-  cudaStream_t copy_stream = nullptr;
-  cudaEvent_t staged_ev = nullptr, compute_ev = nullptr;
-  bool staged = false;
-  double time = 0.0;
-  bool timing = false;
-  std::vector<TimedLaunch> timed;
-  long long tcount[3] = {0, 0, 0};
-  double tms[3] = {0, 0, 0};
-  long long bytes = 0;
-  std::vector<float> mlp;
-  MlpPacked *mlp_dev = nullptr;
-  ExpFilter expf = {};
-  double *rvs_tab = nullptr;
-  double *exr = nullptr;  // (p_r/p0)^-kappa per node level
-  bool have_mlp = false;
-  // curvilinear (warped) meshes: device tables and host geometry (FP64)
-  bool curved = false;
-  float *geo32 = nullptr, *node32 = nullptr;
-  double *wJn = nullptr;
-  std::vector<double> hx_, hz_, hJ_, hJa_, hdelta_;
-};
 
-namespace {
+namespace cmles_host {
 
 cmles_status fail(cmles_handle h, cmles_status st, const std::string &msg) {
   if (h) h->err = msg;
   return st;
 }
-
-#define CK(call)                                                                            \
-  do {                                                                                      \
-    cudaError_t e_ = (call);                                                                \
-    if (e_ != cudaSuccess)                                                                  \
-      return fail(h, CMLES_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
 
 cmles_status dalloc(cmles_handle h, void **p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);
@@ -199,26 +124,21 @@ cmles_status dalloc(cmles_handle h, void **p, size_t bytes) {
 }
 
 // launch bookkeeping: count every kernel; with timing on, bracket by events
-struct LaunchScope {
-  cmles_handle h;
-  int kind, nk;
-  TimedLaunch tl;
-  LaunchScope(cmles_handle h_, int kind_, int nkernels) : h(h_), kind(kind_), nk(nkernels) {
-    h->launches += nk;
-    if (h->timing) {
-      cudaEventCreate(&tl.a);
-      cudaEventCreate(&tl.b);
-      cudaEventRecord(tl.a, h->stream);
-    }
+LaunchScope::LaunchScope(cmles_handle h_, int kind_, int nkernels) : h(h_), kind(kind_), nk(nkernels) {
+  h->launches += nk;
+  if (h->timing) {
+    cudaEventCreate(&tl.a);
+    cudaEventCreate(&tl.b);
+    cudaEventRecord(tl.a, h->stream);
   }
-  ~LaunchScope() {
-    if (h->timing) {
-      cudaEventRecord(tl.b, h->stream);
-      tl.kind = kind;
-      h->timed.push_back(tl);
-    }
+}
+LaunchScope::~LaunchScope() {
+  if (h->timing) {
+    cudaEventRecord(tl.b, h->stream);
+    tl.kind = kind;
+    h->timed.push_back(tl);
   }
-};
+}
 
 void fill_kparams(cmles_handle h) {
   const cmles_params &p = h->prm;
@@ -617,7 +537,9 @@ cmles_status curved_reference(cmles_handle h, const double *rho_r, const double 
   return CMLES_OK;
 }
 
-}  // namespace
+}  // namespace cmles_host
+
+using namespace cmles_host;
 
 extern "C" {
 
@@ -754,7 +676,14 @@ static cmles_status apply_expfilter(cmles_handle h) {
   return CMLES_OK;
 }
 
-cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cmles_handle *out) {
+}  // extern "C"
+
+// cmles_create of a whole mesh (ps null), or of one partition of a mesh
+// split into (x, y) pencils: `mesh` is then the partition's interior as a mesh
+// of its own extent and origin, and ps gives the whole mesh, the partition's
+// place in it and its sides that are walls.
+cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_params *params, const PartSpec *ps,
+                                       cmles_handle *out) {
   if (!mesh || !params || !out) return CMLES_ERR_ARG;
   *out = nullptr;
   if (mesh->N != 4) return CMLES_ERR_ARG;
@@ -783,7 +712,8 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   // the learned closure runs on BF16 tensor cores inside the FP32 kernels
   if (params->closure == CMLES_CLOSURE_MLP && params->precision != CMLES_FP32_ACC64) return CMLES_ERR_ARG;
   long long E = (long long)mesh->nex * mesh->ney * mesh->nez;
-  if (E > 0x7fffffffLL / 8) return CMLES_ERR_MESH;
+  const long long Es = ps ? (long long)(mesh->nex + 2) * (mesh->ney + 2) * mesh->nez : E;
+  if (Es > 0x7fffffffLL / 8) return CMLES_ERR_MESH;
   cmles_handle h = new cmles_t();
   h->mesh = *mesh;
   h->prm = *params;
@@ -792,9 +722,12 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   h->Np = h->Nq * h->Nq * h->Nq;
   h->E = E;
   h->nodes = E * h->Np;
+  h->Es = Es;
+  h->snodes = Es * h->Np;
+  h->part = ps != nullptr;
   lgl_basis(h->N, h->xi, h->w, h->D);
   if (params->filter_order > 0) build_expfilter(h);
-  const size_t n6 = (size_t)h->nodes * 6;
+  const size_t n6 = (size_t)h->snodes * 6;
   const int nlev = mesh->nez * h->Nq;
   cmles_status st = CMLES_OK;
 #define ALLOC(ptr, bytes)                                   \
@@ -812,11 +745,11 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   if (!h->fp32) {
     ALLOC(h->Q[1], n6 * sizeof(double));
     ALLOC(h->dQ, n6 * sizeof(double));
-    ALLOC(h->F2, (size_t)h->nodes * 15 * sizeof(double));
-    ALLOC(h->TH64[0], (size_t)h->nodes * 4 * sizeof(double));
-    ALLOC(h->TH64[1], (size_t)h->nodes * 4 * sizeof(double));
+    ALLOC(h->F2, (size_t)h->snodes * 15 * sizeof(double));
+    ALLOC(h->TH64[0], (size_t)h->snodes * 4 * sizeof(double));
+    ALLOC(h->TH64[1], (size_t)h->snodes * 4 * sizeof(double));
   } else {
-    const size_t n32 = (size_t)E * 128;  // padded nodes
+    const size_t n32 = (size_t)Es * 128;  // padded nodes
     ALLOC(h->S32[0], n32 * 6 * sizeof(float));
     ALLOC(h->S32[1], n32 * 6 * sizeof(float));
     ALLOC(h->dQ32, n32 * 6 * sizeof(float));
@@ -841,7 +774,9 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   ALLOC(h->p_r, nlev * sizeof(double));
   ALLOC(h->qt_r, nlev * sizeof(double));
   ALLOC(h->tau_lev, nlev * sizeof(double));
-  ALLOC(h->tau_col, (size_t)mesh->nex * h->Nq * sizeof(double));
+  // lateral sponge: one value per node column of the whole mesh in x
+  const cmles_mesh &gm = ps ? ps->global : *mesh;
+  ALLOC(h->tau_col, (size_t)gm.nex * h->Nq * sizeof(double));
   ALLOC(h->wq, h->Np * sizeof(double));
   ALLOC(h->flags, 16 * sizeof(int));
   ALLOC(h->rvs_tab, kRvsN * 2 * sizeof(double));
@@ -852,8 +787,14 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   ALLOC(h->prof, (size_t)nlev * 12 * sizeof(double));
 #undef ALLOC
   fill_kparams(h);
+  if (ps) {
+    h->K.part = 1;
+    h->K.gx0 = ps->gx0;
+    h->K.gy0 = ps->gy0;
+    for (int f = 0; f < 4; ++f) h->K.wall[f] = ps->wall[f];
+  }
   // sponge tables (Eq. sponge, reading tau_s = alpha sin^gamma(pi/2 (z - z_s)/(z_top - z_s)))
-  std::vector<double> tl(nlev, 0.0), tc((size_t)mesh->nex * h->Nq, 0.0);
+  std::vector<double> tl(nlev, 0.0), tc((size_t)gm.nex * h->Nq, 0.0);
   const double ztop = mesh->z0 + mesh->Lz;
   for (int l = 0; l < nlev; ++l) {
     const double z = level_z(h, l);
@@ -863,11 +804,11 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   }
   bool lateral = params->sponge_alpha > 0.0 && params->lateral_sponge_frac > 0.0;
   if (lateral) {
-    const double width = params->lateral_sponge_frac * mesh->Lx;
-    const double xl = mesh->x0 + width, xr = mesh->x0 + mesh->Lx - width;
-    for (int ex = 0; ex < mesh->nex; ++ex)
+    const double width = params->lateral_sponge_frac * gm.Lx;
+    const double xl = gm.x0 + width, xr = gm.x0 + gm.Lx - width;
+    for (int ex = 0; ex < gm.nex; ++ex)
       for (int i = 0; i < h->Nq; ++i) {
-        const double x = mesh->x0 + (ex + 0.5 * (h->xi[i] + 1.0)) * h->K.hx;
+        const double x = gm.x0 + (ex + 0.5 * (h->xi[i] + 1.0)) * h->K.hx;
         double t = 0.0;
         if (x < xl) t = params->sponge_alpha * pow(sin(0.5 * M_PI * (xl - x) / width), params->sponge_gamma);
         if (x > xr) t = params->sponge_alpha * pow(sin(0.5 * M_PI * (x - xr) / width), params->sponge_gamma);
@@ -888,7 +829,7 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   if (e == cudaSuccess) e = cudaMemset(h->exr, 0, nlev * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(h->mlp_dev, 0, sizeof(MlpPacked));
   if (e == cudaSuccess && h->dQ) e = cudaMemset(h->dQ, 0, n6 * sizeof(double));
-  if (e == cudaSuccess && h->dQ32) e = cudaMemset(h->dQ32, 0, (size_t)E * 128 * 6 * sizeof(float));
+  if (e == cudaSuccess && h->dQ32) e = cudaMemset(h->dQ32, 0, (size_t)Es * 128 * 6 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(h->Q[0], 0, n6 * sizeof(double));
   if (e != cudaSuccess) {
     cmles_destroy(h);
@@ -906,6 +847,19 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
   }
   *out = h;
   return CMLES_OK;
+}
+
+int cmles_host::lsrk_tables(cmles_handle h, const double **A, const double **B) {
+  const bool l14 = h->prm.integrator == CMLES_LSRK144;
+  *A = l14 ? kLsrk14A : kLsrkA;
+  *B = l14 ? kLsrk14B : kLsrkB;
+  return l14 ? 14 : 5;
+}
+
+extern "C" {
+
+cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cmles_handle *out) {
+  return create_handle(mesh, params, nullptr, out);
 }
 
 cmles_status cmles_destroy(cmles_handle h) {

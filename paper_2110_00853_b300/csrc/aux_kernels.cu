@@ -25,16 +25,24 @@ int budget_blocks(long long nodes) {
 // Quadrature sums sum_e sum_n w_n J Q_v with LGL weights w_n = w_i w_j w_k
 // and the constant element Jacobian J of a flat mesh, plus a count of
 // non-finite entries.  Fixed grid and fixed reduction order: deterministic.
+// On a partition (pnex > 0) the E = pnex x pney x nez elements are the
+// interior of a storage block with one ghost element on each side in x and y.
 __global__ void __launch_bounds__(kBudgetThreads) k_budget_partial(const double *__restrict__ Q, long long E,
                                                                    int Np, const double *__restrict__ wq,
                                                                    double J, double *__restrict__ partials,
-                                                                   const double *__restrict__ wJn) {
+                                                                   const double *__restrict__ wJn, int pnex,
+                                                                   int pney) {
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   const long long nodes = E * Np;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nodes;
        g += (long long)gridDim.x * blockDim.x) {
-    const long long e = g / Np;
-    const int n = (int)(g - e * Np);
+    const long long ei = g / Np;
+    const int n = (int)(g - ei * Np);
+    long long e = ei;
+    if (pnex > 0) {
+      const long long ex = ei % pnex, ey = (ei / pnex) % pney, ez = ei / ((long long)pnex * pney);
+      e = (ex + 1) + (pnex + 2) * ((ey + 1) + (long long)(pney + 2) * ez);
+    }
     const double w = wJn ? wJn[g] : wq[n] * J;
 #pragma unroll
     for (int v = 0; v < 6; ++v) {
@@ -68,8 +76,8 @@ __global__ void k_budget_final(const double *__restrict__ partials, int nblocks,
 }
 
 cudaError_t launch_budgets(const double *Q, long long E, int Np, const double *wq, double J, double *partials,
-                           int nblocks, double *out, cudaStream_t s, const double *wJn) {
-  k_budget_partial<<<nblocks, kBudgetThreads, 0, s>>>(Q, E, Np, wq, J, partials, wJn);
+                           int nblocks, double *out, cudaStream_t s, const double *wJn, int pnex, int pney) {
+  k_budget_partial<<<nblocks, kBudgetThreads, 0, s>>>(Q, E, Np, wq, J, partials, wJn, pnex, pney);
   k_budget_final<<<1, 32, 0, s>>>(partials, nblocks, out);
   return cudaGetLastError();
 }

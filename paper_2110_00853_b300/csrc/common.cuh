@@ -83,6 +83,16 @@ struct KParams {
   int tc_stall;      // test hook: 1 the tensor-core kernels also wait on a barrier nothing arrives on;
                     // 2 their first MMA completion wait gives up at once
   int tiled;         // 1: visit elements in 4 x 4 column tiles (nex, ney multiples of 4)
+  // one partition of a larger mesh split into (x, y) pencils (cmles_group):
+  // the nex x ney x nez elements are the partition's interior, stored with
+  // one ghost element on each side in x and y, (nex + 2) x (ney + 2) x nez
+  // storage elements.  Ghost elements hold only the face nodes their interior
+  // neighbours read, written by the halo exchange.  gx0, gy0: global indices
+  // of the first interior element (sponge columns); wall[s] (s = 0 -x, 1 +x,
+  // 2 -y, 3 +y): 1 where that side of the partition is a wall of the whole
+  // mesh, 0 where a ghost element (a neighbouring partition's, or the
+  // partition's own across a periodic boundary) lies.
+  int part, gx0, gy0, wall[4];
   // FP32 path tables (see dg_fp32.cu): per level 16 floats, per element layer
   // the 5 x 5 differences of rho e_r + p_r along z, per level FP64 offsets
   const float *lev32, *dH32;
@@ -104,25 +114,36 @@ __device__ __forceinline__ int face_node(int d, int a, int t1, int t2) {
   return d == 0 ? a + Nq * (t1 + Nq * t2) : (d == 1 ? t1 + Nq * (a + Nq * t2) : t1 + Nq * (t2 + Nq * a));
 }
 
+// Storage index of the element with (interior) coordinates (ex, ey, ez); on
+// a partition, -1 and nex (ney) are its ghost elements in x (y).
+__host__ __device__ __forceinline__ int storage_index(const KParams &P, int ex, int ey, int ez) {
+  return P.part ? (ex + 1) + (P.nex + 2) * ((ey + 1) + (P.ney + 2) * ez) : ex + P.nex * (ey + P.ney * ez);
+}
+
 // Neighbour of element (ex, ey, ez) across face f (0: -x, 1: +x, 2: -y, 3: +y,
-// 4: -z, 5: +z); -1 marks a wall.
+// 4: -z, 5: +z) as a storage index; -1 marks a wall.
 __device__ __forceinline__ int neighbour(const KParams &P, int ex, int ey, int ez, int f) {
   int c[3] = {ex, ey, ez};
   const int n[3] = {P.nex, P.ney, P.nez};
   const int d = f >> 1;
   int v = c[d] + ((f & 1) ? 1 : -1);
   if (v < 0 || v >= n[d]) {
-    if (!P.periodic[d]) return -1;
-    v = (v + n[d]) % n[d];
+    if (P.part && d < 2) {
+      if (P.wall[f]) return -1;  // otherwise the ghost element at -1 or n[d]
+    } else {
+      if (!P.periodic[d]) return -1;
+      v = (v + n[d]) % n[d];
+    }
   }
   c[d] = v;
-  return c[0] + P.nex * (c[1] + P.ney * c[2]);
+  return storage_index(P, c[0], c[1], c[2]);
 }
 
-// Element visited at position g of a kernel's traversal.  With tiling, the
-// traversal walks 4 x 4 columns of elements bottom to top, so that the x, y
-// and z neighbours of an element are visited close in time and their face
-// data is still in L2 when it is gathered.
+// Element visited at position g of a kernel's traversal (g < P.E, the
+// interior elements): its storage index, and its coordinates in (ex, ey, ez).
+// With tiling, the traversal walks 4 x 4 columns of elements bottom to top,
+// so that the x, y and z neighbours of an element are visited close in time
+// and their face data is still in L2 when it is gathered.
 __device__ __forceinline__ int element_at(const KParams &P, int g, int &ex, int &ey, int &ez) {
   if (P.tiled) {
     const int per_tile = 16 * P.nez;
@@ -136,7 +157,15 @@ __device__ __forceinline__ int element_at(const KParams &P, int g, int &ex, int 
     ey = (g / P.nex) % P.ney;
     ez = g / (P.nex * P.ney);
   }
-  return ex + P.nex * (ey + P.ney * ez);
+  return storage_index(P, ex, ey, ez);
+}
+
+// The same in the plain order x fastest (kernels that do not tile).
+__device__ __forceinline__ int element_lin(const KParams &P, long long g, int &ex, int &ey, int &ez) {
+  ex = (int)(g % P.nex);
+  ey = (int)((g / P.nex) % P.ney);
+  ez = (int)(g / ((long long)P.nex * P.ney));
+  return storage_index(P, ex, ey, ez);
 }
 
 __device__ __forceinline__ double node_z(const KParams &P, int ez, int k) {

@@ -32,7 +32,9 @@ __device__ __forceinline__ void load_node_table(const float *__restrict__ tab, s
   for (int f = 0; f < L_NF; ++f) L[f] = p[f * kNP];
 }
 
-template <int N, int CL>
+// HOOK: the instance launched only under test hook 2 (cmles_test_stall_tc),
+// whose first MMA completion wait gives up at once.
+template <int N, int CL, bool HOOK = false>
 __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *__restrict__ S,
                                                                   const float *__restrict__ TH,
                                                                   float *__restrict__ F2, const KParams P) {
@@ -64,9 +66,9 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
     tc_setup(tcs, &sSlot, &sBar[0]);
     // test hook (see the flat kernel)
     if (P.tc_stall == 1 && !mbar_wait_bounded(&sBar[1], 0, 1 << 14)) stalled = 1;
-    // test hook 2: the first MMA completion wait gives up at once, so the
-    // CTA reaches its tear-down with a committed phase to drain
-    if (P.tc_stall == 2) tcs.first_limit = 0;
+    // test hook 2: the first MMA completion wait gives up at once, while
+    // the MMA is in flight
+    if (HOOK) tcs.hook = 1;
     __syncwarp();
   }
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
       __syncthreads();  // the A operand overwrites the gradient fields
       mlp_tc_put_input(sA, x);
       float y0, y1;
-      mlp_tc_forward(W, sA, tcs, y0, y1);
+      mlp_tc_forward<HOOK>(W, sA, tcs, y0, y1);
       if (t < Np) {
         nut = W.out_scale[0] * fmaxf(y0, 0.f);
         Dt = W.out_scale[1] * fmaxf(y1, 0.f);
@@ -517,6 +519,12 @@ static void grad32c_instance(const float *S, const float *TH, float *F2, const K
   if (!grid)
     grid = CL == 2 ? grid_for_tc((const void *)k_grad32c<4, CL>, 1 << 30, kTcCols)
                    : grid_for((const void *)k_grad32c<4, CL>, 1 << 30, 0);
+  if (CL == 2 && P.tc_stall == 2) {
+    static int hgrid = 0;
+    if (!hgrid) hgrid = grid_for_tc((const void *)k_grad32c<4, 2, true>, 1 << 30, kTcCols);
+    k_grad32c<4, 2, true><<<hgrid < P.E ? hgrid : P.E, 128, 0, s>>>(S, TH, F2, P);
+    return;
+  }
   k_grad32c<4, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, TH, F2, P);
 }
 

@@ -39,7 +39,9 @@ namespace cmles {
 // CL: 1 Smagorinsky-Lilly, 3 Vreman (both with the Richardson correction),
 // 2 learned closure
 // (tensor-core MLP on the velocity and theta_v gradients and Delta).
-template <int N, int CL>
+// HOOK: the instance launched only under test hook 2 (cmles_test_stall_tc),
+// whose first MMA completion wait gives up at once.
+template <int N, int CL, bool HOOK = false>
 __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__restrict__ S, const float *__restrict__ TH,
                                                                  float *__restrict__ F2, const KParams P) {
   constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
@@ -73,9 +75,9 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
     // test hook: a bounded wait on a barrier that nothing arrives on runs
     // out; it is reported like a failed MMA wait but leaves the work intact
     if (P.tc_stall == 1 && !mbar_wait_bounded(&sBar[1], 0, 1 << 14)) stalled = 1;
-    // test hook 2: the first MMA completion wait gives up at once, so the
-    // CTA reaches its tear-down with a committed phase to drain
-    if (P.tc_stall == 2) tcs.first_limit = 0;
+    // test hook 2: the first MMA completion wait gives up at once, while
+    // the MMA is in flight
+    if (HOOK) tcs.hook = 1;
     __syncwarp();
   }
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
       __syncthreads();  // the A operand overwrites the gradient fields
       mlp_tc_put_input(sA, x);
       float y0, y1;
-      mlp_tc_forward(W, sA, tcs, y0, y1);
+      mlp_tc_forward<HOOK>(W, sA, tcs, y0, y1);
       if (t < Np) {
         nut = W.out_scale[0] * fmaxf(y0, 0.f);
         Dt = W.out_scale[1] * fmaxf(y1, 0.f);
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
         R[4] -= L[L_H] * (F.jac[0] * ux + F.jac[1] * vy + F.jac[2] * wz) + F.jac[2] * wdh;
       }
       float tau = L[L_TAU];
-      if (P.tau_col) tau = fmaxf(tau, (float)P.tau_col[ex * Nq + i]);
+      if (P.tau_col) tau = fmaxf(tau, (float)P.tau_col[(ex + P.gx0) * Nq + i]);
       const float rho = L[L_RHO] + sv[0];
       float Sr[3];
       Sr[0] = -tau * (sv[1] - rho * F.u_relax[0]);
@@ -479,9 +481,10 @@ __global__ void k_shadow32(const double *__restrict__ Q64, float *__restrict__ S
   const long long n = (long long)P.E * Np;
   int fail = 0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    const long long e = q / Np;
-    const int node = (int)(q - e * Np);
-    const int ez = (int)(e / ((long long)P.nex * P.ney));
+    const long long g = q / Np;
+    const int node = (int)(q - g * Np);
+    int ex, ey, ez;
+    const long long e = element_lin(P, g, ex, ey, ez);
     const int k = node / (Nq * Nq);
     const double *qr = P.qref64 + (size_t)(ez * Nq + k) * 4;
     float s[6];
@@ -515,6 +518,12 @@ static void grad32_instance(const float *S, const float *TH, float *F2, const KP
   if (!grid)
     grid = CL == 2 ? grid_for_tc((const void *)k_grad32<4, CL>, 1 << 30, kTcCols)
                    : grid_for((const void *)k_grad32<4, CL>, 1 << 30, 0);
+  if (CL == 2 && P.tc_stall == 2) {
+    static int hgrid = 0;
+    if (!hgrid) hgrid = grid_for_tc((const void *)k_grad32<4, 2, true>, 1 << 30, kTcCols);
+    k_grad32<4, 2, true><<<hgrid < P.E ? hgrid : P.E, 128, 0, s>>>(S, TH, F2, P);
+    return;
+  }
   k_grad32<4, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, TH, F2, P);
 }
 

@@ -52,8 +52,9 @@ __global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, co
   const int t = threadIdx.x;
   if (t < Nq * Nq) sD[t] = P.D[t];
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
-  for (int e = blockIdx.x; e < P.E; e += gridDim.x) {
-    const int ex = e % P.nex, ey = (e / P.nex) % P.ney, ez = e / (P.nex * P.ney);
+  for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
+    int ex, ey, ez;
+    const int e = element_lin(P, g, ex, ey, ez);
     if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
     double Y[6], G[6];
     if (t < Np) {
@@ -205,8 +206,9 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
   if (t < Nq * Nq) sD[t] = P.D[t];
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
   int fail = 0;
-  for (int e = blockIdx.x; e < P.E; e += gridDim.x) {
-    const int ex = e % P.nex, ey = (e / P.nex) % P.ney, ez = e / (P.nex * P.ney);
+  for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
+    int ex, ey, ez;
+    const int e = element_lin(P, g, ex, ey, ez);
     if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
     double Y[6];
     if (t < Np) {
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, con
       }
       // sources: -(rho - rho_r) g k, -tau_s (rho u - rho u_relax), -2 Omega x rho u
       double tau = P.tau_lev[lev];
-      if (P.tau_col) tau = fmax(tau, P.tau_col[ex * Nq + i]);
+      if (P.tau_col) tau = fmax(tau, P.tau_col[(ex + P.gx0) * Nq + i]);
       double S[3];
       S[0] = -tau * (Y[1] - Y[0] * P.u_relax[0]);
       S[1] = -tau * (Y[2] - Y[0] * P.u_relax[1]);
@@ -378,9 +380,10 @@ __global__ void k_thermo64(const double *__restrict__ Q, double *__restrict__ TH
   const long long n = (long long)P.E * Np;
   int fail = 0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    const long long e = q / Np;
-    const int node = (int)(q - e * Np);
-    const int ez = (int)(e / ((long long)P.nex * P.ney));
+    const long long g = q / Np;
+    const int node = (int)(q - g * Np);
+    int ex, ey, ez;
+    const long long e = element_lin(P, g, ex, ey, ez);
     const int k = node / (Nq * Nq);
     double Y[6];
 #pragma unroll

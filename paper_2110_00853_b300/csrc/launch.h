@@ -92,9 +92,12 @@ cudaError_t launch_closure_samples(const double *Q, const KParams &P, int N, con
 // Budgets: partial sums per block into partials[nblocks][7] (6 integrals and a
 // non-finite count), then a single-block pass in fixed order into out[7].
 int budget_blocks(long long nodes);
-// wJn: optional per-node w_n J_n (curvilinear meshes); otherwise wq[n] * J
+// wJn: optional per-node w_n J_n (curvilinear meshes); otherwise wq[n] * J.
+// pnex > 0: Q is a partition's storage (pnex x pney interior columns with a
+// ghost element on each side in x and y), summed over the interior.
 cudaError_t launch_budgets(const double *Q, long long E, int Np, const double *wq, double J, double *partials,
-                           int nblocks, double *out, cudaStream_t s, const double *wJn = nullptr);
+                           int nblocks, double *out, cudaStream_t s, const double *wJn = nullptr, int pnex = 0,
+                           int pney = 0);
 
 struct CaseDev {
   int id;

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
 #pragma unroll
     for (int k = 0; k < 16; ++k) S.XT[tc_off(k, t, 16)] = __float2bfloat16_rn(k < kMlpIn ? x[k] : 0.f);
     // ---- forward, layer 1 (a1 kept in TMEM)
-    tc_group_open(st);
+    tc_group_open();
     if (t == 0 && !st.err) {
       tc_fence_after_sync();
       tc_mma(st.tmem + kTrA1, tc_sdesc(S.Aop, 128, kSboA), tc_sdesc(S.W.W1, 128, kSbo1), tc_idesc_bf16(128, kMlpH),
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       float v[32];
-      tc_ld32_if(st, lane_base + kTrA1 + 32 * h, v);
+      tc_ld32(lane_base + kTrA1 + 32 * h, v);
       uint32_t w[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
             make_uint4(w[4 * kk], w[4 * kk + 1], w[4 * kk + 2], w[4 * kk + 3]);
     }
     // ---- layer 2 (a2 to shared memory)
-    tc_group_open(st);
+    tc_group_open();
     if (t == 0 && !st.err) {
       tc_fence_after_sync();
 #pragma unroll
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       float v[32];
-      tc_ld32_if(st, lane_base + kTrA2 + 32 * h, v);
+      tc_ld32(lane_base + kTrA2 + 32 * h, v);
       uint32_t w[16];
 #pragma unroll
       for (int q = 0; q < 32; ++q) S.A2[t * kMlpH + 32 * h + q] = v[q];
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
             make_uint4(w[4 * kk], w[4 * kk + 1], w[4 * kk + 2], w[4 * kk + 3]);
     }
     // ---- layer 3
-    tc_group_open(st);
+    tc_group_open();
     if (t == 0 && !st.err) {
       tc_fence_after_sync();
 #pragma unroll
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
     }
     tc_group_close(st);
     float y0, y1;
-    tc_ld2_if(st, lane_base + kTrY, y0, y1);
+    tc_ld2(lane_base + kTrY, y0, y1);
     // output error and loss
     float dy0 = 0.f, dy1 = 0.f;
     if (valid) {
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
       atomicAdd(&S.g[kMlpOffB2 + i], da);
     }
     // ---- dh1 = da2 W2
-    tc_group_open(st);
+    tc_group_open();
     if (t == 0 && !st.err) {
       tc_fence_after_sync();
 #pragma unroll
@@ -292,8 +292,8 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       float dh[32], a1[32];
-      tc_ld32_if(st, lane_base + kTrDH1 + 32 * h, dh);
-      tc_ld32_if(st, lane_base + kTrA1 + 32 * h, a1);
+      tc_ld32(lane_base + kTrDH1 + 32 * h, dh);
+      tc_ld32(lane_base + kTrA1 + 32 * h, a1);
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         const float da = valid ? dh[q] * dsilu(a1[q]) : 0.f;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
       }
     }
     // ---- gW2 += da2^T h1 and gW1 += da1^T x over the 128 samples
-    tc_group_open(st);
+    tc_group_open();
     if (t == 0 && !st.err) {
       tc_fence_after_sync();
 #pragma unroll
@@ -324,13 +324,13 @@ __global__ void __launch_bounds__(128) k_mlp_train(const MlpPacked *__restrict__
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         float v[32];
-        tc_ld32_if(st, lane_base + kTrGW2 + 32 * h, v);
+        tc_ld32(lane_base + kTrGW2 + 32 * h, v);
 #pragma unroll
         for (int q = 0; q < 32; ++q) S.g[kMlpOffW2 + t * kMlpH + 32 * h + q] += v[q];
       }
     } else {
       float v[32];
-      tc_ld32_if(st, lane_base + kTrGW1, v);
+      tc_ld32(lane_base + kTrGW1, v);
 #pragma unroll
       for (int k = 0; k < kMlpIn; ++k) S.g[kMlpOffW1 + (t - kMlpH) * kMlpIn + k] += v[k];
     }

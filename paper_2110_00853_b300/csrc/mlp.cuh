@@ -107,11 +107,18 @@ constexpr int kTcWaitLimit = 1 << 20;       // mbarrier tries before giving up
 struct TcState {
   uint32_t tmem;    // TMEM base address of this CTA's columns
   uint64_t *mbar;   // MMA completion barrier (shared memory)
-  uint32_t parity;  // parity of the oldest committed phase this thread has not seen complete
-  int pending;      // thread 0: a committed phase it has not seen complete (its wait gave up)
-  int err;          // sticky and CTA-uniform after each group opening: a wait gave up
-  int first_limit;  // tries of the next completion wait (test hook: 0 gives up at once)
+  uint32_t parity;  // parity of the next phase to complete
+  int err;          // sticky: a wait gave up (results of this CTA invalid)
+  int hook;         // test hook (instances built for it only): the next wait gives up at once
 };
+
+// The committed phase that thread 0 has not seen complete, as 1 + its
+// parity (0: none), kept in shared memory rather than in registers: it is
+// written only when a wait gives up and read only by the tear-down.
+__device__ __forceinline__ uint32_t &tc_pending() {
+  __shared__ uint32_t pending;
+  return pending;
+}
 
 // Write this thread's row of the A buffer for layer 1: the 13 inputs (BF16),
 // the three bias columns, and the bias and zero groups of layers 2 and 3
@@ -135,6 +142,7 @@ __device__ __forceinline__ void tc_setup(TcState &s, uint32_t *slot, uint64_t *m
   if (threadIdx.x < 32) tc_alloc(slot, ncols);
   if (threadIdx.x == 0) {
     mbar_init(mbar, 1);
+    tc_pending() = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   tc_fence_before_sync();
@@ -143,22 +151,46 @@ __device__ __forceinline__ void tc_setup(TcState &s, uint32_t *slot, uint64_t *m
   s.tmem = *slot;
   s.mbar = mbar;
   s.parity = 0;
-  s.pending = 0;
   s.err = 0;
-  s.first_limit = kTcWaitLimit;
+  s.hook = 0;
 }
 
-// Tear-down: make sure no MMA of the CTA is still running, free the TMEM
-// columns, and count the CTA once in *err_count if any wait gave up.  Thread
-// 0 issues every commit and waits for each, so at most one committed phase
-// can be unseen (its wait gave up); commits complete in order and none
-// follows it, so a bounded wait on that phase drains the CTA's MMAs before
-// the columns are freed.  All threads must call it.
+// Wait (bounded) for the MMAs thread 0 has committed.  A wait that gives up
+// sets the sticky error flag; thread 0 records the phase it has not seen
+// complete, which the tear-down waits for before freeing the columns.  Once
+// the flag is set thread 0 issues and commits nothing more and later waits
+// make one try, so a failing CTA runs through its remaining work quickly (its
+// results are reported invalid).  HOOK instances (test hook 2) give up on
+// their first wait at once (s.hook).
+template <bool HOOK = false>
+__device__ __forceinline__ void tc_wait_group(TcState &s) {
+  bool ok;
+  if (HOOK && s.hook) {
+    s.hook = 0;
+    ok = false;
+  } else {
+    ok = mbar_wait_bounded(s.mbar, s.parity, s.err ? 1 : kTcWaitLimit);
+  }
+  if (!ok) {
+    if (!s.err && threadIdx.x == 0) tc_pending() = 1u + s.parity;
+    s.err = 1;
+  }
+  s.parity ^= 1u;
+  __syncwarp();  // the TMEM loads that follow are warp-collective
+  tc_fence_after_sync();
+}
+
+// Tear-down: thread 0 waits (bounded) for a committed phase it has not seen
+// complete (commits complete in order and thread 0 commits nothing after a
+// wait gave up, so that phase is the last one), so that no MMA of the CTA
+// still runs when the TMEM columns are freed; the CTA is counted once in
+// *err_count if any of its waits gave up.  All threads must call it.
 __device__ __forceinline__ void tc_teardown(TcState &s, int *err_count, uint32_t ncols = kTcCols) {
   tc_fence_before_sync();
-  s.err = __syncthreads_or(s.err);
-  if (threadIdx.x == 0 && s.pending) {
-    if (mbar_wait_bounded(s.mbar, s.parity, kTcWaitLimit)) s.pending = 0;
+  const int any_err = __syncthreads_or(s.err);
+  if (threadIdx.x == 0) {
+    const uint32_t pend = tc_pending();
+    if (pend) mbar_wait_bounded(s.mbar, pend - 1u, kTcWaitLimit);
   }
   tc_fence_before_sync();
   __syncthreads();
@@ -166,63 +198,29 @@ __device__ __forceinline__ void tc_teardown(TcState &s, int *err_count, uint32_t
     tc_fence_after_sync();
     tc_dealloc(s.tmem, ncols);
   }
-  if (threadIdx.x == 0 && s.err) atomicAdd(err_count, 1);
+  if (threadIdx.x == 0 && any_err) atomicAdd(err_count, 1);
 }
 
 // One MMA group of the CTA: every thread makes its shared-memory operand
-// writes visible to the tensor core and meets the others (tc_group_open,
-// which also makes the error flag CTA-uniform); thread 0 then issues the
-// group's MMAs unless a wait has given up; tc_group_close commits them to the
-// barrier and waits (bounded) for their completion in every thread.  A wait
-// that gives up keeps its phase as the one to drain and sets the error flag;
-// later groups of the CTA issue nothing and wait for nothing.
-__device__ __forceinline__ void tc_group_open(TcState &s) {
+// writes visible to the tensor core and meets the others (tc_group_open);
+// thread 0 then issues the group's MMAs unless one of its waits has given up;
+// tc_group_close commits them to the barrier and waits for their completion
+// in every thread (tc_wait_group).
+__device__ __forceinline__ void tc_group_open() {
   fence_proxy_async_smem();
   tc_fence_before_sync();
-  s.err = __syncthreads_or(s.err);
+  __syncthreads();
 }
 __device__ __forceinline__ void tc_group_close(TcState &s) {
-  if (s.err) return;
-  if (threadIdx.x == 0) {
-    tc_commit(s.mbar);
-    s.pending = 1;
-  }
-  const int limit = s.first_limit;
-  s.first_limit = kTcWaitLimit;
-  if (mbar_wait_bounded(s.mbar, s.parity, limit)) {
-    s.parity ^= 1u;
-    s.pending = 0;
-  } else {
-    s.err = 1;
-  }
-  // warp-uniform, so that the warp-collective TMEM loads that follow are
-  // skipped (tc_ld32_if) by whole warps
-  s.err = __any_sync(0xffffffffu, s.err);
-  tc_fence_after_sync();
-}
-
-// TMEM loads of a group's results, skipped (zeros) once a wait has given up:
-// the accumulator may then still be written by a running MMA.
-__device__ __forceinline__ void tc_ld32_if(const TcState &s, uint32_t taddr, float v[32]) {
-  if (!s.err) {
-    tc_ld32(taddr, v);
-  } else {
-#pragma unroll
-    for (int q = 0; q < 32; ++q) v[q] = 0.f;
-  }
-}
-__device__ __forceinline__ void tc_ld2_if(const TcState &s, uint32_t taddr, float &v0, float &v1) {
-  if (!s.err) {
-    tc_ld2(taddr, v0, v1);
-  } else {
-    v0 = v1 = 0.f;
-  }
+  if (threadIdx.x == 0 && !s.err) tc_commit(s.mbar);
+  tc_wait_group(s);
 }
 
 // Forward pass of the CTA's 128 rows; (y0, y1) of this thread's row.  All
 // 128 threads must call it (it contains block barriers).  The A buffer's
 // layer-1 columns must have been written by every thread and the bias and
 // zero groups (columns 64..79) set.
+template <bool HOOK = false>
 __device__ __forceinline__ void mlp_tc_forward(const MlpTc &W, __nv_bfloat16 *A, TcState &s, float &y0,
                                                float &y1) {
   const int t = threadIdx.x;
@@ -230,7 +228,9 @@ __device__ __forceinline__ void mlp_tc_forward(const MlpTc &W, __nv_bfloat16 *A,
   constexpr uint32_t kSboA = 8 * 16 * kTcKG, kSbo1 = 8 * 16 * kTcKG1;
 #pragma unroll 1
   for (int layer = 0; layer < 3; ++layer) {
-    tc_group_open(s);
+    fence_proxy_async_smem();
+    tc_fence_before_sync();
+    __syncthreads();
     if (t == 0 && !s.err) {
       tc_fence_after_sync();
       if (layer == 0) {
@@ -243,13 +243,22 @@ __device__ __forceinline__ void mlp_tc_forward(const MlpTc &W, __nv_bfloat16 *A,
           tc_mma(s.tmem, tc_sdesc(A + ks * 128, 128, kSboA), tc_sdesc(B + ks * 128, 128, kSboA), idesc,
                  ks > 0 ? 1u : 0u);
       }
+      tc_commit(s.mbar);
     }
-    tc_group_close(s);  // the TMEM loads below are warp-collective: close ends with __syncwarp
+    tc_wait_group<HOOK>(s);
+    // the test instance reads no TMEM once its wait gave up (its MMA may
+    // still be writing it) and leaves the drain to the tear-down
+    const bool skip = HOOK && s.err;
     if (layer < 2) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         float v[32];
-        tc_ld32_if(s, lane_base + 32 * h, v);
+        if (skip) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = 0.f;
+        } else {
+          tc_ld32(lane_base + 32 * h, v);
+        }
         uint32_t w[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) w[q] = silu2_bf16(v[2 * q], v[2 * q + 1]);
@@ -258,8 +267,10 @@ __device__ __forceinline__ void mlp_tc_forward(const MlpTc &W, __nv_bfloat16 *A,
           *reinterpret_cast<uint4 *>(A + tc_off(t, 32 * h + 8 * kk, kTcKG)) =
               make_uint4(w[4 * kk], w[4 * kk + 1], w[4 * kk + 2], w[4 * kk + 3]);
       }
+    } else if (skip) {
+      y0 = y1 = 0.f;
     } else {
-      tc_ld2_if(s, lane_base, y0, y1);
+      tc_ld2(lane_base, y0, y1);
     }
   }
 }

@@ -122,8 +122,8 @@ def test_tensor_core_wait_timeout_is_reported_and_cleared(orc):
 def test_tensor_core_drain_after_a_wait_gives_up(orc):
     """A CTA whose MMA completion wait gives up while its MMA is still in
     flight (test hook mode 2: the first wait of each CTA makes no try) issues
-    no further MMA, skips its Tensor Memory reads, and at its tear-down waits
-    (bounded) for that MMA before freeing the columns.  The launch reports
+    no further MMA, reads no Tensor Memory, and at its tear-down waits
+    (bounded) for that MMA's completion before freeing the columns.  The launch reports
     CMLES_ERR_TIMEOUT with every CTA counted once; the context stays usable
     and the next tendency, with the hook off, is bit-identical to one taken
     before (its CTAs allocate the same Tensor Memory columns)."""
