@@ -240,6 +240,23 @@ cmles_status cmles_diagnostics(cmles_handle h, cmles_diag *out);
  * Synchronises the stream. */
 cmles_status cmles_profiles(cmles_handle h, double *out_host);
 
+/* Kinetic-energy spectrum of the current state (the turbulence diagnostic of
+ * Sec. 5.5, a Fourier transform of the velocity field), on a flat mesh
+ * periodic in x and y; synchronises the stream.  Readings: velocity
+ * u = (rho u)/rho at the nodes; resampled onto a uniform grid of N points per
+ * element and direction at the cell centres xi_s = -1 + (2s+1)/N of each
+ * element (M_x = nex N, M_y = ney N points per level, M_z = nez N levels)
+ * with the element's Lagrange polynomial; per level the discrete Fourier
+ * coefficients u^(p,q) = 1/(M_x M_y) sum_ij u_ij exp(-2 pi i (p i/M_x +
+ * q j/M_y)); E_host[s] (s < nshell) = the level average of the sum of
+ * (|u^|^2 + |v^|^2 + |w^|^2)/2 over the shell s = round(L sqrt((p/L_x)^2 +
+ * (q/L_y)^2)), L = max(L_x, L_y); higher shells are dropped.  By Parseval the
+ * sum over all shells is the grid mean of |u|^2/2.  FP64 throughout; the call
+ * allocates its scratch (the grid and two transforms, 9 doubles per grid
+ * point) on the handle's stream.  Errors: CMLES_ERR_ARG (nshell < 1, warped,
+ * partitioned or not periodic in x and y), CMLES_ERR_CUDA. */
+cmles_status cmles_spectrum(cmles_handle h, int nshell, double *E_host);
+
 /* Learned SGS closure (not in the paper; an extension of Sec. 4):
  * a per-node network 13 -> 64 -> 64 -> 2 with SiLU hidden activations, BF16
  * weights and activations and FP32 accumulation on tensor cores, evaluated

@@ -109,6 +109,7 @@ def load(path=LIB_PATH):
     L.cmles_commit_staged_state.argtypes = [_H]
     L.cmles_hevi_operator.argtypes = [_H, _VP, _VP]
     L.cmles_hevi_solve.argtypes = [_H, _VP, _VP]
+    L.cmles_spectrum.argtypes = [_H, C.c_int, _DP]
     L.cmles_group_create.argtypes = [C.POINTER(Mesh), C.POINTER(Params), C.c_int, C.c_int, C.POINTER(_VP)]
     L.cmles_group_destroy.argtypes = [_VP]
     L.cmles_group_last_error_message.argtypes = [_VP]
@@ -338,6 +339,12 @@ class Solver:
     def profiles(self):
         out = np.zeros((self.nlev, 11))
         self._check(self.L.cmles_profiles(self.h, out.ctypes.data_as(_DP)))
+        return out
+
+    def spectrum(self, nshell):
+        """Kinetic-energy spectrum E[nshell] of the current state (see cmles_spectrum)."""
+        out = np.zeros(nshell)
+        self._check(self.L.cmles_spectrum(self.h, int(nshell), out.ctypes.data_as(_DP)))
         return out
 
     def set_closure_weights(self, flat):
