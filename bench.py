@@ -67,7 +67,14 @@ VARIANTS = {"fp32acc64_mlp": ("fp32", "mlp", "rusanov", "lsrk54"), "fp32acc64_sl
             "fp32acc64_mlp_lsrk144": ("fp32", "mlp", "rusanov", "lsrk144"),
             "fp64_sl_lsrk144": ("fp64", "sl", "rusanov", "lsrk144"),
             "fp64_sl_hevi": ("fp64", "sl", "rusanov", "ark2_hevi"),
-            "fp32acc64_mlp_hevi": ("fp32", "mlp", "rusanov", "ark2_hevi")}
+            "fp32acc64_mlp_hevi": ("fp32", "mlp", "rusanov", "ark2_hevi"),
+            # the flow over the Gaussian ridge at its configured size: 128 x 16 x 64
+            # warped elements (16.4M nodes), curvilinear FP32 kernels
+            "c3_fp32acc64_sl": ("fp32", "sl", "rusanov", "lsrk54"),
+            "c3_fp32acc64_mlp": ("fp32", "mlp", "rusanov", "lsrk54")}
+# the workload of a variant: the throughput box unless its name says otherwise
+def variant_workload(name):
+    return "c3" if name.startswith("c3_") else WORKLOAD
 DTYPE = {"fp32": "f32", "fp64": "f64"}
 # What bounds each dominant kernel, from its ncu capture (profiles/): the
 # roofline above is HBM's, the metric's; the gradient passes are limited by
@@ -252,15 +259,16 @@ def closure_weights():
                                b3=(0.5, 0.5))
 
 
-def workload_mesh(sub):
-    """the throughput box, or a sub-box of it with the same element size
+def workload_mesh(sub, workload=WORKLOAD):
+    """the workload's mesh, or a sub-box of it with the same element size
     (used for small profiling cases)"""
-    return I.mesh(WORKLOAD) if sub is None else I.sub_mesh(WORKLOAD, *sub)
+    return I.mesh(workload) if sub is None else I.sub_mesh(workload, *sub)
 
 
 def run_variant(name, precision, closure, flux, integrator, steps, warmup, world, rank, torch, sub=None):
     from paper_2110_00853_b300 import cmles
-    mesh, phys, case = workload_mesh(sub), I.physics(WORKLOAD, closure=closure), I.case(WORKLOAD)
+    wl = variant_workload(name)
+    mesh, phys, case = workload_mesh(sub, wl), I.physics(wl, closure=closure), I.case(wl)
     phys["flux"] = flux
     phys["integrator"] = integrator
     G = cmles.Solver(mesh, phys, precision=precision)
@@ -461,7 +469,11 @@ def main():
             gbs = r["nodes"] * alg_bytes(vprec, kinds[k], STAGES[vint], vint) / (a / 1e3) / 1e9
             per[kinds[k]] = dict(avg_ms=a, launches=r["kt"]["count"][k], gbs=gbs, hbm_frac=gbs / hbm)
         out_variants[name] = dict(value=v, ms_per_step=r["ms"] / args.steps, kernels=per, finite=r["finite"],
-                                  satadj_failures=r["satadj_failures"])
+                                  satadj_failures=r["satadj_failures"], workload=variant_workload(name),
+                                  nodes=r["nodes"])
+        if variant_workload(name) == "c3":
+            out_variants[name]["bytes_note"] = ("GB/s from the flat-mesh byte counts; the curvilinear kernels "
+                                                "also read per-node metric terms and reference tables")
     e2e = None
     if not args.no_e2e and rank == 0 and sub is None:
         e2e = run_e2e(variants[0][1], variants[0][2], variants[0][3], variants[0][4], max(2, min(args.steps, 4)),

@@ -187,6 +187,7 @@ void fill_kparams(cmles_handle h) {
   K.surface_flux = p.surface_flux;
   K.E_water = p.lhf / p.Lv0;
   K.E_energy = p.shf + p.lhf;
+  K.N = h->N;
   K.nex = m.nex;
   K.ney = m.ney;
   K.nez = m.nez;
@@ -686,7 +687,10 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
                                        cmles_handle *out) {
   if (!mesh || !params || !out) return CMLES_ERR_ARG;
   *out = nullptr;
-  if (mesh->N != 4) return CMLES_ERR_ARG;
+  // flat meshes: the kernels are instantiated for the orders 1 .. 4; warped
+  // meshes and HEVI for order 4
+  if (mesh->N < 1 || mesh->N > 4) return CMLES_ERR_ARG;
+  if ((mesh->warp || params->integrator == CMLES_ARK2_HEVI) && mesh->N != 4) return CMLES_ERR_ARG;
   if (mesh->nex < 1 || mesh->ney < 1 || mesh->nez < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0))
     return CMLES_ERR_MESH;
   // warped (curvilinear) meshes run on the FP32 path

@@ -70,7 +70,8 @@ struct KParams {
   int surface_flux;
   double E_water;    // LHF / L_v0 (kg m^-2 s^-1)
   double E_energy;   // SHF + LHF (W m^-2)
-  // mesh (flat, uniform elements)
+  // mesh (flat, uniform elements); N: the polynomial order
+  int N;
   int nex, ney, nez, E;
   int periodic[3];
   double x0, y0, z0, hx, hy, hz;

@@ -512,60 +512,86 @@ cudaError_t launch_shadow32(const double *Q64, float *S, float *TH, const KParam
   return cudaGetLastError();
 }
 
-template <int CL>
+template <int N, int CL>
 static void grad32_instance(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
   static int grid = 0;
   if (!grid)
-    grid = CL == 2 ? grid_for_tc((const void *)k_grad32<4, CL>, 1 << 30, kTcCols)
-                   : grid_for((const void *)k_grad32<4, CL>, 1 << 30, 0);
+    grid = CL == 2 ? grid_for_tc((const void *)k_grad32<N, CL>, 1 << 30, kTcCols)
+                   : grid_for((const void *)k_grad32<N, CL>, 1 << 30, 0);
   if (CL == 2 && P.tc_stall == 2) {
     static int hgrid = 0;
-    if (!hgrid) hgrid = grid_for_tc((const void *)k_grad32<4, 2, true>, 1 << 30, kTcCols);
-    k_grad32<4, 2, true><<<hgrid < P.E ? hgrid : P.E, 128, 0, s>>>(S, TH, F2, P);
+    if (!hgrid) hgrid = grid_for_tc((const void *)k_grad32<N, 2, true>, 1 << 30, kTcCols);
+    k_grad32<N, 2, true><<<hgrid < P.E ? hgrid : P.E, 128, 0, s>>>(S, TH, F2, P);
     return;
   }
-  k_grad32<4, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, TH, F2, P);
+  k_grad32<N, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, TH, F2, P);
 }
 
-cudaError_t launch_grad32(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
+template <int N>
+static void grad32_order(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
   if (P.closure == 2)
-    grad32_instance<2>(S, TH, F2, P, s);
+    grad32_instance<N, 2>(S, TH, F2, P, s);
   else if (P.closure == 3)
-    grad32_instance<3>(S, TH, F2, P, s);
+    grad32_instance<N, 3>(S, TH, F2, P, s);
   else
-    grad32_instance<1>(S, TH, F2, P, s);
+    grad32_instance<N, 1>(S, TH, F2, P, s);
+}
+
+// the flat-mesh kernels are instantiated for the orders 1 .. 4 (one thread
+// per node of a 128-thread CTA, 128-node padding)
+cudaError_t launch_grad32(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
+  switch (P.N) {
+    case 1: grad32_order<1>(S, TH, F2, P, s); break;
+    case 2: grad32_order<2>(S, TH, F2, P, s); break;
+    case 3: grad32_order<3>(S, TH, F2, P, s); break;
+    case 4: grad32_order<4>(S, TH, F2, P, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
-template <int UPD, int FL>
+template <int N, int UPD, int FL>
 static void k_rhs32_instance(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
                              float *THout, double *Rout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
   static int grid = 0;
-  if (!grid) grid = grid_for((const void *)k_rhs32<4, UPD, FL>, 1 << 30, 0);
-  k_rhs32<4, UPD, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P);
+  if (!grid) grid = grid_for((const void *)k_rhs32<N, UPD, FL>, 1 << 30, 0);
+  k_rhs32<N, UPD, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P);
 }
 
-template <int FL>
+template <int N, int FL>
 static void k_rhs32_dispatch(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
                              float *THout, double *Rout, const StageCoef &sc, bool update, const KParams &P,
                              cudaStream_t s) {
   if (!update)
-    k_rhs32_instance<0, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
+    k_rhs32_instance<N, 0, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
   else if (sc.last)
-    k_rhs32_instance<2, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
+    k_rhs32_instance<N, 2, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
   else
-    k_rhs32_instance<1, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
+    k_rhs32_instance<N, 1, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
+}
+
+template <int N>
+static void rhs32_order(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
+                        float *THout, double *Rout, const StageCoef &sc, bool update, const KParams &P,
+                        cudaStream_t s) {
+  if (P.flux == 2)
+    k_rhs32_dispatch<N, 2>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
+  else if (P.flux == 1)
+    k_rhs32_dispatch<N, 1>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
+  else
+    k_rhs32_dispatch<N, 0>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
 }
 
 cudaError_t launch_rhs32(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
                          float *THout, double *Rout, const StageCoef &sc, bool update, const KParams &P,
                          cudaStream_t s) {
-  if (P.flux == 2)
-    k_rhs32_dispatch<2>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
-  else if (P.flux == 1)
-    k_rhs32_dispatch<1>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
-  else
-    k_rhs32_dispatch<0>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
+  switch (P.N) {
+    case 1: rhs32_order<1>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    case 2: rhs32_order<2>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    case 3: rhs32_order<3>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    case 4: rhs32_order<4>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -440,37 +440,62 @@ cudaError_t launch_thermo64(const double *Q, double *TH, const KParams &P, int N
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad64(const double *Q, const double *TH, double *F2, const KParams &P, cudaStream_t s) {
+template <int N>
+static void grad64_instance(const double *Q, const double *TH, double *F2, const KParams &P, cudaStream_t s) {
   static int grid = 0;
-  if (!grid) grid = grid_for((const void *)k_grad64<4>, 1 << 30);
-  k_grad64<4><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, TH, F2, P);
+  if (!grid) grid = grid_for((const void *)k_grad64<N>, 1 << 30);
+  k_grad64<N><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, TH, F2, P);
+}
+
+// the flat-mesh kernels are instantiated for the orders 1 .. 4 (one thread
+// per node of a 128-thread CTA)
+cudaError_t launch_grad64(const double *Q, const double *TH, double *F2, const KParams &P, cudaStream_t s) {
+  switch (P.N) {
+    case 1: grad64_instance<1>(Q, TH, F2, P, s); break;
+    case 2: grad64_instance<2>(Q, TH, F2, P, s); break;
+    case 3: grad64_instance<3>(Q, TH, F2, P, s); break;
+    case 4: grad64_instance<4>(Q, TH, F2, P, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
-template <bool UPDATE, int FL>
+template <int N, bool UPDATE, int FL>
 static void rhs64_instance(const double *Q, const double *F2, const double *TH, double *dQ, double *Qout,
                            double *THout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
   static int grid = 0;
-  if (!grid) grid = grid_for((const void *)k_rhs64<4, UPDATE, FL>, 1 << 30);
-  k_rhs64<4, UPDATE, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, TH, dQ, Qout, THout, sc, P);
+  if (!grid) grid = grid_for((const void *)k_rhs64<N, UPDATE, FL>, 1 << 30);
+  k_rhs64<N, UPDATE, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, TH, dQ, Qout, THout, sc, P);
+}
+
+template <int N>
+static void rhs64_order(const double *Q, const double *F2, const double *TH, double *dQ, double *Qout,
+                        double *THout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
+  if (update) {
+    if (P.flux == 2)
+      rhs64_instance<N, true, 2>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
+    else if (P.flux == 1)
+      rhs64_instance<N, true, 1>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
+    else
+      rhs64_instance<N, true, 0>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
+  } else {
+    if (P.flux == 2)
+      rhs64_instance<N, false, 2>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
+    else if (P.flux == 1)
+      rhs64_instance<N, false, 1>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
+    else
+      rhs64_instance<N, false, 0>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
+  }
 }
 
 cudaError_t launch_rhs64(const double *Q, const double *F2, const double *TH, double *dQ, double *Qout,
                          double *THout, const StageCoef &sc, bool update, const KParams &P, cudaStream_t s) {
-  if (update) {
-    if (P.flux == 2)
-      rhs64_instance<true, 2>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
-    else if (P.flux == 1)
-      rhs64_instance<true, 1>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
-    else
-      rhs64_instance<true, 0>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
-  } else {
-    if (P.flux == 2)
-      rhs64_instance<false, 2>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
-    else if (P.flux == 1)
-      rhs64_instance<false, 1>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
-    else
-      rhs64_instance<false, 0>(Q, F2, TH, dQ, Qout, THout, sc, P, s);
+  switch (P.N) {
+    case 1: rhs64_order<1>(Q, F2, TH, dQ, Qout, THout, sc, update, P, s); break;
+    case 2: rhs64_order<2>(Q, F2, TH, dQ, Qout, THout, sc, update, P, s); break;
+    case 3: rhs64_order<3>(Q, F2, TH, dQ, Qout, THout, sc, update, P, s); break;
+    case 4: rhs64_order<4>(Q, F2, TH, dQ, Qout, THout, sc, update, P, s); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

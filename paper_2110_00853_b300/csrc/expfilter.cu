@@ -53,11 +53,21 @@ __global__ void __launch_bounds__(128) k_expfilter(double *__restrict__ Q, float
   }
 }
 
-cudaError_t launch_expfilter(double *Q, float *S32, const ExpFilter &F, int N, int E, cudaStream_t s) {
-  if (N != 4) return cudaErrorInvalidValue;
+template <int N>
+static void expfilter_order(double *Q, float *S32, const ExpFilter &F, int E, cudaStream_t s) {
   static int grid = 0;
-  if (!grid) grid = grid_for((const void *)k_expfilter<4>, 1 << 30, 0);
-  k_expfilter<4><<<grid < E ? grid : E, 128, 0, s>>>(Q, S32, F, E);
+  if (!grid) grid = grid_for((const void *)k_expfilter<N>, 1 << 30, 0);
+  k_expfilter<N><<<grid < E ? grid : E, 128, 0, s>>>(Q, S32, F, E);
+}
+
+cudaError_t launch_expfilter(double *Q, float *S32, const ExpFilter &F, int N, int E, cudaStream_t s) {
+  switch (N) {
+    case 1: expfilter_order<1>(Q, S32, F, E, s); break;
+    case 2: expfilter_order<2>(Q, S32, F, E, s); break;
+    case 3: expfilter_order<3>(Q, S32, F, E, s); break;
+    case 4: expfilter_order<4>(Q, S32, F, E, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -66,3 +66,20 @@ def test_create_rejects_unsupported_combinations_without_gpu_work():
     P = cmles.make_params({}, "fp64")
     P.precision = 5
     assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == ERR_ARG
+
+
+def test_create_order_limits_without_gpu_work():
+    """Flat meshes take the orders 1 .. 4 (the instantiated kernels); warped
+    meshes and HEVI only 4; other orders are rejected before any device work."""
+    L = cmles.load()
+    h = ctypes.c_void_p()
+
+    def status(N, precision="fp64", warp=False, **kw):
+        m = cmles.make_mesh(dict(N=N, nex=2, ney=2, nez=2, Lx=1000.0, Ly=1000.0, Lz=1000.0, warp=warp))
+        P = cmles.make_params(kw, precision)
+        return L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h))
+
+    for N in (0, 5, 7, 8):
+        assert status(N) == 1 and status(N, "fp32") == 1
+    assert status(3, "fp32", warp=True) == 1
+    assert status(3, integrator="ark2_hevi") == 1

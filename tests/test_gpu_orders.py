@@ -1,0 +1,124 @@
+"""Polynomial orders other than 4 (the flat-mesh kernels are instantiated for
+N = 1 .. 4): tendency parity with the oracle on the FP64 and the FP32 path
+(moist layer, walls, sponge, surface fluxes; the learned closure at N = 3),
+and order-(N+1) convergence of the FP64 path on the translating isentropic
+vortex (dry, g = 0, triply periodic; Shu 1998), with the GPU's error matching
+the oracle's on the coarse mesh."""
+import numpy as np
+import pytest
+
+from paper_2110_00853_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _levels(arr, mesh):
+    Nq = mesh["N"] + 1
+    return np.array([arr[ez * mesh["nex"] * mesh["ney"], k * Nq * Nq] for ez in range(mesh["nez"])
+                     for k in range(Nq)])
+
+
+def _fuzz(Q, seed, amp_u=3.0, amp_rho=1e-3, amp_e=50.0):
+    rng = np.random.default_rng(seed)
+    Q = Q.copy()
+    rho = Q[:, 0]
+    u = rng.uniform(-amp_u, amp_u, size=(Q.shape[0], 3, Q.shape[2]))
+    Q[:, 4] += 0.5 * rho * (u ** 2).sum(axis=1) + (Q[:, 1:4] * u).sum(axis=1)
+    Q[:, 1:4] += rho[:, None] * u
+    Q[:, 0] *= 1.0 + rng.uniform(-amp_rho, amp_rho, size=rho.shape)
+    Q[:, 4] += rng.uniform(-amp_e, amp_e, size=rho.shape)
+    return Q
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("N,precision,closure", [(1, "fp64", "sl"), (2, "fp64", "vreman"), (3, "fp64", "sl"),
+                                                 (2, "fp32", "sl"), (3, "fp32", "sl"), (3, "fp32", "mlp"),
+                                                 (1, "fp32", "sl")])
+def test_tendency_other_orders(orc, N, precision, closure):
+    from paper_2110_00853_b300 import cmles
+    m = I.sub_mesh("c2", 5, 3, 8, N=N)
+    ph = I.physics("c2", closure=closure)
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case("c2"))
+    Q = _fuzz(Q, 20 + N)
+    G = cmles.Solver(m, ph, precision=precision)
+    G.set_reference(_levels(rr, m), _levels(pr, m), _levels(Q[:, 5] / Q[:, 0], m))
+    if closure == "mlp":
+        from paper_2110_00853_b300 import closure as CL
+        p = CL.init_params(seed=0, in_scale=[100.0] * 9 + [300.0] * 3 + [0.02], out_scale=(5.0, 10.0),
+                           b3=(0.5, 0.5)).astype(np.float64)
+        sizes = (("W1", 64 * 13, True), ("b1", 64, False), ("W2", 64 * 64, True), ("b2", 64, False),
+                 ("W3", 2 * 64, True), ("b3", 2, False))
+        W, o = {}, 0
+        for k, n, is_w in sizes:
+            W[k] = np.array([orc.bf16(x) for x in p[o:o + n]]) if is_w else p[o:o + n].copy()
+            o += n
+        flat = np.concatenate([W[k] for k, _, _ in sizes] + [p[o:o + 13], p[o + 13:o + 15]]).astype(np.float32)
+        S.set_mlp(W, p[o:o + 13], p[o + 13:o + 15])
+        G.set_closure_weights(flat)
+    R_orc, fails = S.rhs(Q)
+    assert fails == 0
+    R_gpu = G.tendency(torch.from_numpy(Q).cuda()).cpu().numpy()
+    tol = 1e-12 if precision == "fp64" else (1e-4 if closure == "mlp" else 1e-5)
+    errs = [_rel(R_gpu[:, v], R_orc[:, v]) for v in range(6)]
+    print(N, precision, closure, "rel L2", errs)
+    for v in range(6):
+        assert errs[v] <= tol, (v, errs)
+        assert np.abs(R_gpu[:, v] - R_orc[:, v]).max() <= 10 * tol * np.abs(R_orc[:, v]).max(), v
+    # and one LSRK step against the oracle's
+    G.set_state(torch.from_numpy(Q).cuda())
+    G.step(1)
+    Qo, _ = S.lsrk54(Q, 1, ph["dt"])
+    Qg = G.get_state().cpu().numpy()
+    for v in range(6):
+        e = _rel(Qg[:, v] - Q[:, v], Qo[:, v] - Q[:, v])
+        assert e <= (1e-11 if precision == "fp64" else (1e-4 if closure == "mlp" else 1e-5)), (v, e)
+    G.close()
+
+
+def _vortex(orc, N, nel, T=0.02, cfl=0.3):
+    """(GPU L2 density error at T, oracle state setup) on an nel x nel x 1 mesh"""
+    from paper_2110_00853_b300 import cmles
+    M = orc.make_mesh(N, nel, nel, 1, 10.0, 10.0, 10.0 / nel, x0=-5.0, y0=-5.0, periodic=(1, 1, 1))
+    P = orc.make_params(closure="none", g=0.0)
+    S = orc.Solver(M, P)
+    c = orc.make_case(10, vortex_beta=5.0, vortex_R=1.0, vortex_U=10.0, vortex_T=300.0, vortex_rho=1.0)
+    Q0, _, _ = S.init_case(c)
+    dt = cfl * 10.0 / nel / N / 360.0
+    n = int(np.ceil(T / dt))
+    mesh = dict(N=N, nex=nel, ney=nel, nez=1, Lx=10.0, Ly=10.0, Lz=10.0 / nel, x0=-5.0, y0=-5.0, z0=0.0,
+                periodic=(1, 1, 1))
+    ph = dict(closure="none", g=0.0, dt=T / n, moist=False)
+    G = cmles.Solver(mesh, ph, precision="fp64")
+    pinf = 1.0 * 287.0 * 300.0
+    G.set_reference(np.full(N + 1, 1.0), np.full(N + 1, pinf), None)
+    G.set_state(torch.from_numpy(Q0).cuda())
+    G.step(n)
+    Qg = G.get_state().cpu().numpy()
+    G.close()
+    Qe = S.vortex_exact(c, T)
+    wJ = S.geometry()["wJ"]
+    err = np.sqrt((wJ * (Qg[:, 0] - Qe[:, 0]) ** 2).sum() / wJ.sum())
+    return err, S, Q0, n, T
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_isentropic_vortex_order_on_the_gpu(orc, N):
+    e8, S, Q0, n, T = _vortex(orc, N, 8)
+    e16, _, _, _, _ = _vortex(orc, N, 16)
+    e32, _, _, _, _ = _vortex(orc, N, 32)
+    # the finer pair: at 8 -> 16 elements the odd order N = 3 is still
+    # pre-asymptotic (order 3.4, the same in the oracle)
+    order = np.log2(e16 / e32)
+    # the oracle's own error on the coarse mesh: the same scheme, so the same error
+    Q1, _ = S.lsrk54(Q0, n, T / n)
+    c = orc.make_case(10, vortex_beta=5.0, vortex_R=1.0, vortex_U=10.0, vortex_T=300.0, vortex_rho=1.0)
+    Qe = S.vortex_exact(c, T)
+    wJ = S.geometry()["wJ"]
+    e8o = np.sqrt((wJ * (Q1[:, 0] - Qe[:, 0]) ** 2).sum() / wJ.sum())
+    print("N", N, "errors", e8, e16, e32, "order", order, "oracle coarse error", e8o)
+    assert abs(e8 - e8o) <= 1e-6 * e8o
+    assert order > N + 0.5, (N, e8, e16, e32, order)
