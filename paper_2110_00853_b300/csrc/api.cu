@@ -687,9 +687,10 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
                                        cmles_handle *out) {
   if (!mesh || !params || !out) return CMLES_ERR_ARG;
   *out = nullptr;
-  // flat meshes: the kernels are instantiated for the orders 1 .. 4; warped
-  // meshes and HEVI for order 4
-  if (mesh->N < 1 || mesh->N > 4) return CMLES_ERR_ARG;
+  // the kernels are instantiated for the orders 1 .. 7 on flat meshes in
+  // FP64, 1 .. 4 on flat meshes in FP32, and 4 on warped meshes and for HEVI
+  if (mesh->N < 1 || mesh->N > 7) return CMLES_ERR_ARG;
+  if (params->precision == CMLES_FP32_ACC64 && mesh->N > 4) return CMLES_ERR_ARG;
   if ((mesh->warp || params->integrator == CMLES_ARK2_HEVI) && mesh->N != 4) return CMLES_ERR_ARG;
   if (mesh->nex < 1 || mesh->ney < 1 || mesh->nez < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0))
     return CMLES_ERR_MESH;

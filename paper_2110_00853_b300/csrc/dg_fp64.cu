@@ -22,6 +22,13 @@
 
 namespace cmles {
 
+// Threads per CTA of the FP64 element kernels: one per node, 128 up to
+// N = 4 (125 nodes), else the nodes rounded up to whole warps (N = 5: 224,
+// N = 6: 352, N = 7: 512).
+__host__ __device__ constexpr int block64(int N) {
+  return (N + 1) * (N + 1) * (N + 1) <= 128 ? 128 : ((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32;
+}
+
 // The thermodynamic fields of a node's state Y at height z and level lev.
 // Not inlined: the flux pass (for the state it advances to) and k_thermo64
 // (for a state set from outside) then run the same compiled code, so that a
@@ -41,10 +48,10 @@ __device__ __noinline__ void thermo_store64(const KParams &P, const double Y[6],
 }
 
 template <int N>
-__global__ void __launch_bounds__(128) k_grad64(const double *__restrict__ Q, const double *__restrict__ TH,
-                                                double *__restrict__ F2, const KParams P) {
+__global__ void __launch_bounds__(block64(N)) k_grad64(const double *__restrict__ Q, const double *__restrict__ TH,
+                                                       double *__restrict__ F2, const KParams P) {
   constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
-  static_assert(Np <= 128, "one node per thread");
+  static_assert(Np <= block64(N), "one node per thread");
   __shared__ double sD[Nq * Nq];
   __shared__ double sG[6][Np];
   __shared__ double sGf[6][6][Nf];
@@ -191,17 +198,31 @@ __device__ __forceinline__ void flux1_dir(const double Y[6], double rinv, double
 }
 
 // FL: numerical flux of F1, 0 Rusanov, 1 HLLC, 2 Roe
+// The flux pass's shared memory (dynamic: above N = 4 it exceeds the 48 KB of
+// static shared memory).
+template <int N>
+struct Rhs64Smem {
+  static constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
+  double sD[Nq * Nq];
+  double sF[6][3][Np];
+  double sY[6][Np];
+  double sL[6][6][Nf];
+  int sNb[6];
+};
+
 template <int N, bool UPDATE, int FL>
-__global__ void __launch_bounds__(128) k_rhs64(const double *__restrict__ Q, const double *__restrict__ F2,
-                                               const double *__restrict__ TH, double *__restrict__ dQ,
-                                               double *__restrict__ Qout, double *__restrict__ THout,
-                                               const StageCoef sc, const KParams P) {
+__global__ void __launch_bounds__(block64(N)) k_rhs64(const double *__restrict__ Q, const double *__restrict__ F2,
+                                                      const double *__restrict__ TH, double *__restrict__ dQ,
+                                                      double *__restrict__ Qout, double *__restrict__ THout,
+                                                      const StageCoef sc, const KParams P) {
   constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
-  __shared__ double sD[Nq * Nq];
-  __shared__ double sF[6][3][Np];
-  __shared__ double sY[6][Np];
-  __shared__ double sL[6][6][Nf];
-  __shared__ int sNb[6];
+  extern __shared__ __align__(16) unsigned char smem_rhs64[];
+  Rhs64Smem<N> &SM = *reinterpret_cast<Rhs64Smem<N> *>(smem_rhs64);
+  auto &sD = SM.sD;
+  auto &sF = SM.sF;
+  auto &sY = SM.sY;
+  auto &sL = SM.sL;
+  auto &sNb = SM.sNb;
   const int t = threadIdx.x;
   if (t < Nq * Nq) sD[t] = P.D[t];
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
@@ -396,11 +417,11 @@ __global__ void k_thermo64(const double *__restrict__ Q, double *__restrict__ TH
 // ------------------------------------------------------------------ launchers
 
 
-int grid_for(const void *fn, int E, size_t smem = 0) {
+int grid_for(const void *fn, int E, size_t smem, int threads) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 128, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
   if (per < 1) per = 1;
   long long g = (long long)nsm * per;
   return (int)(g < E ? g : E);
@@ -443,18 +464,21 @@ cudaError_t launch_thermo64(const double *Q, double *TH, const KParams &P, int N
 template <int N>
 static void grad64_instance(const double *Q, const double *TH, double *F2, const KParams &P, cudaStream_t s) {
   static int grid = 0;
-  if (!grid) grid = grid_for((const void *)k_grad64<N>, 1 << 30);
-  k_grad64<N><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, TH, F2, P);
+  if (!grid) grid = grid_for((const void *)k_grad64<N>, 1 << 30, 0, block64(N));
+  k_grad64<N><<<grid < P.E ? grid : P.E, block64(N), 0, s>>>(Q, TH, F2, P);
 }
 
-// the flat-mesh kernels are instantiated for the orders 1 .. 4 (one thread
-// per node of a 128-thread CTA)
+// the FP64 flat-mesh kernels are instantiated for the orders 1 .. 7 (one
+// thread per node)
 cudaError_t launch_grad64(const double *Q, const double *TH, double *F2, const KParams &P, cudaStream_t s) {
   switch (P.N) {
     case 1: grad64_instance<1>(Q, TH, F2, P, s); break;
     case 2: grad64_instance<2>(Q, TH, F2, P, s); break;
     case 3: grad64_instance<3>(Q, TH, F2, P, s); break;
     case 4: grad64_instance<4>(Q, TH, F2, P, s); break;
+    case 5: grad64_instance<5>(Q, TH, F2, P, s); break;
+    case 6: grad64_instance<6>(Q, TH, F2, P, s); break;
+    case 7: grad64_instance<7>(Q, TH, F2, P, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -464,8 +488,14 @@ template <int N, bool UPDATE, int FL>
 static void rhs64_instance(const double *Q, const double *F2, const double *TH, double *dQ, double *Qout,
                            double *THout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
   static int grid = 0;
-  if (!grid) grid = grid_for((const void *)k_rhs64<N, UPDATE, FL>, 1 << 30);
-  k_rhs64<N, UPDATE, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(Q, F2, TH, dQ, Qout, THout, sc, P);
+  constexpr size_t smem = sizeof(Rhs64Smem<N>);
+  if (!grid) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute((const void *)k_rhs64<N, UPDATE, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+    grid = grid_for((const void *)k_rhs64<N, UPDATE, FL>, 1 << 30, smem, block64(N));
+  }
+  k_rhs64<N, UPDATE, FL><<<grid < P.E ? grid : P.E, block64(N), smem, s>>>(Q, F2, TH, dQ, Qout, THout, sc, P);
 }
 
 template <int N>
@@ -495,6 +525,9 @@ cudaError_t launch_rhs64(const double *Q, const double *F2, const double *TH, do
     case 2: rhs64_order<2>(Q, F2, TH, dQ, Qout, THout, sc, update, P, s); break;
     case 3: rhs64_order<3>(Q, F2, TH, dQ, Qout, THout, sc, update, P, s); break;
     case 4: rhs64_order<4>(Q, F2, TH, dQ, Qout, THout, sc, update, P, s); break;
+    case 5: rhs64_order<5>(Q, F2, TH, dQ, Qout, THout, sc, update, P, s); break;
+    case 6: rhs64_order<6>(Q, F2, TH, dQ, Qout, THout, sc, update, P, s); break;
+    case 7: rhs64_order<7>(Q, F2, TH, dQ, Qout, THout, sc, update, P, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

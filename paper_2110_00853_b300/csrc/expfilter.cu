@@ -11,9 +11,14 @@
 
 namespace cmles {
 
+// threads per CTA: one per node (128 up to N = 4)
+__host__ __device__ constexpr int filter_block(int N) {
+  return (N + 1) * (N + 1) * (N + 1) <= 128 ? 128 : ((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32;
+}
+
 template <int N>
-__global__ void __launch_bounds__(128) k_expfilter(double *__restrict__ Q, float *__restrict__ S32,
-                                                   const ExpFilter Fm, int E) {
+__global__ void __launch_bounds__(filter_block(N)) k_expfilter(double *__restrict__ Q, float *__restrict__ S32,
+                                                               const ExpFilter Fm, int E) {
   constexpr int Nq = N + 1, Np = Nq * Nq * Nq;
   __shared__ double sF[Nq * Nq];
   __shared__ double a[Np], b[Np];
@@ -56,8 +61,8 @@ __global__ void __launch_bounds__(128) k_expfilter(double *__restrict__ Q, float
 template <int N>
 static void expfilter_order(double *Q, float *S32, const ExpFilter &F, int E, cudaStream_t s) {
   static int grid = 0;
-  if (!grid) grid = grid_for((const void *)k_expfilter<N>, 1 << 30, 0);
-  k_expfilter<N><<<grid < E ? grid : E, 128, 0, s>>>(Q, S32, F, E);
+  if (!grid) grid = grid_for((const void *)k_expfilter<N>, 1 << 30, 0, filter_block(N));
+  k_expfilter<N><<<grid < E ? grid : E, filter_block(N), 0, s>>>(Q, S32, F, E);
 }
 
 cudaError_t launch_expfilter(double *Q, float *S32, const ExpFilter &F, int N, int E, cudaStream_t s) {
@@ -66,6 +71,9 @@ cudaError_t launch_expfilter(double *Q, float *S32, const ExpFilter &F, int N, i
     case 2: expfilter_order<2>(Q, S32, F, E, s); break;
     case 3: expfilter_order<3>(Q, S32, F, E, s); break;
     case 4: expfilter_order<4>(Q, S32, F, E, s); break;
+    case 5: expfilter_order<5>(Q, S32, F, E, s); break;
+    case 6: expfilter_order<6>(Q, S32, F, E, s); break;
+    case 7: expfilter_order<7>(Q, S32, F, E, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -69,8 +69,9 @@ def test_create_rejects_unsupported_combinations_without_gpu_work():
 
 
 def test_create_order_limits_without_gpu_work():
-    """Flat meshes take the orders 1 .. 4 (the instantiated kernels); warped
-    meshes and HEVI only 4; other orders are rejected before any device work."""
+    """The FP64 path takes the orders 1 .. 7 on flat meshes, the FP32 path
+    1 .. 4 (the instantiated kernels); warped meshes and HEVI only 4; other
+    orders are rejected before any device work."""
     L = cmles.load()
     h = ctypes.c_void_p()
 
@@ -79,7 +80,10 @@ def test_create_order_limits_without_gpu_work():
         P = cmles.make_params(kw, precision)
         return L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h))
 
-    for N in (0, 5, 7, 8):
-        assert status(N) == 1 and status(N, "fp32") == 1
+    for N in (0, 8, 9):
+        assert status(N) == 1
+    for N in (0, 5, 6, 7, 8):
+        assert status(N, "fp32") == 1
+    assert status(5, integrator="ark2_hevi") == 1
     assert status(3, "fp32", warp=True) == 1
     assert status(3, integrator="ark2_hevi") == 1
