@@ -455,11 +455,23 @@ def main():
     achieved = head["nodes"] * alg_bytes(prec, kinds[dom], hstages, variants[0][4]) / (avg_ms / 1e3) / 1e9
     tb, wi = ncu_counters(variants[0][0], kinds[dom], prec)
     traffic = tb * head["nodes"] if tb is not None else None
-    issue = None
-    if wi is not None and wi == wi:
+    limiter = LIMITER.get((variants[0][0], kinds[dom]), "unmeasured")
+    hbm_view = {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": f"{peak_kind} hbm_gbs"}
+    if wi is not None and wi == wi and limiter.startswith("issue"):
+        # an instruction-issue-bound kernel: its roofline is the SMs' issue
+        # rate (148 SMs x 4 schedulers x one warp instruction per clock at the
+        # maximum SM clock), its achieved rate the ncu instruction count per
+        # element times the elements of one launch over the launch's CUDA-event
+        # time; the HBM view stays beside it
         ipk = issue_peak()
         ach = wi * (head["nodes"] // 125) / (avg_ms / 1e3)
-        issue = {"warp_inst_per_element": wi, "achieved": ach, "peak": ipk, "unit": "warp-inst/s", "frac": ach / ipk}
+        roofline = {"bound": "alu", "kernel": kinds[dom], "achieved": ach, "peak": ipk, "unit": "warp-inst/s",
+                    "frac": ach / ipk, "traffic": traffic, "warp_inst_per_element": wi,
+                    "peak_source": "148 SMs x 4 schedulers x 1 warp instruction/clock x maximum SM clock",
+                    "limiter": limiter, "hbm": hbm_view}
+    else:
+        roofline = dict({"bound": "hbm", "kernel": kinds[dom], "traffic": traffic, "limiter": limiter}, **hbm_view)
     out_variants = {}
     for (name, vprec, _, _, vint), r in zip(variants, results.values()):
         v = whole_job_rate(r["nodes"], world, args.steps, r["ms"], STAGES[vint])
@@ -496,11 +508,7 @@ def main():
                             "flux": variants[0][3], "integrator": variants[0][4],
                             "elements": head["nodes"] // 125, "nodes_per_gpu": head["nodes"],
                             "l2": "inputs larger than L2 (state alone 12 GB)", "parallelism": f"replicas{world}"},
-                    roofline={"bound": "hbm", "kernel": kinds[dom], "achieved": achieved, "peak": hbm,
-                              "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                              "peak_source": f"{peak_kind} hbm_gbs",
-                              "limiter": LIMITER.get((variants[0][0], kinds[dom]), "unmeasured"),
-                              "issue": issue},
+                    roofline=roofline,
                     parity=PARITY[variants[0][0]] if variants[0][0] in PARITY else None,
                     cpu_baseline=cb, e2e=e2e, gpu_launches=head["launches"], clocks=head["clocks"],
                     variants=out_variants)

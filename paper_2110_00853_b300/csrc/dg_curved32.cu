@@ -15,6 +15,7 @@
 // once per node and state, in the kernel that writes the state, which stores
 // p', c, h' and theta_v' (TH) for the next two passes.
 #include "common.cuh"
+#include "dg32_parts.cuh"
 #include "launch.h"
 #include "mlp.cuh"
 #include "thermo32.cuh"
@@ -57,20 +58,7 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
   const MlpTc &W = *reinterpret_cast<const MlpTc *>(sMlpRaw);
   TcState tcs;
   int stalled = 0;
-  if (CL == 2) {
-    const uint4 *src = reinterpret_cast<const uint4 *>(&P.mlp->tc);
-    uint4 *dst = reinterpret_cast<uint4 *>(sMlpRaw);
-    for (int q = t; q < (int)(sizeof(MlpTc) / 16); q += blockDim.x) dst[q] = src[q];
-    fence_proxy_async_smem();
-    if (t == 0) mbar_init(&sBar[1], 1);
-    tc_setup(tcs, &sSlot, &sBar[0]);
-    // test hook (see the flat kernel)
-    if (P.tc_stall == 1 && !mbar_wait_bounded(&sBar[1], 0, 1 << 14)) stalled = 1;
-    // test hook 2: the first MMA completion wait gives up at once, while
-    // the MMA is in flight
-    if (HOOK) tcs.hook = 1;
-    __syncwarp();
-  }
+  if (CL == 2) stalled = learned_setup<HOOK>(P, sMlpRaw, sBar, &sSlot, tcs);
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
   for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
     int ex, ey, ez;
@@ -100,17 +88,10 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
       const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
       const int nn = face_node<Nq>(d, (f & 1) ? 0 : N, t1, t2);
       const float *tn = P.node32 + (size_t)nb * C_NF * kNP + nn;
-      float sp[6];
+      float gf[6];
+      face_primitives(S, TH, nb, nn, tn[L_RHO * kNP], tn[L_QM * kNP], gf);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
-      sp[5] = S[((size_t)nb * 6 + 5) * kNP + nn];
-      const float rinv = fdiv(1.0f, tn[L_RHO * kNP] + sp[0]);
-      sGf[f][0][fn] = sp[1] * rinv;
-      sGf[f][1][fn] = sp[2] * rinv;
-      sGf[f][2][fn] = sp[3] * rinv;
-      sGf[f][3][fn] = TH[((size_t)nb * 4 + 2) * kNP + nn];
-      sGf[f][4][fn] = (sp[5] - tn[L_QM * kNP] * sp[0]) * rinv;
-      sGf[f][5][fn] = TH[((size_t)nb * 4 + 3) * kNP + nn];
+      for (int v = 0; v < 6; ++v) sGf[f][v][fn] = gf[v];
     }
     __syncthreads();
     float gr[6][3];
@@ -171,67 +152,14 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
       if (j == N) lift(3, i + Nq * k);
       if (k == 0) lift(4, i + Nq * j);
       if (k == N) lift(5, i + Nq * j);
-      if (CL == 1 && P.closure == 1) {
-        float S2 = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) {
-            const float Sab = 0.5f * (gr[a][b] + gr[b][a]);
-            S2 += Sab * Sab;
-          }
-        const float Smag2 = 2.0f * S2;
-        if (Smag2 > 0.0f) {
-          const float Smag = sqrtf(Smag2);
-          float fb = 1.0f;
-          if (P.richardson) {
-            const float Ri = F.g / (L[L_THV] + G[5]) * gr[5][2] / Smag2;
-            if (Ri > 0.0f) {
-              const float a = 1.0f - Ri * F.inv_Prt;
-              fb = a > 0.0f ? sqrtf(sqrtf(a)) : 0.0f;
-            }
-          }
-          // (C_s Delta)^2 with Delta = (element volume)^(1/3) / N, per node
-          nut = tab[C_CSD2 * kNP] * Smag * fb;
-          Dt = nut * F.inv_Prt;
-        }
-      }
+      // (C_s Delta)^2 with Delta = (element volume)^(1/3) / N, per node
+      if (CL == 1 && P.closure == 1) eddy_nu<1>(gr, tab[C_CSD2 * kNP], L[L_THV] + G[5], F, P.richardson, nut, Dt);
     }
     if (CL == 2) {
-      float x[kMlpIn];
       const float Delta = t < Np ? P.node32[(size_t)e * C_NF * kNP + C_DELTA * kNP + t] : 0.f;
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) x[3 * a + b] = t < Np ? gr[a][b] * W.in_scale[3 * a + b] : 0.f;
-#pragma unroll
-      for (int b = 0; b < 3; ++b) x[9 + b] = t < Np ? gr[5][b] * W.in_scale[9 + b] : 0.f;
-      x[12] = Delta * W.in_scale[12];
-      __syncthreads();  // the A operand overwrites the gradient fields
-      mlp_tc_put_input(sA, x);
-      float y0, y1;
-      mlp_tc_forward<HOOK>(W, sA, tcs, y0, y1);
-      if (t < Np) {
-        nut = W.out_scale[0] * fmaxf(y0, 0.f);
-        Dt = W.out_scale[1] * fmaxf(y1, 0.f);
-      }
+      learned_nu<HOOK>(W, sA, tcs, gr, Delta, t < Np, nut, Dt);
     }
-    if (t < Np) {
-      const float rho = L[L_RHO] + sv[0];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const float di = -Dt * gr[4][d];
-        float rt[3];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) rt[b] = -2.0f * rho * nut * (0.5f * (gr[d][b] + gr[b][d]));
-        float *o = F2 + ((size_t)e * 15 + d * 5) * kNP + t;
-        o[0] = rho * di;
-        o[1 * kNP] = rt[0] + di * sv[1];
-        o[2 * kNP] = rt[1] + di * sv[2];
-        o[3 * kNP] = rt[2] + di * sv[3];
-        o[4 * kNP] = -rho * Dt * gr[3][d] + (rt[0] * G[0] + rt[1] * G[1] + rt[2] * G[2]);
-      }
-    }
+    if (t < Np) write_f2(F2, e, t, L[L_RHO] + sv[0], nut, Dt, gr, sv, G);
     __syncthreads();
   }
   if (CL == 2) {
@@ -328,9 +256,41 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
       float sm[6], sp[6];
 #pragma unroll
       for (int v = 0; v < 6; ++v) sm[v] = sS[v][n];
-      const float pm = TH[((size_t)e * 4) * kNP + n];
       const float cm = TH[((size_t)e * 4 + 1) * kNP + n];
       const int nb = sNb[f];
+      const float Lf = mag * F.inv_w0 / gn[9 * kNP];
+      if (FL == 0 && nb >= 0) {
+        // Rusanov across an interior face.  The own node's total normal flux
+        // n.(F1 + F2) is sF . n from the first phase, so the lifted jump is
+        // 1/2 n.(F_- - F_+) - 1/2 lambda (s_- - s_+) and only the
+        // neighbour's fluxes are evaluated here.
+        const int nn = face_node<Nq>(d, N - a, t1, t2);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
+        const float pp = TH[((size_t)nb * 4) * kNP + nn];
+        const float cp = TH[((size_t)nb * 4 + 1) * kNP + nn];
+        float fp[6];
+        flux1_normal32(sp, rho_r, rhoq_r, Hr, pp, nv, fp);
+        float f2p[5];
+#pragma unroll
+        for (int c5 = 0; c5 < 5; ++c5) {
+          float fq = 0.f;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) fq += nv[c] * F2[((size_t)nb * 15 + c * 5 + c5) * kNP + nn];
+          f2p[c5] = fq;
+        }
+        const float um = (sm[1] * nv[0] + sm[2] * nv[1] + sm[3] * nv[2]) / (rho_r + sm[0]);
+        const float up = (sp[1] * nv[0] + sp[2] * nv[1] + sp[3] * nv[2]) / (rho_r + sp[0]);
+        const float lam = fmaxf(fabsf(um) + cm, fabsf(up) + cp);
+        const int c_of_v[6] = {0, 1, 2, 3, 4, 0};
+#pragma unroll
+        for (int v = 0; v < 6; ++v) {
+          const float fnm = sg * sF[v][d][n] / mag;  // n . (F1 + F2) at the own node
+          sLf[f][v][fn] = Lf * (0.5f * (fnm - (fp[v] + f2p[c_of_v[v]])) - 0.5f * lam * (sm[v] - sp[v]));
+        }
+        continue;
+      }
+      const float pm = TH[((size_t)e * 4) * kNP + n];
       float pp, cp, f2s[5];
       if (nb >= 0) {
         const int nn = face_node<Nq>(d, N - a, t1, t2);
@@ -398,7 +358,6 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
 #pragma unroll
         for (int v = 0; v < 6; ++v) f1s[v] = 0.5f * (fm[v] + fp[v]) + 0.5f * lam * (sm[v] - sp[v]);
       }
-      const float Lf = mag * F.inv_w0 / gn[9 * kNP];
       const int c_of_v[6] = {0, 1, 2, 3, 4, 0};
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
@@ -428,43 +387,15 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
         if (k == N) r += sLf[5][v][i + Nq * j];
         R[v] = r;
       }
-      const float tau = tab[L_TAU * kNP];
-      const float rho = tab[L_RHO * kNP] + sv[0];
-      float Sr[3];
-      Sr[0] = -tau * (sv[1] - rho * F.u_relax[0]);
-      Sr[1] = -tau * (sv[2] - rho * F.u_relax[1]);
-      Sr[2] = -sv[0] * F.g - tau * (sv[3] - rho * F.u_relax[2]);
-      Sr[0] -= 2.0f * (F.Omega[1] * sv[3] - F.Omega[2] * sv[2]);
-      Sr[1] -= 2.0f * (F.Omega[2] * sv[1] - F.Omega[0] * sv[3]);
-      Sr[2] -= 2.0f * (F.Omega[0] * sv[2] - F.Omega[1] * sv[1]);
-      R[1] += Sr[0];
-      R[2] += Sr[1];
-      R[3] += Sr[2];
-      const double *qr = P.qref64 + (size_t)e * 3 * Np + t;
-      float sn[6];
-#pragma unroll
-      for (int v = 0; v < 6; ++v) {
-        const size_t i64 = ((size_t)e * 6 + v) * Np + t;
-        if (UPD) {
-          const size_t i32 = ((size_t)e * 6 + v) * kNP + t;
-          const float dq = (sc.first ? 0.f : sc.Af * dQ[i32]) + sc.dtf * R[v];
-          const float Bdq = sc.Bf * dq;
-          const float D0 = sc.first ? 0.f : P.D32[i32];
-          if (UPD == 1) {
-            dQ[i32] = dq;
-            P.D32[i32] = D0 + Bdq;
-            sn[v] = sS[v][t] + Bdq;
-          } else {
-            const double qn = Q64[i64] + (double)(D0 + Bdq);
-            Q64[i64] = qn;
-            const double ref = v == 0 ? qr[0] : (v == 4 ? qr[Np] : (v == 5 ? qr[2 * Np] : 0.0));
-            sn[v] = (float)(qn - ref);
-          }
-          Sout[i32] = sn[v];
-        } else {
-          Rout[i64] = (double)R[v];
-        }
-      }
+      momentum_sources(sv, tab[L_RHO * kNP] + sv[0], tab[L_TAU * kNP], F, R);
+      // the update inputs, loaded here rather than with the element's first
+      // loads: this kernel is at its register limit (80) and held across the
+      // face tasks they spill
+      float dq0[6], D0[6], sn[6];
+      double q0[6];
+      if (UPD) stage_inputs<UPD>(P, sc, dQ, Q64, e, t, Np, dq0, D0, q0);
+      stage_update<UPD>(P, sc, R, dq0, D0, q0, sv, P.qref64 + (size_t)e * 3 * Np + t, Np, dQ, Q64, Sout, Rout, e, t,
+                        Np, sn);
       // the thermodynamics of the new state, for the next stage's two passes
       if (UPD) {
         float L[L_NF];

@@ -30,6 +30,7 @@
 // pass and the gradient pass of the next stage, so that neither evaluates it
 // again for its own nodes or its neighbours' face nodes.
 #include "common.cuh"
+#include "dg32_parts.cuh"
 #include "launch.h"
 #include "mlp.cuh"
 #include "thermo32.cuh"
@@ -65,21 +66,7 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
   const MlpTc &W = *reinterpret_cast<const MlpTc *>(sMlpRaw);
   TcState tcs;
   int stalled = 0;
-  if (CL == 2) {
-    const uint4 *src = reinterpret_cast<const uint4 *>(&P.mlp->tc);
-    uint4 *dst = reinterpret_cast<uint4 *>(sMlpRaw);
-    for (int q = t; q < (int)(sizeof(MlpTc) / 16); q += blockDim.x) dst[q] = src[q];
-    fence_proxy_async_smem();
-    if (t == 0) mbar_init(&sBar[1], 1);
-    tc_setup(tcs, &sSlot, &sBar[0]);
-    // test hook: a bounded wait on a barrier that nothing arrives on runs
-    // out; it is reported like a failed MMA wait but leaves the work intact
-    if (P.tc_stall == 1 && !mbar_wait_bounded(&sBar[1], 0, 1 << 14)) stalled = 1;
-    // test hook 2: the first MMA completion wait gives up at once, while
-    // the MMA is in flight
-    if (HOOK) tcs.hook = 1;
-    __syncwarp();
-  }
+  if (CL == 2) stalled = learned_setup<HOOK>(P, sMlpRaw, sBar, &sSlot, tcs);
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
   for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
     int ex, ey, ez;
@@ -110,20 +97,13 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
       const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
       const int a_nb = (f & 1) ? 0 : N;
       const int nn = face_node<Nq>(d, a_nb, t1, t2);
-      float sp[6];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
-      sp[5] = S[((size_t)nb * 6 + 5) * kNP + nn];
       // the shared face node has the same height, hence the same level values
       const int lev = ez * Nq + (d == 2 ? (f & 1 ? N : 0) : t2);
       const float *Lf = P.lev32 + (size_t)lev * L_NF;
-      const float rinv = fdiv(1.0f, Lf[L_RHO] + sp[0]);
-      sGf[f][0][fn] = sp[1] * rinv;
-      sGf[f][1][fn] = sp[2] * rinv;
-      sGf[f][2][fn] = sp[3] * rinv;
-      sGf[f][3][fn] = TH[((size_t)nb * 4 + 2) * kNP + nn];
-      sGf[f][4][fn] = (sp[5] - Lf[L_QM] * sp[0]) * rinv;
-      sGf[f][5][fn] = TH[((size_t)nb * 4 + 3) * kNP + nn];
+      float gf[6];
+      face_primitives(S, TH, nb, nn, Lf[L_RHO], Lf[L_QM], gf);
+#pragma unroll
+      for (int v = 0; v < 6; ++v) sGf[f][v][fn] = gf[v];
     }
     __syncthreads();
     float gr[6][3];
@@ -163,67 +143,12 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
       if (k == 0) lift(4, i + Nq * j);
       if (k == N) lift(5, i + Nq * j);
 
-      if ((CL == 1 && P.closure == 1) || CL == 3) {
-        float S2 = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) {
-            const float Sab = 0.5f * (gr[a][b] + gr[b][a]);
-            S2 += Sab * Sab;
-          }
-        const float Smag2 = 2.0f * S2;
-        if (CL == 1)
-          nut = Smag2 > 0.0f ? F.CsDelta2 * sqrtf(Smag2) : 0.0f;
-        else
-          nut = vreman_nu<float>(gr, F.vr_c, F.vr_d2);
-        if (P.richardson && Smag2 > 0.0f) {
-          const float thv = L[L_THV] + G[5];
-          const float Ri = fdiv(F.g * gr[5][2], thv * Smag2);
-          if (Ri > 0.0f) {
-            const float a = 1.0f - Ri * F.inv_Prt;
-            nut *= a > 0.0f ? sqrtf(sqrtf(a)) : 0.0f;
-          }
-        }
-        Dt = nut * F.inv_Prt;
-      }
+      if ((CL == 1 && P.closure == 1) || CL == 3)
+        eddy_nu<CL == 3 ? 3 : 1>(gr, F.CsDelta2, L[L_THV] + G[5], F, P.richardson, nut, Dt);
     }
-    if (CL == 2) {
-      // closure network inputs: 9 velocity gradients, 3 theta_v gradients,
-      // Delta; the network runs on the tensor cores, row t = node t
-      float x[kMlpIn];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) x[3 * a + b] = t < Np ? gr[a][b] * W.in_scale[3 * a + b] : 0.f;
-#pragma unroll
-      for (int b = 0; b < 3; ++b) x[9 + b] = t < Np ? gr[5][b] * W.in_scale[9 + b] : 0.f;
-      x[12] = t < Np ? F.Delta * W.in_scale[12] : 0.f;
-      __syncthreads();  // the A operand overwrites the gradient fields
-      mlp_tc_put_input(sA, x);
-      float y0, y1;
-      mlp_tc_forward<HOOK>(W, sA, tcs, y0, y1);
-      if (t < Np) {
-        nut = W.out_scale[0] * fmaxf(y0, 0.f);
-        Dt = W.out_scale[1] * fmaxf(y1, 0.f);
-      }
-    }
-    if (t < Np) {
-      const float rho = L[L_RHO] + sv[0];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const float di = -Dt * gr[4][d];
-        float rt[3];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) rt[b] = -2.0f * rho * nut * (0.5f * (gr[d][b] + gr[b][d]));
-        float *o = F2 + ((size_t)e * 15 + d * 5) * kNP + t;
-        o[0] = rho * di;
-        o[1 * kNP] = rt[0] + di * sv[1];
-        o[2 * kNP] = rt[1] + di * sv[2];
-        o[3 * kNP] = rt[2] + di * sv[3];
-        o[4 * kNP] = -rho * Dt * gr[3][d] + (rt[0] * G[0] + rt[1] * G[1] + rt[2] * G[2]);
-      }
-    }
+    // the learned closure on the tensor cores, row t = node t
+    if (CL == 2) learned_nu<HOOK>(W, sA, tcs, gr, F.Delta, t < Np, nut, Dt);
+    if (t < Np) write_f2(F2, e, t, L[L_RHO] + sv[0], nut, Dt, gr, sv, G);
     __syncthreads();
   }
   if (CL == 2) {
@@ -267,15 +192,7 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
     // and starts the step: no register or increment to read)
     float dq0[6], D0[6];
     double q0[6];
-    if (UPD && t < Np) {
-#pragma unroll
-      for (int v = 0; v < 6; ++v) {
-        const size_t i32 = ((size_t)e * 6 + v) * kNP + t;
-        dq0[v] = sc.first ? 0.f : dQ[i32];
-        D0[v] = sc.first ? 0.f : P.D32[i32];
-        if (UPD == 2) q0[v] = Q64[((size_t)e * 6 + v) * Np + t];
-      }
-    }
+    if (UPD && t < Np) stage_inputs<UPD>(P, sc, dQ, Q64, e, t, Np, dq0, D0, q0);
     if (t < Np) {
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
@@ -461,42 +378,10 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
       }
       float tau = L[L_TAU];
       if (P.tau_col) tau = fmaxf(tau, (float)P.tau_col[(ex + P.gx0) * Nq + i]);
-      const float rho = L[L_RHO] + sv[0];
-      float Sr[3];
-      Sr[0] = -tau * (sv[1] - rho * F.u_relax[0]);
-      Sr[1] = -tau * (sv[2] - rho * F.u_relax[1]);
-      Sr[2] = -sv[0] * F.g - tau * (sv[3] - rho * F.u_relax[2]);
-      Sr[0] -= 2.0f * (F.Omega[1] * sv[3] - F.Omega[2] * sv[2]);
-      Sr[1] -= 2.0f * (F.Omega[2] * sv[1] - F.Omega[0] * sv[3]);
-      Sr[2] -= 2.0f * (F.Omega[0] * sv[2] - F.Omega[1] * sv[1]);
-      R[1] += Sr[0];
-      R[2] += Sr[1];
-      R[3] += Sr[2];
-      const double *qr = P.qref64 + (size_t)(ez * Nq + k) * 4;
+      momentum_sources(sv, L[L_RHO] + sv[0], tau, F, R);
       float sn[6];
-#pragma unroll
-      for (int v = 0; v < 6; ++v) {
-        const size_t i64 = ((size_t)e * 6 + v) * Np + t;
-        if (UPD) {
-          const size_t i32 = ((size_t)e * 6 + v) * kNP + t;
-          const float dq = sc.Af * dq0[v] + sc.dtf * R[v];
-          const float Bdq = sc.Bf * dq;
-          if (UPD == 1) {
-            dQ[i32] = dq;
-            P.D32[i32] = D0[v] + Bdq;
-            sn[v] = sS[v][t] + Bdq;
-          } else {
-            // the register is not read again before the next step's first stage
-            const double qn = q0[v] + (double)(D0[v] + Bdq);
-            Q64[i64] = qn;
-            const double ref = v == 0 ? qr[0] : (v == 4 ? qr[1] : (v == 5 ? qr[2] : 0.0));
-            sn[v] = (float)(qn - ref);
-          }
-          Sout[i32] = sn[v];
-        } else {
-          Rout[i64] = (double)R[v];
-        }
-      }
+      stage_update<UPD>(P, sc, R, dq0, D0, q0, sv, P.qref64 + (size_t)(ez * Nq + k) * 4, 1, dQ, Q64, Sout, Rout, e,
+                        t, Np, sn);
       // the thermodynamics of the new state, for the next stage's two passes
       if (UPD) thermo_store32(P, L, sn, THout, e, t, fail);
     }
