@@ -99,8 +99,8 @@ PARITY = {"fp32acc64_mlp": "1e-4 rel L2 per variable vs the FP64 oracle with its
 # is not used (traffic and issue then read null).
 COUNTERS = os.path.join(ROOT, "profiles", "ncu_counters_c5.txt")
 KERNEL_SOURCES = {
-    "grad": ["dg_fp32.cu", "mlp.cuh", "tc.cuh", "common.cuh", "thermo32.cuh"],
-    "rhs": ["dg_fp32.cu", "common.cuh", "thermo32.cuh"],
+    "grad": ["dg_fp32.cu", "dg32_parts.cuh", "mlp.cuh", "tc.cuh", "common.cuh", "thermo32.cuh"],
+    "rhs": ["dg_fp32.cu", "dg32_parts.cuh", "common.cuh", "thermo32.cuh"],
     "grad64": ["dg_fp64.cu", "common.cuh", "thermo.cuh"],
     "rhs64": ["dg_fp64.cu", "common.cuh", "thermo.cuh"],
 }

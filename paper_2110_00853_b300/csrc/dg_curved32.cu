@@ -368,6 +368,13 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
     __syncthreads();
     if (t < Np) {
       const float Jinv = 1.0f / geo[9 * kNP];
+      // the lifted face terms of the node's x, y and z faces, without
+      // branches: weight 1 on a face, 0 (on any valid entry) inside
+      const float wx = (i == 0 || i == N) ? 1.f : 0.f, wy = (j == 0 || j == N) ? 1.f : 0.f,
+                  wz = (k == 0 || k == N) ? 1.f : 0.f;
+      const float *lx = &sLf[i == N ? 1 : 0][0][j + Nq * k];
+      const float *ly = &sLf[j == N ? 3 : 2][0][i + Nq * k];
+      const float *lz = &sLf[k == N ? 5 : 4][0][i + Nq * j];
       float R[6];
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
@@ -379,12 +386,9 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
           a2 += sD[k * Nq + m] * sF[v][2][i + Nq * (j + Nq * m)];
         }
         float r = -Jinv * (a0 + a1 + a2);
-        if (i == 0) r += sLf[0][v][j + Nq * k];
-        if (i == N) r += sLf[1][v][j + Nq * k];
-        if (j == 0) r += sLf[2][v][i + Nq * k];
-        if (j == N) r += sLf[3][v][i + Nq * k];
-        if (k == 0) r += sLf[4][v][i + Nq * j];
-        if (k == N) r += sLf[5][v][i + Nq * j];
+        r = fmaf(wx, lx[v * Nf], r);
+        r = fmaf(wy, ly[v * Nf], r);
+        r = fmaf(wz, lz[v * Nf], r);
         R[v] = r;
       }
       momentum_sources(sv, tab[L_RHO * kNP] + sv[0], tab[L_TAU * kNP], F, R);

@@ -93,8 +93,15 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
     for (int task = t; task < 6 * Nf; task += blockDim.x) {
       const int f = task / Nf, fn = task - f * Nf;
       const int nb = sNb[f];
-      if (nb < 0) continue;
       const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
+      if (nb < 0) {
+        // a wall: the mirror state (normal velocity reversed), so that the
+        // lift below is the same formula on every face
+        const int n = face_node<Nq>(d, (f & 1) ? N : 0, t1, t2);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) sGf[f][v][fn] = v == d ? -sG[v][n] : sG[v][n];
+        continue;
+      }
       const int a_nb = (f & 1) ? 0 : N;
       const int nn = face_node<Nq>(d, a_nb, t1, t2);
       // the shared face node has the same height, hence the same level values
@@ -126,22 +133,22 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
       gr[3][2] += L[L_DZ_HM];
       gr[4][2] += L[L_DZ_Q];
       gr[5][2] += L[L_DZ_THV];
-      auto lift = [&](int f, int fn) {
-        const int d = f >> 1;
-        const float Lf = (f & 1) ? F.lift[d] : -F.lift[d];
-        if (sNb[f] >= 0) {
+      // the lift of the face averages on the node's x, y and z faces (the
+      // mirror state on walls), without branches: factor 0 inside
+      {
+        const float Lx = i == 0 ? -F.lift[0] : (i == N ? F.lift[0] : 0.f);
+        const float Ly = j == 0 ? -F.lift[1] : (j == N ? F.lift[1] : 0.f);
+        const float Lz = k == 0 ? -F.lift[2] : (k == N ? F.lift[2] : 0.f);
+        const float *gx = &sGf[i == N ? 1 : 0][0][j + Nq * k];
+        const float *gy = &sGf[j == N ? 3 : 2][0][i + Nq * k];
+        const float *gz = &sGf[k == N ? 5 : 4][0][i + Nq * j];
 #pragma unroll
-          for (int v = 0; v < 6; ++v) gr[v][d] += Lf * (0.5f * (G[v] + sGf[f][v][fn]) - G[v]);
-        } else {
-          gr[d][d] += Lf * (-G[d]);
+        for (int v = 0; v < 6; ++v) {
+          gr[v][0] += Lx * (0.5f * (G[v] + gx[v * Nf]) - G[v]);
+          gr[v][1] += Ly * (0.5f * (G[v] + gy[v * Nf]) - G[v]);
+          gr[v][2] += Lz * (0.5f * (G[v] + gz[v * Nf]) - G[v]);
         }
-      };
-      if (i == 0) lift(0, j + Nq * k);
-      if (i == N) lift(1, j + Nq * k);
-      if (j == 0) lift(2, i + Nq * k);
-      if (j == N) lift(3, i + Nq * k);
-      if (k == 0) lift(4, i + Nq * j);
-      if (k == N) lift(5, i + Nq * j);
+      }
 
       if ((CL == 1 && P.closure == 1) || CL == 3)
         eddy_nu<CL == 3 ? 3 : 1>(gr, F.CsDelta2, L[L_THV] + G[5], F, P.richardson, nut, Dt);
@@ -342,6 +349,13 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
     }
     __syncthreads();
     if (t < Np) {
+      // the lifted face terms of the node's x, y and z faces, without
+      // branches: weight 1 on a face, 0 (on any valid entry) inside
+      const float wx = (i == 0 || i == N) ? 1.f : 0.f, wy = (j == 0 || j == N) ? 1.f : 0.f,
+                  wz = (k == 0 || k == N) ? 1.f : 0.f;
+      const float *lx = &sLf[i == N ? 1 : 0][0][j + Nq * k];
+      const float *ly = &sLf[j == N ? 3 : 2][0][i + Nq * k];
+      const float *lz = &sLf[k == N ? 5 : 4][0][i + Nq * j];
       float R[6];
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
@@ -353,12 +367,9 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
           a2 += sD[k * Nq + m] * sF[v][2][i + Nq * (j + Nq * m)];
         }
         float r = -(F.jac[0] * a0 + F.jac[1] * a1 + F.jac[2] * a2);
-        if (i == 0) r += sLf[0][v][j + Nq * k];
-        if (i == N) r += sLf[1][v][j + Nq * k];
-        if (j == 0) r += sLf[2][v][i + Nq * k];
-        if (j == N) r += sLf[3][v][i + Nq * k];
-        if (k == 0) r += sLf[4][v][i + Nq * j];
-        if (k == N) r += sLf[5][v][i + Nq * j];
+        r = fmaf(wx, lx[v * Nf], r);
+        r = fmaf(wy, ly[v * Nf], r);
+        r = fmaf(wz, lz[v * Nf], r);
         R[v] = r;
       }
       {

@@ -98,6 +98,18 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32]) {
 #pragma unroll
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
+// Eight consecutive FP32 columns of this thread's lane, waited for.
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
 // Two consecutive FP32 columns.
 __device__ __forceinline__ void tc_ld2(uint32_t taddr, float &v0, float &v1) {
   uint32_t r0, r1;
