@@ -139,28 +139,6 @@ __device__ __forceinline__ int neighbour(const KParams &P, int ex, int ey, int e
   return storage_index(P, d == 0 ? v : ex, d == 1 ? v : ey, d == 2 ? v : ez);
 }
 
-// The same lookup written with coordinate arrays.  Only the FP32 gradient
-// pass with the learned closure uses it: that kernel sits at its 80-register
-// limit, and with the select form above it measured 3 % slower (21.5 against
-// 20.9 ms on the 256M-node box), where the flux pass and the other gradient
-// passes gain 1 to 1.5 %.
-__device__ __forceinline__ int neighbour_indexed(const KParams &P, int ex, int ey, int ez, int f) {
-  int c[3] = {ex, ey, ez};
-  const int n[3] = {P.nex, P.ney, P.nez};
-  const int d = f >> 1;
-  int v = c[d] + ((f & 1) ? 1 : -1);
-  if (v < 0 || v >= n[d]) {
-    if (P.part && d < 2) {
-      if (P.wall[f]) return -1;  // otherwise the ghost element at -1 or n[d]
-    } else {
-      if (!P.periodic[d]) return -1;
-      v = (v + n[d]) % n[d];
-    }
-  }
-  c[d] = v;
-  return storage_index(P, c[0], c[1], c[2]);
-}
-
 // Element visited at position g of a kernel's traversal (g < P.E, the
 // interior elements): its storage index, and its coordinates in (ex, ey, ez).
 // With tiling, the traversal walks 4 x 4 columns of elements bottom to top,
@@ -180,6 +158,21 @@ __device__ __forceinline__ int element_at(const KParams &P, int g, int &ex, int 
     ez = g / (P.nex * P.ney);
   }
   return storage_index(P, ex, ey, ez);
+}
+
+// For the first six lanes of a warp: element g of the traversal, its
+// storage index, layer and column to el[0], el[1], el[2] (lane 0), and its
+// neighbour across face `lane` to nb[lane].
+__device__ __forceinline__ void next_element(const KParams &P, int g, int *el, int *nb) {
+  int ex, ey, ez;
+  const int e = element_at(P, g, ex, ey, ez);
+  const int lane = threadIdx.x & 31;
+  nb[lane] = neighbour(P, ex, ey, ez, lane);
+  if (lane == 0) {
+    el[0] = e;
+    el[1] = ez;
+    el[2] = ex;
+  }
 }
 
 // The same in the plain order x fastest (kernels that do not tile).

@@ -122,19 +122,31 @@ __device__ __forceinline__ void write_f2(float *__restrict__ F2, size_t e, int t
 // The gradient pass's fields (u, v, w, h', q', theta_v') at node nn of
 // element nb, formed from its state and thermodynamic planes exactly as for
 // an own node; rho_r and q_r are the reference values at that node's height.
+// In two steps, so that a thread can have the loads of two face nodes in
+// flight: face_load gathers the seven values (rho', rho u, rho v, rho w,
+// rho q_t', h', theta_v'), face_finish forms the fields.
+__device__ __forceinline__ void face_load(const float *__restrict__ S, const float *__restrict__ TH, size_t nb, int nn,
+                                          float (&raw)[7]) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) raw[v] = S[(nb * 6 + v) * kNP + nn];
+  raw[4] = S[(nb * 6 + 5) * kNP + nn];
+  raw[5] = TH[(nb * 4 + 2) * kNP + nn];
+  raw[6] = TH[(nb * 4 + 3) * kNP + nn];
+}
+__device__ __forceinline__ void face_finish(const float (&raw)[7], float rho_r, float q_r, float (&gf)[6]) {
+  const float rinv = fdiv(1.0f, rho_r + raw[0]);
+  gf[0] = raw[1] * rinv;
+  gf[1] = raw[2] * rinv;
+  gf[2] = raw[3] * rinv;
+  gf[3] = raw[5];
+  gf[4] = (raw[4] - q_r * raw[0]) * rinv;
+  gf[5] = raw[6];
+}
 __device__ __forceinline__ void face_primitives(const float *__restrict__ S, const float *__restrict__ TH, size_t nb,
                                                 int nn, float rho_r, float q_r, float (&gf)[6]) {
-  float sp[6];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) sp[v] = S[(nb * 6 + v) * kNP + nn];
-  sp[5] = S[(nb * 6 + 5) * kNP + nn];
-  const float rinv = fdiv(1.0f, rho_r + sp[0]);
-  gf[0] = sp[1] * rinv;
-  gf[1] = sp[2] * rinv;
-  gf[2] = sp[3] * rinv;
-  gf[3] = TH[(nb * 4 + 2) * kNP + nn];
-  gf[4] = (sp[5] - q_r * sp[0]) * rinv;
-  gf[5] = TH[(nb * 4 + 3) * kNP + nn];
+  float raw[7];
+  face_load(S, TH, nb, nn, raw);
+  face_finish(raw, rho_r, q_r, gf);
 }
 
 // Sources of the momentum equations (Sec. 2, momentum balance): buoyancy of

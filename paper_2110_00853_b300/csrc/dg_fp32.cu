@@ -68,10 +68,14 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
   int stalled = 0;
   if (CL == 2) stalled = learned_setup<HOOK>(P, sMlpRaw, sBar, &sSlot, tcs);
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
+  // the element a CTA visits and its face neighbours, found by six lanes of
+  // warp 0 one element ahead (during the previous element's last phase) and
+  // shared, rather than by every thread
+  __shared__ int sEl[3];
+  if (t < 6 && blockIdx.x < P.E) next_element(P, blockIdx.x, sEl, sNb);
+  __syncthreads();
   for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
-    int ex, ey, ez;
-    const int e = element_at(P, g, ex, ey, ez);
-    if (t < 6) sNb[t] = CL == 2 ? neighbour_indexed(P, ex, ey, ez, t) : neighbour(P, ex, ey, ez, t);
+    const int e = sEl[0], ez = sEl[1];
     float sv[6], G[6];
     const float *L = P.lev32 + (size_t)(ez * Nq + (k < Nq ? k : 0)) * L_NF;
     if (t < Np) {
@@ -90,27 +94,39 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
       for (int v = 0; v < 6; ++v) sG[v][t] = G[v];
     }
     __syncthreads();
-    for (int task = t; task < 6 * Nf; task += blockDim.x) {
-      const int f = task / Nf, fn = task - f * Nf;
-      const int nb = sNb[f];
-      const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
-      if (nb < 0) {
-        // a wall: the mirror state (normal velocity reversed), so that the
-        // lift below is the same formula on every face
-        const int n = face_node<Nq>(d, (f & 1) ? N : 0, t1, t2);
+    {
+      // the 6 Nf face nodes, at most two per thread (task t and t + 128),
+      // with the loads of both in flight before either is finished
+      static_assert(6 * Nf <= 256, "two face nodes per thread at most");
+      float ra[7], rb[7];
+      const int tb = t + 128;
+      auto load = [&](int task, float (&raw)[7]) {
+        const int f = task / Nf, fn = task - f * Nf;
+        const int nb = sNb[f];
+        if (nb >= 0) face_load(S, TH, nb, face_node<Nq>(f >> 1, (f & 1) ? 0 : N, fn % Nq, fn / Nq), raw);
+      };
+      auto finish = [&](int task, const float (&raw)[7]) {
+        const int f = task / Nf, fn = task - f * Nf;
+        const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
+        if (sNb[f] < 0) {
+          // a wall: the mirror state (normal velocity reversed), so that the
+          // lift below is the same formula on every face
+          const int n = face_node<Nq>(d, (f & 1) ? N : 0, t1, t2);
 #pragma unroll
-        for (int v = 0; v < 6; ++v) sGf[f][v][fn] = v == d ? -sG[v][n] : sG[v][n];
-        continue;
-      }
-      const int a_nb = (f & 1) ? 0 : N;
-      const int nn = face_node<Nq>(d, a_nb, t1, t2);
-      // the shared face node has the same height, hence the same level values
-      const int lev = ez * Nq + (d == 2 ? (f & 1 ? N : 0) : t2);
-      const float *Lf = P.lev32 + (size_t)lev * L_NF;
-      float gf[6];
-      face_primitives(S, TH, nb, nn, Lf[L_RHO], Lf[L_QM], gf);
+          for (int v = 0; v < 6; ++v) sGf[f][v][fn] = v == d ? -sG[v][n] : sG[v][n];
+          return;
+        }
+        // the shared face node has the same height, hence the same level values
+        const float *Lf = P.lev32 + (size_t)(ez * Nq + (d == 2 ? (f & 1 ? N : 0) : t2)) * L_NF;
+        float gf[6];
+        face_finish(raw, Lf[L_RHO], Lf[L_QM], gf);
 #pragma unroll
-      for (int v = 0; v < 6; ++v) sGf[f][v][fn] = gf[v];
+        for (int v = 0; v < 6; ++v) sGf[f][v][fn] = gf[v];
+      };
+      if (t < 6 * Nf) load(t, ra);
+      if (tb < 6 * Nf) load(tb, rb);
+      if (t < 6 * Nf) finish(t, ra);
+      if (tb < 6 * Nf) finish(tb, rb);
     }
     __syncthreads();
     float gr[6][3];
@@ -156,6 +172,7 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
     // the learned closure on the tensor cores, row t = node t
     if (CL == 2) learned_nu<HOOK>(W, sA, tcs, gr, F.Delta, t < Np, nut, Dt);
     if (t < Np) write_f2(F2, e, t, L[L_RHO] + sv[0], nut, Dt, gr, sv, G);
+    if (t < 6 && g + (int)gridDim.x < P.E) next_element(P, g + gridDim.x, sEl, sNb);
     __syncthreads();
   }
   if (CL == 2) {
@@ -188,10 +205,12 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
   if (t < Nq * Nq) sD[t] = (float)P.D[t];
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
   int fail = 0;
+  // the element and its neighbours, found one element ahead by six lanes
+  __shared__ int sEl[3];
+  if (t < 6 && blockIdx.x < P.E) next_element(P, blockIdx.x, sEl, sNb);
+  __syncthreads();
   for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
-    int ex, ey, ez;
-    const int e = element_at(P, g, ex, ey, ez);
-    if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
+    const int e = sEl[0], ez = sEl[1], ex = sEl[2];
     const float *L = P.lev32 + (size_t)(ez * Nq + (k < Nq ? k : 0)) * L_NF;
     float sv[6];
     // the update's inputs, loaded with the element's first loads so that
@@ -396,6 +415,7 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
       // the thermodynamics of the new state, for the next stage's two passes
       if (UPD) thermo_store32(P, L, sn, THout, e, t, fail);
     }
+    if (t < 6 && g + (int)gridDim.x < P.E) next_element(P, g + gridDim.x, sEl, sNb);
     __syncthreads();
   }
   if (fail) atomicAdd(P.flags, 1);
