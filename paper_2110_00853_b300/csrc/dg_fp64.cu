@@ -269,9 +269,37 @@ __global__ void __launch_bounds__(block64(N)) k_rhs64(const double *__restrict__
       double Ym[6], Yp[6];
 #pragma unroll
       for (int v = 0; v < 6; ++v) Ym[v] = sY[v][n];
-      const double pm = TH[((size_t)e * 4) * Np + n];
       const double cm = TH[((size_t)e * 4 + 1) * Np + n];
       const int nb = sNb[f];
+      if (FL == 0 && nb >= 0) {
+        // Rusanov across an interior face.  The own node's total normal flux
+        // n.(F1 + F2) is sF from the first phase, so the lifted jump
+        // n.F_- - F* is 1/2 n.(F_- - F_+) - lambda/2 (Y_- - Y_+) and only
+        // the neighbour's F1 is evaluated here.
+        const int nn = face_node<Nq>(d, N - a, t1, t2);
+#pragma unroll
+        for (int v = 0; v < 6; ++v) Yp[v] = Q[((size_t)nb * 6 + v) * Np + nn];
+        const double pp = TH[((size_t)nb * 4) * Np + nn];
+        const double cp = TH[((size_t)nb * 4 + 1) * Np + nn];
+        const double *g2p = F2 + ((size_t)nb * 15 + d * 5) * Np + nn;
+        double fp[6];
+        const double ip = 1.0 / Yp[0];
+        flux1_dir(Yp, ip, pp, pr, d, fp);
+        fp[0] += g2p[0];
+        fp[1] += g2p[1 * Np];
+        fp[2] += g2p[2 * Np];
+        fp[3] += g2p[3 * Np];
+        fp[4] += g2p[4 * Np];
+        fp[5] += g2p[0];
+        const double lm = fabs((d == 0 ? Ym[1] : (d == 1 ? Ym[2] : Ym[3])) / Ym[0]) + cm;
+        const double lp = fabs((d == 0 ? Yp[1] : (d == 1 ? Yp[2] : Yp[3])) * ip) + cp;
+        const double lam = fmax(lm, lp);
+#pragma unroll
+        for (int v = 0; v < 6; ++v)
+          sL[f][v][fn] = P.lift[d] * (0.5 * sg * (sF[v][d][n] - fp[v]) - 0.5 * lam * (Ym[v] - Yp[v]));
+        continue;
+      }
+      const double pm = TH[((size_t)e * 4) * Np + n];
       double pp, cp, f2s[5];
       if (nb >= 0) {
         const int nn = face_node<Nq>(d, N - a, t1, t2);
