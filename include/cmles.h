@@ -127,6 +127,13 @@ typedef struct {
   double filter_alpha;
   int filter_vars;
   int integrator;        /* CMLES_LSRK54 (default), CMLES_LSRK144 or CMLES_ARK2_HEVI */
+  /* Bottom wall (App. A.1): the wall-parallel momentum flux of the
+   * aerodynamic drag law (Eq. drag_law), n.(rho tau) = -rho C_d |u_p| u_p,
+   * with this constant C_d, n the inward normal, rho the density at the wall
+   * node and u_p the wall-parallel velocity at the node of the first
+   * interior layer above it; the energy flux is unchanged.  0 (default):
+   * free slip.  Negative or non-finite: CMLES_ERR_ARG. */
+  double drag_cd;
 } cmles_params;
 
 typedef struct {

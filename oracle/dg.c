@@ -518,6 +518,27 @@ int orc_rhs(orc_solver *s, const double *Q, double *RHS, int form) {
               f2s[0] = -E_w * (-nrm[2]);
               f2s[4] = -(P->shf + P->lhf) * (-nrm[2]);
             }
+            if (d == 2 && side == 0 && P->drag_cd > 0.0) {
+              /* Aerodynamic drag law (Eq. drag_law): with n the inward
+               * normal, n.(rho tau) = -rho C_d |u_p| u_p, u_p the
+               * wall-parallel velocity at the interior point, read as the
+               * node of the first interior layer (k = 1) above this face
+               * node, and rho the density at the wall node.  The outward
+               * normal is -n, so n_out.(rho tau) = +rho C_d |u_p| u_p.  The
+               * energy flux is unchanged (its kinetic part is neglected). */
+              int ni = face_node(Nq, 2, 1, t1, t2);
+              double ui[3], un = 0.0, up2 = 0.0;
+              for (int c = 0; c < 3; ++c) {
+                ui[c] = Q[((size_t)e * 6 + 1 + c) * Np + ni] / Q[((size_t)e * 6 + 0) * Np + ni];
+                un += ui[c] * nrm[c];
+              }
+              for (int c = 0; c < 3; ++c) {
+                ui[c] -= un * nrm[c];
+                up2 += ui[c] * ui[c];
+              }
+              double drag = Ym[0] * P->drag_cd * sqrt(up2);
+              for (int c = 0; c < 3; ++c) f2s[1 + c] = drag * ui[c];
+            }
           }
           if (P->flux == ORC_FLUX_HLLC)
             orc_hllc(P, Ym, Yp, s->z[q], s->p_r[q], nrm, F1s);

@@ -63,6 +63,9 @@ typedef struct {
   double shf, lhf;
   double Omega[3];            /* planetary rotation for the Coriolis term */
   int flux;                   /* ORC_FLUX_*: numerical flux of F1 on faces (Sec. 3.1) */
+  /* bottom wall: wall-parallel momentum flux by the aerodynamic drag law
+   * (Eq. drag_law) with this constant C_d; 0: free slip */
+  double drag_cd;
 } orc_params;
 
 typedef struct orc_solver orc_solver;

@@ -187,6 +187,7 @@ void fill_kparams(cmles_handle h) {
   K.surface_flux = p.surface_flux;
   K.E_water = p.lhf / p.Lv0;
   K.E_energy = p.shf + p.lhf;
+  K.drag_cd = p.drag_cd;
   K.N = h->N;
   K.nex = m.nex;
   K.ney = m.ney;
@@ -255,6 +256,7 @@ void fill_kparams(cmles_handle h) {
   }
   F.E_water = (float)K.E_water;
   F.E_energy = (float)K.E_energy;
+  F.drag_cd = (float)K.drag_cd;
   K.tiled = (m.nex % 4 == 0 && m.ney % 4 == 0) ? 1 : 0;
   K.lev32 = h->lev32;
   K.dH32 = h->dH32;
@@ -575,6 +577,7 @@ void cmles_default_params(cmles_params *p) {
   p->filter_alpha = -log(pow(2.0, -52));
   p->filter_vars = 0xE;
   p->integrator = CMLES_LSRK54;
+  p->drag_cd = 0.0;
 }
 
 // Tangent table of the saturation vapour density rho_vs(T) = p_v*(T)/(R_v T)
@@ -706,6 +709,7 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
     return CMLES_ERR_ARG;
   if (params->filter_order < 0 || !(params->filter_alpha >= 0.0) || (params->filter_vars & ~0xE) != 0)
     return CMLES_ERR_ARG;
+  if (!(params->drag_cd >= 0.0) || !std::isfinite(params->drag_cd)) return CMLES_ERR_ARG;
   if (params->integrator != CMLES_LSRK54 && params->integrator != CMLES_LSRK144 &&
       params->integrator != CMLES_ARK2_HEVI)
     return CMLES_ERR_ARG;

@@ -26,6 +26,7 @@ struct KF {
   float kpow[6];  // binomial coefficients of (1 + v)^-kappa: kpow[n-1] = C(-kappa, n), n = 1..6
   float u_relax[3], Omega[3];
   float E_water, E_energy;
+  float drag_cd;
 };
 
 // Per-level FP32 table of the FP32 path (16 floats per node level).
@@ -70,6 +71,7 @@ struct KParams {
   int surface_flux;
   double E_water;    // LHF / L_v0 (kg m^-2 s^-1)
   double E_energy;   // SHF + LHF (W m^-2)
+  double drag_cd;    // bottom-wall drag coefficient of Eq. drag_law (0: free slip)
   // mesh (flat, uniform elements); N: the polynomial order
   int N;
   int nex, ney, nez, E;

@@ -322,6 +322,21 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
           f2s[0] = -F.E_water * (-nv[2]);
           f2s[4] = -F.E_energy * (-nv[2]);
         }
+        if (f == 4 && F.drag_cd > 0.f) {
+          // drag law (Eq. drag_law) on the terrain: outward flux
+          // rho C_d |u_p| u_p of momentum, u_p the velocity at the node of
+          // the first interior layer above this face node less its component
+          // along the wall normal
+          const int ni = face_node<Nq>(2, 1, t1, t2);
+          const float ri = 1.0f / (P.node32[(size_t)e * C_NF * kNP + L_RHO * kNP + ni] + sS[0][ni]);
+          float up[3] = {sS[1][ni] * ri, sS[2][ni] * ri, sS[3][ni] * ri};
+          const float un = up[0] * nv[0] + up[1] * nv[1] + up[2] * nv[2];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) up[c] -= un * nv[c];
+          const float c0 = (rho_r + sm[0]) * F.drag_cd * sqrtf(up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) f2s[1 + c] = c0 * up[c];
+        }
       }
       float fm[6], fp[6];
       flux1_normal32(sm, rho_r, rhoq_r, Hr, pm, nv, fm);

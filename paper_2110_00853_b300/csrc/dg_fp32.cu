@@ -314,6 +314,17 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
           f2s[0] = -F.E_water;
           f2s[4] = -F.E_energy;
         }
+        if (f == 4 && F.drag_cd > 0.f) {
+          // drag law (Eq. drag_law) on the flat bottom: outward flux
+          // rho C_d |u_p| u_p of the horizontal momentum, u_p from the node
+          // of the first interior layer above this face node
+          const int ni = face_node<Nq>(2, 1, t1, t2);
+          const float ri = fdiv(1.0f, P.lev32[(size_t)(ez * Nq + 1) * L_NF + L_RHO] + sS[0][ni]);
+          const float ux = sS[1][ni] * ri, uy = sS[2][ni] * ri;
+          const float c = (rho_r + sm[0]) * F.drag_cd * sqrtf(ux * ux + uy * uy);
+          f2s[1] = c * ux;
+          f2s[2] = c * uy;
+        }
       }
       float fm[6], fp[6], f1s[6];
       flux1_dev32(sm, rho_r, rhoq_r, pm, d, fm);

@@ -327,6 +327,17 @@ __global__ void __launch_bounds__(block64(N)) k_rhs64(const double *__restrict__
           f2s[0] = -P.E_water;
           f2s[4] = -P.E_energy;
         }
+        if (f == 4 && P.drag_cd > 0.0) {
+          // drag law (Eq. drag_law) on the flat bottom: outward flux
+          // rho C_d |u_p| u_p of the horizontal momentum, u_p from the node
+          // of the first interior layer above this face node
+          const int ni = face_node<Nq>(2, 1, t1, t2);
+          const double ri = 1.0 / sY[0][ni];
+          const double ux = sY[1][ni] * ri, uy = sY[2][ni] * ri;
+          const double c = Ym[0] * P.drag_cd * sqrt(ux * ux + uy * uy);
+          f2s[1] = c * ux;
+          f2s[2] = c * uy;
+        }
       }
       double fm[6], fp[6], f1s[6];
       const double im = 1.0 / Ym[0], ip = 1.0 / Yp[0];

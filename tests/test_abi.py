@@ -66,6 +66,10 @@ def test_create_rejects_unsupported_combinations_without_gpu_work():
     P = cmles.make_params({}, "fp64")
     P.precision = 5
     assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == ERR_ARG
+    # the drag coefficient of the bottom wall: non-negative and finite
+    for cd in (-0.01, float("inf"), float("nan")):
+        P = cmles.make_params({"drag_cd": cd}, "fp64")
+        assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == ERR_ARG, cd
 
 
 def test_create_order_limits_without_gpu_work():
