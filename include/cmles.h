@@ -134,6 +134,14 @@ typedef struct {
    * interior layer above it; the energy flux is unchanged.  0 (default):
    * free slip.  Negative or non-finite: CMLES_ERR_ARG. */
   double drag_cd;
+  /* Wall faces with no-slip velocity (App. A.3): bit f for face f (0 -x,
+   * 1 +x, 2 -y, 3 +y, 4 bottom, 5 top).  There the velocity ghost of the
+   * face fluxes and of the gradient is u+ = -u- (u_bc = 0), elsewhere the
+   * reflection u+ = u- - 2 (n.u-) n; scalars are copied either way and the
+   * wall's diffusive fluxes stay those specified (zero, the surface fluxes,
+   * the drag law).  Bits of periodic directions have no effect; bits above
+   * 5: CMLES_ERR_ARG.  0 (default): free slip everywhere. */
+  int noslip;
 } cmles_params;
 
 typedef struct {

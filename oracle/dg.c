@@ -272,10 +272,12 @@ static void face_normal(const orc_solver *s, int e, int n, int d, int side, doub
 /* Reflecting wall state (Eq. bc-velocity-impenetrable):
  * u+ = u- - 2 (n.u-) n, scalars copied (homogeneous Neumann reading of
  * Eq. bc-general_tracer). */
-static void wall_ghost(const double Ym[6], const double nrm[3], double Yp[6]) {
+static void wall_ghost(const double Ym[6], const double nrm[3], int noslip, double Yp[6]) {
+  /* u+ = 2 u_bc - u- (Eq. bc-velocity-impenetrable): u_bc = u- - (n.u-) n
+   * reflects the normal component; no-slip, u_bc = 0, reverses all three */
   double mn = Ym[1] * nrm[0] + Ym[2] * nrm[1] + Ym[3] * nrm[2];
   Yp[0] = Ym[0];
-  for (int c = 0; c < 3; ++c) Yp[1 + c] = Ym[1 + c] - 2.0 * mn * nrm[c];
+  for (int c = 0; c < 3; ++c) Yp[1 + c] = noslip ? -Ym[1 + c] : Ym[1 + c] - 2.0 * mn * nrm[c];
   Yp[4] = Ym[4];
   Yp[5] = Ym[5];
 }
@@ -351,8 +353,12 @@ int orc_rhs(orc_solver *s, const double *Q, double *RHS, int form) {
             int np = face_node(Nq, d, N - a, t1, t2);
             for (int v = 0; v < 6; ++v) Gp[v] = s->G[((size_t)nb * 6 + v) * Np + np];
           } else {
+            /* the wall ghost of the velocity as in the flux pass (reflected
+             * normal component, or reversed at a no-slip wall); scalars
+             * copied */
             double un = Gm[0] * nrm[0] + Gm[1] * nrm[1] + Gm[2] * nrm[2];
-            for (int c = 0; c < 3; ++c) Gp[c] = Gm[c] - 2.0 * un * nrm[c];
+            const int ns = (P->noslip >> f) & 1;
+            for (int c = 0; c < 3; ++c) Gp[c] = ns ? -Gm[c] : Gm[c] - 2.0 * un * nrm[c];
             for (int v = 3; v < 6; ++v) Gp[v] = Gm[v];
           }
           double lift = Js / (s->w[a] * s->J[(size_t)e * Np + n]);
@@ -506,7 +512,7 @@ int orc_rhs(orc_solver *s, const double *Q, double *RHS, int form) {
               f2s[k] = 0.5 * (f2m[k] + f2p);  /* central flux for F2 (BR1) */
             }
           } else {
-            wall_ghost(Ym, nrm, Yp);
+            wall_ghost(Ym, nrm, (P->noslip >> f) & 1, Yp);
             /* Wall-normal diffusive fluxes are specified directly (App. A.3):
              * zero at free-slip, insulated, impermeable walls; at the bottom
              * with prescribed surface fluxes, the upward energy flux is

@@ -66,6 +66,10 @@ typedef struct {
   /* bottom wall: wall-parallel momentum flux by the aerodynamic drag law
    * (Eq. drag_law) with this constant C_d; 0: free slip */
   double drag_cd;
+  /* wall faces (bit f: 0 -x, 1 +x, 2 -y, 3 +y, 4 bottom, 5 top) where the
+   * velocity ghost is no-slip, u+ = -u- (App. A.3, u_bc = 0), instead of the
+   * reflection of the normal component */
+  int noslip;
 } orc_params;
 
 typedef struct orc_solver orc_solver;

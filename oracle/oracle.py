@@ -41,7 +41,7 @@ class Params(C.Structure):
         ("moist", C.c_int), ("sponge_alpha", C.c_double), ("sponge_zs", C.c_double),
         ("sponge_gamma", C.c_double), ("u_relax", C.c_double * 3), ("lateral_sponge_frac", C.c_double),
         ("surface_flux", C.c_int), ("shf", C.c_double), ("lhf", C.c_double), ("Omega", C.c_double * 3),
-        ("flux", C.c_int), ("drag_cd", C.c_double)]
+        ("flux", C.c_int), ("drag_cd", C.c_double), ("noslip", C.c_int)]
 
 
 class Case(C.Structure):
@@ -147,7 +147,7 @@ def _p(a):
 def make_params(closure="sl", moist=False, Cs=0.21, Prt=1.0 / 3.0, richardson=True, sponge_alpha=0.0,
                 sponge_zs=0.0, sponge_gamma=2.0, u_relax=(0.0, 0.0, 0.0), lateral_sponge_frac=0.0,
                 surface_flux=False, shf=0.0, lhf=0.0, Omega=(0.0, 0.0, 0.0), flux="rusanov", drag_cd=0.0,
-                **const):
+                noslip=0, **const):
     c = dict(CONSTANTS)
     c.update(const)
     P = Params(**c)
@@ -160,6 +160,7 @@ def make_params(closure="sl", moist=False, Cs=0.21, Prt=1.0 / 3.0, richardson=Tr
     P.Omega = (C.c_double * 3)(*Omega)
     P.flux = FLUX[flux]
     P.drag_cd = drag_cd
+    P.noslip = int(noslip)
     return P
 
 

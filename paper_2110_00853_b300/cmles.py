@@ -42,7 +42,8 @@ class Params(C.Structure):
         ("u_relax", C.c_double * 3), ("lateral_sponge_frac", C.c_double), ("surface_flux", C.c_int),
         ("shf", C.c_double), ("lhf", C.c_double), ("Omega", C.c_double * 3), ("precision", C.c_int),
         ("dt", C.c_double), ("satadj_max_iter", C.c_int), ("flux", C.c_int), ("filter_order", C.c_int),
-        ("filter_alpha", C.c_double), ("filter_vars", C.c_int), ("integrator", C.c_int), ("drag_cd", C.c_double)]
+        ("filter_alpha", C.c_double), ("filter_vars", C.c_int), ("integrator", C.c_int), ("drag_cd", C.c_double),
+        ("noslip", C.c_int)]
 
 
 class Diag(C.Structure):

@@ -188,6 +188,7 @@ void fill_kparams(cmles_handle h) {
   K.E_water = p.lhf / p.Lv0;
   K.E_energy = p.shf + p.lhf;
   K.drag_cd = p.drag_cd;
+  K.noslip = p.noslip;
   K.N = h->N;
   K.nex = m.nex;
   K.ney = m.ney;
@@ -578,6 +579,7 @@ void cmles_default_params(cmles_params *p) {
   p->filter_vars = 0xE;
   p->integrator = CMLES_LSRK54;
   p->drag_cd = 0.0;
+  p->noslip = 0;
 }
 
 // Tangent table of the saturation vapour density rho_vs(T) = p_v*(T)/(R_v T)
@@ -710,6 +712,7 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
   if (params->filter_order < 0 || !(params->filter_alpha >= 0.0) || (params->filter_vars & ~0xE) != 0)
     return CMLES_ERR_ARG;
   if (!(params->drag_cd >= 0.0) || !std::isfinite(params->drag_cd)) return CMLES_ERR_ARG;
+  if (params->noslip & ~0x3F) return CMLES_ERR_ARG;
   if (params->integrator != CMLES_LSRK54 && params->integrator != CMLES_LSRK144 &&
       params->integrator != CMLES_ARK2_HEVI)
     return CMLES_ERR_ARG;

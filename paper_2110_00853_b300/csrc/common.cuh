@@ -72,6 +72,7 @@ struct KParams {
   double E_water;    // LHF / L_v0 (kg m^-2 s^-1)
   double E_energy;   // SHF + LHF (W m^-2)
   double drag_cd;    // bottom-wall drag coefficient of Eq. drag_law (0: free slip)
+  int noslip;        // wall faces (bit f) with the no-slip velocity ghost u+ = -u-
   // mesh (flat, uniform elements); N: the polynomial order
   int N;
   int nex, ney, nez, E;

@@ -139,11 +139,16 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
             for (int c = 0; c < 3; ++c) gr[v][c] += Lf * nv[c] * jump;
           }
         } else {
+          // the wall ghost: reflected normal velocity, or at a no-slip wall
+          // every component reversed (jump -G)
+          const bool ns = (P.noslip >> f) & 1;
           const float un = G[0] * nv[0] + G[1] * nv[1] + G[2] * nv[2];
 #pragma unroll
-          for (int v = 0; v < 3; ++v)
+          for (int v = 0; v < 3; ++v) {
+            const float jump = ns ? -G[v] : -un * nv[v];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) gr[v][c] += Lf * nv[c] * (-un * nv[v]);
+            for (int c = 0; c < 3; ++c) gr[v][c] += Lf * nv[c] * jump;
+          }
         }
       };
       if (i == 0) lift(0, j + Nq * k);
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
 #pragma unroll
         for (int v = 0; v < 6; ++v) sp[v] = sm[v];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) sp[1 + c] = sm[1 + c] - 2.0f * mn * nv[c];
+        for (int c = 0; c < 3; ++c) sp[1 + c] = ((P.noslip >> f) & 1) ? -sm[1 + c] : sm[1 + c] - 2.0f * mn * nv[c];
         pp = pm;
         cp = cm;
 #pragma unroll

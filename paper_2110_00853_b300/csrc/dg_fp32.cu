@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
           // lift below is the same formula on every face
           const int n = face_node<Nq>(d, (f & 1) ? N : 0, t1, t2);
 #pragma unroll
-          for (int v = 0; v < 6; ++v) sGf[f][v][fn] = v == d ? -sG[v][n] : sG[v][n];
+          for (int v = 0; v < 6; ++v)
+            sGf[f][v][fn] = (v == d || (v < 3 && ((P.noslip >> f) & 1))) ? -sG[v][n] : sG[v][n];
           return;
         }
         // the shared face node has the same height, hence the same level values
@@ -303,9 +304,11 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
       } else {
 #pragma unroll
         for (int v = 0; v < 6; ++v) sp[v] = sm[v];
-        sp[1] = d == 0 ? -sm[1] : sm[1];
-        sp[2] = d == 1 ? -sm[2] : sm[2];
-        sp[3] = d == 2 ? -sm[3] : sm[3];
+        // (no-slip: u_bc = 0, every velocity component reversed)
+        const bool ns = (P.noslip >> f) & 1;
+        sp[1] = (ns || d == 0) ? -sm[1] : sm[1];
+        sp[2] = (ns || d == 1) ? -sm[2] : sm[2];
+        sp[3] = (ns || d == 2) ? -sm[3] : sm[3];
         pp = pm;
         cp = cm;
 #pragma unroll

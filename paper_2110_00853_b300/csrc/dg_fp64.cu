@@ -122,6 +122,10 @@ __global__ void __launch_bounds__(block64(N)) k_grad64(const double *__restrict_
         if (sNb[f] >= 0) {
 #pragma unroll
           for (int v = 0; v < 6; ++v) gr[v][d] += L * (0.5 * (G[v] + sGf[f][v][fn]) - G[v]);
+        } else if ((P.noslip >> f) & 1) {
+          // no-slip wall: every velocity component's ghost is -G
+#pragma unroll
+          for (int c = 0; c < 3; ++c) gr[c][d] += L * (-G[c]);
         } else {
           gr[d][d] += L * (-G[d]);
         }
@@ -315,9 +319,11 @@ __global__ void __launch_bounds__(block64(N)) k_rhs64(const double *__restrict__
         // reflecting wall state (Eq. bc-velocity-impenetrable), scalars copied
 #pragma unroll
         for (int v = 0; v < 6; ++v) Yp[v] = Ym[v];
-        Yp[1] = d == 0 ? -Ym[1] : Ym[1];
-        Yp[2] = d == 1 ? -Ym[2] : Ym[2];
-        Yp[3] = d == 2 ? -Ym[3] : Ym[3];
+        // (no-slip: u_bc = 0, every velocity component reversed)
+        const bool ns = (P.noslip >> f) & 1;
+        Yp[1] = (ns || d == 0) ? -Ym[1] : Ym[1];
+        Yp[2] = (ns || d == 1) ? -Ym[2] : Ym[2];
+        Yp[3] = (ns || d == 2) ? -Ym[3] : Ym[3];
         pp = pm;
         cp = cm;
         // wall-normal diffusive fluxes specified directly (App. A.3)

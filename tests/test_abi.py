@@ -70,6 +70,9 @@ def test_create_rejects_unsupported_combinations_without_gpu_work():
     for cd in (-0.01, float("inf"), float("nan")):
         P = cmles.make_params({"drag_cd": cd}, "fp64")
         assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == ERR_ARG, cd
+    # no-slip walls: a mask over the six faces
+    P = cmles.make_params({"noslip": 1 << 6}, "fp64")
+    assert L.cmles_create(ctypes.byref(m), ctypes.byref(P), ctypes.byref(h)) == ERR_ARG
 
 
 def test_create_order_limits_without_gpu_work():

@@ -1,8 +1,10 @@
-"""The bottom-wall drag law (App. A.1, Eq. drag_law) on the GPU against the
-oracle: tendencies and one LSRK step with a mean flow over the wall, FP64
-and FP32 on the flat moist layer, FP32 on the warped ridge mesh; and the drag
-term itself (tendency with C_d minus tendency without), which decelerates
-the wall-parallel flow of the bottom face nodes only."""
+"""Wall options on the GPU against the oracle, with a mean flow over the
+walls: the bottom-wall drag law (App. A.1, Eq. drag_law), and no-slip
+velocity ghosts (App. A.3) on the bottom and top walls, alone and together;
+FP64 and FP32 on the flat moist layer, FP32 on the warped ridge mesh;
+tendencies and one LSRK step.  The drag term itself (tendency with C_d minus
+tendency without) decelerates the wall-parallel flow of the bottom face
+nodes only."""
 import numpy as np
 import pytest
 
@@ -111,7 +113,52 @@ def test_drag_tendency_and_step_against_oracle(orc, label, cfg, precision, tol):
     G0.close()
 
 
-def test_drag_rejects_negative_coefficients():
+def test_wall_options_reject_bad_values():
     from paper_2110_00853_b300 import cmles
     with pytest.raises(cmles.CmlesError):
         cmles.Solver(I.sub_mesh("c2", 2, 2, 2), dict(I.physics("c2"), drag_cd=-1.0), precision="fp64")
+    with pytest.raises(cmles.CmlesError):
+        cmles.Solver(I.sub_mesh("c2", 2, 2, 2), dict(I.physics("c2"), noslip=1 << 6), precision="fp64")
+
+
+NOSLIP_CASES = [("flat fp64", "c2", "fp64", 1e-12, 0.0), ("flat fp32", "c2", "fp32", 1e-5, 0.0),
+                ("flat fp32 with drag", "c2", "fp32", 1e-5, CD), ("warped fp32 with drag", "c3", "fp32", 1e-5, CD)]
+
+
+@pytest.mark.parametrize("label,cfg,precision,tol,cd", NOSLIP_CASES, ids=[c[0] for c in NOSLIP_CASES])
+def test_noslip_walls_against_oracle(orc, label, cfg, precision, tol, cd):
+    from paper_2110_00853_b300 import cmles
+    if cfg == "c2":
+        m = I.sub_mesh("c2", 5, 4, 3)
+        ph = dict(I.physics("c2"), drag_cd=cd, noslip=0b110000)
+    else:
+        m = _hill_box()
+        ph = dict(I.physics("c3"), sponge_zs=0.75 * m["Lz"], drag_cd=cd, noslip=0b010000)
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case(cfg))
+    Q = _flow(Q, seed=11)
+    G = cmles.Solver(m, ph, precision=precision)
+    if cfg == "c2":
+        G.set_reference(_levels(rr, m), _levels(pr, m), _levels(Q[:, 5] / Q[:, 0], m))
+    else:
+        G.set_reference(rr.ravel(), pr.ravel(), None)
+    R_orc, fails = S.rhs(Q)
+    assert fails == 0
+    # the no-slip ghost changes the wall tendency: it must differ from free slip
+    S_fs = orc.from_inputs(m, dict(ph, noslip=0))
+    S_fs.set_reference(rr, pr)
+    R_fs, _ = S_fs.rhs(Q)
+    assert _rel(R_orc[:, 1], R_fs[:, 1]) > 1e-3
+    Qd = torch.from_numpy(Q).cuda()
+    R_gpu = G.tendency(Qd).cpu().numpy()
+    for v in range(5):
+        err = _rel(R_gpu[:, v], R_orc[:, v])
+        assert err <= tol, (label, v, err)
+        assert np.abs(R_gpu[:, v] - R_orc[:, v]).max() <= 10 * tol * np.abs(R_orc[:, v]).max(), (label, v)
+    G.set_state(Qd)
+    G.step(1)
+    Qo, _ = S.lsrk54(Q, 1, ph["dt"])
+    Qg = G.get_state().cpu().numpy()
+    for v in range(5):
+        e = _rel(Qg[:, v] - Q[:, v], Qo[:, v] - Q[:, v])
+        assert e <= (1e-11 if precision == "fp64" else 1e-5), (label, v, e)
+    G.close()
