@@ -201,6 +201,9 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
   __shared__ float sU[3][kNP];
   __shared__ float sLf[6][6][Nf];
   __shared__ int sNb[6];
+  // the drag law's C_d |u_p| u_p of the bottom face nodes, from the nodes of
+  // the first interior layer above them
+  __shared__ float sDrag[2][Nf];
   const KF &F = P.f;
   const int t = threadIdx.x;
   if (t < Nq * Nq) sD[t] = (float)P.D[t];
@@ -241,6 +244,12 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
         sF[4][d][t] = f[4] + g2[4 * kNP];
         sF[5][d][t] = f[5] + c0;
         sU[d][t] = fdiv(sv[1 + d], rho);
+      }
+      if (k == 1 && F.drag_cd > 0.f && sNb[4] < 0) {
+        const float ux = sU[0][t], uy = sU[1][t];
+        const float c = F.drag_cd * sqrtf(ux * ux + uy * uy);
+        sDrag[0][i + Nq * j] = c * ux;
+        sDrag[1][i + Nq * j] = c * uy;
       }
     }
     __syncthreads();
@@ -319,14 +328,11 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
         }
         if (f == 4 && F.drag_cd > 0.f) {
           // drag law (Eq. drag_law) on the flat bottom: outward flux
-          // rho C_d |u_p| u_p of the horizontal momentum, u_p from the node
-          // of the first interior layer above this face node
-          const int ni = face_node<Nq>(2, 1, t1, t2);
-          const float ri = fdiv(1.0f, P.lev32[(size_t)(ez * Nq + 1) * L_NF + L_RHO] + sS[0][ni]);
-          const float ux = sS[1][ni] * ri, uy = sS[2][ni] * ri;
-          const float c = (rho_r + sm[0]) * F.drag_cd * sqrtf(ux * ux + uy * uy);
-          f2s[1] = c * ux;
-          f2s[2] = c * uy;
+          // rho C_d |u_p| u_p of the horizontal momentum, C_d |u_p| u_p from
+          // the first phase
+          const float rw = rho_r + sm[0];
+          f2s[1] = rw * sDrag[0][fn];
+          f2s[2] = rw * sDrag[1][fn];
         }
       }
       float fm[6], fp[6], f1s[6];
