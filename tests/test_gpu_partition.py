@@ -66,12 +66,18 @@ CASES = [
     ("moist layer, fp32", I.sub_mesh("c2", 6, 5, 4), "fp32", "sl", (2, 2)),
     ("moist layer, fp32 learned closure", I.sub_mesh("c2", 5, 6, 3), "fp32", "mlp", (2, 3)),
     ("moist layer, fp32 tiled partitions", I.sub_mesh("c2", 8, 8, 2), "fp32", "sl", (2, 2)),
+    # walls in z with the drag law and no-slip ghosts, which every partition holds
+    ("moist layer, fp64 no-slip and drag", I.sub_mesh("c2", 6, 4, 3), "fp64", "sl+walls", (3, 2)),
+    ("moist layer, fp32 no-slip and drag", I.sub_mesh("c2", 8, 4, 3), "fp32", "sl+walls", (2, 2)),
 ]
 
 
 @pytest.mark.parametrize("label,mesh,precision,closure,split", CASES, ids=[c[0] for c in CASES])
 def test_group_tendency_and_steps_are_bit_identical(orc, label, mesh, precision, closure, split):
-    phys = I.physics("c2", closure=closure)
+    if closure == "sl+walls":
+        phys = dict(I.physics("c2", closure="sl"), drag_cd=0.015, noslip=0b110000)
+    else:
+        phys = I.physics("c2", closure=closure)
     S, Q, W, G = _pair(orc, mesh, phys, I.case("c2"), precision, *split, fuzz_seed=3)
     Qd = torch.from_numpy(Q).cuda()
     Rw = W.tendency(Qd).cpu().numpy()
