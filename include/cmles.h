@@ -198,7 +198,9 @@ cmles_status cmles_set_stream(cmles_handle h, void *stream);
  * q_r of the same profile, used only as the FP32 storage offset).  Host
  * arrays of n values: one per node level (n = nez (N+1), level = ez (N+1) + k)
  * for flat meshes, one per node (n = E (N+1)^3) for warped meshes.
- * qt_r may be NULL (zero). */
+ * qt_r may be NULL (zero).  On the FP32 path with z periodic the reference
+ * state must repeat across the wrap (bottom and top levels equal, including
+ * rho e_r with its g z, so g = 0): otherwise CMLES_ERR_ARG. */
 cmles_status cmles_set_reference(cmles_handle h, const double *rho_r_host, const double *p_r_host,
                                  const double *qt_r_host, size_t n);
 

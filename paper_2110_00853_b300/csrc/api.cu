@@ -702,8 +702,6 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
   // warped (curvilinear) meshes run on the FP32 path
   if (mesh->warp && params->precision != CMLES_FP32_ACC64) return CMLES_ERR_ARG;
   if (params->precision != CMLES_FP64 && params->precision != CMLES_FP32_ACC64) return CMLES_ERR_ARG;
-  // the FP32 shadow is relative to a per-level reference: z must not wrap
-  if (params->precision == CMLES_FP32_ACC64 && mesh->periodic[2]) return CMLES_ERR_ARG;
   if (params->closure != CMLES_CLOSURE_NONE && params->closure != CMLES_CLOSURE_SL &&
       params->closure != CMLES_CLOSURE_MLP && params->closure != CMLES_CLOSURE_VREMAN)
     return CMLES_ERR_ARG;
@@ -985,6 +983,21 @@ cmles_status cmles_set_reference(cmles_handle h, const double *rho_r, const doub
     L[L_RVS] = (float)rhovsat64(h, Tr);
   }
   const int Nq = h->Nq;
+  // The FP32 shadow holds deviations from the reference of its node's level,
+  // and a face task takes the reference values of its own face node for the
+  // neighbour's node, which across an element face sits at the same height.
+  // Across a periodic wrap in z the two nodes are the bottom and the top
+  // level, so their reference states (including rho e_r with its g z) must
+  // be equal: a profile that repeats, as with g = 0.
+  if (h->fp32 && h->mesh.periodic[2]) {
+    const size_t top = nlev - 1;
+    auto differ = [](double a, double b) { return fabs(a - b) > 1e-12 * fmax(fabs(a), fabs(b)) + 1e-300; };
+    if (differ(rho_r[0], rho_r[top]) || differ(p_r[0], p_r[top]) || differ(qref[1], qref[top * 4 + 1]) ||
+        differ(qref[2], qref[top * 4 + 2]))
+      return fail(h, CMLES_ERR_ARG,
+                  "cmles_set_reference: periodic z on the FP32 path needs a reference state that repeats across "
+                  "the wrap (with g = 0)");
+  }
   for (int ez = 0; ez < h->mesh.nez; ++ez)
     for (int k = 0; k < Nq; ++k) {
       double dh = 0.0, dth = 0.0, dq = 0.0;
