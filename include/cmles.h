@@ -105,7 +105,7 @@ typedef struct {
                             Richardson factor multiplies SL and Vreman alike */
   double Cs, Prt;        /* Smagorinsky coefficient, turbulent Prandtl number (1/3) */
   int richardson;        /* apply the Richardson correction f_b (Eq. richardson) */
-  int moist;             /* saturation adjustment on (Sec. 2.6) */
+  int moist;             /* saturation adjustment on (Sec. 2.7) */
   double sponge_alpha, sponge_zs, sponge_gamma; /* Rayleigh sponge (App. A.2) */
   double u_relax[3];
   double lateral_sponge_frac;                   /* also damp within this fraction of Lx at both x ends */
@@ -151,6 +151,10 @@ typedef struct {
   int nonfinite;         /* 1 if the state holds a NaN or Inf */
   int satadj_failures;   /* Newton non-convergence count since the previous call */
   int tc_timeouts;       /* CTAs whose tensor-core completion wait gave up since the previous call */
+  int cold_saturated;    /* kernel threads (each counted at most once per launch) whose saturation
+                            adjustment left condensate below freezing (273.15 K) since the previous
+                            call.  Information, not an error: all condensate is kept liquid (no ice
+                            phase), and the status is not changed */
 } cmles_diag;
 
 /* Initial-state description for cmles_init_case (synthetic cases; inputs,

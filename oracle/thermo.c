@@ -9,7 +9,7 @@
 #include "oracle.h"
 
 /* Saturation vapour pressure over liquid from the Clausius-Clapeyron relation
- * integrated with constant heat capacities (Sec. 2.6 cites Romps 2008 for
+ * integrated with constant heat capacities (Sec. 2.7 cites Romps 2008 for
  * this closed form; values of p_tr, T_tr are a reading):
  *   p_v*(T) = p_tr (T/T_tr)^{(c_pv - c_pl)/R_v}
  *             exp[ (L_v0 - (c_pv - c_pl) T_0)/R_v (1/T_tr - 1/T) ],

@@ -48,7 +48,8 @@ class Params(C.Structure):
 
 class Diag(C.Structure):
     _fields_ = [("budget", C.c_double * 6), ("time", C.c_double), ("steps", C.c_longlong),
-                ("nonfinite", C.c_int), ("satadj_failures", C.c_int), ("tc_timeouts", C.c_int)]
+                ("nonfinite", C.c_int), ("satadj_failures", C.c_int), ("tc_timeouts", C.c_int),
+                ("cold_saturated", C.c_int)]
 
 
 class Case(C.Structure):
@@ -335,7 +336,8 @@ class Solver:
         if raise_on_error and st not in (0,):
             self._check(st)
         return dict(budget=np.array(d.budget[:]), time=d.time, steps=d.steps, nonfinite=bool(d.nonfinite),
-                    satadj_failures=d.satadj_failures, tc_timeouts=d.tc_timeouts, status=st)
+                    satadj_failures=d.satadj_failures, tc_timeouts=d.tc_timeouts,
+                    cold_saturated=d.cold_saturated, status=st)
 
     def profiles(self):
         out = np.zeros((self.nlev, 11))
@@ -508,7 +510,8 @@ class Group:
         if raise_on_error and st != 0:
             self._check(st)
         return dict(budget=np.array(d.budget[:]), time=d.time, steps=d.steps, nonfinite=bool(d.nonfinite),
-                    satadj_failures=d.satadj_failures, tc_timeouts=d.tc_timeouts, status=st)
+                    satadj_failures=d.satadj_failures, tc_timeouts=d.tc_timeouts,
+                    cold_saturated=d.cold_saturated, status=st)
 
     def halo_bytes(self):
         return self.L.cmles_group_halo_bytes(self.g)

@@ -1428,6 +1428,7 @@ cmles_status cmles_diagnostics(cmles_handle h, cmles_diag *out) {
   out->nonfinite = res[6] > 0.0 ? 1 : 0;
   out->satadj_failures = flags[0];
   out->tc_timeouts = flags[1];
+  out->cold_saturated = flags[2];
   out->time = h->time;
   out->steps = h->steps;
   if (out->nonfinite) return fail(h, CMLES_ERR_NONFINITE, "state holds non-finite values");

@@ -118,6 +118,19 @@ __device__ __forceinline__ int face_node(int d, int a, int t1, int t2) {
   return d == 0 ? a + Nq * (t1 + Nq * t2) : (d == 1 ? t1 + Nq * (a + Nq * t2) : t1 + Nq * (t2 + Nq * a));
 }
 
+// Freezing temperature (K).  The saturation adjustment keeps all condensate
+// liquid (the ice phase of Sec. 2.7 is not modelled), and a node that
+// condenses below it is counted, for information.
+constexpr double kTfreeze = 273.15;
+
+// Report a thread's thermodynamic flags (bit 0: the saturation adjustment did
+// not converge; bit 1: condensate below freezing) as counts in the device
+// flag words 0 and 2.
+__device__ __forceinline__ void report_thermo_flags(const KParams &P, int fail) {
+  if (fail & 1) atomicAdd(P.flags, 1);
+  if (fail & 2) atomicAdd(P.flags + 2, 1);
+}
+
 // Storage index of the element with (interior) coordinates (ex, ey, ez); on
 // a partition, -1 and nex (ney) are its ghost elements in x (y).
 __host__ __device__ __forceinline__ int storage_index(const KParams &P, int ex, int ey, int ez) {

@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
     }
     __syncthreads();
   }
-  if (fail) atomicAdd(P.flags, 1);
+  report_thermo_flags(P, fail);
 }
 
 // Shadow of an FP64 state on a curvilinear mesh (per-node reference offsets)
@@ -456,7 +456,7 @@ __global__ void k_shadow32c(const double *__restrict__ Q64, float *__restrict__ 
     load_node_table(P.node32, (size_t)e, node, L);
     thermo_store32(P, L, s, TH, (size_t)e, node, fail);
   }
-  if (fail) atomicAdd(P.flags, 1);
+  report_thermo_flags(P, fail);
 }
 
 cudaError_t launch_shadow32c(const double *Q64, float *S, float *TH, const KParams &P, int N, cudaStream_t s) {

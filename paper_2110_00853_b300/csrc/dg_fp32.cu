@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
     if (t < 6 && g + (int)gridDim.x < P.E) next_element(P, g + gridDim.x, sEl, sNb);
     __syncthreads();
   }
-  if (fail) atomicAdd(P.flags, 1);
+  report_thermo_flags(P, fail);
 }
 
 // Shadow of an FP64 state: s = (float)(Q - Q_ref(level)), subtraction in
@@ -468,7 +468,7 @@ __global__ void k_shadow32(const double *__restrict__ Q64, float *__restrict__ S
     }
     thermo_store32(P, P.lev32 + (size_t)(ez * Nq + k) * L_NF, s, TH, (size_t)e, node, fail);
   }
-  if (fail) atomicAdd(P.flags, 1);
+  report_thermo_flags(P, fail);
 }
 
 cudaError_t launch_shadow32(const double *Q64, float *S, float *TH, const KParams &P, int N, cudaStream_t s) {

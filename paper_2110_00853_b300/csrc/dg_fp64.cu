@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(block64(N)) k_rhs64(const double *__restrict__
     }
     __syncthreads();
   }
-  if (fail) atomicAdd(P.flags, 1);
+  report_thermo_flags(P, fail);
 }
 
 // The thermodynamic fields of a given state Q (one thread per node).
@@ -456,7 +456,7 @@ __global__ void k_thermo64(const double *__restrict__ Q, double *__restrict__ TH
     for (int v = 0; v < 6; ++v) Y[v] = Q[(e * 6 + v) * Np + node];
     thermo_store64(P, Y, node_z(P, ez, k), ez * Nq + k, TH, (size_t)e, node, Np, fail);
   }
-  if (fail) atomicAdd(P.flags, 1);
+  report_thermo_flags(P, fail);
 }
 
 // ------------------------------------------------------------------ launchers

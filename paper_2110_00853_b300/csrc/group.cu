@@ -581,6 +581,7 @@ cmles_status cmles_group_diagnostics(cmles_group g, cmles_diag *out) {
     nonfinite += res[6];
     out->satadj_failures += flags[0];
     out->tc_timeouts += flags[1];
+    out->cold_saturated += flags[2];
     out->time = h->time;
     out->steps = h->steps;
   }

@@ -10,7 +10,7 @@ struct Th64 {
 };
 
 // Saturation vapour pressure over liquid, integrated Clausius-Clapeyron with
-// constant heat capacities (Sec. 2.6):
+// constant heat capacities (Sec. 2.7):
 //   p_v* = p_tr (T/T_tr)^a exp(b (1/T_tr - 1/T)), a = (c_pv - c_pl)/R_v,
 //   b = (L_v0 - (c_pv - c_pl) T_0)/R_v, evaluated as one exp of a log-sum.
 __device__ __forceinline__ double pvsat64(const KParams &P, double T) {
@@ -83,9 +83,11 @@ __device__ __forceinline__ void thermo64(const KParams &P, const double Y[6], do
           break;
         }
       }
-      if (!conv) fail = 1;
+      if (!conv) fail |= 1;
       ql = q - pvsat64(P, T) / (rRv * T);
       if (ql < 0.0) ql = 0.0;
+      // condensate below freezing: kept liquid (no ice phase), counted
+      if (ql > 0.0 && T < kTfreeze) fail |= 2;
     }
   }
   const double qv = q - ql;

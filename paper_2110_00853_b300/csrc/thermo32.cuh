@@ -89,7 +89,7 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
           break;
         }
       }
-      if (!conv) fail = 1;
+      if (!conv) fail |= 1;
       T = Tr + Tp;
       rhoqv = rhovsat32(F, T);
       rhoql = rhoq - rhoqv;
@@ -98,6 +98,8 @@ __device__ __forceinline__ void thermo32(const KParams &P, const float *__restri
         rhoql = 0.0f;
         rhoqv = rhoq;
         drqv = qp;
+      } else if (T < (float)kTfreeze) {
+        fail |= 2;  // condensate below freezing: kept liquid (no ice phase), counted
       }
     }
   }

@@ -151,3 +151,36 @@ def test_tensor_core_drain_after_a_wait_gives_up(orc):
         assert np.array_equal(R2, R0)
     with pytest.raises(cmles.CmlesError):
         G.test_stall_tc(3)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_condensate_below_freezing_is_counted_not_an_error(orc, precision):
+    """The saturation adjustment keeps all condensate liquid (no ice phase).
+    A node that condenses below 273.15 K is counted in cold_saturated, for
+    information; the status stays CMLES_OK.  The stratified throughput box
+    saturates only near its lid (the oracle's q_l > 0 nodes there are all
+    colder than 202 K); the moist layer saturates only where it is warmer
+    than 283 K, and counts nothing.  Both a tendency call and a step report
+    (on the FP32 path the shadow kernel and the flux pass each count)."""
+    from paper_2110_00853_b300 import cmles
+    for name, dims, cold in (("c5", (2, 2, 80), True), ("c2", (3, 3, 16), False)):
+        m = I.sub_mesh(name, *dims)
+        ph = I.physics(name)
+        S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case(name))
+        S.rhs(Q)
+        aux = S.intermediates()["aux"]
+        sat = aux[:, 3] > 0
+        assert sat.sum() > 1000
+        T = aux[:, 2][sat]
+        assert (T.max() < 273.15 - 50.0) if cold else (T.min() > 273.15 + 10.0)
+        G = cmles.Solver(m, ph, precision=precision)
+        G.set_reference(_levels(rr, m), _levels(pr, m), _levels(Q[:, 5] / Q[:, 0], m))
+        G.tendency(torch.from_numpy(Q).cuda())
+        d = G.diagnostics(raise_on_error=False)
+        assert d["status"] == 0 and d["satadj_failures"] == 0
+        assert (d["cold_saturated"] > 0) == cold, (name, d["cold_saturated"])
+        G.set_state(torch.from_numpy(Q).cuda())
+        G.step(1)
+        d = G.diagnostics(raise_on_error=False)
+        assert d["status"] == 0 and (d["cold_saturated"] > 0) == cold, (name, d["cold_saturated"])
+        assert G.diagnostics(raise_on_error=False)["cold_saturated"] == 0    # cleared by the report
