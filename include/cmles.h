@@ -236,6 +236,23 @@ cmles_status cmles_get_state_host(cmles_handle h, double *Q_host);
 cmles_status cmles_stage_state_host(cmles_handle h, const double *Q_host);
 cmles_status cmles_commit_staged_state(cmles_handle h);
 
+/* Asynchronous download of the state, the counterpart of the staged upload.
+ * cmles_fetch_state_host starts copying the handle's current state (after
+ * the work already queued on the handle's stream) into Q_host (same layout;
+ * pinned memory for full speed) on an internal copy stream, in 32 chunks,
+ * and returns at once; cmles_wait_fetch blocks until the latest download
+ * has completed (at once if there is none).  Q_host must not be read or
+ * changed by the caller before cmles_wait_fetch returns.  A
+ * cmles_stage_state_host of the same host buffer that follows uploads each
+ * chunk as soon as it has arrived, so that the two directions of a host
+ * round trip overlap on the bus; cmles_set_state_host and
+ * cmles_get_state_host of that buffer wait for the whole download.  Calls
+ * that change a state buffer (set_state, set_state_host, commit, init_case,
+ * step, filter) are ordered after the download on the device, without
+ * blocking the host.  Errors: CMLES_ERR_ARG, CMLES_ERR_CUDA. */
+cmles_status cmles_fetch_state_host(cmles_handle h, double *Q_host);
+cmles_status cmles_wait_fetch(cmles_handle h);
+
 /* RHS of Eq. matrixProblem for the state Q (device, FP64) into RHS (device,
  * FP64, same layout), in the handle's precision.  The handle's own state is
  * left unchanged. */

@@ -109,6 +109,8 @@ def load(path=LIB_PATH):
     L.cmles_test_stall_tc.argtypes = [_H, C.c_int]
     L.cmles_stage_state_host.argtypes = [_H, _VP]
     L.cmles_commit_staged_state.argtypes = [_H]
+    L.cmles_fetch_state_host.argtypes = [_H, _VP]
+    L.cmles_wait_fetch.argtypes = [_H]
     L.cmles_hevi_operator.argtypes = [_H, _VP, _VP]
     L.cmles_hevi_solve.argtypes = [_H, _VP, _VP]
     L.cmles_spectrum.argtypes = [_H, C.c_int, _DP]
@@ -310,6 +312,18 @@ class Solver:
     def commit_staged_state(self):
         """Take the staged state as the state (the handle's stream waits for the copy)."""
         self._check(self.L.cmles_commit_staged_state(self.h))
+
+    def fetch_state_host(self, out):
+        """Start copying the state into the pinned host tensor `out`
+        (asynchronous; read `out` only after wait_fetch)."""
+        assert not out.is_cuda and out.dtype == self.torch.float64 and out.is_contiguous()
+        assert out.numel() == self.E * 6 * self.Np
+        self._fetch_host = out
+        self._check(self.L.cmles_fetch_state_host(self.h, C.c_void_p(out.data_ptr())))
+
+    def wait_fetch(self):
+        """Block until the latest fetch_state_host copy has completed."""
+        self._check(self.L.cmles_wait_fetch(self.h))
 
     def get_state_host(self, out=None):
         if out is None:

@@ -545,6 +545,23 @@ cmles_status curved_reference(cmles_handle h, const double *rho_r, const double 
 
 using namespace cmles_host;
 
+// Order the handle's stream after the latest asynchronous host download, so
+// that work that writes a state buffer cannot overwrite one it still reads
+// (a wait on the device; the host does not block).
+static cmles_status order_after_fetch(cmles_handle h) {
+  if (h->fetch_unordered) {
+    CK(cudaStreamWaitEvent(h->stream, h->fetch_done_ev, 0));
+    h->fetch_unordered = false;
+  }
+  return CMLES_OK;
+}
+
+// Element range [lo, hi) of chunk i of a state of n doubles.
+static void fetch_chunk(size_t n, int i, size_t &lo, size_t &hi) {
+  lo = n * (size_t)i / kFetchChunks;
+  hi = n * (size_t)(i + 1) / kFetchChunks;
+}
+
 extern "C" {
 
 void cmles_default_params(cmles_params *p) {
@@ -874,6 +891,7 @@ cmles_status cmles_create(const cmles_mesh *mesh, const cmles_params *params, cm
 
 cmles_status cmles_destroy(cmles_handle h) {
   if (!h) return CMLES_ERR_ARG;
+  if (h->d2h_stream) cudaStreamSynchronize(h->d2h_stream);  // a download still writing host memory
   for (auto &t : h->timed) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
@@ -889,6 +907,13 @@ cmles_status cmles_destroy(cmles_handle h) {
     if (b) cudaFree(b);
   if (h->hv_tab) cudaFree(h->hv_tab);
   if (h->Qstage) cudaFree(h->Qstage);
+  if (h->d2h_stream) {
+    for (cudaEvent_t ev : h->fetch_ev)
+      if (ev) cudaEventDestroy(ev);
+    if (h->fetch_start_ev) cudaEventDestroy(h->fetch_start_ev);
+    if (h->fetch_done_ev) cudaEventDestroy(h->fetch_done_ev);
+    cudaStreamDestroy(h->d2h_stream);
+  }
   if (h->staged_ev) cudaEventDestroy(h->staged_ev);
   if (h->compute_ev) cudaEventDestroy(h->compute_ev);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
@@ -1023,6 +1048,10 @@ cmles_status cmles_set_reference(cmles_handle h, const double *rho_r, const doub
 
 cmles_status cmles_init_case(cmles_handle h, const cmles_case *c) {
   if (!h || !c) return fail(h, CMLES_ERR_ARG, "cmles_init_case: null argument");
+  {
+    cmles_status st = order_after_fetch(h);
+    if (st != CMLES_OK) return st;
+  }
   if (h->curved) {
     // flow over the terrain (case 3): dry, constant Brunt-Vaisala frequency
     // (Eqs. pressure_hs_brunt and the ideal gas law), uniform velocity u0
@@ -1173,8 +1202,50 @@ cmles_status cmles_init_case(cmles_handle h, const cmles_case *c) {
   return CMLES_OK;
 }
 
+cmles_status cmles_fetch_state_host(cmles_handle h, double *Q_host) {
+  if (!h || !Q_host) return fail(h, CMLES_ERR_ARG, "cmles_fetch_state_host: null argument");
+  if (!h->d2h_stream) {
+    CK(cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t &ev : h->fetch_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->fetch_start_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->fetch_done_ev, cudaEventDisableTiming));
+  }
+  // after the work queued on the handle's stream, and after an uncommitted
+  // staged upload, which may still be reading this host buffer
+  CK(cudaEventRecord(h->fetch_start_ev, h->stream));
+  CK(cudaStreamWaitEvent(h->d2h_stream, h->fetch_start_ev, 0));
+  if (h->staged) CK(cudaStreamWaitEvent(h->d2h_stream, h->staged_ev, 0));
+  const double *src = h->Q[h->cur];
+  const size_t n = (size_t)h->nodes * 6;
+  for (int i = 0; i < kFetchChunks; ++i) {
+    size_t lo, hi;
+    fetch_chunk(n, i, lo, hi);
+    if (hi > lo)
+      CK(cudaMemcpyAsync(Q_host + lo, src + lo, (hi - lo) * sizeof(double), cudaMemcpyDeviceToHost, h->d2h_stream));
+    CK(cudaEventRecord(h->fetch_ev[i], h->d2h_stream));
+  }
+  CK(cudaEventRecord(h->fetch_done_ev, h->d2h_stream));
+  h->fetch_src = src;
+  h->fetch_host = Q_host;
+  h->fetch_pending = true;
+  h->fetch_unordered = true;
+  return CMLES_OK;
+}
+
+cmles_status cmles_wait_fetch(cmles_handle h) {
+  if (!h) return CMLES_ERR_ARG;
+  if (!h->fetch_pending) return CMLES_OK;
+  CK(cudaEventSynchronize(h->fetch_done_ev));
+  h->fetch_pending = false;
+  return CMLES_OK;
+}
+
 cmles_status cmles_set_state(cmles_handle h, const double *Q_dev) {
   if (!h || !Q_dev) return fail(h, CMLES_ERR_ARG, "cmles_set_state: null argument");
+  {
+    cmles_status st = order_after_fetch(h);
+    if (st != CMLES_OK) return st;
+  }
   CK(cudaMemcpyAsync(h->Q[h->cur], Q_dev, (size_t)h->nodes * 6 * sizeof(double), cudaMemcpyDeviceToDevice,
                      h->stream));
   h->shadow_valid = false;
@@ -1190,6 +1261,12 @@ cmles_status cmles_get_state(cmles_handle h, double *Q_dev) {
 
 cmles_status cmles_set_state_host(cmles_handle h, const double *Q_host) {
   if (!h || !Q_host) return fail(h, CMLES_ERR_ARG, "cmles_set_state_host: null argument");
+  {
+    cmles_status st = order_after_fetch(h);
+    if (st != CMLES_OK) return st;
+  }
+  // a download into this host buffer completes before it is read
+  if (h->fetch_pending && h->fetch_host == Q_host) CK(cudaStreamWaitEvent(h->stream, h->fetch_done_ev, 0));
   CK(cudaMemcpyAsync(h->Q[h->cur], Q_host, (size_t)h->nodes * 6 * sizeof(double), cudaMemcpyHostToDevice,
                      h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1210,8 +1287,26 @@ cmles_status cmles_stage_state_host(cmles_handle h, const double *Q_host) {
   // handle's stream: the copy waits for that work, not for later launches
   CK(cudaEventRecord(h->compute_ev, h->stream));
   CK(cudaStreamWaitEvent(h->copy_stream, h->compute_ev, 0));
-  CK(cudaMemcpyAsync(h->Qstage, Q_host, (size_t)h->nodes * 6 * sizeof(double), cudaMemcpyHostToDevice,
-                     h->copy_stream));
+  // ... and for a host download still reading the staging buffer (the state
+  // before a commit)
+  if (h->fetch_unordered && h->fetch_src == h->Qstage) CK(cudaStreamWaitEvent(h->copy_stream, h->fetch_done_ev, 0));
+  const size_t n = (size_t)h->nodes * 6;
+  if (h->fetch_pending && h->fetch_host == Q_host) {
+    // the host buffer is being written by the latest download: upload each
+    // chunk as soon as it has arrived, so that the two directions overlap
+    for (int i = 0; i < kFetchChunks; ++i) {
+      size_t lo, hi;
+      fetch_chunk(n, i, lo, hi);
+      CK(cudaStreamWaitEvent(h->copy_stream, h->fetch_ev[i], 0));
+      if (hi > lo)
+        CK(cudaMemcpyAsync(h->Qstage + lo, Q_host + lo, (hi - lo) * sizeof(double), cudaMemcpyHostToDevice,
+                           h->copy_stream));
+    }
+  } else {
+    // an earlier download into this buffer has completed before the latest one
+    if (h->fetch_pending) CK(cudaStreamWaitEvent(h->copy_stream, h->fetch_done_ev, 0));
+    CK(cudaMemcpyAsync(h->Qstage, Q_host, n * sizeof(double), cudaMemcpyHostToDevice, h->copy_stream));
+  }
   CK(cudaEventRecord(h->staged_ev, h->copy_stream));
   h->staged = true;
   return CMLES_OK;
@@ -1220,6 +1315,10 @@ cmles_status cmles_stage_state_host(cmles_handle h, const double *Q_host) {
 cmles_status cmles_commit_staged_state(cmles_handle h) {
   if (!h) return CMLES_ERR_ARG;
   if (!h->staged) return fail(h, CMLES_ERR_STATE, "cmles_commit_staged_state: nothing staged");
+  {
+    cmles_status st = order_after_fetch(h);
+    if (st != CMLES_OK) return st;
+  }
   CK(cudaStreamWaitEvent(h->stream, h->staged_ev, 0));
   std::swap(h->Q[h->cur], h->Qstage);
   h->staged = false;
@@ -1229,6 +1328,8 @@ cmles_status cmles_commit_staged_state(cmles_handle h) {
 
 cmles_status cmles_get_state_host(cmles_handle h, double *Q_host) {
   if (!h || !Q_host) return fail(h, CMLES_ERR_ARG, "cmles_get_state_host: null argument");
+  // a download into this host buffer lands first
+  if (h->fetch_pending && h->fetch_host == Q_host) CK(cudaStreamWaitEvent(h->stream, h->fetch_done_ev, 0));
   CK(cudaMemcpyAsync(Q_host, h->Q[h->cur], (size_t)h->nodes * 6 * sizeof(double), cudaMemcpyDeviceToHost,
                      h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1362,6 +1463,10 @@ cmles_status cmles_step(cmles_handle h, int nsteps) {
   if (h->prm.closure == CMLES_CLOSURE_MLP && !h->have_mlp)
     return fail(h, CMLES_ERR_STATE, "cmles_step: closure weights not set");
   {
+    cmles_status st = order_after_fetch(h);
+    if (st != CMLES_OK) return st;
+  }
+  {
     cmles_status st = ensure_shadow(h);
     if (st != CMLES_OK) return st;
   }
@@ -1407,6 +1512,10 @@ cmles_status cmles_step(cmles_handle h, int nsteps) {
 cmles_status cmles_filter(cmles_handle h) {
   if (!h) return CMLES_ERR_ARG;
   if (h->prm.filter_order <= 0) return fail(h, CMLES_ERR_ARG, "cmles_filter: filter_order is 0");
+  {
+    cmles_status st = order_after_fetch(h);
+    if (st != CMLES_OK) return st;
+  }
   return apply_expfilter(h);
 }
 

@@ -15,6 +15,10 @@
 
 using namespace cmles;
 
+// Chunks of an asynchronous host download (about 380 MB each for the 12 GB
+// state of the 256M-node box: an upload that follows it lags by one chunk).
+constexpr int kFetchChunks = 32;
+
 struct TimedLaunch {
   int kind;
   cudaEvent_t a, b;
@@ -64,6 +68,16 @@ struct cmles_t {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t staged_ev = nullptr, compute_ev = nullptr;
   bool staged = false;
+  // asynchronous host downloads (cmles_fetch_state_host): chunked copies on
+  // their own stream with one event per chunk, so that an upload of the same
+  // host buffer can follow chunk by chunk
+  cudaStream_t d2h_stream = nullptr;
+  cudaEvent_t fetch_ev[kFetchChunks] = {};
+  cudaEvent_t fetch_start_ev = nullptr, fetch_done_ev = nullptr;
+  const double *fetch_src = nullptr;  // device buffer read by the latest download
+  const double *fetch_host = nullptr; // host buffer it writes
+  bool fetch_pending = false;         // issued and not yet waited for (cmles_wait_fetch)
+  bool fetch_unordered = false;       // the handle's stream is not yet ordered after it
   double time = 0.0;
   bool timing = false;
   std::vector<TimedLaunch> timed;

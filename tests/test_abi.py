@@ -93,3 +93,9 @@ def test_create_order_limits_without_gpu_work():
     assert status(5, integrator="ark2_hevi") == 1
     assert status(3, "fp32", warp=True) == 1
     assert status(3, integrator="ark2_hevi") == 1
+
+
+def test_host_download_calls_reject_a_null_handle_without_gpu_work():
+    L = cmles.load()
+    assert L.cmles_fetch_state_host(None, None) == 1    # CMLES_ERR_ARG
+    assert L.cmles_wait_fetch(None) == 1
