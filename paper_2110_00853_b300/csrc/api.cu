@@ -710,9 +710,10 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
   if (!mesh || !params || !out) return CMLES_ERR_ARG;
   *out = nullptr;
   // the kernels are instantiated for the orders 1 .. 7 on flat meshes in
-  // FP64, 1 .. 4 on flat meshes in FP32, and 4 on warped meshes and for HEVI
+  // both precisions, with the learned closure (one 128-row tensor-core tile
+  // per element) for 1 .. 4, and for 4 on warped meshes and for HEVI
   if (mesh->N < 1 || mesh->N > 7) return CMLES_ERR_ARG;
-  if (params->precision == CMLES_FP32_ACC64 && mesh->N > 4) return CMLES_ERR_ARG;
+  if (params->closure == CMLES_CLOSURE_MLP && mesh->N > 4) return CMLES_ERR_ARG;
   if ((mesh->warp || params->integrator == CMLES_ARK2_HEVI) && mesh->N != 4) return CMLES_ERR_ARG;
   if (mesh->nex < 1 || mesh->ney < 1 || mesh->nez < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0))
     return CMLES_ERR_MESH;
@@ -776,7 +777,7 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
     ALLOC(h->TH64[0], (size_t)h->snodes * 4 * sizeof(double));
     ALLOC(h->TH64[1], (size_t)h->snodes * 4 * sizeof(double));
   } else {
-    const size_t n32 = (size_t)Es * 128;  // padded nodes
+    const size_t n32 = (size_t)Es * np32(mesh->N);  // padded nodes
     ALLOC(h->S32[0], n32 * 6 * sizeof(float));
     ALLOC(h->S32[1], n32 * 6 * sizeof(float));
     ALLOC(h->dQ32, n32 * 6 * sizeof(float));
@@ -856,7 +857,7 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
   if (e == cudaSuccess) e = cudaMemset(h->exr, 0, nlev * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(h->mlp_dev, 0, sizeof(MlpPacked));
   if (e == cudaSuccess && h->dQ) e = cudaMemset(h->dQ, 0, n6 * sizeof(double));
-  if (e == cudaSuccess && h->dQ32) e = cudaMemset(h->dQ32, 0, (size_t)Es * 128 * 6 * sizeof(float));
+  if (e == cudaSuccess && h->dQ32) e = cudaMemset(h->dQ32, 0, (size_t)Es * np32(mesh->N) * 6 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(h->Q[0], 0, n6 * sizeof(double));
   if (e != cudaSuccess) {
     cmles_destroy(h);

@@ -131,6 +131,13 @@ __device__ __forceinline__ void report_thermo_flags(const KParams &P, int fail) 
   if (fail & 2) atomicAdd(P.flags + 2, 1);
 }
 
+// Padded nodes per element of the FP32 arrays at order N: 128 up to N = 4
+// (one node per thread of a 128-thread CTA), above it (N+1)^3 rounded up to
+// a whole warp (224, 352, 512), the CTA size of those orders.
+__host__ __device__ constexpr int np32(int N) {
+  return (N + 1) * (N + 1) * (N + 1) <= 128 ? 128 : ((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32;
+}
+
 // Storage index of the element with (interior) coordinates (ex, ey, ez); on
 // a partition, -1 and nex (ney) are its ghost elements in x (y).
 __host__ __device__ __forceinline__ int storage_index(const KParams &P, int ex, int ey, int ez) {

@@ -101,21 +101,23 @@ __device__ __forceinline__ void eddy_nu(const float (&gr)[6][3], float CsDelta2,
 // The diffusive flux F2 of node t (Eqs. stress_tensor, diff_moisture_flux,
 // diff_energy_flux; in deviation form) along x, y and z: -rho D_t dq/dx_d for the water, the subgrid stress
 // tau_dj = -2 rho nu_t S_dj plus the water's momentum, and the energy's
-// -rho D_t dh/dx_d + tau_dj u_j.  Planes d * 5 + c of the element's 15.
+// -rho D_t dh/dx_d + tau_dj u_j.  Planes d * 5 + c of the element's 15, np
+// padded nodes each.
 __device__ __forceinline__ void write_f2(float *__restrict__ F2, size_t e, int t, float rho, float nut, float Dt,
-                                         const float (&gr)[6][3], const float (&sv)[6], const float (&G)[6]) {
+                                         const float (&gr)[6][3], const float (&sv)[6], const float (&G)[6],
+                                         int np = kNP) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const float di = -Dt * gr[4][d];
     float rt[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) rt[b] = -2.0f * rho * nut * (0.5f * (gr[d][b] + gr[b][d]));
-    float *o = F2 + (e * 15 + d * 5) * kNP + t;
+    float *o = F2 + (e * 15 + d * 5) * np + t;
     o[0] = rho * di;
-    o[1 * kNP] = rt[0] + di * sv[1];
-    o[2 * kNP] = rt[1] + di * sv[2];
-    o[3 * kNP] = rt[2] + di * sv[3];
-    o[4 * kNP] = -rho * Dt * gr[3][d] + (rt[0] * G[0] + rt[1] * G[1] + rt[2] * G[2]);
+    o[1 * np] = rt[0] + di * sv[1];
+    o[2 * np] = rt[1] + di * sv[2];
+    o[3 * np] = rt[2] + di * sv[3];
+    o[4 * np] = -rho * Dt * gr[3][d] + (rt[0] * G[0] + rt[1] * G[1] + rt[2] * G[2]);
   }
 }
 
@@ -126,12 +128,12 @@ __device__ __forceinline__ void write_f2(float *__restrict__ F2, size_t e, int t
 // flight: face_load gathers the seven values (rho', rho u, rho v, rho w,
 // rho q_t', h', theta_v'), face_finish forms the fields.
 __device__ __forceinline__ void face_load(const float *__restrict__ S, const float *__restrict__ TH, size_t nb, int nn,
-                                          float (&raw)[7]) {
+                                          float (&raw)[7], int np = kNP) {
 #pragma unroll
-  for (int v = 0; v < 4; ++v) raw[v] = S[(nb * 6 + v) * kNP + nn];
-  raw[4] = S[(nb * 6 + 5) * kNP + nn];
-  raw[5] = TH[(nb * 4 + 2) * kNP + nn];
-  raw[6] = TH[(nb * 4 + 3) * kNP + nn];
+  for (int v = 0; v < 4; ++v) raw[v] = S[(nb * 6 + v) * np + nn];
+  raw[4] = S[(nb * 6 + 5) * np + nn];
+  raw[5] = TH[(nb * 4 + 2) * np + nn];
+  raw[6] = TH[(nb * 4 + 3) * np + nn];
 }
 __device__ __forceinline__ void face_finish(const float (&raw)[7], float rho_r, float q_r, float (&gf)[6]) {
   const float rinv = fdiv(1.0f, rho_r + raw[0]);
@@ -168,14 +170,16 @@ __device__ __forceinline__ void momentum_sources(const float (&sv)[6], float rho
 
 // The update inputs of node t, loaded early so that their latency overlaps
 // the flux computation: the register dQ and the step's increment D (none in
-// the first stage, A = 0), and in the last stage the FP64 state.
+// the first stage, A = 0), and in the last stage the FP64 state.  Np: nodes
+// per element of the FP64 state, np: padded nodes per element of the FP32
+// arrays.
 template <int UPD>
 __device__ __forceinline__ void stage_inputs(const KParams &P, const StageCoef &sc, const float *__restrict__ dQ,
                                              const double *__restrict__ Q64, size_t e, int t, int Np, float (&dq0)[6],
-                                             float (&D0)[6], double (&q0)[6]) {
+                                             float (&D0)[6], double (&q0)[6], int np = kNP) {
 #pragma unroll
   for (int v = 0; v < 6; ++v) {
-    const size_t i32 = (e * 6 + v) * kNP + t;
+    const size_t i32 = (e * 6 + v) * np + t;
     dq0[v] = sc.first ? 0.f : dQ[i32];
     D0[v] = sc.first ? 0.f : P.D32[i32];
     if (UPD == 2) q0[v] = Q64[(e * 6 + v) * Np + t];
@@ -193,12 +197,13 @@ __device__ __forceinline__ void stage_update(const KParams &P, const StageCoef &
                                              const float (&dq0)[6], const float (&D0)[6], const double (&q0)[6],
                                              const float (&s_old)[6], const double *qr, int qs, float *__restrict__ dQ,
                                              double *__restrict__ Q64, float *__restrict__ Sout,
-                                             double *__restrict__ Rout, size_t e, int t, int Np, float (&sn)[6]) {
+                                             double *__restrict__ Rout, size_t e, int t, int Np, float (&sn)[6],
+                                             int np = kNP) {
 #pragma unroll
   for (int v = 0; v < 6; ++v) {
     const size_t i64 = (e * 6 + v) * Np + t;
     if (UPD) {
-      const size_t i32 = (e * 6 + v) * kNP + t;
+      const size_t i32 = (e * 6 + v) * np + t;
       const float dq = sc.Af * dq0[v] + sc.dtf * R[v];
       const float Bdq = sc.Bf * dq;
       if (UPD == 1) {

@@ -42,23 +42,26 @@ namespace cmles {
 // (tensor-core MLP on the velocity and theta_v gradients and Delta).
 // HOOK: the instance launched only under test hook 2 (cmles_test_stall_tc),
 // whose first MMA completion wait gives up at once.
+// One thread per node: NP = np32(N) threads per CTA (128 up to N = 4, then
+// (N+1)^3 rounded up to a warp), the FP32 arrays padded to NP nodes per
+// element.  The learned closure's row tile is one 128-thread CTA (N <= 4).
 template <int N, int CL, bool HOOK = false>
-__global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__restrict__ S, const float *__restrict__ TH,
-                                                                 float *__restrict__ F2, const KParams P) {
-  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
-  static_assert(Np <= kNP, "one node per thread");
+__global__ void __launch_bounds__(np32(N), N > 4 ? 1 : (CL == 2 ? 6 : 8))
+    k_grad32(const float *__restrict__ S, const float *__restrict__ TH, float *__restrict__ F2, const KParams P) {
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq, NP = np32(N);
+  static_assert(CL != 2 || NP == 128, "the learned closure takes one 128-row tile per element");
   // the gradient fields (own and neighbour face nodes) share their storage
   // with the closure network's A operand, which is written only after every
   // thread has finished its gradient
-  constexpr int kGBytes = (6 * kNP + 36 * Nf) * 4, kABytes = CL == 2 ? kTcAElems * 2 : 0;
+  constexpr int kGBytes = (6 * NP + 36 * Nf) * 4, kABytes = CL == 2 ? kTcAElems * 2 : 0;
   __shared__ float sD[Nq * Nq];
   __shared__ __align__(128) uint8_t sU[kGBytes > kABytes ? kGBytes : kABytes];
   __shared__ int sNb[6];
   __shared__ __align__(16) uint8_t sMlpRaw[CL == 2 ? sizeof(MlpTc) : 16];
   __shared__ __align__(8) uint64_t sBar[2];
   __shared__ uint32_t sSlot;
-  float(*sG)[kNP] = reinterpret_cast<float(*)[kNP]>(sU);
-  float(*sGf)[6][Nf] = reinterpret_cast<float(*)[6][Nf]>(sU + 6 * kNP * 4);
+  float(*sG)[NP] = reinterpret_cast<float(*)[NP]>(sU);
+  float(*sGf)[6][Nf] = reinterpret_cast<float(*)[6][Nf]>(sU + 6 * NP * 4);
   __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(sU);
   const KF &F = P.f;
   const int t = threadIdx.x;
@@ -80,30 +83,30 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
     const float *L = P.lev32 + (size_t)(ez * Nq + (k < Nq ? k : 0)) * L_NF;
     if (t < Np) {
 #pragma unroll
-      for (int v = 0; v < 6; ++v) sv[v] = S[((size_t)e * 6 + v) * kNP + t];
+      for (int v = 0; v < 6; ++v) sv[v] = S[((size_t)e * 6 + v) * NP + t];
       // h' and theta_v' come with the state (its producer ran the
       // thermodynamics); u and q' are formed here exactly as there
       const float rinv = fdiv(1.0f, L[L_RHO] + sv[0]);
       G[0] = sv[1] * rinv;
       G[1] = sv[2] * rinv;
       G[2] = sv[3] * rinv;
-      G[3] = TH[((size_t)e * 4 + 2) * kNP + t];
+      G[3] = TH[((size_t)e * 4 + 2) * NP + t];
       G[4] = (sv[5] - L[L_QM] * sv[0]) * rinv;
-      G[5] = TH[((size_t)e * 4 + 3) * kNP + t];
+      G[5] = TH[((size_t)e * 4 + 3) * NP + t];
 #pragma unroll
       for (int v = 0; v < 6; ++v) sG[v][t] = G[v];
     }
     __syncthreads();
     {
-      // the 6 Nf face nodes, at most two per thread (task t and t + 128),
+      // the 6 Nf face nodes, at most two per thread (task t and t + NP),
       // with the loads of both in flight before either is finished
-      static_assert(6 * Nf <= 256, "two face nodes per thread at most");
+      static_assert(6 * Nf <= 2 * NP, "two face nodes per thread at most");
       float ra[7], rb[7];
-      const int tb = t + 128;
+      const int tb = t + NP;
       auto load = [&](int task, float (&raw)[7]) {
         const int f = task / Nf, fn = task - f * Nf;
         const int nb = sNb[f];
-        if (nb >= 0) face_load(S, TH, nb, face_node<Nq>(f >> 1, (f & 1) ? 0 : N, fn % Nq, fn / Nq), raw);
+        if (nb >= 0) face_load(S, TH, nb, face_node<Nq>(f >> 1, (f & 1) ? 0 : N, fn % Nq, fn / Nq), raw, NP);
       };
       auto finish = [&](int task, const float (&raw)[7]) {
         const int f = task / Nf, fn = task - f * Nf;
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
     }
     // the learned closure on the tensor cores, row t = node t
     if (CL == 2) learned_nu<HOOK>(W, sA, tcs, gr, F.Delta, t < Np, nut, Dt);
-    if (t < Np) write_f2(F2, e, t, L[L_RHO] + sv[0], nut, Dt, gr, sv, G);
+    if (t < Np) write_f2(F2, e, t, L[L_RHO] + sv[0], nut, Dt, gr, sv, G, NP);
     if (t < 6 && g + (int)gridDim.x < P.E) next_element(P, g + gridDim.x, sEl, sNb);
     __syncthreads();
   }
@@ -187,18 +190,28 @@ __global__ void __launch_bounds__(128, CL == 2 ? 6 : 8) k_grad32(const float *__
 // 2 last stage of the step, Q = Q_step_start + D added in FP64 and the shadow
 // rewritten from it.  With UPD 1 and 2 the new shadow's thermodynamic fields
 // go to THout.  p' and c of the input state come from TH.  FL: numerical
-// flux of F1, 0 Rusanov, 1 HLLC, 2 Roe.
+// flux of F1, 0 Rusanov, 1 HLLC, 2 Roe.  One thread per node, NP = np32(N)
+// threads per CTA.
+// The flux pass's 27 node planes (total fluxes, state, velocity) take
+// 27 * 4 * np32(N) bytes of shared memory: static up to N = 6, dynamic at
+// N = 7 (55 KB, beyond the 48 KB of static shared memory).
+__host__ __device__ constexpr int rhs32_dyn_bytes(int N) { return 27 * 4 * np32(N) > 40 * 1024 ? 27 * 4 * np32(N) : 0; }
+
 template <int N, int UPD, int FL>
-__global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__restrict__ S, const float *__restrict__ F2,
-                                                  const float *__restrict__ TH, float *__restrict__ dQ,
-                                                  double *__restrict__ Q64, float *__restrict__ Sout,
-                                                  float *__restrict__ THout, double *__restrict__ Rout,
-                                                  const StageCoef sc, const KParams P) {
-  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
+__global__ void __launch_bounds__(np32(N), N > 4 ? 1 : (FL == 0 ? 7 : 6))
+    k_rhs32(const float *__restrict__ S, const float *__restrict__ F2, const float *__restrict__ TH,
+            float *__restrict__ dQ, double *__restrict__ Q64, float *__restrict__ Sout, float *__restrict__ THout,
+            double *__restrict__ Rout, const StageCoef sc, const KParams P) {
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq, NP = np32(N);
+  constexpr bool DYN = rhs32_dyn_bytes(N) > 0;
   __shared__ float sD[Nq * Nq];
-  __shared__ float sF[6][3][kNP];
-  __shared__ float sS[6][kNP];
-  __shared__ float sU[3][kNP];
+  __shared__ float sFst[DYN ? 1 : 18 * NP];
+  __shared__ float sSst[DYN ? 1 : 6 * NP];
+  __shared__ float sUst[DYN ? 1 : 3 * NP];
+  extern __shared__ __align__(16) float sDyn32[];
+  float(*sF)[3][NP] = reinterpret_cast<float(*)[3][NP]>(DYN ? sDyn32 : sFst);
+  float(*sS)[NP] = reinterpret_cast<float(*)[NP]>(DYN ? sDyn32 + 18 * NP : sSst);
+  float(*sU)[NP] = reinterpret_cast<float(*)[NP]>(DYN ? sDyn32 + 24 * NP : sUst);
   __shared__ float sLf[6][6][Nf];
   __shared__ int sNb[6];
   // the drag law's C_d |u_p| u_p of the bottom face nodes, from the nodes of
@@ -222,26 +235,26 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
     // and starts the step: no register or increment to read)
     float dq0[6], D0[6];
     double q0[6];
-    if (UPD && t < Np) stage_inputs<UPD>(P, sc, dQ, Q64, e, t, Np, dq0, D0, q0);
+    if (UPD && t < Np) stage_inputs<UPD>(P, sc, dQ, Q64, e, t, Np, dq0, D0, q0, NP);
     if (t < Np) {
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
-        sv[v] = S[((size_t)e * 6 + v) * kNP + t];
+        sv[v] = S[((size_t)e * 6 + v) * NP + t];
         sS[v][t] = sv[v];
       }
-      const float pp = TH[((size_t)e * 4) * kNP + t];
+      const float pp = TH[((size_t)e * 4) * NP + t];
       const float rho = L[L_RHO] + sv[0];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         float f[6];
         flux1_dev32(sv, L[L_RHO], L[L_RHOQ], pp, d, f);
-        const float *g2 = F2 + ((size_t)e * 15 + d * 5) * kNP + t;
+        const float *g2 = F2 + ((size_t)e * 15 + d * 5) * NP + t;
         const float c0 = g2[0];
         sF[0][d][t] = f[0] + c0;
-        sF[1][d][t] = f[1] + g2[1 * kNP];
-        sF[2][d][t] = f[2] + g2[2 * kNP];
-        sF[3][d][t] = f[3] + g2[3 * kNP];
-        sF[4][d][t] = f[4] + g2[4 * kNP];
+        sF[1][d][t] = f[1] + g2[1 * NP];
+        sF[2][d][t] = f[2] + g2[2 * NP];
+        sF[3][d][t] = f[3] + g2[3 * NP];
+        sF[4][d][t] = f[4] + g2[4 * NP];
         sF[5][d][t] = f[5] + c0;
         sU[d][t] = fdiv(sv[1 + d], rho);
       }
@@ -264,7 +277,7 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
       float sm[6], sp[6];
 #pragma unroll
       for (int v = 0; v < 6; ++v) sm[v] = sS[v][n];
-      const float cm = TH[((size_t)e * 4 + 1) * kNP + n];
+      const float cm = TH[((size_t)e * 4 + 1) * NP + n];
       const int nb = sNb[f];
       if (FL == 0 && nb >= 0) {
         // Rusanov across an interior face.  The own node's total normal flux
@@ -273,17 +286,17 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
         // the neighbour's F1 is evaluated here (1 % of the pass).
         const int nn = face_node<Nq>(d, N - a, t1, t2);
 #pragma unroll
-        for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
-        const float pp = TH[((size_t)nb * 4) * kNP + nn];
-        const float cp = TH[((size_t)nb * 4 + 1) * kNP + nn];
-        const float *g2p = F2 + ((size_t)nb * 15 + d * 5) * kNP + nn;
+        for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * NP + nn];
+        const float pp = TH[((size_t)nb * 4) * NP + nn];
+        const float cp = TH[((size_t)nb * 4 + 1) * NP + nn];
+        const float *g2p = F2 + ((size_t)nb * 15 + d * 5) * NP + nn;
         float fp[6];
         flux1_dev32(sp, rho_r, rhoq_r, pp, d, fp);
         fp[0] += g2p[0];
-        fp[1] += g2p[1 * kNP];
-        fp[2] += g2p[2 * kNP];
-        fp[3] += g2p[3 * kNP];
-        fp[4] += g2p[4 * kNP];
+        fp[1] += g2p[1 * NP];
+        fp[2] += g2p[2 * NP];
+        fp[3] += g2p[3 * NP];
+        fp[4] += g2p[4 * NP];
         fp[5] += g2p[0];
         const float smd = d == 0 ? sm[1] : (d == 1 ? sm[2] : sm[3]);
         const float spd = d == 0 ? sp[1] : (d == 1 ? sp[2] : sp[3]);
@@ -298,18 +311,18 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
         }
         continue;
       }
-      const float pm = TH[((size_t)e * 4) * kNP + n];
+      const float pm = TH[((size_t)e * 4) * NP + n];
       float pp, cp, f2s[5];
       if (nb >= 0) {
         const int nn = face_node<Nq>(d, N - a, t1, t2);
 #pragma unroll
-        for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
-        pp = TH[((size_t)nb * 4) * kNP + nn];
-        cp = TH[((size_t)nb * 4 + 1) * kNP + nn];
-        const float *g2m = F2 + ((size_t)e * 15 + d * 5) * kNP + n;
-        const float *g2p = F2 + ((size_t)nb * 15 + d * 5) * kNP + nn;
+        for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * NP + nn];
+        pp = TH[((size_t)nb * 4) * NP + nn];
+        cp = TH[((size_t)nb * 4 + 1) * NP + nn];
+        const float *g2m = F2 + ((size_t)e * 15 + d * 5) * NP + n;
+        const float *g2p = F2 + ((size_t)nb * 15 + d * 5) * NP + nn;
 #pragma unroll
-        for (int c = 0; c < 5; ++c) f2s[c] = 0.5f * (sg * g2m[c * kNP] + sg * g2p[c * kNP]);
+        for (int c = 0; c < 5; ++c) f2s[c] = 0.5f * (sg * g2m[c * NP] + sg * g2p[c * NP]);
       } else {
 #pragma unroll
         for (int v = 0; v < 6; ++v) sp[v] = sm[v];
@@ -431,9 +444,9 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
       momentum_sources(sv, L[L_RHO] + sv[0], tau, F, R);
       float sn[6];
       stage_update<UPD>(P, sc, R, dq0, D0, q0, sv, P.qref64 + (size_t)(ez * Nq + k) * 4, 1, dQ, Q64, Sout, Rout, e,
-                        t, Np, sn);
+                        t, Np, sn, NP);
       // the thermodynamics of the new state, for the next stage's two passes
-      if (UPD) thermo_store32(P, L, sn, THout, e, t, fail);
+      if (UPD) thermo_store32(P, L, sn, THout, e, t, fail, NP);
     }
     if (t < 6 && g + (int)gridDim.x < P.E) next_element(P, g + gridDim.x, sEl, sNb);
     __syncthreads();
@@ -443,9 +456,10 @@ __global__ void __launch_bounds__(128, FL == 0 ? 7 : 6) k_rhs32(const float *__r
 
 // Shadow of an FP64 state: s = (float)(Q - Q_ref(level)), subtraction in
 // FP64, with its thermodynamic fields.  Q64 null: the shadow S is given and
-// only its thermodynamic fields are written.
+// only its thermodynamic fields are written.  np: padded nodes per element
+// of the FP32 arrays.
 __global__ void k_shadow32(const double *__restrict__ Q64, float *__restrict__ S, float *__restrict__ TH,
-                           const KParams P, int Np, int Nq) {
+                           const KParams P, int Np, int Nq, int np) {
   const long long n = (long long)P.E * Np;
   int fail = 0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
@@ -461,12 +475,12 @@ __global__ void k_shadow32(const double *__restrict__ Q64, float *__restrict__ S
       if (Q64) {
         const double ref = v == 0 ? qr[0] : (v == 4 ? qr[1] : (v == 5 ? qr[2] : 0.0));
         s[v] = (float)(Q64[(e * 6 + v) * Np + node] - ref);
-        S[(e * 6 + v) * kNP + node] = s[v];
+        S[(e * 6 + v) * np + node] = s[v];
       } else {
-        s[v] = S[(e * 6 + v) * kNP + node];
+        s[v] = S[(e * 6 + v) * np + node];
       }
     }
-    thermo_store32(P, P.lev32 + (size_t)(ez * Nq + k) * L_NF, s, TH, (size_t)e, node, fail);
+    thermo_store32(P, P.lev32 + (size_t)(ez * Nq + k) * L_NF, s, TH, (size_t)e, node, fail, np);
   }
   report_thermo_flags(P, fail);
 }
@@ -476,7 +490,7 @@ cudaError_t launch_shadow32(const double *Q64, float *S, float *TH, const KParam
   long long nodes = (long long)P.E * Np;
   int blocks = (int)((nodes + 255) / 256);
   if (blocks > 148 * 32) blocks = 148 * 32;
-  k_shadow32<<<blocks, 256, 0, s>>>(Q64, S, TH, P, Np, Nq);
+  k_shadow32<<<blocks, 256, 0, s>>>(Q64, S, TH, P, Np, Nq, np32(N));
   return cudaGetLastError();
 }
 
@@ -485,34 +499,44 @@ static void grad32_instance(const float *S, const float *TH, float *F2, const KP
   static int grid = 0;
   if (!grid)
     grid = CL == 2 ? grid_for_tc((const void *)k_grad32<N, CL>, 1 << 30, kTcCols)
-                   : grid_for((const void *)k_grad32<N, CL>, 1 << 30, 0);
-  if (CL == 2 && P.tc_stall == 2) {
-    static int hgrid = 0;
-    if (!hgrid) hgrid = grid_for_tc((const void *)k_grad32<N, 2, true>, 1 << 30, kTcCols);
-    k_grad32<N, 2, true><<<hgrid < P.E ? hgrid : P.E, 128, 0, s>>>(S, TH, F2, P);
-    return;
+                   : grid_for((const void *)k_grad32<N, CL>, 1 << 30, 0, np32(N));
+  if constexpr (CL == 2) {
+    if (P.tc_stall == 2) {
+      static int hgrid = 0;
+      if (!hgrid) hgrid = grid_for_tc((const void *)k_grad32<N, 2, true>, 1 << 30, kTcCols);
+      k_grad32<N, 2, true><<<hgrid < P.E ? hgrid : P.E, 128, 0, s>>>(S, TH, F2, P);
+      return;
+    }
   }
-  k_grad32<N, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, TH, F2, P);
+  k_grad32<N, CL><<<grid < P.E ? grid : P.E, np32(N), 0, s>>>(S, TH, F2, P);
 }
 
+// the learned closure only up to N = 4 (cmles_create rejects it above)
 template <int N>
 static void grad32_order(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
-  if (P.closure == 2)
-    grad32_instance<N, 2>(S, TH, F2, P, s);
-  else if (P.closure == 3)
+  if constexpr (N <= 4) {
+    if (P.closure == 2) {
+      grad32_instance<N, 2>(S, TH, F2, P, s);
+      return;
+    }
+  }
+  if (P.closure == 3)
     grad32_instance<N, 3>(S, TH, F2, P, s);
   else
     grad32_instance<N, 1>(S, TH, F2, P, s);
 }
 
-// the flat-mesh kernels are instantiated for the orders 1 .. 4 (one thread
-// per node of a 128-thread CTA, 128-node padding)
+// the flat-mesh kernels are instantiated for the orders 1 .. 7 (one thread
+// per node, np32(N) threads per CTA and padded nodes per element)
 cudaError_t launch_grad32(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
   switch (P.N) {
     case 1: grad32_order<1>(S, TH, F2, P, s); break;
     case 2: grad32_order<2>(S, TH, F2, P, s); break;
     case 3: grad32_order<3>(S, TH, F2, P, s); break;
     case 4: grad32_order<4>(S, TH, F2, P, s); break;
+    case 5: grad32_order<5>(S, TH, F2, P, s); break;
+    case 6: grad32_order<6>(S, TH, F2, P, s); break;
+    case 7: grad32_order<7>(S, TH, F2, P, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -522,8 +546,13 @@ template <int N, int UPD, int FL>
 static void k_rhs32_instance(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
                              float *THout, double *Rout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
   static int grid = 0;
-  if (!grid) grid = grid_for((const void *)k_rhs32<N, UPD, FL>, 1 << 30, 0);
-  k_rhs32<N, UPD, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P);
+  constexpr int smem = rhs32_dyn_bytes(N);
+  if (!grid) {
+    if (smem > 0)
+      cudaFuncSetAttribute((const void *)k_rhs32<N, UPD, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    grid = grid_for((const void *)k_rhs32<N, UPD, FL>, 1 << 30, smem, np32(N));
+  }
+  k_rhs32<N, UPD, FL><<<grid < P.E ? grid : P.E, np32(N), smem, s>>>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P);
 }
 
 template <int N, int FL>
@@ -558,6 +587,9 @@ cudaError_t launch_rhs32(const float *S, const float *F2, const float *TH, float
     case 2: rhs32_order<2>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
     case 3: rhs32_order<3>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
     case 4: rhs32_order<4>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    case 5: rhs32_order<5>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    case 6: rhs32_order<6>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    case 7: rhs32_order<7>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -11,10 +11,9 @@
 
 namespace cmles {
 
-// threads per CTA: one per node (128 up to N = 4)
-__host__ __device__ constexpr int filter_block(int N) {
-  return (N + 1) * (N + 1) * (N + 1) <= 128 ? 128 : ((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32;
-}
+// threads per CTA: one per node (128 up to N = 4), as many as the FP32
+// arrays' padded nodes per element
+__host__ __device__ constexpr int filter_block(int N) { return np32(N); }
 
 template <int N>
 __global__ void __launch_bounds__(filter_block(N)) k_expfilter(double *__restrict__ Q, float *__restrict__ S32,
@@ -51,7 +50,7 @@ __global__ void __launch_bounds__(filter_block(N)) k_expfilter(double *__restric
 #pragma unroll
         for (int m = 0; m < Nq; ++m) r += sF[k * Nq + m] * a[i + Nq * (j + Nq * m)];
         q[t] = r;
-        if (S32) S32[((size_t)e * 6 + v) * 128 + t] = (float)r;
+        if (S32) S32[((size_t)e * 6 + v) * np32(N) + t] = (float)r;
       }
       __syncthreads();
     }

@@ -211,7 +211,7 @@ HaloSet halo_set(cmles_handle h, int which, bool B, int d) {
   HaloSet H;
   memset(&H, 0, sizeof(H));
   H.Np = h->Np;
-  const int stride = h->fp32 ? 128 : h->Np;
+  const int stride = h->fp32 ? np32(h->N) : h->Np;
   if (!B) {
     H.nf = 2;
     H.f[0] = {h->fp32 ? (void *)h->S32[which] : (void *)h->Q[which], 6, 0, 6, stride};

@@ -6,7 +6,7 @@
 
 namespace cmles {
 
-constexpr int kNP = 128;  // padded nodes per element in the FP32 arrays
+constexpr int kNP = np32(4);  // padded nodes per element in the FP32 arrays up to N = 4
 
 struct Th32 {
   float rho, u[3], qp, Tp, pp, c, hp, thvp;
@@ -141,18 +141,18 @@ __device__ __forceinline__ void flux1_dev32(const float s[6], float rho_r, float
 
 // The thermodynamic fields of a shadow node s that the two passes read
 // (planes of TH per element: p', c, h', theta_v'), stored by whoever writes
-// the node's state.
+// the node's state; np: the arrays' padded nodes per element.
 __device__ __forceinline__ void thermo_store32(const KParams &P, const float *L, const float s[6], float *TH,
-                                               size_t e, int t, int &fail) {
+                                               size_t e, int t, int &fail, int np = kNP) {
   Th32 o;
   if (P.moist)
     thermo32<true>(P, L, s, o, fail);
   else
     thermo32<false>(P, L, s, o, fail);
-  TH[(e * 4 + 0) * kNP + t] = o.pp;
-  TH[(e * 4 + 1) * kNP + t] = o.c;
-  TH[(e * 4 + 2) * kNP + t] = o.hp;
-  TH[(e * 4 + 3) * kNP + t] = o.thvp;
+  TH[(e * 4 + 0) * np + t] = o.pp;
+  TH[(e * 4 + 1) * np + t] = o.c;
+  TH[(e * 4 + 2) * np + t] = o.hp;
+  TH[(e * 4 + 3) * np + t] = o.thvp;
 }
 
 }  // namespace cmles
