@@ -355,10 +355,10 @@ double terrain(const cmles_mesh &m, double x) {
 // Node coordinates (z' = z + z_s(x)(1 - (z - z0)/Lz)), Jacobian, metric terms
 // in the conservative curl form (J a^r)_c = -[curl_xi(X_l grad_xi X_m)]_r with
 // (c, m, l) cyclic, and the per-element filter width; uploads the FP32
-// metrics [E][10][128] and the quadrature weights w_n J_n.
+// metrics [E][10][np32(N)] and the quadrature weights w_n J_n.
 cmles_status build_curved(cmles_handle h) {
   const cmles_mesh &m = h->mesh;
-  const int Nq = h->Nq, Np = h->Np;
+  const int Nq = h->Nq, Np = h->Np, np = np32(h->N);
   const long long E = h->E;
   const double hx = m.Lx / m.nex, hy = m.Ly / m.ney, hz = m.Lz / m.nez;
   h->hx_.resize((size_t)E * Np);
@@ -366,7 +366,7 @@ cmles_status build_curved(cmles_handle h) {
   h->hJ_.resize((size_t)E * Np);
   h->hJa_.resize((size_t)E * Np * 9);
   h->hdelta_.resize(E);
-  std::vector<float> geo((size_t)E * 10 * 128, 0.0f);
+  std::vector<float> geo((size_t)E * 10 * np, 0.0f);
   std::vector<double> wJ((size_t)E * Np);
   std::vector<double> X(3 * Np), dX(9 * Np), V(3 * Np);
   auto at = [&](int i, int j, int k) { return i + Nq * (j + Nq * k); };
@@ -432,8 +432,8 @@ cmles_status build_curved(cmles_handle h) {
       }
     }
     for (int n = 0; n < Np; ++n) {
-      for (int q = 0; q < 9; ++q) geo[((size_t)e * 10 + q) * 128 + n] = (float)h->hJa_[(e * Np + n) * 9 + q];
-      geo[((size_t)e * 10 + 9) * 128 + n] = (float)h->hJ_[e * Np + n];
+      for (int q = 0; q < 9; ++q) geo[((size_t)e * 10 + q) * np + n] = (float)h->hJa_[(e * Np + n) * 9 + q];
+      geo[((size_t)e * 10 + 9) * np + n] = (float)h->hJ_[e * Np + n];
     }
   }
   CK(cudaMemcpy(h->geo32, geo.data(), geo.size() * sizeof(float), cudaMemcpyHostToDevice));
@@ -457,9 +457,9 @@ cmles_status curved_reference(cmles_handle h, const double *rho_r, const double 
   const cmles_params &p = h->prm;
   const cmles_mesh &m = h->mesh;
   const KParams &K = h->K;
-  const int Nq = h->Nq, Np = h->Np, NF = kCurvedNF;
+  const int Nq = h->Nq, Np = h->Np, NF = kCurvedNF, np = np32(h->N);
   const long long E = h->E;
-  std::vector<float> tab((size_t)E * NF * 128, 0.0f);
+  std::vector<float> tab((size_t)E * NF * np, 0.0f);
   std::vector<double> qref((size_t)E * 3 * Np);
   std::vector<double> hr(Np), thr(Np), qr(Np);
   const double ztop = m.z0 + m.Lz;
@@ -489,23 +489,23 @@ cmles_status curved_reference(cmles_handle h, const double *rho_r, const double 
           tau = fmax(tau, tl);
         }
       }
-      float *T = &tab[(size_t)e * NF * 128 + n];
-      T[L_RHO * 128] = (float)rho_r[g];
-      T[L_RHOQ * 128] = (float)(rho_r[g] * q);
-      T[L_T * 128] = (float)Tr;
-      T[L_T_T0 * 128] = (float)(Tr - p.T0);
-      T[L_GZ * 128] = (float)(p.g * z);
-      T[L_P * 128] = (float)p_r[g];
-      T[L_H * 128] = (float)(rhoe + p_r[g]);
-      T[L_HM * 128] = (float)hr[n];
-      T[L_THV * 128] = (float)thr[n];
-      T[L_RHORM * 128] = (float)(rho_r[g] * Rm);
-      T[L_TAU * 128] = (float)tau;
-      T[L_QM * 128] = (float)q;
-      T[L_RVS * 128] = (float)rhovsat64(h, Tr);
+      float *T = &tab[(size_t)e * NF * np + n];
+      T[L_RHO * np] = (float)rho_r[g];
+      T[L_RHOQ * np] = (float)(rho_r[g] * q);
+      T[L_T * np] = (float)Tr;
+      T[L_T_T0 * np] = (float)(Tr - p.T0);
+      T[L_GZ * np] = (float)(p.g * z);
+      T[L_P * np] = (float)p_r[g];
+      T[L_H * np] = (float)(rhoe + p_r[g]);
+      T[L_HM * np] = (float)hr[n];
+      T[L_THV * np] = (float)thr[n];
+      T[L_RHORM * np] = (float)(rho_r[g] * Rm);
+      T[L_TAU * np] = (float)tau;
+      T[L_QM * np] = (float)q;
+      T[L_RVS * np] = (float)rhovsat64(h, Tr);
       const double delta = h->hdelta_[e];
-      T[(NF - 2) * 128] = (float)delta;
-      T[(NF - 1) * 128] = (float)((p.Cs * delta) * (p.Cs * delta));
+      T[(NF - 2) * np] = (float)delta;
+      T[(NF - 1) * np] = (float)((p.Cs * delta) * (p.Cs * delta));
     }
     // reference gradients: (1/J) sum_r (J a^r)_c d/dxi_r
     const double *fields[3] = {hr.data(), qr.data(), thr.data()};
@@ -527,10 +527,10 @@ cmles_status curved_reference(cmles_handle h, const double *rho_r, const double 
         }
         double gc[3];
         for (int c = 0; c < 3; ++c) gc[c] = (ja[0 + c] * dr[0] + ja[3 + c] * dr[1] + ja[6 + c] * dr[2]) / Jn;
-        float *T = &tab[(size_t)e * NF * 128 + n];
-        T[xslot[fi] * 128] = (float)gc[0];
-        T[(xslot[fi] + 1) * 128] = (float)gc[1];
-        T[zslot[fi] * 128] = (float)gc[2];
+        float *T = &tab[(size_t)e * NF * np + n];
+        T[xslot[fi] * np] = (float)gc[0];
+        T[(xslot[fi] + 1) * np] = (float)gc[1];
+        T[zslot[fi] * np] = (float)gc[2];
       }
     }
   }
@@ -710,11 +710,11 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
   if (!mesh || !params || !out) return CMLES_ERR_ARG;
   *out = nullptr;
   // the kernels are instantiated for the orders 1 .. 7 on flat meshes in
-  // both precisions, with the learned closure (one 128-row tensor-core tile
-  // per element) for 1 .. 4, and for 4 on warped meshes and for HEVI
+  // both precisions and on warped meshes (FP32), with the learned closure
+  // (one 128-row tensor-core tile per element) for 1 .. 4, and for 4 with HEVI
   if (mesh->N < 1 || mesh->N > 7) return CMLES_ERR_ARG;
   if (params->closure == CMLES_CLOSURE_MLP && mesh->N > 4) return CMLES_ERR_ARG;
-  if ((mesh->warp || params->integrator == CMLES_ARK2_HEVI) && mesh->N != 4) return CMLES_ERR_ARG;
+  if (params->integrator == CMLES_ARK2_HEVI && mesh->N != 4) return CMLES_ERR_ARG;
   if (mesh->nex < 1 || mesh->ney < 1 || mesh->nez < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0))
     return CMLES_ERR_MESH;
   // warped (curvilinear) meshes run on the FP32 path
@@ -791,8 +791,8 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
   ALLOC(h->dH32, (size_t)mesh->nez * h->Nq * h->Nq * sizeof(float));
   if (h->curved) {
     ALLOC(h->qref64, (size_t)E * 3 * h->Np * sizeof(double));
-    ALLOC(h->geo32, (size_t)E * 10 * 128 * sizeof(float));
-    ALLOC(h->node32, (size_t)E * kCurvedNF * 128 * sizeof(float));
+    ALLOC(h->geo32, (size_t)E * 10 * np32(mesh->N) * sizeof(float));
+    ALLOC(h->node32, (size_t)E * kCurvedNF * np32(mesh->N) * sizeof(float));
     ALLOC(h->wJn, (size_t)E * h->Np * sizeof(double));
   } else {
     ALLOC(h->qref64, (size_t)nlev * 4 * sizeof(double));

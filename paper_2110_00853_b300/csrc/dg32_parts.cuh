@@ -145,9 +145,9 @@ __device__ __forceinline__ void face_finish(const float (&raw)[7], float rho_r, 
   gf[5] = raw[6];
 }
 __device__ __forceinline__ void face_primitives(const float *__restrict__ S, const float *__restrict__ TH, size_t nb,
-                                                int nn, float rho_r, float q_r, float (&gf)[6]) {
+                                                int nn, float rho_r, float q_r, float (&gf)[6], int np = kNP) {
   float raw[7];
-  face_load(S, TH, nb, nn, raw);
+  face_load(S, TH, nb, nn, raw, np);
   face_finish(raw, rho_r, q_r, gf);
 }
 

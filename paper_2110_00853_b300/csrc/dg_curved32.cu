@@ -27,30 +27,34 @@ namespace cmles {
 // and the per-element filter width Delta and (C_s Delta)^2
 enum { C_DX_HM = L_NF, C_DY_HM, C_DX_Q, C_DY_Q, C_DX_THV, C_DY_THV, C_DELTA, C_CSD2, C_NF = 24 };
 
-__device__ __forceinline__ void load_node_table(const float *__restrict__ tab, size_t e, int n, float L[L_NF]) {
-  const float *p = tab + e * C_NF * kNP + n;
+// np: padded nodes per element of the FP32 arrays and tables (np32(N))
+__device__ __forceinline__ void load_node_table(const float *__restrict__ tab, size_t e, int n, float L[L_NF],
+                                                int np = kNP) {
+  const float *p = tab + e * C_NF * np + n;
 #pragma unroll
-  for (int f = 0; f < L_NF; ++f) L[f] = p[f * kNP];
+  for (int f = 0; f < L_NF; ++f) L[f] = p[f * np];
 }
 
 // HOOK: the instance launched only under test hook 2 (cmles_test_stall_tc),
 // whose first MMA completion wait gives up at once.
+// One thread per node, NP = np32(N) threads per CTA; the learned closure's
+// row tile is one 128-thread CTA (N <= 4).
 template <int N, int CL, bool HOOK = false>
-__global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *__restrict__ S,
-                                                                  const float *__restrict__ TH,
-                                                                  float *__restrict__ F2, const KParams P) {
-  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
+__global__ void __launch_bounds__(np32(N), N > 4 ? 1 : (CL == 2 ? 4 : 6))
+    k_grad32c(const float *__restrict__ S, const float *__restrict__ TH, float *__restrict__ F2, const KParams P) {
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq, NP = np32(N);
+  static_assert(CL != 2 || NP == 128, "the learned closure takes one 128-row tile per element");
   // the gradient fields share their storage with the closure network's A
   // operand (written only after every thread has finished its gradient)
-  constexpr int kGBytes = (6 * kNP + 36 * Nf) * 4, kABytes = CL == 2 ? kTcAElems * 2 : 0;
+  constexpr int kGBytes = (6 * NP + 36 * Nf) * 4, kABytes = CL == 2 ? kTcAElems * 2 : 0;
   __shared__ float sD[Nq * Nq];
   __shared__ __align__(128) uint8_t sU[kGBytes > kABytes ? kGBytes : kABytes];
   __shared__ int sNb[6];
   __shared__ __align__(16) uint8_t sMlpRaw[CL == 2 ? sizeof(MlpTc) : 16];
   __shared__ __align__(8) uint64_t sBar[2];
   __shared__ uint32_t sSlot;
-  float(*sG)[kNP] = reinterpret_cast<float(*)[kNP]>(sU);
-  float(*sGf)[6][Nf] = reinterpret_cast<float(*)[6][Nf]>(sU + 6 * kNP * 4);
+  float(*sG)[NP] = reinterpret_cast<float(*)[NP]>(sU);
+  float(*sGf)[6][Nf] = reinterpret_cast<float(*)[6][Nf]>(sU + 6 * NP * 4);
   __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(sU);
   const KF &F = P.f;
   const int t = threadIdx.x;
@@ -66,17 +70,17 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
     if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
     float sv[6], G[6], L[L_NF];
     if (t < Np) {
-      load_node_table(P.node32, e, t, L);
+      load_node_table(P.node32, e, t, L, NP);
 #pragma unroll
-      for (int v = 0; v < 6; ++v) sv[v] = S[((size_t)e * 6 + v) * kNP + t];
+      for (int v = 0; v < 6; ++v) sv[v] = S[((size_t)e * 6 + v) * NP + t];
       // h' and theta_v' come with the state; u and q' formed as there
       const float rinv = fdiv(1.0f, L[L_RHO] + sv[0]);
       G[0] = sv[1] * rinv;
       G[1] = sv[2] * rinv;
       G[2] = sv[3] * rinv;
-      G[3] = TH[((size_t)e * 4 + 2) * kNP + t];
+      G[3] = TH[((size_t)e * 4 + 2) * NP + t];
       G[4] = (sv[5] - L[L_QM] * sv[0]) * rinv;
-      G[5] = TH[((size_t)e * 4 + 3) * kNP + t];
+      G[5] = TH[((size_t)e * 4 + 3) * NP + t];
 #pragma unroll
       for (int v = 0; v < 6; ++v) sG[v][t] = G[v];
     }
@@ -87,9 +91,9 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
       if (nb < 0) continue;
       const int d = f >> 1, t1 = fn % Nq, t2 = fn / Nq;
       const int nn = face_node<Nq>(d, (f & 1) ? 0 : N, t1, t2);
-      const float *tn = P.node32 + (size_t)nb * C_NF * kNP + nn;
+      const float *tn = P.node32 + (size_t)nb * C_NF * NP + nn;
       float gf[6];
-      face_primitives(S, TH, nb, nn, tn[L_RHO * kNP], tn[L_QM * kNP], gf);
+      face_primitives(S, TH, nb, nn, tn[L_RHO * NP], tn[L_QM * NP], gf, NP);
 #pragma unroll
       for (int v = 0; v < 6; ++v) sGf[f][v][fn] = gf[v];
     }
@@ -97,11 +101,11 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
     float gr[6][3];
     float nut = 0.f, Dt = 0.f;
     if (t < Np) {
-      const float *geo = P.geo32 + (size_t)e * 10 * kNP + t;
+      const float *geo = P.geo32 + (size_t)e * 10 * NP + t;
       float Ja[9];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) Ja[q] = geo[q * kNP];
-      const float Jinv = 1.0f / geo[9 * kNP];
+      for (int q = 0; q < 9; ++q) Ja[q] = geo[q * NP];
+      const float Jinv = 1.0f / geo[9 * NP];
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
@@ -114,15 +118,15 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
 #pragma unroll
         for (int c = 0; c < 3; ++c) gr[v][c] = Jinv * (Ja[0 + c] * a0 + Ja[3 + c] * a1 + Ja[6 + c] * a2);
       }
-      const float *tab = P.node32 + (size_t)e * C_NF * kNP + t;
-      gr[3][0] += tab[C_DX_HM * kNP];
-      gr[3][1] += tab[C_DY_HM * kNP];
+      const float *tab = P.node32 + (size_t)e * C_NF * NP + t;
+      gr[3][0] += tab[C_DX_HM * NP];
+      gr[3][1] += tab[C_DY_HM * NP];
       gr[3][2] += L[L_DZ_HM];
-      gr[4][0] += tab[C_DX_Q * kNP];
-      gr[4][1] += tab[C_DY_Q * kNP];
+      gr[4][0] += tab[C_DX_Q * NP];
+      gr[4][1] += tab[C_DY_Q * NP];
       gr[4][2] += L[L_DZ_Q];
-      gr[5][0] += tab[C_DX_THV * kNP];
-      gr[5][1] += tab[C_DY_THV * kNP];
+      gr[5][0] += tab[C_DX_THV * NP];
+      gr[5][1] += tab[C_DY_THV * NP];
       gr[5][2] += L[L_DZ_THV];
       auto lift = [&](int f, int fn) {
         const int d = f >> 1;
@@ -158,13 +162,13 @@ __global__ void __launch_bounds__(128, CL == 2 ? 4 : 6) k_grad32c(const float *_
       if (k == 0) lift(4, i + Nq * j);
       if (k == N) lift(5, i + Nq * j);
       // (C_s Delta)^2 with Delta = (element volume)^(1/3) / N, per node
-      if (CL == 1 && P.closure == 1) eddy_nu<1>(gr, tab[C_CSD2 * kNP], L[L_THV] + G[5], F, P.richardson, nut, Dt);
+      if (CL == 1 && P.closure == 1) eddy_nu<1>(gr, tab[C_CSD2 * NP], L[L_THV] + G[5], F, P.richardson, nut, Dt);
     }
     if (CL == 2) {
-      const float Delta = t < Np ? P.node32[(size_t)e * C_NF * kNP + C_DELTA * kNP + t] : 0.f;
+      const float Delta = t < Np ? P.node32[(size_t)e * C_NF * NP + C_DELTA * NP + t] : 0.f;
       learned_nu<HOOK>(W, sA, tcs, gr, Delta, t < Np, nut, Dt);
     }
-    if (t < Np) write_f2(F2, e, t, L[L_RHO] + sv[0], nut, Dt, gr, sv, G);
+    if (t < Np) write_f2(F2, e, t, L[L_RHO] + sv[0], nut, Dt, gr, sv, G, NP);
     __syncthreads();
   }
   if (CL == 2) {
@@ -190,16 +194,24 @@ __device__ __forceinline__ void flux1_normal32(const float s[6], float rho_r, fl
 // FL: numerical flux of F1, 0 Rusanov, 1 HLLC
 // UPD as in k_rhs32: 0 right-hand side, 1 stage (FP32 step increment),
 // 2 last stage of the step (FP64 accumulation).  FL: 0 Rusanov, 1 HLLC, 2 Roe.
+// One thread per node, NP = np32(N) threads per CTA.  The 24 node planes
+// (contravariant fluxes, state) take 24 * 4 * np32(N) bytes of shared memory:
+// static up to N = 6, dynamic at N = 7 (48 KB).
+__host__ __device__ constexpr int rhs32c_dyn_bytes(int N) { return 24 * 4 * np32(N) > 40 * 1024 ? 24 * 4 * np32(N) : 0; }
+
 template <int N, int UPD, int FL>
-__global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, const float *__restrict__ F2,
-                                                   const float *__restrict__ TH, float *__restrict__ dQ,
-                                                   double *__restrict__ Q64, float *__restrict__ Sout,
-                                                   float *__restrict__ THout, double *__restrict__ Rout,
-                                                   const StageCoef sc, const KParams P) {
-  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq;
+__global__ void __launch_bounds__(np32(N), N > 4 ? 1 : 6)
+    k_rhs32c(const float *__restrict__ S, const float *__restrict__ F2, const float *__restrict__ TH,
+             float *__restrict__ dQ, double *__restrict__ Q64, float *__restrict__ Sout, float *__restrict__ THout,
+             double *__restrict__ Rout, const StageCoef sc, const KParams P) {
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq, NP = np32(N);
+  constexpr bool DYN = rhs32c_dyn_bytes(N) > 0;
   __shared__ float sD[Nq * Nq];
-  __shared__ float sF[6][3][kNP];  // contravariant fluxes J a^r . F
-  __shared__ float sS[6][kNP];
+  __shared__ float sFst[DYN ? 1 : 18 * NP];
+  __shared__ float sSst[DYN ? 1 : 6 * NP];
+  extern __shared__ __align__(16) float sDyn32c[];
+  float(*sF)[3][NP] = reinterpret_cast<float(*)[3][NP]>(DYN ? sDyn32c : sFst);  // contravariant fluxes J a^r . F
+  float(*sS)[NP] = reinterpret_cast<float(*)[NP]>(DYN ? sDyn32c + 18 * NP : sSst);
   __shared__ float sLf[6][6][Nf];
   __shared__ int sNb[6];
   const KF &F = P.f;
@@ -212,34 +224,34 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
     const int e = element_at(P, g, ex, ey, ez);
     if (t < 6) sNb[t] = neighbour(P, ex, ey, ez, t);
     float sv[6];
-    const float *tab = P.node32 + (size_t)e * C_NF * kNP + (t < Np ? t : 0);
-    const float *geo = P.geo32 + (size_t)e * 10 * kNP + (t < Np ? t : 0);
+    const float *tab = P.node32 + (size_t)e * C_NF * NP + (t < Np ? t : 0);
+    const float *geo = P.geo32 + (size_t)e * 10 * NP + (t < Np ? t : 0);
     if (t < Np) {
 #pragma unroll
       for (int v = 0; v < 6; ++v) {
-        sv[v] = S[((size_t)e * 6 + v) * kNP + t];
+        sv[v] = S[((size_t)e * 6 + v) * NP + t];
         sS[v][t] = sv[v];
       }
-      const float pp = TH[((size_t)e * 4) * kNP + t];
-      const float rho = tab[L_RHO * kNP] + sv[0];
+      const float pp = TH[((size_t)e * 4) * NP + t];
+      const float rho = tab[L_RHO * NP] + sv[0];
       const float u[3] = {sv[1] / rho, sv[2] / rho, sv[3] / rho};
-      const float H = tab[L_H * kNP] + (sv[4] + pp);
-      const float rq = tab[L_RHOQ * kNP] + sv[5];
+      const float H = tab[L_H * NP] + (sv[4] + pp);
+      const float rq = tab[L_RHOQ * NP] + sv[5];
       float Fc[6][3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float *g2 = F2 + ((size_t)e * 15 + c * 5) * kNP + t;
+        const float *g2 = F2 + ((size_t)e * 15 + c * 5) * NP + t;
         const float c0 = g2[0];
         Fc[0][c] = sv[1 + c] + c0;
-        Fc[1][c] = sv[1] * u[c] + (c == 0 ? pp : 0.f) + g2[1 * kNP];
-        Fc[2][c] = sv[2] * u[c] + (c == 1 ? pp : 0.f) + g2[2 * kNP];
-        Fc[3][c] = sv[3] * u[c] + (c == 2 ? pp : 0.f) + g2[3 * kNP];
-        Fc[4][c] = H * u[c] + g2[4 * kNP];
+        Fc[1][c] = sv[1] * u[c] + (c == 0 ? pp : 0.f) + g2[1 * NP];
+        Fc[2][c] = sv[2] * u[c] + (c == 1 ? pp : 0.f) + g2[2 * NP];
+        Fc[3][c] = sv[3] * u[c] + (c == 2 ? pp : 0.f) + g2[3 * NP];
+        Fc[4][c] = H * u[c] + g2[4 * NP];
         Fc[5][c] = rq * u[c] + c0;
       }
       float Ja[9];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) Ja[q] = geo[q * kNP];
+      for (int q = 0; q < 9; ++q) Ja[q] = geo[q * NP];
 #pragma unroll
       for (int v = 0; v < 6; ++v)
 #pragma unroll
@@ -252,18 +264,18 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
       const int a = (f & 1) ? N : 0;
       const float sg = (f & 1) ? 1.f : -1.f;
       const int n = face_node<Nq>(d, a, t1, t2);
-      const float *tn = P.node32 + (size_t)e * C_NF * kNP + n;
-      const float *gn = P.geo32 + (size_t)e * 10 * kNP + n;
-      const float ax = gn[(3 * d) * kNP], ay = gn[(3 * d + 1) * kNP], az = gn[(3 * d + 2) * kNP];
+      const float *tn = P.node32 + (size_t)e * C_NF * NP + n;
+      const float *gn = P.geo32 + (size_t)e * 10 * NP + n;
+      const float ax = gn[(3 * d) * NP], ay = gn[(3 * d + 1) * NP], az = gn[(3 * d + 2) * NP];
       const float mag = sqrtf(ax * ax + ay * ay + az * az);
       const float nv[3] = {sg * ax / mag, sg * ay / mag, sg * az / mag};
-      const float rho_r = tn[L_RHO * kNP], rhoq_r = tn[L_RHOQ * kNP], Hr = tn[L_H * kNP];
+      const float rho_r = tn[L_RHO * NP], rhoq_r = tn[L_RHOQ * NP], Hr = tn[L_H * NP];
       float sm[6], sp[6];
 #pragma unroll
       for (int v = 0; v < 6; ++v) sm[v] = sS[v][n];
-      const float cm = TH[((size_t)e * 4 + 1) * kNP + n];
+      const float cm = TH[((size_t)e * 4 + 1) * NP + n];
       const int nb = sNb[f];
-      const float Lf = mag * F.inv_w0 / gn[9 * kNP];
+      const float Lf = mag * F.inv_w0 / gn[9 * NP];
       if (FL == 0 && nb >= 0) {
         // Rusanov across an interior face.  The own node's total normal flux
         // n.(F1 + F2) is sF . n from the first phase, so the lifted jump is
@@ -271,9 +283,9 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
         // neighbour's fluxes are evaluated here.
         const int nn = face_node<Nq>(d, N - a, t1, t2);
 #pragma unroll
-        for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
-        const float pp = TH[((size_t)nb * 4) * kNP + nn];
-        const float cp = TH[((size_t)nb * 4 + 1) * kNP + nn];
+        for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * NP + nn];
+        const float pp = TH[((size_t)nb * 4) * NP + nn];
+        const float cp = TH[((size_t)nb * 4 + 1) * NP + nn];
         float fp[6];
         flux1_normal32(sp, rho_r, rhoq_r, Hr, pp, nv, fp);
         float f2p[5];
@@ -281,7 +293,7 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
         for (int c5 = 0; c5 < 5; ++c5) {
           float fq = 0.f;
 #pragma unroll
-          for (int c = 0; c < 3; ++c) fq += nv[c] * F2[((size_t)nb * 15 + c * 5 + c5) * kNP + nn];
+          for (int c = 0; c < 3; ++c) fq += nv[c] * F2[((size_t)nb * 15 + c * 5 + c5) * NP + nn];
           f2p[c5] = fq;
         }
         const float um = (sm[1] * nv[0] + sm[2] * nv[1] + sm[3] * nv[2]) / (rho_r + sm[0]);
@@ -295,21 +307,21 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
         }
         continue;
       }
-      const float pm = TH[((size_t)e * 4) * kNP + n];
+      const float pm = TH[((size_t)e * 4) * NP + n];
       float pp, cp, f2s[5];
       if (nb >= 0) {
         const int nn = face_node<Nq>(d, N - a, t1, t2);
 #pragma unroll
-        for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * kNP + nn];
-        pp = TH[((size_t)nb * 4) * kNP + nn];
-        cp = TH[((size_t)nb * 4 + 1) * kNP + nn];
+        for (int v = 0; v < 6; ++v) sp[v] = S[((size_t)nb * 6 + v) * NP + nn];
+        pp = TH[((size_t)nb * 4) * NP + nn];
+        cp = TH[((size_t)nb * 4 + 1) * NP + nn];
 #pragma unroll
         for (int c5 = 0; c5 < 5; ++c5) {
           float fm = 0.f, fq = 0.f;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            fm += nv[c] * F2[((size_t)e * 15 + c * 5 + c5) * kNP + n];
-            fq += nv[c] * F2[((size_t)nb * 15 + c * 5 + c5) * kNP + nn];
+            fm += nv[c] * F2[((size_t)e * 15 + c * 5 + c5) * NP + n];
+            fq += nv[c] * F2[((size_t)nb * 15 + c * 5 + c5) * NP + nn];
           }
           f2s[c5] = 0.5f * (fm + fq);
         }
@@ -333,7 +345,7 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
           // the first interior layer above this face node less its component
           // along the wall normal
           const int ni = face_node<Nq>(2, 1, t1, t2);
-          const float ri = 1.0f / (P.node32[(size_t)e * C_NF * kNP + L_RHO * kNP + ni] + sS[0][ni]);
+          const float ri = 1.0f / (P.node32[(size_t)e * C_NF * NP + L_RHO * NP + ni] + sS[0][ni]);
           float up[3] = {sS[1][ni] * ri, sS[2][ni] * ri, sS[3][ni] * ri};
           const float un = up[0] * nv[0] + up[1] * nv[1] + up[2] * nv[2];
 #pragma unroll
@@ -354,7 +366,7 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
         const float rM = rho_r + sm[0], rP = rho_r + sp[0];
         const float iM = fdiv(1.0f, rM), iP = fdiv(1.0f, rP);
         const float uM[3] = {sm[1] * iM, sm[2] * iM, sm[3] * iM}, uP[3] = {sp[1] * iP, sp[2] * iP, sp[3] * iP};
-        const float pr = tn[L_P * kNP], Er = Hr - pr;
+        const float pr = tn[L_P * NP], Er = Hr - pr;
         float J[6];
         const int K = hllc_jump<float>(rM, uM, (rhoq_r + sm[5]) * iM, (Er + sm[4]) * iM, pr + pm, cm, rP, uP,
                                        (rhoq_r + sp[5]) * iP, (Er + sp[4]) * iP, pr + pp, cp, pp - pm, nv, J);
@@ -370,7 +382,7 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
         for (int v = 0; v < 6; ++v) dY[v] = sp[v] - sm[v];
         const RoeConst<float> rk = {F.Rd, F.Rv - F.Rd, F.cvd, F.cvv - F.cvd, F.T0, F.Iv0};
         roe_dissipation<float>(rM, uM, (rhoq_r + sm[5]) * iM, (Hr + sm[4] + pm) * iM, rP, uP, (rhoq_r + sp[5]) * iP,
-                               (Hr + sp[4] + pp) * iP, dY, tn[L_GZ * kNP], nv, rk, D);
+                               (Hr + sp[4] + pp) * iP, dY, tn[L_GZ * NP], nv, rk, D);
 #pragma unroll
         for (int v = 0; v < 6; ++v) f1s[v] = 0.5f * (fm[v] + fp[v]) - 0.5f * D[v];
       } else {
@@ -387,7 +399,7 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
     }
     __syncthreads();
     if (t < Np) {
-      const float Jinv = 1.0f / geo[9 * kNP];
+      const float Jinv = 1.0f / geo[9 * NP];
       // the lifted face terms of the node's x, y and z faces, without
       // branches: weight 1 on a face, 0 (on any valid entry) inside
       const float wx = (i == 0 || i == N) ? 1.f : 0.f, wy = (j == 0 || j == N) ? 1.f : 0.f,
@@ -411,20 +423,20 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
         r = fmaf(wz, lz[v * Nf], r);
         R[v] = r;
       }
-      momentum_sources(sv, tab[L_RHO * kNP] + sv[0], tab[L_TAU * kNP], F, R);
+      momentum_sources(sv, tab[L_RHO * NP] + sv[0], tab[L_TAU * NP], F, R);
       // the update inputs, loaded here rather than with the element's first
       // loads: this kernel is at its register limit (80) and held across the
       // face tasks they spill
       float dq0[6], D0[6], sn[6];
       double q0[6];
-      if (UPD) stage_inputs<UPD>(P, sc, dQ, Q64, e, t, Np, dq0, D0, q0);
+      if (UPD) stage_inputs<UPD>(P, sc, dQ, Q64, e, t, Np, dq0, D0, q0, NP);
       stage_update<UPD>(P, sc, R, dq0, D0, q0, sv, P.qref64 + (size_t)e * 3 * Np + t, Np, dQ, Q64, Sout, Rout, e, t,
-                        Np, sn);
+                        Np, sn, NP);
       // the thermodynamics of the new state, for the next stage's two passes
       if (UPD) {
         float L[L_NF];
-        load_node_table(P.node32, e, t, L);
-        thermo_store32(P, L, sn, THout, e, t, fail);
+        load_node_table(P.node32, e, t, L, NP);
+        thermo_store32(P, L, sn, THout, e, t, fail, NP);
       }
     }
     __syncthreads();
@@ -435,7 +447,7 @@ __global__ void __launch_bounds__(128, 6) k_rhs32c(const float *__restrict__ S, 
 // Shadow of an FP64 state on a curvilinear mesh (per-node reference offsets)
 // with its thermodynamic fields; Q64 null: only the fields of the given S.
 __global__ void k_shadow32c(const double *__restrict__ Q64, float *__restrict__ S, float *__restrict__ TH,
-                            const KParams P, int Np) {
+                            const KParams P, int Np, int np) {
   const long long n = (long long)P.E * Np;
   int fail = 0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
@@ -448,13 +460,13 @@ __global__ void k_shadow32c(const double *__restrict__ Q64, float *__restrict__ 
       if (Q64) {
         const double ref = v == 0 ? qr[0] : (v == 4 ? qr[Np] : (v == 5 ? qr[2 * Np] : 0.0));
         s[v] = (float)(Q64[(e * 6 + v) * Np + node] - ref);
-        S[(e * 6 + v) * kNP + node] = s[v];
+        S[(e * 6 + v) * np + node] = s[v];
       } else {
-        s[v] = S[(e * 6 + v) * kNP + node];
+        s[v] = S[(e * 6 + v) * np + node];
       }
     }
-    load_node_table(P.node32, (size_t)e, node, L);
-    thermo_store32(P, L, s, TH, (size_t)e, node, fail);
+    load_node_table(P.node32, (size_t)e, node, L, np);
+    thermo_store32(P, L, s, TH, (size_t)e, node, fail, np);
   }
   report_thermo_flags(P, fail);
 }
@@ -464,62 +476,105 @@ cudaError_t launch_shadow32c(const double *Q64, float *S, float *TH, const KPara
   long long nodes = (long long)P.E * Np;
   int blocks = (int)((nodes + 255) / 256);
   if (blocks > 148 * 32) blocks = 148 * 32;
-  k_shadow32c<<<blocks, 256, 0, s>>>(Q64, S, TH, P, Np);
+  k_shadow32c<<<blocks, 256, 0, s>>>(Q64, S, TH, P, Np, np32(N));
   return cudaGetLastError();
 }
 
-template <int CL>
+template <int N, int CL>
 static void grad32c_instance(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
   static int grid = 0;
   if (!grid)
-    grid = CL == 2 ? grid_for_tc((const void *)k_grad32c<4, CL>, 1 << 30, kTcCols)
-                   : grid_for((const void *)k_grad32c<4, CL>, 1 << 30, 0);
-  if (CL == 2 && P.tc_stall == 2) {
-    static int hgrid = 0;
-    if (!hgrid) hgrid = grid_for_tc((const void *)k_grad32c<4, 2, true>, 1 << 30, kTcCols);
-    k_grad32c<4, 2, true><<<hgrid < P.E ? hgrid : P.E, 128, 0, s>>>(S, TH, F2, P);
-    return;
+    grid = CL == 2 ? grid_for_tc((const void *)k_grad32c<N, CL>, 1 << 30, kTcCols)
+                   : grid_for((const void *)k_grad32c<N, CL>, 1 << 30, 0, np32(N));
+  if constexpr (CL == 2) {
+    if (P.tc_stall == 2) {
+      static int hgrid = 0;
+      if (!hgrid) hgrid = grid_for_tc((const void *)k_grad32c<N, 2, true>, 1 << 30, kTcCols);
+      k_grad32c<N, 2, true><<<hgrid < P.E ? hgrid : P.E, 128, 0, s>>>(S, TH, F2, P);
+      return;
+    }
   }
-  k_grad32c<4, CL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, TH, F2, P);
+  k_grad32c<N, CL><<<grid < P.E ? grid : P.E, np32(N), 0, s>>>(S, TH, F2, P);
 }
 
+// the learned closure only up to N = 4 (cmles_create rejects it above)
+template <int N>
+static void grad32c_order(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
+  if constexpr (N <= 4) {
+    if (P.closure == 2) {
+      grad32c_instance<N, 2>(S, TH, F2, P, s);
+      return;
+    }
+  }
+  grad32c_instance<N, 1>(S, TH, F2, P, s);
+}
+
+// the curvilinear kernels are instantiated for the orders 1 .. 7 (one thread
+// per node, np32(N) threads per CTA and padded nodes per element)
 cudaError_t launch_grad32c(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
-  if (P.closure == 2)
-    grad32c_instance<2>(S, TH, F2, P, s);
-  else
-    grad32c_instance<1>(S, TH, F2, P, s);
+  switch (P.N) {
+    case 1: grad32c_order<1>(S, TH, F2, P, s); break;
+    case 2: grad32c_order<2>(S, TH, F2, P, s); break;
+    case 3: grad32c_order<3>(S, TH, F2, P, s); break;
+    case 4: grad32c_order<4>(S, TH, F2, P, s); break;
+    case 5: grad32c_order<5>(S, TH, F2, P, s); break;
+    case 6: grad32c_order<6>(S, TH, F2, P, s); break;
+    case 7: grad32c_order<7>(S, TH, F2, P, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
-template <int UPD, int FL>
+template <int N, int UPD, int FL>
 static void k_rhs32c_instance(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
                               float *THout, double *Rout, const StageCoef &sc, const KParams &P, cudaStream_t s) {
   static int grid = 0;
-  if (!grid) grid = grid_for((const void *)k_rhs32c<4, UPD, FL>, 1 << 30, 0);
-  k_rhs32c<4, UPD, FL><<<grid < P.E ? grid : P.E, 128, 0, s>>>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P);
+  constexpr int smem = rhs32c_dyn_bytes(N);
+  if (!grid) {
+    if (smem > 0)
+      cudaFuncSetAttribute((const void *)k_rhs32c<N, UPD, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    grid = grid_for((const void *)k_rhs32c<N, UPD, FL>, 1 << 30, smem, np32(N));
+  }
+  k_rhs32c<N, UPD, FL><<<grid < P.E ? grid : P.E, np32(N), smem, s>>>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P);
 }
 
-template <int FL>
+template <int N, int FL>
 static void k_rhs32c_dispatch(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
                               float *THout, double *Rout, const StageCoef &sc, bool update, const KParams &P,
                               cudaStream_t s) {
   if (!update)
-    k_rhs32c_instance<0, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
+    k_rhs32c_instance<N, 0, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
   else if (sc.last)
-    k_rhs32c_instance<2, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
+    k_rhs32c_instance<N, 2, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
   else
-    k_rhs32c_instance<1, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
+    k_rhs32c_instance<N, 1, FL>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, P, s);
+}
+
+template <int N>
+static void rhs32c_order(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
+                         float *THout, double *Rout, const StageCoef &sc, bool update, const KParams &P,
+                         cudaStream_t s) {
+  if (P.flux == 2)
+    k_rhs32c_dispatch<N, 2>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
+  else if (P.flux == 1)
+    k_rhs32c_dispatch<N, 1>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
+  else
+    k_rhs32c_dispatch<N, 0>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
 }
 
 cudaError_t launch_rhs32c(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,
                           float *THout, double *Rout, const StageCoef &sc, bool update, const KParams &P,
                           cudaStream_t s) {
-  if (P.flux == 2)
-    k_rhs32c_dispatch<2>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
-  else if (P.flux == 1)
-    k_rhs32c_dispatch<1>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
-  else
-    k_rhs32c_dispatch<0>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s);
+  switch (P.N) {
+    case 1: rhs32c_order<1>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    case 2: rhs32c_order<2>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    case 3: rhs32c_order<3>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    case 4: rhs32c_order<4>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    case 5: rhs32c_order<5>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    case 6: rhs32c_order<6>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    case 7: rhs32c_order<7>(S, F2, TH, dQ, Q64, Sout, THout, Rout, sc, update, P, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -12,10 +12,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _hill_box(nex=8, ney=2, nez=8):
+def _hill_box(nex=8, ney=2, nez=8, N=4):
     # a window of the hill configuration's element size around the ridge
     h = 40000.0 / 128
-    return dict(N=4, nex=nex, ney=ney, nez=nez, Lx=nex * h, Ly=ney * h, Lz=nez * h, x0=20000.0 - nex * h / 2,
+    return dict(N=N, nex=nex, ney=ney, nez=nez, Lx=nex * h, Ly=ney * h, Lz=nez * h, x0=20000.0 - nex * h / 2,
                 y0=0.0, z0=0.0, periodic=(1, 1, 0), warp=True, hill_h=400.0, hill_a=1000.0, hill_xc=20000.0)
 
 
@@ -29,11 +29,13 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def _setup(orc, fuzz=True, flux="rusanov"):
+def _setup(orc, fuzz=True, flux="rusanov", N=4, box=(8, 2, 8), dt=None):
     from paper_2110_00853_b300 import cmles
-    m = _hill_box()
+    m = _hill_box(*box, N=N)
     ph = _phys(m)
     ph["flux"] = flux
+    if dt is not None:
+        ph["dt"] = dt
     S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case("c3"))
     if fuzz:
         rng = np.random.default_rng(31)
@@ -93,9 +95,10 @@ def test_warped_steps_track_oracle_and_conserve(orc):
         assert abs(b1[v] - b0[v]) <= 1e-10 * abs(b0[v]), v
 
 
-def test_warped_free_stream(orc):
+@pytest.mark.parametrize("N", [4, 6])
+def test_warped_free_stream(orc, N):
     from paper_2110_00853_b300 import cmles
-    m = _hill_box()
+    m = _hill_box(N=N)
     ph = _phys(m)
     ph.update(g=0.0, sponge_alpha=0.0)
     G = cmles.Solver(m, ph, precision="fp32")
@@ -112,6 +115,37 @@ def test_warped_free_stream(orc):
     inner = (ez > 0) & (ez < m["nez"] - 1)
     # interior elements see no walls: the uniform flow stays uniform up to FP32 rounding
     assert np.abs(R[inner][:, 1:4]).max() < 1e-5 * rho * 100.0 / 100.0
+
+
+@pytest.mark.parametrize("N,flux", [(2, "rusanov"), (3, "hllc"), (5, "rusanov"), (6, "roe"), (7, "rusanov")])
+def test_warped_other_orders_tendency_and_steps(orc, N, flux):
+    """The curvilinear FP32 kernels at orders other than 4 (above 4: CTAs of
+    np32(N) threads, arrays and metric tables padded to as many nodes) on a
+    window around the ridge: the tendency against the oracle's, in norm and
+    node by node, then four steps, with mass and energy conserved."""
+    dt = 0.02 * min(1.0, (4.0 / N) ** 2)      # the step shrinks with the smallest node spacing
+    m, S, Q, G = _setup(orc, flux=flux, N=N, box=(8, 2, 8) if N <= 4 else (6, 2, 6), dt=dt)
+    R_orc, _ = S.rhs(Q)
+    R_gpu = G.tendency(torch.from_numpy(Q).cuda()).cpu().numpy()
+    errs = [_rel(R_gpu[:, v], R_orc[:, v]) for v in range(5)]
+    print("warped fp32 N", N, flux, "rel L2", errs)
+    for v in range(5):
+        assert errs[v] <= 1e-5, (v, errs)
+        assert np.abs(R_gpu[:, v] - R_orc[:, v]).max() <= 1e-4 * np.abs(R_orc[:, v]).max(), v
+    n = 4
+    Q_orc, _ = S.lsrk54(Q, n, dt)
+    G.set_state(torch.from_numpy(Q).cuda())
+    b0 = G.diagnostics()["budget"]
+    G.step(n)
+    Qg = G.get_state().cpu().numpy()
+    b1 = G.diagnostics()["budget"]
+    G.close()
+    for v in range(5):
+        e = _rel(Qg[:, v] - Q[:, v], Q_orc[:, v] - Q[:, v])
+        print("warped N", N, "4-step increment rel L2", v, e)
+        assert e <= 1e-5, v
+    for v in (0, 4):
+        assert abs(b1[v] - b0[v]) <= 1e-10 * abs(b0[v]), v
 
 
 def test_warped_tendency_with_learned_closure(orc):
