@@ -86,8 +86,8 @@ enum { CMLES_FP64 = 0, CMLES_FP32_ACC64 = 1 };
  * z_s(x) = hill_h exp(-((x - hill_xc)/hill_a)^2): elements stacked over the
  * terrain with linear damping to a flat top (Sec. 4.3). */
 typedef struct {
-  int N;                 /* polynomial order: 1..7 on flat and warped meshes
-                            (the learned closure 1..4), 4 with HEVI */
+  int N;                 /* polynomial order: 1..7 on flat and warped meshes,
+                            4 with HEVI */
   int nex, ney, nez;
   double x0, y0, z0;
   double Lx, Ly, Lz;

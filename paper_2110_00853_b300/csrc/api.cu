@@ -710,10 +710,8 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
   if (!mesh || !params || !out) return CMLES_ERR_ARG;
   *out = nullptr;
   // the kernels are instantiated for the orders 1 .. 7 on flat meshes in
-  // both precisions and on warped meshes (FP32), with the learned closure
-  // (one 128-row tensor-core tile per element) for 1 .. 4, and for 4 with HEVI
+  // both precisions and on warped meshes (FP32), and for 4 with HEVI
   if (mesh->N < 1 || mesh->N > 7) return CMLES_ERR_ARG;
-  if (params->closure == CMLES_CLOSURE_MLP && mesh->N > 4) return CMLES_ERR_ARG;
   if (params->integrator == CMLES_ARK2_HEVI && mesh->N != 4) return CMLES_ERR_ARG;
   if (mesh->nex < 1 || mesh->ney < 1 || mesh->nez < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0))
     return CMLES_ERR_MESH;

@@ -20,16 +20,17 @@ namespace cmles {
 // that wait ran out (reported like a failed MMA wait; the work stays intact).
 // HOOK instances (test hook 2) give up their first MMA completion wait at
 // once, while the MMA is in flight.  All threads must call it.
+// ncols: TMEM columns of the CTA (tc_cols_for its row tiles).
 template <bool HOOK>
 __device__ __forceinline__ int learned_setup(const KParams &P, uint8_t *sMlpRaw, uint64_t *sBar, uint32_t *sSlot,
-                                             TcState &tcs) {
+                                             TcState &tcs, uint32_t ncols = kTcCols) {
   const int t = threadIdx.x;
   const uint4 *src = reinterpret_cast<const uint4 *>(&P.mlp->tc);
   uint4 *dst = reinterpret_cast<uint4 *>(sMlpRaw);
   for (int q = t; q < (int)(sizeof(MlpTc) / 16); q += blockDim.x) dst[q] = src[q];
   fence_proxy_async_smem();
   if (t == 0) mbar_init(&sBar[1], 1);
-  tc_setup(tcs, sSlot, &sBar[0]);
+  tc_setup(tcs, sSlot, &sBar[0], ncols);
   int stalled = 0;
   if (P.tc_stall == 1 && !mbar_wait_bounded(&sBar[1], 0, 1 << 14)) stalled = 1;
   if (HOOK) tcs.hook = 1;
@@ -43,8 +44,9 @@ __device__ __forceinline__ int learned_setup(const KParams &P, uint8_t *sMlpRaw,
 // t of the tensor-core evaluation is node t; rows without a node (valid
 // false) carry zeros.  The A operand overwrites shared storage that the
 // gradient fields occupied, hence the block barrier before it is written.
-// All threads must call it.
-template <bool HOOK>
+// All threads must call it.  T: row tiles of 128 rows (CTAs of more than 128
+// threads, N > 4).
+template <bool HOOK, int T = 1>
 __device__ __forceinline__ void learned_nu(const MlpTc &W, __nv_bfloat16 *sA, TcState &tcs, const float (&gr)[6][3],
                                            float Delta, bool valid, float &nut, float &Dt) {
   float x[kMlpIn];
@@ -56,13 +58,30 @@ __device__ __forceinline__ void learned_nu(const MlpTc &W, __nv_bfloat16 *sA, Tc
   for (int b = 0; b < 3; ++b) x[9 + b] = valid ? gr[5][b] * W.in_scale[9 + b] : 0.f;
   x[12] = valid ? Delta * W.in_scale[12] : 0.f;
   __syncthreads();
-  mlp_tc_put_input(sA, x);
+  mlp_tc_put_input<T>(sA, x);
   float y0, y1;
-  mlp_tc_forward<HOOK>(W, sA, tcs, y0, y1);
+  mlp_tc_forward<HOOK, T>(W, sA, tcs, y0, y1);
   if (valid) {
     nut = W.out_scale[0] * fmaxf(y0, 0.f);
     Dt = W.out_scale[1] * fmaxf(y1, 0.f);
   }
+}
+
+// Shared memory of a gradient pass: the gradient fields of the element and
+// its face neighbours (6 np32(N) + 36 (N+1)^2 floats), which the learned
+// closure's A operand overwrites (T = np32(N) / 128 row tiles of kTcAElems
+// BF16 elements).  Static up to N = 4; with the learned closure above it
+// (40 to 80 KB) dynamic, 128 bytes more for the alignment of the operand.
+__host__ __device__ constexpr int grad32_ubytes(int N, int CL) {
+  return (CL == 2 && (np32(N) + 127) / 128 * kTcAElems * 2 > (6 * np32(N) + 36 * (N + 1) * (N + 1)) * 4)
+             ? (np32(N) + 127) / 128 * kTcAElems * 2
+             : (6 * np32(N) + 36 * (N + 1) * (N + 1)) * 4;
+}
+__host__ __device__ constexpr int grad32_dyn_bytes(int N, int CL) {
+  return CL == 2 && N > 4 ? grad32_ubytes(N, CL) + 128 : 0;
+}
+__device__ __forceinline__ uint8_t *align128(uint8_t *p) {
+  return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 127) & ~(uintptr_t)127);
 }
 
 // Eddy viscosity and diffusivity of the algebraic closures from the

@@ -37,18 +37,19 @@ __device__ __forceinline__ void load_node_table(const float *__restrict__ tab, s
 
 // HOOK: the instance launched only under test hook 2 (cmles_test_stall_tc),
 // whose first MMA completion wait gives up at once.
-// One thread per node, NP = np32(N) threads per CTA; the learned closure's
-// row tile is one 128-thread CTA (N <= 4).
+// One thread per node, NP = np32(N) threads per CTA; the learned closure
+// evaluates the CTA's rows in TT tiles of 128.
 template <int N, int CL, bool HOOK = false>
 __global__ void __launch_bounds__(np32(N), N > 4 ? 1 : (CL == 2 ? 4 : 6))
     k_grad32c(const float *__restrict__ S, const float *__restrict__ TH, float *__restrict__ F2, const KParams P) {
-  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq, NP = np32(N);
-  static_assert(CL != 2 || NP == 128, "the learned closure takes one 128-row tile per element");
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq, NP = np32(N), TT = (NP + 127) / 128;
   // the gradient fields share their storage with the closure network's A
   // operand (written only after every thread has finished its gradient)
-  constexpr int kGBytes = (6 * NP + 36 * Nf) * 4, kABytes = CL == 2 ? kTcAElems * 2 : 0;
+  constexpr bool DYN = grad32_dyn_bytes(N, CL) > 0;
   __shared__ float sD[Nq * Nq];
-  __shared__ __align__(128) uint8_t sU[kGBytes > kABytes ? kGBytes : kABytes];
+  __shared__ __align__(128) uint8_t sUst[DYN ? 16 : grad32_ubytes(N, CL)];
+  extern __shared__ __align__(16) uint8_t sDynG32c[];
+  uint8_t *sU = DYN ? align128(sDynG32c) : sUst;
   __shared__ int sNb[6];
   __shared__ __align__(16) uint8_t sMlpRaw[CL == 2 ? sizeof(MlpTc) : 16];
   __shared__ __align__(8) uint64_t sBar[2];
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(np32(N), N > 4 ? 1 : (CL == 2 ? 4 : 6))
   const MlpTc &W = *reinterpret_cast<const MlpTc *>(sMlpRaw);
   TcState tcs;
   int stalled = 0;
-  if (CL == 2) stalled = learned_setup<HOOK>(P, sMlpRaw, sBar, &sSlot, tcs);
+  if (CL == 2) stalled = learned_setup<HOOK>(P, sMlpRaw, sBar, &sSlot, tcs, tc_cols_for(TT));
   const int i = t % Nq, j = (t / Nq) % Nq, k = t / Nf;
   for (int g = blockIdx.x; g < P.E; g += gridDim.x) {
     int ex, ey, ez;
@@ -166,14 +167,14 @@ __global__ void __launch_bounds__(np32(N), N > 4 ? 1 : (CL == 2 ? 4 : 6))
     }
     if (CL == 2) {
       const float Delta = t < Np ? P.node32[(size_t)e * C_NF * NP + C_DELTA * NP + t] : 0.f;
-      learned_nu<HOOK>(W, sA, tcs, gr, Delta, t < Np, nut, Dt);
+      learned_nu<HOOK, TT>(W, sA, tcs, gr, Delta, t < Np, nut, Dt);
     }
     if (t < Np) write_f2(F2, e, t, L[L_RHO] + sv[0], nut, Dt, gr, sv, G, NP);
     __syncthreads();
   }
   if (CL == 2) {
     if (stalled) tcs.err = 1;
-    tc_teardown(tcs, P.flags + 1);
+    tc_teardown(tcs, P.flags + 1, tc_cols_for(TT));
   }
 }
 
@@ -483,10 +484,16 @@ cudaError_t launch_shadow32c(const double *Q64, float *S, float *TH, const KPara
 template <int N, int CL>
 static void grad32c_instance(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
   static int grid = 0;
-  if (!grid)
-    grid = CL == 2 ? grid_for_tc((const void *)k_grad32c<N, CL>, 1 << 30, kTcCols)
+  constexpr int dyn = grad32_dyn_bytes(N, CL);
+  if (!grid) {
+    if (dyn > 0)
+      cudaFuncSetAttribute((const void *)k_grad32c<N, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    grid = CL == 2 ? grid_for_tc((const void *)k_grad32c<N, CL>, 1 << 30, tc_cols_for((np32(N) + 127) / 128),
+                                 np32(N), dyn)
                    : grid_for((const void *)k_grad32c<N, CL>, 1 << 30, 0, np32(N));
-  if constexpr (CL == 2) {
+  }
+  // the test instance of hook 2 is built for the 128-thread CTAs
+  if constexpr (CL == 2 && N <= 4) {
     if (P.tc_stall == 2) {
       static int hgrid = 0;
       if (!hgrid) hgrid = grid_for_tc((const void *)k_grad32c<N, 2, true>, 1 << 30, kTcCols);
@@ -494,19 +501,15 @@ static void grad32c_instance(const float *S, const float *TH, float *F2, const K
       return;
     }
   }
-  k_grad32c<N, CL><<<grid < P.E ? grid : P.E, np32(N), 0, s>>>(S, TH, F2, P);
+  k_grad32c<N, CL><<<grid < P.E ? grid : P.E, np32(N), dyn, s>>>(S, TH, F2, P);
 }
 
-// the learned closure only up to N = 4 (cmles_create rejects it above)
 template <int N>
 static void grad32c_order(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
-  if constexpr (N <= 4) {
-    if (P.closure == 2) {
-      grad32c_instance<N, 2>(S, TH, F2, P, s);
-      return;
-    }
-  }
-  grad32c_instance<N, 1>(S, TH, F2, P, s);
+  if (P.closure == 2)
+    grad32c_instance<N, 2>(S, TH, F2, P, s);
+  else
+    grad32c_instance<N, 1>(S, TH, F2, P, s);
 }
 
 // the curvilinear kernels are instantiated for the orders 1 .. 7 (one thread

@@ -472,11 +472,12 @@ int grid_for(const void *fn, int E, size_t smem, int threads) {
   return (int)(g < E ? g : E);
 }
 
-// Persistent grid of a 128-thread kernel that allocates tmem_cols Tensor
-// Memory columns per CTA: the resident CTAs per SM from its registers and
-// shared memory (the occupancy query reports 1 for such kernels), capped so
-// that the resident CTAs' allocations fit in the SM's 512 columns.
-int grid_for_tc(const void *fn, int E, int tmem_cols) {
+// Persistent grid of a kernel of `threads` threads and dyn_smem bytes of
+// dynamic shared memory that allocates tmem_cols Tensor Memory columns per
+// CTA: the resident CTAs per SM from its registers and shared memory (the
+// occupancy query reports 1 for such kernels), capped so that the resident
+// CTAs' allocations fit in the SM's 512 columns.
+int grid_for_tc(const void *fn, int E, int tmem_cols, int threads, size_t dyn_smem) {
   int dev = 0, nsm = 0, regs_sm = 0, smem_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -487,9 +488,10 @@ int grid_for_tc(const void *fn, int E, int tmem_cols) {
     cudaGetLastError();
     return nsm < E ? nsm : E;
   }
-  const int regs_cta = ((a.numRegs * 32 + 255) / 256 * 256) * 4;  // 4 warps, 256-register granules
+  const int regs_cta = ((a.numRegs * 32 + 255) / 256 * 256) * (threads / 32);  // 256-register granules per warp
   int per = regs_cta > 0 ? regs_sm / regs_cta : 1;
-  const int smem_cta = (int)a.sharedSizeBytes + 1024;  // + the per-CTA reservation
+  if (2048 / threads < per) per = 2048 / threads;
+  const int smem_cta = (int)a.sharedSizeBytes + (int)dyn_smem + 1024;  // + the per-CTA reservation
   if (smem_cta > 0 && smem_sm / smem_cta < per) per = smem_sm / smem_cta;
   if (512 / tmem_cols < per) per = 512 / tmem_cols;
   if (per < 1) per = 1;

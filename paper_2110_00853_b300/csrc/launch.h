@@ -12,7 +12,7 @@ namespace cmles {
 // persistent grid: the resident CTAs per SM of fn (threads per CTA, dynamic
 // shared memory smem) times the SMs, at most E
 int grid_for(const void *fn, int E, size_t smem, int threads = 128);
-int grid_for_tc(const void *fn, int E, int tmem_cols);
+int grid_for_tc(const void *fn, int E, int tmem_cols, int threads = 128, size_t dyn_smem = 0);
 
 // FP64 path (dg_fp64.cu).  TH: the state's thermodynamic fields (p - p_r, c,
 // h_tot, theta_v; four planes per element), written with the state (the flux

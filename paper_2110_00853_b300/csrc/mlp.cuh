@@ -101,7 +101,10 @@ __device__ __forceinline__ uint32_t silu2_bf16(float x0, float x1) {
 // inputs occupy columns 0..15 (13 inputs, then three 1.0 bias columns).
 
 constexpr int kTcAElems = 128 * 8 * kTcKG;  // A buffer, BF16 elements (20 KB)
-constexpr int kTcCols = 64;                 // TMEM columns per CTA
+constexpr int kTcCols = 64;                 // TMEM columns per CTA (per row tile)
+// TMEM columns of a CTA with T row tiles of 128 rows: 64 per tile, the
+// allocation rounded up to a power of two
+__host__ __device__ constexpr int tc_cols_for(int T) { return T <= 1 ? 64 : (T == 2 ? 128 : 256); }
 constexpr int kTcWaitLimit = 1 << 20;       // mbarrier tries before giving up
 
 struct TcState {
@@ -123,9 +126,13 @@ __device__ __forceinline__ uint32_t &tc_pending() {
 // Write this thread's row of the A buffer for layer 1: the 13 inputs (BF16),
 // the three bias columns, and the bias and zero groups of layers 2 and 3
 // (columns 64..79; rewritten every time, so the buffer may share storage
-// with other data between calls).
+// with other data between calls).  With T row tiles (CTAs of more than 128
+// threads) thread t writes row t % 128 of tile t / 128, the tiles kTcAElems
+// apart.
+template <int T = 1>
 __device__ __forceinline__ void mlp_tc_put_input(__nv_bfloat16 *A, const float x[kMlpIn]) {
-  const int t = threadIdx.x;
+  const int t = T > 1 ? (int)(threadIdx.x & 127) : (int)threadIdx.x;
+  if (T > 1) A += (threadIdx.x >> 7) * kTcAElems;
   const uint32_t one2 = pack_bf16(1.0f, 1.0f);
   *reinterpret_cast<uint4 *>(A + tc_off(t, 0, kTcKG)) =
       make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
@@ -216,15 +223,23 @@ __device__ __forceinline__ void tc_group_close(TcState &s) {
   tc_wait_group(s);
 }
 
-// Forward pass of the CTA's 128 rows; (y0, y1) of this thread's row.  All
-// 128 threads must call it (it contains block barriers).  The A buffer's
+// Forward pass of the CTA's 128 T rows; (y0, y1) of this thread's row.  All
+// threads must call it (it contains block barriers).  The A buffer's
 // layer-1 columns must have been written by every thread and the bias and
-// zero groups (columns 64..79) set.
-template <bool HOOK = false>
+// zero groups (columns 64..79) set.  T row tiles (CTAs of more than 128
+// threads): thread 0 issues one chain per tile, tile q's A operand kTcAElems
+// elements after tile 0's and its accumulator in TMEM columns 64 q ..
+// 64 q + 63; thread t owns row t % 128 of tile t / 128, which its warp reads
+// in TMEM lane t % 128 (warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31).
+// Rows of the last tile beyond the CTA's threads are never written or read;
+// an MMA row depends on its own A row only.
+template <bool HOOK = false, int T = 1>
 __device__ __forceinline__ void mlp_tc_forward(const MlpTc &W, __nv_bfloat16 *A, TcState &s, float &y0,
                                                float &y1) {
   const int t = threadIdx.x;
-  const uint32_t lane_base = s.tmem + ((uint32_t)(t & ~31) << 16);
+  const int row = T > 1 ? (t & 127) : t;
+  const uint32_t lane_base = s.tmem + ((uint32_t)(row & ~31) << 16) + (T > 1 ? (uint32_t)(t >> 7) * kTcCols : 0u);
+  __nv_bfloat16 *Arow = T > 1 ? A + (t >> 7) * kTcAElems : A;
   constexpr uint32_t kSboA = 8 * 16 * kTcKG, kSbo1 = 8 * 16 * kTcKG1;
 #pragma unroll 1
   for (int layer = 0; layer < 3; ++layer) {
@@ -233,15 +248,20 @@ __device__ __forceinline__ void mlp_tc_forward(const MlpTc &W, __nv_bfloat16 *A,
     __syncthreads();
     if (t == 0 && !s.err) {
       tc_fence_after_sync();
-      if (layer == 0) {
-        tc_mma(s.tmem, tc_sdesc(A, 128, kSboA), tc_sdesc(W.W1, 128, kSbo1), tc_idesc_bf16(128, kMlpH), 0u);
-      } else {
-        const __nv_bfloat16 *B = layer == 1 ? W.W2 : W.W3;
-        const uint32_t idesc = tc_idesc_bf16(128, layer == 1 ? kMlpH : kTcN3);
 #pragma unroll
-        for (int ks = 0; ks < kTcKG / 2; ++ks)
-          tc_mma(s.tmem, tc_sdesc(A + ks * 128, 128, kSboA), tc_sdesc(B + ks * 128, 128, kSboA), idesc,
-                 ks > 0 ? 1u : 0u);
+      for (int q = 0; q < T; ++q) {
+        const __nv_bfloat16 *Aq = A + q * kTcAElems;
+        const uint32_t dq = s.tmem + (uint32_t)q * kTcCols;
+        if (layer == 0) {
+          tc_mma(dq, tc_sdesc(Aq, 128, kSboA), tc_sdesc(W.W1, 128, kSbo1), tc_idesc_bf16(128, kMlpH), 0u);
+        } else {
+          const __nv_bfloat16 *B = layer == 1 ? W.W2 : W.W3;
+          const uint32_t idesc = tc_idesc_bf16(128, layer == 1 ? kMlpH : kTcN3);
+#pragma unroll
+          for (int ks = 0; ks < kTcKG / 2; ++ks)
+            tc_mma(dq, tc_sdesc(Aq + ks * 128, 128, kSboA), tc_sdesc(B + ks * 128, 128, kSboA), idesc,
+                   ks > 0 ? 1u : 0u);
+        }
       }
       tc_commit(s.mbar);
     }
@@ -266,7 +286,7 @@ __device__ __forceinline__ void mlp_tc_forward(const MlpTc &W, __nv_bfloat16 *A,
         uint32_t w[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) w[q] = silu2_bf16(v[2 * q], v[2 * q + 1]);
-        *reinterpret_cast<uint4 *>(A + tc_off(t, 8 * h, kTcKG)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(Arow + tc_off(row, 8 * h, kTcKG)) = make_uint4(w[0], w[1], w[2], w[3]);
       }
     } else if (skip) {
       y0 = y1 = 0.f;

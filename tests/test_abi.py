@@ -76,8 +76,7 @@ def test_create_rejects_unsupported_combinations_without_gpu_work():
 
 def test_create_order_limits_without_gpu_work():
     """Both precisions take the orders 1 .. 7 on flat meshes and the FP32
-    path on warped meshes (the instantiated kernels), the learned closure
-    1 .. 4 (one 128-row tensor-core tile per element); HEVI only 4; other
+    path on warped meshes (the instantiated kernels); HEVI only 4; other
     orders are rejected before any device work."""
     L = cmles.load()
     h = ctypes.c_void_p()
@@ -91,10 +90,8 @@ def test_create_order_limits_without_gpu_work():
         assert status(N) == 1
     for N in (0, 8):
         assert status(N, "fp32") == 1
-    for N in (5, 6, 7):
-        assert status(N, "fp32", closure="mlp") == 1
+    assert status(8, "fp32", closure="mlp") == 1
     assert status(5, integrator="ark2_hevi") == 1
-    assert status(5, "fp32", warp=True, closure="mlp") == 1
     assert status(8, "fp32", warp=True) == 1
     assert status(3, integrator="ark2_hevi") == 1
 

@@ -148,14 +148,16 @@ def test_warped_other_orders_tendency_and_steps(orc, N, flux):
         assert abs(b1[v] - b0[v]) <= 1e-10 * abs(b0[v]), v
 
 
-def test_warped_tendency_with_learned_closure(orc):
+@pytest.mark.parametrize("N", [4, 6])
+def test_warped_tendency_with_learned_closure(orc, N):
     """The curvilinear gradient pass with the learned closure on the tcgen05
     tensor cores (BF16 network, per-node Delta of the curved elements)
     against the oracle's BF16-defined network: bound 1e-4 relative L2, as
     on the flat mesh (a hidden activation can round to the neighbouring BF16
-    value)."""
+    value).  At N = 6 each element's 343 rows are three tiles of 128 rows
+    (three MMA chains per layer, TMEM column blocks 0, 64, 128)."""
     from paper_2110_00853_b300 import cmles
-    m = _hill_box()
+    m = _hill_box(N=N) if N <= 4 else _hill_box(6, 2, 6, N=N)
     ph = _phys(m)
     ph["closure"] = "mlp"
     S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case("c3"))
@@ -180,7 +182,7 @@ def test_warped_tendency_with_learned_closure(orc):
     G.set_closure_weights(flat)
     R_gpu = G.tendency(torch.from_numpy(Q).cuda()).cpu().numpy()
     errs = [_rel(R_gpu[:, v], R_orc[:, v]) for v in range(5)]
-    print("warped fp32 learned closure rel L2", errs)
+    print("warped fp32 learned closure N", N, "rel L2", errs)
     assert G.diagnostics(raise_on_error=False)["status"] == 0
     for v in range(5):
         assert errs[v] <= 1e-4, (v, errs)
