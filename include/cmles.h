@@ -86,8 +86,7 @@ enum { CMLES_FP64 = 0, CMLES_FP32_ACC64 = 1 };
  * z_s(x) = hill_h exp(-((x - hill_xc)/hill_a)^2): elements stacked over the
  * terrain with linear damping to a flat top (Sec. 4.3). */
 typedef struct {
-  int N;                 /* polynomial order: 1..7 on flat and warped meshes,
-                            4 with HEVI */
+  int N;                 /* polynomial order, 1..7 */
   int nex, ney, nez;
   double x0, y0, z0;
   double Lx, Ly, Lz;

@@ -709,10 +709,9 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
                                        cmles_handle *out) {
   if (!mesh || !params || !out) return CMLES_ERR_ARG;
   *out = nullptr;
-  // the kernels are instantiated for the orders 1 .. 7 on flat meshes in
-  // both precisions and on warped meshes (FP32), and for 4 with HEVI
+  // the kernels are instantiated for the orders 1 .. 7: flat meshes in both
+  // precisions, warped meshes (FP32), HEVI
   if (mesh->N < 1 || mesh->N > 7) return CMLES_ERR_ARG;
-  if (params->integrator == CMLES_ARK2_HEVI && mesh->N != 4) return CMLES_ERR_ARG;
   if (mesh->nex < 1 || mesh->ney < 1 || mesh->nez < 1 || !(mesh->Lx > 0) || !(mesh->Ly > 0) || !(mesh->Lz > 0))
     return CMLES_ERR_MESH;
   // warped (curvilinear) meshes run on the FP32 path
@@ -1365,6 +1364,7 @@ cmles_status ensure_hevi(cmles_handle h) {
   if (h->hv_dt == h->prm.dt) return CMLES_OK;
   const int nez = h->mesh.nez, Nq = h->Nq, nlev = nez * Nq;
   HeviSetup S{};
+  S.N = h->N;
   S.nez = nez;
   S.hz = h->K.hz;
   for (int a = 0; a < Nq; ++a) S.w[a] = h->w[a];

@@ -14,9 +14,9 @@
 // in strong-form nodal DG along z with a Rusanov flux at the reference sound
 // speed c_r (walls mirror rho w); the horizontal momentum and rho q_t keep
 // only that flux's dissipation on the z-faces.  The same operator holds on
-// every vertical line, so its element blocks (15 x 15 for the three coupled
-// unknowns at the five LGL levels of an element) are assembled once on the
-// host, and I - dt gamma L is factored there by block Gaussian elimination
+// every vertical line, so its element blocks (3 (N+1) x 3 (N+1) for the three
+// coupled unknowns at the N + 1 LGL levels of an element, 15 x 15 at N = 4)
+// are assembled once on the host, and I - dt gamma L is factored there by block Gaussian elimination
 // of the block-tridiagonal line matrix.  The kernels below apply L and solve
 // with the factors, one thread per vertical line of nodes.
 #include <math.h>
@@ -29,10 +29,11 @@
 
 namespace cmles {
 
-constexpr int kHB = 15;  // coupled unknowns per element on a line: 5 levels x (rho', rho w, rho e')
+// coupled unknowns per element on a line: N + 1 levels x (rho', rho w, rho e')
+__host__ __device__ constexpr int hevi_hb(int N) { return 3 * (N + 1); }
 
+template <int Nq>
 __device__ __forceinline__ void hevi_line(const KParams &P, long long line, int &ex, int &ey, int &n0) {
-  constexpr int Nq = 5;
   const int ij = (int)(line % (Nq * Nq));
   const long long col = line / (Nq * Nq);
   ex = (int)(col % P.nex);
@@ -40,24 +41,32 @@ __device__ __forceinline__ void hevi_line(const KParams &P, long long line, int 
   n0 = ij;  // i + Nq j: the line's node index at level k is n0 + Nq^2 k
 }
 
-// Per-level table layout (doubles): the diagonal block of L (15 x 15), the
-// two face-coupling blocks of L (3 x 3: rows of the element's bottom level
-// against the lower element's top level, rows of the top level against the
-// upper element's bottom level; every other entry of L's off-diagonal blocks
-// is zero), the inverse G of the elimination's diagonal block (15 x 15) and
-// the three nonzero columns of the back-substitution block E = G C^M (15 x 3).
-constexpr int kTB = 0, kTA = 225, kTC = 234, kTG = 243, kTE = 468, kTStride = 513;
+// Per-level table layout (doubles), HB = hevi_hb(N): the diagonal block of L
+// (HB x HB), the two face-coupling blocks of L (3 x 3: rows of the element's
+// bottom level against the lower element's top level, rows of the top level
+// against the upper element's bottom level; every other entry of L's
+// off-diagonal blocks is zero), the inverse G of the elimination's diagonal
+// block (HB x HB) and the three nonzero columns of the back-substitution
+// block E = G C^M (HB x 3).  At N = 4: offsets 0, 225, 234, 243, 468, stride 513.
+__host__ __device__ constexpr int hevi_tB(int) { return 0; }
+__host__ __device__ constexpr int hevi_tA(int N) { return hevi_hb(N) * hevi_hb(N); }
+__host__ __device__ constexpr int hevi_tC(int N) { return hevi_tA(N) + 9; }
+__host__ __device__ constexpr int hevi_tG(int N) { return hevi_tC(N) + 9; }
+__host__ __device__ constexpr int hevi_tE(int N) { return hevi_tG(N) + hevi_hb(N) * hevi_hb(N); }
+__host__ __device__ constexpr int hevi_stride(int N) { return hevi_tE(N) + 3 * hevi_hb(N); }
 
 // out = L (Q - Q_ref) on every vertical line (all six components).
+template <int N>
 __global__ void k_hevi_apply(const double *__restrict__ Q, double *__restrict__ out, const HeviTables T,
                              const KParams P) {
-  constexpr int Nq = 5, Np = 125, Nf = 25;
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq, kHB = hevi_hb(N), kTB = hevi_tB(N),
+                kTA = hevi_tA(N), kTC = hevi_tC(N), kTStride = hevi_stride(N), kTop = 3 * N;
   const long long nlines = (long long)P.nex * P.ney * Nf;
   const size_t slab = (size_t)P.nex * P.ney;
   for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < nlines;
        line += (long long)gridDim.x * blockDim.x) {
     int ex, ey, n0;
-    hevi_line(P, line, ex, ey, n0);
+    hevi_line<Nq>(P, line, ex, ey, n0);
     const size_t e0 = (size_t)ex + (size_t)P.nex * ey;
     auto load = [&](int ez, double *y) {
       const size_t e = e0 + slab * ez;
@@ -89,7 +98,7 @@ __global__ void k_hevi_apply(const double *__restrict__ Q, double *__restrict__ 
       if (ez + 1 < P.nez)
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-          r[12 + a] += Tz[kTC + 3 * a] * yn[0] + Tz[kTC + 3 * a + 1] * yn[1] + Tz[kTC + 3 * a + 2] * yn[2];
+          r[kTop + a] += Tz[kTC + 3 * a] * yn[0] + Tz[kTC + 3 * a + 1] * yn[1] + Tz[kTC + 3 * a + 2] * yn[2];
       const size_t e = e0 + slab * ez;
 #pragma unroll
       for (int k = 0; k < Nq; ++k) {
@@ -114,7 +123,7 @@ __global__ void k_hevi_apply(const double *__restrict__ Q, double *__restrict__ 
         }
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) ytop_prev[c] = yc[12 + c];
+      for (int c = 0; c < 3; ++c) ytop_prev[c] = yc[kTop + c];
 #pragma unroll
       for (int a = 0; a < kHB; ++a) yc[a] = yn[a];
     }
@@ -122,15 +131,17 @@ __global__ void k_hevi_apply(const double *__restrict__ Q, double *__restrict__ 
 }
 
 // Y = Q_ref + (I - dt gamma L)^-1 (B - Q_ref) on every vertical line.
+template <int N>
 __global__ void k_hevi_solve(const double *__restrict__ Bv, double *__restrict__ Y, const HeviTables T,
                              const KParams P) {
-  constexpr int Nq = 5, Np = 125, Nf = 25;
+  constexpr int Nq = N + 1, Np = Nq * Nq * Nq, Nf = Nq * Nq, kHB = hevi_hb(N), kTA = hevi_tA(N),
+                kTG = hevi_tG(N), kTE = hevi_tE(N), kTStride = hevi_stride(N), kTop = 3 * N;
   const long long nlines = (long long)P.nex * P.ney * Nf;
   const size_t slab = (size_t)P.nex * P.ney;
   for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < nlines;
        line += (long long)gridDim.x * blockDim.x) {
     int ex, ey, n0;
-    hevi_line(P, line, ex, ey, n0);
+    hevi_line<Nq>(P, line, ex, ey, n0);
     const size_t e0 = (size_t)ex + (size_t)P.nex * ey;
     // forward sweep of the block elimination: y_ez = G_ez (b_ez - A^M_ez y_ez-1)
     // with A^M = -dt gamma A^L (nonzero on the face levels only); y kept in Y
@@ -167,7 +178,7 @@ __global__ void k_hevi_solve(const double *__restrict__ Bv, double *__restrict__
         Y[(e * 6 + 4) * Np + n] = y[3 * k + 2];
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) ytop[c] = y[12 + c];
+      for (int c = 0; c < 3; ++c) ytop[c] = y[kTop + c];
     }
     // back sweep: x_ez = y_ez - E_ez x_ez+1 (E nonzero in the columns of the
     // upper element's bottom level), then Y = Q_ref + x
@@ -246,15 +257,44 @@ static int line_grid(long long nlines) {
   return (int)(b < 148 * 16 ? b : 148 * 16);
 }
 
+// one thread per vertical line of nodes, (N+1)^2 lines per element column;
+// the line kernels are instantiated for the orders 1 .. 7
+template <int N>
+static void hevi_apply_order(const double *Q, double *out, const HeviTables &T, const KParams &P, cudaStream_t s) {
+  const long long nlines = (long long)P.nex * P.ney * (N + 1) * (N + 1);
+  k_hevi_apply<N><<<line_grid(nlines), 128, 0, s>>>(Q, out, T, P);
+}
+template <int N>
+static void hevi_solve_order(const double *B, double *Y, const HeviTables &T, const KParams &P, cudaStream_t s) {
+  const long long nlines = (long long)P.nex * P.ney * (N + 1) * (N + 1);
+  k_hevi_solve<N><<<line_grid(nlines), 128, 0, s>>>(B, Y, T, P);
+}
+
 cudaError_t launch_hevi_apply(const double *Q, double *out, const HeviTables &T, const KParams &P, cudaStream_t s) {
-  const long long nlines = (long long)P.nex * P.ney * 25;
-  k_hevi_apply<<<line_grid(nlines), 128, 0, s>>>(Q, out, T, P);
+  switch (P.N) {
+    case 1: hevi_apply_order<1>(Q, out, T, P, s); break;
+    case 2: hevi_apply_order<2>(Q, out, T, P, s); break;
+    case 3: hevi_apply_order<3>(Q, out, T, P, s); break;
+    case 4: hevi_apply_order<4>(Q, out, T, P, s); break;
+    case 5: hevi_apply_order<5>(Q, out, T, P, s); break;
+    case 6: hevi_apply_order<6>(Q, out, T, P, s); break;
+    case 7: hevi_apply_order<7>(Q, out, T, P, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_hevi_solve(const double *B, double *Y, const HeviTables &T, const KParams &P, cudaStream_t s) {
-  const long long nlines = (long long)P.nex * P.ney * 25;
-  k_hevi_solve<<<line_grid(nlines), 128, 0, s>>>(B, Y, T, P);
+  switch (P.N) {
+    case 1: hevi_solve_order<1>(B, Y, T, P, s); break;
+    case 2: hevi_solve_order<2>(B, Y, T, P, s); break;
+    case 3: hevi_solve_order<3>(B, Y, T, P, s); break;
+    case 4: hevi_solve_order<4>(B, Y, T, P, s); break;
+    case 5: hevi_solve_order<5>(B, Y, T, P, s); break;
+    case 6: hevi_solve_order<6>(B, Y, T, P, s); break;
+    case 7: hevi_solve_order<7>(B, Y, T, P, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -304,7 +344,8 @@ bool invert(int n, const double *M, double *inv) {
 }  // namespace
 
 bool hevi_build(const HeviSetup &S, HeviHost &H) {
-  constexpr int Nq = 5, N = 4;
+  const int N = S.N, Nq = N + 1, kHB = hevi_hb(N), kTB = hevi_tB(N), kTA = hevi_tA(N), kTC = hevi_tC(N),
+            kTG = hevi_tG(N), kTE = hevi_tE(N), kTStride = hevi_stride(N), kTop = 3 * N;
   const int nez = S.nez, nlev = nez * Nq;
   const double jz = 2.0 / S.hz;
   H.lift = 2.0 / (S.hz * S.w[0]);
@@ -322,7 +363,7 @@ bool hevi_build(const HeviSetup &S, HeviHost &H) {
     H.lev[4 * l + 1] = rer;
     H.lev[4 * l + 2] = cr[l];
   }
-  // blocks of L: [ez][sub, diag, super][15 x 15], row/col index 3 k + c
+  // blocks of L: [ez][sub, diag, super][kHB x kHB], row/col index 3 k + c
   H.Lb.assign((size_t)nez * 3 * kHB * kHB, 0.0);
   auto dF = [&](int l, int c, int cc) {  // d F_c / d y_cc at level node l
     if (c == 0) return cc == 1 ? 1.0 : 0.0;
@@ -401,12 +442,12 @@ bool hevi_build(const HeviSetup &S, HeviHost &H) {
     }
     for (int i = 0; i < kHB; ++i)
       for (int j = 0; j < kHB; ++j) {
-        const bool a_face = i < 3 && j >= 12, c_face = i >= 12 && j < 3, e_col = j < 3;
+        const bool a_face = i < 3 && j >= kTop, c_face = i >= kTop && j < 3, e_col = j < 3;
         if ((A[i * kHB + j] != 0.0 && !a_face) || (C[i * kHB + j] != 0.0 && !c_face) ||
             (E[i * kHB + j] != 0.0 && !e_col))
           return false;
-        if (a_face) Tz[kTA + 3 * i + (j - 12)] = A[i * kHB + j];
-        if (c_face) Tz[kTC + 3 * (i - 12) + j] = C[i * kHB + j];
+        if (a_face) Tz[kTA + 3 * i + (j - kTop)] = A[i * kHB + j];
+        if (c_face) Tz[kTC + 3 * (i - kTop) + j] = C[i * kHB + j];
         if (e_col) Tz[kTE + 3 * i + j] = E[i * kHB + j];
       }
   }

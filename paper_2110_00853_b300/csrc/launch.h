@@ -59,7 +59,7 @@ struct HeviTables {
   double lift, dtg;   // 2 / (h_z w_0), dt gamma
 };
 struct HeviSetup {
-  int nez;
+  int N, nez;
   double hz, w[kMaxQ], D[kMaxQ * kMaxQ];
   const double *rho_r, *p_r, *qt_r, *z;  // per level node (nez (N+1)); qt_r may be null (0)
   double g, Rd, Rv, cvd, cvv, T0, Iv0, dtg;

@@ -75,9 +75,9 @@ def test_create_rejects_unsupported_combinations_without_gpu_work():
 
 
 def test_create_order_limits_without_gpu_work():
-    """Both precisions take the orders 1 .. 7 on flat meshes and the FP32
-    path on warped meshes (the instantiated kernels); HEVI only 4; other
-    orders are rejected before any device work."""
+    """Both precisions take the orders 1 .. 7 on flat meshes, the FP32 path
+    on warped meshes, and HEVI (the instantiated kernels); other orders are
+    rejected before any device work."""
     L = cmles.load()
     h = ctypes.c_void_p()
 
@@ -91,9 +91,8 @@ def test_create_order_limits_without_gpu_work():
     for N in (0, 8):
         assert status(N, "fp32") == 1
     assert status(8, "fp32", closure="mlp") == 1
-    assert status(5, integrator="ark2_hevi") == 1
+    assert status(8, integrator="ark2_hevi") == 1
     assert status(8, "fp32", warp=True) == 1
-    assert status(3, integrator="ark2_hevi") == 1
 
 
 def test_host_download_calls_reject_a_null_handle_without_gpu_work():

@@ -4,7 +4,7 @@ implicit, its block-tridiagonal line solves and the explicit remainder,
 against the oracle's ARK2 (dense solves of the same operator assembled by
 applying it to unit vectors): step increments to 1e-11 relative L2 on the
 bubble box, and on thin elements at a step beyond the explicit vertical
-acoustic limit."""
+acoustic limit; the operator, the line solve and steps at N = 2, 3, 5, 7."""
 import numpy as np
 import pytest
 
@@ -150,3 +150,42 @@ def test_hevi_fp32_path_tracks_oracle(orc, case):
     errs = [_rel(Qg[:, v] - Q[:, v], Qo[:, v] - Q[:, v]) for v in range(6) if np.abs(Qo[:, v] - Q[:, v]).max() > 0]
     print("HEVI FP32", case, "3 steps rel L2", errs)
     assert max(errs) <= 1e-5, errs
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 7])
+def test_hevi_other_orders_operator_solve_and_steps(orc, N):
+    """The line kernels at orders other than 4 (3 (N+1) coupled unknowns per
+    element on a line, the per-level table sized by N): the operator and the
+    line solve on the bubble box against the oracle's, then three ARK2 steps
+    (the step scaled with the smallest node spacing)."""
+    from paper_2110_00853_b300 import cmles
+    m, c = dict(I.mesh("c1"), N=N), I.case("c1")
+    ph = dict(I.physics("c1"), integrator="ark2_hevi")
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, c)
+    qlev, qnodes = _qt_reference(S, Q, m)
+    S.set_reference_qt(qnodes)
+    rng = np.random.default_rng(5)
+    u = rng.uniform(-0.5, 0.5, size=(Q.shape[0], 3, Q.shape[2]))
+    Q = Q.copy()
+    Q[:, 4] += 0.5 * Q[:, 0] * (u ** 2).sum(1) + (Q[:, 1:4] * u).sum(1)
+    Q[:, 1:4] += Q[:, 0][:, None] * u
+    G = cmles.Solver(m, ph, precision="fp64")
+    G.set_reference(_levels(rr, m), _levels(pr, m), qlev)
+    Qd = torch.from_numpy(Q).cuda()
+    Lg, Lo = G.hevi_operator(Qd).cpu().numpy(), S.vlin(Q)
+    errs = [_rel(Lg[:, v], Lo[:, v]) for v in range(6) if np.abs(Lo[:, v]).max() > 0]
+    print("N", N, "operator rel L2", errs)
+    assert max(errs) <= 1e-13, errs
+    Qr = S.vlin_reference()
+    _, Ai, _ = orc.ark2_tableaux()
+    M = np.eye(6 * m["nez"] * (N + 1)) - ph["dt"] * Ai[1, 1] * S.hevi_line_matrix()
+    Yo, Yg = S._hevi_solve(M, Q, Qr), G.hevi_solve(Qd).cpu().numpy()
+    errs = [_rel(Yg[:, v] - Qr[:, v], Yo[:, v] - Qr[:, v]) for v in range(6)]
+    print("N", N, "solve rel L2", errs)
+    assert errs[0] <= 1e-10 and max(errs[1:]) <= 1e-12, errs
+    G.close()
+    dt = 0.02 * min(1.0, (4.0 / N) ** 2)
+    Q0, Qo, Qg = _run(orc, m, I.physics("c1"), c, 3, dt, fuzz=1.0)
+    errs = [_rel(Qg[:, v] - Q0[:, v], Qo[:, v] - Q0[:, v]) for v in range(6) if np.abs(Qo[:, v] - Q0[:, v]).max() > 0]
+    print("N", N, "HEVI 3 steps rel L2", errs)
+    assert max(errs) <= 1e-11, errs
