@@ -384,7 +384,8 @@ cmles_status cmles_hevi_solve(cmles_handle h, const double *B_dev, double *Y_dev
  *           MMA is still in flight (a test instance of the pass); the CTA
  *           issues no further MMA, reads no Tensor Memory (results invalid),
  *           and at its tear-down waits (bounded) for that MMA's completion
- *           before freeing the columns.
+ *           before freeing the columns.  The test instance exists for the
+ *           128-thread CTAs of N <= 4; above, mode 2 gives CMLES_ERR_ARG.
  * Either way the next cmles_diagnostics returns CMLES_ERR_TIMEOUT with
  * cmles_diag.tc_timeouts = the number of CTAs that gave up (each counted
  * once).  Mode 0 restores normal operation; other values give

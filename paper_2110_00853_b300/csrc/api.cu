@@ -1674,6 +1674,8 @@ cmles_status cmles_hevi_solve(cmles_handle h, const double *B_dev, double *Y_dev
 cmles_status cmles_test_stall_tc(cmles_handle h, int enable) {
   if (!h) return CMLES_ERR_ARG;
   if (enable < 0 || enable > 2) return fail(h, CMLES_ERR_ARG, "cmles_test_stall_tc: mode must be 0, 1 or 2");
+  if (enable == 2 && h->N > 4)
+    return fail(h, CMLES_ERR_ARG, "cmles_test_stall_tc: mode 2 has its test instance for N <= 4 only");
   h->tc_stall = enable;
   h->K.tc_stall = h->tc_stall;
   return CMLES_OK;

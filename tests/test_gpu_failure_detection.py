@@ -153,6 +153,37 @@ def test_tensor_core_drain_after_a_wait_gives_up(orc):
         G.test_stall_tc(3)
 
 
+def test_tensor_core_wait_timeout_with_several_row_tiles(orc):
+    """The same bounded wait in the learned pass above N = 4 (224-thread
+    CTAs, two 128-row tiles and 128 Tensor Memory columns each): every CTA
+    counted once, the tendency unchanged, the next report clean; mode 2,
+    whose test instance is built for 128-thread CTAs, is refused."""
+    from paper_2110_00853_b300 import cmles
+    m = I.sub_mesh("c2", 3, 2, 4, N=5)
+    ph = I.physics("c2", closure="mlp")
+    S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case("c2"))
+    rng = np.random.default_rng(6)
+    G = cmles.Solver(m, ph, precision="fp32")
+    G.set_reference(_levels(rr, m), _levels(pr, m), _levels(Q[:, 5] / Q[:, 0], m))
+    flat = np.concatenate([rng.normal(size=5186) * 0.1, np.ones(13), [1.0, 1.0]]).astype(np.float32)
+    G.set_closure_weights(flat)
+    Qd = torch.from_numpy(Q).cuda()
+    R0 = G.tendency(Qd).cpu().numpy()
+    assert G.diagnostics(raise_on_error=False)["status"] == 0
+    G.test_stall_tc(1)
+    R1 = G.tendency(Qd).cpu().numpy()
+    d = G.diagnostics(raise_on_error=False)
+    assert d["status"] == ERR_TIMEOUT and d["tc_timeouts"] == G.E, (d["tc_timeouts"], G.E)
+    assert np.array_equal(R1, R0)
+    G.test_stall_tc(0)
+    R2 = G.tendency(Qd).cpu().numpy()
+    d = G.diagnostics(raise_on_error=False)
+    assert d["status"] == 0 and d["tc_timeouts"] == 0
+    assert np.array_equal(R2, R0)
+    with pytest.raises(cmles.CmlesError):
+        G.test_stall_tc(2)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_condensate_below_freezing_is_counted_not_an_error(orc, precision):
     """The saturation adjustment keeps all condensate liquid (no ice phase).
