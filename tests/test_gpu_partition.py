@@ -69,6 +69,10 @@ CASES = [
     # walls in z with the drag law and no-slip ghosts, which every partition holds
     ("moist layer, fp64 no-slip and drag", I.sub_mesh("c2", 6, 4, 3), "fp64", "sl+walls", (3, 2)),
     ("moist layer, fp32 no-slip and drag", I.sub_mesh("c2", 8, 4, 3), "fp32", "sl+walls", (2, 2)),
+    # orders above 4: CTAs of more than 128 threads, FP32 arrays padded to np32(N) nodes
+    ("moist layer, fp32 order 5", I.sub_mesh("c2", 4, 4, 3, N=5), "fp32", "sl", (2, 2)),
+    ("moist layer, fp32 learned closure order 6", I.sub_mesh("c2", 4, 3, 2, N=6), "fp32", "mlp", (2, 1)),
+    ("moist layer, fp64 order 7", I.sub_mesh("c2", 4, 3, 2, N=7), "fp64", "vreman", (2, 3)),
 ]
 
 
