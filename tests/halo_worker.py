@@ -105,6 +105,7 @@ def main():
         (dict(N=3, nex=5, ney=3, nez=2, Lx=5.0, Ly=3.0, Lz=2.0, periodic=(0, 1, 0)), 2, 1),
         (dict(N=2, nex=3, ney=5, nez=3, Lx=3.0, Ly=5.0, Lz=3.0, periodic=(1, 1, 0)), 1, 2),
         (dict(N=4, nex=4, ney=4, nez=1, Lx=4.0, Ly=4.0, Lz=1.0, periodic=(1, 0, 0)), 1, 2),
+        (dict(N=6, nex=4, ney=3, nez=2, Lx=4.0, Ly=3.0, Lz=2.0, periodic=(1, 1, 0)), 2, 1),
     ]
     for mesh, px, py in cases:
         out.append(dict(px=px, py=py, periodic=mesh["periodic"], **run_case(mesh, px, py, rank, world)))

@@ -12,6 +12,7 @@ import subprocess
 import sys
 
 import numpy as np
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
@@ -54,10 +55,11 @@ def test_two_rank_halo_exchange(tmp_path):
             assert sorted(c["walls"]) == [s for s in range(4) if nb[s] < 0]
 
 
-def test_halo_plan_counts_and_ranges():
+@pytest.mark.parametrize("N", [4, 7])
+def test_halo_plan_counts_and_ranges(N):
     from paper_2110_00853_b300 import cmles
-    mesh = dict(N=4, nex=7, ney=5, nez=3, Lx=7.0, Ly=5.0, Lz=3.0, periodic=(1, 0, 0))
-    Np = 125
+    mesh = dict(N=N, nex=7, ney=5, nez=3, Lx=7.0, Ly=5.0, Lz=3.0, periodic=(1, 0, 0))
+    Np, Nf = (N + 1) ** 3, (N + 1) ** 2
     total_send = 0
     for rank in range(3 * 2):
         nb, cnt, send, recv = cmles.halo_plan(mesh, 3, 2, rank)
@@ -69,7 +71,7 @@ def test_halo_plan_counts_and_ranges():
         assert nb[2] == (-1 if iy == 0 else rank - 3) and nb[3] == (-1 if iy == 1 else rank + 3)
         for s in range(4):
             along = ny if s < 2 else nx
-            assert cnt[s] == (0 if nb[s] < 0 else 3 * along * 25)
+            assert cnt[s] == (0 if nb[s] < 0 else 3 * along * Nf)
             if cnt[s]:
                 assert send[s].min() >= 0 and send[s].max() < Es * Np
                 assert recv[s].min() >= 0 and recv[s].max() < Es * Np
