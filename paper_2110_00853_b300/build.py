@@ -1,13 +1,17 @@
 """Build the cmles CUDA library in-tree (paper_2110_00853_b300/libcmles.so).
 
 All kernels are compiled for sm_103a only:
-  nvcc -gencode arch=compute_103a,code=sm_103a -O3 -lineinfo -shared -Xcompiler -fPIC
-The library exports the C ABI of include/cmles.h and links the CUDA runtime
-statically, so it loads without a toolkit on the library path.
+  nvcc -gencode arch=compute_103a,code=sm_103a -O3 -lineinfo -Xcompiler -fPIC -c <file>.cu
+one process per source file in parallel (each file is self-contained: no
+device code crosses files), then linked with -shared.  The library exports
+the C ABI of include/cmles.h and links the CUDA runtime statically, so it
+loads without a toolkit on the library path.
 """
 import os
 import subprocess
 import sys
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -32,13 +36,23 @@ def build(force=False, verbose=False):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in _deps()):
             return LIB
-    cmd = [NVCC] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-                           "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-cudart", "static",
-                           "-o", LIB] + sources()
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
+                    "-I" + CSRC]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd))
-    subprocess.check_call(cmd)
+        flags.insert(0, "-Xptxas=-v")
+    with tempfile.TemporaryDirectory() as tmp:
+        objs = [os.path.join(tmp, os.path.basename(src) + ".o") for src in sources()]
+        cmds = [[NVCC] + flags + ["-c", src, "-o", obj] for src, obj in zip(sources(), objs)]
+        if verbose:
+            for c in cmds:
+                print(" ".join(c))
+        with ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as ex:
+            codes = list(ex.map(subprocess.call, cmds))
+        for c, rc in zip(cmds, codes):
+            if rc:
+                raise subprocess.CalledProcessError(rc, c)
+        link = [NVCC] + ARCH + ["-shared", "-cudart", "static", "-o", LIB] + objs
+        subprocess.check_call(link)
     return LIB
 
 
