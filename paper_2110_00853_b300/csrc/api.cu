@@ -366,6 +366,7 @@ cmles_status build_curved(cmles_handle h) {
   h->hJ_.resize((size_t)E * Np);
   h->hJa_.resize((size_t)E * Np * 9);
   h->hdelta_.resize(E);
+  h->hvr_.resize((size_t)E * 3);
   std::vector<float> geo((size_t)E * 10 * np, 0.0f);
   std::vector<double> wJ((size_t)E * Np);
   std::vector<double> X(3 * Np), dX(9 * Np), V(3 * Np);
@@ -394,6 +395,16 @@ cmles_status build_curved(cmles_handle h) {
       X[2 * Np + n] = z;
       h->hx_[e * Np + n] = x;
       h->hz_[e * Np + n] = z;
+    }
+    // Vreman's directional lengths: the extent of the element's nodes along
+    // x, y and z over N (reading for a curved element: its bounding box)
+    for (int c = 0; c < 3; ++c) {
+      double lo = X[c * Np], hi = X[c * Np];
+      for (int n = 1; n < Np; ++n) {
+        lo = fmin(lo, X[c * Np + n]);
+        hi = fmax(hi, X[c * Np + n]);
+      }
+      h->hvr_[e * 3 + c] = ((hi - lo) / h->N) * ((hi - lo) / h->N);
     }
     // metrics from element-local coordinates (the curl form is translation
     // invariant; local coordinates keep the rounding independent of position)
@@ -504,8 +515,9 @@ cmles_status curved_reference(cmles_handle h, const double *rho_r, const double 
       T[L_QM * np] = (float)q;
       T[L_RVS * np] = (float)rhovsat64(h, Tr);
       const double delta = h->hdelta_[e];
-      T[(NF - 2) * np] = (float)delta;
-      T[(NF - 1) * np] = (float)((p.Cs * delta) * (p.Cs * delta));
+      T[kCurvedDelta * np] = (float)delta;
+      T[kCurvedCsd2 * np] = (float)((p.Cs * delta) * (p.Cs * delta));
+      for (int c = 0; c < 3; ++c) T[(kCurvedVr + c) * np] = (float)(h->hvr_[e * 3 + c]);
     }
     // reference gradients: (1/J) sum_r (J a^r)_c d/dxi_r
     const double *fields[3] = {hr.data(), qr.data(), thr.data()};
@@ -732,8 +744,6 @@ cmles_status cmles_host::create_handle(const cmles_mesh *mesh, const cmles_param
   // HEVI: flat meshes with walls at the bottom and top
   if (params->integrator == CMLES_ARK2_HEVI && (mesh->warp || mesh->periodic[2] || mesh->nez < 2))
     return CMLES_ERR_ARG;
-  // Vreman's directional lengths are those of the flat elements
-  if (params->closure == CMLES_CLOSURE_VREMAN && mesh->warp) return CMLES_ERR_ARG;
   // the learned closure runs on BF16 tensor cores inside the FP32 kernels
   if (params->closure == CMLES_CLOSURE_MLP && params->precision != CMLES_FP32_ACC64) return CMLES_ERR_ARG;
   long long E = (long long)mesh->nex * mesh->ney * mesh->nez;

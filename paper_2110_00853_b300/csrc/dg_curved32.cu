@@ -23,9 +23,13 @@
 namespace cmles {
 
 // per-node table fields beyond the level-table layout: x and y components of
-// the reference gradients of h_r, q_r and theta_v,r
-// and the per-element filter width Delta and (C_s Delta)^2
-enum { C_DX_HM = L_NF, C_DY_HM, C_DX_Q, C_DY_Q, C_DX_THV, C_DY_THV, C_DELTA, C_CSD2, C_NF = 24 };
+// the reference gradients of h_r, q_r and theta_v,r, the per-element filter
+// width Delta and (C_s Delta)^2, and Vreman's squared directional lengths
+// Delta_m^2 of the element (its nodes' extent along x, y, z over N)
+enum { C_DX_HM = L_NF, C_DY_HM, C_DX_Q, C_DY_Q, C_DX_THV, C_DY_THV, C_DELTA, C_CSD2, C_VR, C_NF = C_VR + 3 };
+static_assert((int)C_NF == (int)kCurvedNF && (int)C_DELTA == (int)kCurvedDelta && (int)C_CSD2 == (int)kCurvedCsd2 &&
+                  (int)C_VR == (int)kCurvedVr,
+              "node table layout shared with the host");
 
 // np: padded nodes per element of the FP32 arrays and tables (np32(N))
 __device__ __forceinline__ void load_node_table(const float *__restrict__ tab, size_t e, int n, float L[L_NF],
@@ -164,6 +168,13 @@ __global__ void __launch_bounds__(np32(N), N > 4 ? 1 : (CL == 2 ? 4 : 6))
       if (k == N) lift(5, i + Nq * j);
       // (C_s Delta)^2 with Delta = (element volume)^(1/3) / N, per node
       if (CL == 1 && P.closure == 1) eddy_nu<1>(gr, tab[C_CSD2 * NP], L[L_THV] + G[5], F, P.richardson, nut, Dt);
+      if (CL == 3) {
+        // Vreman with the curved element's own directional lengths
+        KF Fv = F;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) Fv.vr_d2[m] = tab[(C_VR + m) * NP];
+        eddy_nu<3>(gr, 0.f, L[L_THV] + G[5], Fv, P.richardson, nut, Dt);
+      }
     }
     if (CL == 2) {
       const float Delta = t < Np ? P.node32[(size_t)e * C_NF * NP + C_DELTA * NP + t] : 0.f;
@@ -508,6 +519,8 @@ template <int N>
 static void grad32c_order(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s) {
   if (P.closure == 2)
     grad32c_instance<N, 2>(S, TH, F2, P, s);
+  else if (P.closure == 3)
+    grad32c_instance<N, 3>(S, TH, F2, P, s);
   else
     grad32c_instance<N, 1>(S, TH, F2, P, s);
 }

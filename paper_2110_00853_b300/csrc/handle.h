@@ -95,6 +95,7 @@ struct cmles_t {
   float *geo32 = nullptr, *node32 = nullptr;
   double *wJn = nullptr;
   std::vector<double> hx_, hz_, hJ_, hJa_, hdelta_;
+  std::vector<double> hvr_;  // warped meshes: Vreman's Delta_m^2 per element (x, y, z)
 };
 
 namespace cmles_host {

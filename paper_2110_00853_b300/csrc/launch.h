@@ -35,7 +35,10 @@ cudaError_t launch_rhs32(const float *S, const float *F2, const float *TH, float
                          cudaStream_t s);
 
 // FP32 path on curvilinear (warped) meshes (dg_curved32.cu)
-enum { kCurvedNF = 24 };
+// per-node table of a warped mesh: fields per node (kCurvedNF), and the slots
+// of the per-element filter width Delta, (C_s Delta)^2 and Vreman's squared
+// directional lengths (three slots)
+enum { kCurvedNF = 27, kCurvedDelta = 22, kCurvedCsd2 = 23, kCurvedVr = 24 };
 cudaError_t launch_shadow32c(const double *Q64, float *S, float *TH, const KParams &P, int N, cudaStream_t s);
 cudaError_t launch_grad32c(const float *S, const float *TH, float *F2, const KParams &P, cudaStream_t s);
 cudaError_t launch_rhs32c(const float *S, const float *F2, const float *TH, float *dQ, double *Q64, float *Sout,

@@ -47,7 +47,6 @@ def test_create_rejects_unsupported_combinations_without_gpu_work():
     ERR_ARG = 1
     assert status(closure="mlp") == ERR_ARG                         # learned closure runs in the FP32 kernels
     assert status(mesh=dict(good, warp=True)) == ERR_ARG             # warped meshes run on the FP32 path
-    assert status(mesh=dict(good, warp=True), precision="fp32", closure="vreman") == ERR_ARG
     P = cmles.make_params({}, "fp64")
     P.flux = 7
     m = cmles.make_mesh(good)

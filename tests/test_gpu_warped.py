@@ -29,11 +29,12 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def _setup(orc, fuzz=True, flux="rusanov", N=4, box=(8, 2, 8), dt=None):
+def _setup(orc, fuzz=True, flux="rusanov", N=4, box=(8, 2, 8), dt=None, closure="sl"):
     from paper_2110_00853_b300 import cmles
     m = _hill_box(*box, N=N)
     ph = _phys(m)
     ph["flux"] = flux
+    ph["closure"] = closure
     if dt is not None:
         ph["dt"] = dt
     S, Q, rr, pr, _ = orc.from_inputs(m, ph, I.case("c3"))
@@ -117,18 +118,23 @@ def test_warped_free_stream(orc, N):
     assert np.abs(R[inner][:, 1:4]).max() < 1e-5 * rho * 100.0 / 100.0
 
 
-@pytest.mark.parametrize("N,flux", [(2, "rusanov"), (3, "hllc"), (5, "rusanov"), (6, "roe"), (7, "rusanov")])
-def test_warped_other_orders_tendency_and_steps(orc, N, flux):
+@pytest.mark.parametrize("N,flux,closure", [(2, "rusanov", "sl"), (3, "hllc", "sl"), (5, "rusanov", "sl"),
+                                            (6, "roe", "sl"), (7, "rusanov", "sl"), (4, "rusanov", "vreman"),
+                                            (5, "hllc", "vreman")])
+def test_warped_other_orders_tendency_and_steps(orc, N, flux, closure):
     """The curvilinear FP32 kernels at orders other than 4 (above 4: CTAs of
-    np32(N) threads, arrays and metric tables padded to as many nodes) on a
-    window around the ridge: the tendency against the oracle's, in norm and
-    node by node, then four steps, with mass and energy conserved."""
+    np32(N) threads, arrays and metric tables padded to as many nodes), and
+    with the Vreman closure (each curved element's directional lengths: its
+    nodes' extent along x, y, z over N), on a window around the ridge: the
+    tendency against the oracle's, in norm and node by node, then four steps,
+    with mass and energy conserved."""
     dt = 0.02 * min(1.0, (4.0 / N) ** 2)      # the step shrinks with the smallest node spacing
-    m, S, Q, G = _setup(orc, flux=flux, N=N, box=(8, 2, 8) if N <= 4 else (6, 2, 6), dt=dt)
+    m, S, Q, G = _setup(orc, flux=flux, N=N, box=(8, 2, 8) if N <= 4 else (6, 2, 6), dt=dt, closure=closure)
     R_orc, _ = S.rhs(Q)
+    assert S.intermediates()["nut"].max() > 0.0      # the closure is active
     R_gpu = G.tendency(torch.from_numpy(Q).cuda()).cpu().numpy()
     errs = [_rel(R_gpu[:, v], R_orc[:, v]) for v in range(5)]
-    print("warped fp32 N", N, flux, "rel L2", errs)
+    print("warped fp32 N", N, flux, closure, "rel L2", errs)
     for v in range(5):
         assert errs[v] <= 1e-5, (v, errs)
         assert np.abs(R_gpu[:, v] - R_orc[:, v]).max() <= 1e-4 * np.abs(R_orc[:, v]).max(), v
